@@ -1,0 +1,363 @@
+"""FP64 CPU oracle for the LSQML ptychography hot path (Pty-Chi, arXiv 2510.20929).
+
+TEST INFRASTRUCTURE ONLY. Nothing on the product path may import or call this
+module: only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use it. It shares no code with the CUDA library; both sides only
+share the seeded input generators, which hold none of the method's arithmetic.
+
+Everything here is plain numpy in float64 / complex128, written to be read
+against the paper, not to be fast:
+
+* Forward model (Sec. 2.1; Eq. 4's F(o, p, Lambda); the exit wave psi = p * o
+  named under Eq. 2): per scan position j the object patch o_j = S_j(O) is cut
+  out at a sub-pixel position, multiplied by each incoherent probe mode P_k,
+  propagated to the far field with a unitary 2-D DFT and the modes are summed
+  incoherently, I_j = sum_k |F(P_k o_j)|^2.
+* Gaussian data term (Eq. 1, amplitude MSE, unnormalised) and its gradient
+  (Eq. 2, the conjugate probe times the exit-wave change), plus the Poisson
+  negative log-likelihood.
+* The LSQML reconstructor named in Sec. 2.2 (self-adaptive step sizes) with
+  the illumination preconditioner of Sec. 1 / Sec. 4, one minibatch at a time
+  (per-batch update, Sec. 2.2 third bullet for the non-compact sampler).
+
+The paper does not print LSQML's update equations. The readings used here
+(bilinear sub-pixel shift, unitary FFT without fftshift, probe-centre
+positions, relative preconditioner regularisers, Tikhonov-regularised 2x2
+step solve, alpha-weighted object scatter, mean-alpha probe step, the
+Poisson exit-wave step) are the repository's documented readings of the
+method; parity of the full iteration against Pty-Chi itself is unpinned
+(no code or printed numbers exist to pin it to). Every other function is
+pinned by the CPU tests (brute-force DFT, Parseval, adjoint dot products,
+finite differences, closed-form special cases, brute-force step search,
+convergence on noiseless data).
+
+Conventions
+-----------
+* Object O: complex [H, W]; probe P: complex [M, N, N]; positions pos:
+  float [J, 2] in (y, x) order, the probe centre in object pixels.
+* Tile origin t = floor(r - N/2), fraction f = r - N/2 - t in [0, 1); the
+  bilinear tile spans (N+1) x (N+1) object pixels starting at t, which must
+  lie inside the object.
+* F is the unitary ("ortho") 2-D DFT with DC at index [0, 0]; measured
+  intensities are stored in that order.
+* Gradients follow the complex convention grad = 2 dL/dz* (PyTorch's), so a
+  real perturbation changes the loss by Re<grad, dz>.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+GAUSSIAN = 0
+POISSON = 1
+
+
+# ---------------------------------------------------------------------------
+# Unitary 2-D DFT (the far-field propagator of the forward model, Sec. 2.1).
+# ---------------------------------------------------------------------------
+def dft2(x: np.ndarray) -> np.ndarray:
+    """Unitary 2-D DFT over the last two axes, DC at [0, 0] (no fftshift)."""
+    return np.fft.fft2(np.asarray(x, dtype=np.complex128), norm="ortho")
+
+
+def idft2(X: np.ndarray) -> np.ndarray:
+    """Inverse of :func:`dft2` (its adjoint, since the transform is unitary)."""
+    return np.fft.ifft2(np.asarray(X, dtype=np.complex128), norm="ortho")
+
+
+# ---------------------------------------------------------------------------
+# Sub-pixel patch extraction S_j and its adjoint S_j^T (object class routine,
+# Sec. 2.1: "object patch extraction/update").
+# ---------------------------------------------------------------------------
+def tile_origin(r, N: int):
+    """Integer tile origin t = floor(r - N/2) and fraction f = r - N/2 - t."""
+    r = np.asarray(r, dtype=np.float64)
+    s = r - N / 2.0
+    t = np.floor(s)
+    return t.astype(np.int64), s - t
+
+
+def in_bounds(r, N: int, H: int, W: int) -> bool:
+    """True when the (N+1)^2 bilinear tile of position r lies inside [H, W]."""
+    t, _ = tile_origin(r, N)
+    return bool(t[0] >= 0 and t[1] >= 0 and t[0] + N + 1 <= H and t[1] + N + 1 <= W)
+
+
+def _corners(O: np.ndarray, t, N: int):
+    ty, tx = int(t[0]), int(t[1])
+    O00 = O[ty:ty + N, tx:tx + N]
+    O01 = O[ty:ty + N, tx + 1:tx + N + 1]
+    O10 = O[ty + 1:ty + N + 1, tx:tx + N]
+    O11 = O[ty + 1:ty + N + 1, tx + 1:tx + N + 1]
+    return O00, O01, O10, O11
+
+
+def extract(O: np.ndarray, r, N: int) -> np.ndarray:
+    """o_j = S_j(O): bilinear interpolation of O on the N x N grid t + f + (a, b)."""
+    t, f = tile_origin(r, N)
+    if not in_bounds(r, N, O.shape[0], O.shape[1]):
+        raise ValueError("position outside the object")
+    fy, fx = f
+    O00, O01, O10, O11 = _corners(O, t, N)
+    return ((1 - fy) * (1 - fx) * O00 + (1 - fy) * fx * O01
+            + fy * (1 - fx) * O10 + fy * fx * O11)
+
+
+def extract_dr(O: np.ndarray, r, N: int):
+    """Derivatives (d o_j / d y, d o_j / d x) of the bilinear patch w.r.t. the position."""
+    t, f = tile_origin(r, N)
+    fy, fx = f
+    O00, O01, O10, O11 = _corners(O, t, N)
+    d_dy = (1 - fx) * (O10 - O00) + fx * (O11 - O01)
+    d_dx = (1 - fy) * (O01 - O00) + fy * (O11 - O10)
+    return d_dy, d_dx
+
+
+def scatter(patch: np.ndarray, r, H: int, W: int) -> np.ndarray:
+    """S_j^T: adds the N x N patch back into an H x W canvas with the bilinear weights."""
+    N = patch.shape[-1]
+    t, f = tile_origin(r, N)
+    if not in_bounds(r, N, H, W):
+        raise ValueError("position outside the object")
+    fy, fx = f
+    ty, tx = int(t[0]), int(t[1])
+    out = np.zeros((H, W), dtype=np.result_type(patch.dtype, np.float64))
+    out[ty:ty + N, tx:tx + N] += (1 - fy) * (1 - fx) * patch
+    out[ty:ty + N, tx + 1:tx + N + 1] += (1 - fy) * fx * patch
+    out[ty + 1:ty + N + 1, tx:tx + N] += fy * (1 - fx) * patch
+    out[ty + 1:ty + N + 1, tx + 1:tx + N + 1] += fy * fx * patch
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Forward model: I_j = sum_k |F(P_k * S_j(O))|^2 (Sec. 2.1, Eq. 4).
+# ---------------------------------------------------------------------------
+def exit_waves(O, P, r):
+    """psi_jk = P_k * o_j for one position (array [M, N, N])."""
+    N = P.shape[-1]
+    return P * extract(O, r, N)[None]
+
+
+def forward(O: np.ndarray, P: np.ndarray, pos: np.ndarray) -> np.ndarray:
+    """Predicted far-field intensities [J, N, N], DC at [0, 0]."""
+    J, N = pos.shape[0], P.shape[-1]
+    out = np.empty((J, N, N), dtype=np.float64)
+    for j in range(J):
+        Psi = dft2(exit_waves(O, P, pos[j]))
+        out[j] = np.sum(np.abs(Psi) ** 2, axis=0)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Data terms. Gaussian = Eq. 1 without its 1/(BHW) prefactor, with eps inside
+# the square root so that its derivative is exact; Poisson = negative
+# log-likelihood up to a data-only constant.
+# ---------------------------------------------------------------------------
+def pattern_loss(I, I_m, noise: int, eps: float) -> float:
+    I = np.asarray(I, np.float64)
+    I_m = np.asarray(I_m, np.float64)
+    if noise == GAUSSIAN:
+        return float(np.sum((np.sqrt(I + eps) - np.sqrt(I_m)) ** 2))
+    if noise == POISSON:
+        return float(np.sum(I - I_m * np.log(I + eps)))
+    raise ValueError("noise model")
+
+
+def dloss_dI(I, I_m, noise: int, eps: float) -> np.ndarray:
+    """dL/dI per detector pixel for the two data terms above."""
+    if noise == GAUSSIAN:
+        return 1.0 - np.sqrt(I_m) / np.sqrt(I + eps)
+    if noise == POISSON:
+        return 1.0 - I_m / (I + eps)
+    raise ValueError("noise model")
+
+
+def modulus_ratio(I, I_m, noise: int, eps: float) -> np.ndarray:
+    """rho such that the projected far field is Psi' = rho * Psi for every mode.
+
+    Gaussian: the magnitude is replaced by the measured amplitude (the psi' of
+    Eq. 2). Poisson: half a gradient step on the likelihood, rho = 1 + (I_m/I - 1)/2.
+    """
+    if noise == GAUSSIAN:
+        return np.sqrt(I_m) / np.sqrt(I + eps)
+    if noise == POISSON:
+        return 1.0 + 0.5 * (I_m / (I + eps) - 1.0)
+    raise ValueError("noise model")
+
+
+# ---------------------------------------------------------------------------
+# Gradients (Eq. 2 generalised to probe and positions; AD reconstructor, Sec. 2.2).
+# ---------------------------------------------------------------------------
+def vjp(O, P, pos, G):
+    """Gradients of L through the forward model given G = dL/dI [J, N, N].
+
+    grad_Psi_k = 2 G Psi_k; grad_psi_k = F^H grad_Psi_k;
+    grad_o_j = sum_k conj(P_k) grad_psi_k; grad_O = sum_j S_j^T grad_o_j;
+    grad_P_k = sum_j conj(o_j) grad_psi_jk; dL/dr_j = Re sum conj(grad_o_j) d o_j/d r.
+    """
+    H, W = O.shape
+    M, N = P.shape[0], P.shape[-1]
+    J = pos.shape[0]
+    gO = np.zeros((H, W), np.complex128)
+    gP = np.zeros((M, N, N), np.complex128)
+    gr = np.zeros((J, 2), np.float64)
+    for j in range(J):
+        o = extract(O, pos[j], N)
+        Psi = dft2(P * o[None])
+        gpsi = idft2(2.0 * G[j][None] * Psi)
+        go = np.sum(np.conj(P) * gpsi, axis=0)
+        gO += scatter(go, pos[j], H, W)
+        gP += np.conj(o)[None] * gpsi
+        d_dy, d_dx = extract_dr(O, pos[j], N)
+        gr[j, 0] = np.real(np.sum(np.conj(go) * d_dy))
+        gr[j, 1] = np.real(np.sum(np.conj(go) * d_dx))
+    return gO, gP, gr
+
+
+def loss_and_gradients(O, P, pos, I_m, noise: int = GAUSSIAN, eps: float = 0.0):
+    """Total loss sum_j L_j and its gradients w.r.t. object, probe modes and positions."""
+    I = forward(O, P, pos)
+    loss = sum(pattern_loss(I[j], I_m[j], noise, eps) for j in range(pos.shape[0]))
+    G = dloss_dI(I, I_m, noise, eps)
+    gO, gP, gr = vjp(O, P, pos, G)
+    return loss, gO, gP, gr
+
+
+# ---------------------------------------------------------------------------
+# LSQML (Sec. 2.2; object preconditioner Sec. 1 and Sec. 4).
+# ---------------------------------------------------------------------------
+@dataclass
+class LsqmlOptions:
+    noise: int = GAUSSIAN
+    batch: int = 256
+    delta_o: float = 1e-3      # relative: delta_O = delta_o * max(illumination)
+    delta_p: float = 1e-3      # relative: delta_P = delta_p * max(sum_j |o_j|^2)
+    lam: float = 1e-6          # 2x2 Tikhonov term, relative to trace(A)/2
+    eps: float = 0.0           # added to I_pred in the data term
+    update_object: bool = True
+    update_probe: bool = True
+
+
+def step_solve(A11, A12, A22, b1, b2, lam):
+    """Per-position step sizes (alpha_O, alpha_P) from the 2x2 normal equations.
+
+    A is regularised by lam * trace(A)/2 on the diagonal. If the determinant is
+    not positive, each step falls back to its own 1x1 solve (zero when the
+    curvature is zero).
+    """
+    tr = 0.5 * (A11 + A22)
+    a11 = A11 + lam * tr
+    a22 = A22 + lam * tr
+    det = a11 * a22 - A12 * A12
+    if det > 0.0:
+        return (a22 * b1 - A12 * b2) / det, (a11 * b2 - A12 * b1) / det
+    return (b1 / a11 if a11 > 0 else 0.0), (b2 / a22 if a22 > 0 else 0.0)
+
+
+def lsqml_batch(O, P, pos, I_m, idx, opts: LsqmlOptions, record: dict | None = None):
+    """One LSQML minibatch over the positions ``idx``; returns (O, P, loss, alpha).
+
+    Steps, per position j of the batch and modes k:
+      o_j = S_j(O); psi_jk = P_k o_j; Psi_jk = F psi_jk; I_j = sum_k |Psi_jk|^2;
+      chi_jk = F^{-1}[(rho_j - 1) Psi_jk] (= F^{-1} Psi'_jk - psi_jk);
+      g_j = sum_k conj(P_k) chi_jk;  h_jk = conj(o_j) chi_jk.
+    Batch accumulators and preconditioned directions:
+      dO_acc = sum_j S_j^T g_j;  illum = sum_j S_j^T sum_k |P_k|^2;
+      dP_acc_k = sum_j h_jk;  Dp = sum_j |o_j|^2;
+      dO_hat = dO_acc / (illum + delta_O);  dP_k = dP_acc_k / (Dp + delta_P).
+    Step sizes: u_jk = S_j(dO_hat) P_k, v_jk = o_j dP_k; A and b are the normal
+    equations of min ||chi_j - a_O u_j - a_P v_j||^2 summed over modes and pixels.
+    Update: O += sum_j S_j^T(alpha_O,j g_j) / (illum + delta_O);
+            P_k += mean_j(alpha_P,j) dP_k.
+    """
+    H, W = O.shape
+    M, N = P.shape[0], P.shape[-1]
+    idx = [int(i) for i in idx]
+    B = len(idx)
+    Sp = np.sum(np.abs(P) ** 2, axis=0)
+
+    loss = 0.0
+    o_all, chi_all, g_all = [], [], []
+    dO_acc = np.zeros((H, W), np.complex128)
+    illum = np.zeros((H, W), np.float64)
+    dP_acc = np.zeros((M, N, N), np.complex128)
+    Dp = np.zeros((N, N), np.float64)
+    for j in idx:
+        o = extract(O, pos[j], N)
+        psi = P * o[None]
+        Psi = dft2(psi)
+        I = np.sum(np.abs(Psi) ** 2, axis=0)
+        loss += pattern_loss(I, I_m[j], opts.noise, opts.eps)
+        rho = modulus_ratio(I, I_m[j], opts.noise, opts.eps)
+        chi = idft2((rho - 1.0)[None] * Psi)
+        g = np.sum(np.conj(P) * chi, axis=0)
+        dO_acc += scatter(g, pos[j], H, W)
+        illum += scatter(Sp, pos[j], H, W)
+        dP_acc += np.conj(o)[None] * chi
+        Dp += np.abs(o) ** 2
+        o_all.append(o)
+        chi_all.append(chi)
+        g_all.append(g)
+
+    delta_O = opts.delta_o * float(np.max(illum))
+    delta_P = opts.delta_p * float(np.max(Dp))
+    dO_hat = dO_acc / (illum + delta_O)
+    if not opts.update_object:
+        dO_hat = np.zeros_like(dO_hat)
+    if opts.update_probe:
+        dP = dP_acc / (Dp + delta_P)[None]
+    else:
+        dP = np.zeros_like(dP_acc)
+
+    alpha = np.zeros((B, 2), np.float64)
+    for i, j in enumerate(idx):
+        o, chi = o_all[i], chi_all[i]
+        u = extract(dO_hat, pos[j], N)[None] * P
+        v = o[None] * dP
+        A11 = float(np.sum(np.abs(u) ** 2))
+        A12 = float(np.real(np.sum(np.conj(u) * v)))
+        A22 = float(np.sum(np.abs(v) ** 2))
+        b1 = float(np.real(np.sum(np.conj(u) * chi)))
+        b2 = float(np.real(np.sum(np.conj(v) * chi)))
+        alpha[i] = step_solve(A11, A12, A22, b1, b2, opts.lam)
+
+    O_new = O.copy()
+    if opts.update_object:
+        upd = np.zeros((H, W), np.complex128)
+        for i, j in enumerate(idx):
+            upd += scatter(alpha[i, 0] * g_all[i], pos[j], H, W)
+        O_new = O + upd / (illum + delta_O)
+    P_new = P.copy()
+    if opts.update_probe:
+        P_new = P + float(np.mean(alpha[:, 1])) * dP
+
+    if record is not None:
+        record.update(dict(dO_acc=dO_acc, illum=illum, dP_acc=dP_acc, Dp=Dp,
+                           delta_O=delta_O, delta_P=delta_P, dO_hat=dO_hat, dP=dP,
+                           chi=np.stack(chi_all), g=np.stack(g_all), alpha=alpha))
+    return O_new, P_new, loss, alpha
+
+
+def lsqml_epoch(O, P, pos, I_m, order, opts: LsqmlOptions):
+    """One epoch: minibatches of ``opts.batch`` positions taken from ``order`` in turn."""
+    O = np.asarray(O, np.complex128).copy()
+    P = np.asarray(P, np.complex128).copy()
+    order = np.asarray(order)
+    J = order.shape[0]
+    loss = 0.0
+    alpha = np.zeros((pos.shape[0], 2), np.float64)
+    for b0 in range(0, J, opts.batch):
+        idx = order[b0:b0 + opts.batch]
+        O, P, l, a = lsqml_batch(O, P, pos, I_m, idx, opts)
+        loss += l
+        alpha[idx] = a
+    return O, P, loss, alpha
+
+
+def align_global_phase(O, O_ref, mask=None):
+    """Multiply O by the unit phase e^{i phi} minimising ||O e^{i phi} - O_ref|| on mask."""
+    if mask is None:
+        mask = np.ones(O.shape, bool)
+    c = np.sum(np.conj(O[mask]) * O_ref[mask])
+    return O * (c / abs(c)) if abs(c) > 0 else O

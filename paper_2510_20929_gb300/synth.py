@@ -1,0 +1,187 @@
+"""Seeded synthetic inputs shaped like the paper's ptychography workloads.
+
+This module generates inputs only: objects, probe modes, scan positions, batch
+orders and Poisson counts. It holds none of the reconstruction arithmetic
+(no patch extraction, no propagation, no data term), so that the CPU oracle
+and the CUDA library can both be fed from it without sharing method code.
+Measured intensities are made by the caller: it propagates the true object
+with its own forward model and passes the noiseless intensities to
+:func:`poisson_counts`.
+
+Recipes (all float64 numpy, seeded with ``numpy.random.default_rng``):
+
+* object: amplitude U[0.8, 1]; phase = white noise smoothed by a Gaussian of
+  ``phase_sigma`` px (periodic boundary), rescaled to +-``phase_max`` rad.
+* single-mode probe: Gaussian amplitude exp(-rho^2 / (2 sigma^2)) times the
+  quadratic phase exp(i q rho^2), rho measured from the window centre N/2.
+* multi-mode probe: Hermite-Gaussian modes H_m(sqrt2 y/w) H_n(sqrt2 x/w)
+  exp(-rho^2/w^2) with the same quadratic phase, orthonormalised by
+  Gram-Schmidt and scaled to the requested power fractions.
+* positions: a jittered raster, or a Fermat spiral r_n = c sqrt(n),
+  theta_n = n * 137.508 deg, both given as probe centres (y, x) in object px.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GOLDEN_ANGLE_DEG = 137.508
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(int(seed))
+
+
+def make_object(H: int, W: int, seed: int, amp_lo: float = 0.8, amp_hi: float = 1.0,
+                phase_sigma: float = 3.0, phase_max: float = 0.5,
+                amp_sigma: float | None = None) -> np.ndarray:
+    """Complex [H, W] object: U[amp_lo, amp_hi] amplitude, smoothed random phase.
+
+    With ``amp_sigma`` the amplitude is smoothed white noise mapped onto
+    [amp_lo, amp_hi] instead of independent uniform draws.
+    """
+    from scipy.ndimage import gaussian_filter
+
+    g = rng(seed)
+    amp = g.uniform(amp_lo, amp_hi, size=(H, W))
+    if amp_sigma is not None:
+        a = gaussian_filter(g.standard_normal((H, W)), sigma=amp_sigma, mode="wrap")
+        amp = amp_lo + (amp_hi - amp_lo) * (a - a.min()) / (a.max() - a.min())
+    noise = g.standard_normal((H, W))
+    ph = gaussian_filter(noise, sigma=phase_sigma, mode="wrap")
+    ph = ph * (phase_max / np.max(np.abs(ph)))
+    return amp * np.exp(1j * ph)
+
+
+def _window_coords(N: int):
+    a = np.arange(N, dtype=np.float64) - N / 2.0
+    return np.meshgrid(a, a, indexing="ij")
+
+
+def gaussian_probe(N: int, sigma: float = 10.0, quad_phase: float = 0.01) -> np.ndarray:
+    """Single-mode probe [1, N, N]: Gaussian amplitude with a quadratic phase."""
+    y, x = _window_coords(N)
+    rho2 = y * y + x * x
+    return (np.exp(-rho2 / (2.0 * sigma * sigma)) * np.exp(1j * quad_phase * rho2))[None]
+
+
+def _hermite(n: int, t: np.ndarray) -> np.ndarray:
+    """Physicists' Hermite polynomial H_n by the three-term recurrence."""
+    h0 = np.ones_like(t)
+    if n == 0:
+        return h0
+    h1 = 2.0 * t
+    for k in range(1, n):
+        h0, h1 = h1, 2.0 * t * h1 - 2.0 * k * h0
+    return h1
+
+
+HG_ORDERS = [(0, 0), (1, 0), (0, 1), (1, 1), (2, 0), (0, 2), (2, 1), (1, 2),
+             (3, 0), (0, 3), (2, 2), (3, 1), (1, 3), (4, 0), (0, 4), (3, 2)]
+
+
+def orthonormalise(modes: np.ndarray) -> np.ndarray:
+    """Modified Gram-Schmidt over the flattened modes (float64/complex128)."""
+    M = modes.shape[0]
+    out = np.array(modes, dtype=np.complex128, copy=True).reshape(M, -1)
+    for k in range(M):
+        for i in range(k):
+            out[k] -= np.vdot(out[i], out[k]) * out[i]
+        out[k] /= np.linalg.norm(out[k])
+    return out.reshape(modes.shape)
+
+
+def hg_probe(N: int, powers, waist: float = 25.0, quad_phase: float = 0.01,
+             total_power: float | None = None) -> np.ndarray:
+    """Incoherent probe [M, N, N] of Hermite-Gaussian modes with power fractions ``powers``."""
+    powers = np.asarray(powers, np.float64)
+    powers = powers / powers.sum()
+    y, x = _window_coords(N)
+    rho2 = y * y + x * x
+    s = math.sqrt(2.0) / waist
+    modes = []
+    for k in range(len(powers)):
+        m, n = HG_ORDERS[k]
+        modes.append(_hermite(m, s * y) * _hermite(n, s * x) * np.exp(-rho2 / waist ** 2)
+                     * np.exp(1j * quad_phase * rho2))
+    modes = orthonormalise(np.stack(modes))
+    if total_power is None:
+        total_power = math.pi * waist * waist / 2.0
+    return modes * np.sqrt(powers * total_power)[:, None, None]
+
+
+def raster_positions(ny: int, nx: int, step: float, center, jitter: float, seed: int) -> np.ndarray:
+    """Jittered raster of probe centres [ny*nx, 2] (y, x), centred on ``center``."""
+    g = rng(seed)
+    iy, ix = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    y = center[0] + (iy.ravel() - (ny - 1) / 2.0) * step
+    x = center[1] + (ix.ravel() - (nx - 1) / 2.0) * step
+    pos = np.stack([y, x], axis=1)
+    pos += g.uniform(-jitter, jitter, size=pos.shape)
+    return pos
+
+
+def fermat_spiral(J: int, c: float, center) -> np.ndarray:
+    """Fermat spiral of probe centres [J, 2] (y, x): r_n = c sqrt(n), theta_n = n * golden angle."""
+    n = np.arange(J, dtype=np.float64)
+    r = c * np.sqrt(n)
+    th = np.deg2rad(GOLDEN_ANGLE_DEG) * n
+    return np.stack([center[0] + r * np.sin(th), center[1] + r * np.cos(th)], axis=1)
+
+
+def random_order(J: int, seed: int) -> np.ndarray:
+    """Random minibatch order (a permutation of 0..J-1), int32."""
+    return rng(seed).permutation(J).astype(np.int32)
+
+
+def poisson_counts(I_true: np.ndarray, seed: int) -> np.ndarray:
+    """Poisson-sampled counts with mean ``I_true`` (float64 array of non-negative means)."""
+    return rng(seed).poisson(np.maximum(I_true, 0.0)).astype(np.float64)
+
+
+def count_scale(total_intensity: float, total_counts: float) -> float:
+    """Factor that maps a total predicted intensity onto ``total_counts`` detector counts."""
+    return float(total_counts) / float(total_intensity)
+
+
+# ---------------------------------------------------------------------------
+# Workloads (probe, true object, positions) for the paper-shaped configurations.
+# ---------------------------------------------------------------------------
+def workload_raster64(seed: int = 1001):
+    """Plain LSQML case: probe 64^2 (sigma 10 px, 0.01 rad/px^2), object 256^2,
+    100 positions on a 10 x 10 raster with 16 px steps and +-0.5 px jitter."""
+    H = W = 256
+    N = 64
+    obj = make_object(H, W, seed)
+    probe = gaussian_probe(N, sigma=10.0, quad_phase=0.01)
+    pos = raster_positions(10, 10, 16.0, (H / 2.0, W / 2.0), 0.5, seed + 7)
+    return dict(name="raster64", H=H, W=W, N=N, M=1, J=100, batch=100,
+                object=obj, probe=probe, pos=pos, total_counts=1e6, counts_per="all")
+
+
+def workload_spiral128(seed: int = 1002, J: int = 4096):
+    """Batched LSQML case: 5 Hermite-Gaussian modes (60/20/10/6/4 %), probe 128^2,
+    object 1024^2, 4096 Fermat-spiral positions (c = 6.9 px), batch 256."""
+    H = W = 1024
+    N = 128
+    obj = make_object(H, W, seed)
+    probe = hg_probe(N, [0.60, 0.20, 0.10, 0.06, 0.04], waist=25.0, quad_phase=0.01)
+    pos = fermat_spiral(J, 6.9, (H / 2.0, W / 2.0))
+    return dict(name="spiral128", H=H, W=W, N=N, M=5, J=J, batch=256,
+                object=obj, probe=probe, pos=pos, total_counts=1e6, counts_per="pattern")
+
+
+def workload_small(N: int = 16, M: int = 2, H: int = 40, W: int = 44, J: int = 12,
+                   seed: int = 7, step: float = 4.0):
+    """Small seeded problem for parity tests: raster positions with sub-pixel jitter."""
+    obj = make_object(H, W, seed, phase_sigma=1.5)
+    if M == 1:
+        probe = gaussian_probe(N, sigma=N / 6.0, quad_phase=0.02)
+    else:
+        probe = hg_probe(N, np.linspace(1.0, 0.3, M), waist=N / 5.0, quad_phase=0.02)
+    ny = int(math.ceil(math.sqrt(J)))
+    nx = int(math.ceil(J / ny))
+    pos = raster_positions(ny, nx, step, (H / 2.0, W / 2.0), 0.45, seed + 3)[:J]
+    return dict(name=f"small{N}", H=H, W=W, N=N, M=M, J=J, batch=J,
+                object=obj, probe=probe, pos=pos)

@@ -1,0 +1,64 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that a pin catches each.
+
+Every case monkeypatches one oracle function with a subtly wrong variant (a
+dropped normalisation, transposed fractions, a flipped sign, a missing
+conjugate) and re-runs a pin from test_oracle_pins; the pin must fail.
+"""
+import numpy as np
+import pytest
+
+from oracle import ptycho_oracle as orc
+from tests import test_oracle_pins as pins
+
+
+def _fails(fn, *args):
+    with pytest.raises(AssertionError):
+        fn(*args)
+
+
+def test_missing_fft_normalisation_is_caught(monkeypatch):
+    monkeypatch.setattr(orc, "dft2", lambda x: np.fft.fft2(np.asarray(x, complex)))
+    _fails(pins.test_dft2_parseval_and_inverse)
+    _fails(pins.test_dft2_matches_bruteforce_definition, 8)
+
+
+def test_transposed_bilinear_fractions_are_caught(monkeypatch):
+    real = orc.tile_origin
+
+    def swapped(r, N):
+        t, f = real(r, N)
+        return t, f[::-1]
+
+    monkeypatch.setattr(orc, "tile_origin", swapped)
+    _fails(pins.test_bilinear_reproduces_affine_functions_exactly)
+
+
+def test_flipped_exit_wave_change_is_caught(monkeypatch):
+    real = orc.modulus_ratio
+    monkeypatch.setattr(orc, "modulus_ratio", lambda I, Im, n, e: 2.0 - real(I, Im, n, e))
+    _fails(pins.test_eq2_object_gradient_is_minus_twice_conj_probe_times_exit_wave_change)
+
+
+def test_wrong_cross_term_sign_in_step_solve_is_caught(monkeypatch):
+    real = orc.step_solve
+    monkeypatch.setattr(orc, "step_solve", lambda a, c, d, b1, b2, lam: real(a, -c, d, b1, b2, lam))
+    _fails(pins.test_step_sizes_solve_the_least_squares_problem)
+
+
+def test_missing_probe_conjugate_in_gradient_is_caught(monkeypatch):
+    real_vjp = orc.vjp
+
+    def wrong(O, P, pos, G):
+        gO, gP, gr = real_vjp(O, P, pos, G)
+        # recompute the object gradient with P instead of conj(P)
+        H, W = O.shape
+        N = P.shape[-1]
+        gO = np.zeros((H, W), complex)
+        for j in range(pos.shape[0]):
+            o = orc.extract(O, pos[j], N)
+            gpsi = orc.idft2(2.0 * G[j][None] * orc.dft2(P * o[None]))
+            gO += orc.scatter(np.sum(P * gpsi, axis=0), pos[j], H, W)
+        return gO, gP, gr
+
+    monkeypatch.setattr(orc, "vjp", wrong)
+    _fails(pins.test_gradients_match_central_finite_differences, orc.GAUSSIAN)

@@ -1,0 +1,324 @@
+"""Pins of the FP64 oracle against what the mathematics fixes (no GPU).
+
+Each test checks the oracle against something other than itself: a brute-force
+DFT, Parseval's identity, exact reproduction of affine functions by bilinear
+interpolation, adjoint dot products, closed-form far fields, central finite
+differences, a library least-squares solve of the step-size problem, the
+single-position reduction to plain CDI, and convergence on noiseless data.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ptycho_oracle as orc
+from paper_2510_20929_gb300 import synth
+
+
+def crandn(g, *shape):
+    return g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+
+# --------------------------------------------------------------------------- DFT
+@pytest.mark.parametrize("N", [2, 4, 8, 16])
+def test_dft2_matches_bruteforce_definition(N):
+    g = np.random.default_rng(N)
+    x = crandn(g, N, N)
+    X = orc.dft2(x)
+    a = np.arange(N)
+    ref = np.zeros((N, N), complex)
+    for u in range(N):
+        for v in range(N):
+            ph = np.exp(-2j * math.pi * (u * a[:, None] + v * a[None, :]) / N)
+            ref[u, v] = np.sum(x * ph) / N
+    assert np.max(np.abs(X - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_dft2_parseval_and_inverse():
+    g = np.random.default_rng(1)
+    x = crandn(g, 3, 32, 32)
+    X = orc.dft2(x)
+    assert abs(np.sum(np.abs(X) ** 2) - np.sum(np.abs(x) ** 2)) < 1e-10 * np.sum(np.abs(x) ** 2)
+    assert np.max(np.abs(orc.idft2(X) - x)) < 1e-12
+
+
+# --------------------------------------------------------------------------- S_j
+def test_integer_position_is_a_crop():
+    g = np.random.default_rng(2)
+    O = crandn(g, 30, 37)
+    N = 8
+    r = np.array([13.0, 21.0])            # t = (9, 17), f = 0
+    o = orc.extract(O, r, N)
+    assert np.array_equal(o, O[9:17, 17:25])
+
+
+def test_bilinear_reproduces_affine_functions_exactly():
+    H, W, N = 33, 41, 8
+    yy, xx = np.meshgrid(np.arange(H, dtype=float), np.arange(W, dtype=float), indexing="ij")
+    c0, cy, cx = 0.3 - 0.2j, 1.7 + 0.4j, -0.9 + 2.1j
+    O = c0 + cy * yy + cx * xx
+    r = np.array([15.37, 19.81])
+    o = orc.extract(O, r, N)
+    a = np.arange(N, dtype=float)
+    ey = r[0] - N / 2 + a[:, None]        # exact sample coordinates t + f + a
+    ex = r[1] - N / 2 + a[None, :]
+    assert np.max(np.abs(o - (c0 + cy * ey + cx * ex))) < 1e-12
+    d_dy, d_dx = orc.extract_dr(O, r, N)
+    assert np.max(np.abs(d_dy - cy)) < 1e-12 and np.max(np.abs(d_dx - cx)) < 1e-12
+
+
+def test_scatter_is_the_adjoint_of_extract():
+    g = np.random.default_rng(3)
+    H, W, N = 29, 34, 8
+    O = crandn(g, H, W)
+    y = crandn(g, N, N)
+    r = np.array([12.61, 17.29])
+    lhs = np.vdot(y, orc.extract(O, r, N))
+    rhs = np.vdot(orc.scatter(y, r, H, W), O)
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+    # partition of unity: the weights of each patch pixel sum to one
+    assert abs(np.sum(orc.scatter(np.ones((N, N)), r, H, W)) - N * N) < 1e-11
+
+
+def test_extract_dr_matches_central_differences():
+    g = np.random.default_rng(4)
+    O = crandn(g, 30, 30)
+    N, r, h = 8, np.array([14.3, 13.6]), 1e-6
+    d_dy, d_dx = orc.extract_dr(O, r, N)
+    fy = (orc.extract(O, r + [h, 0], N) - orc.extract(O, r - [h, 0], N)) / (2 * h)
+    fx = (orc.extract(O, r + [0, h], N) - orc.extract(O, r - [0, h], N)) / (2 * h)
+    assert np.max(np.abs(fy - d_dy)) < 1e-8 and np.max(np.abs(fx - d_dx)) < 1e-8
+
+
+def test_bounds_rule():
+    assert orc.in_bounds([4.0, 4.0], 8, 9, 9)         # t = 0, t + N + 1 = 9
+    assert not orc.in_bounds([3.9, 4.0], 8, 9, 9)     # t = -1
+    assert not orc.in_bounds([5.0, 4.0], 8, 9, 9)     # t + N + 1 = 10 > 9
+
+
+# --------------------------------------------------------------------------- forward model
+def test_forward_parseval_over_modes():
+    w = synth.workload_small(N=16, M=3, J=5)
+    I = orc.forward(w["object"], w["probe"], w["pos"])
+    for j in range(5):
+        o = orc.extract(w["object"], w["pos"][j], 16)
+        ref = np.sum(np.abs(w["probe"] * o[None]) ** 2)
+        assert abs(I[j].sum() - ref) < 1e-11 * ref
+
+
+def test_forward_plane_wave_closed_form():
+    # probe = plane wave with frequency (u0, v0), object constant c -> a single
+    # bright pixel of intensity N^2 |c|^2 at (u0, v0), zero elsewhere
+    N, u0, v0, c = 16, 3, 11, 0.7 - 0.4j
+    a = np.arange(N)
+    P = np.exp(2j * math.pi * (u0 * a[:, None] + v0 * a[None, :]) / N)[None]
+    O = np.full((40, 40), c)
+    I = orc.forward(O, P, np.array([[20.3, 19.6]]))[0]
+    ref = np.zeros((N, N))
+    ref[u0, v0] = N * N * abs(c) ** 2
+    assert np.max(np.abs(I - ref)) < 1e-10
+
+
+def test_forward_delta_probe_closed_form():
+    # probe = delta at (a0, b0) -> flat pattern |o(a0, b0)|^2 / N^2
+    N, a0, b0 = 8, 2, 5
+    P = np.zeros((1, N, N), complex)
+    P[0, a0, b0] = 1.0
+    g = np.random.default_rng(5)
+    O = crandn(g, 20, 20)
+    r = np.array([9.25, 10.5])
+    o = orc.extract(O, r, N)
+    I = orc.forward(O, P, r[None])[0]
+    assert np.max(np.abs(I - abs(o[a0, b0]) ** 2 / N ** 2)) < 1e-13
+
+
+# --------------------------------------------------------------------------- gradients
+def _fd_problem(noise, seed=6):
+    g = np.random.default_rng(seed)
+    w = synth.workload_small(N=8, M=2, H=24, W=24, J=4, seed=seed, step=3.0)
+    O_true, P, pos = w["object"], w["probe"], w["pos"]
+    I_m = synth.poisson_counts(50.0 * orc.forward(O_true, P, pos) / orc.forward(O_true, P, pos).mean(), seed)
+    P = P * math.sqrt(50.0 / orc.forward(O_true, P, pos).mean())
+    O = O_true * (1 + 0.1 * crandn(g, *O_true.shape))
+    return O, P, pos, I_m
+
+
+@pytest.mark.parametrize("noise", [orc.GAUSSIAN, orc.POISSON])
+def test_gradients_match_central_finite_differences(noise):
+    O, P, pos, I_m = _fd_problem(noise)
+    eps = 1e-3
+    L, gO, gP, gr = orc.loss_and_gradients(O, P, pos, I_m, noise, eps)
+    g = np.random.default_rng(7)
+    h = 1e-6
+
+    def L_at(O_, P_, pos_):
+        return orc.loss_and_gradients(O_, P_, pos_, I_m, noise, eps)[0]
+
+    dO = crandn(g, *O.shape)
+    fd = (L_at(O + h * dO, P, pos) - L_at(O - h * dO, P, pos)) / (2 * h)
+    assert abs(fd - np.real(np.vdot(gO, dO))) < 1e-6 * abs(fd)
+    dP = crandn(g, *P.shape)
+    fd = (L_at(O, P + h * dP, pos) - L_at(O, P - h * dP, pos)) / (2 * h)
+    assert abs(fd - np.real(np.vdot(gP, dP))) < 1e-6 * abs(fd)
+    dr = g.standard_normal(pos.shape)
+    fd = (L_at(O, P, pos + h * dr) - L_at(O, P, pos - h * dr)) / (2 * h)
+    assert abs(fd - np.sum(gr * dr)) < 1e-5 * abs(fd)
+
+
+def test_eq2_object_gradient_is_minus_twice_conj_probe_times_exit_wave_change():
+    # Eq. 2: dL/do* = -p* (psi' - psi) per patch (unnormalised), i.e. the
+    # PyTorch-convention gradient is -2 sum_k P_k* chi_k, and the LSQML object
+    # accumulator is minus half the object gradient.
+    O, P, pos, I_m = _fd_problem(orc.GAUSSIAN, seed=8)
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=4, eps=1e-3)
+    rec = {}
+    orc.lsqml_batch(O, P, pos, I_m, range(4), opts, rec)
+    _, gO, _, _ = orc.loss_and_gradients(O, P, pos, I_m, orc.GAUSSIAN, 1e-3)
+    assert np.max(np.abs(rec["dO_acc"] + 0.5 * gO)) < 1e-10 * np.max(np.abs(gO))
+    # psi' - psi computed the long way round: back-propagate the replaced modulus
+    o = orc.extract(O, pos[0], 8)
+    psi = P * o[None]
+    Psi = orc.dft2(psi)
+    I = np.sum(np.abs(Psi) ** 2, axis=0)
+    psi_new = orc.idft2(Psi * np.sqrt(I_m[0]) / np.sqrt(I + 1e-3))
+    assert np.max(np.abs(rec["chi"][0] - (psi_new - psi))) < 1e-12
+
+
+def test_loss_and_gradient_vanish_at_the_truth():
+    w = synth.workload_small(N=8, M=2, H=24, W=24, J=4, step=3.0)
+    I = orc.forward(w["object"], w["probe"], w["pos"])
+    L, gO, gP, gr = orc.loss_and_gradients(w["object"], w["probe"], w["pos"], I, orc.GAUSSIAN, 0.0)
+    assert L < 1e-20 and np.max(np.abs(gO)) < 1e-10 and np.max(np.abs(gr)) < 1e-9
+
+
+def test_gradient_is_sum_over_position_subsets():
+    # Sec. 2.3: summing per-worker gradients equals the full-batch gradient.
+    O, P, pos, I_m = _fd_problem(orc.GAUSSIAN, seed=9)
+    _, gO, gP, gr = orc.loss_and_gradients(O, P, pos, I_m, orc.GAUSSIAN, 1e-3)
+    parts = [orc.loss_and_gradients(O, P, pos[s], I_m[s], orc.GAUSSIAN, 1e-3) for s in ([0, 3], [1, 2])]
+    assert np.max(np.abs(parts[0][1] + parts[1][1] - gO)) < 1e-12 * np.max(np.abs(gO))
+    assert np.max(np.abs(parts[0][2] + parts[1][2] - gP)) < 1e-12 * np.max(np.abs(gP))
+
+
+# --------------------------------------------------------------------------- LSQML step sizes
+def test_step_sizes_solve_the_least_squares_problem():
+    # alpha_j minimises sum_k ||chi_jk - a_O u_jk - a_P v_jk||^2; compare every
+    # position of a batch with numpy's least-squares on the stacked real system.
+    O, P, pos, I_m = _fd_problem(orc.GAUSSIAN, seed=10)
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=4, eps=1e-3, lam=0.0)
+    rec = {}
+    _, _, _, alpha = orc.lsqml_batch(O, P, pos, I_m, range(4), opts, rec)
+    for j in range(4):
+        u = (orc.extract(rec["dO_hat"], pos[j], 8)[None] * P).ravel()
+        v = (orc.extract(O, pos[j], 8)[None] * rec["dP"]).ravel()
+        chi = rec["chi"][j].ravel()
+        Amat = np.concatenate([np.stack([u.real, v.real], 1), np.stack([u.imag, v.imag], 1)])
+        bvec = np.concatenate([chi.real, chi.imag])
+        ref = np.linalg.lstsq(Amat, bvec, rcond=None)[0]
+        assert np.max(np.abs(alpha[j] - ref)) < 1e-8 * np.max(np.abs(ref))
+
+
+def test_step_solve_grid_search_and_fallbacks():
+    g = np.random.default_rng(11)
+    u, v, chi = crandn(g, 50), crandn(g, 50), crandn(g, 50)
+    A11, A22 = np.sum(abs(u) ** 2), np.sum(abs(v) ** 2)
+    A12 = np.real(np.vdot(u, v))
+    b1, b2 = np.real(np.vdot(u, chi)), np.real(np.vdot(v, chi))
+    a = np.array(orc.step_solve(A11, A12, A22, b1, b2, 0.0))
+    q = lambda x: np.sum(np.abs(chi - x[0] * u - x[1] * v) ** 2)
+    grid = np.linspace(-0.05, 0.05, 101)
+    best = min(q(a + [dy, dx]) for dy in grid for dx in grid)
+    assert q(a) <= best + 1e-12
+    # a zero second direction reduces to the 1x1 solve b1 / A11 (lam = 0: det = 0)
+    assert orc.step_solve(A11, 0.0, 0.0, b1, 0.0, 0.0) == (b1 / A11, 0.0)
+    assert orc.step_solve(0.0, 0.0, 0.0, 0.0, 0.0, 1e-6) == (0.0, 0.0)
+
+
+def test_single_position_reduces_to_plain_cdi():
+    # One position at an integer offset, probe known: the LSQML object update
+    # is alpha * conj(P) chi / (|P|^2 + delta) on the patch, with the 1x1 step
+    # alpha = Re<u, chi> / ||u||^2 (lam = 0, probe not updated).
+    g = np.random.default_rng(12)
+    N, H, W = 16, 24, 26
+    P = synth.gaussian_probe(N, sigma=4.0, quad_phase=0.05) * 3.0
+    O_true = synth.make_object(H, W, 3, phase_sigma=1.0)
+    r = np.array([12.0, 13.0])                           # t = (4, 5), f = 0
+    I_m = orc.forward(O_true, P, r[None])
+    O = O_true * (1 + 0.2 * crandn(g, H, W))
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=1, delta_o=1e-2, lam=0.0,
+                            update_probe=False)
+    O_new, P_new, loss, alpha = orc.lsqml_batch(O, P, r[None], I_m, [0], opts)
+    # plain single-view CDI on the crop, written without S_j or the batch sums
+    p = P[0]
+    o = O[4:20, 5:21]
+    Psi = np.fft.fft2(p * o) / N
+    Psi_new = np.sqrt(I_m[0]) * np.exp(1j * np.angle(Psi))
+    chi = np.fft.ifft2(Psi_new) * N - p * o
+    w = np.abs(p) ** 2 + 1e-2 * np.max(np.abs(p) ** 2)
+    d = np.conj(p) * chi / w
+    u = d * p
+    a = np.real(np.vdot(u, chi)) / np.vdot(u, u).real
+    ref = O.copy()
+    ref[4:20, 5:21] += a * d
+    assert abs(alpha[0, 0] - a) < 1e-10 * abs(a) and alpha[0, 1] == 0.0
+    assert np.max(np.abs(O_new - ref)) < 1e-12
+    assert np.array_equal(P_new, P)
+
+
+# --------------------------------------------------------------------------- whole iteration
+def _noiseless_problem(probe_error):
+    N, H, W = 32, 80, 80
+    O_true = synth.make_object(H, W, 21, phase_sigma=2.0, amp_sigma=2.0)
+    P_true = synth.gaussian_probe(N, sigma=5.0, quad_phase=0.02) * 4.0
+    pos = synth.raster_positions(7, 7, 5.0, (H / 2, W / 2), 0.5, 22)
+    I_m = orc.forward(O_true, P_true, pos)
+    O0 = np.ones((H, W), complex)
+    ramp = 1 + probe_error * (np.arange(N)[None, :, None] / N)
+    return O_true, P_true, pos, I_m, O0, P_true * ramp
+
+
+def test_lsqml_converges_to_the_truth_on_noiseless_data():
+    # known probe, flat start, random minibatches of 16: the object converges to
+    # the truth up to the global phase, and the loss falls by three decades
+    O_true, P, pos, I_m, O, _ = _noiseless_problem(0.0)
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=16, eps=1e-12, delta_o=0.1,
+                            update_probe=False)
+    order = synth.random_order(pos.shape[0], 5)
+    illum = sum(orc.scatter(np.abs(P[0]) ** 2, r, *O.shape) for r in pos)
+    mask = illum > 0.5 * illum.max()
+
+    def err(O_):
+        A = orc.align_global_phase(O_, O_true, mask)
+        return np.linalg.norm((A - O_true)[mask]) / np.linalg.norm(O_true[mask])
+
+    e0 = err(O)
+    losses = []
+    for _ in range(40):
+        O, _, L, _ = orc.lsqml_epoch(O, P, pos, I_m, order, opts)
+        losses.append(L)
+    assert err(O) < 0.02 * e0
+    assert losses[-1] < 1e-3 * losses[0]
+
+
+def test_lsqml_joint_probe_update_reduces_the_loss():
+    O_true, P_true, pos, I_m, O, P = _noiseless_problem(0.1)
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=16, eps=1e-12, delta_o=0.1, delta_p=0.1)
+    order = synth.random_order(pos.shape[0], 6)
+    losses = []
+    for _ in range(10):
+        O, P, L, _ = orc.lsqml_epoch(O, P, pos, I_m, order, opts)
+        losses.append(L)
+    assert losses[-1] < 0.02 * losses[0]
+
+
+def test_poisson_lsqml_reduces_the_loss():
+    O_true, P, pos, I_m, O, _ = _noiseless_problem(0.0)
+    I_m = synth.poisson_counts(I_m, 3)
+    opts = orc.LsqmlOptions(noise=orc.POISSON, batch=16, eps=1e-6, delta_o=0.1,
+                            update_probe=False)
+    order = synth.random_order(pos.shape[0], 7)
+    losses = []
+    for _ in range(6):
+        O, _, L, _ = orc.lsqml_epoch(O, P, pos, I_m, order, opts)
+        losses.append(L)
+    assert losses[-1] < losses[0]
