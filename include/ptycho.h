@@ -1,0 +1,152 @@
+/* ptycho.h -- C ABI of the GB300 LSQML ptychography hot path.
+ *
+ * The library implements the data-parallel per-scan-position path of the
+ * LSQML reconstructor described in Pty-Chi (Du et al., arXiv 2510.20929):
+ * the far-field forward model F(o, p, Lambda) of Sec. 2.1 / Eq. 4 (sub-pixel
+ * object patch, incoherent probe modes, unitary 2-D FFT, intensity), the
+ * amplitude data term of Eq. 1 (and the Poisson likelihood), its gradient
+ * (Eq. 2, extended to the probe modes and the scan positions), and one LSQML
+ * epoch: modulus-projected exit-wave update, illumination-preconditioned
+ * object and probe directions (Sec. 1, Sec. 4), per-position least-squares
+ * step sizes (Sec. 2.2), and the minibatch update.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All array arguments are DEVICE pointers owned by the caller, row-major
+ *   and contiguous. "complex64" means interleaved (re, im) float pairs.
+ * - Object O: complex64 [H, W]. Probe P: complex64 [M, N, N] (M incoherent
+ *   modes). Positions: float32 [J, 2], (y, x) probe centre in object pixels.
+ *   Intensities: float32 [J, N, N] with the zero frequency at [0, 0]
+ *   (no fftshift).
+ * - Patch extraction is bilinear: t = floor(r - N/2), f = r - N/2 - t; the
+ *   (N+1) x (N+1) tile starting at t must lie inside the object, i.e.
+ *   0 <= r - N/2 < H - N (same for x). The far-field propagator is the
+ *   unitary ("ortho") 2-D DFT.
+ * - Gradients follow the complex convention grad = 2 dL/dz* (PyTorch's), so
+ *   dL = Re<grad, dz> for a perturbation dz.
+ * - Supported window sizes N: 16, 32, 64, 128. Modes: 1 <= M <= 16.
+ * - The library never allocates device memory. Scratch lives in a caller
+ *   workspace of ptycho_workspace_bytes() bytes (256-byte aligned).
+ * - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *   default stream). Argument errors are returned synchronously before any
+ *   launch. Data errors found on the device (a position whose tile leaves the
+ *   object, an `order` entry outside [0, J), a negative or non-finite measured
+ *   intensity) are recorded in the workspace and returned by
+ *   ptycho_status_read(); such positions are skipped, never read out of bounds.
+ */
+#ifndef PTYCHO_H
+#define PTYCHO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int32_t H, W; /* object size */
+  int32_t N;    /* probe window (N x N) */
+  int32_t M;    /* incoherent probe modes */
+  int32_t J;    /* scan positions */
+} ptycho_dims;
+
+typedef enum {
+  PTYCHO_OK = 0,
+  PTYCHO_ERR_ARG = 1,         /* null pointer, bad size, bad option */
+  PTYCHO_ERR_BOUNDS = 2,      /* (device) a position's tile leaves the object, or a bad order entry */
+  PTYCHO_ERR_NONFINITE = 3,   /* (device) negative or non-finite measured intensity */
+  PTYCHO_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  PTYCHO_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+  PTYCHO_ERR_UNSUPPORTED = 6, /* window size or mode count not built */
+  PTYCHO_ERR_WORKSPACE = 7    /* workspace missing, misaligned or too small */
+} ptycho_status;
+
+typedef enum {
+  PTYCHO_NOISE_GAUSSIAN = 0, /* L = sum (sqrt(I + eps) - sqrt(I_m))^2 (Eq. 1, unnormalised) */
+  PTYCHO_NOISE_POISSON = 1,  /* L = sum (I - I_m log(I + eps)) */
+  PTYCHO_NOISE_VJP = 2       /* ptycho_adjoint only: the `meas` array holds dL/dI */
+} ptycho_noise;
+
+typedef struct {
+  int32_t noise;          /* PTYCHO_NOISE_GAUSSIAN or PTYCHO_NOISE_POISSON */
+  int32_t batch;          /* minibatch size B >= 1 */
+  int32_t update_object;  /* 0/1 */
+  int32_t update_probe;   /* 0/1 */
+  int32_t reserved[4];    /* must be zero */
+  double delta_o;         /* object preconditioner damping, relative to max(illumination) */
+  double delta_p;         /* probe preconditioner damping, relative to max(sum_j |o_j|^2) */
+  double lambda_reg;      /* 2x2 step-size Tikhonov term, relative to trace/2 */
+  double eps;             /* added to the predicted intensity in the data term */
+} ptycho_lsqml_opts;
+
+/* Bytes of workspace needed by every entry point below for these dimensions
+ * and minibatch size (ptycho_adjoint processes positions in chunks of
+ * `batch`). Returns 0 for unsupported dimensions. */
+size_t ptycho_workspace_bytes(const ptycho_dims* dims, int32_t batch);
+
+/* Clears the workspace header (its device status word). Call once on a fresh
+ * workspace before the first entry point that uses it. */
+ptycho_status ptycho_workspace_init(void* ws, size_t ws_bytes, void* stream);
+
+/* Forward model (Sec. 2.1, Eq. 4): I_pred[j] = sum_k |F(P_k * S_j(O))|^2 for
+ * all J positions. I_pred: float32 [J, N, N], overwritten. Positions that
+ * fail the bounds rule leave their I_pred block untouched. */
+ptycho_status ptycho_forward(const ptycho_dims* dims, const float* object, const float* probe,
+                             const float* pos, float* I_pred, void* ws, size_t ws_bytes,
+                             void* stream);
+
+/* Data term and its gradients (Eq. 1 and Eq. 2, extended to probe modes and
+ * positions), exit waves recomputed, never stored. `meas` is the measured
+ * intensity for GAUSSIAN/POISSON, or dL/dI for VJP. All outputs are
+ * ACCUMULATED (+=), so sums over position subsets add up to the full-set
+ * result; zero them first for a plain evaluation:
+ *   g_object complex64 [H, W], g_probe complex64 [M, N, N],
+ *   g_pos float32 [J, 2] (may be NULL), loss float64 scalar (may be NULL;
+ *   untouched for VJP). Positions are processed in chunks of `batch`. */
+ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const float* probe,
+                             const float* pos, const float* meas, int32_t noise, double eps,
+                             int32_t batch, float* g_object, float* g_probe, float* g_pos,
+                             double* loss, void* ws, size_t ws_bytes, void* stream);
+
+/* One LSQML epoch (Sec. 2.2): minibatches of opts->batch positions taken from
+ * `order` (int32 [J], a permutation or any list of indices in [0, J); NULL =
+ * 0..J-1). Per minibatch: exit-wave changes chi_jk, preconditioned object and
+ * probe directions, per-position FP64 2x2 step sizes, then
+ *   O += sum_j S_j^T(alpha_O,j g_j) / (illum + delta_O),
+ *   P_k += mean_j(alpha_P,j) dP_k.
+ * object and probe are updated in place. loss (float64 scalar, may be NULL)
+ * receives the epoch's data term summed over positions, each evaluated at the
+ * state its minibatch started from. alpha (float64 [J, 2], may be NULL)
+ * receives (alpha_O, alpha_P) per position. */
+ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* probe,
+                                 const float* pos, const float* meas, const int32_t* order,
+                                 const ptycho_lsqml_opts* opts, double* loss, double* alpha,
+                                 void* ws, size_t ws_bytes, void* stream);
+
+/* Same epoch with HOST buffers: copies pos, meas and order (and the object and
+ * probe) into device staging areas carved from `ws` (ws_bytes must be at least
+ * ptycho_host_workspace_bytes()), runs the epoch on `stream`, copies object,
+ * probe and loss back, and synchronises the stream before returning. Host
+ * buffers should be pinned for full copy bandwidth. */
+size_t ptycho_host_workspace_bytes(const ptycho_dims* dims, int32_t batch);
+ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, float* probe,
+                                      const float* pos, const float* meas, const int32_t* order,
+                                      const ptycho_lsqml_opts* opts, double* loss, void* ws,
+                                      size_t ws_bytes, void* stream);
+
+/* Synchronises `stream`, returns (and clears) the device-side status recorded
+ * in `ws` since the last read: PTYCHO_OK, PTYCHO_ERR_BOUNDS or
+ * PTYCHO_ERR_NONFINITE (bounds reported first), or PTYCHO_ERR_CUDA. */
+ptycho_status ptycho_status_read(void* ws, void* stream);
+
+/* Static description of a status code. */
+const char* ptycho_status_string(ptycho_status status);
+
+/* Library version string. */
+const char* ptycho_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTYCHO_H */

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libptycho (argument marshalling only).
+
+Every function here validates tensor dtypes, shapes and devices, passes raw
+device pointers and the current CUDA stream to the C ABI declared in
+include/ptycho.h, and raises :class:`PtychoError` on a non-OK status. All
+arithmetic runs in the library's sm_103a kernels; there is no CPU or PyTorch
+fallback, and loading fails loudly if the library has not been built.
+
+Tensor conventions: object complex64 [H, W]; probe complex64 [M, N, N];
+positions float32 [J, 2] (y, x) probe centres; intensities float32 [J, N, N]
+with the zero frequency at [0, 0]; batch order int32 [J].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libptycho.so")
+
+GAUSSIAN, POISSON, VJP = 0, 1, 2
+_NOISE = {"gaussian": GAUSSIAN, "poisson": POISSON, "vjp": VJP}
+
+STATUS = {0: "PTYCHO_OK", 1: "PTYCHO_ERR_ARG", 2: "PTYCHO_ERR_BOUNDS", 3: "PTYCHO_ERR_NONFINITE",
+          4: "PTYCHO_ERR_CUDA", 5: "PTYCHO_ERR_TIMEOUT", 6: "PTYCHO_ERR_UNSUPPORTED",
+          7: "PTYCHO_ERR_WORKSPACE"}
+
+
+class PtychoError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({status_string(status)})")
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("M", ctypes.c_int32), ("J", ctypes.c_int32)]
+
+
+class LsqmlOpts(ctypes.Structure):
+    _fields_ = [("noise", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("update_object", ctypes.c_int32), ("update_probe", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4),
+                ("delta_o", ctypes.c_double), ("delta_p", ctypes.c_double),
+                ("lambda_reg", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+
+
+def lib() -> ctypes.CDLL:
+    """Load libptycho.so (once); raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        dims_p = ctypes.POINTER(Dims)
+        opts_p = ctypes.POINTER(LsqmlOpts)
+        sigs = {
+            "ptycho_workspace_bytes": (ctypes.c_size_t, [dims_p, ctypes.c_int32]),
+            "ptycho_host_workspace_bytes": (ctypes.c_size_t, [dims_p, ctypes.c_int32]),
+            "ptycho_workspace_init": (ctypes.c_int, [_P, ctypes.c_size_t, _P]),
+            "ptycho_forward": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+            "ptycho_adjoint": (ctypes.c_int, [dims_p, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double,
+                                              ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+            "ptycho_lsqml_epoch": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, opts_p, _P, _P, _P,
+                                                  ctypes.c_size_t, _P]),
+            "ptycho_lsqml_epoch_host": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, opts_p, _P, _P,
+                                                       ctypes.c_size_t, _P]),
+            "ptycho_status_read": (ctypes.c_int, [_P, _P]),
+            "ptycho_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "ptycho_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def status_string(status: int) -> str:
+    return lib().ptycho_status_string(int(status)).decode()
+
+
+def _check(st: int, where: str) -> None:
+    if st != 0:
+        raise PtychoError(st, where)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _P(s.cuda_stream)
+
+
+def _ptr(t):
+    return _P(t.data_ptr()) if t is not None else _P(0)
+
+
+def _need(t, name, dtype, shape=None, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def dims_of(obj, probe, pos) -> Dims:
+    H, W = obj.shape
+    M, N, N2 = probe.shape
+    if N != N2:
+        raise ValueError("probe modes must be square")
+    return Dims(H, W, N, M, pos.shape[0])
+
+
+class Workspace:
+    """Caller-owned device scratch for the library (a uint8 torch tensor, 256-B aligned)."""
+
+    def __init__(self, nbytes: int, device, stream=None):
+        self.nbytes = int(nbytes)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        self.ptr = self.buf.data_ptr() + off
+        _check(lib().ptycho_workspace_init(_P(self.ptr), self.nbytes, _stream(stream)), "workspace_init")
+
+    def status(self, stream=None) -> int:
+        """Synchronise and return (and clear) the device-side status."""
+        return lib().ptycho_status_read(_P(self.ptr), _stream(stream))
+
+
+_ws_cache: dict = {}
+
+
+def workspace(dims: Dims, batch: int, device, host: bool = False) -> Workspace:
+    """A cached workspace large enough for these dimensions and minibatch size."""
+    fn = lib().ptycho_host_workspace_bytes if host else lib().ptycho_workspace_bytes
+    need = fn(ctypes.byref(dims), int(batch))
+    if need == 0:
+        raise PtychoError(6, "workspace_bytes")
+    key = (str(device), host)
+    ws = _ws_cache.get(key)
+    if ws is None or ws.nbytes < need:
+        ws = Workspace(need, device)
+        _ws_cache[key] = ws
+    return ws
+
+
+def _finish(ws: Workspace, where: str, check: bool):
+    if check:
+        _check(ws.status(), where)
+
+
+def forward(obj, probe, pos, *, check: bool = True):
+    """Predicted intensities I [J, N, N] = sum_k |F(P_k S_j(O))|^2."""
+    _need(obj, "object", torch.complex64)
+    _need(probe, "probe", torch.complex64, device=obj.device)
+    _need(pos, "positions", torch.float32, device=obj.device)
+    d = dims_of(obj, probe, pos)
+    I = torch.empty((d.J, d.N, d.N), dtype=torch.float32, device=obj.device)
+    ws = workspace(d, 1, obj.device)
+    _check(lib().ptycho_forward(ctypes.byref(d), _ptr(obj), _ptr(probe), _ptr(pos), _ptr(I),
+                                _P(ws.ptr), ws.nbytes, _stream()), "ptycho_forward")
+    _finish(ws, "ptycho_forward", check)
+    return I
+
+
+def adjoint(obj, probe, pos, meas, noise="gaussian", eps: float = 0.0, batch: int = 256, *,
+            positions_grad: bool = True, check: bool = True):
+    """Loss and gradients (grad = 2 dL/dz*): returns (loss, g_object, g_probe, g_pos).
+
+    ``noise`` is "gaussian", "poisson", or "vjp" (then ``meas`` holds dL/dI and
+    the returned loss is None).
+    """
+    nz = _NOISE[noise] if isinstance(noise, str) else int(noise)
+    _need(obj, "object", torch.complex64)
+    _need(probe, "probe", torch.complex64, device=obj.device)
+    _need(pos, "positions", torch.float32, device=obj.device)
+    d = dims_of(obj, probe, pos)
+    _need(meas, "meas", torch.float32, (d.J, d.N, d.N), device=obj.device)
+    B = max(1, min(int(batch), max(d.J, 1)))
+    gO = torch.zeros_like(obj)
+    gP = torch.zeros_like(probe)
+    gr = torch.zeros((d.J, 2), dtype=torch.float32, device=obj.device) if positions_grad else None
+    loss = torch.zeros((), dtype=torch.float64, device=obj.device)
+    ws = workspace(d, B, obj.device)
+    _check(lib().ptycho_adjoint(ctypes.byref(d), _ptr(obj), _ptr(probe), _ptr(pos), _ptr(meas), nz,
+                                float(eps), B, _ptr(gO), _ptr(gP), _ptr(gr),
+                                _ptr(loss) if nz != VJP else _P(0), _P(ws.ptr), ws.nbytes, _stream()),
+           "ptycho_adjoint")
+    _finish(ws, "ptycho_adjoint", check)
+    return (None if nz == VJP else loss), gO, gP, gr
+
+
+def make_opts(noise="gaussian", batch: int = 256, delta_o: float = 0.1, delta_p: float = 0.1,
+              lam: float = 1e-6, eps: float = 1e-9, update_object: bool = True,
+              update_probe: bool = True) -> LsqmlOpts:
+    o = LsqmlOpts()
+    o.noise = _NOISE[noise] if isinstance(noise, str) else int(noise)
+    o.batch = int(batch)
+    o.update_object = int(bool(update_object))
+    o.update_probe = int(bool(update_probe))
+    o.delta_o, o.delta_p, o.lambda_reg, o.eps = float(delta_o), float(delta_p), float(lam), float(eps)
+    return o
+
+
+def lsqml_epoch(obj, probe, pos, meas, order=None, opts: LsqmlOpts | None = None, *,
+                want_alpha: bool = False, check: bool = True, **kw):
+    """One LSQML epoch, updating ``obj`` and ``probe`` in place.
+
+    Returns (loss, alpha): loss is a float64 device scalar; alpha a float64
+    [J, 2] device tensor of (alpha_O, alpha_P) or None.
+    """
+    if opts is None:
+        opts = make_opts(**kw)
+    _need(obj, "object", torch.complex64)
+    _need(probe, "probe", torch.complex64, device=obj.device)
+    _need(pos, "positions", torch.float32, device=obj.device)
+    d = dims_of(obj, probe, pos)
+    _need(meas, "meas", torch.float32, (d.J, d.N, d.N), device=obj.device)
+    if order is not None:
+        _need(order, "order", torch.int32, (d.J,), device=obj.device)
+    loss = torch.zeros((), dtype=torch.float64, device=obj.device)
+    alpha = torch.zeros((pos.shape[0], 2), dtype=torch.float64, device=obj.device) if want_alpha else None
+    ws = workspace(d, opts.batch, obj.device)
+    _check(lib().ptycho_lsqml_epoch(ctypes.byref(d), _ptr(obj), _ptr(probe), _ptr(pos), _ptr(meas),
+                                    _ptr(order), ctypes.byref(opts), _ptr(loss), _ptr(alpha),
+                                    _P(ws.ptr), ws.nbytes, _stream()), "ptycho_lsqml_epoch")
+    _finish(ws, "ptycho_lsqml_epoch", check)
+    return loss, alpha
+
+
+def lsqml_epoch_host(obj, probe, pos, meas, order, opts: LsqmlOpts, device=None):
+    """LSQML epoch on HOST (CPU, ideally pinned) tensors through the host-buffer entry point.
+
+    ``obj`` and ``probe`` (complex64, CPU) are updated in place; returns the loss.
+    """
+    for t, name, dt in ((obj, "object", torch.complex64), (probe, "probe", torch.complex64),
+                        (pos, "positions", torch.float32), (meas, "meas", torch.float32)):
+        if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU {dt} tensor")
+    if order is not None and (order.device.type != "cpu" or order.dtype != torch.int32):
+        raise ValueError("order must be a CPU int32 tensor")
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    d = dims_of(obj, probe, pos)
+    ws = workspace(d, opts.batch, device, host=True)
+    loss = ctypes.c_double(0.0)
+    _check(lib().ptycho_lsqml_epoch_host(ctypes.byref(d), _ptr(obj), _ptr(probe), _ptr(pos), _ptr(meas),
+                                         _ptr(order), ctypes.byref(opts), ctypes.byref(loss),
+                                         _P(ws.ptr), ws.nbytes, _stream()), "ptycho_lsqml_epoch_host")
+    _check(ws.status(), "ptycho_lsqml_epoch_host")
+    return loss.value

@@ -1,0 +1,488 @@
+// C-ABI entry points of libptycho and the object/probe-frame kernels of the
+// LSQML minibatch (preconditioner maxima, probe direction, update).
+//
+// Per minibatch the epoch runs: k_pass1 (per position: forward model, data
+// term, chi, scatter of the object direction and illumination), k_max_illum
+// (max of the illumination for the relative damping delta_O), k_probe_reduce
+// (sum over the batch of conj(o_j) chi_jk and |o_j|^2), k_normP (preconditioned
+// probe direction and the per-pixel planes the step solve needs), k_pass2 (per
+// position: step sizes and the alpha-weighted object scatter), k_update
+// (object and probe update, accumulators cleared for the next batch).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <type_traits>
+
+#include "../../include/ptycho.h"
+#include "common.cuh"
+#include "launch.h"
+
+namespace ptycho {
+
+// ---------------------------------------------------------------------------
+// Object/probe-frame kernels (window size is a runtime argument here).
+// ---------------------------------------------------------------------------
+__global__ void k_init_epoch(int HW, float4* acc, float2* U, int NN, int M, const float2* probe,
+                             float2* dPacc, float* Dp, float* Sp, WsHeader* hdr) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += stride) {
+    acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    U[p] = make_float2(0.f, 0.f);
+  }
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += stride) {
+    float s = 0.f;
+    for (int k = 0; k < M; ++k) {
+      s += cabs2(probe[(size_t)k * NN + p]);
+      dPacc[(size_t)k * NN + p] = make_float2(0.f, 0.f);
+    }
+    Sp[p] = s;
+    Dp[p] = 0.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) memset(hdr->sc, 0, sizeof(hdr->sc));
+}
+
+__global__ void k_max_illum(const float4* acc, int HW, BatchScalars* sc) {
+  __shared__ float red[32];
+  float m = 0.f;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x)
+    m = fmaxf(m, acc[p].z);
+  m = block_max(m, red);
+  if (threadIdx.x == 0) atomicMax(&sc->max_illum, __float_as_uint(m));
+}
+
+// dPacc_k[p] += sum_{i in chunk} h_s[i][k][p];  Dp[p] += sum |o_s[i][p]|^2
+template <int MMAX>
+__global__ void k_probe_reduce(int NN, int M, int nb, int chunk, const float2* __restrict__ h_s,
+                               const float2* __restrict__ o_s, const int* __restrict__ valid,
+                               float2* dPacc, float* Dp) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= NN) return;
+  const int i0 = blockIdx.y * chunk, i1 = min(nb, i0 + chunk);
+  float2 s[MMAX];
+#pragma unroll
+  for (int k = 0; k < MMAX; ++k) s[k] = make_float2(0.f, 0.f);
+  float d = 0.f;
+  for (int i = i0; i < i1; ++i) {
+    if (!valid[i]) continue;
+    const float2* h = h_s + (size_t)i * M * NN + p;
+#pragma unroll
+    for (int k = 0; k < MMAX; ++k)
+      if (k < M) {
+        const float2 v = h[(size_t)k * NN];
+        s[k].x += v.x;
+        s[k].y += v.y;
+      }
+    if (Dp) d += cabs2(o_s[(size_t)i * NN + p]);
+  }
+#pragma unroll
+  for (int k = 0; k < MMAX; ++k)
+    if (k < M) atomicAdd(dPacc + (size_t)k * NN + p, s[k]);
+  if (Dp) atomicAdd(Dp + p, d);
+}
+
+// dP_k = dPacc_k / (Dp + delta_p max(Dp)); Cp = sum_k conj(P_k) dP_k; Sdp = sum_k |dP_k|^2
+__global__ void k_norm_probe(int NN, int M, const float2* dPacc, const float* Dp, const float2* probe,
+                             float delta_p, int update_probe, float2* dP, float2* Cp, float* Sdp) {
+  __shared__ float red[32];
+  float m = 0.f;
+  if (update_probe)
+    for (int p = threadIdx.x; p < NN; p += blockDim.x) m = fmaxf(m, Dp[p]);
+  m = block_max(m, red);
+  const float damp = delta_p * m;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += gridDim.x * blockDim.x) {
+    float2 c = make_float2(0.f, 0.f);
+    float sd = 0.f;
+    const float inv = update_probe ? 1.f / (Dp[p] + damp) : 0.f;
+    for (int k = 0; k < M; ++k) {
+      const size_t q = (size_t)k * NN + p;
+      const float2 v = update_probe ? cscale(dPacc[q], inv) : make_float2(0.f, 0.f);
+      dP[q] = v;
+      c = cadd(c, cmulc(probe[q], v));
+      sd += cabs2(v);
+    }
+    Cp[p] = c;
+    Sdp[p] = sd;
+  }
+}
+
+// O += U / (illum + delta_O); P_k += mean(alpha_P) dP_k; clear accumulators and
+// the next batch's scalar set; refresh Sp = sum_k |P_k|^2.
+__global__ void k_update(int HW, float2* obj, float4* acc, float2* U, float delta_o, int update_object,
+                         int NN, int M, float2* probe, const float2* dP, float2* dPacc, float* Dp, float* Sp,
+                         int update_probe, const BatchScalars* sc, BatchScalars* sc_next) {
+  const int stride = gridDim.x * blockDim.x;
+  const float damp = delta_o * __uint_as_float(sc->max_illum);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += stride) {
+    if (update_object) {
+      const float2 u = U[p];
+      const float inv = 1.f / (acc[p].z + damp);
+      float2 o = obj[p];
+      o.x = fmaf(u.x, inv, o.x);
+      o.y = fmaf(u.y, inv, o.y);
+      obj[p] = o;
+    }
+    acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    U[p] = make_float2(0.f, 0.f);
+  }
+  const float mean_ap = sc->count > 0 ? (float)(sc->sum_alpha_p / (double)sc->count) : 0.f;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += stride) {
+    float s = 0.f;
+    for (int k = 0; k < M; ++k) {
+      const size_t q = (size_t)k * NN + p;
+      float2 v = probe[q];
+      if (update_probe) {
+        const float2 d = dP[q];
+        v.x = fmaf(mean_ap, d.x, v.x);
+        v.y = fmaf(mean_ap, d.y, v.y);
+        probe[q] = v;
+      }
+      s += cabs2(v);
+      dPacc[q] = make_float2(0.f, 0.f);
+    }
+    Sp[p] = s;
+    Dp[p] = 0.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) memset(sc_next, 0, sizeof(BatchScalars));
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout.
+// ---------------------------------------------------------------------------
+struct Layout {
+  size_t hdr, acc, U, psi, o, g, h, dPacc, Dp, dP, Sp, Cp, Sdp, valid, total;
+};
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static Layout make_layout(const ptycho_dims& d, int B) {
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  const size_t HW = (size_t)d.H * d.W, NN = (size_t)d.N * d.N, M = d.M;
+  L.hdr = take(sizeof(WsHeader));
+  L.acc = take(HW * sizeof(float4));
+  L.U = take(HW * sizeof(float2));
+  L.psi = take((size_t)B * M * NN * sizeof(float2));
+  L.o = take((size_t)B * NN * sizeof(float2));
+  L.g = take((size_t)B * NN * sizeof(float2));
+  L.h = take((size_t)B * M * NN * sizeof(float2));
+  L.dPacc = take(M * NN * sizeof(float2));
+  L.Dp = take(NN * sizeof(float));
+  L.dP = take(M * NN * sizeof(float2));
+  L.Sp = take(NN * sizeof(float));
+  L.Cp = take(NN * sizeof(float2));
+  L.Sdp = take(NN * sizeof(float));
+  L.valid = take((size_t)B * sizeof(int));
+  L.total = off;
+  return L;
+}
+
+static bool supported_N(int N) { return N == 16 || N == 32 || N == 64 || N == 128; }
+
+static ptycho_status check_dims(const ptycho_dims* d) {
+  if (!d) return PTYCHO_ERR_ARG;
+  if (!supported_N(d->N) || d->M < 1 || d->M > 16) return PTYCHO_ERR_UNSUPPORTED;
+  if (d->H < d->N + 1 || d->W < d->N + 1 || d->J < 0) return PTYCHO_ERR_ARG;
+  if ((int64_t)d->H * d->W > ((int64_t)1 << 31) - 1) return PTYCHO_ERR_ARG;
+  return PTYCHO_OK;
+}
+
+static ptycho_status check_ws(void* ws, size_t have, size_t need) {
+  if (!ws || ((uintptr_t)ws & 255) != 0 || have < need) return PTYCHO_ERR_WORKSPACE;
+  return PTYCHO_OK;
+}
+
+template <class Fn>
+static cudaError_t dispatch_N(int N, Fn&& fn) {
+  switch (N) {
+    case 16: return fn(std::integral_constant<int, 16>());
+    case 32: return fn(std::integral_constant<int, 32>());
+    case 64: return fn(std::integral_constant<int, 64>());
+    case 128: return fn(std::integral_constant<int, 128>());
+  }
+  return cudaErrorInvalidValue;
+}
+
+static cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s) {
+  return dispatch_N(N, [&](auto c) { return launch_pass1<decltype(c)::value>(a, s); });
+}
+static cudaError_t pass2(int N, const Pass2Args& a, cudaStream_t s) {
+  return dispatch_N(N, [&](auto c) { return launch_pass2<decltype(c)::value>(a, s); });
+}
+
+static cudaError_t probe_reduce(int NN, int M, int nb, const float2* h_s, const float2* o_s, const int* valid,
+                                float2* dPacc, float* Dp, cudaStream_t s) {
+  const int chunk = 16;
+  dim3 grid((NN + 255) / 256, (nb + chunk - 1) / chunk);
+  if (M <= 4)
+    k_probe_reduce<4><<<grid, 256, 0, s>>>(NN, M, nb, chunk, h_s, o_s, valid, dPacc, Dp);
+  else if (M <= 8)
+    k_probe_reduce<8><<<grid, 256, 0, s>>>(NN, M, nb, chunk, h_s, o_s, valid, dPacc, Dp);
+  else
+    k_probe_reduce<16><<<grid, 256, 0, s>>>(NN, M, nb, chunk, h_s, o_s, valid, dPacc, Dp);
+  return cudaGetLastError();
+}
+
+static int grid_for(size_t n, int threads, int cap) {
+  size_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (int)(b > (size_t)cap ? cap : b);
+}
+
+struct Ptrs {
+  WsHeader* hdr;
+  float4* acc;
+  float2 *U, *psi, *o, *g, *h, *dPacc, *dP, *Cp;
+  float *Dp, *Sp, *Sdp;
+  int* valid;
+};
+
+static Ptrs carve(void* ws, const Layout& L) {
+  char* b = (char*)ws;
+  Ptrs p;
+  p.hdr = (WsHeader*)(b + L.hdr);
+  p.acc = (float4*)(b + L.acc);
+  p.U = (float2*)(b + L.U);
+  p.psi = (float2*)(b + L.psi);
+  p.o = (float2*)(b + L.o);
+  p.g = (float2*)(b + L.g);
+  p.h = (float2*)(b + L.h);
+  p.dPacc = (float2*)(b + L.dPacc);
+  p.Dp = (float*)(b + L.Dp);
+  p.dP = (float2*)(b + L.dP);
+  p.Sp = (float*)(b + L.Sp);
+  p.Cp = (float2*)(b + L.Cp);
+  p.Sdp = (float*)(b + L.Sdp);
+  p.valid = (int*)(b + L.valid);
+  return p;
+}
+
+static ptycho_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PTYCHO_OK : PTYCHO_ERR_CUDA; }
+
+static ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const float* pos,
+                               const float* meas, const int32_t* order, const ptycho_lsqml_opts& o,
+                               double* loss, double* alpha, void* ws, cudaStream_t s) {
+  const int B = o.batch, N = d.N, M = d.M, NN = N * N, HW = d.H * d.W;
+  const Layout L = make_layout(d, B);
+  Ptrs w = carve(ws, L);
+  cudaError_t e;
+  if (loss && (e = cudaMemsetAsync(loss, 0, sizeof(double), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  k_init_epoch<<<grid_for(HW > NN ? HW : NN, 256, 4 * 152), 256, 0, s>>>(HW, w.acc, w.U, NN, M, probe, w.dPacc,
+                                                                          w.Dp, w.Sp, w.hdr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  const int nbatch = (d.J + B - 1) / B;
+  for (int b = 0; b < nbatch; ++b) {
+    const int b0 = b * B, nb = (d.J - b0 < B) ? d.J - b0 : B;
+    BatchScalars* sc = &w.hdr->sc[b & 1];
+    BatchScalars* sc_next = &w.hdr->sc[(b + 1) & 1];
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.H = d.H; a.W = d.W; a.M = M; a.J = d.J;
+    a.obj = obj; a.probe = probe; a.pos = pos; a.meas = meas; a.order = order;
+    a.b0 = b0; a.nb = nb;
+    a.mode = (o.noise == PTYCHO_NOISE_POISSON) ? MODE_LSQML_POISSON : MODE_LSQML_GAUSS;
+    a.eps = (float)o.eps;
+    a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
+    a.Sp = w.Sp; a.acc = w.acc;
+    a.loss = loss; a.status = &w.hdr->status;
+    if ((e = pass1(N, a, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    k_max_illum<<<grid_for(HW, 256, 2 * 152), 256, 0, s>>>(w.acc, HW, sc);
+    if (o.update_probe) {
+      if ((e = probe_reduce(NN, M, nb, w.h, w.o, w.valid, w.dPacc, w.Dp, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    }
+    k_norm_probe<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p,
+                                                        o.update_probe, w.dP, w.Cp, w.Sdp);
+    Pass2Args q;
+    memset(&q, 0, sizeof(q));
+    q.H = d.H; q.W = d.W; q.M = M; q.J = d.J;
+    q.pos = pos; q.order = order; q.b0 = b0; q.nb = nb;
+    q.o_s = w.o; q.g_s = w.g; q.h_s = w.h; q.valid = w.valid;
+    q.acc = w.acc; q.Sp = w.Sp; q.Cp = w.Cp; q.Sdp = w.Sdp; q.dP = w.dP;
+    q.U = w.U; q.alpha_out = alpha; q.sc = sc;
+    q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
+    q.update_object = o.update_object; q.update_probe = o.update_probe;
+    if ((e = pass2(N, q, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    k_update<<<grid_for(HW > NN ? HW : NN, 256, 4 * 152), 256, 0, s>>>(
+        HW, obj, w.acc, w.U, (float)o.delta_o, o.update_object, NN, M, probe, w.dP, w.dPacc, w.Dp, w.Sp,
+        o.update_probe, sc, sc_next);
+    if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  }
+  return PTYCHO_OK;
+}
+
+static ptycho_status check_opts(const ptycho_lsqml_opts* o) {
+  if (!o || o->batch < 1 || (o->noise != PTYCHO_NOISE_GAUSSIAN && o->noise != PTYCHO_NOISE_POISSON))
+    return PTYCHO_ERR_ARG;
+  for (int i = 0; i < 4; ++i)
+    if (o->reserved[i] != 0) return PTYCHO_ERR_ARG;
+  if (!(o->delta_o >= 0.0) || !(o->delta_p >= 0.0) || !(o->lambda_reg >= 0.0) || !(o->eps >= 0.0))
+    return PTYCHO_ERR_ARG;
+  return PTYCHO_OK;
+}
+
+}  // namespace ptycho
+
+using namespace ptycho;
+
+extern "C" {
+
+const char* ptycho_version(void) { return "ptycho-gb300 0.1 (sm_103a)"; }
+
+const char* ptycho_status_string(ptycho_status s) {
+  switch (s) {
+    case PTYCHO_OK: return "ok";
+    case PTYCHO_ERR_ARG: return "invalid argument";
+    case PTYCHO_ERR_BOUNDS: return "scan position outside the object (or order entry out of range)";
+    case PTYCHO_ERR_NONFINITE: return "negative or non-finite measured intensity";
+    case PTYCHO_ERR_CUDA: return "CUDA runtime error";
+    case PTYCHO_ERR_TIMEOUT: return "device wait timed out";
+    case PTYCHO_ERR_UNSUPPORTED: return "unsupported window size or mode count";
+    case PTYCHO_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+  }
+  return "unknown status";
+}
+
+ptycho_status ptycho_workspace_init(void* ws, size_t ws_bytes, void* stream) {
+  if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < align256(sizeof(WsHeader))) return PTYCHO_ERR_WORKSPACE;
+  return cuda_status(cudaMemsetAsync(ws, 0, sizeof(WsHeader), (cudaStream_t)stream));
+}
+
+size_t ptycho_workspace_bytes(const ptycho_dims* dims, int32_t batch) {
+  if (check_dims(dims) != PTYCHO_OK || batch < 1) return 0;
+  return make_layout(*dims, batch).total;
+}
+
+ptycho_status ptycho_forward(const ptycho_dims* dims, const float* object, const float* probe, const float* pos,
+                             float* I_pred, void* ws, size_t ws_bytes, void* stream) {
+  ptycho_status st = check_dims(dims);
+  if (st != PTYCHO_OK) return st;
+  if (!object || !probe || (dims->J > 0 && (!pos || !I_pred))) return PTYCHO_ERR_ARG;
+  if ((st = check_ws(ws, ws_bytes, align256(sizeof(WsHeader)))) != PTYCHO_OK) return st;
+  if (dims->J == 0) return PTYCHO_OK;
+  WsHeader* hdr = (WsHeader*)ws;
+  BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.H = dims->H; a.W = dims->W; a.M = dims->M; a.J = dims->J;
+  a.obj = (const float2*)object; a.probe = (const float2*)probe; a.pos = pos;
+  a.b0 = 0; a.nb = dims->J; a.mode = MODE_FWD;
+  a.ipred = I_pred; a.status = &hdr->status;
+  return cuda_status(pass1(dims->N, a, (cudaStream_t)stream));
+}
+
+ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const float* probe, const float* pos,
+                             const float* meas, int32_t noise, double eps, int32_t batch, float* g_object,
+                             float* g_probe, float* g_pos, double* loss, void* ws, size_t ws_bytes,
+                             void* stream) {
+  ptycho_status st = check_dims(dims);
+  if (st != PTYCHO_OK) return st;
+  if (batch < 1 || !(eps >= 0.0)) return PTYCHO_ERR_ARG;
+  if (noise != PTYCHO_NOISE_GAUSSIAN && noise != PTYCHO_NOISE_POISSON && noise != PTYCHO_NOISE_VJP)
+    return PTYCHO_ERR_ARG;
+  if (!object || !probe || !g_object || !g_probe) return PTYCHO_ERR_ARG;
+  if (dims->J > 0 && (!pos || !meas)) return PTYCHO_ERR_ARG;
+  const Layout L = make_layout(*dims, batch);
+  if ((st = check_ws(ws, ws_bytes, L.total)) != PTYCHO_OK) return st;
+  Ptrs w = carve(ws, L);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int NN = dims->N * dims->N;
+  for (int b0 = 0; b0 < dims->J; b0 += batch) {
+    const int nb = (dims->J - b0 < batch) ? dims->J - b0 : batch;
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.H = dims->H; a.W = dims->W; a.M = dims->M; a.J = dims->J;
+    a.obj = (const float2*)object; a.probe = (const float2*)probe; a.pos = pos; a.meas = meas;
+    a.b0 = b0; a.nb = nb;
+    a.mode = noise == PTYCHO_NOISE_GAUSSIAN ? MODE_GRAD_GAUSS
+             : noise == PTYCHO_NOISE_POISSON ? MODE_GRAD_POISSON : MODE_VJP;
+    a.eps = (float)eps;
+    a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
+    a.gobj = (float2*)g_object; a.gpos = g_pos; a.loss = loss; a.status = &w.hdr->status;
+    if (pass1(dims->N, a, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if (probe_reduce(NN, dims->M, nb, w.h, w.o, w.valid, (float2*)g_probe, nullptr, s) != cudaSuccess)
+      return PTYCHO_ERR_CUDA;
+  }
+  return PTYCHO_OK;
+}
+
+ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* probe, const float* pos,
+                                 const float* meas, const int32_t* order, const ptycho_lsqml_opts* opts,
+                                 double* loss, double* alpha, void* ws, size_t ws_bytes, void* stream) {
+  ptycho_status st = check_dims(dims);
+  if (st != PTYCHO_OK) return st;
+  if ((st = check_opts(opts)) != PTYCHO_OK) return st;
+  if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
+  const Layout L = make_layout(*dims, opts->batch);
+  if ((st = check_ws(ws, ws_bytes, L.total)) != PTYCHO_OK) return st;
+  return run_epoch(*dims, (float2*)object, (float2*)probe, pos, meas, order, *opts, loss, alpha, ws,
+                   (cudaStream_t)stream);
+}
+
+static size_t host_extra(const ptycho_dims& d) {
+  const size_t HW = (size_t)d.H * d.W, NN = (size_t)d.N * d.N;
+  return align256(HW * 8) + align256((size_t)d.M * NN * 8) + align256((size_t)d.J * 8) +
+         align256((size_t)d.J * NN * 4) + align256((size_t)d.J * 4) + align256(8);
+}
+
+size_t ptycho_host_workspace_bytes(const ptycho_dims* dims, int32_t batch) {
+  if (check_dims(dims) != PTYCHO_OK || batch < 1) return 0;
+  return make_layout(*dims, batch).total + host_extra(*dims);
+}
+
+ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, float* probe, const float* pos,
+                                      const float* meas, const int32_t* order, const ptycho_lsqml_opts* opts,
+                                      double* loss, void* ws, size_t ws_bytes, void* stream) {
+  ptycho_status st = check_dims(dims);
+  if (st != PTYCHO_OK) return st;
+  if ((st = check_opts(opts)) != PTYCHO_OK) return st;
+  if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
+  const Layout L = make_layout(*dims, opts->batch);
+  if ((st = check_ws(ws, ws_bytes, L.total + host_extra(*dims))) != PTYCHO_OK) return st;
+  const ptycho_dims& d = *dims;
+  const size_t HW = (size_t)d.H * d.W, NN = (size_t)d.N * d.N;
+  char* b = (char*)ws + L.total;
+  float2* dobj = (float2*)b; b += align256(HW * 8);
+  float2* dprobe = (float2*)b; b += align256((size_t)d.M * NN * 8);
+  float* dpos = (float*)b; b += align256((size_t)d.J * 8);
+  float* dmeas = (float*)b; b += align256((size_t)d.J * NN * 4);
+  int32_t* dorder = (int32_t*)b; b += align256((size_t)d.J * 4);
+  double* dloss = (double*)b;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void* dst, const void* src, size_t n, cudaMemcpyKind k) {
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, k, s);
+  };
+  cp(dobj, object, HW * 8, cudaMemcpyHostToDevice);
+  cp(dprobe, probe, (size_t)d.M * NN * 8, cudaMemcpyHostToDevice);
+  cp(dpos, pos, (size_t)d.J * 8, cudaMemcpyHostToDevice);
+  cp(dmeas, meas, (size_t)d.J * NN * 4, cudaMemcpyHostToDevice);
+  if (order) cp(dorder, order, (size_t)d.J * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return PTYCHO_ERR_CUDA;
+  st = run_epoch(d, dobj, dprobe, dpos, dmeas, order ? dorder : nullptr, *opts, dloss, nullptr, ws, s);
+  if (st != PTYCHO_OK) return st;
+  cp(object, dobj, HW * 8, cudaMemcpyDeviceToHost);
+  cp(probe, dprobe, (size_t)d.M * NN * 8, cudaMemcpyDeviceToHost);
+  if (loss) cp(loss, dloss, 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return PTYCHO_ERR_CUDA;
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+ptycho_status ptycho_status_read(void* ws, void* stream) {
+  if (!ws) return PTYCHO_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  WsHeader* hdr = (WsHeader*)ws;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, &hdr->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PTYCHO_ERR_CUDA;
+  if (cudaMemsetAsync(&hdr->status, 0, sizeof(int), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  if (h & FLAG_BOUNDS) return PTYCHO_ERR_BOUNDS;
+  if (h & FLAG_NONFINITE) return PTYCHO_ERR_NONFINITE;
+  return PTYCHO_OK;
+}
+
+}  // extern "C"

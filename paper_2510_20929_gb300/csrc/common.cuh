@@ -1,0 +1,153 @@
+// Device-side helpers shared by the LSQML kernels: argument blocks, bilinear
+// sub-pixel sampling (the object's patch extraction / update routine, Pty-Chi
+// Sec. 2.1), status flags and block reductions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace ptycho {
+
+// Status bits written by kernels into the workspace header (atomicOr).
+enum : int {
+  FLAG_BOUNDS = 1,     // a position's bilinear tile leaves the object, or an order entry is out of range
+  FLAG_NONFINITE = 2,  // a measured intensity is negative or not finite
+};
+
+// What the per-position pass computes after the forward model.
+enum : int {
+  MODE_FWD = 0,          // intensities only
+  MODE_LSQML_GAUSS = 1,  // exit-wave change chi for LSQML, amplitude data term
+  MODE_LSQML_POISSON = 2,
+  MODE_GRAD_GAUSS = 3,   // gradient of the amplitude data term
+  MODE_GRAD_POISSON = 4,
+  MODE_VJP = 5,          // gradient given dL/dI
+};
+
+// Per-batch scalars (two sets, alternated by batch parity so that one batch's
+// update kernel can clear the next batch's set without a race).
+struct BatchScalars {
+  unsigned int max_illum;  // float bits of max(illumination) (non-negative)
+  int count;               // positions whose step sizes were solved
+  double sum_alpha_p;      // sum of alpha_P over the batch
+  double pad[2];
+};
+
+struct WsHeader {
+  int status;
+  int pad[3];
+  BatchScalars sc[2];
+};
+
+struct BatchArgs {
+  int H, W, M, J;
+  const float2* obj;
+  const float2* probe;
+  const float* pos;
+  const float* meas;   // measured intensities, or dL/dI in MODE_VJP
+  const int* order;    // may be null: identity
+  int b0, nb;          // first entry of `order` in this batch, positions in the batch
+  int mode;
+  float eps;
+  float2* psi_s;       // [B, M, N, N] far fields (unitary scale)
+  float2* o_s;         // [B, N, N] object patches
+  float2* g_s;         // [B, N, N] sum_k conj(P_k) chi_k
+  float2* h_s;         // [B, M, N, N] conj(o) chi_k
+  int* valid;          // [B]
+  const float* Sp;     // [N, N] sum_k |P_k|^2 (illumination scatter)
+  float4* acc;         // [H, W] (dO_acc.re, dO_acc.im, illum, unused) or null
+  float2* gobj;        // [H, W] gradient accumulator or null
+  float* ipred;        // [J, N, N] predicted intensities or null
+  float* gpos;         // [J, 2] position gradient or null
+  double* loss;        // scalar accumulator or null
+  int* status;
+};
+
+struct Pass2Args {
+  int H, W, M, J;
+  const float* pos;
+  const int* order;
+  int b0, nb;
+  const float2* o_s;
+  const float2* g_s;
+  const float2* h_s;
+  const int* valid;
+  const float4* acc;
+  const float* Sp;
+  const float2* Cp;
+  const float* Sdp;
+  const float2* dP;
+  float2* U;
+  double* alpha_out;   // [J, 2] or null
+  BatchScalars* sc;
+  float delta_o;       // relative preconditioner damping
+  double lam;
+  int update_object, update_probe;
+};
+
+// Tile origin and fraction of a probe-centre position; false if the bilinear
+// (N+1)^2 tile is not inside the object or the value is not finite.
+__device__ __forceinline__ bool tile_of(float py, float px, int N, int H, int W, int& ty, int& tx,
+                                        float& fy, float& fx) {
+  const float sy = py - 0.5f * (float)N, sx = px - 0.5f * (float)N;
+  // floor(s) >= 0 and floor(s) + N + 1 <= extent  <=>  0 <= s < extent - N (NaN fails)
+  if (!(sy >= 0.f && sy < (float)(H - N) && sx >= 0.f && sx < (float)(W - N))) return false;
+  const float fly = floorf(sy), flx = floorf(sx);
+  ty = (int)fly;
+  tx = (int)flx;
+  fy = sy - fly;
+  fx = sx - flx;
+  return true;
+}
+
+// o = (1-fy)(1-fx) O[y][x] + (1-fy) fx O[y][x+1] + fy (1-fx) O[y+1][x] + fy fx O[y+1][x+1]
+__device__ __forceinline__ float2 bilinear(const float2* __restrict__ O, int W, int y, int x, float fy,
+                                           float fx) {
+  const float2* p = O + (size_t)y * W + x;
+  const float2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + W), d = __ldg(p + W + 1);
+  const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
+  return make_float2(w00 * a.x + w01 * b.x + w10 * c.x + w11 * d.x,
+                     w00 * a.y + w01 * b.y + w10 * c.y + w11 * d.y);
+}
+
+// Block-wide sum of NV doubles; result valid in thread 0. `red` holds 32*NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[warp * NV + q] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red[w * NV + q];
+      v[q] = s;
+    }
+  }
+}
+
+__device__ __forceinline__ float block_max(float v, float* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < nw; ++w) v = fmaxf(v, red[w]);
+  if (threadIdx.x == 0) red[0] = v;
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
+}  // namespace ptycho

@@ -1,0 +1,299 @@
+// Shared-memory 2-D FFT for one N x N complex64 tile per CTA (sm_103a).
+//
+// The far-field propagator of the ptychographic forward model (Pty-Chi,
+// Sec. 2.1; Eq. 4's F(o, p, Lambda)) is a unitary 2-D DFT of each exit wave.
+// This header implements it as two passes of 1-D transforms over the rows and
+// columns of a tile held in shared memory:
+//
+//   * a line (row or column) of N = R1 * R2 points is owned by R1 consecutive
+//     lanes of one warp; lane n holds R2 points x[n + R1*n2] in registers;
+//   * stage 1 is an R2-point DFT in registers, followed by the twiddles
+//     W_N^(n*k2); the lanes then exchange through the line's own storage in
+//     the tile (warp-synchronous, no block barrier) and stage 2 runs R1-point
+//     DFTs, leaving lane n with X[S*(n + R1*k1) + s], S = R2/R1;
+//   * the inverse runs the same stages mirrored (decimation in frequency), so
+//     it consumes the forward's output layout and returns the forward's input
+//     layout.
+//
+// The tile is stored row-major with an XOR swizzle of the low four column
+// bits, chosen (by an offline bank-conflict model of every access family
+// used here) so that the strided row, column and exchange accesses of a warp
+// hit distinct 8-byte bank slots. The swizzle is linear over GF(2), so every
+// address splits into a per-thread part (hoisted out of the unrolled loops)
+// XOR a compile-time part.
+//
+// All transforms here are unnormalised; callers apply the 1/N of the unitary
+// 2-D transform where it folds into other arithmetic.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace ptycho {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+// a * exp(DIR * i * pi / 2): DIR = -1 multiplies by -i (forward), +1 by +i.
+template <int DIR>
+__device__ __forceinline__ float2 rot90(float2 a) {
+  return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+// cos(m*pi/8), sin(m*pi/8) for m = 0..4 (the only irrational twiddles of the
+// 8- and 16-point kernels below).
+#define PT_C1 0.92387953251128674f  // cos(pi/8)
+#define PT_S1 0.38268343236508978f  // sin(pi/8)
+#define PT_C2 0.70710678118654752f  // cos(pi/4)
+
+// a * exp(DIR * i * m * pi / 8), m compile-time in [0, 16).
+template <int DIR, int m>
+__device__ __forceinline__ float2 tw16(float2 a) {
+  constexpr int mm = m & 15;
+  if constexpr (mm == 0) return a;
+  else if constexpr (mm == 4) return rot90<DIR>(a);
+  else if constexpr (mm == 8) return make_float2(-a.x, -a.y);
+  else if constexpr (mm == 12) return rot90<-DIR>(a);
+  else {
+    // cos and sin of mm*pi/8 from the first-octant constants
+    constexpr float cs[16] = {1.f, PT_C1, PT_C2, PT_S1, 0.f, -PT_S1, -PT_C2, -PT_C1,
+                              -1.f, -PT_C1, -PT_C2, -PT_S1, 0.f, PT_S1, PT_C2, PT_C1};
+    constexpr float sn[16] = {0.f, PT_S1, PT_C2, PT_C1, 1.f, PT_C1, PT_C2, PT_S1,
+                              0.f, -PT_S1, -PT_C2, -PT_C1, -1.f, -PT_C1, -PT_C2, -PT_S1};
+    const float c = cs[mm], s = DIR < 0 ? -sn[mm] : sn[mm];
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+  }
+}
+
+// In-register DFTs of size R (natural order in and out), sign DIR.
+template <int R, int DIR> struct Dft;
+
+template <int DIR> struct Dft<1, DIR> {
+  template <class V> __device__ __forceinline__ static void run(V&) {}
+};
+
+template <int DIR> struct Dft<2, DIR> {
+  template <class V> __device__ __forceinline__ static void run(V& v) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <int DIR> struct Dft<4, DIR> {
+  template <class V> __device__ __forceinline__ static void run(V& v) {
+    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    float2 t2 = cadd(v[1], v[3]), t3 = rot90<DIR>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+
+template <int DIR> struct Dft<8, DIR> {
+  template <class V> __device__ __forceinline__ static void run(V& v) {
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4, DIR>::run(e);
+    Dft<4, DIR>::run(o);
+    o[1] = tw16<DIR, 2>(o[1]);
+    o[2] = tw16<DIR, 4>(o[2]);
+    o[3] = tw16<DIR, 6>(o[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = cadd(e[k], o[k]);
+      v[k + 4] = csub(e[k], o[k]);
+    }
+  }
+};
+
+template <int DIR> struct Dft<16, DIR> {
+  // n = b + 4a, k = k1 + 4k2: X[k] = sum_b W16^(b k1) W4^(b k2) sum_a W4^(a k1) v[b + 4a]
+  template <class V> __device__ __forceinline__ static void run(V& v) {
+    float2 y[4][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      float2 t[4] = {v[b], v[b + 4], v[b + 8], v[b + 12]};
+      Dft<4, DIR>::run(t);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) y[b][k1] = t[k1];
+    }
+    y[1][1] = tw16<DIR, 1>(y[1][1]);
+    y[1][2] = tw16<DIR, 2>(y[1][2]);
+    y[1][3] = tw16<DIR, 3>(y[1][3]);
+    y[2][1] = tw16<DIR, 2>(y[2][1]);
+    y[2][2] = tw16<DIR, 4>(y[2][2]);
+    y[2][3] = tw16<DIR, 6>(y[2][3]);
+    y[3][1] = tw16<DIR, 3>(y[3][1]);
+    y[3][2] = tw16<DIR, 6>(y[3][2]);
+    y[3][3] = tw16<DIR, 9>(y[3][3]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      float2 t[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      Dft<4, DIR>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+    }
+  }
+};
+
+// Per-size line split and tile swizzle. fr/fc are linear over GF(2).
+template <int N> struct FftCfg;
+template <> struct FftCfg<16> {
+  static constexpr int R1 = 4, R2 = 4;
+  static constexpr bool KMAJ = false;
+  __host__ __device__ static constexpr int fr(int r) { return ((r << 1) ^ r) & 15; }
+  __host__ __device__ static constexpr int fc(int) { return 0; }
+};
+template <> struct FftCfg<32> {
+  static constexpr int R1 = 4, R2 = 8;
+  static constexpr bool KMAJ = true;
+  __host__ __device__ static constexpr int fr(int r) { return ((r << 1) ^ r) & 15; }
+  __host__ __device__ static constexpr int fc(int) { return 0; }
+};
+template <> struct FftCfg<64> {
+  static constexpr int R1 = 8, R2 = 8;
+  static constexpr bool KMAJ = false;
+  __host__ __device__ static constexpr int fr(int r) { return ((r << 1) ^ (r >> 1)) & 15; }
+  __host__ __device__ static constexpr int fc(int cb) { return cb & 15; }
+};
+template <> struct FftCfg<128> {
+  static constexpr int R1 = 8, R2 = 16;
+  static constexpr bool KMAJ = true;
+  __host__ __device__ static constexpr int fr(int r) { return ((r << 1) ^ r ^ (r >> 2)) & 15; }
+  __host__ __device__ static constexpr int fc(int cb) { return (cb << 1) & 15; }
+};
+
+// Physical float2 index of tile element (r, c) for runtime r, c.
+template <int N>
+__device__ __forceinline__ int tix(int r, int c) {
+  return r * N + (c ^ FftCfg<N>::fr(r) ^ FftCfg<N>::fc(c >> 4));
+}
+
+template <int N>
+struct Fft2 {
+  using C = FftCfg<N>;
+  static constexpr int R1 = C::R1, R2 = C::R2, S = R2 / R1;
+
+  // Address of element i (= i_rt | i_ct, disjoint bits) of `line`.
+  template <bool ROW>
+  __device__ __forceinline__ static int addr(int line, int i_rt, int i_ct) {
+    if constexpr (ROW) {
+      // (r = line, c = i): c ^ fr(r) ^ fc(c >> 4), split over the disjoint parts of c
+      const int base = line * N + (i_rt ^ C::fr(line) ^ C::fc(i_rt >> 4));
+      return base ^ (i_ct ^ C::fc(i_ct >> 4));
+    } else {
+      // (r = i, c = line): r*N + (c ^ fr(r) ^ fc(c >> 4)), split over the parts of r
+      const int base = i_rt * N + (line ^ C::fc(line >> 4) ^ C::fr(i_rt));
+      return (base + i_ct * N) ^ C::fr(i_ct);
+    }
+  }
+
+  // Forward line transform (sign -1). In: v[n2] = x[n + R1*n2].
+  // Out: v[k1*S + s] = X[S*(n + R1*k1) + s]. The line's storage is used for the exchange.
+  template <bool ROW>
+  __device__ __forceinline__ static void line_fwd(float2 (&v)[R2], float2* tile, int line, int n,
+                                                  const float2* tw) {
+    Dft<R2, -1>::run(v);
+#pragma unroll
+    for (int k2 = 1; k2 < R2; ++k2) v[k2] = cmul(v[k2], tw[n * k2]);
+    // exchange: lane n writes Y[n][k2]; lane t reads Y[n1][S*t + s]
+    const int xn = C::KMAJ ? R2 * n : n;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) tile[addr<ROW>(line, xn, C::KMAJ ? k2 : R1 * k2)] = v[k2];
+    __syncwarp();
+    float2 w[S][R1];
+    const int xk = C::KMAJ ? S * n : R1 * S * n;
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1)
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        w[s][n1] = tile[addr<ROW>(line, xk, (C::KMAJ ? R2 * n1 + s : n1 + R1 * s))];
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < S; ++s) Dft<R1, -1>::run(w[s]);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1)
+#pragma unroll
+      for (int s = 0; s < S; ++s) v[k1 * S + s] = w[s][k1];
+  }
+
+  // Inverse line transform (sign +1, unnormalised: returns N * x).
+  // In: v[k1*S + s] = X[S*(n + R1*k1) + s]. Out: v[n2] = x[n + R1*n2].
+  template <bool ROW>
+  __device__ __forceinline__ static void line_inv(float2 (&v)[R2], float2* tile, int line, int n,
+                                                  const float2* tw) {
+    float2 w[S][R1];
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1)
+#pragma unroll
+      for (int s = 0; s < S; ++s) w[s][k1] = v[k1 * S + s];
+#pragma unroll
+    for (int s = 0; s < S; ++s) Dft<R1, 1>::run(w[s]);
+    const int xk = C::KMAJ ? S * n : R1 * S * n;
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1)
+#pragma unroll
+      for (int s = 0; s < S; ++s)
+        tile[addr<ROW>(line, xk, (C::KMAJ ? R2 * n1 + s : n1 + R1 * s))] = w[s][n1];
+    __syncwarp();
+    const int xn = C::KMAJ ? R2 * n : n;
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k2] = tile[addr<ROW>(line, xn, C::KMAJ ? k2 : R1 * k2)];
+    __syncwarp();
+#pragma unroll
+    for (int k2 = 1; k2 < R2; ++k2) v[k2] = cmulc(tw[n * k2], v[k2]);
+    Dft<R2, 1>::run(v);
+  }
+
+  // Load / store a line in the "in" layout (x[n + R1*n2]) or the "out" layout
+  // (X[S*(n + R1*k1) + s] in register k1*S + s).
+  template <bool ROW>
+  __device__ __forceinline__ static void load_in(float2 (&v)[R2], const float2* tile, int line, int n) {
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) v[n2] = tile[addr<ROW>(line, n, R1 * n2)];
+  }
+  template <bool ROW>
+  __device__ __forceinline__ static void store_in(const float2 (&v)[R2], float2* tile, int line, int n) {
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) tile[addr<ROW>(line, n, R1 * n2)] = v[n2];
+  }
+  template <bool ROW>
+  __device__ __forceinline__ static void load_out(float2 (&v)[R2], const float2* tile, int line, int n) {
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1)
+#pragma unroll
+      for (int s = 0; s < S; ++s) v[k1 * S + s] = tile[addr<ROW>(line, S * n, S * R1 * k1 + s)];
+  }
+  template <bool ROW>
+  __device__ __forceinline__ static void store_out(const float2 (&v)[R2], float2* tile, int line, int n) {
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1)
+#pragma unroll
+      for (int s = 0; s < S; ++s) tile[addr<ROW>(line, S * n, S * R1 * k1 + s)] = v[k1 * S + s];
+  }
+
+  // Index (within the line) of register m in the "out" layout, and in the "in" layout.
+  __device__ __forceinline__ static int out_index(int n, int m) { return S * (n + R1 * (m / S)) + (m % S); }
+  __device__ __forceinline__ static int in_index(int n, int m) { return n + R1 * m; }
+};
+
+// Twiddle table tw[m] = exp(-2 pi i m / N), m in [0, N), written by the whole CTA.
+template <int N>
+__device__ __forceinline__ void make_twiddles(float2* tw) {
+  for (int m = threadIdx.x; m < N; m += blockDim.x) {
+    float s, c;
+    sincospif(2.0f * (float)m / (float)N, &s, &c);
+    tw[m] = make_float2(c, -s);
+  }
+}
+
+}  // namespace ptycho

@@ -1,0 +1,420 @@
+// Per-scan-position kernels of the LSQML hot path (templated on the window N).
+//
+// k_pass1: one CTA per position of a minibatch. For every incoherent probe
+//   mode k it extracts the sub-pixel object patch o_j = S_j(O) (bilinear),
+//   forms the exit wave psi_jk = P_k o_j (Pty-Chi Sec. 2.1, the psi = p o of
+//   Eq. 2), propagates it with the unitary 2-D FFT and accumulates the
+//   incoherent intensity I_j = sum_k |Psi_jk|^2 (Eq. 4's forward model). It
+//   then applies the data term (Eq. 1 amplitude loss, or the Poisson
+//   likelihood), forms the far-field correction factor, back-propagates every
+//   mode to chi_jk = F^-1[(rho - 1) Psi_jk] (= psi'_jk - psi_jk of Eq. 2), and
+//   reduces g_j = sum_k conj(P_k) chi_jk and h_jk = conj(o_j) chi_jk. Finally
+//   it scatter-adds S_j^T g_j and the illumination S_j^T sum_k |P_k|^2 into the
+//   object-frame accumulators (the LSQML preconditioner) with vector atomics,
+//   or, in gradient mode, S_j^T of the object gradient and the position
+//   gradient through the bilinear weights.
+// k_pass2: one CTA per position: the five reductions of the per-position
+//   least-squares step (LSQML's self-adaptive step sizes, Sec. 2.2), the
+//   FP64 2x2 solve, and the alpha-weighted object scatter.
+#pragma once
+#include "common.cuh"
+
+namespace ptycho {
+
+template <int N> struct Threads;
+template <> struct Threads<16> { static constexpr int T = 64; };
+template <> struct Threads<32> { static constexpr int T = 128; };
+template <> struct Threads<64> { static constexpr int T = 256; };
+template <> struct Threads<128> { static constexpr int T = 512; };
+
+template <int N>
+struct Pass1Smem {
+  static constexpr int RP = N + 16;  // row pitch of the intensity/factor plane (floats)
+  static constexpr size_t red = 0;
+  static constexpr size_t tile = red + 256 * sizeof(double);
+  static constexpr size_t tw = tile + (size_t)N * N * sizeof(float2);
+  static constexpr size_t rI = tw + (size_t)N * sizeof(float2);
+  static constexpr size_t bytes = rI + (size_t)N * RP * sizeof(float);
+};
+
+// 2-D forward transform of the tile (natural layout on entry). Column pass
+// first, then rows; `out(row, v)` receives each row's unnormalised transform in
+// the line "out" layout: v[m] = X[row][Fft2<N>::out_index(n, m)].
+template <int N, int T, class Out>
+__device__ __forceinline__ void fft2_forward(float2* tile, const float2* tw, Out&& out) {
+  using F = Fft2<N>;
+  constexpr int R1 = F::R1, R2 = F::R2, L = T / R1, ITER = N / L;
+  const int n = threadIdx.x % R1, gid = threadIdx.x / R1;
+#pragma unroll 1
+  for (int it = 0; it < ITER; ++it) {
+    const int col = gid + it * L;
+    float2 v[R2];
+    F::template load_in<false>(v, tile, col, n);
+    F::template line_fwd<false>(v, tile, col, n, tw);
+    F::template store_out<false>(v, tile, col, n);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int it = 0; it < ITER; ++it) {
+    const int row = gid + it * L;
+    float2 v[R2];
+    F::template load_in<true>(v, tile, row, n);
+    F::template line_fwd<true>(v, tile, row, n, tw);
+    out(row, v);
+  }
+}
+
+// 2-D inverse (unnormalised). `in(row, v)` supplies each row in the "out"
+// layout; `out(col, v)` receives each column with v[n2] = x[n + R1*n2][col].
+// The tile must be free on entry.
+template <int N, int T, class In, class Out>
+__device__ __forceinline__ void fft2_inverse(float2* tile, const float2* tw, In&& in, Out&& out) {
+  using F = Fft2<N>;
+  constexpr int R1 = F::R1, R2 = F::R2, L = T / R1, ITER = N / L;
+  const int n = threadIdx.x % R1, gid = threadIdx.x / R1;
+#pragma unroll 1
+  for (int it = 0; it < ITER; ++it) {
+    const int row = gid + it * L;
+    float2 v[R2];
+    in(row, v);
+    F::template line_inv<true>(v, tile, row, n, tw);
+    F::template store_in<true>(v, tile, row, n);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int it = 0; it < ITER; ++it) {
+    const int col = gid + it * L;
+    float2 v[R2];
+    F::template load_out<false>(v, tile, col, n);
+    F::template line_inv<false>(v, tile, col, n, tw);
+    out(col, v);
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(Threads<N>::T) k_pass1(BatchArgs a) {
+  constexpr int T = Threads<N>::T;
+  using F = Fft2<N>;
+  using SM = Pass1Smem<N>;
+  constexpr int R1 = F::R1, R2 = F::R2, NN = N * N, RP = SM::RP;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* red = (double*)(smem + SM::red);
+  float2* tile = (float2*)(smem + SM::tile);
+  float2* tw = (float2*)(smem + SM::tw);
+  float* rI = (float*)(smem + SM::rI);
+
+  const int slot = blockIdx.x;
+  const int tid = threadIdx.x, n = tid % R1;
+  const int e = a.b0 + slot;
+  const int j = a.order ? a.order[e] : e;
+  int ty = 0, tx = 0;
+  float fy = 0.f, fx = 0.f;
+  bool ok = (j >= 0 && j < a.J);
+  if (ok) ok = tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
+  if (!ok) {
+    if (tid == 0) {
+      atomicOr(a.status, FLAG_BOUNDS);
+      if (a.valid) a.valid[slot] = 0;
+    }
+    return;
+  }
+  if (tid == 0 && a.valid) a.valid[slot] = 1;
+  make_twiddles<N>(tw);
+
+  const int M = a.M;
+  const float invN = 1.0f / (float)N;
+  const size_t slotNN = (size_t)slot * NN;
+  float2* psi_s = a.psi_s ? a.psi_s + slotNN * M : nullptr;
+  float2* o_s = a.o_s ? a.o_s + slotNN : nullptr;
+
+  // ---- forward model: I_j = sum_k |F(P_k o_j)|^2 -------------------------------
+#pragma unroll 1
+  for (int k = 0; k < M; ++k) {
+    const float2* Pk = a.probe + (size_t)k * NN;
+    for (int p = tid; p < NN; p += T) {
+      const int r = p / N, c = p % N;
+      float2 o;
+      if (k == 0 || !o_s) {
+        o = bilinear(a.obj, a.W, ty + r, tx + c, fy, fx);
+        if (k == 0 && o_s) o_s[p] = o;
+      } else {
+        o = o_s[p];
+      }
+      tile[tix<N>(r, c)] = cmul(__ldg(Pk + p), o);
+    }
+    __syncthreads();
+    fft2_forward<N, T>(tile, tw, [&](int row, float2 (&v)[R2]) {
+#pragma unroll
+      for (int m = 0; m < R2; ++m) {
+        const int col = F::out_index(n, m);
+        const float2 X = cscale(v[m], invN);
+        const float i2 = cabs2(X);
+        float* ri = rI + row * RP + col;
+        *ri = (k == 0) ? i2 : *ri + i2;
+        if (psi_s) psi_s[(size_t)k * NN + row * N + col] = X;
+      }
+    });
+    __syncthreads();
+  }
+
+  // ---- data term: loss and the far-field factor (same thread owns each pixel) ----
+  const int mode = a.mode;
+  const float eps = a.eps;
+  const float* meas = a.meas + (size_t)j * NN;
+  float lsum = 0.f;
+  bool bad = false;
+  {
+    constexpr int L = T / R1, ITER = N / L;
+    const int gid = tid / R1;
+#pragma unroll 1
+    for (int it = 0; it < ITER; ++it) {
+      const int row = gid + it * L;
+#pragma unroll
+      for (int m = 0; m < R2; ++m) {
+        const int col = F::out_index(n, m);
+        const int pix = row * N + col;
+        const float I = rI[row * RP + col];
+        if (a.ipred) a.ipred[(size_t)j * NN + pix] = I;
+        if (mode == MODE_FWD) continue;
+        const float Im = __ldg(meas + pix);
+        float fac;
+        if (mode == MODE_VJP) {
+          bad |= !isfinite(Im);
+          fac = 2.f * Im;
+        } else {
+          bad |= !(Im >= 0.f) || !isfinite(Im);
+          const float Ie = I + eps;
+          if (mode == MODE_LSQML_GAUSS || mode == MODE_GRAD_GAUSS) {
+            const float sIe = sqrtf(Ie), sIm = sqrtf(Im);
+            const float d = sIe - sIm;
+            lsum = fmaf(d, d, lsum);
+            const float rho = sIm / sIe;
+            fac = (mode == MODE_LSQML_GAUSS) ? rho - 1.f : 2.f * (1.f - rho);
+          } else {
+            lsum += I - Im * logf(Ie);
+            const float q = Im / Ie;
+            fac = (mode == MODE_LSQML_POISSON) ? 0.5f * (q - 1.f) : 2.f * (1.f - q);
+          }
+        }
+        rI[row * RP + col] = fac * invN;
+      }
+    }
+  }
+  if (bad) atomicOr(a.status, FLAG_NONFINITE);
+  if (a.loss && mode != MODE_FWD && mode != MODE_VJP) {
+    double v[1] = {(double)lsum};
+    block_sum<1>(v, red);
+    if (tid == 0) atomicAdd(a.loss, v[0]);
+  }
+  if (mode == MODE_FWD) return;
+
+  // ---- back-propagation: chi_k = F^-1[fac Psi_k], g = sum_k conj(P_k) chi_k, h_k ----
+  float2* g_s = a.g_s + slotNN;
+  float2* h_s = a.h_s + slotNN * M;
+#pragma unroll 1
+  for (int k = 0; k < M; ++k) {
+    const float2* Pk = a.probe + (size_t)k * NN;
+    __syncthreads();
+    fft2_inverse<N, T>(
+        tile, tw,
+        [&](int row, float2 (&v)[R2]) {
+#pragma unroll
+          for (int m = 0; m < R2; ++m) {
+            const int col = F::out_index(n, m);
+            v[m] = cscale(psi_s[(size_t)k * NN + row * N + col], rI[row * RP + col]);
+          }
+        },
+        [&](int col, float2 (&v)[R2]) {
+#pragma unroll
+          for (int n2 = 0; n2 < R2; ++n2) {
+            const int row = F::in_index(n, n2);
+            const int pix = row * N + col;
+            const float2 chi = v[n2];
+            const float2 gc = cmulc(__ldg(Pk + pix), chi);
+            g_s[pix] = (k == 0) ? gc : cadd(g_s[pix], gc);
+            h_s[(size_t)k * NN + pix] = cmulc(o_s[pix], chi);
+          }
+        });
+  }
+  __syncthreads();
+
+  // ---- scatter S_j^T g (and the illumination) into the object frame ----------------
+  for (int p = tid; p < NN; p += T) tile[tix<N>(p / N, p % N)] = g_s[p];
+  __syncthreads();
+  const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
+  const bool lsqml = (mode == MODE_LSQML_GAUSS || mode == MODE_LSQML_POISSON);
+  constexpr int N1 = N + 1;
+  for (int q = tid; q < N1 * N1; q += T) {
+    const int y = q / N1, x = q % N1;
+    float2 s = make_float2(0.f, 0.f);
+    float il = 0.f;
+    if (y < N && x < N) {
+      const float2 g = tile[tix<N>(y, x)];
+      s.x += w00 * g.x; s.y += w00 * g.y;
+      if (lsqml) il += w00 * __ldg(a.Sp + y * N + x);
+    }
+    if (y < N && x > 0) {
+      const float2 g = tile[tix<N>(y, x - 1)];
+      s.x += w01 * g.x; s.y += w01 * g.y;
+      if (lsqml) il += w01 * __ldg(a.Sp + y * N + x - 1);
+    }
+    if (y > 0 && x < N) {
+      const float2 g = tile[tix<N>(y - 1, x)];
+      s.x += w10 * g.x; s.y += w10 * g.y;
+      if (lsqml) il += w10 * __ldg(a.Sp + (y - 1) * N + x);
+    }
+    if (y > 0 && x > 0) {
+      const float2 g = tile[tix<N>(y - 1, x - 1)];
+      s.x += w11 * g.x; s.y += w11 * g.y;
+      if (lsqml) il += w11 * __ldg(a.Sp + (y - 1) * N + x - 1);
+    }
+    const size_t oi = (size_t)(ty + y) * a.W + (tx + x);
+    if (lsqml) atomicAdd(a.acc + oi, make_float4(s.x, s.y, il, 0.f));
+    else atomicAdd(a.gobj + oi, s);
+  }
+
+  // ---- position gradient through the bilinear weights (gradient modes) -------------
+  if (a.gpos) {
+    float gy = 0.f, gx = 0.f;
+    for (int p = tid; p < NN; p += T) {
+      const int r = p / N, c = p % N;
+      const float2* o = a.obj + (size_t)(ty + r) * a.W + (tx + c);
+      const float2 O00 = __ldg(o), O01 = __ldg(o + 1), O10 = __ldg(o + a.W), O11 = __ldg(o + a.W + 1);
+      const float2 dy = make_float2((1.f - fx) * (O10.x - O00.x) + fx * (O11.x - O01.x),
+                                    (1.f - fx) * (O10.y - O00.y) + fx * (O11.y - O01.y));
+      const float2 dx = make_float2((1.f - fy) * (O01.x - O00.x) + fy * (O11.x - O10.x),
+                                    (1.f - fy) * (O01.y - O00.y) + fy * (O11.y - O10.y));
+      const float2 g = tile[tix<N>(r, c)];
+      gy += g.x * dy.x + g.y * dy.y;  // Re(conj(g) dy)
+      gx += g.x * dx.x + g.y * dx.y;
+    }
+    double v[2] = {(double)gy, (double)gx};
+    block_sum<2>(v, red);
+    if (tid == 0) {
+      a.gpos[2 * j] += (float)v[0];
+      a.gpos[2 * j + 1] += (float)v[1];
+    }
+  }
+}
+
+
+template <int N>
+struct Pass2Smem {
+  static constexpr size_t red = 0;
+  static constexpr size_t tile = red + 256 * sizeof(double);
+  static constexpr size_t alpha = tile + (size_t)N * N * sizeof(float2);
+  static constexpr size_t bytes = alpha + 4 * sizeof(double);
+};
+
+template <int N>
+__global__ void __launch_bounds__(Threads<N>::T) k_pass2(Pass2Args a) {
+  constexpr int T = Threads<N>::T, NN = N * N;
+  using SM = Pass2Smem<N>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* red = (double*)(smem + SM::red);
+  float2* tile = (float2*)(smem + SM::tile);
+  double* alpha_sh = (double*)(smem + SM::alpha);
+  const int slot = blockIdx.x, tid = threadIdx.x;
+  if (!a.valid[slot]) return;
+  const int e = a.b0 + slot;
+  const int j = a.order ? a.order[e] : e;
+  int ty, tx;
+  float fy, fx;
+  tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
+  const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
+  const float dmp = a.delta_o * __uint_as_float(a.sc->max_illum);
+  const size_t slotNN = (size_t)slot * NN;
+  const int M = a.M;
+
+  float A11 = 0.f, A12 = 0.f, A22 = 0.f, b1 = 0.f, b2 = 0.f;
+  for (int p = tid; p < NN; p += T) {
+    const int r = p / N, c = p % N;
+    const float2 g = a.g_s[slotNN + p];
+    tile[tix<N>(r, c)] = g;
+    float2 d = make_float2(0.f, 0.f);
+    if (a.update_object) {
+      const float4* q = a.acc + (size_t)(ty + r) * a.W + (tx + c);
+      const float4 q00 = __ldg(q), q01 = __ldg(q + 1), q10 = __ldg(q + a.W), q11 = __ldg(q + a.W + 1);
+      const float i00 = 1.f / (q00.z + dmp), i01 = 1.f / (q01.z + dmp);
+      const float i10 = 1.f / (q10.z + dmp), i11 = 1.f / (q11.z + dmp);
+      d.x = w00 * q00.x * i00 + w01 * q01.x * i01 + w10 * q10.x * i10 + w11 * q11.x * i11;
+      d.y = w00 * q00.y * i00 + w01 * q01.y * i01 + w10 * q10.y * i10 + w11 * q11.y * i11;
+    }
+    const float2 o = a.o_s[slotNN + p];
+    A11 += cabs2(d) * __ldg(a.Sp + p);
+    const float2 od = cmulc(d, o);            // conj(d) o
+    const float2 cp = __ldg(a.Cp + p);
+    A12 += od.x * cp.x - od.y * cp.y;          // Re(conj(d) o Cp)
+    A22 += cabs2(o) * __ldg(a.Sdp + p);
+    b1 += d.x * g.x + d.y * g.y;               // Re(conj(d) g)
+    if (a.update_probe) {
+      for (int k = 0; k < M; ++k) {
+        const float2 dp = __ldg(a.dP + (size_t)k * NN + p);
+        const float2 h = a.h_s[(slotNN * M) + (size_t)k * NN + p];
+        b2 += dp.x * h.x + dp.y * h.y;         // Re(conj(dP_k) h_k)
+      }
+    }
+  }
+  double v[5] = {A11, A12, A22, b1, b2};
+  block_sum<5>(v, red);
+  if (tid == 0) {
+    const double a11 = v[0], a12 = v[1], a22 = v[2], r1 = v[3], r2 = v[4];
+    const double tr = 0.5 * (a11 + a22);
+    const double d11 = a11 + a.lam * tr, d22 = a22 + a.lam * tr;
+    const double det = d11 * d22 - a12 * a12;
+    double aO, aP;
+    if (det > 0.0) {
+      aO = (d22 * r1 - a12 * r2) / det;
+      aP = (d11 * r2 - a12 * r1) / det;
+    } else {
+      aO = d11 > 0.0 ? r1 / d11 : 0.0;
+      aP = d22 > 0.0 ? r2 / d22 : 0.0;
+    }
+    alpha_sh[0] = aO;
+    if (a.alpha_out) {
+      a.alpha_out[2 * j] = aO;
+      a.alpha_out[2 * j + 1] = aP;
+    }
+    atomicAdd(&a.sc->sum_alpha_p, aP);
+    atomicAdd(&a.sc->count, 1);
+  }
+  __syncthreads();
+  if (!a.update_object) return;
+  const float aO = (float)alpha_sh[0];
+  constexpr int N1 = N + 1;
+  for (int q = tid; q < N1 * N1; q += T) {
+    const int y = q / N1, x = q % N1;
+    float2 s = make_float2(0.f, 0.f);
+    if (y < N && x < N) { const float2 g = tile[tix<N>(y, x)]; s.x += w00 * g.x; s.y += w00 * g.y; }
+    if (y < N && x > 0) { const float2 g = tile[tix<N>(y, x - 1)]; s.x += w01 * g.x; s.y += w01 * g.y; }
+    if (y > 0 && x < N) { const float2 g = tile[tix<N>(y - 1, x)]; s.x += w10 * g.x; s.y += w10 * g.y; }
+    if (y > 0 && x > 0) { const float2 g = tile[tix<N>(y - 1, x - 1)]; s.x += w11 * g.x; s.y += w11 * g.y; }
+    atomicAdd(a.U + (size_t)(ty + y) * a.W + (tx + x), make_float2(aO * s.x, aO * s.y));
+  }
+}
+
+}  // namespace ptycho
+
+namespace ptycho {
+
+template <int N>
+cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s) {
+  constexpr size_t sm = Pass1Smem<N>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(k_pass1<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  if (a.nb <= 0) return cudaSuccess;
+  k_pass1<N><<<a.nb, Threads<N>::T, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s) {
+  constexpr size_t sm = Pass2Smem<N>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(k_pass2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  if (a.nb <= 0) return cudaSuccess;
+  k_pass2<N><<<a.nb, Threads<N>::T, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ptycho

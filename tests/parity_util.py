@@ -1,0 +1,46 @@
+"""Helpers shared by the GPU parity tests and the smoke run: seeded problems
+(inputs from paper_2510_20929_gb300.synth, measured data from the FP64 oracle)
+and error metrics."""
+import math
+
+import numpy as np
+
+from oracle import ptycho_oracle as orc
+from paper_2510_20929_gb300 import synth
+
+
+def rel(a, b):
+    """Norm-wise relative error ||a - b|| / ||b||."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    nb = np.linalg.norm(b.ravel())
+    return float(np.linalg.norm((a - b).ravel()) / (nb if nb > 0 else 1.0))
+
+
+def problem(N=16, M=2, H=40, W=44, J=12, seed=7, step=4.0, counts=2e4, perturb=0.15, noisy=True):
+    """Truth, a perturbed estimate, and Poisson-noised intensities (oracle forward)."""
+    w = synth.workload_small(N=N, M=M, H=H, W=W, J=J, seed=seed, step=step)
+    O_true, P, pos = w["object"], w["probe"], w["pos"]
+    I0 = orc.forward(O_true, P, pos)
+    scale = counts / I0.sum(axis=(1, 2)).mean()
+    P = P * math.sqrt(scale)
+    I_true = I0 * scale
+    I_m = synth.poisson_counts(I_true, seed + 11) if noisy else I_true
+    g = np.random.default_rng(seed + 5)
+    O = O_true * (1 + perturb * (g.standard_normal(O_true.shape) + 1j * g.standard_normal(O_true.shape)))
+    return dict(O_true=O_true, O=O, P=P, pos=pos, I_m=I_m, I_true=I_true)
+
+
+def to_dev(x, dtype):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x)).to(dtype).cuda().contiguous()
+
+
+def f32pos(pos):
+    """Positions as the float32 values both sides see."""
+    return np.asarray(pos, np.float32).astype(np.float64)
+
+
+def c64(x):
+    """Round a complex array to complex64 and back (the inputs both sides see)."""
+    return np.asarray(x, np.complex64).astype(np.complex128)

@@ -1,0 +1,110 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+declared in include/ptycho.h, and rejects bad arguments on the host before any
+CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ptycho.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2510_20929_gb300 import api
+    if not os.path.exists(api.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return api.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ptycho_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for n in ("ptycho_forward", "ptycho_adjoint", "ptycho_lsqml_epoch", "ptycho_workspace_bytes",
+              "ptycho_status_read", "ptycho_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_status_strings(L):
+    from paper_2510_20929_gb300 import api
+    for code in range(8):
+        assert len(api.status_string(code)) > 0
+    assert api.status_string(0) == "ok"
+
+
+def _dims(H=64, W=64, N=32, M=2, J=5):
+    from paper_2510_20929_gb300 import api
+    return api.Dims(H, W, N, M, J)
+
+
+def test_workspace_bytes_host_logic(L):
+    from paper_2510_20929_gb300 import api
+    d = _dims()
+    a = L.ptycho_workspace_bytes(ctypes.byref(d), 4)
+    b = L.ptycho_workspace_bytes(ctypes.byref(d), 8)
+    assert a > 0 and b > a and a % 256 == 0
+    # 4 batch-sized scratch planes of M*N*N or N*N complex64 grow linearly in B
+    NN = 32 * 32
+    assert b - a >= 4 * (2 * NN * 8 * 2 + NN * 8 * 2)
+    assert L.ptycho_workspace_bytes(ctypes.byref(_dims(N=48)), 4) == 0     # unsupported N
+    assert L.ptycho_workspace_bytes(ctypes.byref(_dims(M=17)), 4) == 0
+    assert L.ptycho_workspace_bytes(ctypes.byref(_dims(H=32)), 4) == 0     # H < N + 1
+    assert L.ptycho_workspace_bytes(ctypes.byref(d), 0) == 0
+    assert L.ptycho_host_workspace_bytes(ctypes.byref(d), 4) > a
+
+
+def test_arguments_rejected_before_any_launch(L):
+    from paper_2510_20929_gb300 import api
+    P = ctypes.c_void_p
+    fake = P(0x1000)      # never dereferenced: every call below fails its host checks first
+    d = _dims()
+    assert L.ptycho_forward(None, fake, fake, fake, fake, fake, 1 << 20, None) == 1
+    assert L.ptycho_forward(ctypes.byref(_dims(N=48)), fake, fake, fake, fake, fake, 1 << 20, None) == 6
+    assert L.ptycho_forward(ctypes.byref(d), P(0), fake, fake, fake, fake, 1 << 20, None) == 1
+    assert L.ptycho_forward(ctypes.byref(d), fake, fake, fake, fake, P(0), 1 << 20, None) == 7
+    assert L.ptycho_forward(ctypes.byref(d), fake, fake, fake, fake, P(0x1001), 1 << 20, None) == 7
+    opts = api.make_opts(batch=0)
+    assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
+                                P(0), P(0), fake, 1 << 30, None) == 1
+    opts = api.make_opts(batch=4)
+    opts.reserved[2] = 1
+    assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
+                                P(0), P(0), fake, 1 << 30, None) == 1
+    opts = api.make_opts(batch=4, noise=7)
+    assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
+                                P(0), P(0), fake, 1 << 30, None) == 1
+    opts = api.make_opts(batch=4, delta_o=-1.0)
+    assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
+                                P(0), P(0), fake, 1 << 30, None) == 1
+    opts = api.make_opts(batch=4)
+    assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
+                                P(0), P(0), P(0x1000), 16, None) == 7           # workspace too small
+    assert L.ptycho_adjoint(ctypes.byref(d), fake, fake, fake, fake, 9, 0.0, 4, fake, fake, P(0), P(0),
+                            fake, 1 << 30, None) == 1                            # bad noise model
+    assert L.ptycho_adjoint(ctypes.byref(d), fake, fake, fake, fake, 0, -1.0, 4, fake, fake, P(0), P(0),
+                            fake, 1 << 30, None) == 1                            # negative eps
+    assert L.ptycho_status_read(P(0), None) == 7
+    assert L.ptycho_workspace_init(P(0x1001), 1 << 20, None) == 7
+
+
+def test_binding_refuses_cpu_tensors():
+    import torch
+    from paper_2510_20929_gb300 import api
+    obj = torch.zeros(64, 64, dtype=torch.complex64)
+    probe = torch.zeros(1, 32, 32, dtype=torch.complex64)
+    pos = torch.zeros(3, 2)
+    with pytest.raises(ValueError):
+        api.forward(obj, probe, pos)

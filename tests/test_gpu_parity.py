@@ -1,0 +1,114 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 oracle on the
+same seeded inputs (norm-wise relative error, tolerances derived in the design doc)."""
+import numpy as np
+import pytest
+
+from oracle import ptycho_oracle as orc
+from tests.parity_util import c64, f32pos, problem, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL_FWD = 1e-5      # intensities
+TOL_GRAD = 1e-4     # gradients, chi-derived quantities
+TOL_EPOCH = 1e-4    # object/probe after an epoch
+
+
+def _dev(p):
+    import torch
+    O, P, pos, I_m = c64(p["O"]), c64(p["P"]), f32pos(p["pos"]), np.float32(p["I_m"]).astype(np.float64)
+    return (O, P, pos, I_m), (to_dev(O, torch.complex64), to_dev(P, torch.complex64),
+                              to_dev(pos, torch.float32), to_dev(I_m, torch.float32))
+
+
+CASES = [  # N, M, H, W, J, step
+    (16, 1, 40, 44, 12, 4.0),
+    (16, 3, 41, 37, 9, 3.0),
+    (32, 2, 72, 76, 16, 6.0),
+    (64, 1, 160, 150, 25, 12.0),
+    (64, 3, 150, 160, 20, 12.0),
+    (128, 2, 300, 310, 12, 24.0),
+    (128, 5, 290, 300, 9, 30.0),
+]
+
+
+@pytest.mark.parametrize("N,M,H,W,J,step", CASES)
+def test_forward_matches_oracle(N, M, H, W, J, step):
+    from paper_2510_20929_gb300 import api
+    p = problem(N=N, M=M, H=H, W=W, J=J, step=step)
+    (O, P, pos, _), (dO, dP, dpos, _) = _dev(p)
+    I = api.forward(dO, dP, dpos).cpu().numpy()
+    ref = orc.forward(O, P, pos)
+    e = rel(I, ref)
+    print(f"forward N={N} M={M}: rel {e:.3e}")
+    assert e < TOL_FWD
+    for j in range(J):
+        assert rel(I[j], ref[j]) < 10 * TOL_FWD
+
+
+@pytest.mark.parametrize("noise", ["gaussian", "poisson"])
+@pytest.mark.parametrize("N,M,H,W,J,step", [CASES[1], CASES[2], CASES[4], CASES[6]])
+def test_gradients_match_oracle(noise, N, M, H, W, J, step):
+    from paper_2510_20929_gb300 import api
+    p = problem(N=N, M=M, H=H, W=W, J=J, step=step)
+    (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
+    eps = 1e-6
+    nz = orc.GAUSSIAN if noise == "gaussian" else orc.POISSON
+    L_ref, gO_ref, gP_ref, gr_ref = orc.loss_and_gradients(O, P, pos, I_m, nz, eps)
+    loss, gO, gP, gr = api.adjoint(dO, dP, dpos, dI, noise, eps=eps, batch=5)
+    e = (abs(loss.item() - L_ref) / abs(L_ref), rel(gO.cpu().numpy(), gO_ref),
+         rel(gP.cpu().numpy(), gP_ref), rel(gr.cpu().numpy(), gr_ref))
+    print(f"grad {noise} N={N} M={M}: loss {e[0]:.2e} gO {e[1]:.2e} gP {e[2]:.2e} gr {e[3]:.2e}")
+    assert e[0] < TOL_FWD
+    assert max(e[1:]) < TOL_GRAD
+
+
+def test_vjp_matches_oracle():
+    import torch
+    from paper_2510_20929_gb300 import api
+    p = problem(N=32, M=3, H=72, W=76, J=16, step=6.0)
+    (O, P, pos, _), (dO, dP, dpos, _) = _dev(p)
+    G = np.float32(np.random.default_rng(4).standard_normal((16, 32, 32))).astype(np.float64)
+    gO_ref, gP_ref, gr_ref = orc.vjp(O, P, pos, G)
+    loss, gO, gP, gr = api.adjoint(dO, dP, dpos, to_dev(G, torch.float32), "vjp", batch=7)
+    assert loss is None
+    e = (rel(gO.cpu().numpy(), gO_ref), rel(gP.cpu().numpy(), gP_ref), rel(gr.cpu().numpy(), gr_ref))
+    print(f"vjp: {e}")
+    assert max(e) < TOL_GRAD
+
+
+def _epoch_case(N, M, H, W, J, step, batch, noise, update_probe=True, seed=7):
+    import torch
+    from paper_2510_20929_gb300 import api
+    p = problem(N=N, M=M, H=H, W=W, J=J, step=step, seed=seed)
+    (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
+    order = np.random.default_rng(seed).permutation(J).astype(np.int32)
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN if noise == "gaussian" else orc.POISSON, batch=batch,
+                            delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6, update_probe=update_probe)
+    O_ref, P_ref, L_ref, a_ref = orc.lsqml_epoch(O, P, pos, I_m, order, opts)
+    loss, alpha = api.lsqml_epoch(dO, dP, dpos, dI, to_dev(order, torch.int32), noise=noise, batch=batch,
+                                  delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6, update_probe=update_probe,
+                                  want_alpha=True)
+    e = dict(O=rel(dO.cpu().numpy(), O_ref), P=rel(dP.cpu().numpy(), P_ref),
+             alpha=rel(alpha.cpu().numpy(), a_ref), loss=abs(loss.item() - L_ref) / abs(L_ref))
+    print(f"epoch N={N} M={M} J={J} B={batch} {noise}: " + " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    return e
+
+
+@pytest.mark.parametrize("N,M,H,W,J,step,batch", [
+    (16, 2, 40, 44, 12, 4.0, 12),       # one batch
+    (16, 2, 40, 44, 12, 4.0, 5),        # ragged last batch (5, 5, 2)
+    (32, 3, 72, 76, 16, 6.0, 6),
+    (64, 1, 160, 150, 25, 12.0, 8),
+    (128, 5, 290, 300, 9, 30.0, 4),
+])
+@pytest.mark.parametrize("noise", ["gaussian", "poisson"])
+def test_lsqml_epoch_matches_oracle(N, M, H, W, J, step, batch, noise):
+    e = _epoch_case(N, M, H, W, J, step, batch, noise)
+    assert e["loss"] < TOL_FWD
+    assert e["alpha"] < TOL_EPOCH
+    assert e["O"] < TOL_EPOCH and e["P"] < TOL_EPOCH
+
+
+def test_lsqml_epoch_object_only_matches_oracle():
+    e = _epoch_case(32, 2, 72, 76, 16, 6.0, 16, "gaussian", update_probe=False)
+    assert e["O"] < TOL_EPOCH and e["P"] == 0.0 and e["alpha"] < TOL_EPOCH
