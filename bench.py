@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""LSQML epoch throughput on GB300 (patterns/s), with roofline, CPU-oracle and
+end-to-end figures, printed as one JSON line by rank 0.
+
+A step is one LSQML epoch over the whole synthetic workload: for every
+minibatch, the fused per-position pass (sub-pixel patch, probe modes, 2-D FFT,
+intensity, data term, exit-wave change, inverse FFT, object/illumination
+scatter), the probe reductions, the per-position FP64 step sizes and the
+object/probe update. The default workload is the paper-shaped spiral case:
+probe 128 x 128 with 5 Hermite-Gaussian modes, object 1024 x 1024, 4096
+Fermat-spiral positions, minibatch 256, Poisson counts (1e6 per pattern).
+
+--impl reference times the FP64 numpy oracle on host cores on a bounded
+sample of the same workload (the reference arm; the paper's own code is not
+available). With torchrun (N > 1) every rank runs an independent replica of
+the workload (the path has no exchange step on one GPU): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "patterns/s per LSQML epoch (fwd+adjoint) vs plain FP32 at matched error"
+UNIT = "patterns/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+SMS, FP32_LANES, MAX_SM_GHZ = 152, 128, 2.07   # FP32 ALU peak = SMs * lanes * 2 flop * clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["spiral128", "raster64"], default="spiral128")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--positions", type=int, default=0,
+                    help="use only the first J positions of the workload (profiling runs)")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def make_workload(name, positions=0):
+    from paper_2510_20929_gb300 import synth
+    w = synth.workload_spiral128() if name == "spiral128" else synth.workload_raster64()
+    if positions and positions < w["J"]:
+        w["pos"] = w["pos"][:positions]
+        if w["counts_per"] == "all":
+            w["total_counts"] *= positions / w["J"]
+        w["J"] = positions
+        w["name"] += f"-first{positions}"
+    return w
+
+
+def counts_total(w):
+    return w["total_counts"] * (w["J"] if w["counts_per"] == "pattern" else 1)
+
+
+# ----------------------------------------------------------------------------- algorithmic work
+def pass1_work(N, M, B):
+    """Per-launch algorithmic FLOPs and HBM bytes of the fused per-position pass.
+
+    FLOPs: the forward and inverse 2-D FFT of every mode, 5 N^2 log2(N^2) each.
+    Bytes: measured intensities read (4 N^2), the object tile read ((N+1)^2 x 8),
+    the stored patch, g and h planes written ((2 + M) N^2 x 8) and the
+    (dO, illum) accumulator read-modify-write ((N+1)^2 x 16 x 2).
+    """
+    flops = B * 2 * M * 5 * N * N * math.log2(N * N)
+    nbytes = B * (4 * N * N + 8 * (N + 1) ** 2 + 8 * (2 + M) * N * N + 32 * (N + 1) ** 2)
+    return flops, nbytes
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(w, nbatch, batch, seed=5):
+    """Time the FP64 oracle on `nbatch` minibatches of the workload (its own intensities)."""
+    import numpy as np
+    from oracle import ptycho_oracle as orc
+    from paper_2510_20929_gb300 import synth
+    order = synth.random_order(w["J"], seed)
+    idx = order[: nbatch * batch]
+    P = w["probe"]
+    I = orc.forward(w["object"], P, w["pos"][idx])
+    scale = counts_total(w) / (w["J"] * I.sum(axis=(1, 2)).mean())
+    Im = np.zeros((w["J"], w["N"], w["N"]))
+    Im[idx] = synth.poisson_counts(I * scale, seed)
+    P = P * math.sqrt(scale)
+    O = np.ones_like(w["object"])
+    opts = orc.LsqmlOptions(batch=batch, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9)
+    t0 = time.perf_counter()
+    for b in range(nbatch):
+        O, P, _, _ = orc.lsqml_batch(O, P, w["pos"], Im, idx[b * batch:(b + 1) * batch], opts)
+    dt = time.perf_counter() - t0
+    return nbatch * batch / dt, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    w = make_workload(args.workload, args.positions)
+    batch = w["batch"]
+    vals = []
+    for s in range(args.warmup + args.steps):
+        v, dt = oracle_sample(w, 1, batch, seed=5 + s)
+        if s >= args.warmup:
+            vals.append((v, dt))
+    value = statistics.mean(v for v, _ in vals)
+    ms = 1e3 * statistics.mean(dt for _, dt in vals)
+    sample = (f"1 LSQML minibatch of {batch} positions of the {w['name']} workload per step "
+              f"(object {w['H']}x{w['W']}, {w['M']} modes, {w['N']}^2), FP64 numpy oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "J": w["J"], "N": w["N"], "M": w["M"], "H": w["H"], "W": w["W"],
+                   "batch": batch},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2510_20929_gb300 import api, synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = make_workload(args.workload, args.positions)
+    H, W, N, M, J, B = w["H"], w["W"], w["N"], w["M"], w["J"], w["batch"]
+    O_true = torch.tensor(w["object"], dtype=torch.complex64, device=dev)
+    P = torch.tensor(w["probe"], dtype=torch.complex64, device=dev)
+    pos = torch.tensor(w["pos"], dtype=torch.float32, device=dev)
+    I0 = api.forward(O_true, P, pos)
+    scale = counts_total(w) / (J * I0.sum(dim=(1, 2)).mean().item())
+    P *= math.sqrt(scale)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234 + rank)
+    meas = torch.poisson(I0 * scale, generator=gen).contiguous()
+    del I0
+    order = torch.tensor(synth.random_order(J, 5 + rank), dtype=torch.int32, device=dev)
+    O = torch.ones((H, W), dtype=torch.complex64, device=dev)
+    P_est = P.clone()
+    opts = api.make_opts(noise="gaussian", batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        api.lsqml_epoch(O, P_est, pos, meas, order, opts, check=False)
+    api.lsqml_epoch(O, P_est, pos, meas, order, opts, check=True)   # status check outside timing
+    clocks = Clocks(local_rank)
+    api.profile_enable(True)
+    api.profile_read()
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    losses = []
+    for _ in range(args.steps):
+        loss, _ = api.lsqml_epoch(O, P_est, pos, meas, order, opts, check=False)
+        losses.append(loss)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    api.profile_enable(False)
+    prof = api.profile_read()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = t.item()
+    value = world * J / (ms_max * 1e-3)
+    launches = sum(n for n, _ in prof.values())
+
+    # roofline of the dominant kernel (per-launch averages from the events above)
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_n, dom_ms) = dom
+    hbm, hbm_src = peaks()
+    alu_tflops = SMS * FP32_LANES * 2 * MAX_SM_GHZ * 1e-3
+    if dom_name == "k_pass1":
+        flops, nbytes = pass1_work(N, M, B)
+        avg_s = dom_ms / dom_n * 1e-3
+        # count the ragged last batch exactly: total work over total time
+        nb_list = [min(B, J - b0) for b0 in range(0, J, B)]
+        tot_flops = sum(pass1_work(N, M, nb)[0] for nb in nb_list) * (dom_n // len(nb_list))
+        tot_bytes = sum(pass1_work(N, M, nb)[1] for nb in nb_list) * (dom_n // len(nb_list))
+        t_s = dom_ms * 1e-3
+        alu_ach = tot_flops / t_s * 1e-12
+        hbm_ach = tot_bytes / t_s * 1e-9
+        if alu_ach / alu_tflops >= hbm_ach / hbm:
+            roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_tflops, "unit": "TFLOP/s",
+                    "frac": alu_ach / alu_tflops, "traffic": None,
+                    "peak_source": "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"}
+        else:
+            roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm, "unit": "GB/s",
+                    "frac": hbm_ach / hbm, "traffic": None, "peak_source": hbm_src}
+        roof.update({"kernel": dom_name, "launch_ms": avg_s * 1e3,
+                     "alu_frac": alu_ach / alu_tflops, "hbm_frac": hbm_ach / hbm})
+    else:
+        roof = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None, "kernel": dom_name}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "J": J, "N": N, "M": M, "H": H, "W": W, "batch": B,
+                   "noise": "gaussian", "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (measured intensities %.0f MB read every epoch)"
+                         % (J * N * N * 4 / 1e6),
+                   "profiler": "CUDA event pair around every library launch during the timed steps"},
+        "roofline": roof,
+        "gpu_launches": launches,
+        "kernels": {k: {"launches": n, "ms_per_launch": ms_ / max(n, 1), "share": ms_ / sum(
+            v[1] for v in prof.values())} for k, (n, ms_) in prof.items()},
+        "clocks": clk,
+        "final_loss": losses[-1].item() if losses else None,
+    }
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    if not args.no_e2e:
+        hO = torch.ones((H, W), dtype=torch.complex64).pin_memory()
+        hP = P.cpu().pin_memory()
+        hpos = pos.cpu().pin_memory()
+        hmeas = meas.cpu().pin_memory()
+        horder = order.cpu().pin_memory()
+        del meas
+        torch.cuda.empty_cache()
+        for _ in range(max(1, args.warmup)):
+            api.lsqml_epoch_host(hO, hP, hpos, hmeas, horder, opts, device=dev)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            api.lsqml_epoch_host(hO, hP, hpos, hmeas, horder, opts, device=dev)
+        barrier()
+        dt = (time.perf_counter() - t0) / args.steps
+        t = torch.tensor([dt], device=dev, dtype=torch.float64)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        h2d = hO.numel() * 8 + hP.numel() * 8 + hpos.numel() * 4 + hmeas.numel() * 4 + horder.numel() * 4
+        d2h = hO.numel() * 8 + hP.numel() * 8 + 8
+        out["e2e"] = {"value": world * J / t.item(), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h, "ms_per_step": t.item() * 1e3,
+                      "entry": "ptycho_lsqml_epoch_host (pinned host buffers)"}
+
+    if rank == 0 and not args.no_cpu:
+        v, dt = oracle_sample(w, 2, B)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"2 LSQML minibatches of {B} positions of {w['name']} "
+                                         f"(FP64 numpy oracle, single thread), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -143,6 +143,22 @@ ptycho_status ptycho_status_read(void* ws, void* stream);
 /* Static description of a status code. */
 const char* ptycho_status_string(ptycho_status status);
 
+/* Per-kernel timing. When enabled, each kernel launch of the entry points
+ * above is bracketed by a CUDA event pair recorded on the caller's stream
+ * (this adds two event records per launch and is meant for measurement runs,
+ * not production). ptycho_profile_read() synchronises the recorded events,
+ * writes up to `cap` records (kernels with at least one launch since the last
+ * read) and returns how many kernels had launches; it then resets the
+ * counters. */
+typedef struct {
+  char name[32];
+  int32_t launches;
+  int32_t pad;
+  double total_ms;
+} ptycho_kernel_time;
+ptycho_status ptycho_profile_enable(int32_t on);
+int32_t ptycho_profile_read(ptycho_kernel_time* out, int32_t cap);
+
 /* Library version string. */
 const char* ptycho_version(void);
 

@@ -34,6 +34,11 @@ class PtychoError(RuntimeError):
         super().__init__(f"{where}: {STATUS.get(status, status)} ({status_string(status)})")
 
 
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("total_ms", ctypes.c_double)]
+
+
 class Dims(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("N", ctypes.c_int32),
                 ("M", ctypes.c_int32), ("J", ctypes.c_int32)]
@@ -77,6 +82,8 @@ def lib() -> ctypes.CDLL:
             "ptycho_status_read": (ctypes.c_int, [_P, _P]),
             "ptycho_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "ptycho_version": (ctypes.c_char_p, []),
+            "ptycho_profile_enable": (ctypes.c_int, [ctypes.c_int32]),
+            "ptycho_profile_read": (ctypes.c_int32, [ctypes.POINTER(KernelTime), ctypes.c_int32]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -88,6 +95,18 @@ def lib() -> ctypes.CDLL:
 
 def status_string(status: int) -> str:
     return lib().ptycho_status_string(int(status)).decode()
+
+
+def profile_enable(on: bool = True) -> None:
+    """Bracket every library kernel launch with CUDA events on its stream."""
+    _check(lib().ptycho_profile_enable(1 if on else 0), "ptycho_profile_enable")
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total ms)} since the last read (synchronises)."""
+    buf = (KernelTime * 32)()
+    n = lib().ptycho_profile_read(buf, 32)
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(min(n, 32))}
 
 
 def _check(st: int, where: str) -> None:

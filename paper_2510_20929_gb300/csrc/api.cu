@@ -17,6 +17,7 @@
 #include "../../include/ptycho.h"
 #include "common.cuh"
 #include "launch.h"
+#include "profile.h"
 
 namespace ptycho {
 
@@ -208,15 +209,29 @@ static cudaError_t dispatch_N(int N, Fn&& fn) {
   return cudaErrorInvalidValue;
 }
 
+// Runs `launch` bracketed by the profiler's events for kernel `id` (no-op when off).
+template <class F>
+static cudaError_t timed(int id, cudaStream_t s, F&& launch) {
+  cudaEvent_t e0 = profile_begin(id, s);
+  cudaError_t e = launch();
+  profile_end(id, e0, s);
+  return e;
+}
+
 static cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s) {
-  return dispatch_N(N, [&](auto c) { return launch_pass1<decltype(c)::value>(a, s); });
+  return timed(K_PASS1, s, [&] {
+    return dispatch_N(N, [&](auto c) { return launch_pass1<decltype(c)::value>(a, s); });
+  });
 }
 static cudaError_t pass2(int N, const Pass2Args& a, cudaStream_t s) {
-  return dispatch_N(N, [&](auto c) { return launch_pass2<decltype(c)::value>(a, s); });
+  return timed(K_PASS2, s, [&] {
+    return dispatch_N(N, [&](auto c) { return launch_pass2<decltype(c)::value>(a, s); });
+  });
 }
 
 static cudaError_t probe_reduce(int NN, int M, int nb, const float2* h_s, const float2* o_s, const int* valid,
                                 float2* dPacc, float* Dp, cudaStream_t s) {
+  cudaEvent_t e0 = profile_begin(K_PROBE_REDUCE, s);
   const int chunk = 16;
   dim3 grid((NN + 255) / 256, (nb + chunk - 1) / chunk);
   if (M <= 4)
@@ -225,6 +240,7 @@ static cudaError_t probe_reduce(int NN, int M, int nb, const float2* h_s, const 
     k_probe_reduce<8><<<grid, 256, 0, s>>>(NN, M, nb, chunk, h_s, o_s, valid, dPacc, Dp);
   else
     k_probe_reduce<16><<<grid, 256, 0, s>>>(NN, M, nb, chunk, h_s, o_s, valid, dPacc, Dp);
+  profile_end(K_PROBE_REDUCE, e0, s);
   return cudaGetLastError();
 }
 
@@ -270,10 +286,13 @@ static ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe,
   const int B = o.batch, N = d.N, M = d.M, NN = N * N, HW = d.H * d.W;
   const Layout L = make_layout(d, B);
   Ptrs w = carve(ws, L);
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
   if (loss && (e = cudaMemsetAsync(loss, 0, sizeof(double), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
-  k_init_epoch<<<grid_for(HW > NN ? HW : NN, 256, 4 * 152), 256, 0, s>>>(HW, w.acc, w.U, NN, M, probe, w.dPacc,
-                                                                          w.Dp, w.Sp, w.hdr);
+  timed(K_INIT, s, [&] {
+    k_init_epoch<<<grid_for(HW > NN ? HW : NN, 256, 4 * 152), 256, 0, s>>>(HW, w.acc, w.U, NN, M, probe,
+                                                                            w.dPacc, w.Dp, w.Sp, w.hdr);
+    return cudaSuccess;
+  });
   if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
   const int nbatch = (d.J + B - 1) / B;
   for (int b = 0; b < nbatch; ++b) {
@@ -291,12 +310,18 @@ static ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe,
     a.Sp = w.Sp; a.acc = w.acc;
     a.loss = loss; a.status = &w.hdr->status;
     if ((e = pass1(N, a, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    k_max_illum<<<grid_for(HW, 256, 2 * 152), 256, 0, s>>>(w.acc, HW, sc);
+    timed(K_MAX_ILLUM, s, [&] {
+      k_max_illum<<<grid_for(HW, 256, 2 * 152), 256, 0, s>>>(w.acc, HW, sc);
+      return cudaSuccess;
+    });
     if (o.update_probe) {
       if ((e = probe_reduce(NN, M, nb, w.h, w.o, w.valid, w.dPacc, w.Dp, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     }
-    k_norm_probe<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p,
-                                                        o.update_probe, w.dP, w.Cp, w.Sdp);
+    timed(K_NORM_PROBE, s, [&] {
+      k_norm_probe<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p,
+                                                          o.update_probe, w.dP, w.Cp, w.Sdp);
+      return cudaSuccess;
+    });
     Pass2Args q;
     memset(&q, 0, sizeof(q));
     q.H = d.H; q.W = d.W; q.M = M; q.J = d.J;
@@ -307,9 +332,12 @@ static ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe,
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
     if ((e = pass2(N, q, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    k_update<<<grid_for(HW > NN ? HW : NN, 256, 4 * 152), 256, 0, s>>>(
-        HW, obj, w.acc, w.U, (float)o.delta_o, o.update_object, NN, M, probe, w.dP, w.dPacc, w.Dp, w.Sp,
-        o.update_probe, sc, sc_next);
+    timed(K_UPDATE, s, [&] {
+      k_update<<<grid_for(HW > NN ? HW : NN, 256, 4 * 152), 256, 0, s>>>(
+          HW, obj, w.acc, w.U, (float)o.delta_o, o.update_object, NN, M, probe, w.dP, w.dPacc, w.Dp, w.Sp,
+          o.update_probe, sc, sc_next);
+      return cudaSuccess;
+    });
     if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
   }
   return PTYCHO_OK;

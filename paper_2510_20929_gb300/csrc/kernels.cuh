@@ -25,7 +25,7 @@ template <int N> struct Threads;
 template <> struct Threads<16> { static constexpr int T = 64; };
 template <> struct Threads<32> { static constexpr int T = 128; };
 template <> struct Threads<64> { static constexpr int T = 256; };
-template <> struct Threads<128> { static constexpr int T = 512; };
+template <> struct Threads<128> { static constexpr int T = 1024; };
 
 template <int N>
 struct Pass1Smem {
@@ -144,14 +144,28 @@ __global__ void __launch_bounds__(Threads<N>::T) k_pass1(BatchArgs a) {
     }
     __syncthreads();
     fft2_forward<N, T>(tile, tw, [&](int row, float2 (&v)[R2]) {
+      if constexpr (F::S == 2) {
+        // registers (2q, 2q+1) hold two adjacent columns: 16-byte stores
 #pragma unroll
-      for (int m = 0; m < R2; ++m) {
-        const int col = F::out_index(n, m);
-        const float2 X = cscale(v[m], invN);
-        const float i2 = cabs2(X);
-        float* ri = rI + row * RP + col;
-        *ri = (k == 0) ? i2 : *ri + i2;
-        if (psi_s) psi_s[(size_t)k * NN + row * N + col] = X;
+        for (int q = 0; q < R2 / 2; ++q) {
+          const int col = F::out_index(n, 2 * q);
+          const float2 X0 = cscale(v[2 * q], invN), X1 = cscale(v[2 * q + 1], invN);
+          float2* ri = (float2*)(rI + row * RP + col);
+          const float2 i2 = make_float2(cabs2(X0), cabs2(X1));
+          *ri = (k == 0) ? i2 : make_float2(ri->x + i2.x, ri->y + i2.y);
+          if (psi_s)
+            *(float4*)(psi_s + (size_t)k * NN + row * N + col) = make_float4(X0.x, X0.y, X1.x, X1.y);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < R2; ++m) {
+          const int col = F::out_index(n, m);
+          const float2 X = cscale(v[m], invN);
+          const float i2 = cabs2(X);
+          float* ri = rI + row * RP + col;
+          *ri = (k == 0) ? i2 : *ri + i2;
+          if (psi_s) psi_s[(size_t)k * NN + row * N + col] = X;
+        }
       }
     });
     __syncthreads();
@@ -218,10 +232,21 @@ __global__ void __launch_bounds__(Threads<N>::T) k_pass1(BatchArgs a) {
     fft2_inverse<N, T>(
         tile, tw,
         [&](int row, float2 (&v)[R2]) {
+          if constexpr (F::S == 2) {
 #pragma unroll
-          for (int m = 0; m < R2; ++m) {
-            const int col = F::out_index(n, m);
-            v[m] = cscale(psi_s[(size_t)k * NN + row * N + col], rI[row * RP + col]);
+            for (int q = 0; q < R2 / 2; ++q) {
+              const int col = F::out_index(n, 2 * q);
+              const float4 X = *(const float4*)(psi_s + (size_t)k * NN + row * N + col);
+              const float2 f = *(const float2*)(rI + row * RP + col);
+              v[2 * q] = make_float2(X.x * f.x, X.y * f.x);
+              v[2 * q + 1] = make_float2(X.z * f.y, X.w * f.y);
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < R2; ++m) {
+              const int col = F::out_index(n, m);
+              v[m] = cscale(psi_s[(size_t)k * NN + row * N + col], rI[row * RP + col]);
+            }
           }
         },
         [&](int col, float2 (&v)[R2]) {
@@ -298,22 +323,24 @@ __global__ void __launch_bounds__(Threads<N>::T) k_pass1(BatchArgs a) {
 }
 
 
-template <int N>
-struct Pass2Smem {
-  static constexpr size_t red = 0;
-  static constexpr size_t tile = red + 256 * sizeof(double);
-  static constexpr size_t alpha = tile + (size_t)N * N * sizeof(float2);
-  static constexpr size_t bytes = alpha + 4 * sizeof(double);
-};
+constexpr int PASS2_T = 256;
+
+// Bilinear sample of dO_hat = dO_acc / (illum + damp) at the patch pixel whose
+// four corners start at q (the quotient is taken per corner, then interpolated).
+__device__ __forceinline__ float2 dohat(const float4* q, int W, float w00, float w01, float w10, float w11,
+                                        float damp) {
+  const float4 q00 = __ldg(q), q01 = __ldg(q + 1), q10 = __ldg(q + W), q11 = __ldg(q + W + 1);
+  const float i00 = w00 / (q00.z + damp), i01 = w01 / (q01.z + damp);
+  const float i10 = w10 / (q10.z + damp), i11 = w11 / (q11.z + damp);
+  return make_float2(q00.x * i00 + q01.x * i01 + q10.x * i10 + q11.x * i11,
+                     q00.y * i00 + q01.y * i01 + q10.y * i10 + q11.y * i11);
+}
 
 template <int N>
-__global__ void __launch_bounds__(Threads<N>::T) k_pass2(Pass2Args a) {
-  constexpr int T = Threads<N>::T, NN = N * N;
-  using SM = Pass2Smem<N>;
-  extern __shared__ __align__(16) unsigned char smem[];
-  double* red = (double*)(smem + SM::red);
-  float2* tile = (float2*)(smem + SM::tile);
-  double* alpha_sh = (double*)(smem + SM::alpha);
+__global__ void __launch_bounds__(PASS2_T, 3) k_pass2(Pass2Args a) {
+  constexpr int T = PASS2_T, NN = N * N;
+  __shared__ double red[32 * 5];
+  __shared__ double alpha_sh;
   const int slot = blockIdx.x, tid = threadIdx.x;
   if (!a.valid[slot]) return;
   const int e = a.b0 + slot;
@@ -322,37 +349,46 @@ __global__ void __launch_bounds__(Threads<N>::T) k_pass2(Pass2Args a) {
   float fy, fx;
   tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
   const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
-  const float dmp = a.delta_o * __uint_as_float(a.sc->max_illum);
+  const float damp = a.delta_o * __uint_as_float(a.sc->max_illum);
   const size_t slotNN = (size_t)slot * NN;
   const int M = a.M;
+  const float2* g_s = a.g_s + slotNN;
+  const float2* o_s = a.o_s + slotNN;
+  const float2* h_s = a.h_s + slotNN * M;
 
   float A11 = 0.f, A12 = 0.f, A22 = 0.f, b1 = 0.f, b2 = 0.f;
-  for (int p = tid; p < NN; p += T) {
+  // two adjacent pixels per thread and iteration: 16-byte loads of the planes
+  for (int p = 2 * tid; p < NN; p += 2 * T) {
     const int r = p / N, c = p % N;
-    const float2 g = a.g_s[slotNN + p];
-    tile[tix<N>(r, c)] = g;
-    float2 d = make_float2(0.f, 0.f);
-    if (a.update_object) {
-      const float4* q = a.acc + (size_t)(ty + r) * a.W + (tx + c);
-      const float4 q00 = __ldg(q), q01 = __ldg(q + 1), q10 = __ldg(q + a.W), q11 = __ldg(q + a.W + 1);
-      const float i00 = 1.f / (q00.z + dmp), i01 = 1.f / (q01.z + dmp);
-      const float i10 = 1.f / (q10.z + dmp), i11 = 1.f / (q11.z + dmp);
-      d.x = w00 * q00.x * i00 + w01 * q01.x * i01 + w10 * q10.x * i10 + w11 * q11.x * i11;
-      d.y = w00 * q00.y * i00 + w01 * q01.y * i01 + w10 * q10.y * i10 + w11 * q11.y * i11;
+    const float4 g2 = __ldcs((const float4*)(g_s + p));
+    const float4 o2 = __ldcs((const float4*)(o_s + p));
+    const float2 g[2] = {make_float2(g2.x, g2.y), make_float2(g2.z, g2.w)};
+    const float2 o[2] = {make_float2(o2.x, o2.y), make_float2(o2.z, o2.w)};
+    const float2 sp = __ldg((const float2*)(a.Sp + p));
+    const float2 sdp = __ldg((const float2*)(a.Sdp + p));
+    const float4 cp2 = __ldg((const float4*)(a.Cp + p));
+    const float2 cp[2] = {make_float2(cp2.x, cp2.y), make_float2(cp2.z, cp2.w)};
+    const float spv[2] = {sp.x, sp.y}, sdpv[2] = {sdp.x, sdp.y};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      float2 d = make_float2(0.f, 0.f);
+      if (a.update_object)
+        d = dohat(a.acc + (size_t)(ty + r) * a.W + (tx + c + u), a.W, w00, w01, w10, w11, damp);
+      A11 += cabs2(d) * spv[u];
+      const float2 od = cmulc(d, o[u]);       // conj(d) o
+      A12 += od.x * cp[u].x - od.y * cp[u].y;  // Re(conj(d) o Cp)
+      A22 += cabs2(o[u]) * sdpv[u];
+      b1 += d.x * g[u].x + d.y * g[u].y;       // Re(conj(d) g)
     }
-    const float2 o = a.o_s[slotNN + p];
-    A11 += cabs2(d) * __ldg(a.Sp + p);
-    const float2 od = cmulc(d, o);            // conj(d) o
-    const float2 cp = __ldg(a.Cp + p);
-    A12 += od.x * cp.x - od.y * cp.y;          // Re(conj(d) o Cp)
-    A22 += cabs2(o) * __ldg(a.Sdp + p);
-    b1 += d.x * g.x + d.y * g.y;               // Re(conj(d) g)
-    if (a.update_probe) {
-      for (int k = 0; k < M; ++k) {
-        const float2 dp = __ldg(a.dP + (size_t)k * NN + p);
-        const float2 h = a.h_s[(slotNN * M) + (size_t)k * NN + p];
-        b2 += dp.x * h.x + dp.y * h.y;         // Re(conj(dP_k) h_k)
-      }
+  }
+  if (a.update_probe) {
+    // b2 = Re sum_k <dP_k, h_k>: the M planes are contiguous, two pixels per 16-byte load
+    const float4* h4 = (const float4*)h_s;
+    const float4* d4 = (const float4*)a.dP;
+    for (int q = tid; q < M * NN / 2; q += T) {
+      const float4 dp = __ldg(d4 + q);
+      const float4 h = __ldcs(h4 + q);
+      b2 += dp.x * h.x + dp.y * h.y + dp.z * h.z + dp.w * h.w;   // Re(conj(dP_k) h_k)
     }
   }
   double v[5] = {A11, A12, A22, b1, b2};
@@ -370,7 +406,7 @@ __global__ void __launch_bounds__(Threads<N>::T) k_pass2(Pass2Args a) {
       aO = d11 > 0.0 ? r1 / d11 : 0.0;
       aP = d22 > 0.0 ? r2 / d22 : 0.0;
     }
-    alpha_sh[0] = aO;
+    alpha_sh = aO;
     if (a.alpha_out) {
       a.alpha_out[2 * j] = aO;
       a.alpha_out[2 * j + 1] = aP;
@@ -380,16 +416,18 @@ __global__ void __launch_bounds__(Threads<N>::T) k_pass2(Pass2Args a) {
   }
   __syncthreads();
   if (!a.update_object) return;
-  const float aO = (float)alpha_sh[0];
+  const float aO = (float)alpha_sh;
+  const float c00 = aO * w00, c01 = aO * w01, c10 = aO * w10, c11 = aO * w11;
   constexpr int N1 = N + 1;
+  // alpha_O S_j^T g: each object pixel of the (N+1)^2 tile gathers its four patch neighbours
   for (int q = tid; q < N1 * N1; q += T) {
     const int y = q / N1, x = q % N1;
-    float2 s = make_float2(0.f, 0.f);
-    if (y < N && x < N) { const float2 g = tile[tix<N>(y, x)]; s.x += w00 * g.x; s.y += w00 * g.y; }
-    if (y < N && x > 0) { const float2 g = tile[tix<N>(y, x - 1)]; s.x += w01 * g.x; s.y += w01 * g.y; }
-    if (y > 0 && x < N) { const float2 g = tile[tix<N>(y - 1, x)]; s.x += w10 * g.x; s.y += w10 * g.y; }
-    if (y > 0 && x > 0) { const float2 g = tile[tix<N>(y - 1, x - 1)]; s.x += w11 * g.x; s.y += w11 * g.y; }
-    atomicAdd(a.U + (size_t)(ty + y) * a.W + (tx + x), make_float2(aO * s.x, aO * s.y));
+    float2 sacc = make_float2(0.f, 0.f);
+    if (y < N && x < N) { const float2 g = g_s[y * N + x]; sacc.x += c00 * g.x; sacc.y += c00 * g.y; }
+    if (y < N && x > 0) { const float2 g = g_s[y * N + x - 1]; sacc.x += c01 * g.x; sacc.y += c01 * g.y; }
+    if (y > 0 && x < N) { const float2 g = g_s[(y - 1) * N + x]; sacc.x += c10 * g.x; sacc.y += c10 * g.y; }
+    if (y > 0 && x > 0) { const float2 g = g_s[(y - 1) * N + x - 1]; sacc.x += c11 * g.x; sacc.y += c11 * g.y; }
+    atomicAdd(a.U + (size_t)(ty + y) * a.W + (tx + x), sacc);
   }
 }
 
@@ -409,11 +447,8 @@ cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s) {
 
 template <int N>
 cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s) {
-  constexpr size_t sm = Pass2Smem<N>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_pass2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
   if (a.nb <= 0) return cudaSuccess;
-  k_pass2<N><<<a.nb, Threads<N>::T, sm, s>>>(a);
+  k_pass2<N><<<a.nb, PASS2_T, 0, s>>>(a);
   return cudaGetLastError();
 }
 
