@@ -111,6 +111,19 @@ __device__ __forceinline__ float2 bilinear(const float2* __restrict__ O, int W, 
                      w00 * a.y + w01 * b.y + w10 * c.y + w11 * d.y);
 }
 
+// Two horizontally adjacent bilinear samples (columns x and x+1): six corner loads.
+__device__ __forceinline__ void bilinear2(const float2* __restrict__ O, int W, int y, int x, float fy, float fx,
+                                          float2& o0, float2& o1) {
+  const float2* p = O + (size_t)y * W + x;
+  const float2 a0 = __ldg(p), a1 = __ldg(p + 1), a2 = __ldg(p + 2);
+  const float2 b0 = __ldg(p + W), b1 = __ldg(p + W + 1), b2 = __ldg(p + W + 2);
+  const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
+  o0 = make_float2(w00 * a0.x + w01 * a1.x + w10 * b0.x + w11 * b1.x,
+                   w00 * a0.y + w01 * a1.y + w10 * b0.y + w11 * b1.y);
+  o1 = make_float2(w00 * a1.x + w01 * a2.x + w10 * b1.x + w11 * b2.x,
+                   w00 * a1.y + w01 * a2.y + w10 * b1.y + w11 * b2.y);
+}
+
 // Block-wide sum of NV doubles; result valid in thread 0. `red` holds 32*NV doubles.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {

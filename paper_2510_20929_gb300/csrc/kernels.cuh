@@ -92,7 +92,7 @@ __device__ __forceinline__ void fft2_inverse(float2* tile, const float2* tw, In&
 }
 
 template <int N>
-__global__ void __launch_bounds__(Threads<N>::T) k_pass1(BatchArgs a) {
+__global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
   constexpr int T = Threads<N>::T;
   using F = Fft2<N>;
   using SM = Pass1Smem<N>;
@@ -131,16 +131,21 @@ __global__ void __launch_bounds__(Threads<N>::T) k_pass1(BatchArgs a) {
 #pragma unroll 1
   for (int k = 0; k < M; ++k) {
     const float2* Pk = a.probe + (size_t)k * NN;
-    for (int p = tid; p < NN; p += T) {
+    // psi_k = P_k o_j into the tile, two adjacent pixels per thread and iteration
+    for (int p = 2 * tid; p < NN; p += 2 * T) {
       const int r = p / N, c = p % N;
-      float2 o;
+      float2 o0, o1;
       if (k == 0 || !o_s) {
-        o = bilinear(a.obj, a.W, ty + r, tx + c, fy, fx);
-        if (k == 0 && o_s) o_s[p] = o;
+        bilinear2(a.obj, a.W, ty + r, tx + c, fy, fx, o0, o1);
+        if (k == 0 && o_s) *(float4*)(o_s + p) = make_float4(o0.x, o0.y, o1.x, o1.y);
       } else {
-        o = o_s[p];
+        const float4 o2 = *(const float4*)(o_s + p);
+        o0 = make_float2(o2.x, o2.y);
+        o1 = make_float2(o2.z, o2.w);
       }
-      tile[tix<N>(r, c)] = cmul(__ldg(Pk + p), o);
+      const float4 P2 = __ldg((const float4*)(Pk + p));
+      tile[tix<N>(r, c)] = cmul(make_float2(P2.x, P2.y), o0);
+      tile[tix<N>(r, c + 1)] = cmul(make_float2(P2.z, P2.w), o1);
     }
     __syncthreads();
     fft2_forward<N, T>(tile, tw, [&](int row, float2 (&v)[R2]) {
@@ -249,17 +254,24 @@ __global__ void __launch_bounds__(Threads<N>::T) k_pass1(BatchArgs a) {
             }
           }
         },
-        [&](int col, float2 (&v)[R2]) {
-#pragma unroll
-          for (int n2 = 0; n2 < R2; ++n2) {
-            const int row = F::in_index(n, n2);
-            const int pix = row * N + col;
-            const float2 chi = v[n2];
-            const float2 gc = cmulc(__ldg(Pk + pix), chi);
-            g_s[pix] = (k == 0) ? gc : cadd(g_s[pix], gc);
-            h_s[(size_t)k * NN + pix] = cmulc(o_s[pix], chi);
-          }
-        });
+        [&](int col, float2 (&v)[R2]) { F::template store_in<false>(v, tile, col, n); });
+    __syncthreads();
+    // chi_k is in the tile (natural layout): g += conj(P_k) chi_k, h_k = conj(o) chi_k
+    for (int p = 2 * tid; p < NN; p += 2 * T) {
+      const int r = p / N, c = p % N;
+      const float2 x0 = tile[tix<N>(r, c)], x1 = tile[tix<N>(r, c + 1)];
+      const float4 P2 = __ldg((const float4*)(Pk + p));
+      const float4 o2 = *(const float4*)(o_s + p);
+      const float2 g0 = cmulc(make_float2(P2.x, P2.y), x0), g1 = cmulc(make_float2(P2.z, P2.w), x1);
+      float4 gv = make_float4(g0.x, g0.y, g1.x, g1.y);
+      if (k > 0) {
+        const float4 gp = *(const float4*)(g_s + p);
+        gv = make_float4(gv.x + gp.x, gv.y + gp.y, gv.z + gp.z, gv.w + gp.w);
+      }
+      *(float4*)(g_s + p) = gv;
+      const float2 h0 = cmulc(make_float2(o2.x, o2.y), x0), h1 = cmulc(make_float2(o2.z, o2.w), x1);
+      __stcs((float4*)(h_s + (size_t)k * NN + p), make_float4(h0.x, h0.y, h1.x, h1.y));
+    }
   }
   __syncthreads();
 
