@@ -145,31 +145,37 @@ template <int DIR> struct Dft<16, DIR> {
   }
 };
 
-// Per-size line split and tile swizzle. fr/fc are linear over GF(2).
+// Per-size line split and tile swizzle. The swizzle XORs the low four column
+// bits with f(r, c) = fr(r) ^ fc(c >> 4), shift-XOR maps that are linear over
+// GF(2). The maps and the lane assignment (INTER: the R1 lanes of a line are
+// interleaved across the warp rather than consecutive) come from a search over
+// a bank model in which 8-byte accesses are served per half-warp and 16-byte
+// accesses per quarter-warp; with them every shared access family used here
+// needs the minimum 2 (8-byte) or 4 (16-byte) wavefronts per warp instruction.
 template <int N> struct FftCfg;
 template <> struct FftCfg<16> {
   static constexpr int R1 = 4, R2 = 4;
-  static constexpr bool KMAJ = false;
-  __host__ __device__ static constexpr int fr(int r) { return ((r << 1) ^ r) & 15; }
+  static constexpr bool INTER = false;
+  __host__ __device__ static constexpr int fr(int r) { return ((r << 2) ^ r) & 15; }
   __host__ __device__ static constexpr int fc(int) { return 0; }
 };
 template <> struct FftCfg<32> {
   static constexpr int R1 = 4, R2 = 8;
-  static constexpr bool KMAJ = true;
-  __host__ __device__ static constexpr int fr(int r) { return ((r << 1) ^ r) & 15; }
+  static constexpr bool INTER = true;
+  __host__ __device__ static constexpr int fr(int r) { return ((r << 3) ^ (r << 2) ^ r) & 15; }
   __host__ __device__ static constexpr int fc(int) { return 0; }
 };
 template <> struct FftCfg<64> {
   static constexpr int R1 = 8, R2 = 8;
-  static constexpr bool KMAJ = false;
-  __host__ __device__ static constexpr int fr(int r) { return ((r << 1) ^ (r >> 1)) & 15; }
-  __host__ __device__ static constexpr int fc(int cb) { return cb & 15; }
+  static constexpr bool INTER = true;
+  __host__ __device__ static constexpr int fr(int r) { return ((r << 2) ^ (r >> 1)) & 15; }
+  __host__ __device__ static constexpr int fc(int cb) { return (cb << 1) & 15; }
 };
 template <> struct FftCfg<128> {
   static constexpr int R1 = 8, R2 = 16;
-  static constexpr bool KMAJ = true;
-  __host__ __device__ static constexpr int fr(int r) { return ((r << 1) ^ r ^ (r >> 2)) & 15; }
-  __host__ __device__ static constexpr int fc(int cb) { return (cb << 1) & 15; }
+  static constexpr bool INTER = true;
+  __host__ __device__ static constexpr int fr(int r) { return ((r << 3) ^ (r << 1) ^ (r >> 2)) & 15; }
+  __host__ __device__ static constexpr int fc(int cb) { return cb & 15; }
 };
 
 // Physical float2 index of tile element (r, c) for runtime r, c.
@@ -178,10 +184,58 @@ __device__ __forceinline__ int tix(int r, int c) {
   return r * N + (c ^ FftCfg<N>::fr(r) ^ FftCfg<N>::fc(c >> 4));
 }
 
+// Natural-layout traversal of the tile by pixel pairs: thread t handles the
+// pairs (r, c), (r, c+1) with p = 2t + 2T q, c even. The swizzle moves a pair as
+// a unit (it only flips the low column bits), possibly swapping its halves, so
+// every pair is one 16-byte shared-memory access.
+template <int N, int T>
+struct NatPairs {
+  using C = FftCfg<N>;
+  static constexpr int RS = 2 * T / N;           // rows advanced per step (power of two)
+  static constexpr int STEPS = N * N / (2 * T);
+  static_assert(RS >= 1, "needs 2T >= N");
+  int r0, c, xr;
+  __device__ __forceinline__ NatPairs() {
+    const int p = 2 * (int)threadIdx.x;
+    r0 = p / N;
+    c = p % N;
+    xr = c ^ C::fr(r0) ^ C::fc(c >> 4);
+  }
+  __device__ __forceinline__ int row(int q) const { return r0 + RS * q; }
+  __device__ __forceinline__ int pix(int q) const { return row(q) * N + c; }
+  // physical index of pixel (row(q), c); pixel c+1 sits at phys ^ 1
+  __device__ __forceinline__ int phys(int q) const { return row(q) * N + (xr ^ C::fr(RS * q)); }
+};
+
+__device__ __forceinline__ void store_pair(float2* tile, int ph, float2 a, float2 b) {
+  float4* p = (float4*)(tile + (ph & ~1));
+  *p = (ph & 1) ? make_float4(b.x, b.y, a.x, a.y) : make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void load_pair(const float2* tile, int ph, float2& a, float2& b) {
+  const float4 v = *(const float4*)(tile + (ph & ~1));
+  if (ph & 1) {
+    a = make_float2(v.z, v.w);
+    b = make_float2(v.x, v.y);
+  } else {
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+  }
+}
+
 template <int N>
 struct Fft2 {
   using C = FftCfg<N>;
-  static constexpr int R1 = C::R1, R2 = C::R2, S = R2 / R1;
+  static constexpr int R1 = C::R1, R2 = C::R2, S = R2 / R1, G = 32 / R1;
+
+  // Lane n (0..R1-1) within its line and the thread's line slot: the G lines
+  // of a warp are consecutive; the R1 lanes of a line are G lanes apart
+  // (INTER) or consecutive.
+  __device__ __forceinline__ static int line_lane() {
+    return C::INTER ? (int)(threadIdx.x & 31) / G : (int)threadIdx.x % R1;
+  }
+  __device__ __forceinline__ static int line_slot() {
+    return C::INTER ? (int)(threadIdx.x >> 5) * G + (int)(threadIdx.x & 31) % G : (int)threadIdx.x / R1;
+  }
 
   // Address of element i (= i_rt | i_ct, disjoint bits) of `line`.
   template <bool ROW>
@@ -204,19 +258,16 @@ struct Fft2 {
                                                   const float2* tw) {
     Dft<R2, -1>::run(v);
 #pragma unroll
-    for (int k2 = 1; k2 < R2; ++k2) v[k2] = cmul(v[k2], tw[n * k2]);
+    for (int k2 = 1; k2 < R2; ++k2) v[k2] = cmul(v[k2], tw[n * (R2 + 1) + k2]);
     // exchange: lane n writes Y[n][k2]; lane t reads Y[n1][S*t + s]
-    const int xn = C::KMAJ ? R2 * n : n;
 #pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) tile[addr<ROW>(line, xn, C::KMAJ ? k2 : R1 * k2)] = v[k2];
+    for (int k2 = 0; k2 < R2; ++k2) tile[addr<ROW>(line, n, R1 * k2)] = v[k2];
     __syncwarp();
     float2 w[S][R1];
-    const int xk = C::KMAJ ? S * n : R1 * S * n;
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1)
 #pragma unroll
-      for (int s = 0; s < S; ++s)
-        w[s][n1] = tile[addr<ROW>(line, xk, (C::KMAJ ? R2 * n1 + s : n1 + R1 * s))];
+      for (int s = 0; s < S; ++s) w[s][n1] = tile[addr<ROW>(line, R1 * S * n, n1 + R1 * s)];
     __syncwarp();
 #pragma unroll
     for (int s = 0; s < S; ++s) Dft<R1, -1>::run(w[s]);
@@ -238,19 +289,16 @@ struct Fft2 {
       for (int s = 0; s < S; ++s) w[s][k1] = v[k1 * S + s];
 #pragma unroll
     for (int s = 0; s < S; ++s) Dft<R1, 1>::run(w[s]);
-    const int xk = C::KMAJ ? S * n : R1 * S * n;
 #pragma unroll
     for (int n1 = 0; n1 < R1; ++n1)
 #pragma unroll
-      for (int s = 0; s < S; ++s)
-        tile[addr<ROW>(line, xk, (C::KMAJ ? R2 * n1 + s : n1 + R1 * s))] = w[s][n1];
-    __syncwarp();
-    const int xn = C::KMAJ ? R2 * n : n;
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) v[k2] = tile[addr<ROW>(line, xn, C::KMAJ ? k2 : R1 * k2)];
+      for (int s = 0; s < S; ++s) tile[addr<ROW>(line, R1 * S * n, n1 + R1 * s)] = w[s][n1];
     __syncwarp();
 #pragma unroll
-    for (int k2 = 1; k2 < R2; ++k2) v[k2] = cmulc(tw[n * k2], v[k2]);
+    for (int k2 = 0; k2 < R2; ++k2) v[k2] = tile[addr<ROW>(line, n, R1 * k2)];
+    __syncwarp();
+#pragma unroll
+    for (int k2 = 1; k2 < R2; ++k2) v[k2] = cmulc(tw[n * (R2 + 1) + k2], v[k2]);
     Dft<R2, 1>::run(v);
   }
 
@@ -286,12 +334,20 @@ struct Fft2 {
   __device__ __forceinline__ static int in_index(int n, int m) { return n + R1 * m; }
 };
 
-// Twiddle table tw[m] = exp(-2 pi i m / N), m in [0, N), written by the whole CTA.
+// Twiddle table tw[n*(R2+1) + k2] = exp(-2 pi i n k2 / N) for n < R1, k2 <= R2
+// (the padding column makes the per-k2 reads of the R1 lanes of a line hit
+// distinct banks). Written by the whole CTA.
+template <int N>
+struct Twiddles {
+  static constexpr int R1 = FftCfg<N>::R1, R2 = FftCfg<N>::R2, COUNT = R1 * (R2 + 1);
+};
 template <int N>
 __device__ __forceinline__ void make_twiddles(float2* tw) {
-  for (int m = threadIdx.x; m < N; m += blockDim.x) {
+  constexpr int R2 = FftCfg<N>::R2;
+  for (int m = threadIdx.x; m < Twiddles<N>::COUNT; m += blockDim.x) {
+    const int n = m / (R2 + 1), k2 = m % (R2 + 1);
     float s, c;
-    sincospif(2.0f * (float)m / (float)N, &s, &c);
+    sincospif(2.0f * (float)(n * k2) / (float)N, &s, &c);
     tw[m] = make_float2(c, -s);
   }
 }

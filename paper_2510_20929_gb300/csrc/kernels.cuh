@@ -33,7 +33,7 @@ struct Pass1Smem {
   static constexpr size_t red = 0;
   static constexpr size_t tile = red + 256 * sizeof(double);
   static constexpr size_t tw = tile + (size_t)N * N * sizeof(float2);
-  static constexpr size_t rI = tw + (size_t)N * sizeof(float2);
+  static constexpr size_t rI = tw + (size_t)Twiddles<N>::COUNT * sizeof(float2);
   static constexpr size_t bytes = rI + (size_t)N * RP * sizeof(float);
 };
 
@@ -44,7 +44,7 @@ template <int N, int T, class Out>
 __device__ __forceinline__ void fft2_forward(float2* tile, const float2* tw, Out&& out) {
   using F = Fft2<N>;
   constexpr int R1 = F::R1, R2 = F::R2, L = T / R1, ITER = N / L;
-  const int n = threadIdx.x % R1, gid = threadIdx.x / R1;
+  const int n = F::line_lane(), gid = F::line_slot();
 #pragma unroll 1
   for (int it = 0; it < ITER; ++it) {
     const int col = gid + it * L;
@@ -71,7 +71,7 @@ template <int N, int T, class In, class Out>
 __device__ __forceinline__ void fft2_inverse(float2* tile, const float2* tw, In&& in, Out&& out) {
   using F = Fft2<N>;
   constexpr int R1 = F::R1, R2 = F::R2, L = T / R1, ITER = N / L;
-  const int n = threadIdx.x % R1, gid = threadIdx.x / R1;
+  const int n = F::line_lane(), gid = F::line_slot();
 #pragma unroll 1
   for (int it = 0; it < ITER; ++it) {
     const int row = gid + it * L;
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
   float* rI = (float*)(smem + SM::rI);
 
   const int slot = blockIdx.x;
-  const int tid = threadIdx.x, n = tid % R1;
+  const int tid = threadIdx.x, n = F::line_lane();
   const int e = a.b0 + slot;
   const int j = a.order ? a.order[e] : e;
   int ty = 0, tx = 0;
@@ -132,8 +132,10 @@ __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
   for (int k = 0; k < M; ++k) {
     const float2* Pk = a.probe + (size_t)k * NN;
     // psi_k = P_k o_j into the tile, two adjacent pixels per thread and iteration
-    for (int p = 2 * tid; p < NN; p += 2 * T) {
-      const int r = p / N, c = p % N;
+    const NatPairs<N, T> np;
+#pragma unroll 1
+    for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+      const int r = np.row(q), c = np.c, p = np.pix(q);
       float2 o0, o1;
       if (k == 0 || !o_s) {
         bilinear2(a.obj, a.W, ty + r, tx + c, fy, fx, o0, o1);
@@ -144,8 +146,7 @@ __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
         o1 = make_float2(o2.z, o2.w);
       }
       const float4 P2 = __ldg((const float4*)(Pk + p));
-      tile[tix<N>(r, c)] = cmul(make_float2(P2.x, P2.y), o0);
-      tile[tix<N>(r, c + 1)] = cmul(make_float2(P2.z, P2.w), o1);
+      store_pair(tile, np.phys(q), cmul(make_float2(P2.x, P2.y), o0), cmul(make_float2(P2.z, P2.w), o1));
     }
     __syncthreads();
     fft2_forward<N, T>(tile, tw, [&](int row, float2 (&v)[R2]) {
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
   bool bad = false;
   {
     constexpr int L = T / R1, ITER = N / L;
-    const int gid = tid / R1;
+    const int gid = F::line_slot();
 #pragma unroll 1
     for (int it = 0; it < ITER; ++it) {
       const int row = gid + it * L;
@@ -257,9 +258,12 @@ __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
         [&](int col, float2 (&v)[R2]) { F::template store_in<false>(v, tile, col, n); });
     __syncthreads();
     // chi_k is in the tile (natural layout): g += conj(P_k) chi_k, h_k = conj(o) chi_k
-    for (int p = 2 * tid; p < NN; p += 2 * T) {
-      const int r = p / N, c = p % N;
-      const float2 x0 = tile[tix<N>(r, c)], x1 = tile[tix<N>(r, c + 1)];
+    const NatPairs<N, T> np;
+#pragma unroll 1
+    for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+      const int p = np.pix(q);
+      float2 x0, x1;
+      load_pair(tile, np.phys(q), x0, x1);
       const float4 P2 = __ldg((const float4*)(Pk + p));
       const float4 o2 = *(const float4*)(o_s + p);
       const float2 g0 = cmulc(make_float2(P2.x, P2.y), x0), g1 = cmulc(make_float2(P2.z, P2.w), x1);
@@ -276,7 +280,14 @@ __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
   __syncthreads();
 
   // ---- scatter S_j^T g (and the illumination) into the object frame ----------------
-  for (int p = tid; p < NN; p += T) tile[tix<N>(p / N, p % N)] = g_s[p];
+  {
+    const NatPairs<N, T> np;
+#pragma unroll 1
+    for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+      const float4 g2 = *(const float4*)(g_s + np.pix(q));
+      store_pair(tile, np.phys(q), make_float2(g2.x, g2.y), make_float2(g2.z, g2.w));
+    }
+  }
   __syncthreads();
   const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
   const bool lsqml = (mode == MODE_LSQML_GAUSS || mode == MODE_LSQML_POISSON);
