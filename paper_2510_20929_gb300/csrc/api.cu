@@ -1,13 +1,13 @@
 // C-ABI entry points of libptycho and the object/probe-frame kernels of the
-// LSQML minibatch (preconditioner maxima, probe direction, update).
+// LSQML minibatch (probe direction, preconditioner maxima, probe update).
 //
 // Per minibatch the epoch runs: k_pass1 (per position: forward model, data
-// term, chi, scatter of the object direction and illumination), k_max_illum
-// (max of the illumination for the relative damping delta_O), k_probe_reduce
-// (sum over the batch of conj(o_j) chi_jk and |o_j|^2), k_normP (preconditioned
-// probe direction and the per-pixel planes the step solve needs), k_pass2 (per
-// position: step sizes and the alpha-weighted object scatter), k_update
-// (object and probe update, accumulators cleared for the next batch).
+// term, chi, scatter of the object direction and illumination), k_probe_reduce
+// (batch sums of conj(o_j) chi_jk and |o_j|^2 per probe pixel, and the maxima
+// used by the relative dampings), k_norm_probe (preconditioned probe direction
+// and the per-pixel planes of the step solve), k_pass2 (per position: FP64 step
+// sizes and the alpha-weighted, preconditioned object update), a memset of the
+// object-frame accumulator, and k_probe_update.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -24,73 +24,87 @@ namespace ptycho {
 // ---------------------------------------------------------------------------
 // Object/probe-frame kernels (window size is a runtime argument here).
 // ---------------------------------------------------------------------------
-__global__ void k_init_epoch(int HW, float4* acc, float2* U, int NN, int M, const float2* probe,
-                             float2* dPacc, float* Dp, float* Sp, WsHeader* hdr) {
-  const int stride = gridDim.x * blockDim.x;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += stride) {
-    acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-    U[p] = make_float2(0.f, 0.f);
-  }
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += stride) {
+__global__ void k_init_epoch(int NN, int M, const float2* probe, float* Sp, WsHeader* hdr) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += gridDim.x * blockDim.x) {
     float s = 0.f;
-    for (int k = 0; k < M; ++k) {
-      s += cabs2(probe[(size_t)k * NN + p]);
-      dPacc[(size_t)k * NN + p] = make_float2(0.f, 0.f);
-    }
+    for (int k = 0; k < M; ++k) s += cabs2(probe[(size_t)k * NN + p]);
     Sp[p] = s;
-    Dp[p] = 0.f;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) memset(hdr->sc, 0, sizeof(hdr->sc));
 }
 
-__global__ void k_max_illum(const float4* acc, int HW, BatchScalars* sc) {
+// Batch sums per probe pixel, without atomics: for blockIdx.y == 0 the thread
+// (k, q) with k < M sums conj(o_j) chi_jk over the batch (pixel pair q, into
+// dPacc_k, added to its previous value when `accumulate`), and k == M sums
+// |o_j|^2 into Dp and reports max(Dp). Blocks with blockIdx.y == 1 scan the
+// illumination plane for its maximum. U positions are loaded per iteration.
+template <int U>
+__global__ void k_probe_reduce(int NN, int M, int nb, const float2* __restrict__ h_s,
+                               const float2* __restrict__ o_s, const int* __restrict__ valid, float2* dPacc,
+                               int accumulate, float* Dp, const float4* __restrict__ acc, int HW,
+                               BatchScalars* sc) {
   __shared__ float red[32];
-  float m = 0.f;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x)
-    m = fmaxf(m, acc[p].z);
-  m = block_max(m, red);
-  if (threadIdx.x == 0) atomicMax(&sc->max_illum, __float_as_uint(m));
-}
-
-// dPacc_k[p] += sum_{i in chunk} h_s[i][k][p];  Dp[p] += sum |o_s[i][p]|^2
-template <int MMAX>
-__global__ void k_probe_reduce(int NN, int M, int nb, int chunk, const float2* __restrict__ h_s,
-                               const float2* __restrict__ o_s, const int* __restrict__ valid,
-                               float2* dPacc, float* Dp) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= NN) return;
-  const int i0 = blockIdx.y * chunk, i1 = min(nb, i0 + chunk);
-  float2 s[MMAX];
-#pragma unroll
-  for (int k = 0; k < MMAX; ++k) s[k] = make_float2(0.f, 0.f);
-  float d = 0.f;
-  for (int i = i0; i < i1; ++i) {
-    if (!valid[i]) continue;
-    const float2* h = h_s + (size_t)i * M * NN + p;
-#pragma unroll
-    for (int k = 0; k < MMAX; ++k)
-      if (k < M) {
-        const float2 v = h[(size_t)k * NN];
-        s[k].x += v.x;
-        s[k].y += v.y;
-      }
-    if (Dp) d += cabs2(o_s[(size_t)i * NN + p]);
+  if (blockIdx.y == 1) {
+    if (!acc) return;
+    float m = 0.f;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x)
+      m = fmaxf(m, __ldcs(&acc[p].z));
+    m = block_max(m, red);
+    if (threadIdx.x == 0) atomicMax(&sc->max_illum, __float_as_uint(m));
+    return;
   }
+  const int NP = NN / 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = t / NP, q = t % NP;
+  float dmax = 0.f;
+  if (k < M && dPacc) {
+    const float4* h = (const float4*)h_s + (size_t)k * NP + q;
+    const size_t stride = (size_t)M * NP;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < nb; i += U) {
+      float4 v[U];
 #pragma unroll
-  for (int k = 0; k < MMAX; ++k)
-    if (k < M) atomicAdd(dPacc + (size_t)k * NN + p, s[k]);
-  if (Dp) atomicAdd(Dp + p, d);
+      for (int u = 0; u < U; ++u)
+        v[u] = (i + u < nb && valid[i + u]) ? __ldcs(h + (size_t)(i + u) * stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        s.x += v[u].x; s.y += v[u].y; s.z += v[u].z; s.w += v[u].w;
+      }
+    }
+    float4* out = (float4*)dPacc + (size_t)k * NP + q;
+    if (accumulate) {
+      const float4 o = *out;
+      s.x += o.x; s.y += o.y; s.z += o.z; s.w += o.w;
+    }
+    *out = s;
+  } else if (k == M && Dp) {
+    const float4* o = (const float4*)o_s + q;
+    float2 d = make_float2(0.f, 0.f);
+    for (int i = 0; i < nb; i += U) {
+      float4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        v[u] = (i + u < nb && valid[i + u]) ? __ldg(o + (size_t)(i + u) * NP) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        d.x += v[u].x * v[u].x + v[u].y * v[u].y;
+        d.y += v[u].z * v[u].z + v[u].w * v[u].w;
+      }
+    }
+    ((float2*)Dp)[q] = d;
+    dmax = fmaxf(d.x, d.y);
+  }
+  if (Dp) {
+    dmax = block_max(dmax, red);
+    if (threadIdx.x == 0) atomicMax(&sc->max_dp, __float_as_uint(dmax));
+  }
 }
 
 // dP_k = dPacc_k / (Dp + delta_p max(Dp)); Cp = sum_k conj(P_k) dP_k; Sdp = sum_k |dP_k|^2
 __global__ void k_norm_probe(int NN, int M, const float2* dPacc, const float* Dp, const float2* probe,
-                             float delta_p, int update_probe, float2* dP, float2* Cp, float* Sdp) {
-  __shared__ float red[32];
-  float m = 0.f;
-  if (update_probe)
-    for (int p = threadIdx.x; p < NN; p += blockDim.x) m = fmaxf(m, Dp[p]);
-  m = block_max(m, red);
-  const float damp = delta_p * m;
+                             float delta_p, int update_probe, const BatchScalars* sc, float2* dP, float2* Cp,
+                             float* Sdp) {
+  const float damp = delta_p * __uint_as_float(sc->max_dp);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += gridDim.x * blockDim.x) {
     float2 c = make_float2(0.f, 0.f);
     float sd = 0.f;
@@ -107,27 +121,11 @@ __global__ void k_norm_probe(int NN, int M, const float2* dPacc, const float* Dp
   }
 }
 
-// O += U / (illum + delta_O); P_k += mean(alpha_P) dP_k; clear accumulators and
-// the next batch's scalar set; refresh Sp = sum_k |P_k|^2.
-__global__ void k_update(int HW, float2* obj, float4* acc, float2* U, float delta_o, int update_object,
-                         int NN, int M, float2* probe, const float2* dP, float2* dPacc, float* Dp, float* Sp,
-                         int update_probe, const BatchScalars* sc, BatchScalars* sc_next) {
-  const int stride = gridDim.x * blockDim.x;
-  const float damp = delta_o * __uint_as_float(sc->max_illum);
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += stride) {
-    if (update_object) {
-      const float2 u = U[p];
-      const float inv = 1.f / (acc[p].z + damp);
-      float2 o = obj[p];
-      o.x = fmaf(u.x, inv, o.x);
-      o.y = fmaf(u.y, inv, o.y);
-      obj[p] = o;
-    }
-    acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-    U[p] = make_float2(0.f, 0.f);
-  }
+// P_k += mean_j(alpha_P) dP_k; refresh Sp = sum_k |P_k|^2; clear the next batch's scalars.
+__global__ void k_probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
+                               const BatchScalars* sc, BatchScalars* sc_next) {
   const float mean_ap = sc->count > 0 ? (float)(sc->sum_alpha_p / (double)sc->count) : 0.f;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += stride) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += gridDim.x * blockDim.x) {
     float s = 0.f;
     for (int k = 0; k < M; ++k) {
       const size_t q = (size_t)k * NN + p;
@@ -139,10 +137,8 @@ __global__ void k_update(int HW, float2* obj, float4* acc, float2* U, float delt
         probe[q] = v;
       }
       s += cabs2(v);
-      dPacc[q] = make_float2(0.f, 0.f);
     }
     Sp[p] = s;
-    Dp[p] = 0.f;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) memset(sc_next, 0, sizeof(BatchScalars));
 }
@@ -151,7 +147,7 @@ __global__ void k_update(int HW, float2* obj, float4* acc, float2* U, float delt
 // Workspace layout.
 // ---------------------------------------------------------------------------
 struct Layout {
-  size_t hdr, acc, U, psi, o, g, h, dPacc, Dp, dP, Sp, Cp, Sdp, valid, total;
+  size_t hdr, acc, psi, o, g, h, dPacc, Dp, dP, Sp, Cp, Sdp, valid, total;
 };
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -167,7 +163,6 @@ static Layout make_layout(const ptycho_dims& d, int B) {
   const size_t HW = (size_t)d.H * d.W, NN = (size_t)d.N * d.N, M = d.M;
   L.hdr = take(sizeof(WsHeader));
   L.acc = take(HW * sizeof(float4));
-  L.U = take(HW * sizeof(float2));
   L.psi = take((size_t)B * M * NN * sizeof(float2));
   L.o = take((size_t)B * NN * sizeof(float2));
   L.g = take((size_t)B * NN * sizeof(float2));
@@ -230,16 +225,15 @@ static cudaError_t pass2(int N, const Pass2Args& a, cudaStream_t s) {
 }
 
 static cudaError_t probe_reduce(int NN, int M, int nb, const float2* h_s, const float2* o_s, const int* valid,
-                                float2* dPacc, float* Dp, cudaStream_t s) {
+                                float2* dPacc, int accumulate, float* Dp, const float4* acc, int HW,
+                                BatchScalars* sc, cudaStream_t s) {
   cudaEvent_t e0 = profile_begin(K_PROBE_REDUCE, s);
-  const int chunk = 16;
-  dim3 grid((NN + 255) / 256, (nb + chunk - 1) / chunk);
-  if (M <= 4)
-    k_probe_reduce<4><<<grid, 256, 0, s>>>(NN, M, nb, chunk, h_s, o_s, valid, dPacc, Dp);
-  else if (M <= 8)
-    k_probe_reduce<8><<<grid, 256, 0, s>>>(NN, M, nb, chunk, h_s, o_s, valid, dPacc, Dp);
-  else
-    k_probe_reduce<16><<<grid, 256, 0, s>>>(NN, M, nb, chunk, h_s, o_s, valid, dPacc, Dp);
+  const int NP = NN / 2;
+  const int threads = (dPacc ? M * NP : 0) + (Dp ? NP : 0);
+  int bx = (threads + 255) / 256;
+  if (acc && bx < 2 * 152) bx = 2 * 152;
+  dim3 grid(bx > 0 ? bx : 1, acc ? 2 : 1);
+  k_probe_reduce<8><<<grid, 256, 0, s>>>(NN, M, nb, h_s, o_s, valid, dPacc, accumulate, Dp, acc, HW, sc);
   profile_end(K_PROBE_REDUCE, e0, s);
   return cudaGetLastError();
 }
@@ -253,7 +247,7 @@ static int grid_for(size_t n, int threads, int cap) {
 struct Ptrs {
   WsHeader* hdr;
   float4* acc;
-  float2 *U, *psi, *o, *g, *h, *dPacc, *dP, *Cp;
+  float2 *psi, *o, *g, *h, *dPacc, *dP, *Cp;
   float *Dp, *Sp, *Sdp;
   int* valid;
 };
@@ -263,7 +257,6 @@ static Ptrs carve(void* ws, const Layout& L) {
   Ptrs p;
   p.hdr = (WsHeader*)(b + L.hdr);
   p.acc = (float4*)(b + L.acc);
-  p.U = (float2*)(b + L.U);
   p.psi = (float2*)(b + L.psi);
   p.o = (float2*)(b + L.o);
   p.g = (float2*)(b + L.g);
@@ -288,9 +281,9 @@ static ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe,
   Ptrs w = carve(ws, L);
   cudaError_t e = cudaSuccess;
   if (loss && (e = cudaMemsetAsync(loss, 0, sizeof(double), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  if ((e = cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
   timed(K_INIT, s, [&] {
-    k_init_epoch<<<grid_for(HW > NN ? HW : NN, 256, 4 * 152), 256, 0, s>>>(HW, w.acc, w.U, NN, M, probe,
-                                                                            w.dPacc, w.Dp, w.Sp, w.hdr);
+    k_init_epoch<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, probe, w.Sp, w.hdr);
     return cudaSuccess;
   });
   if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
@@ -310,16 +303,12 @@ static ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe,
     a.Sp = w.Sp; a.acc = w.acc;
     a.loss = loss; a.status = &w.hdr->status;
     if ((e = pass1(N, a, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    timed(K_MAX_ILLUM, s, [&] {
-      k_max_illum<<<grid_for(HW, 256, 2 * 152), 256, 0, s>>>(w.acc, HW, sc);
-      return cudaSuccess;
-    });
-    if (o.update_probe) {
-      if ((e = probe_reduce(NN, M, nb, w.h, w.o, w.valid, w.dPacc, w.Dp, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    }
+    if ((e = probe_reduce(NN, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
+                          o.update_probe ? w.Dp : nullptr, w.acc, HW, sc, s)) != cudaSuccess)
+      return PTYCHO_ERR_CUDA;
     timed(K_NORM_PROBE, s, [&] {
       k_norm_probe<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p,
-                                                          o.update_probe, w.dP, w.Cp, w.Sdp);
+                                                          o.update_probe, sc, w.dP, w.Cp, w.Sdp);
       return cudaSuccess;
     });
     Pass2Args q;
@@ -328,14 +317,14 @@ static ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe,
     q.pos = pos; q.order = order; q.b0 = b0; q.nb = nb;
     q.o_s = w.o; q.g_s = w.g; q.h_s = w.h; q.valid = w.valid;
     q.acc = w.acc; q.Sp = w.Sp; q.Cp = w.Cp; q.Sdp = w.Sdp; q.dP = w.dP;
-    q.U = w.U; q.alpha_out = alpha; q.sc = sc;
+    q.obj = obj; q.alpha_out = alpha; q.sc = sc;
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
     if ((e = pass2(N, q, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if ((e = cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     timed(K_UPDATE, s, [&] {
-      k_update<<<grid_for(HW > NN ? HW : NN, 256, 4 * 152), 256, 0, s>>>(
-          HW, obj, w.acc, w.U, (float)o.delta_o, o.update_object, NN, M, probe, w.dP, w.dPacc, w.Dp, w.Sp,
-          o.update_probe, sc, sc_next);
+      k_probe_update<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, probe, w.dP, w.Sp, o.update_probe, sc,
+                                                            sc_next);
       return cudaSuccess;
     });
     if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
@@ -431,7 +420,8 @@ ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const
     a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
     a.gobj = (float2*)g_object; a.gpos = g_pos; a.loss = loss; a.status = &w.hdr->status;
     if (pass1(dims->N, a, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    if (probe_reduce(NN, dims->M, nb, w.h, w.o, w.valid, (float2*)g_probe, nullptr, s) != cudaSuccess)
+    if (probe_reduce(NN, dims->M, nb, w.h, w.o, w.valid, (float2*)g_probe, 1, nullptr, nullptr, 0, nullptr,
+                     s) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
   }
   return PTYCHO_OK;

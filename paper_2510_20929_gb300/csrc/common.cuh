@@ -31,7 +31,9 @@ struct BatchScalars {
   unsigned int max_illum;  // float bits of max(illumination) (non-negative)
   int count;               // positions whose step sizes were solved
   double sum_alpha_p;      // sum of alpha_P over the batch
-  double pad[2];
+  unsigned int max_dp;     // float bits of max(sum_j |o_j|^2) (non-negative)
+  int pad0;
+  double pad[1];
 };
 
 struct WsHeader {
@@ -78,7 +80,7 @@ struct Pass2Args {
   const float2* Cp;
   const float* Sdp;
   const float2* dP;
-  float2* U;
+  float2* obj;         // object, updated in place by the alpha-weighted scatter
   double* alpha_out;   // [J, 2] or null
   BatchScalars* sc;
   float delta_o;       // relative preconditioner damping

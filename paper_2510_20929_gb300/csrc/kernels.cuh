@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
 }
 
 
-constexpr int PASS2_T = 256;
+constexpr int PASS2_T = 512;
 
 // Bilinear sample of dO_hat = dO_acc / (illum + damp) at the patch pixel whose
 // four corners start at q (the quotient is taken per corner, then interpolated).
@@ -360,7 +360,7 @@ __device__ __forceinline__ float2 dohat(const float4* q, int W, float w00, float
 }
 
 template <int N>
-__global__ void __launch_bounds__(PASS2_T, 3) k_pass2(Pass2Args a) {
+__global__ void __launch_bounds__(PASS2_T, 2) k_pass2(Pass2Args a) {
   constexpr int T = PASS2_T, NN = N * N;
   __shared__ double red[32 * 5];
   __shared__ double alpha_sh;
@@ -380,29 +380,18 @@ __global__ void __launch_bounds__(PASS2_T, 3) k_pass2(Pass2Args a) {
   const float2* h_s = a.h_s + slotNN * M;
 
   float A11 = 0.f, A12 = 0.f, A22 = 0.f, b1 = 0.f, b2 = 0.f;
-  // two adjacent pixels per thread and iteration: 16-byte loads of the planes
-  for (int p = 2 * tid; p < NN; p += 2 * T) {
+  for (int p = tid; p < NN; p += T) {
     const int r = p / N, c = p % N;
-    const float4 g2 = __ldcs((const float4*)(g_s + p));
-    const float4 o2 = __ldcs((const float4*)(o_s + p));
-    const float2 g[2] = {make_float2(g2.x, g2.y), make_float2(g2.z, g2.w)};
-    const float2 o[2] = {make_float2(o2.x, o2.y), make_float2(o2.z, o2.w)};
-    const float2 sp = __ldg((const float2*)(a.Sp + p));
-    const float2 sdp = __ldg((const float2*)(a.Sdp + p));
-    const float4 cp2 = __ldg((const float4*)(a.Cp + p));
-    const float2 cp[2] = {make_float2(cp2.x, cp2.y), make_float2(cp2.z, cp2.w)};
-    const float spv[2] = {sp.x, sp.y}, sdpv[2] = {sdp.x, sdp.y};
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      float2 d = make_float2(0.f, 0.f);
-      if (a.update_object)
-        d = dohat(a.acc + (size_t)(ty + r) * a.W + (tx + c + u), a.W, w00, w01, w10, w11, damp);
-      A11 += cabs2(d) * spv[u];
-      const float2 od = cmulc(d, o[u]);       // conj(d) o
-      A12 += od.x * cp[u].x - od.y * cp[u].y;  // Re(conj(d) o Cp)
-      A22 += cabs2(o[u]) * sdpv[u];
-      b1 += d.x * g[u].x + d.y * g[u].y;       // Re(conj(d) g)
-    }
+    const float2 g = __ldcs(g_s + p);
+    const float2 o = __ldcs(o_s + p);
+    float2 d = make_float2(0.f, 0.f);
+    if (a.update_object) d = dohat(a.acc + (size_t)(ty + r) * a.W + (tx + c), a.W, w00, w01, w10, w11, damp);
+    A11 += cabs2(d) * __ldg(a.Sp + p);
+    const float2 od = cmulc(d, o);           // conj(d) o
+    const float2 cp = __ldg(a.Cp + p);
+    A12 += od.x * cp.x - od.y * cp.y;        // Re(conj(d) o Cp)
+    A22 += cabs2(o) * __ldg(a.Sdp + p);
+    b1 += d.x * g.x + d.y * g.y;             // Re(conj(d) g)
   }
   if (a.update_probe) {
     // b2 = Re sum_k <dP_k, h_k>: the M planes are contiguous, two pixels per 16-byte load
@@ -439,10 +428,11 @@ __global__ void __launch_bounds__(PASS2_T, 3) k_pass2(Pass2Args a) {
   }
   __syncthreads();
   if (!a.update_object) return;
+  // O += alpha_O S_j^T g / (illum + delta_O): each object pixel of the (N+1)^2 tile
+  // gathers its four patch neighbours and is divided by its own preconditioner
   const float aO = (float)alpha_sh;
   const float c00 = aO * w00, c01 = aO * w01, c10 = aO * w10, c11 = aO * w11;
   constexpr int N1 = N + 1;
-  // alpha_O S_j^T g: each object pixel of the (N+1)^2 tile gathers its four patch neighbours
   for (int q = tid; q < N1 * N1; q += T) {
     const int y = q / N1, x = q % N1;
     float2 sacc = make_float2(0.f, 0.f);
@@ -450,7 +440,9 @@ __global__ void __launch_bounds__(PASS2_T, 3) k_pass2(Pass2Args a) {
     if (y < N && x > 0) { const float2 g = g_s[y * N + x - 1]; sacc.x += c01 * g.x; sacc.y += c01 * g.y; }
     if (y > 0 && x < N) { const float2 g = g_s[(y - 1) * N + x]; sacc.x += c10 * g.x; sacc.y += c10 * g.y; }
     if (y > 0 && x > 0) { const float2 g = g_s[(y - 1) * N + x - 1]; sacc.x += c11 * g.x; sacc.y += c11 * g.y; }
-    atomicAdd(a.U + (size_t)(ty + y) * a.W + (tx + x), sacc);
+    const size_t oi = (size_t)(ty + y) * a.W + (tx + x);
+    const float inv = 1.f / (__ldg(&a.acc[oi].z) + damp);
+    atomicAdd(a.obj + oi, make_float2(sacc.x * inv, sacc.y * inv));
   }
 }
 
