@@ -59,7 +59,8 @@ typedef enum {
   PTYCHO_ERR_CUDA = 4,        /* a CUDA runtime call failed */
   PTYCHO_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
   PTYCHO_ERR_UNSUPPORTED = 6, /* window size or mode count not built */
-  PTYCHO_ERR_WORKSPACE = 7    /* workspace missing, misaligned or too small */
+  PTYCHO_ERR_WORKSPACE = 7,   /* workspace missing, misaligned or too small */
+  PTYCHO_ERR_TOO_LARGE = 8    /* problem needs more scratch than ptycho_lsqml_epoch_static holds */
 } ptycho_status;
 
 typedef enum {
@@ -134,6 +135,30 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
                                       const float* pos, const float* meas, const int32_t* order,
                                       const ptycho_lsqml_opts* opts, double* loss, void* ws,
                                       size_t ws_bytes, void* stream);
+
+/* Allocation-free epoch, for callers that cannot allocate device memory:
+ * applications that reserve the whole device memory budget up front through
+ * their own allocator, or real-time pipelines that must not call cudaMalloc
+ * because it can synchronise the device. It computes exactly what
+ * ptycho_lsqml_epoch computes (same arguments, minus the workspace), with its
+ * scratch taken from a fixed device array of PTYCHO_STATIC_WS_BYTES bytes that
+ * every GPU loading the library keeps until the process exits. The paper has
+ * no counterpart: this is an interface for embedding the library.
+ * - Returns PTYCHO_ERR_TOO_LARGE, before touching the device, when
+ *   ptycho_workspace_bytes(dims, opts->batch) exceeds PTYCHO_STATIC_WS_BYTES.
+ * - The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make it before any stream
+ *   capture.
+ * - All calls share the one array per device: calls whose work overlaps on the
+ *   GPU (other streams, other host threads) race and must be serialised by
+ *   the caller.
+ * - Synchronises `stream` at the end and returns the device-side status as
+ *   ptycho_status_read() would. No device memory is allocated. */
+#define PTYCHO_STATIC_WS_BYTES (64u * 1024u * 1024u)
+ptycho_status ptycho_lsqml_epoch_static(const ptycho_dims* dims, float* object, float* probe,
+                                        const float* pos, const float* meas, const int32_t* order,
+                                        const ptycho_lsqml_opts* opts, double* loss, double* alpha,
+                                        void* stream);
 
 /* Synchronises `stream`, returns (and clears) the device-side status recorded
  * in `ws` since the last read: PTYCHO_OK, PTYCHO_ERR_BOUNDS or

@@ -25,7 +25,7 @@ _NOISE = {"gaussian": GAUSSIAN, "poisson": POISSON, "vjp": VJP}
 
 STATUS = {0: "PTYCHO_OK", 1: "PTYCHO_ERR_ARG", 2: "PTYCHO_ERR_BOUNDS", 3: "PTYCHO_ERR_NONFINITE",
           4: "PTYCHO_ERR_CUDA", 5: "PTYCHO_ERR_TIMEOUT", 6: "PTYCHO_ERR_UNSUPPORTED",
-          7: "PTYCHO_ERR_WORKSPACE"}
+          7: "PTYCHO_ERR_WORKSPACE", 8: "PTYCHO_ERR_TOO_LARGE"}
 
 
 class PtychoError(RuntimeError):
@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
                                                   ctypes.c_size_t, _P]),
             "ptycho_lsqml_epoch_host": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, opts_p, _P, _P,
                                                        ctypes.c_size_t, _P]),
+            "ptycho_lsqml_epoch_static": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, opts_p, _P, _P, _P]),
             "ptycho_status_read": (ctypes.c_int, [_P, _P]),
             "ptycho_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "ptycho_version": (ctypes.c_char_p, []),

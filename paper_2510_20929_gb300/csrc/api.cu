@@ -360,6 +360,7 @@ const char* ptycho_status_string(ptycho_status s) {
     case PTYCHO_ERR_TIMEOUT: return "device wait timed out";
     case PTYCHO_ERR_UNSUPPORTED: return "unsupported window size or mode count";
     case PTYCHO_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case PTYCHO_ERR_TOO_LARGE: return "problem needs more scratch than the static array holds";
   }
   return "unknown status";
 }
