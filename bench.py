@@ -60,6 +60,33 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_pass1_traffic.txt")
+KERNEL_SOURCES = ["common.cuh", "fft.cuh", "kernels.cuh", "pass_n128.cu"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(KERNEL_SOURCES):
+        with open(os.path.join(ROOT, "paper_2510_20929_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """ncu DRAM bytes per launch recorded for `kernel`, or None if the kernel
+    sources changed since the capture (or no capture is recorded)."""
+    try:
+        cur = kernel_source_hash()
+        for line in open(TRAFFIC_FILE):
+            f = line.split()
+            if len(f) >= 6 and f[0] == "kernel" and f[1] == kernel and f[3] == cur:
+                return float(f[5])
+    except OSError:
+        pass
+    return None
+
+
 def make_workload(name, positions=0):
     from paper_2510_20929_gb300 import synth
     w = synth.workload_spiral128() if name == "spiral128" else synth.workload_raster64()
@@ -268,7 +295,10 @@ def run_ours(args, rank, world, local_rank):
             roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm, "unit": "GB/s",
                     "frac": hbm_ach / hbm, "traffic": None, "peak_source": hbm_src}
         roof.update({"kernel": dom_name, "launch_ms": avg_s * 1e3,
-                     "alu_frac": alu_ach / alu_tflops, "hbm_frac": hbm_ach / hbm})
+                     "alu_frac": alu_ach / alu_tflops, "hbm_frac": hbm_ach / hbm,
+                     "algorithmic_bytes_per_launch": nbytes, "algorithmic_flops_per_launch": flops})
+        if N == 128 and M == 5 and B == 256:
+            roof["traffic"] = recorded_traffic("k_pass1")
     else:
         roof = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                 "traffic": None, "kernel": dom_name}
