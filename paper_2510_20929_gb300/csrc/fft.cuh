@@ -251,14 +251,34 @@ struct Fft2 {
     }
   }
 
+  // Twiddles W_N^(n k2), k2 = 1..R2-1, for lane n: W^1..W^4 from the table,
+  // the rest as W^(4a) W^b (W^8 = W^4 W^4, W^12 = W^8 W^4): at most three
+  // roundings per twiddle and four shared loads instead of R2-1.
+  __device__ __forceinline__ static void twiddles(float2 (&t)[R2], const float2* tw, int n) {
+    t[0] = make_float2(1.f, 0.f);
+    constexpr int L4 = R2 - 1 < 4 ? R2 - 1 : 4;
+#pragma unroll
+    for (int k = 1; k <= L4; ++k) t[k] = tw[n * (R2 + 1) + k];
+#pragma unroll
+    for (int k = 5; k < R2; ++k) {
+      const int a = k & ~3, b = k & 3;
+      if (b == 0) t[k] = cmul(t[a - 4], t[4]);
+      else t[k] = cmul(t[a], t[b]);
+    }
+  }
+
   // Forward line transform (sign -1). In: v[n2] = x[n + R1*n2].
   // Out: v[k1*S + s] = X[S*(n + R1*k1) + s]. The line's storage is used for the exchange.
   template <bool ROW>
   __device__ __forceinline__ static void line_fwd(float2 (&v)[R2], float2* tile, int line, int n,
                                                   const float2* tw) {
     Dft<R2, -1>::run(v);
+    {
+      float2 t[R2];
+      twiddles(t, tw, n);
 #pragma unroll
-    for (int k2 = 1; k2 < R2; ++k2) v[k2] = cmul(v[k2], tw[n * (R2 + 1) + k2]);
+      for (int k2 = 1; k2 < R2; ++k2) v[k2] = cmul(v[k2], t[k2]);
+    }
     // exchange: lane n writes Y[n][k2]; lane t reads Y[n1][S*t + s]
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) tile[addr<ROW>(line, n, R1 * k2)] = v[k2];
@@ -297,8 +317,12 @@ struct Fft2 {
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) v[k2] = tile[addr<ROW>(line, n, R1 * k2)];
     __syncwarp();
+    {
+      float2 t[R2];
+      twiddles(t, tw, n);
 #pragma unroll
-    for (int k2 = 1; k2 < R2; ++k2) v[k2] = cmulc(tw[n * (R2 + 1) + k2], v[k2]);
+      for (int k2 = 1; k2 < R2; ++k2) v[k2] = cmulc(t[k2], v[k2]);
+    }
     Dft<R2, 1>::run(v);
   }
 

@@ -91,6 +91,46 @@ __device__ __forceinline__ void fft2_inverse(float2* tile, const float2* tw, In&
   }
 }
 
+// S_j^T of an N x N patch onto its (N+1)^2 object tile, evaluated separably:
+// h_y(x) = (1-fx) p(y, x) + fx p(y, x-1) and out(y, x) = (1-fy) h_y(x) + fy h_{y-1}(x),
+// with p = 0 outside the patch. A thread owns one tile column x and a run of
+// rows (lanes of a warp emit consecutive x, so the atomics coalesce); each
+// output costs two patch reads. `load(y, x)` returns the patch value as a
+// float4 (unused components zero), `emit(y, x, v)` consumes the tile value.
+template <int N, int T, class Load, class Emit>
+__device__ __forceinline__ void bilinear_scatter(float fy, float fx, Load&& load, Emit&& emit) {
+  constexpr int N1 = N + 1;
+  constexpr int SEG = (T / N1) > 0 ? T / N1 : 1;
+  constexpr int RS = (N1 + SEG - 1) / SEG;
+  const float gx = 1.f - fx, gy = 1.f - fy;
+  for (int item = threadIdx.x; item < N1 * SEG; item += T) {
+    const int seg = item / N1, x = item % N1;
+    const int y0 = seg * RS, y1 = min(N1, y0 + RS);
+    auto hrow = [&](int y) {
+      float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (y < N) {
+        if (x < N) {
+          const float4 a = load(y, x);
+          h = make_float4(gx * a.x, gx * a.y, gx * a.z, gx * a.w);
+        }
+        if (x > 0) {
+          const float4 b = load(y, x - 1);
+          h.x = fmaf(fx, b.x, h.x); h.y = fmaf(fx, b.y, h.y);
+          h.z = fmaf(fx, b.z, h.z); h.w = fmaf(fx, b.w, h.w);
+        }
+      }
+      return h;
+    };
+    float4 hp = (y0 > 0) ? hrow(y0 - 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int y = y0; y < y1; ++y) {
+      const float4 h = hrow(y);
+      emit(y, x, make_float4(fmaf(gy, h.x, fy * hp.x), fmaf(gy, h.y, fy * hp.y), fmaf(gy, h.z, fy * hp.z),
+                             fmaf(gy, h.w, fy * hp.w)));
+      hp = h;
+    }
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
   constexpr int T = Threads<N>::T;
@@ -289,36 +329,25 @@ __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
     }
   }
   __syncthreads();
-  const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
   const bool lsqml = (mode == MODE_LSQML_GAUSS || mode == MODE_LSQML_POISSON);
-  constexpr int N1 = N + 1;
-  for (int q = tid; q < N1 * N1; q += T) {
-    const int y = q / N1, x = q % N1;
-    float2 s = make_float2(0.f, 0.f);
-    float il = 0.f;
-    if (y < N && x < N) {
-      const float2 g = tile[tix<N>(y, x)];
-      s.x += w00 * g.x; s.y += w00 * g.y;
-      if (lsqml) il += w00 * __ldg(a.Sp + y * N + x);
-    }
-    if (y < N && x > 0) {
-      const float2 g = tile[tix<N>(y, x - 1)];
-      s.x += w01 * g.x; s.y += w01 * g.y;
-      if (lsqml) il += w01 * __ldg(a.Sp + y * N + x - 1);
-    }
-    if (y > 0 && x < N) {
-      const float2 g = tile[tix<N>(y - 1, x)];
-      s.x += w10 * g.x; s.y += w10 * g.y;
-      if (lsqml) il += w10 * __ldg(a.Sp + (y - 1) * N + x);
-    }
-    if (y > 0 && x > 0) {
-      const float2 g = tile[tix<N>(y - 1, x - 1)];
-      s.x += w11 * g.x; s.y += w11 * g.y;
-      if (lsqml) il += w11 * __ldg(a.Sp + (y - 1) * N + x - 1);
-    }
-    const size_t oi = (size_t)(ty + y) * a.W + (tx + x);
-    if (lsqml) atomicAdd(a.acc + oi, make_float4(s.x, s.y, il, 0.f));
-    else atomicAdd(a.gobj + oi, s);
+  if (lsqml) {
+    bilinear_scatter<N, T>(
+        fy, fx,
+        [&](int y, int x) {
+          const float2 g = tile[tix<N>(y, x)];
+          return make_float4(g.x, g.y, __ldg(a.Sp + y * N + x), 0.f);
+        },
+        [&](int y, int x, float4 v) {
+          atomicAdd(a.acc + (size_t)(ty + y) * a.W + (tx + x), make_float4(v.x, v.y, v.z, 0.f));
+        });
+  } else {
+    bilinear_scatter<N, T>(
+        fy, fx,
+        [&](int y, int x) {
+          const float2 g = tile[tix<N>(y, x)];
+          return make_float4(g.x, g.y, 0.f, 0.f);
+        },
+        [&](int y, int x, float4 v) { atomicAdd(a.gobj + (size_t)(ty + y) * a.W + (tx + x), make_float2(v.x, v.y)); });
   }
 
   // ---- position gradient through the bilinear weights (gradient modes) -------------
@@ -433,6 +462,8 @@ __global__ void __launch_bounds__(PASS2_T, 2) k_pass2(Pass2Args a) {
   const float aO = (float)alpha_sh;
   const float c00 = aO * w00, c01 = aO * w01, c10 = aO * w10, c11 = aO * w11;
   constexpr int N1 = N + 1;
+  // each object pixel of the (N+1)^2 tile gathers its four patch neighbours
+  // (independent outputs keep many global loads in flight)
   for (int q = tid; q < N1 * N1; q += T) {
     const int y = q / N1, x = q % N1;
     float2 sacc = make_float2(0.f, 0.f);
