@@ -14,7 +14,7 @@
 
 #include <type_traits>
 
-#include "../../include/ptycho.h"
+#include "ptycho.h"
 #include "common.cuh"
 #include "launch.h"
 #include "profile.h"
@@ -233,7 +233,7 @@ static cudaError_t probe_reduce(int NN, int M, int nb, const float2* h_s, const 
   int bx = (threads + 255) / 256;
   if (acc && bx < 2 * 152) bx = 2 * 152;
   dim3 grid(bx > 0 ? bx : 1, acc ? 2 : 1);
-  k_probe_reduce<8><<<grid, 256, 0, s>>>(NN, M, nb, h_s, o_s, valid, dPacc, accumulate, Dp, acc, HW, sc);
+  k_probe_reduce<16><<<grid, 256, 0, s>>>(NN, M, nb, h_s, o_s, valid, dPacc, accumulate, Dp, acc, HW, sc);
   profile_end(K_PROBE_REDUCE, e0, s);
   return cudaGetLastError();
 }

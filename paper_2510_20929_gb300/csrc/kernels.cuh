@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
     const float2* Pk = a.probe + (size_t)k * NN;
     // psi_k = P_k o_j into the tile, two adjacent pixels per thread and iteration
     const NatPairs<N, T> np;
-#pragma unroll 1
+#pragma unroll 4
     for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
       const int r = np.row(q), c = np.c, p = np.pix(q);
       float2 o0, o1;
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
     __syncthreads();
     // chi_k is in the tile (natural layout): g += conj(P_k) chi_k, h_k = conj(o) chi_k
     const NatPairs<N, T> np;
-#pragma unroll 1
+#pragma unroll 2
     for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
       const int p = np.pix(q);
       float2 x0, x1;
@@ -409,6 +409,7 @@ __global__ void __launch_bounds__(PASS2_T, 2) k_pass2(Pass2Args a) {
   const float2* h_s = a.h_s + slotNN * M;
 
   float A11 = 0.f, A12 = 0.f, A22 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll 1
   for (int p = tid; p < NN; p += T) {
     const int r = p / N, c = p % N;
     const float2 g = __ldcs(g_s + p);
@@ -426,7 +427,19 @@ __global__ void __launch_bounds__(PASS2_T, 2) k_pass2(Pass2Args a) {
     // b2 = Re sum_k <dP_k, h_k>: the M planes are contiguous, two pixels per 16-byte load
     const float4* h4 = (const float4*)h_s;
     const float4* d4 = (const float4*)a.dP;
-    for (int q = tid; q < M * NN / 2; q += T) {
+    const int Q = M * NN / 2;
+    int q = tid;
+    for (; q + 3 * T < Q; q += 4 * T) {      // four independent 16-byte streams per thread
+      float4 dp[4], h[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        dp[u] = __ldg(d4 + q + u * T);
+        h[u] = __ldcs(h4 + q + u * T);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) b2 += dp[u].x * h[u].x + dp[u].y * h[u].y + dp[u].z * h[u].z + dp[u].w * h[u].w;
+    }
+    for (; q < Q; q += T) {
       const float4 dp = __ldg(d4 + q);
       const float4 h = __ldcs(h4 + q);
       b2 += dp.x * h.x + dp.y * h.y + dp.z * h.z + dp.w * h.w;   // Re(conj(dP_k) h_k)

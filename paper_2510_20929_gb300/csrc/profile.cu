@@ -3,7 +3,7 @@
 #include <string.h>
 #include <vector>
 
-#include "../../include/ptycho.h"
+#include "ptycho.h"
 #include "profile.h"
 
 namespace ptycho {

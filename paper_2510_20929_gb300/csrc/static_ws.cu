@@ -19,7 +19,7 @@
 
 #include <mutex>
 
-#include "../../include/ptycho.h"
+#include "ptycho.h"
 
 namespace ptycho {
 namespace {
