@@ -215,6 +215,21 @@ def run_reference(args, rank):
     }), flush=True)
 
 
+# ----------------------------------------------------------------------------- multi-rank
+def max_over_ranks(x, world, device="cpu"):
+    """Max of a per-rank float over all ranks (the slowest replica sets the time)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.item()
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # ----------------------------------------------------------------------------- GPU
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -265,11 +280,8 @@ def run_ours(args, rank, world, local_rank):
     api.profile_enable(False)
     prof = api.profile_read()
     ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = t.item()
-    value = world * J / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, world, dev)
+    value = job_throughput(J, world, ms_max * 1e-3)
     launches = sum(n for n, _ in prof.values())
 
     # roofline of the dominant kernel (per-launch averages from the events above)
@@ -336,14 +348,11 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(args.steps):
             api.lsqml_epoch_host(hO, hP, hpos, hmeas, horder, opts, device=dev)
         barrier()
-        dt = (time.perf_counter() - t0) / args.steps
-        t = torch.tensor([dt], device=dev, dtype=torch.float64)
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dt = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
         h2d = hO.numel() * 8 + hP.numel() * 8 + hpos.numel() * 4 + hmeas.numel() * 4 + horder.numel() * 4
         d2h = hO.numel() * 8 + hP.numel() * 8 + 8
-        out["e2e"] = {"value": world * J / t.item(), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                      "d2h_bytes_per_step": d2h, "ms_per_step": t.item() * 1e3,
+        out["e2e"] = {"value": job_throughput(J, world, dt), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3,
                       "entry": "ptycho_lsqml_epoch_host (pinned host buffers)"}
 
     if rank == 0 and not args.no_cpu:

@@ -1,0 +1,133 @@
+"""Parity at the paper-shaped workloads' full sizes, in the launch configuration
+bench.py times (minibatch, window, modes and object size), against the FP64
+oracle: the raster64 workload in full, and the spiral128 workload on one full
+minibatch of 256 positions plus sampled forward outputs and epoch-level
+properties over all 4096 positions."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ptycho_oracle as orc
+from paper_2510_20929_gb300 import synth
+from tests.parity_util import rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL_FWD, TOL_EPOCH = 1e-5, 1e-4
+
+
+def _measured(w, O_true, P, pos, seed):
+    """Oracle intensities of the true object, scaled to the workload's counts, Poisson-sampled."""
+    I = orc.forward(O_true, P, pos)
+    per = w["total_counts"] / (I.sum() if w["counts_per"] == "all" else I.sum(axis=(1, 2)).mean())
+    return P * math.sqrt(per), synth.poisson_counts(I * per, seed)
+
+
+def _f32(x, complex_=False):
+    return np.asarray(x, np.complex64 if complex_ else np.float32).astype(np.complex128 if complex_ else np.float64)
+
+
+@pytest.mark.parametrize("noise", ["gaussian", "poisson"])
+def test_raster64_full_workload(noise):
+    import torch
+    from paper_2510_20929_gb300 import api
+    w = synth.workload_raster64()
+    O_true = _f32(w["object"], True)
+    pos = _f32(w["pos"])
+    P, I_m = _measured(w, O_true, _f32(w["probe"], True), pos, 11)
+    P, I_m = _f32(P, True), _f32(I_m)
+    O0 = np.ones_like(O_true)
+    dO, dP = to_dev(O0, torch.complex64), to_dev(P, torch.complex64)
+    dpos, dI = to_dev(pos, torch.float32), to_dev(I_m, torch.float32)
+    # forward
+    e = rel(api.forward(dO, dP, dpos).cpu().numpy(), orc.forward(O0, P, pos))
+    assert e < TOL_FWD, e
+    # one epoch, one minibatch of all 100 positions (the workload's batch). From the flat
+    # start many pixels are predicted near zero yet hold counts; the Poisson factor
+    # I_m / (I + eps) then amplifies the FP32 rounding of I (about 1e-7 of the peak) by
+    # I_m / eps^2, so the Poisson case takes eps = 1 count (the Gaussian factor is bounded).
+    nz = orc.GAUSSIAN if noise == "gaussian" else orc.POISSON
+    eps = 1e-9 if noise == "gaussian" else 1.0
+    order = synth.random_order(w["J"], 3)
+    opts = orc.LsqmlOptions(noise=nz, batch=w["batch"], delta_o=0.1, delta_p=0.1, lam=1e-6, eps=eps)
+    O_ref, P_ref, L_ref, a_ref = orc.lsqml_epoch(O0, P, pos, I_m, order, opts)
+    loss, alpha = api.lsqml_epoch(dO, dP, dpos, dI, to_dev(order, torch.int32), noise=noise, batch=w["batch"],
+                                  delta_o=0.1, delta_p=0.1, lam=1e-6, eps=eps, want_alpha=True)
+    e = (rel(dO.cpu().numpy(), O_ref), rel(dP.cpu().numpy(), P_ref), rel(alpha.cpu().numpy(), a_ref),
+         abs(loss.item() - L_ref) / abs(L_ref))
+    print(f"raster64 {noise}: O {e[0]:.2e} P {e[1]:.2e} alpha {e[2]:.2e} loss {e[3]:.2e}")
+    assert max(e) < TOL_EPOCH
+
+
+def test_raster64_full_workload_gradients():
+    import torch
+    from paper_2510_20929_gb300 import api
+    w = synth.workload_raster64()
+    O_true = _f32(w["object"], True)
+    pos = _f32(w["pos"])
+    P, I_m = _measured(w, O_true, _f32(w["probe"], True), pos, 12)
+    P, I_m = _f32(P, True), _f32(I_m)
+    g = np.random.default_rng(5)
+    O = _f32(O_true * np.exp(0.3j * g.standard_normal(O_true.shape)), True)
+    L_ref, gO_ref, gP_ref, gr_ref = orc.loss_and_gradients(O, P, pos, I_m, orc.GAUSSIAN, 1e-9)
+    loss, gO, gP, gr = api.adjoint(to_dev(O, torch.complex64), to_dev(P, torch.complex64),
+                                   to_dev(pos, torch.float32), to_dev(I_m, torch.float32), "gaussian", eps=1e-9,
+                                   batch=100)
+    e = (abs(loss.item() - L_ref) / L_ref, rel(gO.cpu().numpy(), gO_ref), rel(gP.cpu().numpy(), gP_ref),
+         rel(gr.cpu().numpy(), gr_ref))
+    print("raster64 gradients:", e)
+    assert e[0] < TOL_FWD and max(e[1:]) < TOL_EPOCH
+
+
+@pytest.fixture(scope="module")
+def spiral():
+    w = synth.workload_spiral128()
+    O_true = _f32(w["object"], True)
+    pos = _f32(w["pos"])
+    order = synth.random_order(w["J"], 5)
+    idx = order[:256]                                   # the first minibatch of the bench's order
+    P, I_sub = _measured(w, O_true, _f32(w["probe"], True), pos[idx], 21)
+    return w, O_true, _f32(P, True), pos, order, idx, _f32(I_sub)
+
+
+def test_spiral128_first_minibatch(spiral):
+    import torch
+    from paper_2510_20929_gb300 import api
+    w, O_true, P, pos, order, idx, I_sub = spiral
+    O0 = np.ones_like(O_true)
+    sub_pos = pos[idx]
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=256, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9)
+    O_ref, P_ref, L_ref, a_ref = orc.lsqml_batch(O0, P, sub_pos, I_sub, range(256), opts)
+    dO, dP = to_dev(O0, torch.complex64), to_dev(P, torch.complex64)
+    loss, alpha = api.lsqml_epoch(dO, dP, to_dev(sub_pos, torch.float32), to_dev(I_sub, torch.float32),
+                                  None, batch=256, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9, want_alpha=True)
+    e = (rel(dO.cpu().numpy(), O_ref), rel(dP.cpu().numpy(), P_ref), rel(alpha.cpu().numpy(), a_ref),
+         abs(loss.item() - L_ref) / abs(L_ref))
+    print(f"spiral128 first minibatch: O {e[0]:.2e} P {e[1]:.2e} alpha {e[2]:.2e} loss {e[3]:.2e}")
+    assert max(e) < TOL_EPOCH
+
+
+def test_spiral128_sampled_forward_and_epoch_properties(spiral):
+    import torch
+    from paper_2510_20929_gb300 import api
+    w, O_true, P, pos, order, idx, _ = spiral
+    dO_true, dP = to_dev(O_true, torch.complex64), to_dev(P, torch.complex64)
+    dpos = to_dev(pos, torch.float32)
+    I = api.forward(dO_true, dP, dpos)
+    sample = np.random.default_rng(9).choice(w["J"], 12, replace=False)
+    ref = orc.forward(O_true, P, pos[sample])
+    e = rel(I[torch.as_tensor(sample, device=I.device)].cpu().numpy(), ref)
+    assert e < TOL_FWD, e
+    # epochs over all 4096 positions: finite, decreasing loss from a flat start (noiseless data)
+    O = torch.ones_like(dO_true)
+    P_est = dP.clone()
+    dorder = to_dev(order, torch.int32)
+    losses = []
+    for _ in range(3):
+        loss, alpha = api.lsqml_epoch(O, P_est, dpos, I, dorder, batch=256, delta_o=0.1, delta_p=0.1,
+                                      eps=1e-9, want_alpha=True)
+        losses.append(loss.item())
+        assert torch.isfinite(alpha).all()
+    print("spiral128 losses:", losses)
+    assert losses[2] < losses[1] < losses[0]
