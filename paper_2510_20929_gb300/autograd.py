@@ -1,0 +1,95 @@
+"""Differentiable forms of the ptychographic forward model (autograd front end).
+
+* :class:`FarField` maps (object, probe modes, positions) to the predicted
+  intensities I_j = sum_k |F(P_k S_j(O))|^2 (Pty-Chi Sec. 2.1, Eq. 4); its
+  backward calls the library's adjoint in vector-Jacobian mode, which
+  recomputes the exit waves instead of storing them, and returns gradients for
+  all three inputs in PyTorch's complex convention (2 dL/dz*).
+* :class:`DataTerm` fuses the forward model with the amplitude (Eq. 1,
+  unnormalised) or Poisson data term and returns the scalar loss; its backward
+  is the fused adjoint (Eq. 2 extended to probe and positions) and never
+  materialises I.
+* :func:`reconstruct_adam` is the automatic-differentiation reconstructor of
+  Sec. 2.2 with torch.optim.Adam on object, probe and positions.
+
+Both Functions only marshal tensors to the C ABI; every arithmetic step runs
+in the CUDA library.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import api
+
+
+class FarField(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, obj, probe, pos):
+        obj, probe, pos = obj.contiguous(), probe.contiguous(), pos.contiguous()
+        ctx.save_for_backward(obj, probe, pos)
+        return api.forward(obj, probe, pos)
+
+    @staticmethod
+    def backward(ctx, gI):
+        obj, probe, pos = ctx.saved_tensors
+        _, gO, gP, gr = api.adjoint(obj, probe, pos, gI.contiguous().to(torch.float32), "vjp",
+                                    batch=256, positions_grad=ctx.needs_input_grad[2])
+        return (gO if ctx.needs_input_grad[0] else None, gP if ctx.needs_input_grad[1] else None,
+                gr if ctx.needs_input_grad[2] else None)
+
+
+class DataTerm(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, obj, probe, pos, meas, noise="gaussian", eps=1e-9):
+        obj, probe, pos, meas = obj.contiguous(), probe.contiguous(), pos.contiguous(), meas.contiguous()
+        loss, gO, gP, gr = api.adjoint(obj, probe, pos, meas, noise, eps=eps, batch=256, positions_grad=True)
+        ctx.save_for_backward(gO, gP, gr)
+        return loss
+
+    @staticmethod
+    def backward(ctx, gL):
+        gO, gP, gr = ctx.saved_tensors
+        s = gL.to(torch.float32)
+        return (gO * s if ctx.needs_input_grad[0] else None, gP * s if ctx.needs_input_grad[1] else None,
+                gr * s if ctx.needs_input_grad[2] else None, None, None, None)
+
+
+def far_field(obj, probe, pos):
+    """Predicted intensities, differentiable in object, probe modes and positions."""
+    return FarField.apply(obj, probe, pos)
+
+
+def data_term(obj, probe, pos, meas, noise="gaussian", eps=1e-9):
+    """Scalar data term (Gaussian amplitude or Poisson), differentiable in object, probe, positions."""
+    return DataTerm.apply(obj, probe, pos, meas, noise, eps)
+
+
+def reconstruct_adam(obj, probe, pos, meas, epochs=10, lr_object=1e-2, lr_probe=1e-2, lr_pos=1e-1,
+                     noise="gaussian", eps=1e-9, update=("object", "probe", "positions")):
+    """Adam on object, probe modes and positions (whole data set per step); returns the loss history.
+
+    Learning rates are in the units of each variable (object and probe
+    amplitudes, pixels for positions). The tensors are updated in place.
+    """
+    params = []
+    obj.requires_grad_("object" in update)
+    probe.requires_grad_("probe" in update)
+    pos.requires_grad_("positions" in update)
+    if "object" in update:
+        params.append({"params": [obj], "lr": lr_object})
+    if "probe" in update:
+        params.append({"params": [probe], "lr": lr_probe})
+    if "positions" in update:
+        params.append({"params": [pos], "lr": lr_pos})
+    opt = torch.optim.Adam(params)
+    hist = []
+    for _ in range(epochs):
+        opt.zero_grad(set_to_none=True)
+        loss = data_term(obj, probe, pos, meas, noise, eps)
+        loss.backward()
+        opt.step()
+        hist.append(loss.item())
+    obj.requires_grad_(False)
+    probe.requires_grad_(False)
+    pos.requires_grad_(False)
+    return hist
