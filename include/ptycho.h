@@ -74,12 +74,19 @@ typedef struct {
   int32_t batch;          /* minibatch size B >= 1 */
   int32_t update_object;  /* 0/1 */
   int32_t update_probe;   /* 0/1 */
-  int32_t reserved[4];    /* must be zero */
+  int32_t flags;          /* PTYCHO_FLAG_* bits */
+  int32_t reserved[3];    /* must be zero */
   double delta_o;         /* object preconditioner damping, relative to max(illumination) */
   double delta_p;         /* probe preconditioner damping, relative to max(sum_j |o_j|^2) */
   double lambda_reg;      /* 2x2 step-size Tikhonov term, relative to trace/2 */
   double eps;             /* added to the predicted intensity in the data term */
 } ptycho_lsqml_opts;
+
+/* opts->flags: capture the epoch's launch sequence into a CUDA graph on the
+ * first call with a given set of arguments (pointers, sizes, options) and
+ * replay it on later identical calls, which then cost one graph launch. The
+ * first such call must not itself be inside a stream capture. */
+#define PTYCHO_FLAG_GRAPH 1
 
 /* Bytes of workspace needed by every entry point below for these dimensions
  * and minibatch size (ptycho_adjoint processes positions in chunks of
@@ -124,6 +131,25 @@ ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* 
                                  const float* pos, const float* meas, const int32_t* order,
                                  const ptycho_lsqml_opts* opts, double* loss, double* alpha,
                                  void* ws, size_t ws_bytes, void* stream);
+
+/* Batched serving: one LSQML epoch for each of n independent reconstructions
+ * of possibly different sizes (arrays of n dimensions, options and device
+ * pointers; `orders` may be NULL, or hold NULL entries). losses: float64 [n]
+ * device array or NULL. Workspace: ptycho_workspace_bytes_batched() bytes,
+ * split into one section per reconstruction in argument order. Each
+ * reconstruction computes exactly what ptycho_lsqml_epoch computes for it;
+ * their minibatches run concurrently on internal worker streams forked from
+ * and joined back into `stream`. If every opts[i].flags has PTYCHO_FLAG_GRAPH,
+ * the launch sequence is captured once and replayed as one graph launch.
+ * Section i starts at the sum of ptycho_workspace_bytes(dims[k], opts[k].batch)
+ * over k < i; its status word is cleared at the start of the call and read
+ * with ptycho_status_read(section). */
+size_t ptycho_workspace_bytes_batched(int32_t n, const ptycho_dims* dims, const ptycho_lsqml_opts* opts);
+ptycho_status ptycho_lsqml_epoch_batched(int32_t n, const ptycho_dims* dims, float* const* objects,
+                                         float* const* probes, const float* const* pos,
+                                         const float* const* meas, const int32_t* const* orders,
+                                         const ptycho_lsqml_opts* opts, double* losses, void* ws,
+                                         size_t ws_bytes, void* stream);
 
 /* Same epoch with HOST buffers: copies pos, meas and order (and the object and
  * probe) into device staging areas carved from `ws` (ws_bytes must be at least

@@ -21,6 +21,7 @@ import torch
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libptycho.so")
 
 GAUSSIAN, POISSON, VJP = 0, 1, 2
+FLAG_GRAPH = 1
 _NOISE = {"gaussian": GAUSSIAN, "poisson": POISSON, "vjp": VJP}
 
 STATUS = {0: "PTYCHO_OK", 1: "PTYCHO_ERR_ARG", 2: "PTYCHO_ERR_BOUNDS", 3: "PTYCHO_ERR_NONFINITE",
@@ -47,7 +48,7 @@ class Dims(ctypes.Structure):
 class LsqmlOpts(ctypes.Structure):
     _fields_ = [("noise", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("update_object", ctypes.c_int32), ("update_probe", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4),
+                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
                 ("delta_o", ctypes.c_double), ("delta_p", ctypes.c_double),
                 ("lambda_reg", ctypes.c_double), ("eps", ctypes.c_double)]
 
@@ -80,6 +81,9 @@ def lib() -> ctypes.CDLL:
             "ptycho_lsqml_epoch_host": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, opts_p, _P, _P,
                                                        ctypes.c_size_t, _P]),
             "ptycho_lsqml_epoch_static": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, opts_p, _P, _P, _P]),
+            "ptycho_workspace_bytes_batched": (ctypes.c_size_t, [ctypes.c_int32, dims_p, opts_p]),
+            "ptycho_lsqml_epoch_batched": (ctypes.c_int, [ctypes.c_int32, dims_p, _P, _P, _P, _P, _P, opts_p, _P,
+                                                          _P, ctypes.c_size_t, _P]),
             "ptycho_status_read": (ctypes.c_int, [_P, _P]),
             "ptycho_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "ptycho_version": (ctypes.c_char_p, []),
@@ -227,8 +231,9 @@ def adjoint(obj, probe, pos, meas, noise="gaussian", eps: float = 0.0, batch: in
 
 def make_opts(noise="gaussian", batch: int = 256, delta_o: float = 0.1, delta_p: float = 0.1,
               lam: float = 1e-6, eps: float = 1e-9, update_object: bool = True,
-              update_probe: bool = True) -> LsqmlOpts:
+              update_probe: bool = True, graph: bool = False) -> LsqmlOpts:
     o = LsqmlOpts()
+    o.flags = FLAG_GRAPH if graph else 0
     o.noise = _NOISE[noise] if isinstance(noise, str) else int(noise)
     o.batch = int(batch)
     o.update_object = int(bool(update_object))
@@ -261,6 +266,53 @@ def lsqml_epoch(obj, probe, pos, meas, order=None, opts: LsqmlOpts | None = None
                                     _P(ws.ptr), ws.nbytes, _stream()), "ptycho_lsqml_epoch")
     _finish(ws, "ptycho_lsqml_epoch", check)
     return loss, alpha
+
+
+def lsqml_epoch_batched(recons, opts, *, check: bool = True):
+    """One epoch for each of several independent reconstructions, run concurrently.
+
+    ``recons`` is a list of (obj, probe, pos, meas, order) tuples of CUDA
+    tensors (order may be None); ``opts`` one LsqmlOpts or a list of them.
+    Objects and probes are updated in place; returns the float64 [n] losses.
+    """
+    n = len(recons)
+    if n == 0:
+        raise ValueError("no reconstructions")
+    opts_list = opts if isinstance(opts, (list, tuple)) else [opts] * n
+    dev = recons[0][0].device
+    dims = (Dims * n)()
+    OA = (LsqmlOpts * n)(*opts_list)
+    ptrs = {k: (ctypes.c_void_p * n)() for k in ("o", "p", "r", "m", "q")}
+    for i, (obj, probe, pos, meas, order) in enumerate(recons):
+        _need(obj, "object", torch.complex64, device=dev)
+        _need(probe, "probe", torch.complex64, device=dev)
+        _need(pos, "positions", torch.float32, device=dev)
+        d = dims_of(obj, probe, pos)
+        _need(meas, "meas", torch.float32, (d.J, d.N, d.N), device=dev)
+        if order is not None:
+            _need(order, "order", torch.int32, (d.J,), device=dev)
+        dims[i] = d
+        ptrs["o"][i], ptrs["p"][i], ptrs["r"][i], ptrs["m"][i] = (obj.data_ptr(), probe.data_ptr(),
+                                                                   pos.data_ptr(), meas.data_ptr())
+        ptrs["q"][i] = order.data_ptr() if order is not None else None
+    need = lib().ptycho_workspace_bytes_batched(n, dims, OA)
+    if need == 0:
+        raise PtychoError(6, "workspace_bytes_batched")
+    key = (str(dev), "batched")
+    ws = _ws_cache.get(key)
+    if ws is None or ws.nbytes < need:
+        ws = Workspace(need, dev)
+        _ws_cache[key] = ws
+    losses = torch.zeros(n, dtype=torch.float64, device=dev)
+    _check(lib().ptycho_lsqml_epoch_batched(n, dims, ptrs["o"], ptrs["p"], ptrs["r"], ptrs["m"], ptrs["q"], OA,
+                                            _ptr(losses), _P(ws.ptr), ws.nbytes, _stream()),
+           "ptycho_lsqml_epoch_batched")
+    if check:
+        off = 0
+        for i in range(n):
+            _check(lib().ptycho_status_read(_P(ws.ptr + off), _stream()), f"ptycho_lsqml_epoch_batched[{i}]")
+            off += lib().ptycho_workspace_bytes(ctypes.byref(dims[i]), OA[i].batch)
+    return losses
 
 
 def lsqml_epoch_host(obj, probe, pos, meas, order, opts: LsqmlOpts, device=None):

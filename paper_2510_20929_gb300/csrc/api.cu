@@ -18,6 +18,7 @@
 #include "common.cuh"
 #include "launch.h"
 #include "profile.h"
+#include "internal.h"
 
 namespace ptycho {
 
@@ -146,13 +147,9 @@ __global__ void k_probe_update(int NN, int M, float2* probe, const float2* dP, f
 // ---------------------------------------------------------------------------
 // Workspace layout.
 // ---------------------------------------------------------------------------
-struct Layout {
-  size_t hdr, acc, psi, o, g, h, dPacc, Dp, dP, Sp, Cp, Sdp, valid, total;
-};
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
-
-static Layout make_layout(const ptycho_dims& d, int B) {
+Layout make_layout(const ptycho_dims& d, int B) {
   Layout L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -180,7 +177,7 @@ static Layout make_layout(const ptycho_dims& d, int B) {
 
 static bool supported_N(int N) { return N == 16 || N == 32 || N == 64 || N == 128; }
 
-static ptycho_status check_dims(const ptycho_dims* d) {
+ptycho_status check_dims(const ptycho_dims* d) {
   if (!d) return PTYCHO_ERR_ARG;
   if (!supported_N(d->N) || d->M < 1 || d->M > 16) return PTYCHO_ERR_UNSUPPORTED;
   if (d->H < d->N + 1 || d->W < d->N + 1 || d->J < 0) return PTYCHO_ERR_ARG;
@@ -273,7 +270,7 @@ static Ptrs carve(void* ws, const Layout& L) {
 
 static ptycho_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PTYCHO_OK : PTYCHO_ERR_CUDA; }
 
-static ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const float* pos,
+ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const float* pos,
                                const float* meas, const int32_t* order, const ptycho_lsqml_opts& o,
                                double* loss, double* alpha, void* ws, cudaStream_t s) {
   const int B = o.batch, N = d.N, M = d.M, NN = N * N, HW = d.H * d.W;
@@ -332,11 +329,12 @@ static ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe,
   return PTYCHO_OK;
 }
 
-static ptycho_status check_opts(const ptycho_lsqml_opts* o) {
+ptycho_status check_opts(const ptycho_lsqml_opts* o) {
   if (!o || o->batch < 1 || (o->noise != PTYCHO_NOISE_GAUSSIAN && o->noise != PTYCHO_NOISE_POISSON))
     return PTYCHO_ERR_ARG;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (o->reserved[i] != 0) return PTYCHO_ERR_ARG;
+  if (o->flags & ~(int32_t)PTYCHO_FLAG_GRAPH) return PTYCHO_ERR_ARG;
   if (!(o->delta_o >= 0.0) || !(o->delta_p >= 0.0) || !(o->lambda_reg >= 0.0) || !(o->eps >= 0.0))
     return PTYCHO_ERR_ARG;
   return PTYCHO_OK;
@@ -437,8 +435,13 @@ ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* 
   if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
   const Layout L = make_layout(*dims, opts->batch);
   if ((st = check_ws(ws, ws_bytes, L.total)) != PTYCHO_OK) return st;
-  return run_epoch(*dims, (float2*)object, (float2*)probe, pos, meas, order, *opts, loss, alpha, ws,
-                   (cudaStream_t)stream);
+  auto body = [&](cudaStream_t s) {
+    return run_epoch(*dims, (float2*)object, (float2*)probe, pos, meas, order, *opts, loss, alpha, ws, s);
+  };
+  if (!(opts->flags & PTYCHO_FLAG_GRAPH)) return body((cudaStream_t)stream);
+  GraphKey key;
+  key.add(*dims).add(object).add(probe).add(pos).add(meas).add(order).add(*opts).add(loss).add(alpha).add(ws);
+  return run_graphed(key, (cudaStream_t)stream, body);
 }
 
 static size_t host_extra(const ptycho_dims& d) {

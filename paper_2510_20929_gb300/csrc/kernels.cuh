@@ -494,10 +494,25 @@ __global__ void __launch_bounds__(PASS2_T, 2) k_pass2(Pass2Args a) {
 
 namespace ptycho {
 
+// Opts a kernel into more than 48 KB of dynamic shared memory, once per device
+// (so that no attribute call happens while a stream is being captured).
+template <class K>
+cudaError_t smem_optin(K kernel, size_t bytes, unsigned long long* done_mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (__atomic_load_n(done_mask, __ATOMIC_ACQUIRE) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) __atomic_fetch_or(done_mask, bit, __ATOMIC_ACQ_REL);
+  return e;
+}
+
 template <int N>
 cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s) {
   constexpr size_t sm = Pass1Smem<N>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_pass1<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  static unsigned long long done = 0;
+  cudaError_t e = smem_optin(k_pass1<N>, sm, &done);
   if (e != cudaSuccess) return e;
   if (a.nb <= 0) return cudaSuccess;
   k_pass1<N><<<a.nb, Threads<N>::T, sm, s>>>(a);

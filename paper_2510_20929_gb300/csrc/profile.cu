@@ -55,6 +55,8 @@ bool profiling_on() { return g_on; }
 cudaEvent_t profile_begin(int id, cudaStream_t s) {
   (void)id;
   if (!g_on) return nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t a = take_event();
   if (a) cudaEventRecord(a, s);

@@ -63,7 +63,10 @@ extern "C" ptycho_status ptycho_lsqml_epoch_static(const ptycho_dims* dims, floa
   // the array keeps the previous call's contents: clear its status word first
   // (the epoch itself zeroes every accumulator it reads)
   if ((st = ptycho_workspace_init(ws, need, stream)) != PTYCHO_OK) return st;
-  if ((st = ptycho_lsqml_epoch(dims, object, probe, pos, meas, order, opts, loss, alpha, ws, need, stream)) !=
+  // graph capture would let the driver allocate for the executable graph: run eagerly
+  ptycho_lsqml_opts o = *opts;
+  o.flags &= ~(int32_t)PTYCHO_FLAG_GRAPH;
+  if ((st = ptycho_lsqml_epoch(dims, object, probe, pos, meas, order, &o, loss, alpha, ws, need, stream)) !=
       PTYCHO_OK)
     return st;
   return ptycho_status_read(ws, stream);

@@ -185,3 +185,28 @@ def workload_small(N: int = 16, M: int = 2, H: int = 40, W: int = 44, J: int = 1
     pos = raster_positions(ny, nx, step, (H / 2.0, W / 2.0), 0.45, seed + 3)[:J]
     return dict(name=f"small{N}", H=H, W=W, N=N, M=M, J=J, batch=J,
                 object=obj, probe=probe, pos=pos)
+
+
+def workload_uneven(n: int = 16, seed: int = 1005, N_choices=(64, 128), J_range=(500, 20000),
+                    counts_range=(1e5, 1e7)):
+    """Independent reconstructions of uneven size for batched serving: per
+    reconstruction a window N drawn from ``N_choices``, J ~ U[J_range], a
+    Gaussian probe (1/e^2 diameter D = 0.4 N), a Fermat spiral with spacing
+    0.6 D (about 40% overlap), an object of side 2 (c sqrt(J) + N/2 + 2)
+    rounded up to a multiple of 32, and total counts log-uniform in
+    ``counts_range`` per pattern set."""
+    g = rng(seed)
+    out = []
+    for i in range(n):
+        N = int(g.choice(N_choices))
+        J = int(g.integers(J_range[0], J_range[1] + 1))
+        D = 0.4 * N
+        c = 0.6 * D / math.sqrt(math.pi)   # mean nearest-neighbour spacing of r = c sqrt(n) is c sqrt(pi)
+        side = int(math.ceil(2 * (c * math.sqrt(J) + N / 2 + 2) / 32.0) * 32)
+        obj = make_object(side, side, seed * 100 + i)
+        probe = gaussian_probe(N, sigma=D / 4.0, quad_phase=0.2 / N)
+        pos = fermat_spiral(J, c, (side / 2.0, side / 2.0))
+        counts = float(np.exp(g.uniform(math.log(counts_range[0]), math.log(counts_range[1]))))
+        out.append(dict(name=f"uneven{i}", H=side, W=side, N=N, M=1, J=J, batch=min(256, J), object=obj,
+                        probe=probe, pos=pos, total_counts=counts, counts_per="all"))
+    return out
