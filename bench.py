@@ -252,7 +252,7 @@ def run_ours(args, rank, world, local_rank):
     order = torch.tensor(synth.random_order(J, 5 + rank), dtype=torch.int32, device=dev)
     O = torch.ones((H, W), dtype=torch.complex64, device=dev)
     P_est = P.clone()
-    opts = api.make_opts(noise="gaussian", batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9)
+    opts = api.make_opts(noise="gaussian", batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9, autotune=True)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -326,6 +326,7 @@ def run_ours(args, rank, world, local_rank):
                    "profiler": "CUDA event pair around every library launch during the timed steps"},
         "roofline": roof,
         "gpu_launches": launches,
+        "autotune": api.tuning(api.dims_of(O, P_est, pos), B),
         "kernels": {k: {"launches": n, "ms_per_launch": ms_ / max(n, 1), "share": ms_ / sum(
             v[1] for v in prof.values())} for k, (n, ms_) in prof.items()},
         "clocks": clk,

@@ -87,6 +87,17 @@ typedef struct {
  * replay it on later identical calls, which then cost one graph launch. The
  * first such call must not itself be inside a stream capture. */
 #define PTYCHO_FLAG_GRAPH 1
+/* opts->flags: on the first epoch for a given device and (N, M, H, W, batch),
+ * time the CTA-size variants of the two per-position kernels on the first
+ * minibatch (synchronising the stream; skipped while capturing) and use the
+ * fastest from then on. Without it, or before tuning, the defaults are used. */
+#define PTYCHO_FLAG_AUTOTUNE 2
+
+/* Autotuner result for these dimensions and batch on the current device:
+ * returns 1 and the chosen variants (0 = default CTA size, 1 = alternative)
+ * and the measured milliseconds of both variants, or 0 if not tuned. */
+int32_t ptycho_tuning_read(const ptycho_dims* dims, int32_t batch, int32_t* variant_pass1,
+                           int32_t* variant_pass2, float* ms_pass1, float* ms_pass2);
 
 /* Bytes of workspace needed by every entry point below for these dimensions
  * and minibatch size (ptycho_adjoint processes positions in chunks of

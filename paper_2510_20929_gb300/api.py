@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libptycho.s
 
 GAUSSIAN, POISSON, VJP = 0, 1, 2
 FLAG_GRAPH = 1
+FLAG_AUTOTUNE = 2
 _NOISE = {"gaussian": GAUSSIAN, "poisson": POISSON, "vjp": VJP}
 
 STATUS = {0: "PTYCHO_OK", 1: "PTYCHO_ERR_ARG", 2: "PTYCHO_ERR_BOUNDS", 3: "PTYCHO_ERR_NONFINITE",
@@ -82,6 +83,9 @@ def lib() -> ctypes.CDLL:
                                                        ctypes.c_size_t, _P]),
             "ptycho_lsqml_epoch_static": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, opts_p, _P, _P, _P]),
             "ptycho_workspace_bytes_batched": (ctypes.c_size_t, [ctypes.c_int32, dims_p, opts_p]),
+            "ptycho_tuning_read": (ctypes.c_int32, [dims_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
+                                                    ctypes.POINTER(ctypes.c_float)]),
             "ptycho_lsqml_epoch_batched": (ctypes.c_int, [ctypes.c_int32, dims_p, _P, _P, _P, _P, _P, opts_p, _P,
                                                           _P, ctypes.c_size_t, _P]),
             "ptycho_status_read": (ctypes.c_int, [_P, _P]),
@@ -231,9 +235,9 @@ def adjoint(obj, probe, pos, meas, noise="gaussian", eps: float = 0.0, batch: in
 
 def make_opts(noise="gaussian", batch: int = 256, delta_o: float = 0.1, delta_p: float = 0.1,
               lam: float = 1e-6, eps: float = 1e-9, update_object: bool = True,
-              update_probe: bool = True, graph: bool = False) -> LsqmlOpts:
+              update_probe: bool = True, graph: bool = False, autotune: bool = False) -> LsqmlOpts:
     o = LsqmlOpts()
-    o.flags = FLAG_GRAPH if graph else 0
+    o.flags = (FLAG_GRAPH if graph else 0) | (FLAG_AUTOTUNE if autotune else 0)
     o.noise = _NOISE[noise] if isinstance(noise, str) else int(noise)
     o.batch = int(batch)
     o.update_object = int(bool(update_object))
@@ -266,6 +270,16 @@ def lsqml_epoch(obj, probe, pos, meas, order=None, opts: LsqmlOpts | None = None
                                     _P(ws.ptr), ws.nbytes, _stream()), "ptycho_lsqml_epoch")
     _finish(ws, "ptycho_lsqml_epoch", check)
     return loss, alpha
+
+
+def tuning(dims: Dims, batch: int):
+    """Autotuner choice for these dimensions on the current device, or None:
+    {"pass1": variant, "pass2": variant, "pass1_ms": [default, alt], "pass2_ms": [...]}."""
+    v1, v2 = ctypes.c_int32(0), ctypes.c_int32(0)
+    m1, m2 = (ctypes.c_float * 2)(), (ctypes.c_float * 2)()
+    if not lib().ptycho_tuning_read(ctypes.byref(dims), int(batch), ctypes.byref(v1), ctypes.byref(v2), m1, m2):
+        return None
+    return {"pass1": v1.value, "pass2": v2.value, "pass1_ms": list(m1), "pass2_ms": list(m2)}
 
 
 def lsqml_epoch_batched(recons, opts, *, check: bool = True):

@@ -12,7 +12,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "ptycho.h"
 #include "common.cuh"
@@ -210,15 +212,73 @@ static cudaError_t timed(int id, cudaStream_t s, F&& launch) {
   return e;
 }
 
-static cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s) {
+static cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s, int variant = 0) {
   return timed(K_PASS1, s, [&] {
-    return dispatch_N(N, [&](auto c) { return launch_pass1<decltype(c)::value>(a, s); });
+    return dispatch_N(N, [&](auto c) { return launch_pass1<decltype(c)::value>(a, s, variant); });
   });
 }
-static cudaError_t pass2(int N, const Pass2Args& a, cudaStream_t s) {
+static cudaError_t pass2(int N, const Pass2Args& a, cudaStream_t s, int variant = 0) {
   return timed(K_PASS2, s, [&] {
-    return dispatch_N(N, [&](auto c) { return launch_pass2<decltype(c)::value>(a, s); });
+    return dispatch_N(N, [&](auto c) { return launch_pass2<decltype(c)::value>(a, s, variant); });
   });
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: CTA-size variants of the two per-position passes, chosen per
+// (device, N, M, H, W, B) by timing each candidate on the first minibatch.
+// ---------------------------------------------------------------------------
+struct TuneKey {
+  int dev, N, M, H, W, B;
+  bool operator==(const TuneKey& o) const {
+    return dev == o.dev && N == o.N && M == o.M && H == o.H && W == o.W && B == o.B;
+  }
+};
+struct TuneEntry {
+  TuneKey key;
+  int v1, v2;
+  float ms1[2], ms2[2];
+};
+static std::mutex g_tune_mu;
+static std::vector<TuneEntry> g_tune;
+
+static bool tune_lookup(const TuneKey& k, TuneEntry* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& e : g_tune)
+    if (e.key == k) {
+      *out = e;
+      return true;
+    }
+  return false;
+}
+
+static void tune_store(const TuneEntry& t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& e : g_tune)
+    if (e.key == t.key) {
+      e = t;
+      return;
+    }
+  g_tune.push_back(t);
+}
+
+// Mean time of `reps` runs of launch() on stream s (after one warm-up run).
+template <class F>
+static float time_launch(cudaStream_t s, int reps, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return 1e30f;
+  float ms = 1e30f;
+  if (launch() == cudaSuccess && cudaEventRecord(a, s) == cudaSuccess) {
+    bool ok = true;
+    for (int r = 0; r < reps && ok; ++r) ok = launch() == cudaSuccess;
+    if (ok && cudaEventRecord(b, s) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+      ms /= (float)reps;
+    else
+      ms = 1e30f;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
 }
 
 static cudaError_t probe_reduce(int NN, int M, int nb, const float2* h_s, const float2* o_s, const int* valid,
@@ -270,6 +330,58 @@ static Ptrs carve(void* ws, const Layout& L) {
 
 static ptycho_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PTYCHO_OK : PTYCHO_ERR_CUDA; }
 
+// Times both CTA-size variants of k_pass1 and k_pass2 on the epoch's first
+// minibatch, without side effects on the caller's data: the loss is not
+// written, k_pass2's object update goes to the far-field scratch (when it is
+// large enough to stand in for the object, else k_pass2 keeps its default),
+// and the accumulators and batch scalars are cleared again afterwards.
+static ptycho_status autotune(const ptycho_dims& d, float2* obj, float2* probe, const float* pos, const float* meas,
+                              const int32_t* order, const ptycho_lsqml_opts& o, const Ptrs& w, const Layout& L,
+                              cudaStream_t s, TuneEntry* t) {
+  const int B = o.batch, N = d.N, M = d.M, NN = N * N, HW = d.H * d.W;
+  const int nb = d.J < B ? d.J : B;
+  BatchScalars* sc = &w.hdr->sc[0];
+  BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.H = d.H; a.W = d.W; a.M = M; a.J = d.J;
+  a.obj = obj; a.probe = probe; a.pos = pos; a.meas = meas; a.order = order;
+  a.b0 = 0; a.nb = nb;
+  a.mode = (o.noise == PTYCHO_NOISE_POISSON) ? MODE_LSQML_POISSON : MODE_LSQML_GAUSS;
+  a.eps = (float)o.eps;
+  a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
+  a.Sp = w.Sp; a.acc = w.acc; a.loss = nullptr; a.status = &w.hdr->status;
+  for (int v = 0; v < 2; ++v) t->ms1[v] = time_launch(s, 3, [&] { return pass1(N, a, s, v); });
+  t->v1 = t->ms1[1] < t->ms1[0] ? 1 : 0;
+  // one clean pass 1 with the chosen variant feeds the pass-2 candidates
+  if (cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  if (pass1(N, a, s, t->v1) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  if (probe_reduce(NN, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
+                   o.update_probe ? w.Dp : nullptr, w.acc, HW, sc, s) != cudaSuccess)
+    return PTYCHO_ERR_CUDA;
+  k_norm_probe<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p,
+                                                      o.update_probe, sc, w.dP, w.Cp, w.Sdp);
+  t->v2 = 0;
+  t->ms2[0] = t->ms2[1] = 0.f;
+  if (L.o - L.psi >= (size_t)HW * sizeof(float2) && o.update_object) {
+    Pass2Args q;
+    memset(&q, 0, sizeof(q));
+    q.H = d.H; q.W = d.W; q.M = M; q.J = d.J;
+    q.pos = pos; q.order = order; q.b0 = 0; q.nb = nb;
+    q.o_s = w.o; q.g_s = w.g; q.h_s = w.h; q.valid = w.valid;
+    q.acc = w.acc; q.Sp = w.Sp; q.Cp = w.Cp; q.Sdp = w.Sdp; q.dP = w.dP;
+    q.obj = w.psi;  // stand-in object: the far-field scratch
+    q.sc = sc;
+    q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
+    q.update_object = o.update_object; q.update_probe = o.update_probe;
+    for (int v = 0; v < 2; ++v) t->ms2[v] = time_launch(s, 3, [&] { return pass2(N, q, s, v); });
+    t->v2 = t->ms2[1] < t->ms2[0] ? 1 : 0;
+  }
+  // restore the epoch's starting state of the accumulators and scalars
+  if (cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  k_init_epoch<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, probe, w.Sp, w.hdr);
+  return cudaGetLastError() == cudaSuccess ? PTYCHO_OK : PTYCHO_ERR_CUDA;
+}
+
 ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const float* pos,
                                const float* meas, const int32_t* order, const ptycho_lsqml_opts& o,
                                double* loss, double* alpha, void* ws, cudaStream_t s) {
@@ -284,6 +396,17 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const 
     return cudaSuccess;
   });
   if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  TuneEntry tune{{dev, N, M, d.H, d.W, B}, 0, 0, {0.f, 0.f}, {0.f, 0.f}};
+  if (!tune_lookup(tune.key, &tune) && (o.flags & PTYCHO_FLAG_AUTOTUNE) && d.J > 0) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      ptycho_status ts = autotune(d, obj, probe, pos, meas, order, o, w, L, s, &tune);
+      if (ts != PTYCHO_OK) return ts;
+      tune_store(tune);
+    }
+  }
   const int nbatch = (d.J + B - 1) / B;
   for (int b = 0; b < nbatch; ++b) {
     const int b0 = b * B, nb = (d.J - b0 < B) ? d.J - b0 : B;
@@ -299,7 +422,7 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const 
     a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
     a.Sp = w.Sp; a.acc = w.acc;
     a.loss = loss; a.status = &w.hdr->status;
-    if ((e = pass1(N, a, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if ((e = pass1(N, a, s, tune.v1)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if ((e = probe_reduce(NN, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
                           o.update_probe ? w.Dp : nullptr, w.acc, HW, sc, s)) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
@@ -317,7 +440,7 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const 
     q.obj = obj; q.alpha_out = alpha; q.sc = sc;
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
-    if ((e = pass2(N, q, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if ((e = pass2(N, q, s, tune.v2)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if ((e = cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     timed(K_UPDATE, s, [&] {
       k_probe_update<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, probe, w.dP, w.Sp, o.update_probe, sc,
@@ -334,7 +457,7 @@ ptycho_status check_opts(const ptycho_lsqml_opts* o) {
     return PTYCHO_ERR_ARG;
   for (int i = 0; i < 3; ++i)
     if (o->reserved[i] != 0) return PTYCHO_ERR_ARG;
-  if (o->flags & ~(int32_t)PTYCHO_FLAG_GRAPH) return PTYCHO_ERR_ARG;
+  if (o->flags & ~(int32_t)(PTYCHO_FLAG_GRAPH | PTYCHO_FLAG_AUTOTUNE)) return PTYCHO_ERR_ARG;
   if (!(o->delta_o >= 0.0) || !(o->delta_p >= 0.0) || !(o->lambda_reg >= 0.0) || !(o->eps >= 0.0))
     return PTYCHO_ERR_ARG;
   return PTYCHO_OK;
@@ -361,6 +484,20 @@ const char* ptycho_status_string(ptycho_status s) {
     case PTYCHO_ERR_TOO_LARGE: return "problem needs more scratch than the static array holds";
   }
   return "unknown status";
+}
+
+int32_t ptycho_tuning_read(const ptycho_dims* dims, int32_t batch, int32_t* variant_pass1, int32_t* variant_pass2,
+                           float* ms_pass1, float* ms_pass2) {
+  if (!dims) return 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  TuneEntry t;
+  if (!tune_lookup({dev, dims->N, dims->M, dims->H, dims->W, batch}, &t)) return 0;
+  if (variant_pass1) *variant_pass1 = t.v1;
+  if (variant_pass2) *variant_pass2 = t.v2;
+  if (ms_pass1) { ms_pass1[0] = t.ms1[0]; ms_pass1[1] = t.ms1[1]; }
+  if (ms_pass2) { ms_pass2[0] = t.ms2[0]; ms_pass2[1] = t.ms2[1]; }
+  return 1;
 }
 
 ptycho_status ptycho_workspace_init(void* ws, size_t ws_bytes, void* stream) {

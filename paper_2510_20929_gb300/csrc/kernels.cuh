@@ -21,11 +21,14 @@
 
 namespace ptycho {
 
+// CTA sizes of the per-position pass: the default and the alternative the
+// autotuner may pick (the full count of line slots N*R1, or half of it with
+// two lines per thread).
 template <int N> struct Threads;
-template <> struct Threads<16> { static constexpr int T = 64; };
-template <> struct Threads<32> { static constexpr int T = 128; };
-template <> struct Threads<64> { static constexpr int T = 256; };
-template <> struct Threads<128> { static constexpr int T = 1024; };
+template <> struct Threads<16> { static constexpr int T = 64, ALT = 32; };
+template <> struct Threads<32> { static constexpr int T = 128, ALT = 64; };
+template <> struct Threads<64> { static constexpr int T = 256, ALT = 512; };
+template <> struct Threads<128> { static constexpr int T = 1024, ALT = 512; };
 
 template <int N>
 struct Pass1Smem {
@@ -131,9 +134,8 @@ __device__ __forceinline__ void bilinear_scatter(float fy, float fx, Load&& load
   }
 }
 
-template <int N>
-__global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
-  constexpr int T = Threads<N>::T;
+template <int N, int T>
+__global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
   using F = Fft2<N>;
   using SM = Pass1Smem<N>;
   constexpr int R1 = F::R1, R2 = F::R2, NN = N * N, RP = SM::RP;
@@ -375,7 +377,8 @@ __global__ void __launch_bounds__(Threads<N>::T, 1) k_pass1(BatchArgs a) {
 }
 
 
-constexpr int PASS2_T = 512;
+// CTA sizes of the step-size pass (default, alternative).
+constexpr int PASS2_T = 512, PASS2_ALT = 256;
 
 // Bilinear sample of dO_hat = dO_acc / (illum + damp) at the patch pixel whose
 // four corners start at q (the quotient is taken per corner, then interpolated).
@@ -388,9 +391,9 @@ __device__ __forceinline__ float2 dohat(const float4* q, int W, float w00, float
                      q00.y * i00 + q01.y * i01 + q10.y * i10 + q11.y * i11);
 }
 
-template <int N>
-__global__ void __launch_bounds__(PASS2_T, 2) k_pass2(Pass2Args a) {
-  constexpr int T = PASS2_T, NN = N * N;
+template <int N, int T>
+__global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
+  constexpr int NN = N * N;
   __shared__ double red[32 * 5];
   __shared__ double alpha_sh;
   const int slot = blockIdx.x, tid = threadIdx.x;
@@ -508,21 +511,28 @@ cudaError_t smem_optin(K kernel, size_t bytes, unsigned long long* done_mask) {
   return e;
 }
 
-template <int N>
-cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s) {
+template <int N, int T>
+cudaError_t launch_pass1_t(const BatchArgs& a, cudaStream_t s) {
   constexpr size_t sm = Pass1Smem<N>::bytes;
   static unsigned long long done = 0;
-  cudaError_t e = smem_optin(k_pass1<N>, sm, &done);
+  cudaError_t e = smem_optin(k_pass1<N, T>, sm, &done);
   if (e != cudaSuccess) return e;
   if (a.nb <= 0) return cudaSuccess;
-  k_pass1<N><<<a.nb, Threads<N>::T, sm, s>>>(a);
+  k_pass1<N, T><<<a.nb, T, sm, s>>>(a);
   return cudaGetLastError();
 }
 
+// variant 0: default CTA size, 1: the alternative
 template <int N>
-cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s) {
+cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s, int variant) {
+  return variant == 1 ? launch_pass1_t<N, Threads<N>::ALT>(a, s) : launch_pass1_t<N, Threads<N>::T>(a, s);
+}
+
+template <int N>
+cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s, int variant) {
   if (a.nb <= 0) return cudaSuccess;
-  k_pass2<N><<<a.nb, PASS2_T, 0, s>>>(a);
+  if (variant == 1) k_pass2<N, PASS2_ALT><<<a.nb, PASS2_ALT, 0, s>>>(a);
+  else k_pass2<N, PASS2_T><<<a.nb, PASS2_T, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 namespace ptycho {
 struct BatchArgs;
 struct Pass2Args;
-template <int N> cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s);
-template <int N> cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s);
+// variant 0 = default CTA size, 1 = the alternative CTA size (autotuner)
+template <int N> cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s, int variant);
+template <int N> cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s, int variant);
 }  // namespace ptycho

@@ -3,6 +3,6 @@
 #include "launch.h"
 
 namespace ptycho {
-template cudaError_t launch_pass1<16>(const BatchArgs&, cudaStream_t);
-template cudaError_t launch_pass2<16>(const Pass2Args&, cudaStream_t);
+template cudaError_t launch_pass1<16>(const BatchArgs&, cudaStream_t, int);
+template cudaError_t launch_pass2<16>(const Pass2Args&, cudaStream_t, int);
 }  // namespace ptycho

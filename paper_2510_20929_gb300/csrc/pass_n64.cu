@@ -3,6 +3,6 @@
 #include "launch.h"
 
 namespace ptycho {
-template cudaError_t launch_pass1<64>(const BatchArgs&, cudaStream_t);
-template cudaError_t launch_pass2<64>(const Pass2Args&, cudaStream_t);
+template cudaError_t launch_pass1<64>(const BatchArgs&, cudaStream_t, int);
+template cudaError_t launch_pass2<64>(const Pass2Args&, cudaStream_t, int);
 }  // namespace ptycho

@@ -83,3 +83,19 @@ def test_uneven_workload_generator_stays_in_bounds():
     for w in ws:
         s = w["pos"] - w["N"] / 2.0
         assert s.min() >= 0 and s.max() < w["H"] - w["N"]
+
+
+def test_autotuned_epoch_matches_default_and_records_its_choice():
+    from paper_2510_20929_gb300 import api
+    it = _gpu_inputs([SHAPES[1]])[0]
+    O0, P0, pos, meas, order = it["dev"]
+    Od, Pd, Ot, Pt = O0.clone(), P0.clone(), O0.clone(), P0.clone()
+    ld, _ = api.lsqml_epoch(Od, Pd, pos, meas, order, api.make_opts(batch=8, delta_o=0.1, delta_p=0.1, eps=1e-6))
+    lt, _ = api.lsqml_epoch(Ot, Pt, pos, meas, order,
+                            api.make_opts(batch=8, delta_o=0.1, delta_p=0.1, eps=1e-6, autotune=True))
+    e = (rel(Ot.cpu().numpy(), Od.cpu().numpy()), rel(Pt.cpu().numpy(), Pd.cpu().numpy()),
+         abs(lt.item() - ld.item()) / abs(ld.item()))
+    t = api.tuning(api.dims_of(O0, P0, pos), 8)
+    print("autotune:", e, t)
+    assert max(e) < TOL_EPOCH
+    assert t is not None and t["pass1"] in (0, 1) and t["pass2"] in (0, 1) and min(t["pass1_ms"]) > 0
