@@ -222,22 +222,11 @@ __device__ __forceinline__ void load_pair(const float2* tile, int ph, float2& a,
   }
 }
 
+// Addressing of a square N x N tile with the FftCfg<N> swizzle: element i
+// (= i_rt | i_ct, disjoint bits, i_ct compile-time) of a row or column line.
 template <int N>
-struct Fft2 {
+struct SquareAddr {
   using C = FftCfg<N>;
-  static constexpr int R1 = C::R1, R2 = C::R2, S = R2 / R1, G = 32 / R1;
-
-  // Lane n (0..R1-1) within its line and the thread's line slot: the G lines
-  // of a warp are consecutive; the R1 lanes of a line are G lanes apart
-  // (INTER) or consecutive.
-  __device__ __forceinline__ static int line_lane() {
-    return C::INTER ? (int)(threadIdx.x & 31) / G : (int)threadIdx.x % R1;
-  }
-  __device__ __forceinline__ static int line_slot() {
-    return C::INTER ? (int)(threadIdx.x >> 5) * G + (int)(threadIdx.x & 31) % G : (int)threadIdx.x / R1;
-  }
-
-  // Address of element i (= i_rt | i_ct, disjoint bits) of `line`.
   template <bool ROW>
   __device__ __forceinline__ static int addr(int line, int i_rt, int i_ct) {
     if constexpr (ROW) {
@@ -249,6 +238,28 @@ struct Fft2 {
       const int base = i_rt * N + (line ^ C::fc(line >> 4) ^ C::fr(i_rt));
       return (base + i_ct * N) ^ C::fr(i_ct);
     }
+  }
+};
+
+// Line transforms of length R1*R2 on lines of a shared tile addressed by Addr.
+template <int R1_, int R2_, bool INTER_, class Addr>
+struct LineFft {
+  static constexpr int R1 = R1_, R2 = R2_, S = R2 / R1, G = 32 / R1;
+  static constexpr bool INTER = INTER_;
+
+  // Lane n (0..R1-1) within its line and the thread's line slot: the G lines
+  // of a warp are consecutive; the R1 lanes of a line are G lanes apart
+  // (INTER) or consecutive.
+  __device__ __forceinline__ static int line_lane() {
+    return INTER ? (int)(threadIdx.x & 31) / G : (int)threadIdx.x % R1;
+  }
+  __device__ __forceinline__ static int line_slot() {
+    return INTER ? (int)(threadIdx.x >> 5) * G + (int)(threadIdx.x & 31) % G : (int)threadIdx.x / R1;
+  }
+
+  template <bool ROW>
+  __device__ __forceinline__ static int addr(int line, int i_rt, int i_ct) {
+    return Addr::template addr<ROW>(line, i_rt, i_ct);
   }
 
   // Twiddles W_N^(n k2), k2 = 1..R2-1, for lane n: W^1..W^4 from the table,
@@ -358,6 +369,9 @@ struct Fft2 {
   __device__ __forceinline__ static int in_index(int n, int m) { return n + R1 * m; }
 };
 
+template <int N>
+struct Fft2 : LineFft<FftCfg<N>::R1, FftCfg<N>::R2, FftCfg<N>::INTER, SquareAddr<N>> {};
+
 // Twiddle table tw[n*(R2+1) + k2] = exp(-2 pi i n k2 / N) for n < R1, k2 <= R2
 // (the padding column makes the per-k2 reads of the R1 lanes of a line hit
 // distinct banks). Written by the whole CTA.
@@ -365,15 +379,19 @@ template <int N>
 struct Twiddles {
   static constexpr int R1 = FftCfg<N>::R1, R2 = FftCfg<N>::R2, COUNT = R1 * (R2 + 1);
 };
-template <int N>
-__device__ __forceinline__ void make_twiddles(float2* tw) {
-  constexpr int R2 = FftCfg<N>::R2;
-  for (int m = threadIdx.x; m < Twiddles<N>::COUNT; m += blockDim.x) {
+template <int L, int R1, int R2>
+__device__ __forceinline__ void make_line_twiddles(float2* tw) {
+  for (int m = threadIdx.x; m < R1 * (R2 + 1); m += blockDim.x) {
     const int n = m / (R2 + 1), k2 = m % (R2 + 1);
     float s, c;
-    sincospif(2.0f * (float)(n * k2) / (float)N, &s, &c);
+    sincospif(2.0f * (float)(n * k2) / (float)L, &s, &c);
     tw[m] = make_float2(c, -s);
   }
+}
+
+template <int N>
+__device__ __forceinline__ void make_twiddles(float2* tw) {
+  make_line_twiddles<N, FftCfg<N>::R1, FftCfg<N>::R2>(tw);
 }
 
 }  // namespace ptycho
