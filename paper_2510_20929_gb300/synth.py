@@ -172,6 +172,21 @@ def workload_spiral128(seed: int = 1002, J: int = 4096):
                 object=obj, probe=probe, pos=pos, total_counts=1e6, counts_per="pattern")
 
 
+def workload_spiral256(seed: int = 1003, J: int = 10000, pos_error: float = 1.5):
+    """Differentiable case: 8 Hermite-Gaussian modes (orders up to 3; power
+    halving per mode), probe 256^2, object 2048^2, 10,000 Fermat-spiral
+    positions (c = 8.85 px), initial positions = truth + N(0, pos_error px)."""
+    H = W = 2048
+    N = 256
+    obj = make_object(H, W, seed)
+    powers = [0.5 ** k for k in range(8)]
+    probe = hg_probe(N, powers, waist=40.0, quad_phase=0.005)
+    pos = fermat_spiral(J, 8.85, (H / 2.0, W / 2.0))
+    pos0 = pos + rng(seed + 1).normal(0.0, pos_error, size=pos.shape)
+    return dict(name="spiral256", H=H, W=W, N=N, M=8, J=J, batch=256, object=obj, probe=probe, pos=pos,
+                pos_init=pos0, total_counts=1e6, counts_per="pattern")
+
+
 def workload_small(N: int = 16, M: int = 2, H: int = 40, W: int = 44, J: int = 12,
                    seed: int = 7, step: float = 4.0):
     """Small seeded problem for parity tests: raster positions with sub-pixel jitter."""

@@ -131,3 +131,52 @@ def test_spiral128_sampled_forward_and_epoch_properties(spiral):
         assert torch.isfinite(alpha).all()
     print("spiral128 losses:", losses)
     assert losses[2] < losses[1] < losses[0]
+
+
+@pytest.fixture(scope="module")
+def spiral256():
+    w = synth.workload_spiral256()
+    return w
+
+
+def test_spiral256_sampled_gradients_match_oracle(spiral256):
+    # the full 2048^2 object and 8-mode 256^2 probe; the data term over four
+    # sampled positions of the perturbed scan, against the oracle on the same four
+    import torch
+    from paper_2510_20929_gb300.autograd import data_term
+    w = spiral256
+    idx = np.array([17, 2500, 6001, 9876])
+    O = _f32(w["object"] * np.exp(0.2j), True)
+    P = _f32(w["probe"] * 4.0, True)
+    pos_true, pos0 = _f32(w["pos"][idx]), _f32(w["pos_init"][idx])
+    I_m = _f32(synth.poisson_counts(orc.forward(_f32(w["object"], True), P, pos_true), 5))
+    L, gO, gP, gr = orc.loss_and_gradients(O, P, pos0, I_m, orc.GAUSSIAN, 1e-6)
+    dO, dP, dpos = to_dev(O, torch.complex64), to_dev(P, torch.complex64), to_dev(pos0, torch.float32)
+    for t in (dO, dP, dpos):
+        t.requires_grad_(True)
+    loss = data_term(dO, dP, dpos, to_dev(I_m, torch.float32), "gaussian", 1e-6)
+    loss.backward()
+    e = (abs(loss.item() - L) / L, rel(dO.grad.cpu().numpy(), gO), rel(dP.grad.cpu().numpy(), gP),
+         rel(dpos.grad.cpu().numpy(), gr))
+    print("spiral256 sampled gradients:", e)
+    assert e[0] < TOL_FWD and max(e[1:]) < TOL_EPOCH
+
+
+def test_spiral256_adam_on_all_three_reduces_loss_and_position_error(spiral256):
+    # Adam on object, probe and positions over all 10,000 positions from
+    # N(0, 1.5 px) position errors (data: the forward model at the true positions)
+    import torch
+    from paper_2510_20929_gb300 import api
+    from paper_2510_20929_gb300.autograd import reconstruct_adam
+    w = spiral256
+    O_true = to_dev(_f32(w["object"], True), torch.complex64)
+    P = to_dev(_f32(w["probe"] * 4.0, True), torch.complex64)
+    pos_true = to_dev(_f32(w["pos"]), torch.float32)
+    I_m = api.forward(O_true, P, pos_true)
+    pos = to_dev(_f32(w["pos_init"]), torch.float32)
+    O = O_true.clone()
+    rmse0 = (pos - pos_true).pow(2).mean().sqrt().item()
+    hist = reconstruct_adam(O, P.clone(), pos, I_m, epochs=20, lr_object=1e-3, lr_probe=1e-3, lr_pos=0.1)
+    rmse = (pos - pos_true).pow(2).mean().sqrt().item()
+    print("spiral256 Adam: loss", hist[0], "->", hist[-1], "position rmse", rmse0, "->", rmse)
+    assert hist[-1] < 0.7 * hist[0] and rmse < 0.95 * rmse0
