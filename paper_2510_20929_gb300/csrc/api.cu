@@ -177,7 +177,7 @@ Layout make_layout(const ptycho_dims& d, int B) {
   return L;
 }
 
-static bool supported_N(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 256; }
+static bool supported_N(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 192 || N == 256; }
 
 ptycho_status check_dims(const ptycho_dims* d) {
   if (!d) return PTYCHO_ERR_ARG;
@@ -199,6 +199,7 @@ static cudaError_t dispatch_N(int N, Fn&& fn) {
     case 32: return fn(std::integral_constant<int, 32>());
     case 64: return fn(std::integral_constant<int, 64>());
     case 128: return fn(std::integral_constant<int, 128>());
+    case 192: return fn(std::integral_constant<int, 192>());
     case 256: return fn(std::integral_constant<int, 256>());
   }
   return cudaErrorInvalidValue;

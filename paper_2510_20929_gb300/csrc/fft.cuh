@@ -145,6 +145,69 @@ template <int DIR> struct Dft<16, DIR> {
   }
 };
 
+// a * exp(DIR * i * m * pi / 12), m compile-time (the 24-point twiddles).
+template <int DIR, int m>
+__device__ __forceinline__ float2 tw24(float2 a) {
+  constexpr int mm = m % 24;
+  if constexpr (mm == 0) return a;
+  else if constexpr (mm == 6) return rot90<DIR>(a);
+  else if constexpr (mm == 12) return make_float2(-a.x, -a.y);
+  else if constexpr (mm == 18) return rot90<-DIR>(a);
+  else {
+    // cos and sin of multiples of 15 degrees
+    constexpr float c15 = 0.96592582628906829f, s15 = 0.25881904510252076f;
+    constexpr float c30 = 0.86602540378443865f, c45 = 0.70710678118654752f;
+    constexpr float cs[24] = {1.f,  c15,  c30,  c45,  0.5f,  s15,  0.f, -s15, -0.5f, -c45, -c30, -c15,
+                              -1.f, -c15, -c30, -c45, -0.5f, -s15, 0.f, s15,  0.5f,  c45,  c30,  c15};
+    constexpr float sn[24] = {0.f,  s15,  0.5f,  c45,  c30,  c15,  1.f,  c15,  c30,  c45,  0.5f,  s15,
+                              0.f, -s15, -0.5f, -c45, -c30, -c15, -1.f, -c15, -c30, -c45, -0.5f, -s15};
+    const float c = cs[mm], s = DIR < 0 ? -sn[mm] : sn[mm];
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+  }
+}
+
+template <int DIR> struct Dft<3, DIR> {
+  // X0 = v0 + (v1 + v2); X1,2 = v0 - (v1 + v2)/2 +- i DIR sin(2 pi / 3) (v1 - v2)
+  template <class V> __device__ __forceinline__ static void run(V& v) {
+    constexpr float s3 = 0.86602540378443865f;
+    const float2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+    const float2 m = make_float2(fmaf(-0.5f, t1.x, v[0].x), fmaf(-0.5f, t1.y, v[0].y));
+    const float2 r = make_float2(-DIR * s3 * t2.y, DIR * s3 * t2.x);   // i DIR s3 t2
+    v[0] = cadd(v[0], t1);
+    v[1] = cadd(m, r);
+    v[2] = csub(m, r);
+  }
+};
+
+template <int DIR> struct Dft<24, DIR> {
+  // n = b + 3a, k = k1 + 8k2: X[k] = sum_b W3^(b k2) W24^(b k1) sum_a W8^(a k1) v[b + 3a]
+  template <class V> __device__ __forceinline__ static void run(V& v) {
+    float2 y[3][8];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      float2 t[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) t[a] = v[b + 3 * a];
+      Dft<8, DIR>::run(t);
+#pragma unroll
+      for (int k1 = 0; k1 < 8; ++k1) y[b][k1] = t[k1];
+    }
+    y[1][1] = tw24<DIR, 1>(y[1][1]); y[1][2] = tw24<DIR, 2>(y[1][2]); y[1][3] = tw24<DIR, 3>(y[1][3]);
+    y[1][4] = tw24<DIR, 4>(y[1][4]); y[1][5] = tw24<DIR, 5>(y[1][5]); y[1][6] = tw24<DIR, 6>(y[1][6]);
+    y[1][7] = tw24<DIR, 7>(y[1][7]);
+    y[2][1] = tw24<DIR, 2>(y[2][1]); y[2][2] = tw24<DIR, 4>(y[2][2]); y[2][3] = tw24<DIR, 6>(y[2][3]);
+    y[2][4] = tw24<DIR, 8>(y[2][4]); y[2][5] = tw24<DIR, 10>(y[2][5]); y[2][6] = tw24<DIR, 12>(y[2][6]);
+    y[2][7] = tw24<DIR, 14>(y[2][7]);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+      float2 t[3] = {y[0][k1], y[1][k1], y[2][k1]};
+      Dft<3, DIR>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < 3; ++k2) v[k1 + 8 * k2] = t[k2];
+    }
+  }
+};
+
 // Per-size line split and tile swizzle. The swizzle XORs the low four column
 // bits with f(r, c) = fr(r) ^ fc(c >> 4), shift-XOR maps that are linear over
 // GF(2). The maps and the lane assignment (INTER: the R1 lanes of a line are

@@ -1,96 +1,124 @@
-// Per-position pass for 256 x 256 windows on a cluster of four CTAs.
+// Per-position pass for windows larger than one CTA's shared memory, on a
+// cluster of Q CTAs (N = 256: Q = 4; N = 192: Q = 3).
 //
-// The 256 x 256 complex tile (512 KB) does not fit one CTA's shared memory,
-// so a cluster of Q = 4 CTAs shares it: CTA q holds the 64 rows 64q .. 64q+63.
-// The 2-D DFT runs as
-//   * 256-point transforms of the CTA's own rows (shared memory, as in the
+// The N x N complex tile is shared by the cluster: CTA q holds the 64 rows
+// 64q .. 64q+63 (N = 64 Q). The 2-D DFT runs as
+//   * N-point transforms of the CTA's own rows (shared memory, as in the
 //     single-CTA kernel);
-//   * the column transform split as 256 = 4 x 64 (decimation in time over the
-//     row index R = 64q + r): a 4-point DFT across the cluster for every
+//   * the column transform split as N = Q x 64 (decimation in time over the
+//     row index R = 64q + r): a Q-point DFT across the cluster for every
 //     (r, c), reading the other CTAs' tiles through distributed shared memory,
-//     times the twiddle W_256^(r k1), after which CTA k1 holds the inputs of
-//     the outputs k = k1 + 4 k2; then 64-point transforms of its local columns;
+//     times the twiddle W_N^(r k1), after which CTA k1 holds the inputs of
+//     the outputs k = k1 + Q k2; then 64-point transforms of its local columns;
 //   * the inverse mirrors it: local 64-point column inverses, the conjugate
-//     twiddle and 4-point inverse DFT across the cluster, local row inverses.
+//     twiddle and Q-point inverse DFT across the cluster, local row inverses.
 // Everything else (patch gather, data term, back-propagation, scatter, the
 // position gradient) follows the single-CTA k_pass1 on the CTA's own rows;
-// the far fields of CTA q are the frequency rows q + 4 k2.
+// the far fields of CTA q are the frequency rows q + Q k2.
 #pragma once
 #include <cooperative_groups.h>
 
 #include "kernels.cuh"
 
 namespace ptycho {
-namespace n256 {
+namespace cl {
 
 namespace cg = cooperative_groups;
 
-constexpr int N = 256, Q = 4, LR = 64, T = 1024;
-constexpr int NN = N * N, LNN = LR * N;
+// Swizzles of the local 64 x N tile (column bits XOR f(r, c), linear over
+// GF(2)), chosen with the half-warp bank model for the row and column lines.
+struct Swz256 {  // f = ((r << 2) ^ (r >> 1) ^ (c >> 4)) & 15
+  __host__ __device__ static constexpr int fr(int r) { return ((r << 2) ^ (r >> 1)) & 15; }
+  __host__ __device__ static constexpr int fcb(int c) { return (c >> 4) & 15; }
+};
+struct Swz192 {  // f = ((r << 3) ^ (r << 1) ^ (r >> 2) ^ (c >> 6)) & 15
+  __host__ __device__ static constexpr int fr(int r) { return ((r << 3) ^ (r << 1) ^ (r >> 2)) & 15; }
+  __host__ __device__ static constexpr int fcb(int c) { return (c >> 6) & 15; }
+};
 
-// Local 64 x 256 tile: column bits XOR f(r, c) = ((r << 2) ^ (r >> 1) ^ (c >> 4)) & 15,
-// chosen with the same half-warp bank model for 256-point row lines (lanes
-// consecutive) and 64-point column lines (lanes interleaved).
-__host__ __device__ constexpr int fr(int r) { return ((r << 2) ^ (r >> 1)) & 15; }
-__host__ __device__ constexpr int fcb(int c) { return (c >> 4) & 15; }
-__device__ __forceinline__ int tix(int r, int c) { return r * N + (c ^ fr(r) ^ fcb(c)); }
-
+// Element i = i_rt + i_ct of a row or column line of the local 64 x N tile.
+// For power-of-two N with disjoint bits in i_rt and i_ct the linear swizzle
+// splits into a hoisted per-line part XOR a compile-time part; otherwise (N =
+// 192, or the S = 3 exchange offsets) the column is formed first.
+template <int N, class Z>
 struct RectAddr {
+  static constexpr bool POW2 = (N & (N - 1)) == 0;
   template <bool ROW>
   __device__ __forceinline__ static int addr(int line, int i_rt, int i_ct) {
-    if constexpr (ROW) {
-      const int base = line * N + (i_rt ^ fr(line) ^ fcb(i_rt));
-      return base ^ (i_ct ^ fcb(i_ct));
+    if constexpr (ROW && POW2) {
+      const int base = line * N + (i_rt ^ Z::fr(line) ^ Z::fcb(i_rt));
+      return base ^ (i_ct ^ Z::fcb(i_ct));
+    } else if constexpr (ROW) {
+      const int c = i_rt + i_ct;
+      return line * N + (c ^ Z::fr(line) ^ Z::fcb(c));
     } else {
-      const int base = i_rt * N + (line ^ fcb(line) ^ fr(i_rt));
-      return (base + i_ct * N) ^ fr(i_ct);
+      const int base = i_rt * N + (line ^ Z::fcb(line) ^ Z::fr(i_rt));
+      return (base + i_ct * N) ^ Z::fr(i_ct);
     }
   }
 };
 
-using RowF = LineFft<16, 16, false, RectAddr>;   // 256-point rows
-using ColF = LineFft<8, 8, true, RectAddr>;      // 64-point local columns
-
-struct Smem {
-  static constexpr int RP = N + 16;
-  static constexpr size_t red = 0;
-  static constexpr size_t tile = red + 256 * sizeof(double);
-  static constexpr size_t twr = tile + (size_t)LNN * sizeof(float2);
-  static constexpr size_t twc = twr + 16 * 17 * sizeof(float2);
-  static constexpr size_t tw256 = twc + 8 * 9 * sizeof(float2);
-  static constexpr size_t rI = tw256 + 256 * sizeof(float2);
-  static constexpr size_t bytes = rI + (size_t)LR * RP * sizeof(float);
+template <int N_, int Q_, int T_, int RR1_, int RR2_, bool RINTER_, bool CINTER_, class Z_>
+struct Cfg {
+  static constexpr int N = N_, Q = Q_, T = T_, LR = 64, NN = N * N, LNN = LR * N;
+  static constexpr int RR1 = RR1_, RR2 = RR2_;
+  using Z = Z_;
+  using RowF = LineFft<RR1, RR2, RINTER_, RectAddr<N, Z>>;   // N-point rows
+  using ColF = LineFft<8, 8, CINTER_, RectAddr<N, Z>>;       // 64-point local columns
+  static constexpr int ROW_ITER = LR * RR1 / T, COL_ITER = N * 8 / T;
+  static constexpr int NAT_STEPS = LNN / (2 * T);              // natural pixel pairs per thread
+  static constexpr int XB = N / 64, XPAIRS = 2048 / T;        // exchange column blocks, pairs per thread
+  static_assert(ROW_ITER >= 1 && COL_ITER >= 1 && XPAIRS >= 1, "CTA size");
+  __device__ __forceinline__ static int tix(int r, int c) { return r * N + (c ^ Z::fr(r) ^ Z::fcb(c)); }
+  struct Smem {
+    static constexpr int RP = N + 16;
+    static constexpr size_t red = 0;
+    static constexpr size_t tile = red + 256 * sizeof(double);
+    static constexpr size_t twr = tile + (size_t)LNN * sizeof(float2);
+    static constexpr size_t twc = twr + RR1 * (RR2 + 1) * sizeof(float2);
+    static constexpr size_t twn = twc + 8 * 9 * sizeof(float2);
+    static constexpr size_t twq = twn + N * sizeof(float2);
+    static constexpr size_t rI = twq + 8 * sizeof(float2);
+    static constexpr size_t bytes = rI + (size_t)LR * RP * sizeof(float);
+  };
 };
 
-// a * W4^m (W4 = e^{-2 pi i / 4}); m taken mod 4
-__device__ __forceinline__ float2 w4mul(float2 a, int m) {
-  switch (m & 3) {
-    case 0: return a;
-    case 1: return make_float2(a.y, -a.x);
-    case 2: return make_float2(-a.x, -a.y);
-    default: return make_float2(-a.y, a.x);
+using Cfg256 = Cfg<256, 4, 1024, 16, 16, false, true, Swz256>;
+using Cfg192 = Cfg<192, 3, 512, 8, 24, true, false, Swz192>;
+
+// a * W_Q^m (W_Q = e^{-2 pi i / Q}) from the table twq[m mod Q].
+template <int Q>
+__device__ __forceinline__ float2 wqmul(float2 a, int m, const float2* twq) {
+  if constexpr (Q == 4) {
+    switch (m & 3) {
+      case 0: return a;
+      case 1: return make_float2(a.y, -a.x);
+      case 2: return make_float2(-a.x, -a.y);
+      default: return make_float2(-a.y, a.x);
+    }
+  } else {
+    const int mm = ((m % Q) + Q) % Q;
+    return mm == 0 ? a : cmul(a, twq[mm]);
   }
 }
 
-// Natural local pixel pairs: thread t handles p = 2t + 2T s (s < 8): local row
-// p / 256, columns c, c+1.
-constexpr int NAT_STEPS = LNN / (2 * T);
-
-// Cross-cluster 4-point DFT of the tiles, in four column quarters.
-// Forward: tile_q <- W256^(r q) sum_q' W4^(q' q) tile_q'.
-// Inverse: tile_q <- sum_k1 W4^(-q k1) conj(W256^(r k1)) tile_k1.
-template <bool FWD>
-__device__ __forceinline__ void cross_exchange(cg::cluster_group& cluster, float2* tile, const float2* tw256, int q) {
+// Cross-cluster Q-point DFT of the tiles, in blocks of 64 columns.
+// Forward: tile_q <- W_N^(r q) sum_q' W_Q^(q' q) tile_q'.
+// Inverse: tile_q <- sum_k1 W_Q^(-q k1) conj(W_N^(r k1)) tile_k1.
+template <class C, bool FWD>
+__device__ __forceinline__ void cross_exchange(cg::cluster_group& cluster, float2* tile, const float2* twn,
+                                               const float2* twq, int q) {
+  constexpr int Q = C::Q, P = C::XPAIRS;
   float2* src[Q];
 #pragma unroll
   for (int qq = 0; qq < Q; ++qq) src[qq] = cluster.map_shared_rank(tile, qq);
 #pragma unroll 1
-  for (int h = 0; h < 4; ++h) {
-    float2 acc[2][2];
-    int rr[2], cc[2];
+  for (int h = 0; h < C::XB; ++h) {
+    float2 acc[P][2];
+    int rr[P], cc[P];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int p = 2 * (int)threadIdx.x + 2 * T * j;   // within a 64 x 64 quarter: 4096 pixels
+    for (int j = 0; j < P; ++j) {
+      const int p = 2 * (int)threadIdx.x + 2 * C::T * j;   // within a 64 x 64 block: 4096 pixels
       rr[j] = p / 64;
       cc[j] = 64 * h + p % 64;
       acc[j][0] = acc[j][1] = make_float2(0.f, 0.f);
@@ -98,29 +126,29 @@ __device__ __forceinline__ void cross_exchange(cg::cluster_group& cluster, float
 #pragma unroll
     for (int qq = 0; qq < Q; ++qq) {
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
+      for (int j = 0; j < P; ++j) {
         float2 x0, x1;
-        load_pair(src[qq], tix(rr[j], cc[j]), x0, x1);
+        load_pair(src[qq], C::tix(rr[j], cc[j]), x0, x1);
         if constexpr (FWD) {
           const int m = qq * q;
-          acc[j][0] = cadd(acc[j][0], w4mul(x0, m));
-          acc[j][1] = cadd(acc[j][1], w4mul(x1, m));
+          acc[j][0] = cadd(acc[j][0], wqmul<Q>(x0, m, twq));
+          acc[j][1] = cadd(acc[j][1], wqmul<Q>(x1, m, twq));
         } else {
-          const float2 t = tw256[(rr[j] * qq) & 255];     // W256^(r k1), conjugated below
+          const float2 t = twn[rr[j] * qq];     // W_N^(r k1), conjugated below
           const int m = -(q * qq);
-          acc[j][0] = cadd(acc[j][0], w4mul(cmulc(t, x0), m));
-          acc[j][1] = cadd(acc[j][1], w4mul(cmulc(t, x1), m));
+          acc[j][0] = cadd(acc[j][0], wqmul<Q>(cmulc(t, x0), m, twq));
+          acc[j][1] = cadd(acc[j][1], wqmul<Q>(cmulc(t, x1), m, twq));
         }
       }
     }
-    cluster.sync();   // every CTA has read this quarter of every tile
+    cluster.sync();   // every CTA has read this block of every tile
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < P; ++j) {
       if constexpr (FWD) {
-        const float2 t = tw256[(rr[j] * q) & 255];
-        store_pair(tile, tix(rr[j], cc[j]), cmul(acc[j][0], t), cmul(acc[j][1], t));
+        const float2 t = twn[rr[j] * q];
+        store_pair(tile, C::tix(rr[j], cc[j]), cmul(acc[j][0], t), cmul(acc[j][1], t));
       } else {
-        store_pair(tile, tix(rr[j], cc[j]), acc[j][0], acc[j][1]);
+        store_pair(tile, C::tix(rr[j], cc[j]), acc[j][0], acc[j][1]);
       }
     }
   }
@@ -128,64 +156,77 @@ __device__ __forceinline__ void cross_exchange(cg::cluster_group& cluster, float
 }
 
 // 2-D forward DFT (unnormalised) of the cluster's tile; on return CTA q's tile
-// holds the frequency rows q + 4 k2 (local row k2), natural layout.
+// holds the frequency rows q + Q k2 (local row k2), natural layout.
+template <class C>
 __device__ __forceinline__ void fwd2d(cg::cluster_group& cluster, float2* tile, const float2* twr,
-                                      const float2* twc, const float2* tw256, int q) {
-  {
-    const int n = RowF::line_lane(), row = RowF::line_slot();
-    float2 v[16];
-    RowF::load_in<true>(v, tile, row, n);
-    RowF::line_fwd<true>(v, tile, row, n, twr);
-    RowF::store_out<true>(v, tile, row, n);
+                                      const float2* twc, const float2* twn, const float2* twq, int q) {
+  using RowF = typename C::RowF;
+  using ColF = typename C::ColF;
+#pragma unroll 1
+  for (int it = 0; it < C::ROW_ITER; ++it) {
+    const int n = RowF::line_lane(), row = RowF::line_slot() + (C::T / C::RR1) * it;
+    float2 v[C::RR2];
+    RowF::template load_in<true>(v, tile, row, n);
+    RowF::template line_fwd<true>(v, tile, row, n, twr);
+    RowF::template store_out<true>(v, tile, row, n);
   }
   cluster.sync();
-  cross_exchange<true>(cluster, tile, tw256, q);
+  cross_exchange<C, true>(cluster, tile, twn, twq, q);
 #pragma unroll 1
-  for (int it = 0; it < 2; ++it) {
-    const int n = ColF::line_lane(), col = ColF::line_slot() + 128 * it;
+  for (int it = 0; it < C::COL_ITER; ++it) {
+    const int n = ColF::line_lane(), col = ColF::line_slot() + (C::T / 8) * it;
     float2 v[8];
-    ColF::load_in<false>(v, tile, col, n);
-    ColF::line_fwd<false>(v, tile, col, n, twc);
-    ColF::store_out<false>(v, tile, col, n);
+    ColF::template load_in<false>(v, tile, col, n);
+    ColF::template line_fwd<false>(v, tile, col, n, twc);
+    ColF::template store_out<false>(v, tile, col, n);
   }
   __syncthreads();
 }
 
-// 2-D inverse DFT (unnormalised): tile_q holds frequency rows q + 4 k2 on entry
+// 2-D inverse DFT (unnormalised): tile_q holds frequency rows q + Q k2 on entry
 // and the spatial rows 64q + r on return, natural layout.
+template <class C>
 __device__ __forceinline__ void inv2d(cg::cluster_group& cluster, float2* tile, const float2* twr,
-                                      const float2* twc, const float2* tw256, int q) {
+                                      const float2* twc, const float2* twn, const float2* twq, int q) {
+  using RowF = typename C::RowF;
+  using ColF = typename C::ColF;
 #pragma unroll 1
-  for (int it = 0; it < 2; ++it) {
-    const int n = ColF::line_lane(), col = ColF::line_slot() + 128 * it;
+  for (int it = 0; it < C::COL_ITER; ++it) {
+    const int n = ColF::line_lane(), col = ColF::line_slot() + (C::T / 8) * it;
     float2 v[8];
-    ColF::load_out<false>(v, tile, col, n);
-    ColF::line_inv<false>(v, tile, col, n, twc);
-    ColF::store_in<false>(v, tile, col, n);
+    ColF::template load_out<false>(v, tile, col, n);
+    ColF::template line_inv<false>(v, tile, col, n, twc);
+    ColF::template store_in<false>(v, tile, col, n);
   }
   __syncthreads();
   cluster.sync();
-  cross_exchange<false>(cluster, tile, tw256, q);
-  {
-    const int n = RowF::line_lane(), row = RowF::line_slot();
-    float2 v[16];
-    RowF::load_out<true>(v, tile, row, n);
-    RowF::line_inv<true>(v, tile, row, n, twr);
-    RowF::store_in<true>(v, tile, row, n);
+  cross_exchange<C, false>(cluster, tile, twn, twq, q);
+#pragma unroll 1
+  for (int it = 0; it < C::ROW_ITER; ++it) {
+    const int n = RowF::line_lane(), row = RowF::line_slot() + (C::T / C::RR1) * it;
+    float2 v[C::RR2];
+    RowF::template load_out<true>(v, tile, row, n);
+    RowF::template line_inv<true>(v, tile, row, n, twr);
+    RowF::template store_in<true>(v, tile, row, n);
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(T, 1) k_pass1_c256(BatchArgs a) {
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
+  constexpr int N = C::N, Q = C::Q, T = C::T, LR = C::LR, NN = C::NN, LNN = C::LNN;
+  constexpr int NAT_STEPS = C::NAT_STEPS;
+  using SM = typename C::Smem;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem[];
-  double* red = (double*)(smem + Smem::red);
-  float2* tile = (float2*)(smem + Smem::tile);
-  float2* twr = (float2*)(smem + Smem::twr);
-  float2* twc = (float2*)(smem + Smem::twc);
-  float2* tw256 = (float2*)(smem + Smem::tw256);
-  float* rI = (float*)(smem + Smem::rI);
-  constexpr int RP = Smem::RP;
+  double* red = (double*)(smem + SM::red);
+  float2* tile = (float2*)(smem + SM::tile);
+  float2* twr = (float2*)(smem + SM::twr);
+  float2* twc = (float2*)(smem + SM::twc);
+  float2* twn = (float2*)(smem + SM::twn);
+  float2* twq = (float2*)(smem + SM::twq);
+  float* rI = (float*)(smem + SM::rI);
+  constexpr int RP = SM::RP;
 
   const int q = (int)cluster.block_rank();
   const int slot = blockIdx.x / Q;
@@ -204,12 +245,17 @@ __global__ void __launch_bounds__(T, 1) k_pass1_c256(BatchArgs a) {
     return;
   }
   if (tid == 0 && q == 0 && a.valid) a.valid[slot] = 1;
-  make_line_twiddles<256, 16, 16>(twr);
+  make_line_twiddles<N, C::RR1, C::RR2>(twr);
   make_line_twiddles<64, 8, 8>(twc);
-  for (int m = tid; m < 256; m += T) {
+  for (int m = tid; m < N + Q; m += T) {
     float s, c;
-    sincospif(2.0f * (float)m / 256.0f, &s, &c);
-    tw256[m] = make_float2(c, -s);
+    if (m < N) {
+      sincospif(2.0f * (float)m / (float)N, &s, &c);
+      twn[m] = make_float2(c, -s);
+    } else {
+      sincospif(2.0f * (float)(m - N) / (float)Q, &s, &c);
+      twq[m - N] = make_float2(c, -s);
+    }
   }
 
   const int M = a.M;
@@ -238,26 +284,26 @@ __global__ void __launch_bounds__(T, 1) k_pass1_c256(BatchArgs a) {
         o1 = make_float2(o2.z, o2.w);
       }
       const float4 P2 = __ldg((const float4*)(Pk + p));
-      store_pair(tile, tix(r, c), cmul(make_float2(P2.x, P2.y), o0), cmul(make_float2(P2.z, P2.w), o1));
+      store_pair(tile, C::tix(r, c), cmul(make_float2(P2.x, P2.y), o0), cmul(make_float2(P2.z, P2.w), o1));
     }
     __syncthreads();
-    fwd2d(cluster, tile, twr, twc, tw256, q);
+    fwd2d<C>(cluster, tile, twr, twc, twn, twq, q);
 #pragma unroll 2
     for (int s = 0; s < NAT_STEPS; ++s) {
       const int pl = 2 * tid + 2 * T * s, r = pl / N, c = pl % N;   // r = local frequency row k2
       float2 X0, X1;
-      load_pair(tile, tix(r, c), X0, X1);
+      load_pair(tile, C::tix(r, c), X0, X1);
       X0 = cscale(X0, invN);
       X1 = cscale(X1, invN);
       float2* ri = (float2*)(rI + r * RP + c);
       const float2 i2 = make_float2(cabs2(X0), cabs2(X1));
       *ri = (k == 0) ? i2 : make_float2(ri->x + i2.x, ri->y + i2.y);
       if (psi_s)
-        *(float4*)(psi_s + (size_t)k * NN + (q + 4 * r) * N + c) = make_float4(X0.x, X0.y, X1.x, X1.y);
+        *(float4*)(psi_s + (size_t)k * NN + (q + Q * r) * N + c) = make_float4(X0.x, X0.y, X1.x, X1.y);
     }
   }
 
-  // ---- data term (frequency rows q + 4 k2) ----------------------------------------
+  // ---- data term (frequency rows q + Q k2) ----------------------------------------
   const int mode = a.mode;
   const float eps = a.eps;
   const float* meas = a.meas + (size_t)j * NN;
@@ -266,7 +312,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1_c256(BatchArgs a) {
 #pragma unroll 1
   for (int s = 0; s < NAT_STEPS; ++s) {
     const int pl = 2 * tid + 2 * T * s, r = pl / N, c = pl % N;
-    const int pix = (q + 4 * r) * N + c;
+    const int pix = (q + Q * r) * N + c;
     float* ri = rI + r * RP + c;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -317,18 +363,18 @@ __global__ void __launch_bounds__(T, 1) k_pass1_c256(BatchArgs a) {
 #pragma unroll 2
     for (int s = 0; s < NAT_STEPS; ++s) {
       const int pl = 2 * tid + 2 * T * s, r = pl / N, c = pl % N;
-      const float4 X = *(const float4*)(psi_s + (size_t)k * NN + (q + 4 * r) * N + c);
+      const float4 X = *(const float4*)(psi_s + (size_t)k * NN + (q + Q * r) * N + c);
       const float2 f = *(const float2*)(rI + r * RP + c);
-      store_pair(tile, tix(r, c), make_float2(X.x * f.x, X.y * f.x), make_float2(X.z * f.y, X.w * f.y));
+      store_pair(tile, C::tix(r, c), make_float2(X.x * f.x, X.y * f.x), make_float2(X.z * f.y, X.w * f.y));
     }
     __syncthreads();
-    inv2d(cluster, tile, twr, twc, tw256, q);
+    inv2d<C>(cluster, tile, twr, twc, twn, twq, q);
 #pragma unroll 2
     for (int s = 0; s < NAT_STEPS; ++s) {
       const int pl = 2 * tid + 2 * T * s, r = pl / N, c = pl % N;
       const int p = (rowbase + r) * N + c;
       float2 x0, x1;
-      load_pair(tile, tix(r, c), x0, x1);
+      load_pair(tile, C::tix(r, c), x0, x1);
       const float4 P2 = __ldg((const float4*)(Pk + p));
       const float4 o2 = *(const float4*)(o_s + p);
       const float2 g0 = cmulc(make_float2(P2.x, P2.y), x0), g1 = cmulc(make_float2(P2.z, P2.w), x1);
@@ -369,7 +415,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1_c256(BatchArgs a) {
       }
       return h;
     };
-    constexpr int SEG = T / N1;                       // 3 row segments of the CTA's rows
+    constexpr int SEG = T / N1 > 0 ? T / N1 : 1;      // row segments of the CTA's rows
     const int rows = y1 - y0, rs = (rows + SEG - 1) / SEG;
     for (int item = tid; item < N1 * SEG; item += T) {
       const int sg = item / N1, x = item % N1;
@@ -412,6 +458,6 @@ __global__ void __launch_bounds__(T, 1) k_pass1_c256(BatchArgs a) {
   }
 }
 
-}  // namespace n256
+}  // namespace cl
 
 }  // namespace ptycho

@@ -1,5 +1,6 @@
-"""256 x 256 windows (four-CTA cluster kernel) against the FP64 oracle:
-forward intensities, gradients and LSQML epochs, including a ragged last batch."""
+"""Cluster windows (256 x 256 on four CTAs, 192 x 192 on three) against the FP64
+oracle: forward intensities, gradients and LSQML epochs, including a ragged
+last batch."""
 import numpy as np
 import pytest
 
@@ -16,36 +17,38 @@ def _dev(p):
                               to_dev(pos, torch.float32), to_dev(I_m, torch.float32))
 
 
-@pytest.mark.parametrize("M", [1, 3])
-def test_forward_n256(M):
+@pytest.mark.parametrize("N,M", [(256, 1), (256, 3), (192, 1), (192, 3)])
+def test_forward_cluster(N, M):
     from paper_2510_20929_gb300 import api
-    p = problem(N=256, M=M, H=330, W=340, J=6, step=20.0)
+    p = problem(N=N, M=M, H=N + 74, W=N + 84, J=6, step=20.0)
     (O, P, pos, _), (dO, dP, dpos, _) = _dev(p)
     I = api.forward(dO, dP, dpos).cpu().numpy()
     ref = orc.forward(O, P, pos)
     e = rel(I, ref)
-    print(f"forward N=256 M={M}: {e:.3e}")
+    print(f"forward N={N} M={M}: {e:.3e}")
     assert e < 1e-5
 
 
+@pytest.mark.parametrize("N", [256, 192])
 @pytest.mark.parametrize("noise", ["gaussian", "poisson"])
-def test_gradients_n256(noise):
+def test_gradients_cluster(noise, N):
     from paper_2510_20929_gb300 import api
-    p = problem(N=256, M=2, H=320, W=330, J=5, step=20.0)
+    p = problem(N=N, M=2, H=N + 64, W=N + 74, J=5, step=20.0)
     (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
     nz = orc.GAUSSIAN if noise == "gaussian" else orc.POISSON
     L, gO, gP, gr = orc.loss_and_gradients(O, P, pos, I_m, nz, 1e-6)
     loss, dgO, dgP, dgr = api.adjoint(dO, dP, dpos, dI, noise, eps=1e-6, batch=3)
     e = (abs(loss.item() - L) / abs(L), rel(dgO.cpu().numpy(), gO), rel(dgP.cpu().numpy(), gP),
          rel(dgr.cpu().numpy(), gr))
-    print(f"grad N=256 {noise}: {e}")
+    print(f"grad N={N} {noise}: {e}")
     assert e[0] < 1e-5 and max(e[1:]) < 1e-4
 
 
-def test_lsqml_epoch_n256():
+@pytest.mark.parametrize("N", [256, 192])
+def test_lsqml_epoch_cluster(N):
     import torch
     from paper_2510_20929_gb300 import api
-    p = problem(N=256, M=2, H=320, W=330, J=7, step=18.0)
+    p = problem(N=N, M=2, H=N + 64, W=N + 74, J=7, step=18.0)
     (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
     order = np.random.default_rng(1).permutation(7).astype(np.int32)
     opts = orc.LsqmlOptions(batch=3, delta_o=0.1, delta_p=0.1, eps=1e-6)
@@ -54,5 +57,5 @@ def test_lsqml_epoch_n256():
                                   delta_p=0.1, eps=1e-6, want_alpha=True)
     e = (rel(dO.cpu().numpy(), O_ref), rel(dP.cpu().numpy(), P_ref), rel(alpha.cpu().numpy(), a_ref),
          abs(loss.item() - L_ref) / abs(L_ref))
-    print(f"epoch N=256: {e}")
+    print(f"epoch N={N}: {e}")
     assert max(e) < 1e-4
