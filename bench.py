@@ -366,7 +366,7 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_uneven(args, rank, world, local_rank):
-    """Batched serving of 16 uneven reconstructions (windows 64/128, J ~ U[500, 20000]):
+    """Batched serving of 16 uneven reconstructions (windows 64/128/192/256, J ~ U[500, 20000]):
     one epoch of every reconstruction per step, batched (with and without graph
     replay) against the same reconstructions run one after the other."""
     import torch

@@ -202,7 +202,7 @@ def workload_small(N: int = 16, M: int = 2, H: int = 40, W: int = 44, J: int = 1
                 object=obj, probe=probe, pos=pos)
 
 
-def workload_uneven(n: int = 16, seed: int = 1005, N_choices=(64, 128), J_range=(500, 20000),
+def workload_uneven(n: int = 16, seed: int = 1005, N_choices=(64, 128, 192, 256), J_range=(500, 20000),
                     counts_range=(1e5, 1e7)):
     """Independent reconstructions of uneven size for batched serving: per
     reconstruction a window N drawn from ``N_choices``, J ~ U[J_range], a

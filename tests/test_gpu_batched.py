@@ -29,7 +29,8 @@ def _gpu_inputs(shapes):
 
 
 SHAPES = [(32, 2, 72, 76, 16, 6.0, 6), (64, 1, 150, 160, 20, 12.0, 8), (16, 3, 41, 37, 9, 3.0, 9),
-          (64, 3, 160, 150, 25, 12.0, 10), (128, 2, 300, 310, 12, 24.0, 5)]
+          (64, 3, 160, 150, 25, 12.0, 10), (128, 2, 300, 310, 12, 24.0, 5), (192, 1, 256, 266, 6, 20.0, 4),
+          (256, 2, 320, 330, 5, 20.0, 3)]
 
 
 @pytest.mark.parametrize("graph", [False, True])
