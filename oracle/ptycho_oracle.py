@@ -361,3 +361,66 @@ def align_global_phase(O, O_ref, mask=None):
         mask = np.ones(O.shape, bool)
     c = np.sum(np.conj(O[mask]) * O_ref[mask])
     return O * (c / abs(c)) if abs(c) > 0 else O
+
+
+# ---------------------------------------------------------------------------
+# Orthogonal probe relaxation (Sec. 2.1: scan-point-specific probes; Sec. 3.2).
+# The primary probe mode of position j is sum_m w_jm U_m over K eigenmodes U
+# with real weights w [J, K]; the other incoherent modes are shared.
+# ---------------------------------------------------------------------------
+def opr_primary(U, w_j):
+    """Primary probe mode of one position: sum_m w_jm U_m."""
+    return np.tensordot(np.asarray(w_j, np.float64), U, axes=(0, 0))
+
+
+def opr_modes(U, w_j, P_rest):
+    """All incoherent modes of one position: [sum_m w_jm U_m, P_rest...]."""
+    P0 = opr_primary(U, w_j)[None]
+    return np.concatenate([P0, P_rest], axis=0) if P_rest is not None and len(P_rest) else P0
+
+
+def forward_opr(O, U, w, P_rest, pos):
+    """Predicted intensities with position-dependent primary modes [J, N, N]."""
+    J, N = pos.shape[0], U.shape[-1]
+    out = np.empty((J, N, N), np.float64)
+    for j in range(J):
+        Psi = dft2(opr_modes(U, w[j], P_rest) * extract(O, pos[j], N)[None])
+        out[j] = np.sum(np.abs(Psi) ** 2, axis=0)
+    return out
+
+
+def vjp_opr(O, U, w, P_rest, pos, G):
+    """Gradients through the OPR forward model given G = dL/dI.
+
+    With g_P0 = conj(o_j) grad_psi_j0: grad U_m = sum_j w_jm g_P0 and
+    dL/dw_jm = Re<U_m, g_P0> (w real); the rest as in :func:`vjp`.
+    """
+    H, W = O.shape
+    K, N = U.shape[0], U.shape[-1]
+    J = pos.shape[0]
+    gO = np.zeros((H, W), np.complex128)
+    gU = np.zeros_like(U, dtype=np.complex128)
+    gw = np.zeros((J, K), np.float64)
+    gP = np.zeros_like(P_rest, dtype=np.complex128) if P_rest is not None else None
+    gr = np.zeros((J, 2), np.float64)
+    for j in range(J):
+        o = extract(O, pos[j], N)
+        Pj = opr_modes(U, w[j], P_rest)
+        gpsi = idft2(2.0 * G[j][None] * dft2(Pj * o[None]))
+        go = np.sum(np.conj(Pj) * gpsi, axis=0)
+        gO += scatter(go, pos[j], H, W)
+        gP0 = np.conj(o) * gpsi[0]
+        gU += np.asarray(w[j], np.float64)[:, None, None] * gP0[None]
+        gw[j] = np.real(np.sum(np.conj(U) * gP0[None], axis=(1, 2)))
+        if gP is not None:
+            gP += np.conj(o)[None] * gpsi[1:]
+        d_dy, d_dx = extract_dr(O, pos[j], N)
+        gr[j, 0] = np.real(np.sum(np.conj(go) * d_dy))
+        gr[j, 1] = np.real(np.sum(np.conj(go) * d_dx))
+    return gO, gU, gw, gP, gr
+
+
+def loss_and_gradients_opr(O, U, w, P_rest, pos, I_m, noise=GAUSSIAN, eps=0.0):
+    I = forward_opr(O, U, w, P_rest, pos)
+    loss = sum(pattern_loss(I[j], I_m[j], noise, eps) for j in range(pos.shape[0]))
+    return (loss,) + vjp_opr(O, U, w, P_rest, pos, dloss_dI(I, I_m, noise, eps))

@@ -322,3 +322,44 @@ def test_poisson_lsqml_reduces_the_loss():
         O, _, L, _ = orc.lsqml_epoch(O, P, pos, I_m, order, opts)
         losses.append(L)
     assert losses[-1] < losses[0]
+
+
+# --------------------------------------------------------------------------- orthogonal probe relaxation
+def _opr_problem(seed=13):
+    g = np.random.default_rng(seed)
+    w = synth.workload_small(N=8, M=3, H=24, W=24, J=4, seed=seed, step=3.0)
+    P = w["probe"] * 3.0
+    U = np.stack([P[0], 0.3 * P[1] * np.exp(0.4j)])             # two eigenmodes of the primary mode
+    wts = 1.0 + 0.1 * g.standard_normal((4, 2))
+    I_m = synth.poisson_counts(orc.forward_opr(w["object"], U, wts, P[1:], w["pos"]), seed)
+    O = w["object"] * (1 + 0.1 * crandn(g, 24, 24))
+    return O, U, wts, P[1:], w["pos"], I_m
+
+
+def test_opr_with_one_unit_weight_mode_is_the_shared_probe_model():
+    O, U, wts, P_rest, pos, I_m = _opr_problem()
+    U1, w1 = U[:1], np.ones((4, 1))
+    P = np.concatenate([U1, P_rest])
+    assert np.max(np.abs(orc.forward_opr(O, U1, w1, P_rest, pos) - orc.forward(O, P, pos))) < 1e-12
+    G = np.random.default_rng(2).standard_normal(I_m.shape)
+    gO, gU, gw, gP, gr = orc.vjp_opr(O, U1, w1, P_rest, pos, G)
+    gO_ref, gP_ref, gr_ref = orc.vjp(O, P, pos, G)
+    assert np.max(np.abs(gO - gO_ref)) < 1e-10 and np.max(np.abs(gr - gr_ref)) < 1e-10
+    assert np.max(np.abs(gU[0] - gP_ref[0])) < 1e-10 and np.max(np.abs(gP - gP_ref[1:])) < 1e-10
+
+
+def test_opr_gradients_match_central_finite_differences():
+    O, U, wts, P_rest, pos, I_m = _opr_problem()
+    L, gO, gU, gw, gP, gr = orc.loss_and_gradients_opr(O, U, wts, P_rest, pos, I_m, orc.GAUSSIAN, 1e-3)
+    g = np.random.default_rng(3)
+    h = 1e-6
+
+    def L_at(U_, w_):
+        return orc.loss_and_gradients_opr(O, U_, w_, P_rest, pos, I_m, orc.GAUSSIAN, 1e-3)[0]
+
+    dU = crandn(g, *U.shape)
+    fd = (L_at(U + h * dU, wts) - L_at(U - h * dU, wts)) / (2 * h)
+    assert abs(fd - np.real(np.vdot(gU, dU))) < 1e-6 * abs(fd)
+    dw = g.standard_normal(wts.shape)
+    fd = (L_at(U, wts + h * dw) - L_at(U, wts - h * dw)) / (2 * h)
+    assert abs(fd - np.sum(gw * dw)) < 1e-6 * abs(fd)
