@@ -424,3 +424,151 @@ def loss_and_gradients_opr(O, U, w, P_rest, pos, I_m, noise=GAUSSIAN, eps=0.0):
     I = forward_opr(O, U, w, P_rest, pos)
     loss = sum(pattern_loss(I[j], I_m[j], noise, eps) for j in range(pos.shape[0]))
     return (loss,) + vjp_opr(O, U, w, P_rest, pos, dloss_dI(I, I_m, noise, eps))
+
+
+@dataclass
+class OprOptions:
+    """Options of the LSQML minibatch with orthogonal probe relaxation."""
+    update_weights: bool = True
+    weight_step: float = 1.0      # relaxation of the per-position weight update
+
+
+def weight_solve(A, b, lam):
+    """Damped normal equations (A + lam (tr A / K) I) dw = b in FP64 (Cholesky).
+
+    A singular (or non-positive) damped system gives dw = 0.
+    """
+    A = np.asarray(A, np.float64)
+    K = A.shape[0]
+    Ad = A + lam * (np.trace(A) / K) * np.eye(K)
+    try:
+        L = np.linalg.cholesky(Ad)
+    except np.linalg.LinAlgError:
+        return np.zeros(K)
+    y = np.linalg.solve(L, np.asarray(b, np.float64))
+    return np.linalg.solve(L.T, y)
+
+
+def lsqml_batch_opr(O, U, w, P_rest, pos, I_m, idx, opts: LsqmlOptions, opr: OprOptions,
+                    record: dict | None = None):
+    """One LSQML minibatch with a relaxed primary probe mode (Sec. 2.1, OPR).
+
+    Returns (O, U, w, P_rest, loss, alpha). Position j's modes are
+    [P_j0, P_rest...] with P_j0 = sum_m w_jm U_m (U [K, N, N], w [J, K] real).
+    The exit waves, chi, g_j = sum_k conj(P_jk) chi_jk, h_jk = conj(o_j) chi_jk,
+    the object direction and the shared modes' directions are those of
+    :func:`lsqml_batch` with the per-position primary mode, the illumination
+    included. The eigenmodes take the weighted probe direction
+      dU_m = (sum_j w_jm h_j0) / (D_m + delta_P),  D_m = sum_j w_jm^2 |o_j|^2,
+    with delta_P = delta_p max(max Dp, max_m D_m); the primary-mode direction
+    of position j is then dP_j0 = sum_m w_jm dU_m in the step-size system, and
+    U_m += mean(alpha_P) dU_m with the shared modes. The weights of each
+    position move by the least-squares fit of the primary mode's exit-wave
+    change onto the eigenmodes' exit waves: min over real dw of
+    ||chi_j0 - sum_m dw_m U_m o_j||^2 (normal equations A_mn = Re<U_m o_j, U_n o_j>,
+    b_m = Re<U_m o_j, chi_j0>, damped by lam tr(A)/K), w_j += weight_step dw,
+    taken with this batch's U and chi.
+    """
+    H, W = O.shape
+    K, N = U.shape[0], U.shape[-1]
+    Mr = 0 if P_rest is None else P_rest.shape[0]
+    idx = [int(i) for i in idx]
+    B = len(idx)
+    Sp_rest = np.sum(np.abs(P_rest) ** 2, axis=0) if Mr else np.zeros((N, N))
+
+    loss = 0.0
+    o_all, chi_all, g_all = [], [], []
+    dO_acc = np.zeros((H, W), np.complex128)
+    illum = np.zeros((H, W), np.float64)
+    dP_acc = np.zeros((Mr, N, N), np.complex128)
+    dU_acc = np.zeros((K, N, N), np.complex128)
+    Dp = np.zeros((N, N), np.float64)
+    D = np.zeros((K, N, N), np.float64)
+    for j in idx:
+        o = extract(O, pos[j], N)
+        Pj = opr_modes(U, w[j], P_rest)
+        Psi = dft2(Pj * o[None])
+        I = np.sum(np.abs(Psi) ** 2, axis=0)
+        loss += pattern_loss(I, I_m[j], opts.noise, opts.eps)
+        rho = modulus_ratio(I, I_m[j], opts.noise, opts.eps)
+        chi = idft2((rho - 1.0)[None] * Psi)
+        g = np.sum(np.conj(Pj) * chi, axis=0)
+        dO_acc += scatter(g, pos[j], H, W)
+        illum += scatter(Sp_rest + np.abs(Pj[0]) ** 2, pos[j], H, W)
+        h = np.conj(o)[None] * chi
+        dP_acc += h[1:]
+        dU_acc += np.asarray(w[j], np.float64)[:, None, None] * h[0][None]
+        Dp += np.abs(o) ** 2
+        D += (np.asarray(w[j], np.float64) ** 2)[:, None, None] * (np.abs(o) ** 2)[None]
+        o_all.append(o)
+        chi_all.append(chi)
+        g_all.append(g)
+
+    delta_O = opts.delta_o * float(np.max(illum))
+    delta_P = opts.delta_p * max(float(np.max(Dp)), float(np.max(D)))
+    dO_hat = dO_acc / (illum + delta_O) if opts.update_object else np.zeros((H, W), np.complex128)
+    if opts.update_probe:
+        dP = dP_acc / (Dp + delta_P)[None]
+        dU = dU_acc / (D + delta_P)
+    else:
+        dP, dU = np.zeros_like(dP_acc), np.zeros_like(dU_acc)
+
+    alpha = np.zeros((B, 2), np.float64)
+    dw = np.zeros((B, K), np.float64)
+    for i, j in enumerate(idx):
+        o, chi = o_all[i], chi_all[i]
+        Pj = opr_modes(U, w[j], P_rest)
+        dPj = np.concatenate([opr_primary(dU, w[j])[None], dP], axis=0)
+        u = extract(dO_hat, pos[j], N)[None] * Pj
+        v = o[None] * dPj
+        A11 = float(np.sum(np.abs(u) ** 2))
+        A12 = float(np.real(np.sum(np.conj(u) * v)))
+        A22 = float(np.sum(np.abs(v) ** 2))
+        b1 = float(np.real(np.sum(np.conj(u) * chi)))
+        b2 = float(np.real(np.sum(np.conj(v) * chi)))
+        alpha[i] = step_solve(A11, A12, A22, b1, b2, opts.lam)
+        if opr.update_weights:
+            E = U * o[None]                                   # eigenmode exit waves
+            A = np.real(np.einsum("mxy,nxy->mn", np.conj(E), E))
+            b = np.real(np.einsum("mxy,xy->m", np.conj(E), chi[0]))
+            dw[i] = weight_solve(A, b, opts.lam)
+
+    O_new = O.copy()
+    if opts.update_object:
+        upd = np.zeros((H, W), np.complex128)
+        for i, j in enumerate(idx):
+            upd += scatter(alpha[i, 0] * g_all[i], pos[j], H, W)
+        O_new = O + upd / (illum + delta_O)
+    U_new, P_new = U.copy(), (P_rest.copy() if Mr else P_rest)
+    if opts.update_probe:
+        a_p = float(np.mean(alpha[:, 1]))
+        U_new = U + a_p * dU
+        if Mr:
+            P_new = P_rest + a_p * dP
+    w_new = np.array(w, np.float64, copy=True)
+    if opr.update_weights:
+        for i, j in enumerate(idx):
+            w_new[j] += opr.weight_step * dw[i]
+
+    if record is not None:
+        record.update(dict(dO_acc=dO_acc, illum=illum, dP_acc=dP_acc, dU_acc=dU_acc, Dp=Dp, D=D,
+                           delta_O=delta_O, delta_P=delta_P, dU=dU, dP=dP, dw=dw,
+                           chi=np.stack(chi_all), alpha=alpha))
+    return O_new, U_new, w_new, P_new, loss, alpha
+
+
+def lsqml_epoch_opr(O, U, w, P_rest, pos, I_m, order, opts: LsqmlOptions, opr: OprOptions):
+    """One OPR epoch: minibatches of ``opts.batch`` positions taken from ``order`` in turn."""
+    O = np.asarray(O, np.complex128).copy()
+    U = np.asarray(U, np.complex128).copy()
+    w = np.asarray(w, np.float64).copy()
+    P_rest = None if P_rest is None else np.asarray(P_rest, np.complex128).copy()
+    order = np.asarray(order)
+    loss = 0.0
+    alpha = np.zeros((pos.shape[0], 2), np.float64)
+    for b0 in range(0, order.shape[0], opts.batch):
+        idx = order[b0:b0 + opts.batch]
+        O, U, w, P_rest, l, a = lsqml_batch_opr(O, U, w, P_rest, pos, I_m, idx, opts, opr)
+        loss += l
+        alpha[idx] = a
+    return O, U, w, P_rest, loss, alpha

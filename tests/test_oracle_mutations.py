@@ -62,3 +62,15 @@ def test_missing_probe_conjugate_in_gradient_is_caught(monkeypatch):
 
     monkeypatch.setattr(orc, "vjp", wrong)
     _fails(pins.test_gradients_match_central_finite_differences, orc.GAUSSIAN)
+
+
+def test_eigenmodes_paired_with_the_wrong_weights_are_caught(monkeypatch):
+    real = orc.opr_primary
+    monkeypatch.setattr(orc, "opr_primary", lambda U, w_j: real(U, np.asarray(w_j)[::-1]))
+    _fails(pins.test_opr_unit_weights_select_one_eigenmode)
+
+
+def test_weight_update_of_the_wrong_sign_is_caught(monkeypatch):
+    real = orc.weight_solve
+    monkeypatch.setattr(orc, "weight_solve", lambda A, b, lam: -real(A, b, lam))
+    _fails(pins.test_lsqml_opr_truth_is_a_fixed_point_and_weights_converge)

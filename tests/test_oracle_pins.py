@@ -348,6 +348,16 @@ def test_opr_with_one_unit_weight_mode_is_the_shared_probe_model():
     assert np.max(np.abs(gU[0] - gP_ref[0])) < 1e-10 and np.max(np.abs(gP - gP_ref[1:])) < 1e-10
 
 
+def test_opr_unit_weights_select_one_eigenmode():
+    # w_j = e_m makes U_m the primary mode of every position (the plain model)
+    O, U, wts, P_rest, pos, I_m = _opr_problem()
+    for m in range(U.shape[0]):
+        e = np.zeros((4, U.shape[0]))
+        e[:, m] = 1.0
+        ref = orc.forward(O, np.concatenate([U[m:m + 1], P_rest]), pos)
+        assert np.max(np.abs(orc.forward_opr(O, U, e, P_rest, pos) - ref)) < 1e-12 * np.max(ref)
+
+
 def test_opr_gradients_match_central_finite_differences():
     O, U, wts, P_rest, pos, I_m = _opr_problem()
     L, gO, gU, gw, gP, gr = orc.loss_and_gradients_opr(O, U, wts, P_rest, pos, I_m, orc.GAUSSIAN, 1e-3)
@@ -363,3 +373,65 @@ def test_opr_gradients_match_central_finite_differences():
     dw = g.standard_normal(wts.shape)
     fd = (L_at(U, wts + h * dw) - L_at(U, wts - h * dw)) / (2 * h)
     assert abs(fd - np.sum(gw * dw)) < 1e-6 * abs(fd)
+
+
+def test_lsqml_opr_with_one_unit_weight_mode_is_plain_lsqml():
+    O, U, wts, P_rest, pos, I_m = _opr_problem()
+    P = np.concatenate([U[:1], P_rest])
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=4, eps=1e-3, delta_o=0.1, delta_p=0.1)
+    idx = [2, 0, 3, 1]
+    O1, P1, L1, a1 = orc.lsqml_batch(O, P, pos, I_m, idx, opts)
+    O2, U2, w2, Pr2, L2, a2 = orc.lsqml_batch_opr(O, U[:1], np.ones((4, 1)), P_rest, pos, I_m, idx, opts,
+                                                  orc.OprOptions(update_weights=False))
+    assert abs(L1 - L2) < 1e-12 * abs(L1)
+    assert np.max(np.abs(a1 - a2)) < 1e-10 * np.max(np.abs(a1))
+    assert np.max(np.abs(O1 - O2)) < 1e-12
+    assert np.max(np.abs(P1 - np.concatenate([U2, Pr2]))) < 1e-12
+    assert np.all(w2 == 1.0)
+
+
+def test_lsqml_opr_is_equivariant_under_weight_rescaling():
+    # (s w, U / s) is the same probe family: with no probe damping and no
+    # regularisation (whose trace term mixes the modes' scales) the batch
+    # update maps to the rescaled update of (w, U)
+    O, U, wts, P_rest, pos, I_m = _opr_problem()
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=4, eps=1e-3, delta_o=0.1, delta_p=0.0, lam=0.0)
+    opr = orc.OprOptions(update_weights=True, weight_step=0.7)
+    idx = [1, 3, 0, 2]
+    s = np.array([2.5, 0.4])
+    O1, U1, w1, Pr1, L1, a1 = orc.lsqml_batch_opr(O, U, wts, P_rest, pos, I_m, idx, opts, opr)
+    O2, U2, w2, Pr2, L2, a2 = orc.lsqml_batch_opr(O, U / s[:, None, None], wts * s[None], P_rest, pos, I_m,
+                                                  idx, opts, opr)
+    assert abs(L1 - L2) < 1e-11 * abs(L1)
+    assert np.max(np.abs(a1 - a2)) < 1e-9 * np.max(np.abs(a1))
+    assert np.max(np.abs(O1 - O2)) < 1e-11
+    assert np.max(np.abs(U1 - U2 * s[:, None, None])) < 1e-11 * np.max(np.abs(U1))
+    assert np.max(np.abs(w1 - w2 / s[None])) < 1e-11
+    assert np.max(np.abs(Pr1 - Pr2)) < 1e-12
+
+
+def _opr_noiseless(seed=17):
+    g = np.random.default_rng(seed)
+    N, H, W, J = 16, 48, 48, 25
+    O = synth.make_object(H, W, seed, phase_sigma=2.0, amp_sigma=2.0)
+    modes = synth.hg_probe(N, [0.6, 0.2, 0.15, 0.05], waist=3.5, quad_phase=0.02) * 6.0
+    U, P_rest = modes[:3], modes[3:]
+    pos = synth.raster_positions(5, 5, 4.0, (H / 2, W / 2), 0.5, seed)
+    w_true = 1.0 + 0.1 * g.standard_normal((J, 3))
+    I_m = orc.forward_opr(O, U, w_true, P_rest, pos)
+    return O, U, w_true, P_rest, pos, I_m, g
+
+
+def test_lsqml_opr_truth_is_a_fixed_point_and_weights_converge():
+    O, U, w_true, P_rest, pos, I_m, g = _opr_noiseless()
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=5, eps=0.0, delta_o=0.1, delta_p=0.1,
+                            update_object=False, update_probe=False)
+    opr = orc.OprOptions(update_weights=True)
+    order = synth.random_order(pos.shape[0], 3)
+    O1, U1, w1, Pr1, L, _ = orc.lsqml_epoch_opr(O, U, w_true, P_rest, pos, I_m, order, opts, opr)
+    assert L < 1e-20 and np.max(np.abs(w1 - w_true)) < 1e-12 and np.max(np.abs(O1 - O)) == 0.0
+    w = w_true + 0.05 * g.standard_normal(w_true.shape)
+    e0 = np.linalg.norm(w - w_true)
+    for _ in range(12):   # linear convergence, about 0.77 per epoch
+        _, _, w, _, L, _ = orc.lsqml_epoch_opr(O, U, w, P_rest, pos, I_m, order, opts, opr)
+    assert np.linalg.norm(w - w_true) < 0.05 * e0
