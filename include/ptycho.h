@@ -200,6 +200,60 @@ ptycho_status ptycho_lsqml_epoch_static(const ptycho_dims* dims, float* object, 
                                         const ptycho_lsqml_opts* opts, double* loss, double* alpha,
                                         void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Orthogonal probe relaxation (Sec. 2.1: scan-point-specific probes). The
+ * primary probe mode of position j is P_j0 = sum_m w[j][m] U[m] over K
+ * eigenmodes U (complex64 [K, N, N], 1 <= K <= 8) with real weights w
+ * (float32 [J, K]); the other dims->M - 1 modes are shared by all positions
+ * (P_rest, complex64 [M - 1, N, N]; may be NULL when M == 1). dims->M counts
+ * every mode, the primary one included. The per-position kernels synthesise
+ * P_j0 on chip.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t K;              /* eigenmodes, 1..8 */
+  int32_t update_weights; /* 0/1: per-position least-squares weight update */
+  int32_t reserved[2];    /* must be zero */
+  double weight_step;     /* relaxation of the weight update (1 = the full least-squares step) */
+} ptycho_opr_opts;
+
+/* Workspace bytes of the three OPR entry points below (0 if unsupported). */
+size_t ptycho_workspace_bytes_opr(const ptycho_dims* dims, int32_t K, int32_t batch);
+
+/* Forward model with the relaxed primary mode: I_pred[j] = |F(P_j0 S_j(O))|^2
+ * + sum_k |F(P_rest_k S_j(O))|^2. As ptycho_forward otherwise. */
+ptycho_status ptycho_forward_opr(const ptycho_dims* dims, int32_t K, const float* object, const float* U,
+                                 const float* w, const float* P_rest, const float* pos, float* I_pred,
+                                 void* ws, size_t ws_bytes, void* stream);
+
+/* Gradients of the data term through the relaxed model, ACCUMULATED (+=) as
+ * in ptycho_adjoint: g_object [H, W], g_U complex64 [K, N, N]
+ * (sum_j w_jm conj(o_j) times the exit-wave gradient of mode 0), g_w float32
+ * [J, K] (Re<U_m, that product>, may be NULL), g_P_rest [M - 1, N, N] (NULL
+ * when M == 1), g_pos [J, 2] (may be NULL), loss (may be NULL). */
+ptycho_status ptycho_adjoint_opr(const ptycho_dims* dims, int32_t K, const float* object, const float* U,
+                                 const float* w, const float* P_rest, const float* pos, const float* meas,
+                                 int32_t noise, double eps, int32_t batch, float* g_object, float* g_U,
+                                 float* g_w, float* g_P_rest, float* g_pos, double* loss, void* ws,
+                                 size_t ws_bytes, void* stream);
+
+/* One LSQML epoch with the relaxed primary mode. Per minibatch, as
+ * ptycho_lsqml_epoch with these differences: the illumination and the step
+ * sizes use each position's own primary mode; the eigenmodes move with the
+ * probe step, U_m += mean_j(alpha_P,j) dU_m, along
+ *   dU_m = sum_j w_jm conj(o_j) chi_j0 / (D_m + delta_P),
+ *   D_m = sum_j w_jm^2 |o_j|^2, delta_P = delta_p max(sum_j |o_j|^2, D),
+ * whose per-position image sum_m w_jm dU_m is the primary mode's direction in
+ * the step-size system; and, with opr->update_weights, each position's
+ * weights move by weight_step times the least-squares fit (FP64, damped by
+ * lambda_reg tr(A)/K) of chi_j0 with the exit waves U_m o_j, taken with this
+ * minibatch's U and chi. U, w, P_rest and the object are updated in place.
+ * PTYCHO_FLAG_GRAPH is honoured; PTYCHO_FLAG_AUTOTUNE is ignored (default CTA
+ * sizes). */
+ptycho_status ptycho_lsqml_epoch_opr(const ptycho_dims* dims, const ptycho_opr_opts* opr, float* object,
+                                     float* U, float* w, float* P_rest, const float* pos, const float* meas,
+                                     const int32_t* order, const ptycho_lsqml_opts* opts, double* loss,
+                                     double* alpha, void* ws, size_t ws_bytes, void* stream);
+
 /* Synchronises `stream`, returns (and clears) the device-side status recorded
  * in `ws` since the last read: PTYCHO_OK, PTYCHO_ERR_BOUNDS or
  * PTYCHO_ERR_NONFINITE (bounds reported first), or PTYCHO_ERR_CUDA. */

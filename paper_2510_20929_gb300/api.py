@@ -54,6 +54,11 @@ class LsqmlOpts(ctypes.Structure):
                 ("lambda_reg", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
+class OprOpts(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("update_weights", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+                ("weight_step", ctypes.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 _P = ctypes.c_void_p
@@ -70,7 +75,16 @@ def lib() -> ctypes.CDLL:
         L = ctypes.CDLL(LIB_PATH)
         dims_p = ctypes.POINTER(Dims)
         opts_p = ctypes.POINTER(LsqmlOpts)
+        opr_p = ctypes.POINTER(OprOpts)
         sigs = {
+            "ptycho_workspace_bytes_opr": (ctypes.c_size_t, [dims_p, ctypes.c_int32, ctypes.c_int32]),
+            "ptycho_forward_opr": (ctypes.c_int, [dims_p, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P,
+                                                  ctypes.c_size_t, _P]),
+            "ptycho_adjoint_opr": (ctypes.c_int, [dims_p, ctypes.c_int32, _P, _P, _P, _P, _P, _P, ctypes.c_int32,
+                                                  ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P,
+                                                  ctypes.c_size_t, _P]),
+            "ptycho_lsqml_epoch_opr": (ctypes.c_int, [dims_p, opr_p, _P, _P, _P, _P, _P, _P, _P, opts_p, _P, _P,
+                                                      _P, ctypes.c_size_t, _P]),
             "ptycho_workspace_bytes": (ctypes.c_size_t, [dims_p, ctypes.c_int32]),
             "ptycho_host_workspace_bytes": (ctypes.c_size_t, [dims_p, ctypes.c_int32]),
             "ptycho_workspace_init": (ctypes.c_int, [_P, ctypes.c_size_t, _P]),
@@ -173,10 +187,14 @@ class Workspace:
 _ws_cache: dict = {}
 
 
-def workspace(dims: Dims, batch: int, device, host: bool = False) -> Workspace:
-    """A cached workspace large enough for these dimensions and minibatch size."""
-    fn = lib().ptycho_host_workspace_bytes if host else lib().ptycho_workspace_bytes
-    need = fn(ctypes.byref(dims), int(batch))
+def workspace(dims: Dims, batch: int, device, host: bool = False, opr_K: int = 0) -> Workspace:
+    """A cached workspace large enough for these dimensions and minibatch size
+    (and, with opr_K > 0, for the relaxed-probe entry points with K eigenmodes)."""
+    if opr_K > 0:
+        need = lib().ptycho_workspace_bytes_opr(ctypes.byref(dims), int(opr_K), int(batch))
+    else:
+        fn = lib().ptycho_host_workspace_bytes if host else lib().ptycho_workspace_bytes
+        need = fn(ctypes.byref(dims), int(batch))
     if need == 0:
         raise PtychoError(6, "workspace_bytes")
     key = (str(device), host)
@@ -349,3 +367,98 @@ def lsqml_epoch_host(obj, probe, pos, meas, order, opts: LsqmlOpts, device=None)
                                          _P(ws.ptr), ws.nbytes, _stream()), "ptycho_lsqml_epoch_host")
     _check(ws.status(), "ptycho_lsqml_epoch_host")
     return loss.value
+
+
+# ---------------------------------------------------------------------------
+# Orthogonal probe relaxation: primary mode P_j0 = sum_m w[j, m] U[m] over K
+# eigenmodes U complex64 [K, N, N] with real weights w float32 [J, K]; the
+# shared modes P_rest complex64 [M - 1, N, N] (None when there are none).
+# ---------------------------------------------------------------------------
+def _opr_dims(obj, U, w, P_rest, pos) -> Dims:
+    _need(obj, "object", torch.complex64)
+    _need(U, "eigenmodes", torch.complex64, device=obj.device)
+    K, N, N2 = U.shape
+    if N != N2:
+        raise ValueError("eigenmodes must be square")
+    _need(pos, "positions", torch.float32, device=obj.device)
+    J = pos.shape[0]
+    _need(w, "weights", torch.float32, (J, K), device=obj.device)
+    Mr = 0
+    if P_rest is not None:
+        _need(P_rest, "shared modes", torch.complex64, device=obj.device)
+        if tuple(P_rest.shape[1:]) != (N, N):
+            raise ValueError("shared modes must match the eigenmodes' window")
+        Mr = P_rest.shape[0]
+    H, W = obj.shape
+    return Dims(H, W, N, 1 + Mr, J)
+
+
+def forward_opr(obj, U, w, P_rest, pos, *, check: bool = True):
+    """Predicted intensities [J, N, N] with the relaxed primary mode."""
+    d = _opr_dims(obj, U, w, P_rest, pos)
+    I = torch.empty((d.J, d.N, d.N), dtype=torch.float32, device=obj.device)
+    ws = workspace(d, 1, obj.device)
+    _check(lib().ptycho_forward_opr(ctypes.byref(d), U.shape[0], _ptr(obj), _ptr(U), _ptr(w), _ptr(P_rest),
+                                    _ptr(pos), _ptr(I), _P(ws.ptr), ws.nbytes, _stream()), "ptycho_forward_opr")
+    _finish(ws, "ptycho_forward_opr", check)
+    return I
+
+
+def adjoint_opr(obj, U, w, P_rest, pos, meas, noise="gaussian", eps: float = 0.0, batch: int = 256, *,
+                positions_grad: bool = True, weights_grad: bool = True, check: bool = True):
+    """Loss and gradients through the relaxed model: (loss, g_object, g_U, g_w, g_P_rest, g_pos).
+
+    Complex gradients are 2 dL/dz*; g_w = dL/dw (real). ``noise`` as in :func:`adjoint`.
+    """
+    nz = _NOISE[noise] if isinstance(noise, str) else int(noise)
+    d = _opr_dims(obj, U, w, P_rest, pos)
+    K = U.shape[0]
+    _need(meas, "meas", torch.float32, (d.J, d.N, d.N), device=obj.device)
+    B = max(1, min(int(batch), max(d.J, 1)))
+    gO, gU = torch.zeros_like(obj), torch.zeros_like(U)
+    gw = torch.zeros_like(w) if weights_grad else None
+    gP = torch.zeros_like(P_rest) if P_rest is not None else None
+    gr = torch.zeros((d.J, 2), dtype=torch.float32, device=obj.device) if positions_grad else None
+    loss = torch.zeros((), dtype=torch.float64, device=obj.device)
+    ws = workspace(d, B, obj.device, opr_K=K)
+    _check(lib().ptycho_adjoint_opr(ctypes.byref(d), K, _ptr(obj), _ptr(U), _ptr(w), _ptr(P_rest), _ptr(pos),
+                                    _ptr(meas), nz, float(eps), B, _ptr(gO), _ptr(gU), _ptr(gw), _ptr(gP), _ptr(gr),
+                                    _ptr(loss) if nz != VJP else _P(0), _P(ws.ptr), ws.nbytes, _stream()),
+           "ptycho_adjoint_opr")
+    _finish(ws, "ptycho_adjoint_opr", check)
+    return (None if nz == VJP else loss), gO, gU, gw, gP, gr
+
+
+def make_opr_opts(K: int, update_weights: bool = True, weight_step: float = 1.0) -> OprOpts:
+    r = OprOpts()
+    r.K = int(K)
+    r.update_weights = int(bool(update_weights))
+    r.weight_step = float(weight_step)
+    return r
+
+
+def lsqml_epoch_opr(obj, U, w, P_rest, pos, meas, order=None, opts: LsqmlOpts | None = None,
+                    opr: OprOpts | None = None, *, want_alpha: bool = False, check: bool = True, **kw):
+    """One LSQML epoch with the relaxed primary mode; updates obj, U, w, P_rest in place.
+
+    Returns (loss, alpha) as :func:`lsqml_epoch`.
+    """
+    if opts is None:
+        opts = make_opts(**kw)
+    d = _opr_dims(obj, U, w, P_rest, pos)
+    if opr is None:
+        opr = make_opr_opts(U.shape[0])
+    if opr.K != U.shape[0]:
+        raise ValueError("opr.K must equal the number of eigenmodes")
+    _need(meas, "meas", torch.float32, (d.J, d.N, d.N), device=obj.device)
+    if order is not None:
+        _need(order, "order", torch.int32, device=obj.device)
+    loss = torch.zeros((), dtype=torch.float64, device=obj.device)
+    alpha = torch.zeros((d.J, 2), dtype=torch.float64, device=obj.device) if want_alpha else None
+    ws = workspace(d, opts.batch, obj.device, opr_K=opr.K)
+    _check(lib().ptycho_lsqml_epoch_opr(ctypes.byref(d), ctypes.byref(opr), _ptr(obj), _ptr(U), _ptr(w),
+                                        _ptr(P_rest), _ptr(pos), _ptr(meas), _ptr(order), ctypes.byref(opts),
+                                        _ptr(loss), _ptr(alpha), _P(ws.ptr), ws.nbytes, _stream()),
+           "ptycho_lsqml_epoch_opr")
+    _finish(ws, "ptycho_lsqml_epoch_opr", check)
+    return loss, alpha

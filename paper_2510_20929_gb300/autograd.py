@@ -11,6 +11,10 @@
   materialises I.
 * :func:`reconstruct_adam` is the automatic-differentiation reconstructor of
   Sec. 2.2 with torch.optim.Adam on object, probe and positions.
+* :class:`DataTermOPR` is the data term with orthogonal probe relaxation
+  (Sec. 2.1: the primary mode of position j is sum_m w_jm U_m), differentiable
+  in the object, the eigenmodes U, the real weights w, the shared modes and
+  the positions; :func:`reconstruct_adam_opr` runs Adam on all of them.
 
 Both Functions only marshal tensors to the C ABI; every arithmetic step runs
 in the CUDA library.
@@ -54,6 +58,30 @@ class DataTerm(torch.autograd.Function):
                 gr * s if ctx.needs_input_grad[2] else None, None, None, None)
 
 
+class DataTermOPR(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, obj, U, w, P_rest, pos, meas, noise="gaussian", eps=1e-9):
+        c = [t.contiguous() if t is not None else None for t in (obj, U, w, P_rest, pos, meas)]
+        loss, gO, gU, gw, gP, gr = api.adjoint_opr(*c, noise, eps=eps, batch=256)
+        ctx.has_rest = gP is not None
+        ctx.save_for_backward(gO, gU, gw, gr, *([gP] if gP is not None else []))
+        return loss
+
+    @staticmethod
+    def backward(ctx, gL):
+        gO, gU, gw, gr, *rest = ctx.saved_tensors
+        gP = rest[0] if ctx.has_rest else None
+        s = gL.to(torch.float32)
+        need = ctx.needs_input_grad
+        return (gO * s if need[0] else None, gU * s if need[1] else None, gw * s if need[2] else None,
+                gP * s if (need[3] and gP is not None) else None, gr * s if need[4] else None, None, None, None)
+
+
+def data_term_opr(obj, U, w, P_rest, pos, meas, noise="gaussian", eps=1e-9):
+    """Scalar data term with the relaxed primary mode (differentiable in obj, U, w, P_rest, pos)."""
+    return DataTermOPR.apply(obj, U, w, P_rest, pos, meas, noise, eps)
+
+
 def far_field(obj, probe, pos):
     """Predicted intensities, differentiable in object, probe modes and positions."""
     return FarField.apply(obj, probe, pos)
@@ -92,4 +120,34 @@ def reconstruct_adam(obj, probe, pos, meas, epochs=10, lr_object=1e-2, lr_probe=
     obj.requires_grad_(False)
     probe.requires_grad_(False)
     pos.requires_grad_(False)
+    return hist
+
+
+def reconstruct_adam_opr(obj, U, w, P_rest, pos, meas, epochs=10, lr_object=1e-2, lr_probe=1e-2,
+                         lr_weights=1e-2, lr_pos=1e-1, noise="gaussian", eps=1e-9,
+                         update=("object", "eigenmodes", "weights", "probe", "positions")):
+    """Adam with orthogonal probe relaxation; returns the loss history (tensors updated in place).
+
+    "probe" in ``update`` refers to the shared modes P_rest (ignored when None).
+    """
+    groups = [("object", obj, lr_object), ("eigenmodes", U, lr_probe), ("weights", w, lr_weights),
+              ("probe", P_rest, lr_probe), ("positions", pos, lr_pos)]
+    params = []
+    for name, t, lr in groups:
+        if t is None:
+            continue
+        t.requires_grad_(name in update)
+        if name in update:
+            params.append({"params": [t], "lr": lr})
+    opt = torch.optim.Adam(params)
+    hist = []
+    for _ in range(epochs):
+        opt.zero_grad(set_to_none=True)
+        loss = data_term_opr(obj, U, w, P_rest, pos, meas, noise, eps)
+        loss.backward()
+        opt.step()
+        hist.append(loss.item())
+    for _, t, _ in groups:
+        if t is not None:
+            t.requires_grad_(False)
     return hist

@@ -37,12 +37,13 @@ __global__ void k_init_epoch(int NN, int M, const float2* probe, float* Sp, WsHe
 }
 
 // Batch sums per probe pixel, without atomics: for blockIdx.y == 0 the thread
-// (k, q) with k < M sums conj(o_j) chi_jk over the batch (pixel pair q, into
-// dPacc_k, added to its previous value when `accumulate`), and k == M sums
-// |o_j|^2 into Dp and reports max(Dp). Blocks with blockIdx.y == 1 scan the
-// illumination plane for its maximum. U positions are loaded per iteration.
+// (k, q) with k < Mc sums conj(o_j) chi_j,k0+k over the batch (pixel pair q,
+// into dPacc_k, added to its previous value when `accumulate`; each slot holds
+// Ms planes), and k == Mc sums |o_j|^2 into Dp and reports max(Dp). Blocks
+// with blockIdx.y == 1 scan the illumination plane for its maximum. U
+// positions are loaded per iteration.
 template <int U>
-__global__ void k_probe_reduce(int NN, int M, int nb, const float2* __restrict__ h_s,
+__global__ void k_probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* __restrict__ h_s,
                                const float2* __restrict__ o_s, const int* __restrict__ valid, float2* dPacc,
                                int accumulate, float* Dp, const float4* __restrict__ acc, int HW,
                                BatchScalars* sc) {
@@ -60,9 +61,9 @@ __global__ void k_probe_reduce(int NN, int M, int nb, const float2* __restrict__
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = t / NP, q = t % NP;
   float dmax = 0.f;
-  if (k < M && dPacc) {
-    const float4* h = (const float4*)h_s + (size_t)k * NP + q;
-    const size_t stride = (size_t)M * NP;
+  if (k < Mc && dPacc) {
+    const float4* h = (const float4*)h_s + (size_t)(k0 + k) * NP + q;
+    const size_t stride = (size_t)Ms * NP;
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = 0; i < nb; i += U) {
       float4 v[U];
@@ -80,7 +81,7 @@ __global__ void k_probe_reduce(int NN, int M, int nb, const float2* __restrict__
       s.x += o.x; s.y += o.y; s.z += o.z; s.w += o.w;
     }
     *out = s;
-  } else if (k == M && Dp) {
+  } else if (k == Mc && Dp) {
     const float4* o = (const float4*)o_s + q;
     float2 d = make_float2(0.f, 0.f);
     for (int i = 0; i < nb; i += U) {
@@ -124,7 +125,8 @@ __global__ void k_norm_probe(int NN, int M, const float2* dPacc, const float* Dp
   }
 }
 
-// P_k += mean_j(alpha_P) dP_k; refresh Sp = sum_k |P_k|^2; clear the next batch's scalars.
+// P_k += mean_j(alpha_P) dP_k; refresh Sp = sum_k |P_k|^2 (when Sp is set); clear the next
+// batch's scalars.
 __global__ void k_probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
                                const BatchScalars* sc, BatchScalars* sc_next) {
   const float mean_ap = sc->count > 0 ? (float)(sc->sum_alpha_p / (double)sc->count) : 0.f;
@@ -141,7 +143,7 @@ __global__ void k_probe_update(int NN, int M, float2* probe, const float2* dP, f
       }
       s += cabs2(v);
     }
-    Sp[p] = s;
+    if (Sp) Sp[p] = s;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) memset(sc_next, 0, sizeof(BatchScalars));
 }
@@ -151,7 +153,7 @@ __global__ void k_probe_update(int NN, int M, float2* probe, const float2* dP, f
 // ---------------------------------------------------------------------------
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-Layout make_layout(const ptycho_dims& d, int B) {
+Layout make_layout(const ptycho_dims& d, int B, int K) {
   Layout L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -173,6 +175,13 @@ Layout make_layout(const ptycho_dims& d, int B) {
   L.Cp = take(NN * sizeof(float2));
   L.Sdp = take(NN * sizeof(float));
   L.valid = take((size_t)B * sizeof(int));
+  L.p0 = L.dUacc = L.Du = L.dU = 0;
+  if (K > 0) {
+    L.p0 = take((size_t)B * NN * sizeof(float2));
+    L.dUacc = take((size_t)K * NN * sizeof(float2));
+    L.Du = take((size_t)K * NN * sizeof(float));
+    L.dU = take((size_t)K * NN * sizeof(float2));
+  }
   L.total = off;
   return L;
 }
@@ -187,7 +196,7 @@ ptycho_status check_dims(const ptycho_dims* d) {
   return PTYCHO_OK;
 }
 
-static ptycho_status check_ws(void* ws, size_t have, size_t need) {
+ptycho_status check_ws(void* ws, size_t have, size_t need) {
   if (!ws || ((uintptr_t)ws & 255) != 0 || have < need) return PTYCHO_ERR_WORKSPACE;
   return PTYCHO_OK;
 }
@@ -214,12 +223,12 @@ static cudaError_t timed(int id, cudaStream_t s, F&& launch) {
   return e;
 }
 
-static cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s, int variant = 0) {
+cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s, int variant) {
   return timed(K_PASS1, s, [&] {
     return dispatch_N(N, [&](auto c) { return launch_pass1<decltype(c)::value>(a, s, variant); });
   });
 }
-static cudaError_t pass2(int N, const Pass2Args& a, cudaStream_t s, int variant = 0) {
+cudaError_t pass2(int N, const Pass2Args& a, cudaStream_t s, int variant) {
   return timed(K_PASS2, s, [&] {
     return dispatch_N(N, [&](auto c) { return launch_pass2<decltype(c)::value>(a, s, variant); });
   });
@@ -283,35 +292,53 @@ static float time_launch(cudaStream_t s, int reps, F&& launch) {
   return ms;
 }
 
-static cudaError_t probe_reduce(int NN, int M, int nb, const float2* h_s, const float2* o_s, const int* valid,
-                                float2* dPacc, int accumulate, float* Dp, const float4* acc, int HW,
-                                BatchScalars* sc, cudaStream_t s) {
+cudaError_t probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* h_s, const float2* o_s,
+                         const int* valid, float2* dPacc, int accumulate, float* Dp, const float4* acc, int HW,
+                         BatchScalars* sc, cudaStream_t s) {
   cudaEvent_t e0 = profile_begin(K_PROBE_REDUCE, s);
   const int NP = NN / 2;
-  const int threads = (dPacc ? M * NP : 0) + (Dp ? NP : 0);
+  const int threads = (dPacc ? Mc * NP : 0) + (Dp ? NP : 0);
   int bx = (threads + 255) / 256;
   if (acc && bx < 2 * 152) bx = 2 * 152;
   dim3 grid(bx > 0 ? bx : 1, acc ? 2 : 1);
-  k_probe_reduce<16><<<grid, 256, 0, s>>>(NN, M, nb, h_s, o_s, valid, dPacc, accumulate, Dp, acc, HW, sc);
+  k_probe_reduce<16><<<grid, 256, 0, s>>>(NN, k0, Mc, Ms, nb, h_s, o_s, valid, dPacc, accumulate, Dp, acc, HW,
+                                          sc);
   profile_end(K_PROBE_REDUCE, e0, s);
   return cudaGetLastError();
 }
 
-static int grid_for(size_t n, int threads, int cap) {
+int grid_for(size_t n, int threads, int cap) {
   size_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
   return (int)(b > (size_t)cap ? cap : b);
 }
 
-struct Ptrs {
-  WsHeader* hdr;
-  float4* acc;
-  float2 *psi, *o, *g, *h, *dPacc, *dP, *Cp;
-  float *Dp, *Sp, *Sdp;
-  int* valid;
-};
+cudaError_t norm_probe(int NN, int M, const float2* dPacc, const float* Dp, const float2* probe, float delta_p,
+                       int update_probe, const BatchScalars* sc, float2* dP, float2* Cp, float* Sdp,
+                       cudaStream_t s) {
+  return timed(K_NORM_PROBE, s, [&] {
+    k_norm_probe<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, dPacc, Dp, probe, delta_p, update_probe, sc, dP, Cp,
+                                                        Sdp);
+    return cudaGetLastError();
+  });
+}
 
-static Ptrs carve(void* ws, const Layout& L) {
+cudaError_t probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
+                         const BatchScalars* sc, BatchScalars* sc_next, cudaStream_t s) {
+  return timed(K_UPDATE, s, [&] {
+    k_probe_update<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, probe, dP, Sp, update_probe, sc, sc_next);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t init_epoch(int NN, int M, const float2* probe, float* Sp, WsHeader* hdr, cudaStream_t s) {
+  return timed(K_INIT, s, [&] {
+    k_init_epoch<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, probe, Sp, hdr);
+    return cudaGetLastError();
+  });
+}
+
+Ptrs carve(void* ws, const Layout& L) {
   char* b = (char*)ws;
   Ptrs p;
   p.hdr = (WsHeader*)(b + L.hdr);
@@ -327,10 +354,14 @@ static Ptrs carve(void* ws, const Layout& L) {
   p.Cp = (float2*)(b + L.Cp);
   p.Sdp = (float*)(b + L.Sdp);
   p.valid = (int*)(b + L.valid);
+  p.p0 = L.p0 ? (float2*)(b + L.p0) : nullptr;
+  p.dUacc = L.dUacc ? (float2*)(b + L.dUacc) : nullptr;
+  p.Du = L.Du ? (float*)(b + L.Du) : nullptr;
+  p.dU = L.dU ? (float2*)(b + L.dU) : nullptr;
   return p;
 }
 
-static ptycho_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PTYCHO_OK : PTYCHO_ERR_CUDA; }
+ptycho_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PTYCHO_OK : PTYCHO_ERR_CUDA; }
 
 // Times both CTA-size variants of k_pass1 and k_pass2 on the epoch's first
 // minibatch, without side effects on the caller's data: the loss is not
@@ -357,11 +388,12 @@ static ptycho_status autotune(const ptycho_dims& d, float2* obj, float2* probe, 
   // one clean pass 1 with the chosen variant feeds the pass-2 candidates
   if (cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
   if (pass1(N, a, s, t->v1) != cudaSuccess) return PTYCHO_ERR_CUDA;
-  if (probe_reduce(NN, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
+  if (probe_reduce(NN, 0, M, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
                    o.update_probe ? w.Dp : nullptr, w.acc, HW, sc, s) != cudaSuccess)
     return PTYCHO_ERR_CUDA;
-  k_norm_probe<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p,
-                                                      o.update_probe, sc, w.dP, w.Cp, w.Sdp);
+  if (norm_probe(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p, o.update_probe, sc, w.dP, w.Cp, w.Sdp, s) !=
+      cudaSuccess)
+    return PTYCHO_ERR_CUDA;
   t->v2 = 0;
   t->ms2[0] = t->ms2[1] = 0.f;
   if (L.o - L.psi >= (size_t)HW * sizeof(float2) && o.update_object) {
@@ -380,8 +412,7 @@ static ptycho_status autotune(const ptycho_dims& d, float2* obj, float2* probe, 
   }
   // restore the epoch's starting state of the accumulators and scalars
   if (cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
-  k_init_epoch<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, probe, w.Sp, w.hdr);
-  return cudaGetLastError() == cudaSuccess ? PTYCHO_OK : PTYCHO_ERR_CUDA;
+  return init_epoch(NN, M, probe, w.Sp, w.hdr, s) == cudaSuccess ? PTYCHO_OK : PTYCHO_ERR_CUDA;
 }
 
 ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const float* pos,
@@ -393,11 +424,7 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const 
   cudaError_t e = cudaSuccess;
   if (loss && (e = cudaMemsetAsync(loss, 0, sizeof(double), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
   if ((e = cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
-  timed(K_INIT, s, [&] {
-    k_init_epoch<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, probe, w.Sp, w.hdr);
-    return cudaSuccess;
-  });
-  if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  if ((e = init_epoch(NN, M, probe, w.Sp, w.hdr, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
   int dev = 0;
   cudaGetDevice(&dev);
   TuneEntry tune{{dev, N, M, d.H, d.W, B}, 0, 0, {0.f, 0.f}, {0.f, 0.f}};
@@ -425,14 +452,12 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const 
     a.Sp = w.Sp; a.acc = w.acc;
     a.loss = loss; a.status = &w.hdr->status;
     if ((e = pass1(N, a, s, tune.v1)) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    if ((e = probe_reduce(NN, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
+    if ((e = probe_reduce(NN, 0, M, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
                           o.update_probe ? w.Dp : nullptr, w.acc, HW, sc, s)) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
-    timed(K_NORM_PROBE, s, [&] {
-      k_norm_probe<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p,
-                                                          o.update_probe, sc, w.dP, w.Cp, w.Sdp);
-      return cudaSuccess;
-    });
+    if ((e = norm_probe(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p, o.update_probe, sc, w.dP, w.Cp, w.Sdp,
+                        s)) != cudaSuccess)
+      return PTYCHO_ERR_CUDA;
     Pass2Args q;
     memset(&q, 0, sizeof(q));
     q.H = d.H; q.W = d.W; q.M = M; q.J = d.J;
@@ -444,12 +469,8 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const 
     q.update_object = o.update_object; q.update_probe = o.update_probe;
     if ((e = pass2(N, q, s, tune.v2)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if ((e = cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    timed(K_UPDATE, s, [&] {
-      k_probe_update<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, probe, w.dP, w.Sp, o.update_probe, sc,
-                                                            sc_next);
-      return cudaSuccess;
-    });
-    if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if ((e = probe_update(NN, M, probe, w.dP, w.Sp, o.update_probe, sc, sc_next, s)) != cudaSuccess)
+      return PTYCHO_ERR_CUDA;
   }
   return PTYCHO_OK;
 }
@@ -558,8 +579,8 @@ ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const
     a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
     a.gobj = (float2*)g_object; a.gpos = g_pos; a.loss = loss; a.status = &w.hdr->status;
     if (pass1(dims->N, a, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    if (probe_reduce(NN, dims->M, nb, w.h, w.o, w.valid, (float2*)g_probe, 1, nullptr, nullptr, 0, nullptr,
-                     s) != cudaSuccess)
+    if (probe_reduce(NN, 0, dims->M, dims->M, nb, w.h, w.o, w.valid, (float2*)g_probe, 1, nullptr, nullptr, 0,
+                     nullptr, s) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
   }
   return PTYCHO_OK;

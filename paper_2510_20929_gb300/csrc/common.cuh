@@ -64,6 +64,13 @@ struct BatchArgs {
   float* gpos;         // [J, 2] position gradient or null
   double* loss;        // scalar accumulator or null
   int* status;
+  // Orthogonal probe relaxation: when opr_U is set, the primary mode of
+  // position j is sum_m opr_w[j][m] opr_U[m] and `probe` holds the M - 1
+  // shared modes; p0_s receives the synthesised primary mode per slot.
+  const float2* opr_U; // [K, N, N] or null
+  const float* opr_w;  // [J, K]
+  int K;
+  float2* p0_s;        // [B, N, N] (null in the forward mode)
 };
 
 struct Pass2Args {
@@ -86,7 +93,44 @@ struct Pass2Args {
   float delta_o;       // relative preconditioner damping
   double lam;
   int update_object, update_probe;
+  // Orthogonal probe relaxation (Cp, Sp, Sdp, dP then cover the shared modes)
+  const float2* opr_dU; // [K, N, N] eigenmode directions, or null
+  const float* opr_w;   // [J, K]
+  int K;
+  const float2* p0_s;   // [B, N, N] primary mode of each slot
 };
+
+constexpr int OPR_KMAX = 8;   // eigenmodes of the relaxed primary probe mode
+
+// Shared probe mode k, or null for the synthesised primary mode (OPR).
+template <bool OPR>
+__device__ __forceinline__ const float2* shared_mode(const BatchArgs& a, int k, int NN) {
+  if (OPR) return k == 0 ? nullptr : a.probe + (size_t)(k - 1) * NN;
+  return a.probe + (size_t)k * NN;
+}
+
+// sum_m wj[m] V_m at the pixel pair starting at p (V: [K, N, N], 16-byte pairs).
+__device__ __forceinline__ float4 opr_pair(const float2* __restrict__ V, const float* wj, int K, int NN, int p) {
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+  for (int m = 0; m < K; ++m) {
+    const float4 u = __ldg((const float4*)(V + (size_t)m * NN + p));
+    const float w = wj[m];
+    s.x = fmaf(w, u.x, s.x); s.y = fmaf(w, u.y, s.y); s.z = fmaf(w, u.z, s.z); s.w = fmaf(w, u.w, s.w);
+  }
+  return s;
+}
+
+// sum_m wj[m] V_m at one pixel.
+__device__ __forceinline__ float2 opr_pixel(const float2* __restrict__ V, const float* wj, int K, int NN, int p) {
+  float2 s = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int m = 0; m < K; ++m) {
+    const float2 u = __ldg(V + (size_t)m * NN + p);
+    s.x = fmaf(wj[m], u.x, s.x); s.y = fmaf(wj[m], u.y, s.y);
+  }
+  return s;
+}
 
 // Tile origin and fraction of a probe-centre position; false if the bilinear
 // (N+1)^2 tile is not inside the object or the value is not finite.

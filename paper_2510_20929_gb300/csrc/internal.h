@@ -11,13 +11,50 @@
 namespace ptycho {
 
 struct Layout {
-  size_t hdr, acc, psi, o, g, h, dPacc, Dp, dP, Sp, Cp, Sdp, valid, total;
+  size_t hdr, acc, psi, o, g, h, dPacc, Dp, dP, Sp, Cp, Sdp, valid;
+  size_t p0, dUacc, Du, dU;   // orthogonal probe relaxation (K > 0) only
+  size_t total;
+};
+
+// Device pointers of the workspace regions.
+struct Ptrs {
+  struct WsHeader* hdr;
+  float4* acc;
+  float2 *psi, *o, *g, *h, *dPacc, *dP, *Cp;
+  float *Dp, *Sp, *Sdp;
+  int* valid;
+  float2 *p0, *dUacc, *dU;
+  float* Du;
 };
 
 size_t align256(size_t b);
-Layout make_layout(const ptycho_dims& d, int B);
+// Workspace regions for a minibatch of B positions; K > 0 adds the regions of
+// the relaxed primary probe mode with K eigenmodes.
+Layout make_layout(const ptycho_dims& d, int B, int K = 0);
+Ptrs carve(void* ws, const Layout& L);
 ptycho_status check_dims(const ptycho_dims* d);
 ptycho_status check_opts(const ptycho_lsqml_opts* o);
+ptycho_status check_ws(void* ws, size_t have, size_t need);
+ptycho_status cuda_status(cudaError_t e);
+int grid_for(size_t n, int threads, int cap);
+
+struct BatchArgs;
+struct Pass2Args;
+struct BatchScalars;
+// Launch wrappers (profiled) shared by the entry points.
+cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s, int variant = 0);
+cudaError_t pass2(int N, const Pass2Args& a, cudaStream_t s, int variant = 0);
+// Batch sums of h over the Mc modes starting at plane k0 of each slot (slots
+// hold Ms planes), Dp = sum |o|^2 and the illumination maximum.
+cudaError_t probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* h_s, const float2* o_s,
+                         const int* valid, float2* dPacc, int accumulate, float* Dp, const float4* acc, int HW,
+                         BatchScalars* sc, cudaStream_t s);
+cudaError_t norm_probe(int NN, int M, const float2* dPacc, const float* Dp, const float2* probe, float delta_p,
+                       int update_probe, const BatchScalars* sc, float2* dP, float2* Cp, float* Sdp,
+                       cudaStream_t s);
+cudaError_t probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
+                         const BatchScalars* sc, BatchScalars* sc_next, cudaStream_t s);
+cudaError_t init_epoch(int NN, int M, const float2* probe, float* Sp, struct WsHeader* hdr, cudaStream_t s);
 // One LSQML epoch on stream s with workspace ws (arguments already validated).
 ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const float* pos, const float* meas,
                         const int32_t* order, const ptycho_lsqml_opts& o, double* loss, double* alpha, void* ws,

@@ -134,7 +134,9 @@ __device__ __forceinline__ void bilinear_scatter(float fy, float fx, Load&& load
   }
 }
 
-template <int N, int T>
+// OPR: the primary probe mode is synthesised per position (a separate
+// instantiation, so that the shared-probe kernel carries none of it).
+template <int N, int T, bool OPR>
 __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
   using F = Fft2<N>;
   using SM = Pass1Smem<N>;
@@ -166,13 +168,19 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
   const int M = a.M;
   const float invN = 1.0f / (float)N;
   const size_t slotNN = (size_t)slot * NN;
+  float* wj = (float*)(red + 128);   // this position's eigenmode weights (OPR)
+  float2* p0 = (OPR && a.p0_s) ? a.p0_s + slotNN : nullptr;
+  if (OPR) {
+    if (tid < a.K) wj[tid] = a.opr_w[(size_t)j * a.K + tid];
+    __syncthreads();
+  }
   float2* psi_s = a.psi_s ? a.psi_s + slotNN * M : nullptr;
   float2* o_s = a.o_s ? a.o_s + slotNN : nullptr;
 
   // ---- forward model: I_j = sum_k |F(P_k o_j)|^2 -------------------------------
 #pragma unroll 1
   for (int k = 0; k < M; ++k) {
-    const float2* Pk = a.probe + (size_t)k * NN;
+    const float2* Pk = shared_mode<OPR>(a, k, NN);
     // psi_k = P_k o_j into the tile, two adjacent pixels per thread and iteration
     const NatPairs<N, T> np;
 #pragma unroll 4
@@ -187,7 +195,13 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
         o0 = make_float2(o2.x, o2.y);
         o1 = make_float2(o2.z, o2.w);
       }
-      const float4 P2 = __ldg((const float4*)(Pk + p));
+      float4 P2;
+      if (!OPR || Pk) {
+        P2 = __ldg((const float4*)(Pk + p));
+      } else {   // relaxed primary mode of this position
+        P2 = opr_pair(a.opr_U, wj, a.K, NN, p);
+        if (p0) *(float4*)(p0 + p) = P2;
+      }
       store_pair(tile, np.phys(q), cmul(make_float2(P2.x, P2.y), o0), cmul(make_float2(P2.z, P2.w), o1));
     }
     __syncthreads();
@@ -275,7 +289,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
   float2* h_s = a.h_s + slotNN * M;
 #pragma unroll 1
   for (int k = 0; k < M; ++k) {
-    const float2* Pk = a.probe + (size_t)k * NN;
+    const float2* Pk = shared_mode<OPR>(a, k, NN);
     __syncthreads();
     fft2_inverse<N, T>(
         tile, tw,
@@ -306,7 +320,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
       const int p = np.pix(q);
       float2 x0, x1;
       load_pair(tile, np.phys(q), x0, x1);
-      const float4 P2 = __ldg((const float4*)(Pk + p));
+      const float4 P2 = (!OPR || Pk) ? __ldg((const float4*)(Pk + p)) : *(const float4*)(p0 + p);
       const float4 o2 = *(const float4*)(o_s + p);
       const float2 g0 = cmulc(make_float2(P2.x, P2.y), x0), g1 = cmulc(make_float2(P2.z, P2.w), x1);
       float4 gv = make_float4(g0.x, g0.y, g1.x, g1.y);
@@ -337,7 +351,8 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
         fy, fx,
         [&](int y, int x) {
           const float2 g = tile[tix<N>(y, x)];
-          return make_float4(g.x, g.y, __ldg(a.Sp + y * N + x), 0.f);
+          const float sp = __ldg(a.Sp + y * N + x) + ((OPR && p0) ? cabs2(p0[y * N + x]) : 0.f);
+          return make_float4(g.x, g.y, sp, 0.f);
         },
         [&](int y, int x, float4 v) {
           atomicAdd(a.acc + (size_t)(ty + y) * a.W + (tx + x), make_float4(v.x, v.y, v.z, 0.f));
@@ -391,7 +406,7 @@ __device__ __forceinline__ float2 dohat(const float4* q, int W, float w00, float
                      q00.y * i00 + q01.y * i01 + q10.y * i10 + q11.y * i11);
 }
 
-template <int N, int T>
+template <int N, int T, bool OPR>
 __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
   constexpr int NN = N * N;
   __shared__ double red[32 * 5];
@@ -410,6 +425,15 @@ __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
   const float2* g_s = a.g_s + slotNN;
   const float2* o_s = a.o_s + slotNN;
   const float2* h_s = a.h_s + slotNN * M;
+  // OPR: the primary mode P_j0 and its direction sum_m w_jm dU_m differ per
+  // position; Sp, Cp, Sdp and dP then hold the shared modes only
+  constexpr bool opr = OPR;
+  __shared__ float wsh[OPR_KMAX];
+  if (opr) {
+    if (tid < a.K) wsh[tid] = a.opr_w[(size_t)j * a.K + tid];
+    __syncthreads();
+  }
+  const float2* p0 = opr ? a.p0_s + slotNN : nullptr;
 
   float A11 = 0.f, A12 = 0.f, A22 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll 1
@@ -419,18 +443,31 @@ __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
     const float2 o = __ldcs(o_s + p);
     float2 d = make_float2(0.f, 0.f);
     if (a.update_object) d = dohat(a.acc + (size_t)(ty + r) * a.W + (tx + c), a.W, w00, w01, w10, w11, damp);
-    A11 += cabs2(d) * __ldg(a.Sp + p);
+    float sp = __ldg(a.Sp + p), sdp = __ldg(a.Sdp + p);
+    float2 cp = __ldg(a.Cp + p);
+    if (opr) {
+      const float2 P0 = p0[p];
+      sp += cabs2(P0);
+      if (a.update_probe) {
+        const float2 d0 = opr_pixel(a.opr_dU, wsh, a.K, NN, p);
+        cp = cadd(cp, cmulc(P0, d0));
+        sdp += cabs2(d0);
+        const float2 h0 = __ldcs(h_s + p);
+        b2 += d0.x * h0.x + d0.y * h0.y;     // Re(conj(dP_j0) h_j0)
+      }
+    }
+    A11 += cabs2(d) * sp;
     const float2 od = cmulc(d, o);           // conj(d) o
-    const float2 cp = __ldg(a.Cp + p);
     A12 += od.x * cp.x - od.y * cp.y;        // Re(conj(d) o Cp)
-    A22 += cabs2(o) * __ldg(a.Sdp + p);
+    A22 += cabs2(o) * sdp;
     b1 += d.x * g.x + d.y * g.y;             // Re(conj(d) g)
   }
   if (a.update_probe) {
-    // b2 = Re sum_k <dP_k, h_k>: the M planes are contiguous, two pixels per 16-byte load
-    const float4* h4 = (const float4*)h_s;
+    // b2 = Re sum_k <dP_k, h_k> over the shared modes: their planes are
+    // contiguous, two pixels per 16-byte load
+    const float4* h4 = (const float4*)(h_s + (opr ? NN : 0));
     const float4* d4 = (const float4*)a.dP;
-    const int Q = M * NN / 2;
+    const int Q = (opr ? M - 1 : M) * NN / 2;
     int q = tid;
     for (; q + 3 * T < Q; q += 4 * T) {      // four independent 16-byte streams per thread
       float4 dp[4], h[4];
@@ -511,28 +548,32 @@ cudaError_t smem_optin(K kernel, size_t bytes, unsigned long long* done_mask) {
   return e;
 }
 
-template <int N, int T>
+template <int N, int T, bool OPR>
 cudaError_t launch_pass1_t(const BatchArgs& a, cudaStream_t s) {
   constexpr size_t sm = Pass1Smem<N>::bytes;
   static unsigned long long done = 0;
-  cudaError_t e = smem_optin(k_pass1<N, T>, sm, &done);
+  cudaError_t e = smem_optin(k_pass1<N, T, OPR>, sm, &done);
   if (e != cudaSuccess) return e;
   if (a.nb <= 0) return cudaSuccess;
-  k_pass1<N, T><<<a.nb, T, sm, s>>>(a);
+  k_pass1<N, T, OPR><<<a.nb, T, sm, s>>>(a);
   return cudaGetLastError();
 }
 
-// variant 0: default CTA size, 1: the alternative
+// variant 0: default CTA size, 1: the alternative (the relaxed-probe form has
+// the default only)
 template <int N>
 cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s, int variant) {
-  return variant == 1 ? launch_pass1_t<N, Threads<N>::ALT>(a, s) : launch_pass1_t<N, Threads<N>::T>(a, s);
+  if (a.opr_U) return launch_pass1_t<N, Threads<N>::T, true>(a, s);
+  return variant == 1 ? launch_pass1_t<N, Threads<N>::ALT, false>(a, s)
+                      : launch_pass1_t<N, Threads<N>::T, false>(a, s);
 }
 
 template <int N>
 cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s, int variant) {
   if (a.nb <= 0) return cudaSuccess;
-  if (variant == 1) k_pass2<N, PASS2_ALT><<<a.nb, PASS2_ALT, 0, s>>>(a);
-  else k_pass2<N, PASS2_T><<<a.nb, PASS2_T, 0, s>>>(a);
+  if (a.opr_dU) k_pass2<N, PASS2_T, true><<<a.nb, PASS2_T, 0, s>>>(a);
+  else if (variant == 1) k_pass2<N, PASS2_ALT, false><<<a.nb, PASS2_ALT, 0, s>>>(a);
+  else k_pass2<N, PASS2_T, false><<<a.nb, PASS2_T, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -212,7 +212,7 @@ __device__ __forceinline__ void inv2d(cg::cluster_group& cluster, float2* tile, 
   __syncthreads();
 }
 
-template <class C>
+template <class C, bool OPR>
 __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
   constexpr int N = C::N, Q = C::Q, T = C::T, LR = C::LR, NN = C::NN, LNN = C::LNN;
   constexpr int NAT_STEPS = C::NAT_STEPS;
@@ -261,6 +261,12 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
   const int M = a.M;
   const float invN = 1.0f / (float)N;
   const size_t slotNN = (size_t)slot * NN;
+  float* wj = (float*)(red + 128);   // this position's eigenmode weights (OPR)
+  float2* p0 = (OPR && a.p0_s) ? a.p0_s + slotNN : nullptr;
+  if (OPR) {
+    if (tid < a.K) wj[tid] = a.opr_w[(size_t)j * a.K + tid];
+    __syncthreads();
+  }
   float2* psi_s = a.psi_s ? a.psi_s + slotNN * M : nullptr;
   float2* o_s = a.o_s ? a.o_s + slotNN : nullptr;
   const int rowbase = LR * q;   // first spatial row of this CTA
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
   // ---- forward model --------------------------------------------------------------
 #pragma unroll 1
   for (int k = 0; k < M; ++k) {
-    const float2* Pk = a.probe + (size_t)k * NN;
+    const float2* Pk = shared_mode<OPR>(a, k, NN);
     __syncthreads();
 #pragma unroll 2
     for (int s = 0; s < NAT_STEPS; ++s) {
@@ -283,7 +289,13 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
         o0 = make_float2(o2.x, o2.y);
         o1 = make_float2(o2.z, o2.w);
       }
-      const float4 P2 = __ldg((const float4*)(Pk + p));
+      float4 P2;
+      if (!OPR || Pk) {
+        P2 = __ldg((const float4*)(Pk + p));
+      } else {   // relaxed primary mode of this position
+        P2 = opr_pair(a.opr_U, wj, a.K, NN, p);
+        if (p0) *(float4*)(p0 + p) = P2;
+      }
       store_pair(tile, C::tix(r, c), cmul(make_float2(P2.x, P2.y), o0), cmul(make_float2(P2.z, P2.w), o1));
     }
     __syncthreads();
@@ -358,7 +370,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
   float2* h_s = a.h_s + slotNN * M;
 #pragma unroll 1
   for (int k = 0; k < M; ++k) {
-    const float2* Pk = a.probe + (size_t)k * NN;
+    const float2* Pk = shared_mode<OPR>(a, k, NN);
     __syncthreads();
 #pragma unroll 2
     for (int s = 0; s < NAT_STEPS; ++s) {
@@ -375,7 +387,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
       const int p = (rowbase + r) * N + c;
       float2 x0, x1;
       load_pair(tile, C::tix(r, c), x0, x1);
-      const float4 P2 = __ldg((const float4*)(Pk + p));
+      const float4 P2 = (!OPR || Pk) ? __ldg((const float4*)(Pk + p)) : *(const float4*)(p0 + p);
       const float4 o2 = *(const float4*)(o_s + p);
       const float2 g0 = cmulc(make_float2(P2.x, P2.y), x0), g1 = cmulc(make_float2(P2.z, P2.w), x1);
       float4 gv = make_float4(g0.x, g0.y, g1.x, g1.y);
@@ -399,7 +411,8 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
     const float gx = 1.f - fx, gy = 1.f - fy;
     auto loadg = [&](int y, int x) {
       const float2 g = g_s[y * N + x];
-      return make_float4(g.x, g.y, lsqml ? __ldg(a.Sp + y * N + x) : 0.f, 0.f);
+      const float sp = lsqml ? __ldg(a.Sp + y * N + x) + ((OPR && p0) ? cabs2(p0[y * N + x]) : 0.f) : 0.f;
+      return make_float4(g.x, g.y, sp, 0.f);
     };
     auto hrow = [&](int y, int x) {
       float4 h = make_float4(0.f, 0.f, 0.f, 0.f);

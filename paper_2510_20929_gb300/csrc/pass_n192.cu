@@ -5,9 +5,9 @@
 
 namespace ptycho {
 
-template <class C>
+template <class C, bool OPR>
 static cudaError_t launch_cluster(const BatchArgs& a, cudaStream_t s, unsigned long long* done) {
-  cudaError_t e = smem_optin(cl::k_pass1_cluster<C>, C::Smem::bytes, done);
+  cudaError_t e = smem_optin(cl::k_pass1_cluster<C, OPR>, C::Smem::bytes, done);
   if (e != cudaSuccess) return e;
   if (a.nb <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
@@ -22,13 +22,14 @@ static cudaError_t launch_cluster(const BatchArgs& a, cudaStream_t s, unsigned l
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, cl::k_pass1_cluster<C>, a);
+  return cudaLaunchKernelEx(&cfg, cl::k_pass1_cluster<C, OPR>, a);
 }
 
 template <>
 cudaError_t launch_pass1<192>(const BatchArgs& a, cudaStream_t s, int) {
-  static unsigned long long done = 0;
-  return launch_cluster<cl::Cfg192>(a, s, &done);
+  static unsigned long long done = 0, done_opr = 0;
+  if (a.opr_U) return launch_cluster<cl::Cfg192, true>(a, s, &done_opr);
+  return launch_cluster<cl::Cfg192, false>(a, s, &done);
 }
 
 template cudaError_t launch_pass2<192>(const Pass2Args&, cudaStream_t, int);

@@ -45,8 +45,8 @@ void drain_locked() {
 }  // namespace
 
 const char* kernel_name(int id) {
-  static const char* names[K_COUNT] = {"k_pass1",      "k_pass2",        "k_probe_reduce",
-                                       "k_norm_probe", "k_probe_update", "k_init_epoch"};
+  static const char* names[K_COUNT] = {"k_pass1",      "k_pass2",        "k_probe_reduce", "k_norm_probe",
+                                       "k_probe_update", "k_init_epoch", "k_opr_reduce",   "k_opr_weights"};
   return (id >= 0 && id < K_COUNT) ? names[id] : "?";
 }
 

@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 
 namespace ptycho {
-enum KernelId : int { K_PASS1 = 0, K_PASS2, K_PROBE_REDUCE, K_NORM_PROBE, K_UPDATE, K_INIT, K_COUNT };
+enum KernelId : int {
+  K_PASS1 = 0, K_PASS2, K_PROBE_REDUCE, K_NORM_PROBE, K_UPDATE, K_INIT, K_OPR_REDUCE, K_OPR_WEIGHTS, K_COUNT
+};
 const char* kernel_name(int id);
 bool profiling_on();
 // Returns an event to record before the launch (or null when profiling is off).

@@ -44,3 +44,27 @@ def f32pos(pos):
 def c64(x):
     """Round a complex array to complex64 and back (the inputs both sides see)."""
     return np.asarray(x, np.complex64).astype(np.complex128)
+
+
+def opr_problem(N=16, K=3, M=2, H=40, W=44, J=12, seed=7, step=4.0, counts=2e4, perturb=0.15, w_perturb=0.05,
+                noisy=True):
+    """Relaxed-probe problem: K eigenmodes and M - 1 shared modes (Hermite-Gaussian
+    modes of one probe), true weights drawn from N(1, 0.1), Poisson-noised
+    intensities from the oracle's relaxed forward model, and a start with a
+    perturbed object and perturbed weights."""
+    w = synth.workload_small(N=N, M=K + M - 1, H=H, W=W, J=J, seed=seed, step=step)
+    O_true, modes, pos = w["object"], w["probe"], w["pos"]
+    if K + M - 1 == 1:
+        modes = modes[None] if modes.ndim == 2 else modes
+    g = np.random.default_rng(seed + 21)
+    w_true = 1.0 + 0.1 * g.standard_normal((J, K))
+    U, P_rest = modes[:K], (modes[K:] if M > 1 else None)
+    I0 = orc.forward_opr(O_true, U, w_true, P_rest, pos)
+    s = math.sqrt(counts / I0.sum(axis=(1, 2)).mean())
+    U = U * s
+    P_rest = P_rest * s if P_rest is not None else None
+    I_true = I0 * s * s
+    I_m = synth.poisson_counts(I_true, seed + 11) if noisy else I_true
+    O = O_true * (1 + perturb * (g.standard_normal(O_true.shape) + 1j * g.standard_normal(O_true.shape)))
+    w0 = w_true + w_perturb * g.standard_normal(w_true.shape)
+    return dict(O_true=O_true, O=O, U=U, w=w0, w_true=w_true, P_rest=P_rest, pos=pos, I_m=I_m)
