@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["spiral128", "raster64", "uneven16", "spiral256"], default="spiral128")
+    ap.add_argument("--workload", choices=["spiral128", "raster64", "uneven16", "uneven16opr", "spiral256"], default="spiral128")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--positions", type=int, default=0,
@@ -365,28 +365,41 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(out), flush=True)
 
 
-def run_uneven(args, rank, world, local_rank):
+def run_uneven(args, rank, world, local_rank, opr_K=0):
     """Batched serving of 16 uneven reconstructions (windows 64/128/192/256, J ~ U[500, 20000]):
     one epoch of every reconstruction per step, batched (with and without graph
-    replay) against the same reconstructions run one after the other."""
+    replay) against the same reconstructions run one after the other. With
+    opr_K > 0 every reconstruction relaxes its primary probe mode over opr_K
+    eigenmodes (orthogonal probe relaxation, true weights N(1, 0.1), the
+    reconstruction starting from unit weights) and the step also updates the
+    eigenmodes and the weights."""
     import torch
     from paper_2510_20929_gb300 import api, synth
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    ws = synth.workload_uneven(16, seed=1005 + rank)
+    ws = synth.workload_uneven(16, seed=1005 + rank, opr_K=opr_K)
     recons, opts = [], []
     gen = torch.Generator(device=dev)
     gen.manual_seed(77 + rank)
     for w in ws:
         Ot = torch.tensor(w["object"], dtype=torch.complex64, device=dev)
-        P = torch.tensor(w["probe"], dtype=torch.complex64, device=dev)
         pos = torch.tensor(w["pos"], dtype=torch.float32, device=dev)
-        I0 = api.forward(Ot, P, pos)
-        scale = w["total_counts"] / I0.sum().item()
-        P *= math.sqrt(scale)
-        meas = torch.poisson(I0 * scale, generator=gen)
         order = torch.tensor(synth.random_order(w["J"], 3), dtype=torch.int32, device=dev)
-        recons.append([torch.ones_like(Ot), P, pos, meas, order])
+        if opr_K:
+            U = torch.tensor(w["opr_U"], dtype=torch.complex64, device=dev)
+            wt = torch.tensor(w["opr_w"], dtype=torch.float32, device=dev)
+            I0 = api.forward_opr(Ot, U, wt, None, pos)
+            scale = w["total_counts"] / I0.sum().item()
+            U *= math.sqrt(scale)
+            meas = torch.poisson(I0 * scale, generator=gen)
+            recons.append([torch.ones_like(Ot), U, torch.ones_like(wt), None, pos, meas, order])
+        else:
+            P = torch.tensor(w["probe"], dtype=torch.complex64, device=dev)
+            I0 = api.forward(Ot, P, pos)
+            scale = w["total_counts"] / I0.sum().item()
+            P *= math.sqrt(scale)
+            meas = torch.poisson(I0 * scale, generator=gen)
+            recons.append([torch.ones_like(Ot), P, pos, meas, order])
         del Ot, I0
     total = sum(w["J"] for w in ws)
 
@@ -402,16 +415,35 @@ def run_uneven(args, rank, world, local_rank):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / steps
 
-    def sequential():
-        for (O, P, pos, meas, order), w in zip(recons, ws):
-            api.lsqml_epoch(O, P, pos, meas, order, api.make_opts(batch=w["batch"]), check=False)
-
     o_eager = [api.make_opts(batch=w["batch"]) for w in ws]
     o_graph = [api.make_opts(batch=w["batch"], graph=True) for w in ws]
+    if opr_K:
+        oprs = api.make_opr_opts(opr_K)
+
+        def sequential():
+            for r, o in zip(recons, o_eager):
+                api.lsqml_epoch_opr(*r[:6], r[6], o, oprs, check=False)
+
+        def batched(o):
+            return api.lsqml_epoch_opr_batched(recons, o, oprs, check=False)
+
+        def checked():
+            return api.lsqml_epoch_opr_batched(recons, o_graph, oprs, check=True)
+    else:
+        def sequential():
+            for (O, P, pos, meas, order), o in zip(recons, o_eager):
+                api.lsqml_epoch(O, P, pos, meas, order, o, check=False)
+
+        def batched(o):
+            return api.lsqml_epoch_batched(recons, o, check=False)
+
+        def checked():
+            return api.lsqml_epoch_batched(recons, o_graph, check=True)
+
     ms_seq = timed(sequential, args.steps)
-    ms_b = timed(lambda: api.lsqml_epoch_batched(recons, o_eager, check=False), args.steps)
-    ms_g = timed(lambda: api.lsqml_epoch_batched(recons, o_graph, check=False), args.steps)
-    api.lsqml_epoch_batched(recons, o_graph, check=True)
+    ms_b = timed(lambda: batched(o_eager), args.steps)
+    ms_g = timed(lambda: batched(o_graph), args.steps)
+    checked()
     ms_max = max_over_ranks(ms_g, world, dev)
     if rank == 0:
         print(json.dumps({
@@ -419,8 +451,9 @@ def run_uneven(args, rank, world, local_rank):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "uneven16", "reconstructions": len(ws), "positions": total,
-                       "windows": sorted({w["N"] for w in ws}), "J": [w["J"] for w in ws]},
+            "config": {"workload": "uneven16opr" if opr_K else "uneven16", "reconstructions": len(ws),
+                       "positions": total, "windows": sorted({w["N"] for w in ws}), "J": [w["J"] for w in ws],
+                       "opr_eigenmodes": opr_K},
             "batched_graph_ms": ms_g, "batched_eager_ms": ms_b, "sequential_ms": ms_seq,
             "speedup_vs_sequential": ms_seq / ms_g,
         }), flush=True)
@@ -500,6 +533,8 @@ def main():
     try:
         if args.workload == "uneven16":
             run_uneven(args, rank, world, local_rank)
+        elif args.workload == "uneven16opr":
+            run_uneven(args, rank, world, local_rank, opr_K=8)
         elif args.workload == "spiral256":
             run_ad256(args, rank, world, local_rank)
         else:

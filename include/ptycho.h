@@ -254,6 +254,21 @@ ptycho_status ptycho_lsqml_epoch_opr(const ptycho_dims* dims, const ptycho_opr_o
                                      const int32_t* order, const ptycho_lsqml_opts* opts, double* loss,
                                      double* alpha, void* ws, size_t ws_bytes, void* stream);
 
+/* Batched serving with the relaxed primary mode: ptycho_lsqml_epoch_opr for
+ * each of n reconstructions, run concurrently as ptycho_lsqml_epoch_batched
+ * runs its reconstructions (arrays of n entries; P_rest may be NULL when
+ * every dims[i].M == 1, `orders` may be NULL or hold NULL entries). Section i
+ * of the workspace has ptycho_workspace_bytes_opr(dims[i], opr[i].K,
+ * opts[i].batch) bytes. */
+size_t ptycho_workspace_bytes_opr_batched(int32_t n, const ptycho_dims* dims, const ptycho_opr_opts* opr,
+                                          const ptycho_lsqml_opts* opts);
+ptycho_status ptycho_lsqml_epoch_opr_batched(int32_t n, const ptycho_dims* dims, const ptycho_opr_opts* opr,
+                                             float* const* objects, float* const* U, float* const* w,
+                                             float* const* P_rest, const float* const* pos,
+                                             const float* const* meas, const int32_t* const* orders,
+                                             const ptycho_lsqml_opts* opts, double* losses, void* ws,
+                                             size_t ws_bytes, void* stream);
+
 /* Synchronises `stream`, returns (and clears) the device-side status recorded
  * in `ws` since the last read: PTYCHO_OK, PTYCHO_ERR_BOUNDS or
  * PTYCHO_ERR_NONFINITE (bounds reported first), or PTYCHO_ERR_CUDA. */

@@ -85,6 +85,9 @@ def lib() -> ctypes.CDLL:
                                                   ctypes.c_size_t, _P]),
             "ptycho_lsqml_epoch_opr": (ctypes.c_int, [dims_p, opr_p, _P, _P, _P, _P, _P, _P, _P, opts_p, _P, _P,
                                                       _P, ctypes.c_size_t, _P]),
+            "ptycho_workspace_bytes_opr_batched": (ctypes.c_size_t, [ctypes.c_int32, dims_p, opr_p, opts_p]),
+            "ptycho_lsqml_epoch_opr_batched": (ctypes.c_int, [ctypes.c_int32, dims_p, opr_p, _P, _P, _P, _P, _P,
+                                                              _P, _P, opts_p, _P, _P, ctypes.c_size_t, _P]),
             "ptycho_workspace_bytes": (ctypes.c_size_t, [dims_p, ctypes.c_int32]),
             "ptycho_host_workspace_bytes": (ctypes.c_size_t, [dims_p, ctypes.c_int32]),
             "ptycho_workspace_init": (ctypes.c_int, [_P, ctypes.c_size_t, _P]),
@@ -462,3 +465,55 @@ def lsqml_epoch_opr(obj, U, w, P_rest, pos, meas, order=None, opts: LsqmlOpts | 
            "ptycho_lsqml_epoch_opr")
     _finish(ws, "ptycho_lsqml_epoch_opr", check)
     return loss, alpha
+
+
+def lsqml_epoch_opr_batched(recons, opts, oprs, *, check: bool = True):
+    """One relaxed-probe LSQML epoch for each of several reconstructions, run concurrently.
+
+    ``recons`` is a list of (obj, U, w, P_rest, pos, meas, order) tuples (P_rest
+    and order may be None); ``opts`` and ``oprs`` one options struct or a list.
+    Updates obj, U, w, P_rest in place; returns the float64 [n] losses.
+    """
+    n = len(recons)
+    if n == 0:
+        raise ValueError("no reconstructions")
+    opts_list = opts if isinstance(opts, (list, tuple)) else [opts] * n
+    opr_list = oprs if isinstance(oprs, (list, tuple)) else [oprs] * n
+    dev = recons[0][0].device
+    dims = (Dims * n)()
+    OA = (LsqmlOpts * n)(*opts_list)
+    RA = (OprOpts * n)(*opr_list)
+    ptrs = {k: (ctypes.c_void_p * n)() for k in ("o", "u", "w", "p", "r", "m", "q")}
+    any_rest = False
+    for i, (obj, U, w, P_rest, pos, meas, order) in enumerate(recons):
+        d = _opr_dims(obj, U, w, P_rest, pos)
+        if RA[i].K != U.shape[0]:
+            raise ValueError("opr.K must equal the number of eigenmodes")
+        _need(meas, "meas", torch.float32, (d.J, d.N, d.N), device=dev)
+        if order is not None:
+            _need(order, "order", torch.int32, (d.J,), device=dev)
+        dims[i] = d
+        ptrs["o"][i], ptrs["u"][i], ptrs["w"][i] = obj.data_ptr(), U.data_ptr(), w.data_ptr()
+        ptrs["p"][i] = P_rest.data_ptr() if P_rest is not None else None
+        any_rest = any_rest or P_rest is not None
+        ptrs["r"][i], ptrs["m"][i] = pos.data_ptr(), meas.data_ptr()
+        ptrs["q"][i] = order.data_ptr() if order is not None else None
+    need = lib().ptycho_workspace_bytes_opr_batched(n, dims, RA, OA)
+    if need == 0:
+        raise PtychoError(6, "workspace_bytes_opr_batched")
+    key = (str(dev), "batched")
+    ws = _ws_cache.get(key)
+    if ws is None or ws.nbytes < need:
+        ws = Workspace(need, dev)
+        _ws_cache[key] = ws
+    losses = torch.zeros(n, dtype=torch.float64, device=dev)
+    _check(lib().ptycho_lsqml_epoch_opr_batched(n, dims, RA, ptrs["o"], ptrs["u"], ptrs["w"],
+                                                ptrs["p"] if any_rest else None, ptrs["r"], ptrs["m"], ptrs["q"], OA,
+                                                _ptr(losses), _P(ws.ptr), ws.nbytes, _stream()),
+           "ptycho_lsqml_epoch_opr_batched")
+    if check:
+        off = 0
+        for i in range(n):
+            _check(lib().ptycho_status_read(_P(ws.ptr + off), _stream()), f"ptycho_lsqml_epoch_opr_batched[{i}]")
+            off += lib().ptycho_workspace_bytes_opr(ctypes.byref(dims[i]), RA[i].K, OA[i].batch)
+    return losses

@@ -148,6 +148,43 @@ __global__ void k_probe_update(int NN, int M, float2* probe, const float2* dP, f
   if (blockIdx.x == 0 && threadIdx.x == 0) memset(sc_next, 0, sizeof(BatchScalars));
 }
 
+// Object tile of the batch's slot blockIdx.y (false: the slot was skipped by
+// pass 1). Blocks blockIdx.x walk its (N+1)^2 pixels.
+__device__ __forceinline__ bool slot_tile(int N, int H, int W, int J, const float* pos, const int* order, int b0,
+                                          const int* valid, int& ty, int& tx) {
+  const int slot = blockIdx.y;
+  if (!valid[slot]) return false;
+  const int e = b0 + slot;
+  const int j = order ? order[e] : e;
+  float fy, fx;
+  return tile_of(pos[2 * j], pos[2 * j + 1], N, H, W, ty, tx, fy, fx);
+}
+
+// max(illumination) over the tiles of the batch (all non-zero illumination
+// of the minibatch lies in them).
+__global__ void k_tile_illum_max(int N, int H, int W, int J, const float* pos, const int* order, int b0,
+                                 const int* valid, const float4* __restrict__ acc, BatchScalars* sc) {
+  __shared__ float red[32];
+  int ty, tx;
+  if (!slot_tile(N, H, W, J, pos, order, b0, valid, ty, tx)) return;
+  const int N1 = N + 1;
+  float m = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N1 * N1; i += gridDim.x * blockDim.x)
+    m = fmaxf(m, __ldcs(&acc[(size_t)(ty + i / N1) * W + tx + i % N1].z));
+  m = block_max(m, red);
+  if (threadIdx.x == 0) atomicMax(&sc->max_illum, __float_as_uint(m));
+}
+
+// Zeroes the batch's tiles of the accumulator.
+__global__ void k_tile_clear(int N, int H, int W, int J, const float* pos, const int* order, int b0,
+                             const int* valid, float4* acc) {
+  int ty, tx;
+  if (!slot_tile(N, H, W, J, pos, order, b0, valid, ty, tx)) return;
+  const int N1 = N + 1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N1 * N1; i += gridDim.x * blockDim.x)
+    acc[(size_t)(ty + i / N1) * W + tx + i % N1] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // ---------------------------------------------------------------------------
 // Workspace layout.
 // ---------------------------------------------------------------------------
@@ -175,12 +212,13 @@ Layout make_layout(const ptycho_dims& d, int B, int K) {
   L.Cp = take(NN * sizeof(float2));
   L.Sdp = take(NN * sizeof(float));
   L.valid = take((size_t)B * sizeof(int));
-  L.p0 = L.dUacc = L.Du = L.dU = 0;
+  L.p0 = L.dUacc = L.Du = L.dU = L.gram = 0;
   if (K > 0) {
     L.p0 = take((size_t)B * NN * sizeof(float2));
     L.dUacc = take((size_t)K * NN * sizeof(float2));
     L.Du = take((size_t)K * NN * sizeof(float));
     L.dU = take((size_t)K * NN * sizeof(float2));
+    L.gram = take((size_t)B * (OPR_KMAX * (OPR_KMAX + 1) / 2 + OPR_KMAX) * sizeof(double));   // weight-step sums
   }
   L.total = off;
   return L;
@@ -338,6 +376,33 @@ cudaError_t init_epoch(int NN, int M, const float2* probe, float* Sp, WsHeader* 
   });
 }
 
+bool tiles_cheaper(int nb, int N, int H, int W) {
+  // tile rows are short, strided runs: count them twice against the plane
+  return 2 * (size_t)nb * (N + 1) * (N + 1) < (size_t)H * W;
+}
+
+static dim3 tile_grid(int nb, int N) {
+  const int n1 = (N + 1) * (N + 1);
+  return dim3((unsigned)((n1 + 1023) / 1024), (unsigned)nb);
+}
+
+cudaError_t tile_illum_max(const ptycho_dims& d, int nb, int b0, const float* pos, const int32_t* order,
+                           const int* valid, const float4* acc, BatchScalars* sc, cudaStream_t s) {
+  return timed(K_TILE_MAX, s, [&] {
+    k_tile_illum_max<<<tile_grid(nb, d.N), 256, 0, s>>>(d.N, d.H, d.W, d.J, pos, order, b0, valid, acc, sc);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t clear_acc(bool tiles, const ptycho_dims& d, int nb, int b0, const float* pos, const int32_t* order,
+                      const int* valid, float4* acc, cudaStream_t s) {
+  if (!tiles) return cudaMemsetAsync(acc, 0, (size_t)d.H * d.W * sizeof(float4), s);
+  return timed(K_TILE_CLEAR, s, [&] {
+    k_tile_clear<<<tile_grid(nb, d.N), 256, 0, s>>>(d.N, d.H, d.W, d.J, pos, order, b0, valid, acc);
+    return cudaGetLastError();
+  });
+}
+
 Ptrs carve(void* ws, const Layout& L) {
   char* b = (char*)ws;
   Ptrs p;
@@ -358,6 +423,7 @@ Ptrs carve(void* ws, const Layout& L) {
   p.dUacc = L.dUacc ? (float2*)(b + L.dUacc) : nullptr;
   p.Du = L.Du ? (float*)(b + L.Du) : nullptr;
   p.dU = L.dU ? (float2*)(b + L.dU) : nullptr;
+  p.gram = L.gram ? (double*)(b + L.gram) : nullptr;
   return p;
 }
 
@@ -452,9 +518,11 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const 
     a.Sp = w.Sp; a.acc = w.acc;
     a.loss = loss; a.status = &w.hdr->status;
     if ((e = pass1(N, a, s, tune.v1)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    const bool tiles = tiles_cheaper(nb, N, d.H, d.W);
     if ((e = probe_reduce(NN, 0, M, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
-                          o.update_probe ? w.Dp : nullptr, w.acc, HW, sc, s)) != cudaSuccess)
+                          o.update_probe ? w.Dp : nullptr, tiles ? nullptr : w.acc, HW, sc, s)) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
+    if (tiles && tile_illum_max(d, nb, b0, pos, order, w.valid, w.acc, sc, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if ((e = norm_probe(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p, o.update_probe, sc, w.dP, w.Cp, w.Sdp,
                         s)) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
@@ -468,7 +536,7 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const 
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
     if ((e = pass2(N, q, s, tune.v2)) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    if ((e = cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if ((e = clear_acc(tiles, d, nb, b0, pos, order, w.valid, w.acc, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if ((e = probe_update(NN, M, probe, w.dP, w.Sp, o.update_probe, sc, sc_next, s)) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
   }

@@ -110,6 +110,41 @@ ptycho_status graph_store(const GraphKey& key, cudaGraphExec_t exec) {
   return PTYCHO_OK;
 }
 
+// Runs run(i, section_i, worker stream) for every reconstruction, forked from
+// and joined back into `origin`; section i of `ws` has section(i) bytes and
+// its status word is cleared first.
+template <class Section, class Run>
+static ptycho_status run_sections(int n, void* ws, cudaStream_t origin, Section&& section, Run&& run) {
+  cudaStream_t* workers = nullptr;
+  int nw = 0;
+  ptycho_status rs = worker_streams(&workers, &nw);
+  if (rs != PTYCHO_OK) return rs;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins((size_t)(n < nw ? n : nw), nullptr);
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  for (auto& e : joins)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rs = PTYCHO_ERR_CUDA;
+  if (rs == PTYCHO_OK && cudaEventRecord(fork, origin) != cudaSuccess) rs = PTYCHO_ERR_CUDA;
+  for (int k = 0; rs == PTYCHO_OK && k < (int)joins.size(); ++k)
+    if (cudaStreamWaitEvent(workers[k], fork, 0) != cudaSuccess) rs = PTYCHO_ERR_CUDA;
+  char* base = (char*)ws;
+  for (int i = 0; rs == PTYCHO_OK && i < n; ++i) {
+    if (cudaMemsetAsync(base, 0, 256, workers[i % nw]) != cudaSuccess) {
+      rs = PTYCHO_ERR_CUDA;
+      break;
+    }
+    rs = run(i, (void*)base, workers[i % nw]);
+    base += section(i);
+  }
+  for (int k = 0; rs == PTYCHO_OK && k < (int)joins.size(); ++k)
+    if (cudaEventRecord(joins[k], workers[k]) != cudaSuccess || cudaStreamWaitEvent(origin, joins[k], 0) != cudaSuccess)
+      rs = PTYCHO_ERR_CUDA;
+  cudaEventDestroy(fork);
+  for (auto& e : joins)
+    if (e) cudaEventDestroy(e);
+  return rs;
+}
+
 }  // namespace ptycho
 
 using namespace ptycho;
@@ -139,43 +174,14 @@ ptycho_status ptycho_lsqml_epoch_batched(int32_t n, const ptycho_dims* dims, flo
   }
   const size_t need = ptycho_workspace_bytes_batched(n, dims, opts);
   if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < need) return PTYCHO_ERR_WORKSPACE;
-  cudaStream_t* workers = nullptr;
-  int nw = 0;
-  if ((st = worker_streams(&workers, &nw)) != PTYCHO_OK) return st;
-
-  auto body = [&](cudaStream_t origin) -> ptycho_status {
-    cudaEvent_t fork = nullptr;
-    std::vector<cudaEvent_t> joins((size_t)(n < nw ? n : nw), nullptr);
-    ptycho_status rs = PTYCHO_OK;
-    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    for (auto& e : joins)
-      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rs = PTYCHO_ERR_CUDA;
-    if (rs == PTYCHO_OK && cudaEventRecord(fork, origin) != cudaSuccess) rs = PTYCHO_ERR_CUDA;
-    for (int w = 0; rs == PTYCHO_OK && w < (int)joins.size(); ++w)
-      if (cudaStreamWaitEvent(workers[w], fork, 0) != cudaSuccess) rs = PTYCHO_ERR_CUDA;
-    char* base = (char*)ws;
-    for (int i = 0; rs == PTYCHO_OK && i < n; ++i) {
-      const size_t bytes = make_layout(dims[i], opts[i].batch).total;
-      // each section's status word starts the call cleared
-      if (cudaMemsetAsync(base, 0, 256, workers[i % nw]) != cudaSuccess) {
-        rs = PTYCHO_ERR_CUDA;
-        break;
-      }
-      ptycho_lsqml_opts oi = opts[i];
-      oi.flags = 0;
-      rs = run_epoch(dims[i], (float2*)objects[i], (float2*)probes[i], pos[i], meas[i], orders ? orders[i] : nullptr,
-                     oi, losses ? losses + i : nullptr, nullptr, base, workers[i % nw]);
-      base += bytes;
-    }
-    for (int w = 0; rs == PTYCHO_OK && w < (int)joins.size(); ++w)
-      if (cudaEventRecord(joins[w], workers[w]) != cudaSuccess || cudaStreamWaitEvent(origin, joins[w], 0) != cudaSuccess)
-        rs = PTYCHO_ERR_CUDA;
-    cudaEventDestroy(fork);
-    for (auto& e : joins)
-      if (e) cudaEventDestroy(e);
-    return rs;
+  auto section = [&](int i) { return make_layout(dims[i], opts[i].batch).total; };
+  auto run = [&](int i, void* base, cudaStream_t s) {
+    ptycho_lsqml_opts oi = opts[i];
+    oi.flags = 0;
+    return run_epoch(dims[i], (float2*)objects[i], (float2*)probes[i], pos[i], meas[i],
+                     orders ? orders[i] : nullptr, oi, losses ? losses + i : nullptr, nullptr, base, s);
   };
-
+  auto body = [&](cudaStream_t origin) { return run_sections(n, ws, origin, section, run); };
   bool graph = true;
   for (int i = 0; i < n; ++i) graph = graph && (opts[i].flags & PTYCHO_FLAG_GRAPH);
   if (!graph) return body((cudaStream_t)stream);
@@ -183,6 +189,56 @@ ptycho_status ptycho_lsqml_epoch_batched(int32_t n, const ptycho_dims* dims, flo
   key.add(n).add(ws).add(losses).add(orders != nullptr);
   for (int i = 0; i < n; ++i)
     key.add(dims[i]).add(opts[i]).add(objects[i]).add(probes[i]).add(pos[i]).add(meas[i]).add(orders ? orders[i] : nullptr);
+  return run_graphed(key, (cudaStream_t)stream, body);
+}
+
+size_t ptycho_workspace_bytes_opr_batched(int32_t n, const ptycho_dims* dims, const ptycho_opr_opts* opr,
+                                          const ptycho_lsqml_opts* opts) {
+  if (n < 1 || !dims || !opr || !opts) return 0;
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t b = ptycho_workspace_bytes_opr(&dims[i], opr[i].K, opts[i].batch);
+    if (b == 0) return 0;
+    total += b;
+  }
+  return total;
+}
+
+ptycho_status ptycho_lsqml_epoch_opr_batched(int32_t n, const ptycho_dims* dims, const ptycho_opr_opts* opr,
+                                             float* const* objects, float* const* U, float* const* w,
+                                             float* const* P_rest, const float* const* pos,
+                                             const float* const* meas, const int32_t* const* orders,
+                                             const ptycho_lsqml_opts* opts, double* losses, void* ws,
+                                             size_t ws_bytes, void* stream) {
+  if (n < 1 || !dims || !opr || !objects || !U || !w || !pos || !meas || !opts) return PTYCHO_ERR_ARG;
+  ptycho_status st;
+  for (int i = 0; i < n; ++i) {
+    if ((st = check_dims(&dims[i])) != PTYCHO_OK) return st;
+    if ((st = check_opr_opts(&opr[i])) != PTYCHO_OK) return st;
+    if ((st = check_opts(&opts[i])) != PTYCHO_OK) return st;
+    if (!objects[i] || !U[i] || (dims[i].M > 1 && (!P_rest || !P_rest[i])) ||
+        (dims[i].J > 0 && (!pos[i] || !meas[i] || !w[i])))
+      return PTYCHO_ERR_ARG;
+  }
+  const size_t need = ptycho_workspace_bytes_opr_batched(n, dims, opr, opts);
+  if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < need) return PTYCHO_ERR_WORKSPACE;
+  auto section = [&](int i) { return make_layout(dims[i], opts[i].batch, opr[i].K).total; };
+  auto run = [&](int i, void* base, cudaStream_t s) {
+    ptycho_lsqml_opts oi = opts[i];
+    oi.flags = 0;
+    return run_epoch_opr(dims[i], opr[i], (float2*)objects[i], (float2*)U[i], w[i],
+                         P_rest ? (float2*)P_rest[i] : nullptr, pos[i], meas[i], orders ? orders[i] : nullptr, oi,
+                         losses ? losses + i : nullptr, nullptr, base, s);
+  };
+  auto body = [&](cudaStream_t origin) { return run_sections(n, ws, origin, section, run); };
+  bool graph = true;
+  for (int i = 0; i < n; ++i) graph = graph && (opts[i].flags & PTYCHO_FLAG_GRAPH);
+  if (!graph) return body((cudaStream_t)stream);
+  GraphKey key;
+  key.add(n).add(ws).add(losses).add(orders != nullptr).add(P_rest != nullptr);
+  for (int i = 0; i < n; ++i)
+    key.add(dims[i]).add(opr[i]).add(opts[i]).add(objects[i]).add(U[i]).add(w[i])
+        .add(P_rest ? P_rest[i] : nullptr).add(pos[i]).add(meas[i]).add(orders ? orders[i] : nullptr);
   return run_graphed(key, (cudaStream_t)stream, body);
 }
 

@@ -112,7 +112,7 @@ __device__ __forceinline__ const float2* shared_mode(const BatchArgs& a, int k, 
 // sum_m wj[m] V_m at the pixel pair starting at p (V: [K, N, N], 16-byte pairs).
 __device__ __forceinline__ float4 opr_pair(const float2* __restrict__ V, const float* wj, int K, int NN, int p) {
   float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 1
+#pragma unroll 4   // four independent loads in flight
   for (int m = 0; m < K; ++m) {
     const float4 u = __ldg((const float4*)(V + (size_t)m * NN + p));
     const float w = wj[m];
@@ -124,7 +124,7 @@ __device__ __forceinline__ float4 opr_pair(const float2* __restrict__ V, const f
 // sum_m wj[m] V_m at one pixel.
 __device__ __forceinline__ float2 opr_pixel(const float2* __restrict__ V, const float* wj, int K, int NN, int p) {
   float2 s = make_float2(0.f, 0.f);
-#pragma unroll 1
+#pragma unroll 4
   for (int m = 0; m < K; ++m) {
     const float2 u = __ldg(V + (size_t)m * NN + p);
     s.x = fmaf(wj[m], u.x, s.x); s.y = fmaf(wj[m], u.y, s.y);

@@ -12,7 +12,7 @@ namespace ptycho {
 
 struct Layout {
   size_t hdr, acc, psi, o, g, h, dPacc, Dp, dP, Sp, Cp, Sdp, valid;
-  size_t p0, dUacc, Du, dU;   // orthogonal probe relaxation (K > 0) only
+  size_t p0, dUacc, Du, dU, gram;   // orthogonal probe relaxation (K > 0) only
   size_t total;
 };
 
@@ -25,6 +25,7 @@ struct Ptrs {
   int* valid;
   float2 *p0, *dUacc, *dU;
   float* Du;
+  double* gram;
 };
 
 size_t align256(size_t b);
@@ -55,10 +56,24 @@ cudaError_t norm_probe(int NN, int M, const float2* dPacc, const float* Dp, cons
 cudaError_t probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
                          const BatchScalars* sc, BatchScalars* sc_next, cudaStream_t s);
 cudaError_t init_epoch(int NN, int M, const float2* probe, float* Sp, struct WsHeader* hdr, cudaStream_t s);
+// True when a minibatch's object tiles are cheaper to visit than the whole
+// object plane: the illumination maximum then scans only those tiles
+// (tile_illum_max) and the accumulator is cleared tile by tile (clear_acc).
+bool tiles_cheaper(int nb, int N, int H, int W);
+cudaError_t tile_illum_max(const ptycho_dims& d, int nb, int b0, const float* pos, const int32_t* order,
+                           const int* valid, const float4* acc, BatchScalars* sc, cudaStream_t s);
+cudaError_t clear_acc(bool tiles, const ptycho_dims& d, int nb, int b0, const float* pos, const int32_t* order,
+                      const int* valid, float4* acc, cudaStream_t s);
 // One LSQML epoch on stream s with workspace ws (arguments already validated).
 ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const float* pos, const float* meas,
                         const int32_t* order, const ptycho_lsqml_opts& o, double* loss, double* alpha, void* ws,
                         cudaStream_t s);
+
+// One LSQML epoch with orthogonal probe relaxation (arguments already validated).
+ptycho_status run_epoch_opr(const ptycho_dims& d, const ptycho_opr_opts& r, float2* obj, float2* U, float* wts,
+                            float2* P_rest, const float* pos, const float* meas, const int32_t* order,
+                            const ptycho_lsqml_opts& o, double* loss, double* alpha, void* ws, cudaStream_t s);
+ptycho_status check_opr_opts(const ptycho_opr_opts* r);
 
 // Byte-exact key of a captured launch sequence (dimensions, options, pointers).
 struct GraphKey {

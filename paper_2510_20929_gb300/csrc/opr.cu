@@ -92,88 +92,200 @@ __global__ void k_norm_opr(size_t n, const float2* dUacc, const float* D, int up
     dU[p] = update_probe ? cscale(dUacc[p], 1.f / (D[p] + damp)) : make_float2(0.f, 0.f);
 }
 
-// One CTA per slot of the batch. b_m = Re<U_m, h_j0>; in gradient form
-// (gw set) b is added to dL/dw_j. Otherwise the damped normal equations
-// (A + lam tr(A)/K I) dw = b with A_mn = sum |o_j|^2 Re(conj(U_m) U_n) are
-// solved in FP64 (Cholesky; no update if the system is not positive
-// definite) and w_j += step dw.
+// Per-slot sums of the weight step (FP64 atomics into gram[slot]):
+// gram[NA + m] = b_m = Re<U_m, h_j0>, and with `ls`
+// gram[t(m, n)] = A_mn = sum |o_j|^2 Re(conj(U_m) U_n) for m <= n.
+// A CTA takes GRAM_SLOTS slots (one warp each) and the pixel range
+// [blockIdx.x * span, +span) in chunks of GRAM_CHUNK pixels. Each chunk's
+// eigenmode values, h_j0 and o_j are copied into shared memory with cp.async
+// (double-buffered: the next chunk is in flight while this one is summed), so
+// that U is fetched once per CTA instead of once per slot. span and the
+// window area are multiples of GRAM_CHUNK.
+constexpr int GRAM_SLOTS = 8, GRAM_CHUNK = 256;
+
 template <int KM>
-__global__ void __launch_bounds__(256) k_opr_weights(int N, int M, int K, int b0, const int* __restrict__ order,
-                                                     const int* __restrict__ valid, const float2* __restrict__ U,
-                                                     const float2* __restrict__ h_s, const float2* __restrict__ o_s,
-                                                     float* w, float* gw, double lam, float step) {
+struct GramSmem {
+  float2 u[2][KM][GRAM_CHUNK];
+  float2 h[2][GRAM_SLOTS][GRAM_CHUNK];
+  float2 o[2][GRAM_SLOTS][GRAM_CHUNK];
+};
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
+
+template <int KM>
+__global__ void __launch_bounds__(32 * GRAM_SLOTS, 2) k_opr_gram(int N, int M, int K, int ls, int nb, int span,
+                                                                 const int* __restrict__ valid,
+                                                                 const float2* __restrict__ U,
+                                                                 const float2* __restrict__ h_s,
+                                                                 const float2* __restrict__ o_s, double* gram) {
   constexpr int NA = KM * (KM + 1) / 2, NV = NA + KM;
-  __shared__ double red[32 * NV];
-  const int slot = blockIdx.x;
-  if (!valid[slot]) return;
-  const int e = b0 + slot;
-  const int j = order ? order[e] : e;
-  const int NN = N * N, NP = NN / 2;
-  const bool ls = (gw == nullptr);
-  const float4* h = (const float4*)(h_s + (size_t)slot * M * NN);
-  const float4* o = (const float4*)(o_s + (size_t)slot * NN);
+  extern __shared__ __align__(16) unsigned char gsm[];
+  GramSmem<KM>& sm = *(GramSmem<KM>*)gsm;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot0 = blockIdx.y * GRAM_SLOTS;
+  const int slot = slot0 + warp;
+  const bool active = slot < nb && valid[slot];
+  const int NN = N * N;
+  const int p0 = blockIdx.x * span, p1 = min(NN, p0 + span);
+  // eigenmode rows m >= K are never copied: zero them once
+  for (int i = threadIdx.x; i < 2 * KM * GRAM_CHUNK; i += blockDim.x) {
+    const int b = i / (KM * GRAM_CHUNK), m = (i / GRAM_CHUNK) % KM, q = i % GRAM_CHUNK;
+    if (m >= K) sm.u[b][m][q] = make_float2(0.f, 0.f);
+  }
+  auto stage = [&](int c0, int b) {
+    for (int i = threadIdx.x; i < K * GRAM_CHUNK; i += blockDim.x) {
+      const int m = i / GRAM_CHUNK, q = i % GRAM_CHUNK;
+      cp_async8(&sm.u[b][m][q], U + (size_t)m * NN + c0 + q);
+    }
+    for (int i = threadIdx.x; i < GRAM_SLOTS * GRAM_CHUNK; i += blockDim.x) {
+      const int sl = i / GRAM_CHUNK, q = i % GRAM_CHUNK, sg = slot0 + sl;
+      if (sg < nb) {
+        cp_async8(&sm.h[b][sl][q], h_s + (size_t)sg * M * NN + c0 + q);
+        if (ls) cp_async8(&sm.o[b][sl][q], o_s + (size_t)sg * NN + c0 + q);
+      }
+    }
+    cp_async_commit();
+  };
   float acc[NV];
 #pragma unroll
   for (int t = 0; t < NV; ++t) acc[t] = 0.f;
-  for (int q = threadIdx.x; q < NP; q += blockDim.x) {
-    const float4 hv = __ldg(h + q);
-    float4 u[KM];
-#pragma unroll
-    for (int m = 0; m < KM; ++m)
-      u[m] = m < K ? __ldg((const float4*)(U + (size_t)m * NN) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int m = 0; m < KM; ++m)   // Re(conj(U_m) h) at both pixels
-      acc[NA + m] += u[m].x * hv.x + u[m].y * hv.y + u[m].z * hv.z + u[m].w * hv.w;
-    if (ls) {
-      const float4 ov = __ldg(o + q);
-      const float oa0 = ov.x * ov.x + ov.y * ov.y, oa1 = ov.z * ov.z + ov.w * ov.w;
-      int t = 0;
-#pragma unroll
-      for (int m = 0; m < KM; ++m)
-#pragma unroll
-        for (int n = m; n < KM; ++n, ++t)
-          acc[t] += oa0 * (u[m].x * u[n].x + u[m].y * u[n].y) + oa1 * (u[m].z * u[n].z + u[m].w * u[n].w);
+  stage(p0, 0);
+  int b = 0;
+  for (int c0 = p0; c0 < p1; c0 += GRAM_CHUNK, b ^= 1) {
+    if (c0 + GRAM_CHUNK < p1) {
+      stage(c0 + GRAM_CHUNK, b ^ 1);
+      cp_async_wait<1>();   // this chunk's group has landed (the next may be in flight)
+    } else {
+      cp_async_wait<0>();
     }
-  }
-  double v[NV];
+    __syncthreads();
+    if (active) {
+      for (int q = lane; q < GRAM_CHUNK; q += 32) {
+        const float2 hv = sm.h[b][warp][q];
+        float2 u[KM];
 #pragma unroll
-  for (int t = 0; t < NV; ++t) v[t] = (double)acc[t];
-  block_sum<NV>(v, red);
-  if (threadIdx.x != 0) return;
-  if (!ls) {
-    for (int m = 0; m < K; ++m) atomicAdd(gw + (size_t)j * K + m, (float)v[NA + m]);
-    return;
+        for (int m = 0; m < KM; ++m) u[m] = sm.u[b][m][q];
+#pragma unroll
+        for (int m = 0; m < KM; ++m) acc[NA + m] += u[m].x * hv.x + u[m].y * hv.y;   // Re(conj(U_m) h)
+        if (ls) {
+          const float2 ov = sm.o[b][warp][q];
+          const float c = ov.x * ov.x + ov.y * ov.y;
+          int t = 0;
+#pragma unroll
+          for (int m = 0; m < KM; ++m) {
+            const float cx = c * u[m].x, cy = c * u[m].y;
+#pragma unroll
+            for (int n = m; n < KM; ++n, ++t) acc[t] = fmaf(cx, u[n].x, fmaf(cy, u[n].y, acc[t]));
+          }
+        }
+      }
+    }
+    __syncthreads();   // buffer b is refilled by the stage two chunks ahead
   }
-  double A[KM][KM], L[KM][KM], y[KM];
-  int t = 0;
-  for (int m = 0; m < KM; ++m)
-    for (int n = m; n < KM; ++n, ++t) A[m][n] = A[n][m] = v[t];
+  if (!active) return;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    float x = acc[t];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0 && (ls || t >= NA)) atomicAdd(gram + (size_t)slot * NV + t, (double)x);
+  }
+}
+
+// In-register FP64 solve of (A + dmp I) x = b for K unknowns (Cholesky on the
+// packed upper triangle a[t(m, n)], m <= n); false if not positive definite.
+template <int K, int KM>
+__device__ __forceinline__ bool chol_solve(const double* v, double lam, double (&x)[KM]) {
+  constexpr int NA = KM * (KM + 1) / 2;
+  double L[K][K];
   double tr = 0.0;
-  for (int m = 0; m < K; ++m) tr += A[m][m];
+#pragma unroll
+  for (int m = 0; m < K; ++m) tr += v[m * KM - m * (m - 1) / 2];   // A_mm
   const double dmp = lam * tr / (double)K;
+#pragma unroll
   for (int r = 0; r < K; ++r) {
+#pragma unroll
     for (int c = 0; c <= r; ++c) {
-      double sum = A[r][c] + (r == c ? dmp : 0.0);
+      double sum = v[c * KM - c * (c - 1) / 2 + (r - c)] + (r == c ? dmp : 0.0);   // A_cr, c <= r
+#pragma unroll
       for (int k = 0; k < c; ++k) sum -= L[r][k] * L[c][k];
       if (r == c) {
-        if (!(sum > 0.0)) return;   // not positive definite: no weight update
+        if (!(sum > 0.0)) return false;
         L[r][r] = sqrt(sum);
       } else {
         L[r][c] = sum / L[c][c];
       }
     }
   }
-  for (int r = 0; r < K; ++r) {    // L y = b
+#pragma unroll
+  for (int r = 0; r < K; ++r) {   // L y = b
     double sum = v[NA + r];
-    for (int k = 0; k < r; ++k) sum -= L[r][k] * y[k];
-    y[r] = sum / L[r][r];
+#pragma unroll
+    for (int k = 0; k < r; ++k) sum -= L[r][k] * x[k];
+    x[r] = sum / L[r][r];
   }
-  for (int r = K - 1; r >= 0; --r) {   // L^T x = y (x stored in y)
-    double sum = y[r];
-    for (int k = r + 1; k < K; ++k) sum -= L[k][r] * y[k];
-    y[r] = sum / L[r][r];
+#pragma unroll
+  for (int r = K - 1; r >= 0; --r) {   // L^T x = y
+    double sum = x[r];
+#pragma unroll
+    for (int k = r + 1; k < K; ++k) sum -= L[k][r] * x[k];
+    x[r] = sum / L[r][r];
   }
-  for (int m = 0; m < K; ++m) w[(size_t)j * K + m] += (float)(step * y[m]);
+  return true;
+}
+
+// One thread per slot. Gradient form (gw set): dL/dw_j += b. Otherwise the
+// damped normal equations (A + lam tr(A)/K I) dw = b are solved in FP64
+// (Cholesky; no update if the system is not positive definite) and
+// w_j += step dw.
+template <int KM>
+__global__ void k_opr_solve(int nb, int K, int b0, const int* __restrict__ order, const int* __restrict__ valid,
+                            const double* __restrict__ gram, float* w, float* gw, double lam, float step) {
+  constexpr int NA = KM * (KM + 1) / 2, NV = NA + KM;
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nb || !valid[slot]) return;
+  const int e = b0 + slot;
+  const int j = order ? order[e] : e;
+  const double* v = gram + (size_t)slot * NV;
+  if (gw) {
+    for (int m = 0; m < K; ++m) gw[(size_t)j * K + m] += (float)v[NA + m];
+    return;
+  }
+  double x[KM];
+  bool ok = false;
+  switch (K) {
+    case 1: ok = chol_solve<1, KM>(v, lam, x); break;
+    case 2: ok = chol_solve<2, KM>(v, lam, x); break;
+    case 3: ok = chol_solve<3, KM>(v, lam, x); break;
+    case 4: ok = chol_solve<4, KM>(v, lam, x); break;
+    case 5: ok = chol_solve<5, KM>(v, lam, x); break;
+    case 6: ok = chol_solve<6, KM>(v, lam, x); break;
+    case 7: ok = chol_solve<7, KM>(v, lam, x); break;
+    case 8: ok = chol_solve<8, KM>(v, lam, x); break;
+  }
+  if (!ok) return;   // not positive definite: no weight update
+  for (int m = 0; m < K; ++m) w[(size_t)j * K + m] += (float)(step * x[m]);
+}
+
+constexpr int OPR_NV = OPR_KMAX * (OPR_KMAX + 1) / 2 + OPR_KMAX;   // sums per slot of the weight step
+
+// Opts a kernel into more than 48 KB of dynamic shared memory, once per device.
+template <class Kern>
+static cudaError_t smem_optin_once(Kern kernel, size_t bytes, unsigned long long* done_mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (__atomic_load_n(done_mask, __ATOMIC_ACQUIRE) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) __atomic_fetch_or(done_mask, bit, __ATOMIC_ACQ_REL);
+  return e;
 }
 
 static cudaError_t opr_reduce(int NN, int M, int K, int nb, int b0, const int* order, const float* w,
@@ -194,13 +306,31 @@ static cudaError_t opr_reduce(int NN, int M, int K, int nb, int b0, const int* o
   return cudaGetLastError();
 }
 
+// Weight gradient (gw set) or least-squares weight update of the batch's
+// positions; `gram` is the per-slot scratch of OPR_NV doubles.
 static cudaError_t opr_weights(int N, int M, int K, int nb, int b0, const int* order, const int* valid,
                                const float2* U, const float2* h_s, const float2* o_s, float* w, float* gw,
-                               double lam, float step, cudaStream_t s) {
+                               double* gram, double lam, float step, cudaStream_t s) {
   cudaEvent_t e0 = profile_begin(K_OPR_WEIGHTS, s);
-  k_opr_weights<OPR_KMAX><<<nb, 256, 0, s>>>(N, M, K, b0, order, valid, U, h_s, o_s, w, gw, lam, step);
+  cudaError_t e = cudaMemsetAsync(gram, 0, (size_t)nb * OPR_NV * sizeof(double), s);
+  if (e == cudaSuccess) {
+    // pixel spans of whole chunks, enough CTAs for two per SM
+    const int NN = N * N, groups = (nb + GRAM_SLOTS - 1) / GRAM_SLOTS;
+    int parts = (2 * 152 + groups - 1) / groups;
+    const int max_parts = (NN + GRAM_CHUNK - 1) / GRAM_CHUNK;
+    if (parts > max_parts) parts = max_parts;
+    const int span = ((NN + parts - 1) / parts + GRAM_CHUNK - 1) / GRAM_CHUNK * GRAM_CHUNK;
+    parts = (NN + span - 1) / span;
+    static unsigned long long done = 0;
+    e = smem_optin_once(k_opr_gram<OPR_KMAX>, sizeof(GramSmem<OPR_KMAX>), &done);
+    if (e == cudaSuccess)
+      k_opr_gram<OPR_KMAX><<<dim3(parts, groups), 32 * GRAM_SLOTS, sizeof(GramSmem<OPR_KMAX>), s>>>(
+          N, M, K, gw ? 0 : 1, nb, span, valid, U, h_s, o_s, gram);
+    k_opr_solve<OPR_KMAX><<<(nb + 31) / 32, 32, 0, s>>>(nb, K, b0, order, valid, gram, w, gw, lam, step);
+    e = cudaGetLastError();
+  }
   profile_end(K_OPR_WEIGHTS, e0, s);
-  return cudaGetLastError();
+  return e;
 }
 
 static ptycho_status check_opr_dims(const ptycho_dims* d, int32_t K) {
@@ -210,7 +340,7 @@ static ptycho_status check_opr_dims(const ptycho_dims* d, int32_t K) {
   return PTYCHO_OK;
 }
 
-static ptycho_status check_opr_opts(const ptycho_opr_opts* r) {
+ptycho_status check_opr_opts(const ptycho_opr_opts* r) {
   if (!r) return PTYCHO_ERR_ARG;
   if (r->K < 1 || r->K > OPR_KMAX) return PTYCHO_ERR_UNSUPPORTED;
   if ((r->update_weights != 0 && r->update_weights != 1) || r->reserved[0] != 0 || r->reserved[1] != 0)
@@ -250,9 +380,11 @@ ptycho_status run_epoch_opr(const ptycho_dims& d, const ptycho_opr_opts& r, floa
     a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid; a.p0_s = w.p0;
     a.Sp = w.Sp; a.acc = w.acc; a.loss = loss; a.status = &w.hdr->status;
     if (pass1(N, a, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    const bool tiles = tiles_cheaper(nb, N, d.H, d.W);
     if (probe_reduce(NN, 1, M - 1, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
-                     o.update_probe ? w.Dp : nullptr, w.acc, HW, sc, s) != cudaSuccess)
+                     o.update_probe ? w.Dp : nullptr, tiles ? nullptr : w.acc, HW, sc, s) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
+    if (tiles && tile_illum_max(d, nb, b0, pos, order, w.valid, w.acc, sc, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if (o.update_probe) {
       if (cudaMemsetAsync(w.dUacc, 0, KNN * sizeof(float2), s) != cudaSuccess ||
           cudaMemsetAsync(w.Du, 0, KNN * sizeof(float), s) != cudaSuccess)
@@ -279,10 +411,10 @@ ptycho_status run_epoch_opr(const ptycho_dims& d, const ptycho_opr_opts& r, floa
     q.update_object = o.update_object; q.update_probe = o.update_probe;
     q.opr_dU = w.dU; q.opr_w = wts; q.K = K; q.p0_s = w.p0;
     if (pass2(N, q, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    if (r.update_weights && opr_weights(N, M, K, nb, b0, order, w.valid, U, w.h, w.o, wts, nullptr, o.lambda_reg,
-                                        (float)r.weight_step, s) != cudaSuccess)
+    if (r.update_weights && opr_weights(N, M, K, nb, b0, order, w.valid, U, w.h, w.o, wts, nullptr, w.gram,
+                                        o.lambda_reg, (float)r.weight_step, s) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
-    if (cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if (clear_acc(tiles, d, nb, b0, pos, order, w.valid, w.acc, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if (probe_update(NN, M - 1, P_rest, w.dP, w.Sp, o.update_probe, sc, sc_next, s) != cudaSuccess ||
         probe_update(NN, K, U, w.dU, nullptr, o.update_probe, sc, sc_next, s) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
@@ -349,8 +481,8 @@ ptycho_status ptycho_adjoint_opr(const ptycho_dims* dims, int32_t K, const float
       return PTYCHO_ERR_CUDA;
     if (opr_reduce(NN, M, K, nb, b0, nullptr, w, wp.h, wp.o, wp.valid, (float2*)g_U, nullptr, s) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
-    if (g_w && opr_weights(N, M, K, nb, b0, nullptr, wp.valid, (const float2*)U, wp.h, wp.o, nullptr, g_w, 0.0,
-                           0.f, s) != cudaSuccess)
+    if (g_w && opr_weights(N, M, K, nb, b0, nullptr, wp.valid, (const float2*)U, wp.h, wp.o, nullptr, g_w,
+                           wp.gram, 0.0, 0.f, s) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
   }
   return PTYCHO_OK;

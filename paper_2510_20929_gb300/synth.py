@@ -203,13 +203,15 @@ def workload_small(N: int = 16, M: int = 2, H: int = 40, W: int = 44, J: int = 1
 
 
 def workload_uneven(n: int = 16, seed: int = 1005, N_choices=(64, 128, 192, 256), J_range=(500, 20000),
-                    counts_range=(1e5, 1e7)):
+                    counts_range=(1e5, 1e7), opr_K: int = 0):
     """Independent reconstructions of uneven size for batched serving: per
     reconstruction a window N drawn from ``N_choices``, J ~ U[J_range], a
     Gaussian probe (1/e^2 diameter D = 0.4 N), a Fermat spiral with spacing
     0.6 D (about 40% overlap), an object of side 2 (c sqrt(J) + N/2 + 2)
     rounded up to a multiple of 32, and total counts log-uniform in
-    ``counts_range`` per pattern set."""
+    ``counts_range`` per pattern set. With ``opr_K`` > 0 each reconstruction
+    also gets ``opr_K`` eigenmodes of its primary probe mode and per-position
+    weights drawn from N(1, 0.1) (orthogonal probe relaxation)."""
     g = rng(seed)
     out = []
     for i in range(n):
@@ -224,4 +226,10 @@ def workload_uneven(n: int = 16, seed: int = 1005, N_choices=(64, 128, 192, 256)
         counts = float(np.exp(g.uniform(math.log(counts_range[0]), math.log(counts_range[1]))))
         out.append(dict(name=f"uneven{i}", H=side, W=side, N=N, M=1, J=J, batch=min(256, J), object=obj,
                         probe=probe, pos=pos, total_counts=counts, counts_per="all"))
+        if opr_K:
+            # relaxed primary mode: K Hermite-Gaussian eigenmodes (waist D/2,
+            # power falling off from the fundamental) with weights N(1, 0.1)
+            powers = [1.0] + [0.3 * 0.6 ** k for k in range(opr_K - 1)]
+            out[-1]["opr_U"] = hg_probe(N, powers, waist=D / 2.0, quad_phase=0.2 / N)
+            out[-1]["opr_w"] = 1.0 + 0.1 * rng(seed * 1000 + 17 + i).standard_normal((J, opr_K))
     return out

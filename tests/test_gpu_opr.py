@@ -136,7 +136,7 @@ def test_lsqml_epoch_opr_poisson_matches_oracle():
     assert max(e.values()) < TOL_EPOCH
 
 
-@pytest.mark.parametrize("N,K,M,H,W,J,step", CLUSTER_CASES)
+@pytest.mark.parametrize("N,K,M,H,W,J,step", CLUSTER_CASES + [(32, 3, 2, 300, 280, 12, 6.0)])
 def test_lsqml_epoch_opr_cluster_windows_match_oracle(N, K, M, H, W, J, step):
     e, moved = _epoch_case(N, K, M, H, W, J, step, 3, True)
     print(f"lsqml_opr N={N} K={K} M={M}:", " ".join(f"{k} {v:.2e}" for k, v in e.items()))
@@ -204,3 +204,33 @@ def test_data_term_opr_autograd_and_adam():
                                          lr_weights=1e-2, update=("object", "eigenmodes", "weights"))
     print("adam opr loss:", hist[0], hist[-1])
     assert hist[-1] < 0.5 * hist[0]
+
+
+OPR_SHAPES = [  # N, K, M, H, W, J, step, batch
+    (32, 3, 2, 72, 76, 16, 6.0, 6), (64, 8, 1, 150, 160, 14, 12.0, 5), (16, 2, 3, 41, 37, 9, 3.0, 9),
+    (128, 4, 1, 290, 300, 9, 30.0, 4), (192, 2, 2, 230, 236, 4, 12.0, 3), (256, 8, 1, 290, 296, 3, 12.0, 2)]
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_opr_batched_matches_oracle_per_reconstruction(graph):
+    import torch
+    from paper_2510_20929_gb300 import api
+    recons, refs, opts, oprs = [], [], [], []
+    for i, (N, K, M, H, W, J, step, B) in enumerate(OPR_SHAPES):
+        h = _host(opr_problem(N=N, K=K, M=M, H=H, W=W, J=J, step=step, seed=60 + i))
+        O, U, w, Pr, pos, I_m = h
+        order = np.random.default_rng(i).permutation(J).astype(np.int32)
+        refs.append(orc.lsqml_epoch_opr(O, U, w, Pr, pos, I_m, order,
+                                        orc.LsqmlOptions(batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6),
+                                        orc.OprOptions(update_weights=True, weight_step=0.8)))
+        recons.append(list(_dev(h)) + [to_dev(order, torch.int32)])
+        opts.append(api.make_opts(batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6, graph=graph))
+        oprs.append(api.make_opr_opts(K, weight_step=0.8))
+    losses = api.lsqml_epoch_opr_batched(recons, opts, oprs).cpu().numpy()
+    for i, ((dO, dU, dw, dPr, _, _, _), (O1, U1, w1, Pr1, L1, _)) in enumerate(zip(recons, refs)):
+        e = [rel(dO.cpu().numpy(), O1), rel(dU.cpu().numpy(), U1), rel(dw.cpu().numpy(), w1),
+             abs(losses[i] - L1) / abs(L1)]
+        if Pr1 is not None:
+            e.append(rel(dPr.cpu().numpy(), Pr1))
+        print(f"opr batched[{i}] N={OPR_SHAPES[i][0]}:", " ".join(f"{x:.2e}" for x in e))
+        assert max(e) < TOL_EPOCH

@@ -109,6 +109,18 @@ def test_lsqml_epoch_matches_oracle(N, M, H, W, J, step, batch, noise):
     assert e["O"] < TOL_EPOCH and e["P"] < TOL_EPOCH
 
 
+@pytest.mark.parametrize("N,M,H,W,J,step,batch", [
+    (16, 2, 200, 180, 12, 4.0, 4),
+    (64, 1, 600, 620, 10, 12.0, 3),
+    (256, 1, 600, 620, 4, 10.0, 2),
+])
+def test_lsqml_epoch_on_a_large_object_matches_oracle(N, M, H, W, J, step, batch):
+    # the batch's tiles cover a small part of the object: the illumination
+    # maximum and the accumulator clear visit only those tiles
+    e = _epoch_case(N, M, H, W, J, step, batch, "gaussian")
+    assert e["loss"] < TOL_FWD and e["alpha"] < TOL_EPOCH and e["O"] < TOL_EPOCH and e["P"] < TOL_EPOCH
+
+
 def test_lsqml_epoch_object_only_matches_oracle():
     e = _epoch_case(32, 2, 72, 76, 16, 6.0, 16, "gaussian", update_probe=False)
     assert e["O"] < TOL_EPOCH and e["P"] == 0.0 and e["alpha"] < TOL_EPOCH
