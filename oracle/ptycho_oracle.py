@@ -237,6 +237,10 @@ class LsqmlOptions:
     eps: float = 0.0           # added to I_pred in the data term
     update_object: bool = True
     update_probe: bool = True
+    update_positions: bool = False   # least-squares position correction per minibatch
+    pos_step: float = 1.0            # relaxation of the position step
+    pos_max_shift: float = 1.0       # per-minibatch clamp of each position component (px)
+    object_per_epoch: bool = False   # accumulate the object update over the epoch, apply once
 
 
 def step_solve(A11, A12, A22, b1, b2, lam):
@@ -253,6 +257,39 @@ def step_solve(A11, A12, A22, b1, b2, lam):
     if det > 0.0:
         return (a22 * b1 - A12 * b2) / det, (a11 * b2 - A12 * b1) / det
     return (b1 / a11 if a11 > 0 else 0.0), (b2 / a22 if a22 > 0 else 0.0)
+
+
+POS_MARGIN = 1.0 / 64.0   # corrected positions stay this far inside the bounds rule's upper limit
+
+
+def position_step(O, P, r, g, lam):
+    """Least-squares shift of one scan position (position correction, Sec. 1 / Sec. 2.1).
+
+    A shift dr moves the exit waves by P_k (d o / d r) dr; the step is
+    argmin_dr sum_k ||chi_k - P_k (d_y dr_y + d_x dr_x)||^2 with the patch
+    derivatives d = d o_j / d r of the bilinear extraction. Its normal
+    equations sum the modes into Sp = sum_k |P_k|^2 and g = sum_k conj(P_k) chi_k:
+      A = sum_p Sp [|d_y|^2, Re(conj(d_y) d_x); ., |d_x|^2],
+      b = sum_p [Re(conj(d_y) g), Re(conj(d_x) g)],
+    solved like the step sizes (damping lam tr(A)/2, 1x1 fallbacks).
+    """
+    N = P.shape[-1]
+    d_y, d_x = extract_dr(O, r, N)
+    Sp = np.sum(np.abs(P) ** 2, axis=0)
+    A11 = float(np.sum(Sp * np.abs(d_y) ** 2))
+    A12 = float(np.sum(Sp * np.real(np.conj(d_y) * d_x)))
+    A22 = float(np.sum(Sp * np.abs(d_x) ** 2))
+    b1 = float(np.real(np.sum(np.conj(d_y) * g)))
+    b2 = float(np.real(np.sum(np.conj(d_x) * g)))
+    return np.array(step_solve(A11, A12, A22, b1, b2, lam))
+
+
+def corrected_position(r, dr, opts: LsqmlOptions, N: int, H: int, W: int):
+    """r + pos_step * clip(dr, +-pos_max_shift), kept inside the bounds rule."""
+    m = opts.pos_max_shift
+    new = np.asarray(r, np.float64) + opts.pos_step * np.clip(dr, -m, m)
+    return np.array([np.clip(new[0], N / 2.0, H - N / 2.0 - POS_MARGIN),
+                     np.clip(new[1], N / 2.0, W - N / 2.0 - POS_MARGIN)])
 
 
 def lsqml_batch(O, P, pos, I_m, idx, opts: LsqmlOptions, record: dict | None = None):
@@ -323,36 +360,67 @@ def lsqml_batch(O, P, pos, I_m, idx, opts: LsqmlOptions, record: dict | None = N
         alpha[i] = step_solve(A11, A12, A22, b1, b2, opts.lam)
 
     O_new = O.copy()
+    dO = np.zeros((H, W), np.complex128)
     if opts.update_object:
         upd = np.zeros((H, W), np.complex128)
         for i, j in enumerate(idx):
             upd += scatter(alpha[i, 0] * g_all[i], pos[j], H, W)
-        O_new = O + upd / (illum + delta_O)
+        dO = upd / (illum + delta_O)
+        if not opts.object_per_epoch:
+            O_new = O + dO
     P_new = P.copy()
     if opts.update_probe:
         P_new = P + float(np.mean(alpha[:, 1])) * dP
+    pos_new = np.array(pos, np.float64, copy=True)
+    if opts.update_positions:   # shifts from this minibatch's chi, at the object it started from
+        for i, j in enumerate(idx):
+            dr = position_step(O, P, pos[j], g_all[i], opts.lam)
+            pos_new[j] = corrected_position(pos[j], dr, opts, N, H, W)
 
     if record is not None:
         record.update(dict(dO_acc=dO_acc, illum=illum, dP_acc=dP_acc, Dp=Dp,
                            delta_O=delta_O, delta_P=delta_P, dO_hat=dO_hat, dP=dP,
-                           chi=np.stack(chi_all), g=np.stack(g_all), alpha=alpha))
+                           chi=np.stack(chi_all), g=np.stack(g_all), alpha=alpha, dO=dO, pos=pos_new))
     return O_new, P_new, loss, alpha
 
 
 def lsqml_epoch(O, P, pos, I_m, order, opts: LsqmlOptions):
-    """One epoch: minibatches of ``opts.batch`` positions taken from ``order`` in turn."""
+    """One epoch: minibatches of ``opts.batch`` positions taken from ``order`` in turn.
+
+    Returns (O, P, loss, alpha); :func:`lsqml_epoch_state` also returns the
+    corrected positions.
+    """
+    O, P, _, loss, alpha = lsqml_epoch_state(O, P, pos, I_m, order, opts)
+    return O, P, loss, alpha
+
+
+def lsqml_epoch_state(O, P, pos, I_m, order, opts: LsqmlOptions):
+    """One epoch; returns (O, P, pos, loss, alpha).
+
+    With ``opts.object_per_epoch`` (the mode LSQML takes with the compact
+    sampler, Sec. 2.2) every minibatch sees the object the epoch started from;
+    the minibatches' object updates are summed and applied once at the end.
+    The probe and (with ``update_positions``) the positions change per minibatch.
+    """
     O = np.asarray(O, np.complex128).copy()
     P = np.asarray(P, np.complex128).copy()
+    pos = np.asarray(pos, np.float64).copy()
     order = np.asarray(order)
     J = order.shape[0]
     loss = 0.0
     alpha = np.zeros((pos.shape[0], 2), np.float64)
+    dO_epoch = np.zeros_like(O)
     for b0 in range(0, J, opts.batch):
         idx = order[b0:b0 + opts.batch]
-        O, P, l, a = lsqml_batch(O, P, pos, I_m, idx, opts)
+        rec = {}
+        O, P, l, a = lsqml_batch(O, P, pos, I_m, idx, opts, rec)
+        pos = rec["pos"]
+        dO_epoch += rec["dO"]
         loss += l
         alpha[idx] = a
-    return O, P, loss, alpha
+    if opts.object_per_epoch:
+        O = O + dO_epoch
+    return O, P, pos, loss, alpha
 
 
 def align_global_phase(O, O_ref, mask=None):

@@ -74,3 +74,20 @@ def test_weight_update_of_the_wrong_sign_is_caught(monkeypatch):
     real = orc.weight_solve
     monkeypatch.setattr(orc, "weight_solve", lambda A, b, lam: -real(A, b, lam))
     _fails(pins.test_lsqml_opr_truth_is_a_fixed_point_and_weights_converge)
+
+
+def test_position_step_with_swapped_derivatives_is_caught(monkeypatch):
+    real = orc.extract_dr
+    monkeypatch.setattr(orc, "extract_dr", lambda O, r, N: real(O, r, N)[::-1])
+    _fails(pins.test_position_correction_converges_to_the_true_positions)
+
+
+def test_per_epoch_update_applied_per_batch_is_caught(monkeypatch):
+    real = orc.lsqml_batch
+
+    def per_batch(O, P, pos, I_m, idx, opts, record=None):
+        import dataclasses
+        return real(O, P, pos, I_m, idx, dataclasses.replace(opts, object_per_epoch=False), record)
+
+    monkeypatch.setattr(orc, "lsqml_batch", per_batch)
+    _fails(pins.test_per_epoch_object_update_does_not_depend_on_the_batch_order)

@@ -435,3 +435,74 @@ def test_lsqml_opr_truth_is_a_fixed_point_and_weights_converge():
     for _ in range(12):   # linear convergence, about 0.77 per epoch
         _, _, w, _, L, _ = orc.lsqml_epoch_opr(O, U, w, P_rest, pos, I_m, order, opts, opr)
     assert np.linalg.norm(w - w_true) < 0.05 * e0
+
+
+# --------------------------------------------------------------------------- position correction, per-epoch object update
+def test_position_step_solves_the_least_squares_problem():
+    # the closed-form 2x2 system equals numpy's least squares on the stacked
+    # real system sum_k ||chi_k - P_k (d_y dr_y + d_x dr_x)||^2
+    g = np.random.default_rng(21)
+    O = synth.make_object(40, 40, 4, phase_sigma=1.5)
+    P = crandn(g, 2, 12, 12)
+    r = np.array([19.3, 20.6])
+    chi = crandn(g, 2, 12, 12)
+    d_y, d_x = orc.extract_dr(O, r, 12)
+    cols = [np.concatenate([np.real(P * d[None]).ravel(), np.imag(P * d[None]).ravel()]) for d in (d_y, d_x)]
+    rhs = np.concatenate([np.real(chi).ravel(), np.imag(chi).ravel()])
+    ref = np.linalg.lstsq(np.stack(cols, axis=1), rhs, rcond=None)[0]
+    got = orc.position_step(O, P, r, np.sum(np.conj(P) * chi, axis=0), 0.0)
+    assert np.max(np.abs(got - ref)) < 1e-10 * np.max(np.abs(ref))
+
+
+def _position_problem(seed=31):
+    N, H, W = 16, 64, 64
+    O = synth.make_object(H, W, seed, phase_sigma=2.0, amp_sigma=2.0)
+    P = synth.gaussian_probe(N, sigma=3.0, quad_phase=0.05) * 5.0
+    pos_true = synth.raster_positions(6, 6, 5.0, (H / 2, W / 2), 0.4, seed)
+    I_m = orc.forward(O, P, pos_true)
+    g = np.random.default_rng(seed)
+    pos0 = pos_true + g.uniform(-1.0, 1.0, pos_true.shape)
+    return O, P, pos_true, pos0, I_m
+
+
+def test_position_correction_converges_to_the_true_positions():
+    O, P, pos_true, pos, I_m = _position_problem()
+    opts = orc.LsqmlOptions(batch=6, eps=0.0, update_object=False, update_probe=False, update_positions=True,
+                            pos_step=1.0, pos_max_shift=1.0)
+    order = synth.random_order(pos.shape[0], 2)
+    e0 = np.sqrt(np.mean((pos - pos_true) ** 2))
+    for _ in range(15):   # linear convergence, about 0.75 per epoch
+        _, _, pos, _, _ = orc.lsqml_epoch_state(O, P, pos, I_m, order, opts)
+    e = np.sqrt(np.mean((pos - pos_true) ** 2))
+    assert e < 0.05 * e0
+    # the truth is a fixed point
+    _, _, p1, _, _ = orc.lsqml_epoch_state(O, P, pos_true, I_m, order, opts)
+    assert np.max(np.abs(p1 - pos_true)) < 1e-9
+
+
+def test_per_epoch_object_update_with_one_batch_is_the_per_batch_update():
+    O_true, P, pos, I_m, O, _ = _noiseless_problem(0.0)
+    order = synth.random_order(pos.shape[0], 8)
+    a = orc.LsqmlOptions(batch=pos.shape[0], eps=1e-12, delta_o=0.1, delta_p=0.1)
+    b = orc.LsqmlOptions(batch=pos.shape[0], eps=1e-12, delta_o=0.1, delta_p=0.1, object_per_epoch=True)
+    Oa, Pa, La, _ = orc.lsqml_epoch(O, P, pos, I_m, order, a)
+    Ob, Pb, Lb, _ = orc.lsqml_epoch(O, P, pos, I_m, order, b)
+    assert np.max(np.abs(Oa - Ob)) < 1e-12 and np.max(np.abs(Pa - Pb)) < 1e-12 and La == Lb
+
+
+def test_per_epoch_object_update_does_not_depend_on_the_batch_order():
+    # every minibatch sees the epoch's starting object and (without probe
+    # updates) the same probe, so the summed update ignores the batch order;
+    # the per-batch update does not
+    O_true, P, pos, I_m, O, _ = _noiseless_problem(0.0)
+    order = synth.random_order(pos.shape[0], 9)
+    B = 7
+    batches = [order[i:i + B] for i in range(0, len(order), B)]
+    # the full groups in reverse order; the ragged last group stays last so that
+    # the grouping is unchanged
+    reordered = np.concatenate([b for b in batches if len(b) == B][::-1] + [b for b in batches if len(b) < B])
+    for per_epoch in (True, False):
+        o = orc.LsqmlOptions(batch=B, eps=1e-12, delta_o=0.1, update_probe=False, object_per_epoch=per_epoch)
+        diff = np.max(np.abs(orc.lsqml_epoch(O, P, pos, I_m, order, o)[0]
+                             - orc.lsqml_epoch(O, P, pos, I_m, reordered, o)[0]))
+        assert (diff < 1e-12) if per_epoch else (diff > 1e-6)
