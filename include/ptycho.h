@@ -73,16 +73,24 @@ typedef enum {
 } ptycho_noise;
 
 typedef struct {
-  int32_t noise;          /* PTYCHO_NOISE_GAUSSIAN or PTYCHO_NOISE_POISSON */
-  int32_t batch;          /* minibatch size B >= 1 */
-  int32_t update_object;  /* 0/1 */
-  int32_t update_probe;   /* 0/1 */
-  int32_t flags;          /* PTYCHO_FLAG_* bits */
-  int32_t reserved[3];    /* must be zero */
-  double delta_o;         /* object preconditioner damping, relative to max(illumination) */
-  double delta_p;         /* probe preconditioner damping, relative to max(sum_j |o_j|^2) */
-  double lambda_reg;      /* 2x2 step-size Tikhonov term, relative to trace/2 */
-  double eps;             /* added to the predicted intensity in the data term */
+  int32_t noise;            /* PTYCHO_NOISE_GAUSSIAN or PTYCHO_NOISE_POISSON */
+  int32_t batch;            /* minibatch size B >= 1 */
+  int32_t update_object;    /* 0/1 */
+  int32_t update_probe;     /* 0/1 */
+  int32_t flags;            /* PTYCHO_FLAG_* bits */
+  int32_t update_positions; /* 0/1: least-squares position correction per minibatch; the
+                               positions array is then updated in place */
+  int32_t object_per_epoch; /* 0/1: accumulate the object update over the epoch and apply it
+                               once at its end (the update cadence LSQML takes with the
+                               compact sampler, Sec. 2.2); needs the larger workspace of
+                               ptycho_workspace_bytes_opts */
+  int32_t reserved;         /* must be zero */
+  double delta_o;           /* object preconditioner damping, relative to max(illumination) */
+  double delta_p;           /* probe preconditioner damping, relative to max(sum_j |o_j|^2) */
+  double lambda_reg;        /* 2x2 step-size Tikhonov term, relative to trace/2 */
+  double eps;               /* added to the predicted intensity in the data term */
+  double pos_step;          /* relaxation of the position step (1 = the least-squares step) */
+  double pos_max_shift;     /* clamp of each component of a minibatch's position step, px */
 } ptycho_lsqml_opts;
 
 /* opts->flags: capture the epoch's launch sequence into a CUDA graph on the
@@ -104,8 +112,11 @@ int32_t ptycho_tuning_read(const ptycho_dims* dims, int32_t batch, int32_t* vari
 
 /* Bytes of workspace needed by every entry point below for these dimensions
  * and minibatch size (ptycho_adjoint processes positions in chunks of
- * `batch`). Returns 0 for unsupported dimensions. */
+ * `batch`) with object_per_epoch = 0. Returns 0 for unsupported dimensions.
+ * ptycho_workspace_bytes_opts gives the size for a set of epoch options
+ * (object_per_epoch adds an H x W complex64 epoch accumulator). */
 size_t ptycho_workspace_bytes(const ptycho_dims* dims, int32_t batch);
+size_t ptycho_workspace_bytes_opts(const ptycho_dims* dims, const ptycho_lsqml_opts* opts);
 
 /* Clears the workspace header (its device status word). Call once on a fresh
  * workspace before the first entry point that uses it. */
@@ -140,9 +151,18 @@ ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const
  * object and probe are updated in place. loss (float64 scalar, may be NULL)
  * receives the epoch's data term summed over positions, each evaluated at the
  * state its minibatch started from. alpha (float64 [J, 2], may be NULL)
- * receives (alpha_O, alpha_P) per position. */
+ * receives (alpha_O, alpha_P) per position.
+ * With opts->update_positions each position of a minibatch also moves by
+ * pos_step times its least-squares shift (position correction, Sec. 1 /
+ * Sec. 2.1): argmin_dr sum_k ||chi_jk - P_k (d o_j / d r) dr||^2 over the
+ * bilinear patch derivatives at the object the minibatch started from,
+ * solved in FP64 like the step sizes, each component clamped to
+ * +-pos_max_shift and the result kept inside the bounds rule (at most
+ * H - N/2 - 1/64). With opts->object_per_epoch every minibatch sees the
+ * epoch's starting object and the object updates are applied together at
+ * the end of the epoch. */
 ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* probe,
-                                 const float* pos, const float* meas, const int32_t* order,
+                                 float* pos, const float* meas, const int32_t* order,
                                  const ptycho_lsqml_opts* opts, double* loss, double* alpha,
                                  void* ws, size_t ws_bytes, void* stream);
 
@@ -160,19 +180,21 @@ ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* 
  * with ptycho_status_read(section). */
 size_t ptycho_workspace_bytes_batched(int32_t n, const ptycho_dims* dims, const ptycho_lsqml_opts* opts);
 ptycho_status ptycho_lsqml_epoch_batched(int32_t n, const ptycho_dims* dims, float* const* objects,
-                                         float* const* probes, const float* const* pos,
+                                         float* const* probes, float* const* pos,
                                          const float* const* meas, const int32_t* const* orders,
                                          const ptycho_lsqml_opts* opts, double* losses, void* ws,
                                          size_t ws_bytes, void* stream);
 
 /* Same epoch with HOST buffers: copies pos, meas and order (and the object and
  * probe) into device staging areas carved from `ws` (ws_bytes must be at least
- * ptycho_host_workspace_bytes()), runs the epoch on `stream`, copies object,
- * probe and loss back, and synchronises the stream before returning. Host
- * buffers should be pinned for full copy bandwidth. */
+ * ptycho_host_workspace_bytes(), or ptycho_host_workspace_bytes_opts() for
+ * these options), runs the epoch on `stream`, copies object, probe, loss (and
+ * the positions when they are corrected) back, and synchronises the stream
+ * before returning. Host buffers should be pinned for full copy bandwidth. */
 size_t ptycho_host_workspace_bytes(const ptycho_dims* dims, int32_t batch);
+size_t ptycho_host_workspace_bytes_opts(const ptycho_dims* dims, const ptycho_lsqml_opts* opts);
 ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, float* probe,
-                                      const float* pos, const float* meas, const int32_t* order,
+                                      float* pos, const float* meas, const int32_t* order,
                                       const ptycho_lsqml_opts* opts, double* loss, void* ws,
                                       size_t ws_bytes, void* stream);
 
@@ -185,7 +207,7 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
  * every GPU loading the library keeps until the process exits. The paper has
  * no counterpart: this is an interface for embedding the library.
  * - Returns PTYCHO_ERR_TOO_LARGE, before touching the device, when
- *   ptycho_workspace_bytes(dims, opts->batch) exceeds PTYCHO_STATIC_WS_BYTES.
+ *   ptycho_workspace_bytes_opts(dims, opts) exceeds PTYCHO_STATIC_WS_BYTES.
  * - The first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make it before any stream
  *   capture.
@@ -196,7 +218,7 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
  *   ptycho_status_read() would. No device memory is allocated. */
 #define PTYCHO_STATIC_WS_BYTES (64u * 1024u * 1024u)
 ptycho_status ptycho_lsqml_epoch_static(const ptycho_dims* dims, float* object, float* probe,
-                                        const float* pos, const float* meas, const int32_t* order,
+                                        float* pos, const float* meas, const int32_t* order,
                                         const ptycho_lsqml_opts* opts, double* loss, double* alpha,
                                         void* stream);
 
@@ -248,7 +270,8 @@ ptycho_status ptycho_adjoint_opr(const ptycho_dims* dims, int32_t K, const float
  * lambda_reg tr(A)/K) of chi_j0 with the exit waves U_m o_j, taken with this
  * minibatch's U and chi. U, w, P_rest and the object are updated in place.
  * PTYCHO_FLAG_GRAPH is honoured; PTYCHO_FLAG_AUTOTUNE is ignored (default CTA
- * sizes). */
+ * sizes); update_positions and object_per_epoch are not supported with OPR
+ * (PTYCHO_ERR_UNSUPPORTED). */
 ptycho_status ptycho_lsqml_epoch_opr(const ptycho_dims* dims, const ptycho_opr_opts* opr, float* object,
                                      float* U, float* w, float* P_rest, const float* pos, const float* meas,
                                      const int32_t* order, const ptycho_lsqml_opts* opts, double* loss,

@@ -49,9 +49,11 @@ class Dims(ctypes.Structure):
 class LsqmlOpts(ctypes.Structure):
     _fields_ = [("noise", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("update_object", ctypes.c_int32), ("update_probe", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+                ("flags", ctypes.c_int32), ("update_positions", ctypes.c_int32),
+                ("object_per_epoch", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("delta_o", ctypes.c_double), ("delta_p", ctypes.c_double),
-                ("lambda_reg", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("lambda_reg", ctypes.c_double), ("eps", ctypes.c_double),
+                ("pos_step", ctypes.c_double), ("pos_max_shift", ctypes.c_double)]
 
 
 class OprOpts(ctypes.Structure):
@@ -89,6 +91,8 @@ def lib() -> ctypes.CDLL:
             "ptycho_lsqml_epoch_opr_batched": (ctypes.c_int, [ctypes.c_int32, dims_p, opr_p, _P, _P, _P, _P, _P,
                                                               _P, _P, opts_p, _P, _P, ctypes.c_size_t, _P]),
             "ptycho_workspace_bytes": (ctypes.c_size_t, [dims_p, ctypes.c_int32]),
+            "ptycho_workspace_bytes_opts": (ctypes.c_size_t, [dims_p, opts_p]),
+            "ptycho_host_workspace_bytes_opts": (ctypes.c_size_t, [dims_p, opts_p]),
             "ptycho_host_workspace_bytes": (ctypes.c_size_t, [dims_p, ctypes.c_int32]),
             "ptycho_workspace_init": (ctypes.c_int, [_P, ctypes.c_size_t, _P]),
             "ptycho_forward": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
@@ -190,11 +194,15 @@ class Workspace:
 _ws_cache: dict = {}
 
 
-def workspace(dims: Dims, batch: int, device, host: bool = False, opr_K: int = 0) -> Workspace:
+def workspace(dims: Dims, batch: int, device, host: bool = False, opr_K: int = 0, opts=None) -> Workspace:
     """A cached workspace large enough for these dimensions and minibatch size
-    (and, with opr_K > 0, for the relaxed-probe entry points with K eigenmodes)."""
+    (with opr_K > 0, for the relaxed-probe entry points with K eigenmodes; with
+    ``opts``, for an LSQML epoch with those options)."""
     if opr_K > 0:
         need = lib().ptycho_workspace_bytes_opr(ctypes.byref(dims), int(opr_K), int(batch))
+    elif opts is not None:
+        fn = lib().ptycho_host_workspace_bytes_opts if host else lib().ptycho_workspace_bytes_opts
+        need = fn(ctypes.byref(dims), ctypes.byref(opts))
     else:
         fn = lib().ptycho_host_workspace_bytes if host else lib().ptycho_workspace_bytes
         need = fn(ctypes.byref(dims), int(batch))
@@ -256,20 +264,26 @@ def adjoint(obj, probe, pos, meas, noise="gaussian", eps: float = 0.0, batch: in
 
 def make_opts(noise="gaussian", batch: int = 256, delta_o: float = 0.1, delta_p: float = 0.1,
               lam: float = 1e-6, eps: float = 1e-9, update_object: bool = True,
-              update_probe: bool = True, graph: bool = False, autotune: bool = False) -> LsqmlOpts:
+              update_probe: bool = True, graph: bool = False, autotune: bool = False,
+              update_positions: bool = False, pos_step: float = 1.0, pos_max_shift: float = 1.0,
+              object_per_epoch: bool = False) -> LsqmlOpts:
     o = LsqmlOpts()
     o.flags = (FLAG_GRAPH if graph else 0) | (FLAG_AUTOTUNE if autotune else 0)
     o.noise = _NOISE[noise] if isinstance(noise, str) else int(noise)
     o.batch = int(batch)
     o.update_object = int(bool(update_object))
     o.update_probe = int(bool(update_probe))
+    o.update_positions = int(bool(update_positions))
+    o.object_per_epoch = int(bool(object_per_epoch))
     o.delta_o, o.delta_p, o.lambda_reg, o.eps = float(delta_o), float(delta_p), float(lam), float(eps)
+    o.pos_step, o.pos_max_shift = float(pos_step), float(pos_max_shift)
     return o
 
 
 def lsqml_epoch(obj, probe, pos, meas, order=None, opts: LsqmlOpts | None = None, *,
                 want_alpha: bool = False, check: bool = True, **kw):
-    """One LSQML epoch, updating ``obj`` and ``probe`` in place.
+    """One LSQML epoch, updating ``obj`` and ``probe`` (and, with
+    ``update_positions``, ``pos``) in place.
 
     Returns (loss, alpha): loss is a float64 device scalar; alpha a float64
     [J, 2] device tensor of (alpha_O, alpha_P) or None.
@@ -285,7 +299,7 @@ def lsqml_epoch(obj, probe, pos, meas, order=None, opts: LsqmlOpts | None = None
         _need(order, "order", torch.int32, (d.J,), device=obj.device)
     loss = torch.zeros((), dtype=torch.float64, device=obj.device)
     alpha = torch.zeros((pos.shape[0], 2), dtype=torch.float64, device=obj.device) if want_alpha else None
-    ws = workspace(d, opts.batch, obj.device)
+    ws = workspace(d, opts.batch, obj.device, opts=opts)
     _check(lib().ptycho_lsqml_epoch(ctypes.byref(d), _ptr(obj), _ptr(probe), _ptr(pos), _ptr(meas),
                                     _ptr(order), ctypes.byref(opts), _ptr(loss), _ptr(alpha),
                                     _P(ws.ptr), ws.nbytes, _stream()), "ptycho_lsqml_epoch")
@@ -346,14 +360,15 @@ def lsqml_epoch_batched(recons, opts, *, check: bool = True):
         off = 0
         for i in range(n):
             _check(lib().ptycho_status_read(_P(ws.ptr + off), _stream()), f"ptycho_lsqml_epoch_batched[{i}]")
-            off += lib().ptycho_workspace_bytes(ctypes.byref(dims[i]), OA[i].batch)
+            off += lib().ptycho_workspace_bytes_opts(ctypes.byref(dims[i]), ctypes.byref(OA[i]))
     return losses
 
 
 def lsqml_epoch_host(obj, probe, pos, meas, order, opts: LsqmlOpts, device=None):
     """LSQML epoch on HOST (CPU, ideally pinned) tensors through the host-buffer entry point.
 
-    ``obj`` and ``probe`` (complex64, CPU) are updated in place; returns the loss.
+    ``obj`` and ``probe`` (complex64, CPU; ``pos`` too with update_positions)
+    are updated in place; returns the loss.
     """
     for t, name, dt in ((obj, "object", torch.complex64), (probe, "probe", torch.complex64),
                         (pos, "positions", torch.float32), (meas, "meas", torch.float32)):
@@ -363,7 +378,7 @@ def lsqml_epoch_host(obj, probe, pos, meas, order, opts: LsqmlOpts, device=None)
         raise ValueError("order must be a CPU int32 tensor")
     device = device or torch.device("cuda", torch.cuda.current_device())
     d = dims_of(obj, probe, pos)
-    ws = workspace(d, opts.batch, device, host=True)
+    ws = workspace(d, opts.batch, device, host=True, opts=opts)
     loss = ctypes.c_double(0.0)
     _check(lib().ptycho_lsqml_epoch_host(ctypes.byref(d), _ptr(obj), _ptr(probe), _ptr(pos), _ptr(meas),
                                          _ptr(order), ctypes.byref(opts), ctypes.byref(loss),

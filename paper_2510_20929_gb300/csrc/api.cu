@@ -185,12 +185,51 @@ __global__ void k_tile_clear(int N, int H, int W, int J, const float* pos, const
     acc[(size_t)(ty + i / N1) * W + tx + i % N1] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Position correction: one thread per slot solves the least-squares shift
+// from its five sums (FP64, the damping and fallbacks of the step sizes),
+// clamps each component to +-max_shift, moves the position by step times it
+// and keeps it inside the bounds rule, at most extent - N/2 - 1/64.
+__global__ void k_pos_apply(int nb, int b0, const int* __restrict__ order, const int* __restrict__ valid,
+                            const double* __restrict__ possum, float* pos, int N, int H, int W, double lam,
+                            double step, double max_shift) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= nb || !valid[slot]) return;
+  const int e = b0 + slot;
+  const int j = order ? order[e] : e;
+  const double* v = possum + (size_t)slot * 5;
+  const double a11 = v[0], a12 = v[1], a22 = v[2], r1 = v[3], r2 = v[4];
+  const double tr = 0.5 * (a11 + a22);
+  const double d11 = a11 + lam * tr, d22 = a22 + lam * tr;
+  const double det = d11 * d22 - a12 * a12;
+  double dy, dx;
+  if (det > 0.0) {
+    dy = (d22 * r1 - a12 * r2) / det;
+    dx = (d11 * r2 - a12 * r1) / det;
+  } else {
+    dy = d11 > 0.0 ? r1 / d11 : 0.0;
+    dx = d22 > 0.0 ? r2 / d22 : 0.0;
+  }
+  dy = fmin(fmax(dy, -max_shift), max_shift);
+  dx = fmin(fmax(dx, -max_shift), max_shift);
+  const double lo = 0.5 * N, margin = 1.0 / 64.0;
+  const double y = fmin(fmax((double)pos[2 * j] + step * dy, lo), (double)H - lo - margin);
+  const double x = fmin(fmax((double)pos[2 * j + 1] + step * dx, lo), (double)W - lo - margin);
+  pos[2 * j] = (float)y;
+  pos[2 * j + 1] = (float)x;
+}
+
+// O += dO (the epoch's accumulated object update).
+__global__ void k_add_plane(size_t n, float2* O, const float2* __restrict__ dO) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+    O[p] = cadd(O[p], dO[p]);
+}
+
 // ---------------------------------------------------------------------------
 // Workspace layout.
 // ---------------------------------------------------------------------------
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-Layout make_layout(const ptycho_dims& d, int B, int K) {
+Layout make_layout(const ptycho_dims& d, int B, int K, bool epoch_object) {
   Layout L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -220,8 +259,14 @@ Layout make_layout(const ptycho_dims& d, int B, int K) {
     L.dU = take((size_t)K * NN * sizeof(float2));
     L.gram = take((size_t)B * (OPR_KMAX * (OPR_KMAX + 1) / 2 + OPR_KMAX) * sizeof(double));   // weight-step sums
   }
+  L.possum = take((size_t)B * 5 * sizeof(double));
+  L.dOe = epoch_object ? take(HW * sizeof(float2)) : 0;
   L.total = off;
   return L;
+}
+
+Layout layout_for(const ptycho_dims& d, const ptycho_lsqml_opts& o) {
+  return make_layout(d, o.batch, 0, o.object_per_epoch != 0);
 }
 
 static bool supported_N(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 192 || N == 256; }
@@ -424,6 +469,8 @@ Ptrs carve(void* ws, const Layout& L) {
   p.Du = L.Du ? (float*)(b + L.Du) : nullptr;
   p.dU = L.dU ? (float2*)(b + L.dU) : nullptr;
   p.gram = L.gram ? (double*)(b + L.gram) : nullptr;
+  p.possum = (double*)(b + L.possum);
+  p.dOe = L.dOe ? (float2*)(b + L.dOe) : nullptr;
   return p;
 }
 
@@ -481,16 +528,18 @@ static ptycho_status autotune(const ptycho_dims& d, float2* obj, float2* probe, 
   return init_epoch(NN, M, probe, w.Sp, w.hdr, s) == cudaSuccess ? PTYCHO_OK : PTYCHO_ERR_CUDA;
 }
 
-ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const float* pos,
+ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float* pos,
                                const float* meas, const int32_t* order, const ptycho_lsqml_opts& o,
                                double* loss, double* alpha, void* ws, cudaStream_t s) {
   const int B = o.batch, N = d.N, M = d.M, NN = N * N, HW = d.H * d.W;
-  const Layout L = make_layout(d, B);
+  const Layout L = layout_for(d, o);
   Ptrs w = carve(ws, L);
   cudaError_t e = cudaSuccess;
   if (loss && (e = cudaMemsetAsync(loss, 0, sizeof(double), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
   if ((e = cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
   if ((e = init_epoch(NN, M, probe, w.Sp, w.hdr, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  if (o.object_per_epoch && (e = cudaMemsetAsync(w.dOe, 0, (size_t)HW * sizeof(float2), s)) != cudaSuccess)
+    return PTYCHO_ERR_CUDA;
   int dev = 0;
   cudaGetDevice(&dev);
   TuneEntry tune{{dev, N, M, d.H, d.W, B}, 0, 0, {0.f, 0.f}, {0.f, 0.f}};
@@ -517,6 +566,11 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const 
     a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
     a.Sp = w.Sp; a.acc = w.acc;
     a.loss = loss; a.status = &w.hdr->status;
+    if (o.update_positions) {
+      a.possum = w.possum;
+      if ((e = cudaMemsetAsync(w.possum, 0, (size_t)nb * 5 * sizeof(double), s)) != cudaSuccess)
+        return PTYCHO_ERR_CUDA;
+    }
     if ((e = pass1(N, a, s, tune.v1)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     const bool tiles = tiles_cheaper(nb, N, d.H, d.W);
     if ((e = probe_reduce(NN, 0, M, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
@@ -532,13 +586,22 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const 
     q.pos = pos; q.order = order; q.b0 = b0; q.nb = nb;
     q.o_s = w.o; q.g_s = w.g; q.h_s = w.h; q.valid = w.valid;
     q.acc = w.acc; q.Sp = w.Sp; q.Cp = w.Cp; q.Sdp = w.Sdp; q.dP = w.dP;
-    q.obj = obj; q.alpha_out = alpha; q.sc = sc;
+    q.obj = o.object_per_epoch ? w.dOe : obj; q.alpha_out = alpha; q.sc = sc;
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
     if ((e = pass2(N, q, s, tune.v2)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if ((e = clear_acc(tiles, d, nb, b0, pos, order, w.valid, w.acc, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if ((e = probe_update(NN, M, probe, w.dP, w.Sp, o.update_probe, sc, sc_next, s)) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
+    if (o.update_positions) {   // last: pass 2 and the tile clear read this batch's positions
+      k_pos_apply<<<(nb + 127) / 128, 128, 0, s>>>(nb, b0, order, w.valid, w.possum, pos, N, d.H, d.W,
+                                                   o.lambda_reg, o.pos_step, o.pos_max_shift);
+      if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    }
+  }
+  if (o.object_per_epoch) {
+    k_add_plane<<<grid_for((size_t)HW, 256, 4 * 152), 256, 0, s>>>((size_t)HW, obj, w.dOe);
+    if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
   }
   return PTYCHO_OK;
 }
@@ -546,8 +609,11 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const 
 ptycho_status check_opts(const ptycho_lsqml_opts* o) {
   if (!o || o->batch < 1 || (o->noise != PTYCHO_NOISE_GAUSSIAN && o->noise != PTYCHO_NOISE_POISSON))
     return PTYCHO_ERR_ARG;
-  for (int i = 0; i < 3; ++i)
-    if (o->reserved[i] != 0) return PTYCHO_ERR_ARG;
+  if (o->reserved != 0) return PTYCHO_ERR_ARG;
+  if ((o->update_positions != 0 && o->update_positions != 1) || (o->object_per_epoch != 0 && o->object_per_epoch != 1))
+    return PTYCHO_ERR_ARG;
+  if (!(o->pos_step >= 0.0) || !(o->pos_step < 1e30) || !(o->pos_max_shift >= 0.0) || !(o->pos_max_shift < 1e30))
+    return PTYCHO_ERR_ARG;
   if (o->flags & ~(int32_t)(PTYCHO_FLAG_GRAPH | PTYCHO_FLAG_AUTOTUNE)) return PTYCHO_ERR_ARG;
   if (!(o->delta_o >= 0.0) || !(o->delta_p >= 0.0) || !(o->lambda_reg >= 0.0) || !(o->eps >= 0.0))
     return PTYCHO_ERR_ARG;
@@ -599,6 +665,11 @@ ptycho_status ptycho_workspace_init(void* ws, size_t ws_bytes, void* stream) {
 size_t ptycho_workspace_bytes(const ptycho_dims* dims, int32_t batch) {
   if (check_dims(dims) != PTYCHO_OK || batch < 1) return 0;
   return make_layout(*dims, batch).total;
+}
+
+size_t ptycho_workspace_bytes_opts(const ptycho_dims* dims, const ptycho_lsqml_opts* opts) {
+  if (check_dims(dims) != PTYCHO_OK || check_opts(opts) != PTYCHO_OK) return 0;
+  return layout_for(*dims, *opts).total;
 }
 
 ptycho_status ptycho_forward(const ptycho_dims* dims, const float* object, const float* probe, const float* pos,
@@ -654,14 +725,14 @@ ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const
   return PTYCHO_OK;
 }
 
-ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* probe, const float* pos,
+ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* probe, float* pos,
                                  const float* meas, const int32_t* order, const ptycho_lsqml_opts* opts,
                                  double* loss, double* alpha, void* ws, size_t ws_bytes, void* stream) {
   ptycho_status st = check_dims(dims);
   if (st != PTYCHO_OK) return st;
   if ((st = check_opts(opts)) != PTYCHO_OK) return st;
   if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
-  const Layout L = make_layout(*dims, opts->batch);
+  const Layout L = layout_for(*dims, *opts);
   if ((st = check_ws(ws, ws_bytes, L.total)) != PTYCHO_OK) return st;
   auto body = [&](cudaStream_t s) {
     return run_epoch(*dims, (float2*)object, (float2*)probe, pos, meas, order, *opts, loss, alpha, ws, s);
@@ -672,7 +743,7 @@ ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* 
   return run_graphed(key, (cudaStream_t)stream, body);
 }
 
-static size_t host_extra(const ptycho_dims& d) {
+static size_t host_extra(const ptycho_dims& d) {  // device staging of the host buffers
   const size_t HW = (size_t)d.H * d.W, NN = (size_t)d.N * d.N;
   return align256(HW * 8) + align256((size_t)d.M * NN * 8) + align256((size_t)d.J * 8) +
          align256((size_t)d.J * NN * 4) + align256((size_t)d.J * 4) + align256(8);
@@ -683,14 +754,19 @@ size_t ptycho_host_workspace_bytes(const ptycho_dims* dims, int32_t batch) {
   return make_layout(*dims, batch).total + host_extra(*dims);
 }
 
-ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, float* probe, const float* pos,
+size_t ptycho_host_workspace_bytes_opts(const ptycho_dims* dims, const ptycho_lsqml_opts* opts) {
+  if (check_dims(dims) != PTYCHO_OK || check_opts(opts) != PTYCHO_OK) return 0;
+  return layout_for(*dims, *opts).total + host_extra(*dims);
+}
+
+ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, float* probe, float* pos,
                                       const float* meas, const int32_t* order, const ptycho_lsqml_opts* opts,
                                       double* loss, void* ws, size_t ws_bytes, void* stream) {
   ptycho_status st = check_dims(dims);
   if (st != PTYCHO_OK) return st;
   if ((st = check_opts(opts)) != PTYCHO_OK) return st;
   if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
-  const Layout L = make_layout(*dims, opts->batch);
+  const Layout L = layout_for(*dims, *opts);
   if ((st = check_ws(ws, ws_bytes, L.total + host_extra(*dims))) != PTYCHO_OK) return st;
   const ptycho_dims& d = *dims;
   const size_t HW = (size_t)d.H * d.W, NN = (size_t)d.N * d.N;
@@ -716,6 +792,7 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
   if (st != PTYCHO_OK) return st;
   cp(object, dobj, HW * 8, cudaMemcpyDeviceToHost);
   cp(probe, dprobe, (size_t)d.M * NN * 8, cudaMemcpyDeviceToHost);
+  if (opts->update_positions) cp(pos, dpos, (size_t)d.J * 8, cudaMemcpyDeviceToHost);
   if (loss) cp(loss, dloss, 8, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return PTYCHO_ERR_CUDA;
   return cuda_status(cudaStreamSynchronize(s));

@@ -156,13 +156,14 @@ size_t ptycho_workspace_bytes_batched(int32_t n, const ptycho_dims* dims, const 
   size_t total = 0;
   for (int i = 0; i < n; ++i) {
     if (check_dims(&dims[i]) != PTYCHO_OK || opts[i].batch < 1) return 0;
-    total += make_layout(dims[i], opts[i].batch).total;
+    if (check_opts(&opts[i]) != PTYCHO_OK) return 0;
+    total += layout_for(dims[i], opts[i]).total;
   }
   return total;
 }
 
 ptycho_status ptycho_lsqml_epoch_batched(int32_t n, const ptycho_dims* dims, float* const* objects,
-                                         float* const* probes, const float* const* pos, const float* const* meas,
+                                         float* const* probes, float* const* pos, const float* const* meas,
                                          const int32_t* const* orders, const ptycho_lsqml_opts* opts,
                                          double* losses, void* ws, size_t ws_bytes, void* stream) {
   if (n < 1 || !dims || !objects || !probes || !pos || !meas || !opts) return PTYCHO_ERR_ARG;
@@ -174,7 +175,7 @@ ptycho_status ptycho_lsqml_epoch_batched(int32_t n, const ptycho_dims* dims, flo
   }
   const size_t need = ptycho_workspace_bytes_batched(n, dims, opts);
   if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < need) return PTYCHO_ERR_WORKSPACE;
-  auto section = [&](int i) { return make_layout(dims[i], opts[i].batch).total; };
+  auto section = [&](int i) { return layout_for(dims[i], opts[i]).total; };
   auto run = [&](int i, void* base, cudaStream_t s) {
     ptycho_lsqml_opts oi = opts[i];
     oi.flags = 0;
@@ -216,6 +217,7 @@ ptycho_status ptycho_lsqml_epoch_opr_batched(int32_t n, const ptycho_dims* dims,
     if ((st = check_dims(&dims[i])) != PTYCHO_OK) return st;
     if ((st = check_opr_opts(&opr[i])) != PTYCHO_OK) return st;
     if ((st = check_opts(&opts[i])) != PTYCHO_OK) return st;
+    if (opts[i].update_positions || opts[i].object_per_epoch) return PTYCHO_ERR_UNSUPPORTED;
     if (!objects[i] || !U[i] || (dims[i].M > 1 && (!P_rest || !P_rest[i])) ||
         (dims[i].J > 0 && (!pos[i] || !meas[i] || !w[i])))
       return PTYCHO_ERR_ARG;

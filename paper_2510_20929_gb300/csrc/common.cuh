@@ -71,6 +71,9 @@ struct BatchArgs {
   const float* opr_w;  // [J, K]
   int K;
   float2* p0_s;        // [B, N, N] (null in the forward mode)
+  // Position correction (LSQML): per slot the sums A11, A12, A22, b1, b2 of
+  // the least-squares shift, FP64, accumulated with atomics (or null).
+  double* possum;      // [B, 5]
 };
 
 struct Pass2Args {

@@ -13,6 +13,8 @@ namespace ptycho {
 struct Layout {
   size_t hdr, acc, psi, o, g, h, dPacc, Dp, dP, Sp, Cp, Sdp, valid;
   size_t p0, dUacc, Du, dU, gram;   // orthogonal probe relaxation (K > 0) only
+  size_t possum;                     // position-correction sums [B, 5] (FP64)
+  size_t dOe;                        // epoch object accumulator [H, W] (object_per_epoch) or 0
   size_t total;
 };
 
@@ -26,12 +28,16 @@ struct Ptrs {
   float2 *p0, *dUacc, *dU;
   float* Du;
   double* gram;
+  double* possum;
+  float2* dOe;
 };
 
 size_t align256(size_t b);
 // Workspace regions for a minibatch of B positions; K > 0 adds the regions of
 // the relaxed primary probe mode with K eigenmodes.
-Layout make_layout(const ptycho_dims& d, int B, int K = 0);
+Layout make_layout(const ptycho_dims& d, int B, int K = 0, bool epoch_object = false);
+// The layout one LSQML epoch with these options uses.
+Layout layout_for(const ptycho_dims& d, const ptycho_lsqml_opts& o);
 Ptrs carve(void* ws, const Layout& L);
 ptycho_status check_dims(const ptycho_dims* d);
 ptycho_status check_opts(const ptycho_lsqml_opts* o);
@@ -65,7 +71,7 @@ cudaError_t tile_illum_max(const ptycho_dims& d, int nb, int b0, const float* po
 cudaError_t clear_acc(bool tiles, const ptycho_dims& d, int nb, int b0, const float* pos, const int32_t* order,
                       const int* valid, float4* acc, cudaStream_t s);
 // One LSQML epoch on stream s with workspace ws (arguments already validated).
-ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, const float* pos, const float* meas,
+ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float* pos, const float* meas,
                         const int32_t* order, const ptycho_lsqml_opts& o, double* loss, double* alpha, void* ws,
                         cudaStream_t s);
 

@@ -367,9 +367,11 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
         [&](int y, int x, float4 v) { atomicAdd(a.gobj + (size_t)(ty + y) * a.W + (tx + x), make_float2(v.x, v.y)); });
   }
 
-  // ---- position gradient through the bilinear weights (gradient modes) -------------
-  if (a.gpos) {
-    float gy = 0.f, gx = 0.f;
+  // ---- position gradient through the bilinear weights (gradient modes), or the
+  // ---- sums of the least-squares position step (LSQML position correction)
+  if (a.gpos || a.possum) {
+    const bool ls = a.possum != nullptr;
+    float gy = 0.f, gx = 0.f, a11 = 0.f, a12 = 0.f, a22 = 0.f;
     for (int p = tid; p < NN; p += T) {
       const int r = p / N, c = p % N;
       const float2* o = a.obj + (size_t)(ty + r) * a.W + (tx + c);
@@ -381,12 +383,25 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
       const float2 g = tile[tix<N>(r, c)];
       gy += g.x * dy.x + g.y * dy.y;  // Re(conj(g) dy)
       gx += g.x * dx.x + g.y * dx.y;
+      if (ls) {   // sum_k abs(P_k)^2 times the derivative products
+        const float sp = __ldg(a.Sp + p) + ((OPR && p0) ? cabs2(p0[p]) : 0.f);
+        a11 = fmaf(sp, cabs2(dy), a11);
+        a12 = fmaf(sp, dy.x * dx.x + dy.y * dx.y, a12);
+        a22 = fmaf(sp, cabs2(dx), a22);
+      }
     }
-    double v[2] = {(double)gy, (double)gx};
-    block_sum<2>(v, red);
-    if (tid == 0) {
-      a.gpos[2 * j] += (float)v[0];
-      a.gpos[2 * j + 1] += (float)v[1];
+    if (ls) {
+      double v[5] = {(double)a11, (double)a12, (double)a22, (double)gy, (double)gx};
+      block_sum<5>(v, red);
+      if (tid == 0)
+        for (int q = 0; q < 5; ++q) atomicAdd(a.possum + (size_t)slot * 5 + q, v[q]);
+    } else {
+      double v[2] = {(double)gy, (double)gx};
+      block_sum<2>(v, red);
+      if (tid == 0) {
+        a.gpos[2 * j] += (float)v[0];
+        a.gpos[2 * j + 1] += (float)v[1];
+      }
     }
   }
 }

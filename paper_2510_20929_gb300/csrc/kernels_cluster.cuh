@@ -447,9 +447,11 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
     }
   }
 
-  // ---- position gradient (gradient modes), this CTA's rows ----------------------------
-  if (a.gpos) {
-    float gyv = 0.f, gxv = 0.f;
+  // ---- position gradient (gradient modes) or the least-squares position-step
+  // ---- sums (LSQML position correction), this CTA's rows ----------------------------
+  if (a.gpos || a.possum) {
+    const bool ls = a.possum != nullptr;
+    float gyv = 0.f, gxv = 0.f, a11 = 0.f, a12 = 0.f, a22 = 0.f;
     for (int pl = tid; pl < LNN; pl += T) {
       const int r = rowbase + pl / N, c = pl % N;
       const float2* o = a.obj + (size_t)(ty + r) * a.W + (tx + c);
@@ -461,12 +463,26 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
       const float2 g = g_s[r * N + c];
       gyv += g.x * dy.x + g.y * dy.y;
       gxv += g.x * dx.x + g.y * dx.y;
+      if (ls) {
+        const int p = r * N + c;
+        const float sp = __ldg(a.Sp + p) + ((OPR && p0) ? cabs2(p0[p]) : 0.f);
+        a11 = fmaf(sp, cabs2(dy), a11);
+        a12 = fmaf(sp, dy.x * dx.x + dy.y * dx.y, a12);
+        a22 = fmaf(sp, cabs2(dx), a22);
+      }
     }
-    double v[2] = {(double)gyv, (double)gxv};
-    block_sum<2>(v, red);
-    if (tid == 0) {
-      atomicAdd(a.gpos + 2 * j, (float)v[0]);
-      atomicAdd(a.gpos + 2 * j + 1, (float)v[1]);
+    if (ls) {
+      double v[5] = {(double)a11, (double)a12, (double)a22, (double)gyv, (double)gxv};
+      block_sum<5>(v, red);
+      if (tid == 0)
+        for (int q = 0; q < 5; ++q) atomicAdd(a.possum + (size_t)slot * 5 + q, v[q]);
+    } else {
+      double v[2] = {(double)gyv, (double)gxv};
+      block_sum<2>(v, red);
+      if (tid == 0) {
+        atomicAdd(a.gpos + 2 * j, (float)v[0]);
+        atomicAdd(a.gpos + 2 * j + 1, (float)v[1]);
+      }
     }
   }
 }

@@ -49,12 +49,13 @@ ptycho_status static_scratch(void** out) {
 }  // namespace ptycho
 
 extern "C" ptycho_status ptycho_lsqml_epoch_static(const ptycho_dims* dims, float* object, float* probe,
-                                                   const float* pos, const float* meas, const int32_t* order,
+                                                   float* pos, const float* meas, const int32_t* order,
                                                    const ptycho_lsqml_opts* opts, double* loss, double* alpha,
                                                    void* stream) {
   if (!dims || !opts || opts->batch < 1) return PTYCHO_ERR_ARG;
-  const size_t need = ptycho_workspace_bytes(dims, opts->batch);
-  if (need == 0) return PTYCHO_ERR_UNSUPPORTED;
+  if (ptycho_workspace_bytes(dims, opts->batch) == 0) return PTYCHO_ERR_UNSUPPORTED;
+  const size_t need = ptycho_workspace_bytes_opts(dims, opts);
+  if (need == 0) return PTYCHO_ERR_ARG;   // the dimensions are supported: the options are not valid
   if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
   if (need > (size_t)PTYCHO_STATIC_WS_BYTES) return PTYCHO_ERR_TOO_LARGE;
   void* ws = nullptr;

@@ -80,9 +80,24 @@ def test_arguments_rejected_before_any_launch(L):
     assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
                                 P(0), P(0), fake, 1 << 30, None) == 1
     opts = api.make_opts(batch=4)
-    opts.reserved[2] = 1
+    opts.reserved = 1
     assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
                                 P(0), P(0), fake, 1 << 30, None) == 1
+    for bad in (dict(pos_step=-1.0), dict(pos_max_shift=float("nan"))):
+        opts = api.make_opts(batch=4, update_positions=True, **bad)
+        assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
+                                    P(0), P(0), fake, 1 << 30, None) == 1
+    opts = api.make_opts(batch=4)
+    opts.object_per_epoch = 2
+    assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
+                                P(0), P(0), fake, 1 << 30, None) == 1
+    # the per-epoch object accumulator needs H x W complex64 more workspace
+    per_epoch = api.make_opts(batch=4, object_per_epoch=True)
+    base = L.ptycho_workspace_bytes(ctypes.byref(d), 4)
+    assert L.ptycho_workspace_bytes_opts(ctypes.byref(d), ctypes.byref(api.make_opts(batch=4))) == base
+    assert L.ptycho_workspace_bytes_opts(ctypes.byref(d), ctypes.byref(per_epoch)) >= base + d.H * d.W * 8
+    assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(per_epoch),
+                                P(0), P(0), P(0x1000), base, None) == 7
     opts = api.make_opts(batch=4, noise=7)
     assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
                                 P(0), P(0), fake, 1 << 30, None) == 1

@@ -124,3 +124,71 @@ def test_lsqml_epoch_on_a_large_object_matches_oracle(N, M, H, W, J, step, batch
 def test_lsqml_epoch_object_only_matches_oracle():
     e = _epoch_case(32, 2, 72, 76, 16, 6.0, 16, "gaussian", update_probe=False)
     assert e["O"] < TOL_EPOCH and e["P"] == 0.0 and e["alpha"] < TOL_EPOCH
+
+
+def _state_case(N, M, H, W, J, step, batch, update_positions, object_per_epoch, seed=11, shift=0.8):
+    import torch
+    from paper_2510_20929_gb300 import api
+    p = problem(N=N, M=M, H=H, W=W, J=J, step=step, seed=seed)
+    g = np.random.default_rng(seed + 3)
+    p["pos"] = p["pos"] + (g.uniform(-shift, shift, p["pos"].shape) if update_positions else 0.0)
+    (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
+    order = np.random.default_rng(seed).permutation(J).astype(np.int32)
+    kw = dict(batch=batch, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6)
+    opts = orc.LsqmlOptions(**kw, update_positions=update_positions, pos_step=0.9, pos_max_shift=0.5,
+                            object_per_epoch=object_per_epoch)
+    O_ref, P_ref, pos_ref, L_ref, a_ref = orc.lsqml_epoch_state(O, P, pos, I_m, order, opts)
+    loss, alpha = api.lsqml_epoch(dO, dP, dpos, dI, to_dev(order, torch.int32), want_alpha=True, **kw,
+                                  update_positions=update_positions, pos_step=0.9, pos_max_shift=0.5,
+                                  object_per_epoch=object_per_epoch)
+    e = dict(O=rel(dO.cpu().numpy(), O_ref), P=rel(dP.cpu().numpy(), P_ref),
+             alpha=rel(alpha.cpu().numpy(), a_ref), loss=abs(loss.item() - L_ref) / abs(L_ref))
+    dpos_err = float(np.max(np.abs(dpos.cpu().numpy().astype(np.float64) - pos_ref)))
+    moved = float(np.max(np.abs(pos_ref - pos)))
+    print(f"epoch N={N} M={M} pos={update_positions} per_epoch={object_per_epoch}: "
+          + " ".join(f"{k} {v:.2e}" for k, v in e.items()) + f" pos {dpos_err:.2e} px (moved {moved:.2e})")
+    return e, dpos_err, moved
+
+
+@pytest.mark.parametrize("N,M,H,W,J,step,batch", [
+    (16, 2, 44, 48, 12, 4.0, 5),
+    (64, 3, 160, 150, 14, 12.0, 6),
+    (128, 2, 300, 310, 9, 24.0, 4),
+    (256, 1, 320, 330, 4, 20.0, 3),
+])
+def test_lsqml_epoch_with_position_correction_matches_oracle(N, M, H, W, J, step, batch):
+    e, dpos_err, moved = _state_case(N, M, H, W, J, step, batch, True, False)
+    assert max(e.values()) < TOL_EPOCH
+    assert moved > 1e-3 and dpos_err < 1e-3   # px; positions are float32 values near 100 px
+
+
+@pytest.mark.parametrize("N,M,H,W,J,step,batch", [
+    (16, 2, 44, 48, 12, 4.0, 5),
+    (64, 1, 160, 150, 25, 12.0, 8),
+    (192, 1, 256, 266, 6, 20.0, 4),
+])
+def test_lsqml_epoch_with_per_epoch_object_update_matches_oracle(N, M, H, W, J, step, batch):
+    e, _, _ = _state_case(N, M, H, W, J, step, batch, False, True)
+    assert max(e.values()) < TOL_EPOCH
+
+
+def test_lsqml_epoch_with_both_modes_on_host_buffers_matches_oracle():
+    import torch
+    from paper_2510_20929_gb300 import api
+    p = problem(N=32, M=2, H=72, W=76, J=16, step=6.0, seed=13)
+    p["pos"] = p["pos"] + np.random.default_rng(4).uniform(-0.5, 0.5, p["pos"].shape)
+    O, P, pos, I_m = c64(p["O"]), c64(p["P"]), f32pos(p["pos"]), np.float32(p["I_m"]).astype(np.float64)
+    order = np.random.default_rng(2).permutation(16).astype(np.int32)
+    kw = dict(batch=6, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6)
+    opts = orc.LsqmlOptions(**kw, update_positions=True, object_per_epoch=True)
+    O_ref, P_ref, pos_ref, L_ref, _ = orc.lsqml_epoch_state(O, P, pos, I_m, order, opts)
+    hO = torch.tensor(O, dtype=torch.complex64).pin_memory()
+    hP = torch.tensor(P, dtype=torch.complex64).pin_memory()
+    hpos = torch.tensor(pos, dtype=torch.float32).pin_memory()
+    hI = torch.tensor(I_m, dtype=torch.float32).pin_memory()
+    L = api.lsqml_epoch_host(hO, hP, hpos, hI, torch.tensor(order), api.make_opts(**kw, update_positions=True,
+                                                                                   object_per_epoch=True))
+    e = (rel(hO.numpy(), O_ref), rel(hP.numpy(), P_ref), abs(L - L_ref) / L_ref,
+         float(np.max(np.abs(hpos.numpy() - pos_ref))))
+    print("host epoch, both modes:", e)
+    assert max(e[:3]) < TOL_EPOCH and e[3] < 1e-3
