@@ -292,6 +292,27 @@ ptycho_status ptycho_lsqml_epoch_opr_batched(int32_t n, const ptycho_dims* dims,
                                              const ptycho_lsqml_opts* opts, double* losses, void* ws,
                                              size_t ws_bytes, void* stream);
 
+/* Minibatch samplers (Sec. 2.1: random, uniform and compact batches).
+ * Writes `order` (int32 [J], a permutation of 0..J-1) for the epoch entry
+ * points, whose consecutive chunks of `batch` entries are the minibatches.
+ * HOST pointers; pos float32 [J, 2] (y, x). Pure host code, no GPU work.
+ *   RANDOM:  Fisher-Yates driven by SplitMix64 from `seed`.
+ *   COMPACT: spatially connected clusters: recursive splits at an index along
+ *            the longer side of the bounding box (stable sort by that
+ *            coordinate), every cluster but the last exactly `batch` long, so
+ *            each minibatch is one cluster (pair it with object_per_epoch).
+ *   UNIFORM: `batch` balanced compact clusters read round-robin, so each
+ *            minibatch takes one position from every part of the scan field.
+ * Returns PTYCHO_ERR_ARG for a bad kind, batch < 1, null pointers with J > 0,
+ * or a non-finite position. `seed` is used by RANDOM only. */
+typedef enum {
+  PTYCHO_SAMPLER_RANDOM = 0,
+  PTYCHO_SAMPLER_UNIFORM = 1,
+  PTYCHO_SAMPLER_COMPACT = 2
+} ptycho_sampler;
+ptycho_status ptycho_sampler_order(const float* pos, int32_t J, int32_t batch, int32_t kind, uint64_t seed,
+                                   int32_t* order);
+
 /* Synchronises `stream`, returns (and clears) the device-side status recorded
  * in `ws` since the last read: PTYCHO_OK, PTYCHO_ERR_BOUNDS or
  * PTYCHO_ERR_NONFINITE (bounds reported first), or PTYCHO_ERR_CUDA. */

@@ -640,3 +640,57 @@ def lsqml_epoch_opr(O, U, w, P_rest, pos, I_m, order, opts: LsqmlOptions, opr: O
         loss += l
         alpha[idx] = a
     return O, U, w, P_rest, loss, alpha
+
+
+# ---------------------------------------------------------------------------
+# Minibatch samplers (Sec. 2.1: random, uniform and compact batches).
+# Index work, compared bit-exactly with the library; positions as float32.
+# ---------------------------------------------------------------------------
+SAMPLER_RANDOM, SAMPLER_UNIFORM, SAMPLER_COMPACT = 0, 1, 2
+_MASK64 = (1 << 64) - 1
+
+
+def splitmix64(state: int):
+    """One SplitMix64 step (Steele, Lea and Flood 2014): returns (new_state, output)."""
+    state = (state + 0x9E3779B97F4A7C15) & _MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return state, z ^ (z >> 31)
+
+
+def _kd_split(pos32, idx, groups, cap, out):
+    """Recursive spatial split of the index list ``idx`` into ``groups`` clusters."""
+    n = len(idx)
+    if groups <= 1 or n <= 1:
+        out.append(list(idx))
+        return
+    ys, xs = pos32[idx, 0], pos32[idx, 1]
+    axis = 0 if (ys.max() - ys.min()) >= (xs.max() - xs.min()) else 1
+    idx = [idx[i] for i in np.argsort(pos32[idx, axis], kind="stable")]
+    g1 = groups // 2
+    g2 = groups - g1
+    n1 = min(n, g1 * cap) if cap > 0 else (n * g1 + groups // 2) // groups
+    _kd_split(pos32, idx[:n1], g1, cap, out)
+    _kd_split(pos32, idx[n1:], g2, cap, out)
+
+
+def sampler_order(pos, batch: int, kind: int, seed: int = 0) -> np.ndarray:
+    """Batch order of the random, uniform or compact sampler (see the C header)."""
+    pos32 = np.asarray(pos, np.float32)
+    J = pos32.shape[0]
+    if kind == SAMPLER_RANDOM:
+        idx = list(range(J))
+        state = seed & _MASK64
+        for i in range(J - 1, 0, -1):
+            state, z = splitmix64(state)
+            k = z % (i + 1)
+            idx[i], idx[k] = idx[k], idx[i]
+        return np.array(idx, np.int32)
+    groups = []
+    if kind == SAMPLER_COMPACT:
+        _kd_split(pos32, list(range(J)), -(-J // batch), batch, groups)
+        return np.array([i for g in groups for i in g], np.int32)
+    _kd_split(pos32, list(range(J)), min(batch, max(J, 1)), 0, groups)
+    longest = max(len(g) for g in groups)
+    return np.array([g[t] for t in range(longest) for g in groups if t < len(g)], np.int32)

@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
                                                               _P, _P, opts_p, _P, _P, ctypes.c_size_t, _P]),
             "ptycho_workspace_bytes": (ctypes.c_size_t, [dims_p, ctypes.c_int32]),
             "ptycho_workspace_bytes_opts": (ctypes.c_size_t, [dims_p, opts_p]),
+            "ptycho_sampler_order": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                    ctypes.c_uint64, _P]),
             "ptycho_host_workspace_bytes_opts": (ctypes.c_size_t, [dims_p, opts_p]),
             "ptycho_host_workspace_bytes": (ctypes.c_size_t, [dims_p, ctypes.c_int32]),
             "ptycho_workspace_init": (ctypes.c_int, [_P, ctypes.c_size_t, _P]),
@@ -260,6 +262,22 @@ def adjoint(obj, probe, pos, meas, noise="gaussian", eps: float = 0.0, batch: in
            "ptycho_adjoint")
     _finish(ws, "ptycho_adjoint", check)
     return (None if nz == VJP else loss), gO, gP, gr
+
+
+SAMPLERS = {"random": 0, "uniform": 1, "compact": 2}
+
+
+def sampler_order(pos, batch: int, kind="compact", seed: int = 0):
+    """Minibatch order (int32 CPU tensor [J]) of the random, uniform or compact
+    sampler for positions ``pos`` (float32 [J, 2], any device; copied to the host)."""
+    p = pos.detach().to("cpu", torch.float32).contiguous() if isinstance(pos, torch.Tensor) else \
+        torch.as_tensor(pos, dtype=torch.float32).contiguous()
+    J = p.shape[0]
+    out = torch.empty(J, dtype=torch.int32)
+    k = SAMPLERS[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().ptycho_sampler_order(_P(p.data_ptr()), J, int(batch), k, int(seed) & ((1 << 64) - 1),
+                                      _P(out.data_ptr())), "ptycho_sampler_order")
+    return out
 
 
 def make_opts(noise="gaussian", batch: int = 256, delta_o: float = 0.1, delta_p: float = 0.1,

@@ -192,3 +192,23 @@ def test_lsqml_epoch_with_both_modes_on_host_buffers_matches_oracle():
          float(np.max(np.abs(hpos.numpy() - pos_ref))))
     print("host epoch, both modes:", e)
     assert max(e[:3]) < TOL_EPOCH and e[3] < 1e-3
+
+
+def test_compact_sampler_with_per_epoch_object_update_matches_oracle():
+    # the compact sampler's order and the accumulate-once object update, as
+    # LSQML pairs them, over an epoch of several minibatches
+    import torch
+    from paper_2510_20929_gb300 import api
+    p = problem(N=32, M=2, H=120, W=124, J=64, step=6.0, seed=17)
+    (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
+    order = api.sampler_order(torch.tensor(pos, dtype=torch.float32), 16, "compact").numpy()
+    assert np.array_equal(order, orc.sampler_order(pos, 16, orc.SAMPLER_COMPACT))
+    kw = dict(batch=16, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6)
+    O_ref, P_ref, _, L_ref, a_ref = orc.lsqml_epoch_state(O, P, pos, I_m, order,
+                                                          orc.LsqmlOptions(**kw, object_per_epoch=True))
+    loss, alpha = api.lsqml_epoch(dO, dP, dpos, dI, to_dev(order, torch.int32), want_alpha=True, **kw,
+                                  object_per_epoch=True)
+    e = (rel(dO.cpu().numpy(), O_ref), rel(dP.cpu().numpy(), P_ref), rel(alpha.cpu().numpy(), a_ref),
+         abs(loss.item() - L_ref) / L_ref)
+    print("compact + per-epoch:", e)
+    assert max(e) < TOL_EPOCH
