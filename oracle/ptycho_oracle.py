@@ -694,3 +694,97 @@ def sampler_order(pos, batch: int, kind: int, seed: int = 0) -> np.ndarray:
     _kd_split(pos32, list(range(J)), min(batch, max(J, 1)), 0, groups)
     longest = max(len(g) for g in groups)
     return np.array([g[t] for t in range(longest) for g in groups if t < len(g)], np.int32)
+
+
+# ---------------------------------------------------------------------------
+# Multislice (Sec. 1 and Sec. 2.1: multislice modelling). The object has S
+# slices [S, H, W]; the wave is multiplied by each slice's patch and carried to
+# the next slice by the angular-spectrum propagator.
+# ---------------------------------------------------------------------------
+def asm_propagator(N: int, pixel_size: float, wavelength: float, dz: float) -> np.ndarray:
+    """Angular-spectrum transfer function on the N x N FFT grid (no fftshift).
+
+    H(f) = exp(i 2 pi dz (sqrt(1/lambda^2 - |f|^2) - 1/lambda)) with the
+    spatial frequencies f = k / (N pixel_size); the constant phase 2 pi dz /
+    lambda is dropped (a global phase) and evanescent frequencies are set to 0.
+    The bracket is evaluated as -|f|^2 / (sqrt(1/lambda^2 - |f|^2) + 1/lambda).
+    """
+    f = np.fft.fftfreq(N, d=pixel_size)
+    fy, fx = np.meshgrid(f, f, indexing="ij")
+    f2 = fy * fy + fx * fx
+    inv_l2 = 1.0 / (wavelength * wavelength)
+    prop = f2 < inv_l2
+    kz = np.sqrt(np.where(prop, inv_l2 - f2, 0.0))
+    phase = 2.0 * np.pi * dz * (-f2 / (kz + 1.0 / wavelength))
+    return np.where(prop, np.exp(1j * phase), 0.0)
+
+
+def propagate(psi: np.ndarray, Hf: np.ndarray) -> np.ndarray:
+    """F^-1 [H F psi] over the last two axes."""
+    return idft2(Hf * dft2(psi))
+
+
+def exit_waves_ms(Os, P, r, Hf):
+    """Per-mode exit waves after the last slice, and each slice's incident wave.
+
+    Os: [S, H, W]; returns (psi_out [M, N, N], incident [S, M, N, N], patches [S, N, N]).
+    """
+    N = P.shape[-1]
+    S = Os.shape[0]
+    o = np.stack([extract(Os[s], r, N) for s in range(S)])
+    inc = np.empty((S,) + P.shape, np.complex128)
+    psi = np.asarray(P, np.complex128)
+    for s in range(S):
+        if s > 0:
+            psi = propagate(psi, Hf)
+        inc[s] = psi
+        psi = psi * o[s][None]
+    return psi, inc, o
+
+
+def forward_ms(Os, P, pos, Hf):
+    """Predicted intensities [J, N, N] of the multislice model."""
+    out = np.empty((pos.shape[0], P.shape[-1], P.shape[-1]), np.float64)
+    for j in range(pos.shape[0]):
+        psi, _, _ = exit_waves_ms(Os, P, pos[j], Hf)
+        out[j] = np.sum(np.abs(dft2(psi)) ** 2, axis=0)
+    return out
+
+
+def vjp_ms(Os, P, pos, Hf, G):
+    """Gradients (2 dL/dz*) of the multislice model given G = dL/dI.
+
+    Backward through the slices: at slice s the wave leaving it is
+    incident_s * o_s, so g(o_s) += conj(incident_s) g_out and the gradient
+    reaching the slice entrance is conj(o_s) g_out; the propagator's adjoint
+    is F^-1 [conj(H) F .]. The probe gradient is the entrance gradient of
+    slice 0; the position gradient sums each slice's patch derivative.
+    """
+    S, H, W = Os.shape
+    N = P.shape[-1]
+    gO = np.zeros((S, H, W), np.complex128)
+    gP = np.zeros_like(P, dtype=np.complex128)
+    gr = np.zeros((pos.shape[0], 2), np.float64)
+    Hc = np.conj(Hf)
+    for j in range(pos.shape[0]):
+        psi, inc, o = exit_waves_ms(Os, P, pos[j], Hf)
+        g = idft2(2.0 * G[j][None] * dft2(psi))       # gradient w.r.t. the exit waves
+        go = np.zeros((S, N, N), np.complex128)
+        for s in range(S - 1, -1, -1):
+            go[s] = np.sum(np.conj(inc[s]) * g, axis=0)
+            g = np.conj(o[s])[None] * g
+            if s > 0:
+                g = propagate(g, Hc)
+        gP += g
+        for s in range(S):
+            gO[s] += scatter(go[s], pos[j], H, W)
+            d_dy, d_dx = extract_dr(Os[s], pos[j], N)
+            gr[j, 0] += np.real(np.sum(np.conj(go[s]) * d_dy))
+            gr[j, 1] += np.real(np.sum(np.conj(go[s]) * d_dx))
+    return gO, gP, gr
+
+
+def loss_and_gradients_ms(Os, P, pos, Hf, I_m, noise=GAUSSIAN, eps=0.0):
+    I = forward_ms(Os, P, pos, Hf)
+    loss = sum(pattern_loss(I[j], I_m[j], noise, eps) for j in range(pos.shape[0]))
+    return (loss,) + vjp_ms(Os, P, pos, Hf, dloss_dI(I, I_m, noise, eps))

@@ -91,3 +91,9 @@ def test_per_epoch_update_applied_per_batch_is_caught(monkeypatch):
 
     monkeypatch.setattr(orc, "lsqml_batch", per_batch)
     _fails(pins.test_per_epoch_object_update_does_not_depend_on_the_batch_order)
+
+
+def test_propagator_of_the_wrong_handedness_is_caught(monkeypatch):
+    real = orc.asm_propagator
+    monkeypatch.setattr(orc, "asm_propagator", lambda *a: np.conj(real(*a)))
+    _fails(pins.test_asm_propagator_properties)

@@ -506,3 +506,80 @@ def test_per_epoch_object_update_does_not_depend_on_the_batch_order():
         diff = np.max(np.abs(orc.lsqml_epoch(O, P, pos, I_m, order, o)[0]
                              - orc.lsqml_epoch(O, P, pos, I_m, reordered, o)[0]))
         assert (diff < 1e-12) if per_epoch else (diff > 1e-6)
+
+
+# --------------------------------------------------------------------------- multislice
+def test_asm_propagator_properties():
+    N, px, lam = 32, 10e-9, 0.1e-9
+    H1 = orc.asm_propagator(N, px, lam, 1e-6)
+    H2 = orc.asm_propagator(N, px, lam, 2.5e-6)
+    H3 = orc.asm_propagator(N, px, lam, 3.5e-6)
+    assert np.max(np.abs(H1 * H2 - H3)) < 1e-12                      # propagation composes
+    assert np.max(np.abs(orc.asm_propagator(N, px, lam, 0.0) - 1.0)) == 0.0
+    assert np.max(np.abs(np.abs(H1) - 1.0)) < 1e-14                   # no evanescent waves here
+    # paraxial (Fresnel) limit: phase -> -pi lambda dz |f|^2, relative error ~ (lambda f)^2 / 4
+    f = np.fft.fftfreq(N, d=px)
+    f2 = f[:, None] ** 2 + f[None, :] ** 2
+    fres = -np.pi * lam * 1e-6 * f2
+    assert np.max(np.abs(np.angle(H1) - fres)) < 1e-4 * np.max(np.abs(fres))
+    # frequencies beyond 1/lambda are evanescent and removed
+    Hc = orc.asm_propagator(8, 0.4, 1.0, 1.0)
+    f = np.fft.fftfreq(8, d=0.4)
+    ev = (f[:, None] ** 2 + f[None, :] ** 2) >= 1.0
+    assert ev.any() and np.all(Hc[ev] == 0) and np.all(np.abs(Hc[~ev]) > 0.99)
+
+
+def _ms_problem(S=3, seed=19, M=2):
+    g = np.random.default_rng(seed)
+    w = synth.workload_small(N=8, M=M, H=24, W=24, J=4, seed=seed, step=3.0)
+    Os = np.stack([w["object"] ** (1.0 / S) * np.exp(0.2j * g.standard_normal((24, 24))) for _ in range(S)])
+    Hf = orc.asm_propagator(8, 10e-9, 0.1e-9, 40e-6)   # a strong propagator for an 8-px window
+    I_m = synth.poisson_counts(orc.forward_ms(Os, w["probe"] * 3.0, w["pos"], Hf), seed)
+    return Os, w["probe"] * 3.0, w["pos"], Hf, I_m
+
+
+def test_multislice_with_one_slice_is_the_single_slice_model():
+    Os, P, pos, Hf, I_m = _ms_problem(S=1)
+    assert np.max(np.abs(orc.forward_ms(Os, P, pos, Hf) - orc.forward(Os[0], P, pos))) < 1e-12
+    G = np.random.default_rng(1).standard_normal(I_m.shape)
+    gO, gP, gr = orc.vjp_ms(Os, P, pos, Hf, G)
+    gO1, gP1, gr1 = orc.vjp(Os[0], P, pos, G)
+    assert np.max(np.abs(gO[0] - gO1)) < 1e-10 and np.max(np.abs(gP - gP1)) < 1e-10
+    assert np.max(np.abs(gr - gr1)) < 1e-10
+
+
+def test_multislice_without_propagation_is_the_product_object():
+    # integer positions: the patches are crops, so the patch of a product is
+    # the product of the patches
+    Os, P, pos, _, _ = _ms_problem(S=3)
+    pos = np.round(pos)
+    one = orc.asm_propagator(8, 10e-9, 0.1e-9, 0.0)
+    ref = orc.forward(Os[0] * Os[1] * Os[2], P, pos)
+    assert np.max(np.abs(orc.forward_ms(Os, P, pos, one) - ref)) < 1e-11 * np.max(ref)
+
+
+def test_multislice_conserves_energy_through_pure_phase_slices():
+    Os, P, pos, Hf, _ = _ms_problem(S=4)
+    Os = np.exp(1j * np.angle(Os))
+    I = orc.forward_ms(Os, P, np.round(pos), Hf)   # crops of pure-phase slices are pure phase
+    assert np.max(np.abs(I.sum(axis=(1, 2)) - np.sum(np.abs(P) ** 2))) < 1e-10 * np.sum(np.abs(P) ** 2)
+
+
+def test_multislice_gradients_match_central_finite_differences():
+    Os, P, pos, Hf, I_m = _ms_problem(S=3)
+    L, gO, gP, gr = orc.loss_and_gradients_ms(Os, P, pos, Hf, I_m, orc.GAUSSIAN, 1e-3)
+    g = np.random.default_rng(5)
+    h = 1e-6
+
+    def L_at(Os_, P_, pos_):
+        return orc.loss_and_gradients_ms(Os_, P_, pos_, Hf, I_m, orc.GAUSSIAN, 1e-3)[0]
+
+    dO = crandn(g, *Os.shape)
+    fd = (L_at(Os + h * dO, P, pos) - L_at(Os - h * dO, P, pos)) / (2 * h)
+    assert abs(fd - np.real(np.vdot(gO, dO))) < 1e-6 * abs(fd)
+    dP = crandn(g, *P.shape)
+    fd = (L_at(Os, P + h * dP, pos) - L_at(Os, P - h * dP, pos)) / (2 * h)
+    assert abs(fd - np.real(np.vdot(gP, dP))) < 1e-6 * abs(fd)
+    dr = g.standard_normal(pos.shape) * 0.1
+    fd = (L_at(Os, P, pos + h * dr) - L_at(Os, P, pos - h * dr)) / (2 * h)
+    assert abs(fd - np.sum(gr * dr)) < 1e-5 * abs(fd)
