@@ -292,6 +292,44 @@ ptycho_status ptycho_lsqml_epoch_opr_batched(int32_t n, const ptycho_dims* dims,
                                              const ptycho_lsqml_opts* opts, double* losses, void* ws,
                                              size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Multislice (Sec. 1 and Sec. 2.1: multislice modelling). The object has S
+ * slices, complex64 [S, H, W]. For position j and mode k the wave entering
+ * slice 0 is P_k; the wave leaving slice s is its incident wave times
+ * S_j(O^(s)); between slices the wave is propagated by the angular spectrum,
+ * F^-1[H F psi] with H(f) = exp(i 2 pi dz (sqrt(1/lambda^2 - |f|^2) - 1/lambda))
+ * on the FFT grid f = k / (N pixel_size) (the constant phase 2 pi dz / lambda
+ * dropped, evanescent frequencies zero; computed in FP64 on the device); the
+ * far field of the last slice gives I_j = sum_k |F psi_jk|^2. Windows 16..128,
+ * 1 <= S <= 16. The incident waves of slices 1..S-1 are kept in the workspace
+ * for the backward pass (B M (S-1) N^2 complex64).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t S;          /* object slices */
+  int32_t reserved;   /* must be zero */
+  double dz;          /* slice spacing */
+  double wavelength;  /* same unit as dz */
+  double pixel_size;  /* object pixel, same unit */
+} ptycho_multislice;
+
+/* Workspace bytes of the two multislice entry points (0 if unsupported). */
+size_t ptycho_workspace_bytes_ms(const ptycho_dims* dims, const ptycho_multislice* ms, int32_t batch);
+
+/* Multislice forward model, positions in chunks of `batch`. I_pred float32
+ * [J, N, N], overwritten. */
+ptycho_status ptycho_forward_ms(const ptycho_dims* dims, const ptycho_multislice* ms, const float* object,
+                                const float* probe, const float* pos, float* I_pred, int32_t batch, void* ws,
+                                size_t ws_bytes, void* stream);
+
+/* Data term and gradients (2 dL/dz*) through the multislice model, all
+ * ACCUMULATED (+=): g_object complex64 [S, H, W], g_probe [M, N, N], g_pos
+ * float32 [J, 2] (may be NULL), loss (may be NULL; untouched for VJP). As
+ * ptycho_adjoint otherwise. */
+ptycho_status ptycho_adjoint_ms(const ptycho_dims* dims, const ptycho_multislice* ms, const float* object,
+                                const float* probe, const float* pos, const float* meas, int32_t noise,
+                                double eps, int32_t batch, float* g_object, float* g_probe, float* g_pos,
+                                double* loss, void* ws, size_t ws_bytes, void* stream);
+
 /* Minibatch samplers (Sec. 2.1: random, uniform and compact batches).
  * Writes `order` (int32 [J], a permutation of 0..J-1) for the epoch entry
  * points, whose consecutive chunks of `batch` entries are the minibatches.

@@ -56,6 +56,11 @@ class LsqmlOpts(ctypes.Structure):
                 ("pos_step", ctypes.c_double), ("pos_max_shift", ctypes.c_double)]
 
 
+class Multislice(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int32), ("reserved", ctypes.c_int32), ("dz", ctypes.c_double),
+                ("wavelength", ctypes.c_double), ("pixel_size", ctypes.c_double)]
+
+
 class OprOpts(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("update_weights", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
                 ("weight_step", ctypes.c_double)]
@@ -78,7 +83,13 @@ def lib() -> ctypes.CDLL:
         dims_p = ctypes.POINTER(Dims)
         opts_p = ctypes.POINTER(LsqmlOpts)
         opr_p = ctypes.POINTER(OprOpts)
+        ms_p = ctypes.POINTER(Multislice)
         sigs = {
+            "ptycho_workspace_bytes_ms": (ctypes.c_size_t, [dims_p, ms_p, ctypes.c_int32]),
+            "ptycho_forward_ms": (ctypes.c_int, [dims_p, ms_p, _P, _P, _P, _P, ctypes.c_int32, _P, ctypes.c_size_t,
+                                                 _P]),
+            "ptycho_adjoint_ms": (ctypes.c_int, [dims_p, ms_p, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double,
+                                                 ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
             "ptycho_workspace_bytes_opr": (ctypes.c_size_t, [dims_p, ctypes.c_int32, ctypes.c_int32]),
             "ptycho_forward_opr": (ctypes.c_int, [dims_p, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P,
                                                   ctypes.c_size_t, _P]),
@@ -550,3 +561,68 @@ def lsqml_epoch_opr_batched(recons, opts, oprs, *, check: bool = True):
             _check(lib().ptycho_status_read(_P(ws.ptr + off), _stream()), f"ptycho_lsqml_epoch_opr_batched[{i}]")
             off += lib().ptycho_workspace_bytes_opr(ctypes.byref(dims[i]), RA[i].K, OA[i].batch)
     return losses
+
+
+# ---------------------------------------------------------------------------
+# Multislice: object slices complex64 [S, H, W], angular-spectrum propagation
+# between slices (spacing dz, wavelength and pixel size in one unit).
+# ---------------------------------------------------------------------------
+def make_multislice(S: int, dz: float, wavelength: float, pixel_size: float) -> Multislice:
+    m = Multislice()
+    m.S, m.dz, m.wavelength, m.pixel_size = int(S), float(dz), float(wavelength), float(pixel_size)
+    return m
+
+
+def _ms_dims(obj, probe, pos, ms):
+    _need(obj, "object slices", torch.complex64)
+    _need(probe, "probe", torch.complex64, device=obj.device)
+    _need(pos, "positions", torch.float32, device=obj.device)
+    if obj.dim() != 3 or obj.shape[0] != ms.S:
+        raise ValueError("object must be [S, H, W] with S = ms.S")
+    M, N, N2 = probe.shape
+    if N != N2:
+        raise ValueError("probe modes must be square")
+    return Dims(obj.shape[1], obj.shape[2], N, M, pos.shape[0])
+
+
+def _ms_workspace(d, ms, batch, device):
+    need = lib().ptycho_workspace_bytes_ms(ctypes.byref(d), ctypes.byref(ms), int(batch))
+    if need == 0:
+        raise PtychoError(6, "workspace_bytes_ms")
+    key = (str(device), "ms")
+    ws = _ws_cache.get(key)
+    if ws is None or ws.nbytes < need:
+        ws = Workspace(need, device)
+        _ws_cache[key] = ws
+    return ws
+
+
+def forward_ms(obj, probe, pos, ms: Multislice, batch: int = 256, *, check: bool = True):
+    """Predicted intensities [J, N, N] of the multislice model."""
+    d = _ms_dims(obj, probe, pos, ms)
+    B = max(1, min(int(batch), max(d.J, 1)))
+    I = torch.empty((d.J, d.N, d.N), dtype=torch.float32, device=obj.device)
+    ws = _ms_workspace(d, ms, B, obj.device)
+    _check(lib().ptycho_forward_ms(ctypes.byref(d), ctypes.byref(ms), _ptr(obj), _ptr(probe), _ptr(pos), _ptr(I), B,
+                                   _P(ws.ptr), ws.nbytes, _stream()), "ptycho_forward_ms")
+    _finish(ws, "ptycho_forward_ms", check)
+    return I
+
+
+def adjoint_ms(obj, probe, pos, meas, ms: Multislice, noise="gaussian", eps: float = 0.0, batch: int = 256, *,
+               positions_grad: bool = True, check: bool = True):
+    """Loss and gradients through the multislice model: (loss, g_object [S, H, W], g_probe, g_pos)."""
+    nz = _NOISE[noise] if isinstance(noise, str) else int(noise)
+    d = _ms_dims(obj, probe, pos, ms)
+    _need(meas, "meas", torch.float32, (d.J, d.N, d.N), device=obj.device)
+    B = max(1, min(int(batch), max(d.J, 1)))
+    gO, gP = torch.zeros_like(obj), torch.zeros_like(probe)
+    gr = torch.zeros((d.J, 2), dtype=torch.float32, device=obj.device) if positions_grad else None
+    loss = torch.zeros((), dtype=torch.float64, device=obj.device)
+    ws = _ms_workspace(d, ms, B, obj.device)
+    _check(lib().ptycho_adjoint_ms(ctypes.byref(d), ctypes.byref(ms), _ptr(obj), _ptr(probe), _ptr(pos), _ptr(meas),
+                                   nz, float(eps), B, _ptr(gO), _ptr(gP), _ptr(gr),
+                                   _ptr(loss) if nz != VJP else _P(0), _P(ws.ptr), ws.nbytes, _stream()),
+           "ptycho_adjoint_ms")
+    _finish(ws, "ptycho_adjoint_ms", check)
+    return (None if nz == VJP else loss), gO, gP, gr

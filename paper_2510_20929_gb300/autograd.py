@@ -15,6 +15,9 @@
   (Sec. 2.1: the primary mode of position j is sum_m w_jm U_m), differentiable
   in the object, the eigenmodes U, the real weights w, the shared modes and
   the positions; :func:`reconstruct_adam_opr` runs Adam on all of them.
+* :class:`FarFieldMS` and :class:`DataTermMS` are the multislice forms
+  (object slices [S, H, W], angular-spectrum propagation between slices);
+  :func:`reconstruct_adam_ms` runs Adam on the slices, probe and positions.
 
 Both Functions only marshal tensors to the C ABI; every arithmetic step runs
 in the CUDA library.
@@ -75,6 +78,50 @@ class DataTermOPR(torch.autograd.Function):
         need = ctx.needs_input_grad
         return (gO * s if need[0] else None, gU * s if need[1] else None, gw * s if need[2] else None,
                 gP * s if (need[3] and gP is not None) else None, gr * s if need[4] else None, None, None, None)
+
+
+class FarFieldMS(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, obj, probe, pos, ms):
+        obj, probe, pos = obj.contiguous(), probe.contiguous(), pos.contiguous()
+        ctx.save_for_backward(obj, probe, pos)
+        ctx.ms = ms
+        return api.forward_ms(obj, probe, pos, ms)
+
+    @staticmethod
+    def backward(ctx, gI):
+        obj, probe, pos = ctx.saved_tensors
+        _, gO, gP, gr = api.adjoint_ms(obj, probe, pos, gI.contiguous().to(torch.float32), ctx.ms, "vjp",
+                                       positions_grad=ctx.needs_input_grad[2])
+        need = ctx.needs_input_grad
+        return gO if need[0] else None, gP if need[1] else None, gr if need[2] else None, None
+
+
+class DataTermMS(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, obj, probe, pos, meas, ms, noise="gaussian", eps=1e-9):
+        loss, gO, gP, gr = api.adjoint_ms(obj.contiguous(), probe.contiguous(), pos.contiguous(), meas.contiguous(),
+                                          ms, noise, eps=eps, positions_grad=True)
+        ctx.save_for_backward(gO, gP, gr)
+        return loss
+
+    @staticmethod
+    def backward(ctx, gL):
+        gO, gP, gr = ctx.saved_tensors
+        s = gL.to(torch.float32)
+        need = ctx.needs_input_grad
+        return (gO * s if need[0] else None, gP * s if need[1] else None, gr * s if need[2] else None,
+                None, None, None, None)
+
+
+def far_field_ms(obj, probe, pos, ms):
+    """Multislice intensities, differentiable in the object slices, probe modes and positions."""
+    return FarFieldMS.apply(obj, probe, pos, ms)
+
+
+def data_term_ms(obj, probe, pos, meas, ms, noise="gaussian", eps=1e-9):
+    """Scalar data term of the multislice model (differentiable in slices, probe, positions)."""
+    return DataTermMS.apply(obj, probe, pos, meas, ms, noise, eps)
 
 
 def data_term_opr(obj, U, w, P_rest, pos, meas, noise="gaussian", eps=1e-9):
@@ -150,4 +197,27 @@ def reconstruct_adam_opr(obj, U, w, P_rest, pos, meas, epochs=10, lr_object=1e-2
     for _, t, _ in groups:
         if t is not None:
             t.requires_grad_(False)
+    return hist
+
+
+def reconstruct_adam_ms(obj, probe, pos, meas, ms, epochs=10, lr_object=1e-2, lr_probe=1e-2, lr_pos=1e-1,
+                        noise="gaussian", eps=1e-9, update=("object", "probe", "positions")):
+    """Adam on the object slices [S, H, W], probe modes and positions of the
+    multislice model; returns the loss history (tensors updated in place)."""
+    groups = [("object", obj, lr_object), ("probe", probe, lr_probe), ("positions", pos, lr_pos)]
+    params = []
+    for name, t, lr in groups:
+        t.requires_grad_(name in update)
+        if name in update:
+            params.append({"params": [t], "lr": lr})
+    opt = torch.optim.Adam(params)
+    hist = []
+    for _ in range(epochs):
+        opt.zero_grad(set_to_none=True)
+        loss = data_term_ms(obj, probe, pos, meas, ms, noise, eps)
+        loss.backward()
+        opt.step()
+        hist.append(loss.item())
+    for _, t, _ in groups:
+        t.requires_grad_(False)
     return hist

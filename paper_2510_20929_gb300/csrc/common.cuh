@@ -103,6 +103,29 @@ struct Pass2Args {
   const float2* p0_s;   // [B, N, N] primary mode of each slot
 };
 
+// Arguments of the multislice per-position pass (kernels_ms.cuh).
+struct MsArgs {
+  int H, W, M, J, S;
+  const float2* obj;    // [S, H, W]
+  const float2* probe;  // [M, N, N]
+  const float* pos;
+  const float* meas;    // measured intensities, or dL/dI in MODE_VJP
+  int b0, nb, mode;
+  float eps;
+  const float2* Hf;     // [N, N] propagator, FFT order
+  float2* psi_s;        // [B, M, N, N] far fields (unitary scale)
+  float2* o_s;          // [B, S, N, N] slice patches
+  float2* in_s;         // [B, M, S - 1, N, N] incident waves of slices 1..S-1
+  float2* go_s;         // [B, S, N, N] per-slice object gradients (patch frame)
+  float2* h_s;          // [B, M, N, N] probe gradient of each position
+  int* valid;           // [B]
+  float2* gobj;         // [S, H, W] gradient accumulator, or null
+  float* ipred;         // [J, N, N] or null
+  float* gpos;          // [J, 2] or null
+  double* loss;
+  int* status;
+};
+
 constexpr int OPR_KMAX = 8;   // eigenmodes of the relaxed primary probe mode
 
 // Shared probe mode k, or null for the synthesised primary mode (OPR).

@@ -1,0 +1,331 @@
+// Multislice forward model and its adjoint (Pty-Chi Sec. 1 and Sec. 2.1:
+// multislice modelling), for windows held by one CTA (N <= 128).
+//
+// The object has S slices [S, H, W]. For position j and probe mode k the wave
+// entering slice 0 is P_k; the wave leaving slice s is (incident_s) o_j^(s)
+// with o_j^(s) = S_j(O^(s)); between slices it is carried by the
+// angular-spectrum propagator, incident_s = F^-1[H F (leaving_{s-1})]. The
+// far field of the last slice's exit wave gives I_j = sum_k |F psi|^2.
+//
+// k_pass1_ms: one CTA per position. It extracts all slice patches once,
+// runs every mode through the slices in shared memory (a propagation is a
+// column FFT pass, a fused row pass that transforms, multiplies by H / N^2 and
+// transforms back, and an inverse column pass), keeps the incident waves of
+// slices 1..S-1 in scratch for the backward pass, and forms the data term as
+// the single-slice kernel does. The backward pass runs each mode from the far
+// field back through the slices (conj(H) propagation), accumulating the
+// per-slice object gradients conj(incident_s) g and the probe gradient
+// conj(o^(0)) g, then scatters every slice's gradient into its plane and
+// sums the position gradient over the slices.
+#pragma once
+#include "kernels.cuh"
+
+namespace ptycho {
+
+// Propagates the tile (natural layout, spatial domain) to the next slice:
+// tile <- F^-1[H F tile] (CONJ: conj(H), the adjoint). Ends synchronised.
+template <int N, int T, bool CONJ>
+__device__ __forceinline__ void propagate_tile(float2* tile, const float2* tw, const float2* __restrict__ Hf) {
+  using F = Fft2<N>;
+  constexpr int R1 = F::R1, R2 = F::R2, L = T / R1, ITER = N / L;
+  const int n = F::line_lane(), gid = F::line_slot();
+  const float s = 1.0f / (float)(N * N);
+#pragma unroll 1
+  for (int it = 0; it < ITER; ++it) {
+    const int col = gid + it * L;
+    float2 v[R2];
+    F::template load_in<false>(v, tile, col, n);
+    F::template line_fwd<false>(v, tile, col, n, tw);
+    F::template store_out<false>(v, tile, col, n);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int it = 0; it < ITER; ++it) {
+    const int row = gid + it * L;
+    float2 v[R2];
+    F::template load_in<true>(v, tile, row, n);
+    F::template line_fwd<true>(v, tile, row, n, tw);
+#pragma unroll
+    for (int m = 0; m < R2; ++m) {
+      float2 h = __ldg(Hf + row * N + F::out_index(n, m));
+      if (CONJ) h.y = -h.y;
+      v[m] = cscale(cmul(v[m], h), s);
+    }
+    F::template line_inv<true>(v, tile, row, n, tw);
+    F::template store_in<true>(v, tile, row, n);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int it = 0; it < ITER; ++it) {
+    const int col = gid + it * L;
+    float2 v[R2];
+    F::template load_out<false>(v, tile, col, n);
+    F::template line_inv<false>(v, tile, col, n, tw);
+    F::template store_in<false>(v, tile, col, n);
+  }
+  __syncthreads();
+}
+
+template <int N, int T>
+__global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
+  using F = Fft2<N>;
+  using SM = Pass1Smem<N>;
+  constexpr int R2 = F::R2, NN = N * N, RP = SM::RP;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* red = (double*)(smem + SM::red);
+  float2* tile = (float2*)(smem + SM::tile);
+  float2* tw = (float2*)(smem + SM::tw);
+  float* rI = (float*)(smem + SM::rI);
+
+  const int slot = blockIdx.x;
+  const int tid = threadIdx.x, n = F::line_lane();
+  const int j = a.b0 + slot;
+  int ty = 0, tx = 0;
+  float fy = 0.f, fx = 0.f;
+  bool ok = (j >= 0 && j < a.J);
+  if (ok) ok = tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
+  if (!ok) {
+    if (tid == 0) {
+      atomicOr(a.status, FLAG_BOUNDS);
+      if (a.valid) a.valid[slot] = 0;
+    }
+    return;
+  }
+  if (tid == 0 && a.valid) a.valid[slot] = 1;
+  make_twiddles<N>(tw);
+
+  const int M = a.M, S = a.S;
+  const size_t HW = (size_t)a.H * a.W;
+  const float invN = 1.0f / (float)N;
+  const size_t slotNN = (size_t)slot * NN;
+  const int mode = a.mode;
+  const bool grad = mode != MODE_FWD;
+  float2* psi_s = grad ? a.psi_s + slotNN * M : nullptr;
+  float2* o_s = a.o_s + slotNN * S;
+  const NatPairs<N, T> np;
+
+  // ---- slice patches o^(s) = S_j(O^(s)) -------------------------------------------
+  for (int s = 0; s < S; ++s) {
+#pragma unroll 2
+    for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+      float2 o0, o1;
+      bilinear2(a.obj + s * HW, a.W, ty + np.row(q), tx + np.c, fy, fx, o0, o1);
+      *(float4*)(o_s + (size_t)s * NN + np.pix(q)) = make_float4(o0.x, o0.y, o1.x, o1.y);
+    }
+  }
+  __syncthreads();
+
+  // ---- forward: every mode through the slices, then the far field --------------------
+#pragma unroll 1
+  for (int k = 0; k < M; ++k) {
+    const float2* Pk = a.probe + (size_t)k * NN;
+#pragma unroll 2
+    for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+      const int p = np.pix(q);
+      const float4 o2 = *(const float4*)(o_s + p);
+      const float4 P2 = __ldg((const float4*)(Pk + p));
+      store_pair(tile, np.phys(q), cmul(make_float2(P2.x, P2.y), make_float2(o2.x, o2.y)),
+                 cmul(make_float2(P2.z, P2.w), make_float2(o2.z, o2.w)));
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int s = 1; s < S; ++s) {
+      propagate_tile<N, T, false>(tile, tw, a.Hf);
+      float2* inc = grad ? a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN) : nullptr;
+#pragma unroll 2
+      for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+        const int p = np.pix(q);
+        float2 x0, x1;
+        load_pair(tile, np.phys(q), x0, x1);
+        if (grad) *(float4*)(inc + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        const float4 o2 = *(const float4*)(o_s + (size_t)s * NN + p);
+        store_pair(tile, np.phys(q), cmul(x0, make_float2(o2.x, o2.y)), cmul(x1, make_float2(o2.z, o2.w)));
+      }
+      __syncthreads();
+    }
+    fft2_forward<N, T>(tile, tw, [&](int row, float2 (&v)[R2]) {
+#pragma unroll
+      for (int m = 0; m < R2; ++m) {
+        const int col = F::out_index(n, m);
+        const float2 X = cscale(v[m], invN);
+        float* ri = rI + row * RP + col;
+        *ri = (k == 0) ? cabs2(X) : *ri + cabs2(X);
+        if (grad) psi_s[(size_t)k * NN + row * N + col] = X;
+      }
+    });
+    __syncthreads();
+  }
+
+  // ---- data term (as in the single-slice pass) ---------------------------------------
+  const float eps = a.eps;
+  const float* meas = a.meas ? a.meas + (size_t)j * NN : nullptr;
+  float lsum = 0.f;
+  bool bad = false;
+  {
+    constexpr int L = T / F::R1, ITER = N / L;
+    const int gid = F::line_slot();
+#pragma unroll 1
+    for (int it = 0; it < ITER; ++it) {
+      const int row = gid + it * L;
+#pragma unroll
+      for (int m = 0; m < R2; ++m) {
+        const int col = F::out_index(n, m);
+        const int pix = row * N + col;
+        const float I = rI[row * RP + col];
+        if (a.ipred) a.ipred[(size_t)j * NN + pix] = I;
+        if (!grad) continue;
+        const float Im = __ldg(meas + pix);
+        float fac;
+        if (mode == MODE_VJP) {
+          bad |= !isfinite(Im);
+          fac = 2.f * Im;
+        } else {
+          bad |= !(Im >= 0.f) || !isfinite(Im);
+          const float Ie = I + eps;
+          if (mode == MODE_GRAD_GAUSS) {
+            const float sIe = sqrtf(Ie), sIm = sqrtf(Im), d = sIe - sIm;
+            lsum = fmaf(d, d, lsum);
+            fac = 2.f * (1.f - sIm / sIe);
+          } else {
+            lsum += I - Im * logf(Ie);
+            fac = 2.f * (1.f - Im / Ie);
+          }
+        }
+        rI[row * RP + col] = fac * invN;
+      }
+    }
+  }
+  if (bad) atomicOr(a.status, FLAG_NONFINITE);
+  if (a.loss && grad && mode != MODE_VJP) {
+    double v[1] = {(double)lsum};
+    block_sum<1>(v, red);
+    if (tid == 0) atomicAdd(a.loss, v[0]);
+  }
+  if (!grad) return;
+
+  // ---- backward: each mode from the far field back through the slices ---------------
+  float2* go_s = a.go_s + slotNN * S;
+  float2* h_s = a.h_s + slotNN * M;
+#pragma unroll 1
+  for (int k = 0; k < M; ++k) {
+    const float2* Pk = a.probe + (size_t)k * NN;
+    __syncthreads();
+    fft2_inverse<N, T>(
+        tile, tw,
+        [&](int row, float2 (&v)[R2]) {
+#pragma unroll
+          for (int m = 0; m < R2; ++m) {
+            const int col = F::out_index(n, m);
+            v[m] = cscale(psi_s[(size_t)k * NN + row * N + col], rI[row * RP + col]);
+          }
+        },
+        [&](int col, float2 (&v)[R2]) { F::template store_in<false>(v, tile, col, n); });
+    __syncthreads();
+#pragma unroll 1
+    for (int s = S - 1; s >= 1; --s) {
+      const float2* inc = a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN);
+#pragma unroll 2
+      for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+        const int p = np.pix(q);
+        float2 g0, g1;
+        load_pair(tile, np.phys(q), g0, g1);
+        const float4 i2 = *(const float4*)(inc + p);
+        const float4 o2 = *(const float4*)(o_s + (size_t)s * NN + p);
+        float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 a0 = cmulc(make_float2(i2.x, i2.y), g0), a1 = cmulc(make_float2(i2.z, i2.w), g1);
+        float4* gp = (float4*)(go_s + (size_t)s * NN + p);
+        gv = make_float4(a0.x, a0.y, a1.x, a1.y);
+        if (k > 0) {
+          const float4 prev = *gp;
+          gv = make_float4(gv.x + prev.x, gv.y + prev.y, gv.z + prev.z, gv.w + prev.w);
+        }
+        *gp = gv;
+        store_pair(tile, np.phys(q), cmulc(make_float2(o2.x, o2.y), g0), cmulc(make_float2(o2.z, o2.w), g1));
+      }
+      __syncthreads();
+      propagate_tile<N, T, true>(tile, tw, a.Hf);
+    }
+    // slice 0: object gradient conj(P_k) g, probe gradient conj(o^(0)) g
+#pragma unroll 2
+    for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+      const int p = np.pix(q);
+      float2 g0, g1;
+      load_pair(tile, np.phys(q), g0, g1);
+      const float4 P2 = __ldg((const float4*)(Pk + p));
+      const float4 o2 = *(const float4*)(o_s + p);
+      const float2 a0 = cmulc(make_float2(P2.x, P2.y), g0), a1 = cmulc(make_float2(P2.z, P2.w), g1);
+      float4 gv = make_float4(a0.x, a0.y, a1.x, a1.y);
+      float4* gp = (float4*)(go_s + p);
+      if (k > 0) {
+        const float4 prev = *gp;
+        gv = make_float4(gv.x + prev.x, gv.y + prev.y, gv.z + prev.z, gv.w + prev.w);
+      }
+      *gp = gv;
+      const float2 h0 = cmulc(make_float2(o2.x, o2.y), g0), h1 = cmulc(make_float2(o2.z, o2.w), g1);
+      __stcs((float4*)(h_s + (size_t)k * NN + p), make_float4(h0.x, h0.y, h1.x, h1.y));
+    }
+  }
+  __syncthreads();
+
+  // ---- per slice: scatter S_j^T of its gradient; position gradient over the slices ----
+  float gyv = 0.f, gxv = 0.f;
+#pragma unroll 1
+  for (int s = 0; s < S; ++s) {
+#pragma unroll 2
+    for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+      const float4 g2 = *(const float4*)(go_s + (size_t)s * NN + np.pix(q));
+      store_pair(tile, np.phys(q), make_float2(g2.x, g2.y), make_float2(g2.z, g2.w));
+    }
+    __syncthreads();
+    if (a.gobj) {
+      float2* gplane = a.gobj + s * HW;
+      bilinear_scatter<N, T>(
+          fy, fx,
+          [&](int y, int x) {
+            const float2 g = tile[tix<N>(y, x)];
+            return make_float4(g.x, g.y, 0.f, 0.f);
+          },
+          [&](int y, int x, float4 v) { atomicAdd(gplane + (size_t)(ty + y) * a.W + (tx + x), make_float2(v.x, v.y)); });
+    }
+    if (a.gpos) {
+      const float2* Os = a.obj + s * HW;
+      for (int p = tid; p < NN; p += T) {
+        const int r = p / N, c = p % N;
+        const float2* o = Os + (size_t)(ty + r) * a.W + (tx + c);
+        const float2 O00 = __ldg(o), O01 = __ldg(o + 1), O10 = __ldg(o + a.W), O11 = __ldg(o + a.W + 1);
+        const float2 dy = make_float2((1.f - fx) * (O10.x - O00.x) + fx * (O11.x - O01.x),
+                                      (1.f - fx) * (O10.y - O00.y) + fx * (O11.y - O01.y));
+        const float2 dx = make_float2((1.f - fy) * (O01.x - O00.x) + fy * (O11.x - O10.x),
+                                      (1.f - fy) * (O01.y - O00.y) + fy * (O11.y - O10.y));
+        const float2 g = tile[tix<N>(r, c)];
+        gyv += g.x * dy.x + g.y * dy.y;
+        gxv += g.x * dx.x + g.y * dx.y;
+      }
+    }
+    __syncthreads();
+  }
+  if (a.gpos) {
+    double v[2] = {(double)gyv, (double)gxv};
+    block_sum<2>(v, red);
+    if (tid == 0) {
+      a.gpos[2 * j] += (float)v[0];
+      a.gpos[2 * j + 1] += (float)v[1];
+    }
+  }
+}
+
+// CTA size of the multislice pass: the default of the single-slice pass, but
+// 512 threads at N = 128 (the slice loops need more than 64 registers).
+template <int N>
+cudaError_t launch_pass1_ms(const MsArgs& a, cudaStream_t s) {
+  constexpr int T = N == 128 ? 512 : Threads<N>::T;
+  constexpr size_t sm = Pass1Smem<N>::bytes;
+  static unsigned long long done = 0;
+  cudaError_t e = smem_optin(k_pass1_ms<N, T>, sm, &done);
+  if (e != cudaSuccess) return e;
+  if (a.nb <= 0) return cudaSuccess;
+  k_pass1_ms<N, T><<<a.nb, T, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ptycho

@@ -6,7 +6,10 @@
 namespace ptycho {
 struct BatchArgs;
 struct Pass2Args;
+struct MsArgs;
 // variant 0 = default CTA size, 1 = the alternative CTA size (autotuner)
 template <int N> cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s, int variant);
 template <int N> cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s, int variant);
+// multislice per-position pass (N <= 128)
+template <int N> cudaError_t launch_pass1_ms(const MsArgs& a, cudaStream_t s);
 }  // namespace ptycho

@@ -1,0 +1,110 @@
+"""GPU parity of the multislice entry points against the FP64 oracle: forward
+model and gradients (all slices, probe modes, positions) with the
+angular-spectrum propagator, for windows 16..128 and 1..4 slices."""
+import numpy as np
+import pytest
+
+from oracle import ptycho_oracle as orc
+from paper_2510_20929_gb300 import synth
+from tests.parity_util import c64, f32pos, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL_FWD = 1e-5
+TOL_GRAD = 1e-4
+LAM, PX = 0.1e-9, 10e-9
+
+
+def ms_problem(N, M, S, H, W, J, step, dz, seed=7, counts=2e4):
+    w = synth.workload_small(N=N, M=M, H=H, W=W, J=J, seed=seed, step=step)
+    g = np.random.default_rng(seed + 1)
+    # slices: the sample's amplitude spread over the slices, each with its own phase texture
+    Os = np.stack([w["object"] ** (1.0 / S) * np.exp(0.3j * synth.make_object(H, W, seed + 10 + s).imag)
+                   for s in range(S)])
+    Hf = orc.asm_propagator(N, PX, LAM, dz)
+    I0 = orc.forward_ms(Os, w["probe"], w["pos"], Hf)
+    P = w["probe"] * np.sqrt(counts / I0.sum(axis=(1, 2)).mean())
+    I_m = synth.poisson_counts(orc.forward_ms(Os, P, w["pos"], Hf), seed + 2)
+    Os0 = Os * (1 + 0.1 * (g.standard_normal(Os.shape) + 1j * g.standard_normal(Os.shape)))
+    return c64(Os0), c64(P), f32pos(w["pos"]), Hf, np.float32(I_m).astype(np.float64)
+
+
+def _dev(Os, P, pos, I_m):
+    import torch
+    return (to_dev(Os, torch.complex64), to_dev(P, torch.complex64), to_dev(pos, torch.float32),
+            to_dev(I_m, torch.float32))
+
+
+CASES = [  # N, M, S, H, W, J, step, dz
+    (16, 1, 1, 40, 44, 9, 4.0, 2e-6),
+    (16, 2, 3, 41, 37, 9, 3.0, 40e-6),
+    (32, 2, 4, 72, 76, 12, 6.0, 10e-6),
+    (64, 3, 2, 150, 160, 10, 12.0, 4e-6),
+    (128, 2, 4, 290, 300, 6, 30.0, 2e-6),
+]
+
+
+@pytest.mark.parametrize("N,M,S,H,W,J,step,dz", CASES)
+def test_forward_ms_matches_oracle(N, M, S, H, W, J, step, dz):
+    from paper_2510_20929_gb300 import api
+    Os, P, pos, Hf, I_m = ms_problem(N, M, S, H, W, J, step, dz)
+    dO, dP, dpos, _ = _dev(Os, P, pos, I_m)
+    ms = api.make_multislice(S, dz, LAM, PX)
+    I = api.forward_ms(dO, dP, dpos, ms, batch=4).cpu().numpy()   # ragged chunks
+    ref = orc.forward_ms(Os, P, pos, Hf)
+    e = rel(I, ref)
+    print(f"forward_ms N={N} M={M} S={S}: rel {e:.3e}")
+    assert e < TOL_FWD
+
+
+@pytest.mark.parametrize("noise", ["gaussian", "poisson"])
+@pytest.mark.parametrize("N,M,S,H,W,J,step,dz", CASES[1:])
+def test_adjoint_ms_matches_oracle(noise, N, M, S, H, W, J, step, dz):
+    from paper_2510_20929_gb300 import api
+    Os, P, pos, Hf, I_m = ms_problem(N, M, S, H, W, J, step, dz)
+    nz = orc.GAUSSIAN if noise == "gaussian" else orc.POISSON
+    L_ref, gO_ref, gP_ref, gr_ref = orc.loss_and_gradients_ms(Os, P, pos, Hf, I_m, nz, 1e-6)
+    loss, gO, gP, gr = api.adjoint_ms(*_dev(Os, P, pos, I_m), api.make_multislice(S, dz, LAM, PX), noise, eps=1e-6,
+                                      batch=4)
+    e = [abs(loss.item() - L_ref) / abs(L_ref), rel(gO.cpu().numpy(), gO_ref), rel(gP.cpu().numpy(), gP_ref),
+         rel(gr.cpu().numpy(), gr_ref)]
+    print(f"adjoint_ms {noise} N={N} M={M} S={S}:", " ".join(f"{x:.2e}" for x in e))
+    assert max(e) < TOL_GRAD
+
+
+def test_adjoint_ms_vjp_and_one_slice_equals_the_single_slice_path():
+    import torch
+    from paper_2510_20929_gb300 import api
+    Os, P, pos, Hf, I_m = ms_problem(32, 2, 3, 72, 76, 12, 6.0, 10e-6)
+    G = np.random.default_rng(2).standard_normal(I_m.shape).astype(np.float32).astype(np.float64)
+    gO_ref, gP_ref, gr_ref = orc.vjp_ms(Os, P, pos, Hf, G)
+    dO, dP, dpos, _ = _dev(Os, P, pos, I_m)
+    loss, gO, gP, gr = api.adjoint_ms(dO, dP, dpos, to_dev(G, torch.float32), api.make_multislice(3, 10e-6, LAM, PX),
+                                      "vjp", batch=5)
+    assert loss is None
+    e = (rel(gO.cpu().numpy(), gO_ref), rel(gP.cpu().numpy(), gP_ref), rel(gr.cpu().numpy(), gr_ref))
+    print("vjp_ms:", e)
+    assert max(e) < TOL_GRAD
+    # one slice: the multislice pass computes what the single-slice pass computes
+    ms1 = api.make_multislice(1, 10e-6, LAM, PX)
+    d1 = dO[:1].contiguous()
+    l1, g1, p1, r1 = api.adjoint_ms(d1, dP, dpos, to_dev(I_m, torch.float32), ms1, "gaussian", eps=1e-6)
+    l0, g0, p0, r0 = api.adjoint(d1[0], dP, dpos, to_dev(I_m, torch.float32), "gaussian", eps=1e-6)
+    assert rel(g1[0].cpu().numpy(), g0.cpu().numpy()) < 1e-5 and rel(p1.cpu().numpy(), p0.cpu().numpy()) < 1e-5
+    assert abs(l1.item() - l0.item()) < 1e-6 * abs(l0.item())
+
+
+def test_multislice_autograd_and_adam():
+    import torch
+    from paper_2510_20929_gb300 import api, autograd
+    Os, P, pos, Hf, I_m = ms_problem(32, 2, 3, 72, 76, 12, 6.0, 10e-6)
+    dO, dP, dpos, dI = _dev(Os, P, pos, I_m)
+    ms = api.make_multislice(3, 10e-6, LAM, PX)
+    x = dO.clone().requires_grad_(True)
+    I = autograd.far_field_ms(x, dP, dpos, ms)
+    (I * to_dev(np.ones_like(I_m), torch.float32)).sum().backward()
+    gO_ref = orc.vjp_ms(Os, P, pos, Hf, np.ones_like(I_m))[0]
+    assert rel(x.grad.cpu().numpy(), gO_ref) < TOL_GRAD
+    hist = autograd.reconstruct_adam_ms(dO, dP, dpos, dI, ms, epochs=40, lr_object=2e-2, update=("object",))
+    print("adam ms:", hist[0], hist[-1])
+    assert hist[-1] < 0.5 * hist[0]
