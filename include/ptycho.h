@@ -300,8 +300,8 @@ ptycho_status ptycho_lsqml_epoch_opr_batched(int32_t n, const ptycho_dims* dims,
  * F^-1[H F psi] with H(f) = exp(i 2 pi dz (sqrt(1/lambda^2 - |f|^2) - 1/lambda))
  * on the FFT grid f = k / (N pixel_size) (the constant phase 2 pi dz / lambda
  * dropped, evanescent frequencies zero; computed in FP64 on the device); the
- * far field of the last slice gives I_j = sum_k |F psi_jk|^2. Windows 16..128,
- * 1 <= S <= 16. The incident waves of slices 1..S-1 are kept in the workspace
+ * far field of the last slice gives I_j = sum_k |F psi_jk|^2. Every window
+ * size, 1 <= S <= 16. The incident waves of slices 1..S-1 are kept in the workspace
  * for the backward pass (B M (S-1) N^2 complex64).
  * ------------------------------------------------------------------------- */
 typedef struct {

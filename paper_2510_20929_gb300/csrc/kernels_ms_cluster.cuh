@@ -1,0 +1,347 @@
+// Multislice per-position pass for the cluster windows (N = 192, 256): the
+// model and the phases of k_pass1_ms, with the N x N tile shared by a cluster
+// of Q CTAs as in k_pass1_cluster. CTA q holds the spatial rows 64q..64q+63;
+// a 2-D transform (cl::fwd2d) leaves it the frequency rows q + Q k2, so a
+// propagation is fwd2d, a multiplication of those rows by H / N^2, and
+// cl::inv2d back to the CTA's spatial rows.
+#pragma once
+#include "kernels_cluster.cuh"
+
+namespace ptycho {
+namespace cl {
+
+// tile <- F^-1[H F tile] over the cluster (CONJ: conj(H)); ends synchronised.
+template <class C, bool CONJ>
+__device__ __forceinline__ void propagate_cluster(cg::cluster_group& cluster, float2* tile, const float2* twr,
+                                                  const float2* twc, const float2* twn, const float2* twq, int q,
+                                                  const float2* __restrict__ Hf) {
+  constexpr int N = C::N, Q = C::Q, T = C::T;
+  const float sc = 1.0f / (float)(N * N);
+  fwd2d<C>(cluster, tile, twr, twc, twn, twq, q);
+#pragma unroll 2
+  for (int s = 0; s < C::NAT_STEPS; ++s) {
+    const int pl = 2 * (int)threadIdx.x + 2 * T * s, r = pl / N, c = pl % N;   // local frequency row r
+    float2 x0, x1;
+    load_pair(tile, C::tix(r, c), x0, x1);
+    const float4 h2 = __ldg((const float4*)(Hf + (size_t)(q + Q * r) * N + c));
+    float2 h0 = make_float2(h2.x, h2.y), h1 = make_float2(h2.z, h2.w);
+    if (CONJ) {
+      h0.y = -h0.y;
+      h1.y = -h1.y;
+    }
+    store_pair(tile, C::tix(r, c), cscale(cmul(x0, h0), sc), cscale(cmul(x1, h1), sc));
+  }
+  __syncthreads();
+  inv2d<C>(cluster, tile, twr, twc, twn, twq, q);
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
+  constexpr int N = C::N, Q = C::Q, T = C::T, LR = C::LR, NN = C::NN, LNN = C::LNN;
+  constexpr int NAT_STEPS = C::NAT_STEPS;
+  using SM = typename C::Smem;
+  constexpr int RP = SM::RP;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* red = (double*)(smem + SM::red);
+  float2* tile = (float2*)(smem + SM::tile);
+  float2* twr = (float2*)(smem + SM::twr);
+  float2* twc = (float2*)(smem + SM::twc);
+  float2* twn = (float2*)(smem + SM::twn);
+  float2* twq = (float2*)(smem + SM::twq);
+  float* rI = (float*)(smem + SM::rI);
+
+  const int q = (int)cluster.block_rank();
+  const int slot = blockIdx.x / Q;
+  const int tid = threadIdx.x;
+  const int j = a.b0 + slot;
+  int ty = 0, tx = 0;
+  float fy = 0.f, fx = 0.f;
+  bool ok = (j >= 0 && j < a.J);
+  if (ok) ok = tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
+  if (!ok) {   // the same decision in every CTA of the cluster
+    if (tid == 0 && q == 0) {
+      atomicOr(a.status, FLAG_BOUNDS);
+      if (a.valid) a.valid[slot] = 0;
+    }
+    return;
+  }
+  if (tid == 0 && q == 0 && a.valid) a.valid[slot] = 1;
+  make_line_twiddles<N, C::RR1, C::RR2>(twr);
+  make_line_twiddles<64, 8, 8>(twc);
+  for (int m = tid; m < N + Q; m += T) {
+    float s, c;
+    if (m < N) {
+      sincospif(2.0f * (float)m / (float)N, &s, &c);
+      twn[m] = make_float2(c, -s);
+    } else {
+      sincospif(2.0f * (float)(m - N) / (float)Q, &s, &c);
+      twq[m - N] = make_float2(c, -s);
+    }
+  }
+
+  const int M = a.M, S = a.S, mode = a.mode;
+  const bool grad = mode != MODE_FWD;
+  const size_t HW = (size_t)a.H * a.W;
+  const float invN = 1.0f / (float)N;
+  const size_t slotNN = (size_t)slot * NN;
+  const int rowbase = LR * q;
+  float2* psi_s = grad ? a.psi_s + slotNN * M : nullptr;
+  float2* o_s = a.o_s + slotNN * S;
+
+  // ---- slice patches of this CTA's rows ----------------------------------------------
+  for (int s = 0; s < S; ++s) {
+#pragma unroll 2
+    for (int st = 0; st < NAT_STEPS; ++st) {
+      const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+      float2 o0, o1;
+      bilinear2(a.obj + s * HW, a.W, ty + rowbase + r, tx + c, fy, fx, o0, o1);
+      *(float4*)(o_s + (size_t)s * NN + (rowbase + r) * N + c) = make_float4(o0.x, o0.y, o1.x, o1.y);
+    }
+  }
+
+  // ---- forward -----------------------------------------------------------------------
+#pragma unroll 1
+  for (int k = 0; k < M; ++k) {
+    const float2* Pk = a.probe + (size_t)k * NN;
+    __syncthreads();
+#pragma unroll 2
+    for (int st = 0; st < NAT_STEPS; ++st) {
+      const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+      const int p = (rowbase + r) * N + c;
+      const float4 o2 = *(const float4*)(o_s + p);
+      const float4 P2 = __ldg((const float4*)(Pk + p));
+      store_pair(tile, C::tix(r, c), cmul(make_float2(P2.x, P2.y), make_float2(o2.x, o2.y)),
+                 cmul(make_float2(P2.z, P2.w), make_float2(o2.z, o2.w)));
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int s = 1; s < S; ++s) {
+      propagate_cluster<C, false>(cluster, tile, twr, twc, twn, twq, q, a.Hf);
+      float2* inc = grad ? a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN) : nullptr;
+#pragma unroll 2
+      for (int st = 0; st < NAT_STEPS; ++st) {
+        const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+        const int p = (rowbase + r) * N + c;
+        float2 x0, x1;
+        load_pair(tile, C::tix(r, c), x0, x1);
+        if (grad) *(float4*)(inc + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        const float4 o2 = *(const float4*)(o_s + (size_t)s * NN + p);
+        store_pair(tile, C::tix(r, c), cmul(x0, make_float2(o2.x, o2.y)), cmul(x1, make_float2(o2.z, o2.w)));
+      }
+      __syncthreads();
+    }
+    fwd2d<C>(cluster, tile, twr, twc, twn, twq, q);
+#pragma unroll 2
+    for (int st = 0; st < NAT_STEPS; ++st) {
+      const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;   // local frequency row r
+      float2 X0, X1;
+      load_pair(tile, C::tix(r, c), X0, X1);
+      X0 = cscale(X0, invN);
+      X1 = cscale(X1, invN);
+      float2* ri = (float2*)(rI + r * RP + c);
+      const float2 i2 = make_float2(cabs2(X0), cabs2(X1));
+      *ri = (k == 0) ? i2 : make_float2(ri->x + i2.x, ri->y + i2.y);
+      if (grad) *(float4*)(psi_s + (size_t)k * NN + (q + Q * r) * N + c) = make_float4(X0.x, X0.y, X1.x, X1.y);
+    }
+  }
+
+  // ---- data term (frequency rows q + Q k2) ------------------------------------------
+  const float eps = a.eps;
+  const float* meas = a.meas ? a.meas + (size_t)j * NN : nullptr;
+  float lsum = 0.f;
+  bool bad = false;
+#pragma unroll 1
+  for (int st = 0; st < NAT_STEPS; ++st) {
+    const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+    const int pix = (q + Q * r) * N + c;
+    float* ri = rI + r * RP + c;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float I = ri[u];
+      if (a.ipred) a.ipred[(size_t)j * NN + pix + u] = I;
+      if (!grad) continue;
+      const float Im = __ldg(meas + pix + u);
+      float fac;
+      if (mode == MODE_VJP) {
+        bad |= !isfinite(Im);
+        fac = 2.f * Im;
+      } else {
+        bad |= !(Im >= 0.f) || !isfinite(Im);
+        const float Ie = I + eps;
+        if (mode == MODE_GRAD_GAUSS) {
+          const float sIe = sqrtf(Ie), sIm = sqrtf(Im), d = sIe - sIm;
+          lsum = fmaf(d, d, lsum);
+          fac = 2.f * (1.f - sIm / sIe);
+        } else {
+          lsum += I - Im * logf(Ie);
+          fac = 2.f * (1.f - Im / Ie);
+        }
+      }
+      ri[u] = fac * invN;
+    }
+  }
+  if (bad) atomicOr(a.status, FLAG_NONFINITE);
+  if (a.loss && grad && mode != MODE_VJP) {
+    double v[1] = {(double)lsum};
+    block_sum<1>(v, red);
+    if (tid == 0) atomicAdd(a.loss, v[0]);
+  }
+  if (!grad) {
+    cluster.sync();   // no CTA leaves while another may still read its tile
+    return;
+  }
+
+  // ---- backward ----------------------------------------------------------------------
+  float2* go_s = a.go_s + slotNN * S;
+  float2* h_s = a.h_s + slotNN * M;
+#pragma unroll 1
+  for (int k = 0; k < M; ++k) {
+    const float2* Pk = a.probe + (size_t)k * NN;
+    __syncthreads();
+#pragma unroll 2
+    for (int st = 0; st < NAT_STEPS; ++st) {
+      const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+      const float4 X = *(const float4*)(psi_s + (size_t)k * NN + (q + Q * r) * N + c);
+      const float2 f = *(const float2*)(rI + r * RP + c);
+      store_pair(tile, C::tix(r, c), make_float2(X.x * f.x, X.y * f.x), make_float2(X.z * f.y, X.w * f.y));
+    }
+    __syncthreads();
+    inv2d<C>(cluster, tile, twr, twc, twn, twq, q);
+#pragma unroll 1
+    for (int s = S - 1; s >= 1; --s) {
+      const float2* inc = a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN);
+#pragma unroll 2
+      for (int st = 0; st < NAT_STEPS; ++st) {
+        const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+        const int p = (rowbase + r) * N + c;
+        float2 g0, g1;
+        load_pair(tile, C::tix(r, c), g0, g1);
+        const float4 i2 = *(const float4*)(inc + p);
+        const float4 o2 = *(const float4*)(o_s + (size_t)s * NN + p);
+        const float2 a0 = cmulc(make_float2(i2.x, i2.y), g0), a1 = cmulc(make_float2(i2.z, i2.w), g1);
+        float4 gv = make_float4(a0.x, a0.y, a1.x, a1.y);
+        float4* gp = (float4*)(go_s + (size_t)s * NN + p);
+        if (k > 0) {
+          const float4 prev = *gp;
+          gv = make_float4(gv.x + prev.x, gv.y + prev.y, gv.z + prev.z, gv.w + prev.w);
+        }
+        *gp = gv;
+        store_pair(tile, C::tix(r, c), cmulc(make_float2(o2.x, o2.y), g0), cmulc(make_float2(o2.z, o2.w), g1));
+      }
+      __syncthreads();
+      propagate_cluster<C, true>(cluster, tile, twr, twc, twn, twq, q, a.Hf);
+    }
+#pragma unroll 2
+    for (int st = 0; st < NAT_STEPS; ++st) {
+      const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+      const int p = (rowbase + r) * N + c;
+      float2 g0, g1;
+      load_pair(tile, C::tix(r, c), g0, g1);
+      const float4 P2 = __ldg((const float4*)(Pk + p));
+      const float4 o2 = *(const float4*)(o_s + p);
+      const float2 a0 = cmulc(make_float2(P2.x, P2.y), g0), a1 = cmulc(make_float2(P2.z, P2.w), g1);
+      float4 gv = make_float4(a0.x, a0.y, a1.x, a1.y);
+      float4* gp = (float4*)(go_s + p);
+      if (k > 0) {
+        const float4 prev = *gp;
+        gv = make_float4(gv.x + prev.x, gv.y + prev.y, gv.z + prev.z, gv.w + prev.w);
+      }
+      *gp = gv;
+      const float2 h0 = cmulc(make_float2(o2.x, o2.y), g0), h1 = cmulc(make_float2(o2.z, o2.w), g1);
+      __stcs((float4*)(h_s + (size_t)k * NN + p), make_float4(h0.x, h0.y, h1.x, h1.y));
+    }
+  }
+  // every CTA's rows of the slice gradients are written (the scatter reads one
+  // row of the neighbour); also no CTA leaves while another reads its tile
+  cluster.sync();
+
+  // ---- per slice: scatter rows 64q .. 64q+63 (+ row N); position gradient -----------
+  float gyv = 0.f, gxv = 0.f;
+  const int y0 = rowbase, y1 = rowbase + LR + (q == Q - 1 ? 1 : 0);
+  constexpr int N1 = N + 1;
+  const float gx = 1.f - fx, gy = 1.f - fy;
+#pragma unroll 1
+  for (int s = 0; s < S; ++s) {
+    const float2* gsl = go_s + (size_t)s * NN;
+    if (a.gobj) {
+      float2* gplane = a.gobj + s * HW;
+      auto hrow = [&](int y, int x) {
+        float2 h = make_float2(0.f, 0.f);
+        if (y >= 0 && y < N) {
+          if (x < N) {
+            const float2 v = gsl[y * N + x];
+            h = make_float2(gx * v.x, gx * v.y);
+          }
+          if (x > 0) {
+            const float2 v = gsl[y * N + x - 1];
+            h.x = fmaf(fx, v.x, h.x);
+            h.y = fmaf(fx, v.y, h.y);
+          }
+        }
+        return h;
+      };
+      constexpr int SEG = T / N1 > 0 ? T / N1 : 1;
+      const int rows = y1 - y0, rs = (rows + SEG - 1) / SEG;
+      for (int item = tid; item < N1 * SEG; item += T) {
+        const int sg = item / N1, x = item % N1;
+        const int ya = y0 + sg * rs, yb = min(y1, ya + rs);
+        if (ya >= yb) continue;
+        float2 hp = hrow(ya - 1, x);
+        for (int y = ya; y < yb; ++y) {
+          const float2 hc = hrow(y, x);
+          atomicAdd(gplane + (size_t)(ty + y) * a.W + (tx + x),
+                    make_float2(fmaf(gy, hc.x, fy * hp.x), fmaf(gy, hc.y, fy * hp.y)));
+          hp = hc;
+        }
+      }
+    }
+    if (a.gpos) {
+      const float2* Os = a.obj + s * HW;
+      for (int pl = tid; pl < LNN; pl += T) {
+        const int r = rowbase + pl / N, c = pl % N;
+        const float2* o = Os + (size_t)(ty + r) * a.W + (tx + c);
+        const float2 O00 = __ldg(o), O01 = __ldg(o + 1), O10 = __ldg(o + a.W), O11 = __ldg(o + a.W + 1);
+        const float2 dy = make_float2((1.f - fx) * (O10.x - O00.x) + fx * (O11.x - O01.x),
+                                      (1.f - fx) * (O10.y - O00.y) + fx * (O11.y - O01.y));
+        const float2 dx = make_float2((1.f - fy) * (O01.x - O00.x) + fy * (O11.x - O10.x),
+                                      (1.f - fy) * (O01.y - O00.y) + fy * (O11.y - O10.y));
+        const float2 g = gsl[r * N + c];
+        gyv += g.x * dy.x + g.y * dy.y;
+        gxv += g.x * dx.x + g.y * dx.y;
+      }
+    }
+  }
+  if (a.gpos) {
+    double v[2] = {(double)gyv, (double)gxv};
+    block_sum<2>(v, red);
+    if (tid == 0) {
+      atomicAdd(a.gpos + 2 * j, (float)v[0]);
+      atomicAdd(a.gpos + 2 * j + 1, (float)v[1]);
+    }
+  }
+}
+
+}  // namespace cl
+
+template <class C>
+cudaError_t launch_ms_cluster(const MsArgs& a, cudaStream_t s, unsigned long long* done) {
+  cudaError_t e = smem_optin(cl::k_pass1_ms_cluster<C>, C::Smem::bytes, done);
+  if (e != cudaSuccess) return e;
+  if (a.nb <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(C::Q * a.nb));
+  cfg.blockDim = dim3(C::T);
+  cfg.dynamicSmemBytes = C::Smem::bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C::Q;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, cl::k_pass1_ms_cluster<C>, a);
+}
+
+}  // namespace ptycho

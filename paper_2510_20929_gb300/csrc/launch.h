@@ -10,6 +10,8 @@ struct MsArgs;
 // variant 0 = default CTA size, 1 = the alternative CTA size (autotuner)
 template <int N> cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s, int variant);
 template <int N> cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s, int variant);
-// multislice per-position pass (N <= 128)
+// multislice per-position pass
 template <int N> cudaError_t launch_pass1_ms(const MsArgs& a, cudaStream_t s);
+template <> cudaError_t launch_pass1_ms<192>(const MsArgs& a, cudaStream_t s);
+template <> cudaError_t launch_pass1_ms<256>(const MsArgs& a, cudaStream_t s);
 }  // namespace ptycho

@@ -1,0 +1,20 @@
+// Multislice per-position pass for the cluster windows: 256 x 256 (four CTAs)
+// and 192 x 192 (three CTAs).
+#include "kernels_ms_cluster.cuh"
+#include "launch.h"
+
+namespace ptycho {
+
+template <>
+cudaError_t launch_pass1_ms<256>(const MsArgs& a, cudaStream_t s) {
+  static unsigned long long done = 0;
+  return launch_ms_cluster<cl::Cfg256>(a, s, &done);
+}
+
+template <>
+cudaError_t launch_pass1_ms<192>(const MsArgs& a, cudaStream_t s) {
+  static unsigned long long done = 0;
+  return launch_ms_cluster<cl::Cfg192>(a, s, &done);
+}
+
+}  // namespace ptycho

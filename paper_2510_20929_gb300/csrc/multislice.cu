@@ -1,6 +1,7 @@
 // Multislice entry points (Pty-Chi Sec. 1 and Sec. 2.1: multislice modelling):
 // the angular-spectrum propagator, the forward model and the adjoint of the
-// multislice per-position pass (kernels_ms.cuh). Windows 16..128.
+// multislice per-position pass (kernels_ms.cuh; kernels_ms_cluster.cuh for the
+// 192 and 256 windows).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -67,7 +68,7 @@ ptycho_status check_ms(const ptycho_dims* d, const ptycho_multislice* ms) {
   const ptycho_status st = check_dims(d);
   if (st != PTYCHO_OK) return st;
   if (!ms || ms->reserved != 0) return PTYCHO_ERR_ARG;
-  if (ms->S < 1 || ms->S > 16 || d->N > 128) return PTYCHO_ERR_UNSUPPORTED;
+  if (ms->S < 1 || ms->S > 16) return PTYCHO_ERR_UNSUPPORTED;
   if (!(ms->wavelength > 0.0) || !(ms->pixel_size > 0.0) || !(fabs(ms->dz) < 1e300)) return PTYCHO_ERR_ARG;
   if ((int64_t)ms->S * d->H * d->W > ((int64_t)1 << 31) - 1) return PTYCHO_ERR_ARG;
   return PTYCHO_OK;
@@ -81,6 +82,8 @@ cudaError_t pass1_ms(int N, const MsArgs& a, cudaStream_t s) {
     case 32: e = launch_pass1_ms<32>(a, s); break;
     case 64: e = launch_pass1_ms<64>(a, s); break;
     case 128: e = launch_pass1_ms<128>(a, s); break;
+    case 192: e = launch_pass1_ms<192>(a, s); break;
+    case 256: e = launch_pass1_ms<256>(a, s); break;
   }
   profile_end(K_PASS1_MS, e0, s);
   return e;

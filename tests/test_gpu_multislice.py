@@ -41,6 +41,8 @@ CASES = [  # N, M, S, H, W, J, step, dz
     (32, 2, 4, 72, 76, 12, 6.0, 10e-6),
     (64, 3, 2, 150, 160, 10, 12.0, 4e-6),
     (128, 2, 4, 290, 300, 6, 30.0, 2e-6),
+    (192, 1, 2, 230, 236, 4, 12.0, 2e-6),
+    (256, 2, 3, 290, 296, 3, 12.0, 2e-6),
 ]
 
 
