@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["spiral128", "raster64", "uneven16", "uneven16opr", "spiral256"], default="spiral128")
+    ap.add_argument("--workload", choices=["spiral128", "raster64", "uneven16", "uneven16opr", "spiral256", "multislice256"], default="spiral128")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--positions", type=int, default=0,
@@ -518,6 +518,68 @@ def run_ad256(args, rank, world, local_rank):
         }), flush=True)
 
 
+def run_ms256(args, rank, world, local_rank):
+    """Multislice case: 4 slices of 2048^2, probe 256^2 with 4 modes, 8000
+    positions; a step is one Adam step on the slices and the probe (fused
+    multislice data term and adjoint over all positions, minibatches of 512
+    inside the library call)."""
+    import torch
+    from paper_2510_20929_gb300 import api, synth
+    from paper_2510_20929_gb300.autograd import data_term_ms
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = synth.workload_multislice256()
+    ms = api.make_multislice(w["S"], w["dz"], w["wavelength"], w["pixel_size"])
+    Os_true = torch.tensor(w["slices"], dtype=torch.complex64, device=dev)
+    P = torch.tensor(w["probe"], dtype=torch.complex64, device=dev)
+    pos = torch.tensor(w["pos"], dtype=torch.float32, device=dev)
+    I0 = api.forward_ms(Os_true, P, pos, ms, batch=w["batch"])
+    scale = w["total_counts"] / I0.sum(dim=(1, 2)).mean().item()
+    P *= math.sqrt(scale)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(101 + rank)
+    meas = torch.poisson(I0 * scale, generator=gen)
+    del I0
+    Os = torch.ones_like(Os_true).requires_grad_(True)
+    Pe = P.clone().requires_grad_(True)
+    opt = torch.optim.Adam([{"params": [Os], "lr": 1e-2}, {"params": [Pe], "lr": 1e-3}])
+
+    def step():
+        opt.zero_grad(set_to_none=True)
+        loss = data_term_ms(Os, Pe, pos, meas, ms, "gaussian", 1e-9, w["batch"])
+        loss.backward()
+        opt.step()
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    api.profile_enable(True)
+    api.profile_read()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        loss = step()
+    e1.record()
+    torch.cuda.synchronize()
+    prof = api.profile_read()
+    api.profile_enable(False)
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": job_throughput(w["J"], world, ms_step * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "multislice256-adam", "J": w["J"], "N": 256, "M": 4, "S": w["S"], "H": 2048,
+                       "W": 2048, "dz_m": w["dz"], "wavelength_m": w["wavelength"], "pixel_m": w["pixel_size"],
+                       "batch": w["batch"],
+                       "step": "one Adam step on the object slices and the probe (fused multislice data term "
+                               "and adjoint)"},
+            "kernels": {k: {"launches": n, "ms_per_launch": t / max(n, 1)} for k, (n, t) in prof.items()},
+            "final_loss": loss.item(),
+        }), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -537,6 +599,8 @@ def main():
             run_uneven(args, rank, world, local_rank, opr_K=8)
         elif args.workload == "spiral256":
             run_ad256(args, rank, world, local_rank)
+        elif args.workload == "multislice256":
+            run_ms256(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

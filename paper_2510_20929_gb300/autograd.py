@@ -99,9 +99,9 @@ class FarFieldMS(torch.autograd.Function):
 
 class DataTermMS(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, obj, probe, pos, meas, ms, noise="gaussian", eps=1e-9):
+    def forward(ctx, obj, probe, pos, meas, ms, noise="gaussian", eps=1e-9, batch=256):
         loss, gO, gP, gr = api.adjoint_ms(obj.contiguous(), probe.contiguous(), pos.contiguous(), meas.contiguous(),
-                                          ms, noise, eps=eps, positions_grad=True)
+                                          ms, noise, eps=eps, batch=batch, positions_grad=True)
         ctx.save_for_backward(gO, gP, gr)
         return loss
 
@@ -111,7 +111,7 @@ class DataTermMS(torch.autograd.Function):
         s = gL.to(torch.float32)
         need = ctx.needs_input_grad
         return (gO * s if need[0] else None, gP * s if need[1] else None, gr * s if need[2] else None,
-                None, None, None, None)
+                None, None, None, None, None)
 
 
 def far_field_ms(obj, probe, pos, ms):
@@ -119,9 +119,10 @@ def far_field_ms(obj, probe, pos, ms):
     return FarFieldMS.apply(obj, probe, pos, ms)
 
 
-def data_term_ms(obj, probe, pos, meas, ms, noise="gaussian", eps=1e-9):
-    """Scalar data term of the multislice model (differentiable in slices, probe, positions)."""
-    return DataTermMS.apply(obj, probe, pos, meas, ms, noise, eps)
+def data_term_ms(obj, probe, pos, meas, ms, noise="gaussian", eps=1e-9, batch=256):
+    """Scalar data term of the multislice model (differentiable in slices, probe, positions);
+    positions are processed in minibatches of ``batch`` inside the library call."""
+    return DataTermMS.apply(obj, probe, pos, meas, ms, noise, eps, batch)
 
 
 def data_term_opr(obj, U, w, P_rest, pos, meas, noise="gaussian", eps=1e-9):

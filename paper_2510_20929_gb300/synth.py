@@ -187,6 +187,22 @@ def workload_spiral256(seed: int = 1003, J: int = 10000, pos_error: float = 1.5)
                 pos_init=pos0, total_counts=1e6, counts_per="pattern")
 
 
+def workload_multislice256(seed: int = 1004, J: int = 8000, S: int = 4):
+    """Multislice case: S slices of 2048^2 (each with the object recipe, the
+    phase range divided among the slices), slice spacing 2 um, wavelength
+    0.1 nm, pixel 10 nm; probe 256^2 with 4 Hermite-Gaussian modes (power
+    halving per mode, waist 40 px); 8000 Fermat-spiral positions (c = 9.9 px);
+    minibatch 512."""
+    H = W = 2048
+    N = 256
+    slices = np.stack([make_object(H, W, seed * 10 + s, amp_lo=0.8 ** (1.0 / S), phase_max=0.5 / S)
+                       for s in range(S)])
+    probe = hg_probe(N, [0.5 ** k for k in range(4)], waist=40.0, quad_phase=0.005)
+    pos = fermat_spiral(J, 9.9, (H / 2.0, W / 2.0))
+    return dict(name="multislice256", H=H, W=W, N=N, M=4, S=S, J=J, batch=512, slices=slices, probe=probe,
+                pos=pos, dz=2e-6, wavelength=0.1e-9, pixel_size=10e-9, total_counts=1e6, counts_per="pattern")
+
+
 def workload_small(N: int = 16, M: int = 2, H: int = 40, W: int = 44, J: int = 12,
                    seed: int = 7, step: float = 4.0):
     """Small seeded problem for parity tests: raster positions with sub-pixel jitter."""
