@@ -373,6 +373,11 @@ typedef struct {
   double total_ms;
 } ptycho_kernel_time;
 ptycho_status ptycho_profile_enable(int32_t on);
+/* Restricts the recording to the kernel of this name (as reported by
+ * ptycho_profile_read), or records every kernel again for NULL. Returns 1, or
+ * 0 (and changes nothing) for an unknown name. Recording one kernel costs two
+ * event records per launch of that kernel only. */
+int32_t ptycho_profile_select(const char* name);
 int32_t ptycho_profile_read(ptycho_kernel_time* out, int32_t cap);
 
 /* Library version string. */

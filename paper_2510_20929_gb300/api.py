@@ -127,6 +127,7 @@ def lib() -> ctypes.CDLL:
             "ptycho_version": (ctypes.c_char_p, []),
             "ptycho_profile_enable": (ctypes.c_int, [ctypes.c_int32]),
             "ptycho_profile_read": (ctypes.c_int32, [ctypes.POINTER(KernelTime), ctypes.c_int32]),
+            "ptycho_profile_select": (ctypes.c_int32, [ctypes.c_char_p]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -140,8 +141,11 @@ def status_string(status: int) -> str:
     return lib().ptycho_status_string(int(status)).decode()
 
 
-def profile_enable(on: bool = True) -> None:
-    """Bracket every library kernel launch with CUDA events on its stream."""
+def profile_enable(on: bool = True, only: str | None = None) -> None:
+    """Bracket every library kernel launch (or only those of kernel ``only``)
+    with CUDA events on its stream."""
+    if not lib().ptycho_profile_select(only.encode() if only else None):
+        raise ValueError(f"unknown kernel name {only!r}")
     _check(lib().ptycho_profile_enable(1 if on else 0), "ptycho_profile_enable")
 
 

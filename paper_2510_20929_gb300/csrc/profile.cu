@@ -14,6 +14,7 @@ struct Pending {
 };
 std::mutex g_mu;
 bool g_on = false;
+int g_only = -1;   // record only this kernel id (-1: all)
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_pool;
 double g_ms[K_COUNT];
@@ -54,8 +55,7 @@ const char* kernel_name(int id) {
 bool profiling_on() { return g_on; }
 
 cudaEvent_t profile_begin(int id, cudaStream_t s) {
-  (void)id;
-  if (!g_on) return nullptr;
+  if (!g_on || (g_only >= 0 && id != g_only)) return nullptr;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -82,6 +82,20 @@ ptycho_status ptycho_profile_enable(int32_t on) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_on = on != 0;
   return PTYCHO_OK;
+}
+
+int32_t ptycho_profile_select(const char* name) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!name) {
+    g_only = -1;
+    return 1;
+  }
+  for (int id = 0; id < K_COUNT; ++id)
+    if (strcmp(name, kernel_name(id)) == 0) {
+      g_only = id;
+      return 1;
+    }
+  return 0;
 }
 
 int32_t ptycho_profile_read(ptycho_kernel_time* out, int32_t cap) {
