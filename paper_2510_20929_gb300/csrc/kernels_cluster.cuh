@@ -366,10 +366,11 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
   }
 
   // ---- back-propagation -------------------------------------------------------------
+  // modes last to first: the far fields written last are read first (L2)
   float2* g_s = a.g_s + slotNN;
   float2* h_s = a.h_s + slotNN * M;
 #pragma unroll 1
-  for (int k = 0; k < M; ++k) {
+  for (int k = M - 1; k >= 0; --k) {
     const float2* Pk = shared_mode<OPR>(a, k, NN);
     __syncthreads();
 #pragma unroll 2
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
       const float4 o2 = *(const float4*)(o_s + p);
       const float2 g0 = cmulc(make_float2(P2.x, P2.y), x0), g1 = cmulc(make_float2(P2.z, P2.w), x1);
       float4 gv = make_float4(g0.x, g0.y, g1.x, g1.y);
-      if (k > 0) {
+      if (k < M - 1) {
         const float4 gp = *(const float4*)(g_s + p);
         gv = make_float4(gv.x + gp.x, gv.y + gp.y, gv.z + gp.z, gv.w + gp.w);
       }
