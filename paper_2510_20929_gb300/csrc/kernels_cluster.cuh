@@ -102,53 +102,61 @@ __device__ __forceinline__ float2 wqmul(float2 a, int m, const float2* twq) {
   }
 }
 
-// Cross-cluster Q-point DFT of the tiles, in blocks of 64 columns.
+// Cross-cluster Q-point DFT of the tiles, in blocks of 64 columns, two blocks
+// per cluster barrier when the block count is even (the barrier orders every
+// CTA's reads of a block before its owner overwrites it; fewer, larger steps
+// halve the barrier latency).
 // Forward: tile_q <- W_N^(r q) sum_q' W_Q^(q' q) tile_q'.
 // Inverse: tile_q <- sum_k1 W_Q^(-q k1) conj(W_N^(r k1)) tile_k1.
 template <class C, bool FWD>
 __device__ __forceinline__ void cross_exchange(cg::cluster_group& cluster, float2* tile, const float2* twn,
                                                const float2* twq, int q) {
-  constexpr int Q = C::Q, P = C::XPAIRS;
+  constexpr int Q = C::Q, P = C::XPAIRS, XB = C::XB, GB = XB % 2 == 0 ? 2 : 1;
   float2* src[Q];
 #pragma unroll
   for (int qq = 0; qq < Q; ++qq) src[qq] = cluster.map_shared_rank(tile, qq);
 #pragma unroll 1
-  for (int h = 0; h < C::XB; ++h) {
-    float2 acc[P][2];
-    int rr[P], cc[P];
+  for (int h0 = 0; h0 < XB; h0 += GB) {
+    float2 acc[GB][P][2];
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-      const int p = 2 * (int)threadIdx.x + 2 * C::T * j;   // within a 64 x 64 block: 4096 pixels
-      rr[j] = p / 64;
-      cc[j] = 64 * h + p % 64;
-      acc[j][0] = acc[j][1] = make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int qq = 0; qq < Q; ++qq) {
+    for (int hh = 0; hh < GB; ++hh) {
+      const int h = h0 + hh;
 #pragma unroll
       for (int j = 0; j < P; ++j) {
-        float2 x0, x1;
-        load_pair(src[qq], C::tix(rr[j], cc[j]), x0, x1);
-        if constexpr (FWD) {
-          const int m = qq * q;
-          acc[j][0] = cadd(acc[j][0], wqmul<Q>(x0, m, twq));
-          acc[j][1] = cadd(acc[j][1], wqmul<Q>(x1, m, twq));
-        } else {
-          const float2 t = twn[rr[j] * qq];     // W_N^(r k1), conjugated below
-          const int m = -(q * qq);
-          acc[j][0] = cadd(acc[j][0], wqmul<Q>(cmulc(t, x0), m, twq));
-          acc[j][1] = cadd(acc[j][1], wqmul<Q>(cmulc(t, x1), m, twq));
+        const int p = 2 * (int)threadIdx.x + 2 * C::T * j;   // within a 64 x 64 block: 4096 pixels
+        const int rr = p / 64, cc = 64 * h + p % 64;
+        acc[hh][j][0] = acc[hh][j][1] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int qq = 0; qq < Q; ++qq) {
+          float2 x0, x1;
+          load_pair(src[qq], C::tix(rr, cc), x0, x1);
+          if constexpr (FWD) {
+            const int m = qq * q;
+            acc[hh][j][0] = cadd(acc[hh][j][0], wqmul<Q>(x0, m, twq));
+            acc[hh][j][1] = cadd(acc[hh][j][1], wqmul<Q>(x1, m, twq));
+          } else {
+            const float2 t = twn[rr * qq];     // W_N^(r k1), conjugated below
+            const int m = -(q * qq);
+            acc[hh][j][0] = cadd(acc[hh][j][0], wqmul<Q>(cmulc(t, x0), m, twq));
+            acc[hh][j][1] = cadd(acc[hh][j][1], wqmul<Q>(cmulc(t, x1), m, twq));
+          }
         }
       }
     }
-    cluster.sync();   // every CTA has read this block of every tile
+    cluster.sync();   // every CTA has read these blocks of every tile
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
-      if constexpr (FWD) {
-        const float2 t = twn[rr[j] * q];
-        store_pair(tile, C::tix(rr[j], cc[j]), cmul(acc[j][0], t), cmul(acc[j][1], t));
-      } else {
-        store_pair(tile, C::tix(rr[j], cc[j]), acc[j][0], acc[j][1]);
+    for (int hh = 0; hh < GB; ++hh) {
+      const int h = h0 + hh;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const int p = 2 * (int)threadIdx.x + 2 * C::T * j;
+        const int rr = p / 64, cc = 64 * h + p % 64;
+        if constexpr (FWD) {
+          const float2 t = twn[rr * q];
+          store_pair(tile, C::tix(rr, cc), cmul(acc[hh][j][0], t), cmul(acc[hh][j][1], t));
+        } else {
+          store_pair(tile, C::tix(rr, cc), acc[hh][j][0], acc[hh][j][1]);
+        }
       }
     }
   }
