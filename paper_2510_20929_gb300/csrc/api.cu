@@ -48,6 +48,7 @@ __global__ void k_probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const flo
                                int accumulate, float* Dp, const float4* __restrict__ acc, int HW,
                                BatchScalars* sc) {
   __shared__ float red[32];
+  wait_prior_grid();
   if (blockIdx.y == 1) {
     if (!acc) return;
     float m = 0.f;
@@ -108,6 +109,7 @@ __global__ void k_probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const flo
 __global__ void k_norm_probe(int NN, int M, const float2* dPacc, const float* Dp, const float2* probe,
                              float delta_p, int update_probe, const BatchScalars* sc, float2* dP, float2* Cp,
                              float* Sdp) {
+  wait_prior_grid();
   const float damp = delta_p * __uint_as_float(sc->max_dp);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += gridDim.x * blockDim.x) {
     float2 c = make_float2(0.f, 0.f);
@@ -129,6 +131,7 @@ __global__ void k_norm_probe(int NN, int M, const float2* dPacc, const float* Dp
 // batch's scalars.
 __global__ void k_probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
                                const BatchScalars* sc, BatchScalars* sc_next) {
+  wait_prior_grid();
   const float mean_ap = sc->count > 0 ? (float)(sc->sum_alpha_p / (double)sc->count) : 0.f;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += gridDim.x * blockDim.x) {
     float s = 0.f;
@@ -216,6 +219,13 @@ __global__ void k_pos_apply(int nb, int b0, const int* __restrict__ order, const
   const double x = fmin(fmax((double)pos[2 * j + 1] + step * dx, lo), (double)W - lo - margin);
   pos[2 * j] = (float)y;
   pos[2 * j + 1] = (float)x;
+}
+
+// Zeroes n float4 (the object-frame accumulator of one minibatch).
+__global__ void k_clear_plane(size_t n, float4* acc) {
+  wait_prior_grid();
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+    acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // O += dO (the epoch's accumulated object update).
@@ -384,10 +394,10 @@ cudaError_t probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* h
   int bx = (threads + 255) / 256;
   if (acc && bx < 2 * 152) bx = 2 * 152;
   dim3 grid(bx > 0 ? bx : 1, acc ? 2 : 1);
-  k_probe_reduce<16><<<grid, 256, 0, s>>>(NN, k0, Mc, Ms, nb, h_s, o_s, valid, dPacc, accumulate, Dp, acc, HW,
-                                          sc);
+  const cudaError_t e = launch_pdl(k_probe_reduce<16>, grid, dim3(256), 0, s, NN, k0, Mc, Ms, nb, h_s, o_s, valid,
+                                   dPacc, accumulate, Dp, acc, HW, sc);
   profile_end(K_PROBE_REDUCE, e0, s);
-  return cudaGetLastError();
+  return e;
 }
 
 int grid_for(size_t n, int threads, int cap) {
@@ -400,17 +410,16 @@ cudaError_t norm_probe(int NN, int M, const float2* dPacc, const float* Dp, cons
                        int update_probe, const BatchScalars* sc, float2* dP, float2* Cp, float* Sdp,
                        cudaStream_t s) {
   return timed(K_NORM_PROBE, s, [&] {
-    k_norm_probe<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, dPacc, Dp, probe, delta_p, update_probe, sc, dP, Cp,
-                                                        Sdp);
-    return cudaGetLastError();
+    return launch_pdl(k_norm_probe, dim3(grid_for(NN, 256, 152)), dim3(256), 0, s, NN, M, dPacc, Dp, probe, delta_p,
+                      update_probe, sc, dP, Cp, Sdp);
   });
 }
 
 cudaError_t probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
                          const BatchScalars* sc, BatchScalars* sc_next, cudaStream_t s) {
   return timed(K_UPDATE, s, [&] {
-    k_probe_update<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, probe, dP, Sp, update_probe, sc, sc_next);
-    return cudaGetLastError();
+    return launch_pdl(k_probe_update, dim3(grid_for(NN, 256, 152)), dim3(256), 0, s, NN, M, probe, dP, Sp,
+                      update_probe, sc, sc_next);
   });
 }
 
@@ -441,7 +450,10 @@ cudaError_t tile_illum_max(const ptycho_dims& d, int nb, int b0, const float* po
 
 cudaError_t clear_acc(bool tiles, const ptycho_dims& d, int nb, int b0, const float* pos, const int32_t* order,
                       const int* valid, float4* acc, cudaStream_t s) {
-  if (!tiles) return cudaMemsetAsync(acc, 0, (size_t)d.H * d.W * sizeof(float4), s);
+  if (!tiles) {
+    const size_t n = (size_t)d.H * d.W;
+    return launch_pdl(k_clear_plane, dim3(grid_for(n, 256, 8 * 152)), dim3(256), 0, s, n, acc);
+  }
   return timed(K_TILE_CLEAR, s, [&] {
     k_tile_clear<<<tile_grid(nb, d.N), 256, 0, s>>>(d.N, d.H, d.W, d.J, pos, order, b0, valid, acc);
     return cudaGetLastError();

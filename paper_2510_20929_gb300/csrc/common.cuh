@@ -158,6 +158,30 @@ __device__ __forceinline__ float2 opr_pixel(const float2* __restrict__ V, const 
   return s;
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream serialization attribute may start while its predecessor on the
+// stream drains; it waits here, before its first global memory access, until
+// the predecessor has completed and its writes are visible (a no-op for a
+// kernel launched without the attribute).
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+// Launches `kernel` with the programmatic stream serialization attribute.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 // Tile origin and fraction of a probe-centre position; false if the bilinear
 // (N+1)^2 tile is not inside the object or the value is not finite.
 __device__ __forceinline__ bool tile_of(float py, float px, int N, int H, int W, int& ty, int& tx,

@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
   using SM = Pass1Smem<N>;
   constexpr int R1 = F::R1, R2 = F::R2, NN = N * N, RP = SM::RP;
   extern __shared__ __align__(16) unsigned char smem[];
+  wait_prior_grid();
   double* red = (double*)(smem + SM::red);
   float2* tile = (float2*)(smem + SM::tile);
   float2* tw = (float2*)(smem + SM::tw);
@@ -426,6 +427,7 @@ __device__ __forceinline__ float2 dohat(const float4* q, int W, float w00, float
 template <int N, int T, bool OPR>
 __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
   constexpr int NN = N * N;
+  wait_prior_grid();
   __shared__ double red[32 * 5];
   __shared__ double alpha_sh;
   const int slot = blockIdx.x, tid = threadIdx.x;
@@ -572,8 +574,7 @@ cudaError_t launch_pass1_t(const BatchArgs& a, cudaStream_t s) {
   cudaError_t e = smem_optin(k_pass1<N, T, OPR>, sm, &done);
   if (e != cudaSuccess) return e;
   if (a.nb <= 0) return cudaSuccess;
-  k_pass1<N, T, OPR><<<a.nb, T, sm, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_pass1<N, T, OPR>, dim3(a.nb), dim3(T), sm, s, a);
 }
 
 // variant 0: default CTA size, 1: the alternative (the relaxed-probe form has
@@ -588,10 +589,9 @@ cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s, int variant) {
 template <int N>
 cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s, int variant) {
   if (a.nb <= 0) return cudaSuccess;
-  if (a.opr_dU) k_pass2<N, PASS2_T, true><<<a.nb, PASS2_T, 0, s>>>(a);
-  else if (variant == 1) k_pass2<N, PASS2_ALT, false><<<a.nb, PASS2_ALT, 0, s>>>(a);
-  else k_pass2<N, PASS2_T, false><<<a.nb, PASS2_T, 0, s>>>(a);
-  return cudaGetLastError();
+  if (a.opr_dU) return launch_pdl(k_pass2<N, PASS2_T, true>, dim3(a.nb), dim3(PASS2_T), 0, s, a);
+  if (variant == 1) return launch_pdl(k_pass2<N, PASS2_ALT, false>, dim3(a.nb), dim3(PASS2_ALT), 0, s, a);
+  return launch_pdl(k_pass2<N, PASS2_T, false>, dim3(a.nb), dim3(PASS2_T), 0, s, a);
 }
 
 }  // namespace ptycho
