@@ -452,7 +452,9 @@ cudaError_t clear_acc(bool tiles, const ptycho_dims& d, int nb, int b0, const fl
                       const int* valid, float4* acc, cudaStream_t s) {
   if (!tiles) {
     const size_t n = (size_t)d.H * d.W;
-    return launch_pdl(k_clear_plane, dim3(grid_for(n, 256, 8 * 152)), dim3(256), 0, s, n, acc);
+    return timed(K_CLEAR_PLANE, s, [&] {
+      return launch_pdl(k_clear_plane, dim3(grid_for(n, 256, 8 * 152)), dim3(256), 0, s, n, acc);
+    });
   }
   return timed(K_TILE_CLEAR, s, [&] {
     k_tile_clear<<<tile_grid(nb, d.N), 256, 0, s>>>(d.N, d.H, d.W, d.J, pos, order, b0, valid, acc);
