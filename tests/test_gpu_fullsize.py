@@ -180,3 +180,115 @@ def test_spiral256_adam_on_all_three_reduces_loss_and_position_error(spiral256):
     rmse = (pos - pos_true).pow(2).mean().sqrt().item()
     print("spiral256 Adam: loss", hist[0], "->", hist[-1], "position rmse", rmse0, "->", rmse)
     assert hist[-1] < 0.7 * hist[0] and rmse < 0.95 * rmse0
+
+
+# --------------------------------------------------------------------------- multislice (4 slices of 2048^2)
+@pytest.fixture(scope="module")
+def multislice256():
+    return synth.workload_multislice256()
+
+
+def test_multislice256_sampled_forward_and_gradients_match_oracle(multislice256):
+    # the full 4 x 2048^2 slices and the 4-mode 256^2 probe with the workload's
+    # propagator; forward and gradients over four sampled positions, in the
+    # launch configuration of the bench (minibatch 512)
+    import torch
+    from paper_2510_20929_gb300 import api
+    w = multislice256
+    idx = np.array([3, 2100, 5555, 7999])
+    Os = _f32(w["slices"], True)
+    P = _f32(w["probe"] * 4.0, True)
+    pos = _f32(w["pos"][idx])
+    Hf = orc.asm_propagator(256, w["pixel_size"], w["wavelength"], w["dz"])
+    ms = api.make_multislice(w["S"], w["dz"], w["wavelength"], w["pixel_size"])
+    dOs, dP, dpos = to_dev(Os, torch.complex64), to_dev(P, torch.complex64), to_dev(pos, torch.float32)
+    I = api.forward_ms(dOs, dP, dpos, ms, batch=w["batch"]).cpu().numpy()
+    ref = orc.forward_ms(Os, P, pos, Hf)
+    e_fwd = rel(I, ref)
+    I_m = _f32(synth.poisson_counts(ref * 1.05, 9))
+    L, gO, gP, gr = orc.loss_and_gradients_ms(Os, P, pos, Hf, I_m, orc.GAUSSIAN, 1e-6)
+    loss, dgO, dgP, dgr = api.adjoint_ms(dOs, dP, dpos, to_dev(I_m, torch.float32), ms, "gaussian", eps=1e-6,
+                                         batch=w["batch"])
+    e = (e_fwd, abs(loss.item() - L) / L, rel(dgO.cpu().numpy(), gO), rel(dgP.cpu().numpy(), gP),
+         rel(dgr.cpu().numpy(), gr))
+    print("multislice256 sampled:", e)
+    assert e[0] < 10 * TOL_FWD and e[1] < TOL_FWD and max(e[2:]) < TOL_EPOCH
+
+
+def test_multislice256_adam_over_all_positions_reduces_the_loss(multislice256):
+    import torch
+    from paper_2510_20929_gb300 import api
+    from paper_2510_20929_gb300.autograd import reconstruct_adam_ms
+    w = multislice256
+    ms = api.make_multislice(w["S"], w["dz"], w["wavelength"], w["pixel_size"])
+    Os_true = to_dev(_f32(w["slices"], True), torch.complex64)
+    P = to_dev(_f32(w["probe"] * 4.0, True), torch.complex64)
+    pos = to_dev(_f32(w["pos"]), torch.float32)
+    I_m = api.forward_ms(Os_true, P, pos, ms, batch=w["batch"])
+    Os = torch.ones_like(Os_true)
+    hist = reconstruct_adam_ms(Os, P.clone(), pos, I_m, ms, epochs=6, lr_object=1e-2, update=("object",))
+    print("multislice256 Adam:", hist)
+    assert all(math.isfinite(h) for h in hist) and hist[-1] < 0.8 * hist[0]
+
+
+# --------------------------------------------------------------------------- uneven serving with OPR (16 reconstructions)
+def test_uneven16_opr_batched_epoch_matches_oracle_on_sampled_minibatches():
+    # three reconstructions of the serving mix (windows 64, 128 and 192 with
+    # their full objects and 8 eigenmodes), one batched graph-replayed epoch
+    # over the first positions of each (the oracle's scatter is O(H W) per
+    # position, so it takes the reconstructions with the smallest objects),
+    # against the oracle's minibatch
+    import torch
+    from paper_2510_20929_gb300 import api
+    ws = synth.workload_uneven(16, seed=1005, opr_K=8)
+    recons, opts, oprs, refs = [], [], [], []
+    for i, n in ((12, 64), (0, 64), (1, 16)):
+        w = ws[i]
+        O_true = _f32(w["object"], True)
+        pos = _f32(w["pos"][:n])
+        wt = _f32(w["opr_w"][:n])
+        I0 = orc.forward_opr(O_true, _f32(w["opr_U"], True), wt, None, pos)
+        sc = math.sqrt(w["total_counts"] / w["J"] / I0.sum(axis=(1, 2)).mean())
+        U = _f32(w["opr_U"] * sc, True)
+        Im = _f32(synth.poisson_counts(I0 * sc * sc, 100 + i))
+        O0, w0 = np.ones_like(O_true), np.ones((n, 8))
+        refs.append(orc.lsqml_batch_opr(O0, U, w0, None, pos, Im, np.arange(n),
+                                        orc.LsqmlOptions(batch=n, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6),
+                                        orc.OprOptions()))
+        recons.append([to_dev(O0, torch.complex64), to_dev(U, torch.complex64), to_dev(w0, torch.float32), None,
+                       to_dev(pos, torch.float32), to_dev(Im, torch.float32), None])
+        opts.append(api.make_opts(batch=n, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6, graph=True))
+        oprs.append(api.make_opr_opts(8))
+    losses = api.lsqml_epoch_opr_batched(recons, opts, oprs).cpu().numpy()
+    for (dO, dU, dw, _, _, _, _), (O1, U1, w1, _, L1, _), L in zip(recons, refs, losses):
+        e = (rel(dO.cpu().numpy(), O1), rel(dU.cpu().numpy(), U1), rel(dw.cpu().numpy(), w1), abs(L - L1) / L1)
+        print("uneven16opr first positions:", " ".join(f"{x:.2e}" for x in e))
+        assert max(e) < TOL_EPOCH
+
+
+def test_uneven16_opr_full_epochs_are_finite_and_lower_every_data_term():
+    # all 16 reconstructions at full size (194,169 positions), data from the
+    # GPU forward model with the true weights, three batched epochs from unit weights
+    import torch
+    from paper_2510_20929_gb300 import api
+    dev = torch.device("cuda", 0)
+    ws = synth.workload_uneven(16, seed=1005, opr_K=8)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    recons = []
+    for w in ws:
+        Ot = torch.tensor(w["object"], dtype=torch.complex64, device=dev)
+        pos = torch.tensor(w["pos"], dtype=torch.float32, device=dev)
+        U = torch.tensor(w["opr_U"], dtype=torch.complex64, device=dev)
+        wt = torch.tensor(w["opr_w"], dtype=torch.float32, device=dev)
+        I0 = api.forward_opr(Ot, U, wt, None, pos)
+        s = w["total_counts"] / I0.sum().item()
+        U *= math.sqrt(s)
+        recons.append([torch.ones_like(Ot), U, torch.ones_like(wt), None, pos, torch.poisson(I0 * s, generator=gen),
+                       torch.tensor(synth.random_order(w["J"], 3), dtype=torch.int32, device=dev)])
+        del Ot, I0
+    opts = [api.make_opts(batch=w["batch"], graph=True) for w in ws]
+    hist = [api.lsqml_epoch_opr_batched(recons, opts, api.make_opr_opts(8)).cpu().numpy() for _ in range(3)]
+    print("uneven16opr losses per epoch:", [h.sum() for h in hist])
+    assert all(np.isfinite(h).all() for h in hist)
+    assert np.all(hist[2] < hist[0])
