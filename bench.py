@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", choices=["spiral128", "raster64", "uneven16", "uneven16opr", "spiral256", "multislice256"], default="spiral128")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precision", choices=["fp32", "bf16x3"], default="fp32",
+                    help="far-field arithmetic of the timed epochs: FP32 FFTs or split-BF16 DFT-GEMMs")
     ap.add_argument("--positions", type=int, default=0,
                     help="use only the first J positions of the workload (profiling runs)")
     return ap.parse_args()
@@ -58,6 +60,18 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+FALLBACK_BF16_SUSTAINED = 1700.0
+
+
+def bf16_peak():
+    """Sustained dense BF16 tensor peak (TFLOP/s): the DFT-GEMM kernel runs inside a long step."""
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured (sustained bf16)"
+    except Exception:
+        return FALLBACK_BF16_SUSTAINED, "fallback (sustained bf16)"
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_pass1_traffic.txt")
@@ -116,6 +130,17 @@ def pass1_work(N, M, B):
     flops = B * 2 * M * 5 * N * N * math.log2(N * N)
     nbytes = B * (4 * N * N + 8 * (N + 1) ** 2 + 8 * (2 + M) * N * N + 32 * (N + 1) ** 2)
     return flops, nbytes
+
+
+def far_tc_work(N, M, B):
+    """Per-launch tensor FLOPs of the split-BF16 DFT-GEMM far-field stage.
+
+    Each 2-D transform is two passes of four real 128 x N x N GEMMs (the DFT
+    operand has 128 rows, zero beyond N), each with three split terms; a
+    position takes M forward and M inverse transforms.
+    """
+    per_transform = 2 * 4 * 3 * 2 * 128 * N * N
+    return B * 2 * M * per_transform
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -253,7 +278,8 @@ def run_ours(args, rank, world, local_rank):
     order = torch.tensor(synth.random_order(J, 5 + rank), dtype=torch.int32, device=dev)
     O = torch.ones((H, W), dtype=torch.complex64, device=dev)
     P_est = P.clone()
-    opts = api.make_opts(noise="gaussian", batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9, autotune=True)
+    opts = api.make_opts(noise="gaussian", batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9, autotune=True,
+                         precision=args.precision)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -326,6 +352,15 @@ def run_ours(args, rank, world, local_rank):
                      "algorithmic_bytes_per_launch": nbytes, "algorithmic_flops_per_launch": flops})
         if N == 128 and M == 5 and B == 256:
             roof["traffic"] = recorded_traffic("k_pass1")
+    elif dom_name == "k_far_tc":
+        nb_list = [min(B, J - b0) for b0 in range(0, J, B)]
+        tot_flops = sum(far_tc_work(N, M, nb) for nb in nb_list) * (dom_n // len(nb_list))
+        t_s = dom_ms * 1e-3
+        peak, src = bf16_peak()
+        ach = tot_flops / t_s * 1e-12
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": src, "kernel": dom_name, "launch_ms": dom_ms / dom_n,
+                "algorithmic_flops_per_launch": far_tc_work(N, M, B)}
     else:
         roof = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
                 "traffic": None, "kernel": dom_name}
@@ -333,9 +368,10 @@ def run_ours(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16x3 (f32 accumulate)",
+        "data": "synthetic",
         "config": {"workload": w["name"], "J": J, "N": N, "M": M, "H": H, "W": W, "batch": B,
-                   "noise": "gaussian", "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "noise": "gaussian", "precision": args.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (measured intensities %.0f MB read every epoch)"
                          % (J * N * N * 4 / 1e6),
                    "profiler": "CUDA event pair around every launch of the dominant kernel in every %d-th "

@@ -60,7 +60,7 @@ typedef enum {
   PTYCHO_ERR_BOUNDS = 2,      /* (device) a position's tile leaves the object, or a bad order entry */
   PTYCHO_ERR_NONFINITE = 3,   /* (device) negative or non-finite measured intensity */
   PTYCHO_ERR_CUDA = 4,        /* a CUDA runtime call failed */
-  PTYCHO_ERR_TIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+  PTYCHO_ERR_TIMEOUT = 5,     /* (device) a bounded wait of the tensor-core pipeline gave up */
   PTYCHO_ERR_UNSUPPORTED = 6, /* window size or mode count not built */
   PTYCHO_ERR_WORKSPACE = 7,   /* workspace missing, misaligned or too small */
   PTYCHO_ERR_TOO_LARGE = 8    /* problem needs more scratch than ptycho_lsqml_epoch_static holds */
@@ -84,7 +84,7 @@ typedef struct {
                                once at its end (the update cadence LSQML takes with the
                                compact sampler, Sec. 2.2); needs the larger workspace of
                                ptycho_workspace_bytes_opts */
-  int32_t reserved;         /* must be zero */
+  int32_t precision;        /* PTYCHO_PRECISION_FP32 or PTYCHO_PRECISION_BF16X3 */
   double delta_o;           /* object preconditioner damping, relative to max(illumination) */
   double delta_p;           /* probe preconditioner damping, relative to max(sum_j |o_j|^2) */
   double lambda_reg;        /* 2x2 step-size Tikhonov term, relative to trace/2 */
@@ -92,6 +92,18 @@ typedef struct {
   double pos_step;          /* relaxation of the position step (1 = the least-squares step) */
   double pos_max_shift;     /* clamp of each component of a minibatch's position step, px */
 } ptycho_lsqml_opts;
+
+/* opts->precision: how the far-field transforms F and F^-1 are evaluated.
+ * FP32: shared-memory radix FFTs in FP32 (every window size).
+ * BF16X3: the 2-D DFT as dense complex GEMMs on the tensor cores (tcgen05,
+ * FP32 accumulation in tensor memory) with every operand split into BF16
+ * hi + lo parts and three products per real product (hi*hi + lo*hi + hi*lo);
+ * windows N = 32, 64 and 128 (others: PTYCHO_ERR_UNSUPPORTED), the shared
+ * probe only (the relaxed-probe and multislice entry points take FP32). Its
+ * per-element error against exact arithmetic is about 2^-17 of the operand
+ * magnitudes, accumulated over N terms per pass. */
+#define PTYCHO_PRECISION_FP32 0
+#define PTYCHO_PRECISION_BF16X3 1
 
 /* opts->flags: capture the epoch's launch sequence into a CUDA graph on the
  * first call with a given set of arguments (pointers, sizes, options) and
@@ -141,6 +153,19 @@ ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const
                              const float* pos, const float* meas, int32_t noise, double eps,
                              int32_t batch, float* g_object, float* g_probe, float* g_pos,
                              double* loss, void* ws, size_t ws_bytes, void* stream);
+
+/* ptycho_forward and ptycho_adjoint with the far-field precision chosen
+ * (PTYCHO_PRECISION_*). The forward form processes positions in chunks of
+ * `batch` and then needs ptycho_workspace_bytes(dims, batch) of workspace
+ * (with FP32 the header suffices, as for ptycho_forward). */
+ptycho_status ptycho_forward_ex(const ptycho_dims* dims, int32_t precision, int32_t batch,
+                                const float* object, const float* probe, const float* pos,
+                                float* I_pred, void* ws, size_t ws_bytes, void* stream);
+ptycho_status ptycho_adjoint_ex(const ptycho_dims* dims, int32_t precision, const float* object,
+                                const float* probe, const float* pos, const float* meas,
+                                int32_t noise, double eps, int32_t batch, float* g_object,
+                                float* g_probe, float* g_pos, double* loss, void* ws,
+                                size_t ws_bytes, void* stream);
 
 /* One LSQML epoch (Sec. 2.2): minibatches of opts->batch positions taken from
  * `order` (int32 [J], a permutation or any list of indices in [0, J); NULL =
@@ -352,8 +377,9 @@ ptycho_status ptycho_sampler_order(const float* pos, int32_t J, int32_t batch, i
                                    int32_t* order);
 
 /* Synchronises `stream`, returns (and clears) the device-side status recorded
- * in `ws` since the last read: PTYCHO_OK, PTYCHO_ERR_BOUNDS or
- * PTYCHO_ERR_NONFINITE (bounds reported first), or PTYCHO_ERR_CUDA. */
+ * in `ws` since the last read: PTYCHO_OK, PTYCHO_ERR_TIMEOUT, PTYCHO_ERR_BOUNDS
+ * or PTYCHO_ERR_NONFINITE (reported in that order of precedence), or
+ * PTYCHO_ERR_CUDA. */
 ptycho_status ptycho_status_read(void* ws, void* stream);
 
 /* Static description of a status code. */

@@ -50,7 +50,7 @@ class LsqmlOpts(ctypes.Structure):
     _fields_ = [("noise", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("update_object", ctypes.c_int32), ("update_probe", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("update_positions", ctypes.c_int32),
-                ("object_per_epoch", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("object_per_epoch", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("delta_o", ctypes.c_double), ("delta_p", ctypes.c_double),
                 ("lambda_reg", ctypes.c_double), ("eps", ctypes.c_double),
                 ("pos_step", ctypes.c_double), ("pos_max_shift", ctypes.c_double)]
@@ -109,6 +109,11 @@ def lib() -> ctypes.CDLL:
             "ptycho_host_workspace_bytes": (ctypes.c_size_t, [dims_p, ctypes.c_int32]),
             "ptycho_workspace_init": (ctypes.c_int, [_P, ctypes.c_size_t, _P]),
             "ptycho_forward": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+            "ptycho_forward_ex": (ctypes.c_int, [dims_p, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P,
+                                                 ctypes.c_size_t, _P]),
+            "ptycho_adjoint_ex": (ctypes.c_int, [dims_p, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32,
+                                                 ctypes.c_double, ctypes.c_int32, _P, _P, _P, _P, _P,
+                                                 ctypes.c_size_t, _P]),
             "ptycho_adjoint": (ctypes.c_int, [dims_p, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double,
                                               ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
             "ptycho_lsqml_epoch": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, opts_p, _P, _P, _P,
@@ -238,22 +243,34 @@ def _finish(ws: Workspace, where: str, check: bool):
         _check(ws.status(), where)
 
 
-def forward(obj, probe, pos, *, check: bool = True):
-    """Predicted intensities I [J, N, N] = sum_k |F(P_k S_j(O))|^2."""
+PRECISIONS = {"fp32": 0, "bf16x3": 1}
+
+
+def _precision(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def forward(obj, probe, pos, *, precision="fp32", batch: int = 256, check: bool = True):
+    """Predicted intensities I [J, N, N] = sum_k |F(P_k S_j(O))|^2.
+
+    ``precision`` "bf16x3" evaluates F as split-BF16 DFT-GEMMs on the tensor
+    cores (windows 32, 64, 128), in chunks of ``batch`` positions."""
     _need(obj, "object", torch.complex64)
     _need(probe, "probe", torch.complex64, device=obj.device)
     _need(pos, "positions", torch.float32, device=obj.device)
     d = dims_of(obj, probe, pos)
     I = torch.empty((d.J, d.N, d.N), dtype=torch.float32, device=obj.device)
-    ws = workspace(d, 1, obj.device)
-    _check(lib().ptycho_forward(ctypes.byref(d), _ptr(obj), _ptr(probe), _ptr(pos), _ptr(I),
-                                _P(ws.ptr), ws.nbytes, _stream()), "ptycho_forward")
-    _finish(ws, "ptycho_forward", check)
+    pr = _precision(precision)
+    B = max(1, min(int(batch), max(d.J, 1)))
+    ws = workspace(d, B if pr else 1, obj.device)
+    _check(lib().ptycho_forward_ex(ctypes.byref(d), pr, B, _ptr(obj), _ptr(probe), _ptr(pos), _ptr(I),
+                                   _P(ws.ptr), ws.nbytes, _stream()), "ptycho_forward_ex")
+    _finish(ws, "ptycho_forward_ex", check)
     return I
 
 
 def adjoint(obj, probe, pos, meas, noise="gaussian", eps: float = 0.0, batch: int = 256, *,
-            positions_grad: bool = True, check: bool = True):
+            positions_grad: bool = True, precision="fp32", check: bool = True):
     """Loss and gradients (grad = 2 dL/dz*): returns (loss, g_object, g_probe, g_pos).
 
     ``noise`` is "gaussian", "poisson", or "vjp" (then ``meas`` holds dL/dI and
@@ -271,11 +288,11 @@ def adjoint(obj, probe, pos, meas, noise="gaussian", eps: float = 0.0, batch: in
     gr = torch.zeros((d.J, 2), dtype=torch.float32, device=obj.device) if positions_grad else None
     loss = torch.zeros((), dtype=torch.float64, device=obj.device)
     ws = workspace(d, B, obj.device)
-    _check(lib().ptycho_adjoint(ctypes.byref(d), _ptr(obj), _ptr(probe), _ptr(pos), _ptr(meas), nz,
-                                float(eps), B, _ptr(gO), _ptr(gP), _ptr(gr),
-                                _ptr(loss) if nz != VJP else _P(0), _P(ws.ptr), ws.nbytes, _stream()),
-           "ptycho_adjoint")
-    _finish(ws, "ptycho_adjoint", check)
+    _check(lib().ptycho_adjoint_ex(ctypes.byref(d), _precision(precision), _ptr(obj), _ptr(probe), _ptr(pos),
+                                   _ptr(meas), nz, float(eps), B, _ptr(gO), _ptr(gP), _ptr(gr),
+                                   _ptr(loss) if nz != VJP else _P(0), _P(ws.ptr), ws.nbytes, _stream()),
+           "ptycho_adjoint_ex")
+    _finish(ws, "ptycho_adjoint_ex", check)
     return (None if nz == VJP else loss), gO, gP, gr
 
 
@@ -299,7 +316,7 @@ def make_opts(noise="gaussian", batch: int = 256, delta_o: float = 0.1, delta_p:
               lam: float = 1e-6, eps: float = 1e-9, update_object: bool = True,
               update_probe: bool = True, graph: bool = False, autotune: bool = False,
               update_positions: bool = False, pos_step: float = 1.0, pos_max_shift: float = 1.0,
-              object_per_epoch: bool = False) -> LsqmlOpts:
+              object_per_epoch: bool = False, precision="fp32") -> LsqmlOpts:
     o = LsqmlOpts()
     o.flags = (FLAG_GRAPH if graph else 0) | (FLAG_AUTOTUNE if autotune else 0)
     o.noise = _NOISE[noise] if isinstance(noise, str) else int(noise)
@@ -308,6 +325,7 @@ def make_opts(noise="gaussian", batch: int = 256, delta_o: float = 0.1, delta_p:
     o.update_probe = int(bool(update_probe))
     o.update_positions = int(bool(update_positions))
     o.object_per_epoch = int(bool(object_per_epoch))
+    o.precision = _precision(precision)
     o.delta_o, o.delta_p, o.lambda_reg, o.eps = float(delta_o), float(delta_p), float(lam), float(eps)
     o.pos_step, o.pos_max_shift = float(pos_step), float(pos_max_shift)
     return o

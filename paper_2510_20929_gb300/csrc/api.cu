@@ -271,6 +271,12 @@ Layout make_layout(const ptycho_dims& d, int B, int K, bool epoch_object) {
   }
   L.possum = take((size_t)B * 5 * sizeof(double));
   L.dOe = epoch_object ? take(HW * sizeof(float2)) : 0;
+  L.dft = 0;
+  switch (d.N) {
+    case 32: L.dft = take(dft_plane_bytes<32>()); break;
+    case 64: L.dft = take(dft_plane_bytes<64>()); break;
+    case 128: L.dft = take(dft_plane_bytes<128>()); break;
+  }
   L.total = off;
   return L;
 }
@@ -321,6 +327,44 @@ cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s, int variant) {
     return dispatch_N(N, [&](auto c) { return launch_pass1<decltype(c)::value>(a, s, variant); });
   });
 }
+bool dft_gemm_supported(int N) { return N == 32 || N == 64 || N == 128; }
+
+ptycho_status check_precision(int N, int precision) {
+  if (precision == PTYCHO_PRECISION_FP32) return PTYCHO_OK;
+  if (precision != PTYCHO_PRECISION_BF16X3) return PTYCHO_ERR_ARG;
+  return dft_gemm_supported(N) ? PTYCHO_OK : PTYCHO_ERR_UNSUPPORTED;
+}
+
+template <class Fn>
+static cudaError_t dispatch_tc(int N, Fn&& fn) {
+  switch (N) {
+    case 32: return fn(std::integral_constant<int, 32>());
+    case 64: return fn(std::integral_constant<int, 64>());
+    case 128: return fn(std::integral_constant<int, 128>());
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t dft_planes(int N, void* dft, cudaStream_t s) {
+  return timed(K_DFT_PLANES, s, [&] {
+    return dispatch_tc(N, [&](auto c) { return launch_dft_planes<decltype(c)::value>(dft, s); });
+  });
+}
+
+cudaError_t pass1_dft(int N, const BatchArgs& a, const void* dft, cudaStream_t s) {
+  cudaError_t e = timed(K_PASS1_EXIT, s, [&] {
+    return dispatch_tc(N, [&](auto c) { return launch_pass1_part<decltype(c)::value>(a, s, 1); });
+  });
+  if (e != cudaSuccess) return e;
+  e = timed(K_FAR_TC, s, [&] {
+    return dispatch_tc(N, [&](auto c) { return launch_far_tc<decltype(c)::value>(a, dft, s); });
+  });
+  if (e != cudaSuccess || a.mode == MODE_FWD) return e;
+  return timed(K_PASS1_OVERLAP, s, [&] {
+    return dispatch_tc(N, [&](auto c) { return launch_pass1_part<decltype(c)::value>(a, s, 2); });
+  });
+}
+
 cudaError_t pass2(int N, const Pass2Args& a, cudaStream_t s, int variant) {
   return timed(K_PASS2, s, [&] {
     return dispatch_N(N, [&](auto c) { return launch_pass2<decltype(c)::value>(a, s, variant); });
@@ -485,6 +529,7 @@ Ptrs carve(void* ws, const Layout& L) {
   p.gram = L.gram ? (double*)(b + L.gram) : nullptr;
   p.possum = (double*)(b + L.possum);
   p.dOe = L.dOe ? (float2*)(b + L.dOe) : nullptr;
+  p.dft = L.dft ? (void*)(b + L.dft) : nullptr;
   return p;
 }
 
@@ -554,10 +599,12 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
   if ((e = init_epoch(NN, M, probe, w.Sp, w.hdr, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
   if (o.object_per_epoch && (e = cudaMemsetAsync(w.dOe, 0, (size_t)HW * sizeof(float2), s)) != cudaSuccess)
     return PTYCHO_ERR_CUDA;
+  const bool tc = o.precision == PTYCHO_PRECISION_BF16X3;
+  if (tc && (e = dft_planes(N, w.dft, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
   int dev = 0;
   cudaGetDevice(&dev);
   TuneEntry tune{{dev, N, M, d.H, d.W, B}, 0, 0, {0.f, 0.f}, {0.f, 0.f}};
-  if (!tune_lookup(tune.key, &tune) && (o.flags & PTYCHO_FLAG_AUTOTUNE) && d.J > 0) {
+  if (!tc && !tune_lookup(tune.key, &tune) && (o.flags & PTYCHO_FLAG_AUTOTUNE) && d.J > 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
       ptycho_status ts = autotune(d, obj, probe, pos, meas, order, o, w, L, s, &tune);
@@ -585,7 +632,7 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
       if ((e = cudaMemsetAsync(w.possum, 0, (size_t)nb * 5 * sizeof(double), s)) != cudaSuccess)
         return PTYCHO_ERR_CUDA;
     }
-    if ((e = pass1(N, a, s, tune.v1)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if ((e = tc ? pass1_dft(N, a, w.dft, s) : pass1(N, a, s, tune.v1)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     const bool tiles = tiles_cheaper(nb, N, d.H, d.W);
     if ((e = probe_reduce(NN, 0, M, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
                           o.update_probe ? w.Dp : nullptr, tiles ? nullptr : w.acc, HW, sc, s)) != cudaSuccess)
@@ -623,7 +670,7 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
 ptycho_status check_opts(const ptycho_lsqml_opts* o) {
   if (!o || o->batch < 1 || (o->noise != PTYCHO_NOISE_GAUSSIAN && o->noise != PTYCHO_NOISE_POISSON))
     return PTYCHO_ERR_ARG;
-  if (o->reserved != 0) return PTYCHO_ERR_ARG;
+  if (o->precision != PTYCHO_PRECISION_FP32 && o->precision != PTYCHO_PRECISION_BF16X3) return PTYCHO_ERR_ARG;
   if ((o->update_positions != 0 && o->update_positions != 1) || (o->object_per_epoch != 0 && o->object_per_epoch != 1))
     return PTYCHO_ERR_ARG;
   if (!(o->pos_step >= 0.0) || !(o->pos_step < 1e30) || !(o->pos_max_shift >= 0.0) || !(o->pos_max_shift < 1e30))
@@ -686,29 +733,52 @@ size_t ptycho_workspace_bytes_opts(const ptycho_dims* dims, const ptycho_lsqml_o
   return layout_for(*dims, *opts).total;
 }
 
-ptycho_status ptycho_forward(const ptycho_dims* dims, const float* object, const float* probe, const float* pos,
-                             float* I_pred, void* ws, size_t ws_bytes, void* stream) {
+ptycho_status ptycho_forward_ex(const ptycho_dims* dims, int32_t precision, int32_t batch, const float* object,
+                                const float* probe, const float* pos, float* I_pred, void* ws, size_t ws_bytes,
+                                void* stream) {
   ptycho_status st = check_dims(dims);
   if (st != PTYCHO_OK) return st;
+  if ((st = check_precision(dims->N, precision)) != PTYCHO_OK) return st;
+  if (batch < 1) return PTYCHO_ERR_ARG;
   if (!object || !probe || (dims->J > 0 && (!pos || !I_pred))) return PTYCHO_ERR_ARG;
-  if ((st = check_ws(ws, ws_bytes, align256(sizeof(WsHeader)))) != PTYCHO_OK) return st;
+  const bool tc = precision == PTYCHO_PRECISION_BF16X3;
+  const Layout L = make_layout(*dims, batch);
+  if ((st = check_ws(ws, ws_bytes, tc ? L.total : align256(sizeof(WsHeader)))) != PTYCHO_OK) return st;
   if (dims->J == 0) return PTYCHO_OK;
-  WsHeader* hdr = (WsHeader*)ws;
+  cudaStream_t s = (cudaStream_t)stream;
   BatchArgs a;
   memset(&a, 0, sizeof(a));
   a.H = dims->H; a.W = dims->W; a.M = dims->M; a.J = dims->J;
   a.obj = (const float2*)object; a.probe = (const float2*)probe; a.pos = pos;
-  a.b0 = 0; a.nb = dims->J; a.mode = MODE_FWD;
-  a.ipred = I_pred; a.status = &hdr->status;
-  return cuda_status(pass1(dims->N, a, (cudaStream_t)stream));
+  a.mode = MODE_FWD;
+  a.ipred = I_pred; a.status = &((WsHeader*)ws)->status;
+  if (!tc) {
+    a.b0 = 0; a.nb = dims->J;
+    return cuda_status(pass1(dims->N, a, s));
+  }
+  Ptrs w = carve(ws, L);
+  if (dft_planes(dims->N, w.dft, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  a.psi_s = w.psi; a.valid = w.valid;
+  for (int b0 = 0; b0 < dims->J; b0 += batch) {
+    a.b0 = b0;
+    a.nb = (dims->J - b0 < batch) ? dims->J - b0 : batch;
+    if (pass1_dft(dims->N, a, w.dft, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  }
+  return PTYCHO_OK;
 }
 
-ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const float* probe, const float* pos,
-                             const float* meas, int32_t noise, double eps, int32_t batch, float* g_object,
-                             float* g_probe, float* g_pos, double* loss, void* ws, size_t ws_bytes,
-                             void* stream) {
+ptycho_status ptycho_forward(const ptycho_dims* dims, const float* object, const float* probe, const float* pos,
+                             float* I_pred, void* ws, size_t ws_bytes, void* stream) {
+  return ptycho_forward_ex(dims, PTYCHO_PRECISION_FP32, 1, object, probe, pos, I_pred, ws, ws_bytes, stream);
+}
+
+ptycho_status ptycho_adjoint_ex(const ptycho_dims* dims, int32_t precision, const float* object, const float* probe,
+                                const float* pos, const float* meas, int32_t noise, double eps, int32_t batch,
+                                float* g_object, float* g_probe, float* g_pos, double* loss, void* ws,
+                                size_t ws_bytes, void* stream) {
   ptycho_status st = check_dims(dims);
   if (st != PTYCHO_OK) return st;
+  if ((st = check_precision(dims->N, precision)) != PTYCHO_OK) return st;
   if (batch < 1 || !(eps >= 0.0)) return PTYCHO_ERR_ARG;
   if (noise != PTYCHO_NOISE_GAUSSIAN && noise != PTYCHO_NOISE_POISSON && noise != PTYCHO_NOISE_VJP)
     return PTYCHO_ERR_ARG;
@@ -719,6 +789,8 @@ ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const
   Ptrs w = carve(ws, L);
   cudaStream_t s = (cudaStream_t)stream;
   const int NN = dims->N * dims->N;
+  const bool tc = precision == PTYCHO_PRECISION_BF16X3;
+  if (tc && dims->J > 0 && dft_planes(dims->N, w.dft, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
   for (int b0 = 0; b0 < dims->J; b0 += batch) {
     const int nb = (dims->J - b0 < batch) ? dims->J - b0 : batch;
     BatchArgs a;
@@ -731,12 +803,20 @@ ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const
     a.eps = (float)eps;
     a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
     a.gobj = (float2*)g_object; a.gpos = g_pos; a.loss = loss; a.status = &w.hdr->status;
-    if (pass1(dims->N, a, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if ((tc ? pass1_dft(dims->N, a, w.dft, s) : pass1(dims->N, a, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if (probe_reduce(NN, 0, dims->M, dims->M, nb, w.h, w.o, w.valid, (float2*)g_probe, 1, nullptr, nullptr, 0,
                      nullptr, s) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
   }
   return PTYCHO_OK;
+}
+
+ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const float* probe, const float* pos,
+                             const float* meas, int32_t noise, double eps, int32_t batch, float* g_object,
+                             float* g_probe, float* g_pos, double* loss, void* ws, size_t ws_bytes,
+                             void* stream) {
+  return ptycho_adjoint_ex(dims, PTYCHO_PRECISION_FP32, object, probe, pos, meas, noise, eps, batch, g_object,
+                           g_probe, g_pos, loss, ws, ws_bytes, stream);
 }
 
 ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* probe, float* pos,
@@ -745,6 +825,7 @@ ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* 
   ptycho_status st = check_dims(dims);
   if (st != PTYCHO_OK) return st;
   if ((st = check_opts(opts)) != PTYCHO_OK) return st;
+  if ((st = check_precision(dims->N, opts->precision)) != PTYCHO_OK) return st;
   if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
   const Layout L = layout_for(*dims, *opts);
   if ((st = check_ws(ws, ws_bytes, L.total)) != PTYCHO_OK) return st;
@@ -779,6 +860,7 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
   ptycho_status st = check_dims(dims);
   if (st != PTYCHO_OK) return st;
   if ((st = check_opts(opts)) != PTYCHO_OK) return st;
+  if ((st = check_precision(dims->N, opts->precision)) != PTYCHO_OK) return st;
   if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
   const Layout L = layout_for(*dims, *opts);
   if ((st = check_ws(ws, ws_bytes, L.total + host_extra(*dims))) != PTYCHO_OK) return st;
@@ -821,6 +903,7 @@ ptycho_status ptycho_status_read(void* ws, void* stream) {
     return PTYCHO_ERR_CUDA;
   if (cudaMemsetAsync(&hdr->status, 0, sizeof(int), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  if (h & FLAG_TIMEOUT) return PTYCHO_ERR_TIMEOUT;
   if (h & FLAG_BOUNDS) return PTYCHO_ERR_BOUNDS;
   if (h & FLAG_NONFINITE) return PTYCHO_ERR_NONFINITE;
   return PTYCHO_OK;

@@ -171,6 +171,7 @@ ptycho_status ptycho_lsqml_epoch_batched(int32_t n, const ptycho_dims* dims, flo
   for (int i = 0; i < n; ++i) {
     if ((st = check_dims(&dims[i])) != PTYCHO_OK) return st;
     if ((st = check_opts(&opts[i])) != PTYCHO_OK) return st;
+    if ((st = check_precision(dims[i].N, opts[i].precision)) != PTYCHO_OK) return st;
     if (!objects[i] || !probes[i] || (dims[i].J > 0 && (!pos[i] || !meas[i]))) return PTYCHO_ERR_ARG;
   }
   const size_t need = ptycho_workspace_bytes_batched(n, dims, opts);
@@ -217,7 +218,8 @@ ptycho_status ptycho_lsqml_epoch_opr_batched(int32_t n, const ptycho_dims* dims,
     if ((st = check_dims(&dims[i])) != PTYCHO_OK) return st;
     if ((st = check_opr_opts(&opr[i])) != PTYCHO_OK) return st;
     if ((st = check_opts(&opts[i])) != PTYCHO_OK) return st;
-    if (opts[i].update_positions || opts[i].object_per_epoch) return PTYCHO_ERR_UNSUPPORTED;
+    if (opts[i].update_positions || opts[i].object_per_epoch || opts[i].precision != PTYCHO_PRECISION_FP32)
+      return PTYCHO_ERR_UNSUPPORTED;
     if (!objects[i] || !U[i] || (dims[i].M > 1 && (!P_rest || !P_rest[i])) ||
         (dims[i].J > 0 && (!pos[i] || !meas[i] || !w[i])))
       return PTYCHO_ERR_ARG;

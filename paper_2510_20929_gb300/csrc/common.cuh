@@ -13,6 +13,7 @@ namespace ptycho {
 enum : int {
   FLAG_BOUNDS = 1,     // a position's bilinear tile leaves the object, or an order entry is out of range
   FLAG_NONFINITE = 2,  // a measured intensity is negative or not finite
+  FLAG_TIMEOUT = 4,    // a bounded wait on the tensor-core pipeline gave up
 };
 
 // What the per-position pass computes after the forward model.

@@ -15,6 +15,7 @@ struct Layout {
   size_t p0, dUacc, Du, dU, gram;   // orthogonal probe relaxation (K > 0) only
   size_t possum;                     // position-correction sums [B, 5] (FP64)
   size_t dOe;                        // epoch object accumulator [H, W] (object_per_epoch) or 0
+  size_t dft;                        // DFT-matrix chunks of the split-BF16 DFT-GEMM (N <= 128) or 0
   size_t total;
 };
 
@@ -30,6 +31,7 @@ struct Ptrs {
   double* gram;
   double* possum;
   float2* dOe;
+  void* dft;
 };
 
 size_t align256(size_t b);
@@ -51,6 +53,15 @@ struct BatchScalars;
 // Launch wrappers (profiled) shared by the entry points.
 cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s, int variant = 0);
 cudaError_t pass2(int N, const Pass2Args& a, cudaStream_t s, int variant = 0);
+// True when the split-BF16 DFT-GEMM form is built for window N.
+bool dft_gemm_supported(int N);
+// PTYCHO_OK, or the error for an unknown precision (ARG) or one not built for N (UNSUPPORTED).
+ptycho_status check_precision(int N, int precision);
+// Fills the DFT chunks of the workspace (once per call of an entry point).
+cudaError_t dft_planes(int N, void* dft, cudaStream_t s);
+// The per-position pass with the far field on the tensor cores: exit waves,
+// k_far_tc, then (unless the mode is the forward model) the overlap-add part.
+cudaError_t pass1_dft(int N, const BatchArgs& a, const void* dft, cudaStream_t s);
 // Batch sums of h over the Mc modes starting at plane k0 of each slot (slots
 // hold Ms planes), Dp = sum |o|^2 and the illumination maximum.
 cudaError_t probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* h_s, const float2* o_s,

@@ -136,7 +136,13 @@ __device__ __forceinline__ void bilinear_scatter(float fy, float fx, Load&& load
 
 // OPR: the primary probe mode is synthesised per position (a separate
 // instantiation, so that the shared-probe kernel carries none of it).
-template <int N, int T, bool OPR>
+// PART 0 is the whole pass. With the far field evaluated elsewhere (the
+// tensor-core DFT-GEMM stage, k_far_tc) it runs in two parts around it:
+// PART 1 writes the exit waves psi_jk to the far-field scratch (and the
+// patches, the relaxed primary mode and the slot flags) and stops; PART 2
+// reads chi_jk from the scratch and does the rest (g, h, the overlap-add, the
+// position sums).
+template <int N, int T, bool OPR, int PART>
 __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
   using F = Fft2<N>;
   using SM = Pass1Smem<N>;
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
     return;
   }
   if (tid == 0 && a.valid) a.valid[slot] = 1;
-  make_twiddles<N>(tw);
+  if (PART == 0) make_twiddles<N>(tw);
 
   const int M = a.M;
   const float invN = 1.0f / (float)N;
@@ -180,7 +186,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
 
   // ---- forward model: I_j = sum_k |F(P_k o_j)|^2 -------------------------------
 #pragma unroll 1
-  for (int k = 0; k < M; ++k) {
+  for (int k = 0; k < (PART == 2 ? 0 : M); ++k) {
     const float2* Pk = shared_mode<OPR>(a, k, NN);
     // psi_k = P_k o_j into the tile, two adjacent pixels per thread and iteration
     const NatPairs<N, T> np;
@@ -203,8 +209,13 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
         P2 = opr_pair(a.opr_U, wj, a.K, NN, p);
         if (p0) *(float4*)(p0 + p) = P2;
       }
-      store_pair(tile, np.phys(q), cmul(make_float2(P2.x, P2.y), o0), cmul(make_float2(P2.z, P2.w), o1));
+      const float2 x0 = cmul(make_float2(P2.x, P2.y), o0), x1 = cmul(make_float2(P2.z, P2.w), o1);
+      if constexpr (PART == 1)
+        *(float4*)(psi_s + (size_t)k * NN + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+      else
+        store_pair(tile, np.phys(q), x0, x1);
     }
+    if constexpr (PART == 1) continue;
     __syncthreads();
     fft2_forward<N, T>(tile, tw, [&](int row, float2 (&v)[R2]) {
       if constexpr (F::S == 2) {
@@ -234,56 +245,59 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
     __syncthreads();
   }
 
-  // ---- data term: loss and the far-field factor (same thread owns each pixel) ----
+  if constexpr (PART == 1) return;
   const int mode = a.mode;
-  const float eps = a.eps;
-  const float* meas = a.meas + (size_t)j * NN;
-  float lsum = 0.f;
-  bool bad = false;
-  {
-    constexpr int L = T / R1, ITER = N / L;
-    const int gid = F::line_slot();
+  // ---- data term: loss and the far-field factor (same thread owns each pixel) ----
+  if constexpr (PART == 0) {
+    const float eps = a.eps;
+    const float* meas = a.meas + (size_t)j * NN;
+    float lsum = 0.f;
+    bool bad = false;
+    {
+      constexpr int L = T / R1, ITER = N / L;
+      const int gid = F::line_slot();
 #pragma unroll 1
-    for (int it = 0; it < ITER; ++it) {
-      const int row = gid + it * L;
+      for (int it = 0; it < ITER; ++it) {
+        const int row = gid + it * L;
 #pragma unroll
-      for (int m = 0; m < R2; ++m) {
-        const int col = F::out_index(n, m);
-        const int pix = row * N + col;
-        const float I = rI[row * RP + col];
-        if (a.ipred) a.ipred[(size_t)j * NN + pix] = I;
-        if (mode == MODE_FWD) continue;
-        const float Im = __ldg(meas + pix);
-        float fac;
-        if (mode == MODE_VJP) {
-          bad |= !isfinite(Im);
-          fac = 2.f * Im;
-        } else {
-          bad |= !(Im >= 0.f) || !isfinite(Im);
-          const float Ie = I + eps;
-          if (mode == MODE_LSQML_GAUSS || mode == MODE_GRAD_GAUSS) {
-            const float sIe = sqrtf(Ie), sIm = sqrtf(Im);
-            const float d = sIe - sIm;
-            lsum = fmaf(d, d, lsum);
-            const float rho = sIm / sIe;
-            fac = (mode == MODE_LSQML_GAUSS) ? rho - 1.f : 2.f * (1.f - rho);
+        for (int m = 0; m < R2; ++m) {
+          const int col = F::out_index(n, m);
+          const int pix = row * N + col;
+          const float I = rI[row * RP + col];
+          if (a.ipred) a.ipred[(size_t)j * NN + pix] = I;
+          if (mode == MODE_FWD) continue;
+          const float Im = __ldg(meas + pix);
+          float fac;
+          if (mode == MODE_VJP) {
+            bad |= !isfinite(Im);
+            fac = 2.f * Im;
           } else {
-            lsum += I - Im * logf(Ie);
-            const float q = Im / Ie;
-            fac = (mode == MODE_LSQML_POISSON) ? 0.5f * (q - 1.f) : 2.f * (1.f - q);
+            bad |= !(Im >= 0.f) || !isfinite(Im);
+            const float Ie = I + eps;
+            if (mode == MODE_LSQML_GAUSS || mode == MODE_GRAD_GAUSS) {
+              const float sIe = sqrtf(Ie), sIm = sqrtf(Im);
+              const float d = sIe - sIm;
+              lsum = fmaf(d, d, lsum);
+              const float rho = sIm / sIe;
+              fac = (mode == MODE_LSQML_GAUSS) ? rho - 1.f : 2.f * (1.f - rho);
+            } else {
+              lsum += I - Im * logf(Ie);
+              const float q = Im / Ie;
+              fac = (mode == MODE_LSQML_POISSON) ? 0.5f * (q - 1.f) : 2.f * (1.f - q);
+            }
           }
+          rI[row * RP + col] = fac * invN;
         }
-        rI[row * RP + col] = fac * invN;
       }
     }
+    if (bad) atomicOr(a.status, FLAG_NONFINITE);
+    if (a.loss && mode != MODE_FWD && mode != MODE_VJP) {
+      double v[1] = {(double)lsum};
+      block_sum<1>(v, red);
+      if (tid == 0) atomicAdd(a.loss, v[0]);
+    }
+    if (mode == MODE_FWD) return;
   }
-  if (bad) atomicOr(a.status, FLAG_NONFINITE);
-  if (a.loss && mode != MODE_FWD && mode != MODE_VJP) {
-    double v[1] = {(double)lsum};
-    block_sum<1>(v, red);
-    if (tid == 0) atomicAdd(a.loss, v[0]);
-  }
-  if (mode == MODE_FWD) return;
 
   // ---- back-propagation: chi_k = F^-1[fac Psi_k], g = sum_k conj(P_k) chi_k, h_k ----
   // The modes run last to first: the far fields written last are read first,
@@ -293,36 +307,45 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
 #pragma unroll 1
   for (int k = M - 1; k >= 0; --k) {
     const float2* Pk = shared_mode<OPR>(a, k, NN);
-    __syncthreads();
-    fft2_inverse<N, T>(
-        tile, tw,
-        [&](int row, float2 (&v)[R2]) {
-          if constexpr (F::S == 2) {
+    if constexpr (PART == 0) {
+      __syncthreads();
+      fft2_inverse<N, T>(
+          tile, tw,
+          [&](int row, float2 (&v)[R2]) {
+            if constexpr (F::S == 2) {
 #pragma unroll
-            for (int q = 0; q < R2 / 2; ++q) {
-              const int col = F::out_index(n, 2 * q);
-              const float4 X = *(const float4*)(psi_s + (size_t)k * NN + row * N + col);
-              const float2 f = *(const float2*)(rI + row * RP + col);
-              v[2 * q] = make_float2(X.x * f.x, X.y * f.x);
-              v[2 * q + 1] = make_float2(X.z * f.y, X.w * f.y);
-            }
-          } else {
+              for (int q = 0; q < R2 / 2; ++q) {
+                const int col = F::out_index(n, 2 * q);
+                const float4 X = *(const float4*)(psi_s + (size_t)k * NN + row * N + col);
+                const float2 f = *(const float2*)(rI + row * RP + col);
+                v[2 * q] = make_float2(X.x * f.x, X.y * f.x);
+                v[2 * q + 1] = make_float2(X.z * f.y, X.w * f.y);
+              }
+            } else {
 #pragma unroll
-            for (int m = 0; m < R2; ++m) {
-              const int col = F::out_index(n, m);
-              v[m] = cscale(psi_s[(size_t)k * NN + row * N + col], rI[row * RP + col]);
+              for (int m = 0; m < R2; ++m) {
+                const int col = F::out_index(n, m);
+                v[m] = cscale(psi_s[(size_t)k * NN + row * N + col], rI[row * RP + col]);
+              }
             }
-          }
-        },
-        [&](int col, float2 (&v)[R2]) { F::template store_in<false>(v, tile, col, n); });
-    __syncthreads();
-    // chi_k is in the tile (natural layout): g += conj(P_k) chi_k, h_k = conj(o) chi_k
+          },
+          [&](int col, float2 (&v)[R2]) { F::template store_in<false>(v, tile, col, n); });
+      __syncthreads();
+    }
+    // chi_k (natural layout) is in the tile, or in PART 2 in the scratch:
+    // g += conj(P_k) chi_k, h_k = conj(o) chi_k
     const NatPairs<N, T> np;
 #pragma unroll 2
     for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
       const int p = np.pix(q);
       float2 x0, x1;
-      load_pair(tile, np.phys(q), x0, x1);
+      if constexpr (PART == 2) {
+        const float4 c = *(const float4*)(psi_s + (size_t)k * NN + p);
+        x0 = make_float2(c.x, c.y);
+        x1 = make_float2(c.z, c.w);
+      } else {
+        load_pair(tile, np.phys(q), x0, x1);
+      }
       const float4 P2 = (!OPR || Pk) ? __ldg((const float4*)(Pk + p)) : *(const float4*)(p0 + p);
       const float4 o2 = *(const float4*)(o_s + p);
       const float2 g0 = cmulc(make_float2(P2.x, P2.y), x0), g1 = cmulc(make_float2(P2.z, P2.w), x1);
@@ -567,14 +590,14 @@ cudaError_t smem_optin(K kernel, size_t bytes, unsigned long long* done_mask) {
   return e;
 }
 
-template <int N, int T, bool OPR>
+template <int N, int T, bool OPR, int PART = 0>
 cudaError_t launch_pass1_t(const BatchArgs& a, cudaStream_t s) {
   constexpr size_t sm = Pass1Smem<N>::bytes;
   static unsigned long long done = 0;
-  cudaError_t e = smem_optin(k_pass1<N, T, OPR>, sm, &done);
+  cudaError_t e = smem_optin(k_pass1<N, T, OPR, PART>, sm, &done);
   if (e != cudaSuccess) return e;
   if (a.nb <= 0) return cudaSuccess;
-  return launch_pdl(k_pass1<N, T, OPR>, dim3(a.nb), dim3(T), sm, s, a);
+  return launch_pdl(k_pass1<N, T, OPR, PART>, dim3(a.nb), dim3(T), sm, s, a);
 }
 
 // variant 0: default CTA size, 1: the alternative (the relaxed-probe form has

@@ -14,4 +14,11 @@ template <int N> cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s, in
 template <int N> cudaError_t launch_pass1_ms(const MsArgs& a, cudaStream_t s);
 template <> cudaError_t launch_pass1_ms<192>(const MsArgs& a, cudaStream_t s);
 template <> cudaError_t launch_pass1_ms<256>(const MsArgs& a, cudaStream_t s);
+// split-BF16 DFT-GEMM form (N = 32, 64, 128): bytes of the DFT chunks, their
+// fill, the two parts of the per-position pass (part 1: exit waves, part 2:
+// overlap-add) and the tensor-core far-field stage between them
+template <int N> size_t dft_plane_bytes();
+template <int N> cudaError_t launch_dft_planes(void* dft, cudaStream_t s);
+template <int N> cudaError_t launch_pass1_part(const BatchArgs& a, cudaStream_t s, int part);
+template <int N> cudaError_t launch_far_tc(const BatchArgs& a, const void* dft, cudaStream_t s);
 }  // namespace ptycho

@@ -496,7 +496,8 @@ ptycho_status ptycho_lsqml_epoch_opr(const ptycho_dims* dims, const ptycho_opr_o
   if (st != PTYCHO_OK) return st;
   if ((st = check_opr_opts(opr)) != PTYCHO_OK) return st;
   if ((st = check_opts(opts)) != PTYCHO_OK) return st;
-  if (opts->update_positions || opts->object_per_epoch) return PTYCHO_ERR_UNSUPPORTED;
+  if (opts->update_positions || opts->object_per_epoch || opts->precision != PTYCHO_PRECISION_FP32)
+    return PTYCHO_ERR_UNSUPPORTED;
   if (!object || !U || (dims->M > 1 && !P_rest) || (dims->J > 0 && (!pos || !meas || !w))) return PTYCHO_ERR_ARG;
   const Layout L = make_layout(*dims, opts->batch, opr->K);
   if ((st = check_ws(ws, ws_bytes, L.total)) != PTYCHO_OK) return st;

@@ -49,7 +49,8 @@ const char* kernel_name(int id) {
   static const char* names[K_COUNT] = {"k_pass1",      "k_pass2",        "k_probe_reduce", "k_norm_probe",
                                        "k_probe_update", "k_init_epoch", "k_opr_reduce",   "k_opr_weights",
                                        "k_tile_illum_max", "k_tile_clear", "k_pass1_ms",
-                                       "k_clear_plane"};
+                                       "k_clear_plane", "k_pass1_exit", "k_far_tc", "k_pass1_overlap",
+                                       "k_dft_planes"};
   return (id >= 0 && id < K_COUNT) ? names[id] : "?";
 }
 

@@ -7,7 +7,7 @@
 namespace ptycho {
 enum KernelId : int {
   K_PASS1 = 0, K_PASS2, K_PROBE_REDUCE, K_NORM_PROBE, K_UPDATE, K_INIT, K_OPR_REDUCE, K_OPR_WEIGHTS, K_TILE_MAX, K_TILE_CLEAR,
-  K_PASS1_MS, K_CLEAR_PLANE, K_COUNT
+  K_PASS1_MS, K_CLEAR_PLANE, K_PASS1_EXIT, K_FAR_TC, K_PASS1_OVERLAP, K_DFT_PLANES, K_COUNT
 };
 const char* kernel_name(int id);
 bool profiling_on();

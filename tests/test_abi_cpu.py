@@ -80,7 +80,7 @@ def test_arguments_rejected_before_any_launch(L):
     assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
                                 P(0), P(0), fake, 1 << 30, None) == 1
     opts = api.make_opts(batch=4)
-    opts.reserved = 1
+    opts.precision = 7
     assert L.ptycho_lsqml_epoch(ctypes.byref(d), fake, fake, fake, fake, P(0), ctypes.byref(opts),
                                 P(0), P(0), fake, 1 << 30, None) == 1
     for bad in (dict(pos_step=-1.0), dict(pos_max_shift=float("nan"))):
@@ -113,6 +113,21 @@ def test_arguments_rejected_before_any_launch(L):
                             fake, 1 << 30, None) == 1                            # negative eps
     assert L.ptycho_status_read(P(0), None) == 7
     assert L.ptycho_workspace_init(P(0x1001), 1 << 20, None) == 7
+    # the split-BF16 DFT-GEMM precision: windows 32, 64, 128 only, an unknown precision is an argument error
+    tc = api.make_opts(batch=4, precision="bf16x3")
+    d256 = _dims(H=300, W=300, N=256)
+    assert L.ptycho_lsqml_epoch(ctypes.byref(d256), fake, fake, fake, fake, P(0), ctypes.byref(tc),
+                                P(0), P(0), fake, 1 << 30, None) == 6
+    assert L.ptycho_forward_ex(ctypes.byref(_dims(N=16)), 1, 4, fake, fake, fake, fake, fake, 1 << 30, None) == 6
+    assert L.ptycho_forward_ex(ctypes.byref(d), 2, 4, fake, fake, fake, fake, fake, 1 << 30, None) == 1
+    assert L.ptycho_forward_ex(ctypes.byref(d), 1, 0, fake, fake, fake, fake, fake, 1 << 30, None) == 1
+    assert L.ptycho_forward_ex(ctypes.byref(d), 1, 4, fake, fake, fake, fake, P(0x1000), 4096, None) == 7
+    assert L.ptycho_adjoint_ex(ctypes.byref(d256), 1, fake, fake, fake, fake, 0, 0.0, 4, fake, fake, P(0), P(0),
+                               fake, 1 << 30, None) == 6
+    # the relaxed-probe epoch takes FP32 only
+    opr = api.make_opr_opts(2)
+    assert L.ptycho_lsqml_epoch_opr(ctypes.byref(d), ctypes.byref(opr), fake, fake, fake, fake, fake, fake,
+                                    P(0), ctypes.byref(tc), P(0), P(0), fake, 1 << 30, None) == 6
 
 
 def test_binding_refuses_cpu_tensors():
