@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", choices=["spiral128", "raster64", "uneven16", "uneven16opr", "spiral256", "multislice256"], default="spiral128")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP32 vs split-BF16 comparison at matched reconstruction error")
     ap.add_argument("--precision", choices=["fp32", "bf16x3"], default="fp32",
                     help="far-field arithmetic of the timed epochs: FP32 FFTs or split-BF16 DFT-GEMMs")
     ap.add_argument("--positions", type=int, default=0,
@@ -256,6 +258,64 @@ def job_throughput(units_per_rank, world, seconds):
     return world * units_per_rank / seconds
 
 
+# ----------------------------------------------------------------------------- precision comparison
+COMPARE_EPOCHS = 20
+
+
+def object_error(O, O_true, pos, N):
+    """Phase-aligned relative object error over the scanned region (the box of
+    probe centres widened by N/4): min over a global phase of ||O e^{i phi} - O_true|| / ||O_true||."""
+    import torch
+    lo = (pos.min(dim=0).values - N / 4).floor().clamp(min=0).long().tolist()
+    hi = (pos.max(dim=0).values + N / 4).ceil().long().tolist()
+    a = O[lo[0]:hi[0], lo[1]:hi[1]].to(torch.complex128)
+    b = O_true[lo[0]:hi[0], lo[1]:hi[1]].to(torch.complex128)
+    c = (a.conj() * b).sum()
+    ph = c / c.abs() if c.abs() > 0 else 1.0
+    return ((a * ph - b).norm() / b.norm()).item()
+
+
+def precision_comparison(api, O_true, P, pos, meas, order, B, steps, warmup, dev):
+    """FP32 FFTs against split-BF16 DFT-GEMMs on the same seeded data: COMPARE_EPOCHS
+    epochs from the same start (unit object, true probe) with each precision, the
+    final loss and phase-aligned object error, and each precision's epoch time
+    (CUDA events around `steps` epochs after `warmup`). Matched: object errors
+    within 1 % of each other."""
+    import torch
+    res = {}
+    H, W = O_true.shape
+    stream = torch.cuda.current_stream()
+    for prec in ("fp32", "bf16x3"):
+        opts = api.make_opts(noise="gaussian", batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9,
+                             precision=prec)
+        O = torch.ones((H, W), dtype=torch.complex64, device=dev)
+        Pe = P.clone()
+        loss = None
+        for _ in range(COMPARE_EPOCHS):
+            loss, _ = api.lsqml_epoch(O, Pe, pos, meas, order, opts, check=False)
+        api.workspace(api.dims_of(O, Pe, pos), B, dev, opts=opts).status()
+        err = object_error(O, O_true, pos, P.shape[-1])
+        for _ in range(warmup):
+            api.lsqml_epoch(O, Pe, pos, meas, order, opts, check=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            api.lsqml_epoch(O, Pe, pos, meas, order, opts, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[prec] = {"patterns_per_s": pos.shape[0] / (ms * 1e-3), "ms_per_epoch": ms,
+                     "final_loss": loss.item(), "object_error": err}
+    e32, e16 = res["fp32"]["object_error"], res["bf16x3"]["object_error"]
+    res.update({"epochs": COMPARE_EPOCHS,
+                "speedup_bf16x3_vs_fp32": res["bf16x3"]["patterns_per_s"] / res["fp32"]["patterns_per_s"],
+                "object_error_rel_diff": abs(e16 - e32) / e32,
+                "matched": abs(e16 - e32) <= 0.01 * e32,
+                "start": "unit object, true probe; Gaussian data term; same order and data"})
+    return res
+
+
 # ----------------------------------------------------------------------------- GPU
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -385,6 +445,10 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "final_loss": losses[-1].item() if losses else None,
     }
+
+    if not args.no_compare and N in (32, 64, 128):
+        out["precision_comparison"] = precision_comparison(api, O_true, P, pos, meas, order, B,
+                                                           min(args.steps, 20), args.warmup, dev)
 
     # end to end through the host-buffer entry point (pinned host memory)
     if not args.no_e2e:

@@ -135,23 +135,30 @@ __device__ __forceinline__ void put8(unsigned char* planes, int row, int k0, con
 template <int N, bool SCALE>
 __device__ __forceinline__ void rows_to_planes(unsigned char* planes, const float2* src, int row, int c0,
                                                const float (&f)[N / 2]) {
+  // 16 columns (eight 16-byte loads) in flight per step
 #pragma unroll
-  for (int g = 0; g < N / 16; ++g) {
+  for (int g = 0; g < N / 16; g += 2) {
     const float4* s = (const float4*)(src + (size_t)row * N + c0 + 8 * g);
-    float re[8], im[8];
+    float4 v[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float4 v = s[q];
-      re[2 * q] = v.x; im[2 * q] = v.y; re[2 * q + 1] = v.z; im[2 * q + 1] = v.w;
-    }
-    if (SCALE) {
+    for (int q = 0; q < 8; ++q) v[q] = __ldcg(s + q);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        re[i] *= f[8 * g + i];
-        im[i] *= f[8 * g + i];
+    for (int h = 0; h < 2; ++h) {
+      float re[8], im[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        re[2 * q] = v[4 * h + q].x; im[2 * q] = v[4 * h + q].y;
+        re[2 * q + 1] = v[4 * h + q].z; im[2 * q + 1] = v[4 * h + q].w;
       }
+      if (SCALE) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          re[i] *= f[8 * (g + h) + i];
+          im[i] *= f[8 * (g + h) + i];
+        }
+      }
+      put8<N>(planes, row, c0 + 8 * (g + h), re, im);
     }
-    put8<N>(planes, row, c0 + 8 * g, re, im);
   }
 }
 
@@ -159,14 +166,21 @@ __device__ __forceinline__ void rows_to_planes(unsigned char* planes, const floa
 // as the next pass's B operand.
 template <int N>
 __device__ __forceinline__ void tmem_to_planes(unsigned char* planes, uint32_t trow, int row, int c0) {
+  constexpr int G = N / 32 < 2 ? N / 32 : 2;   // 16-column groups per TMEM round trip
 #pragma unroll 1
-  for (int g = 0; g < N / 32; ++g) {
-    float re[16], im[16];
-    tc::tmem_ld16(trow + c0 + 16 * g, re);
-    tc::tmem_ld16(trow + N + c0 + 16 * g, im);
+  for (int g = 0; g < N / 32; g += G) {
+    float re[G][16], im[G][16];
+#pragma unroll
+    for (int h = 0; h < G; ++h) {
+      tc::tmem_ld16(trow + c0 + 16 * (g + h), re[h]);
+      tc::tmem_ld16(trow + N + c0 + 16 * (g + h), im[h]);
+    }
     tc::tmem_wait_ld();
-    put8<N>(planes, row, c0 + 16 * g, re, im);
-    put8<N>(planes, row, c0 + 16 * g + 8, re + 8, im + 8);
+#pragma unroll
+    for (int h = 0; h < G; ++h) {
+      put8<N>(planes, row, c0 + 16 * (g + h), re[h], im[h]);
+      put8<N>(planes, row, c0 + 16 * (g + h) + 8, re[h] + 8, im[h] + 8);
+    }
   }
 }
 
@@ -176,21 +190,30 @@ __device__ __forceinline__ void tmem_to_planes(unsigned char* planes, uint32_t t
 template <int N, bool ACC>
 __device__ __forceinline__ void tmem_to_global(float2* dst, uint32_t trow, int row, int c0, float scale,
                                                float (&acc)[N / 2], bool first) {
+  constexpr int G = N / 32 < 2 ? N / 32 : 2;   // 16-column groups per TMEM round trip
 #pragma unroll
-  for (int g = 0; g < N / 32; ++g) {
-    float re[16], im[16];
-    tc::tmem_ld16(trow + c0 + 16 * g, re);
-    tc::tmem_ld16(trow + N + c0 + 16 * g, im);
+  for (int g = 0; g < N / 32; g += G) {
+    float re[G][16], im[G][16];
+#pragma unroll
+    for (int h = 0; h < G; ++h) {
+      tc::tmem_ld16(trow + c0 + 16 * (g + h), re[h]);
+      tc::tmem_ld16(trow + N + c0 + 16 * (g + h), im[h]);
+    }
     tc::tmem_wait_ld();
-    float4* d = (float4*)(dst + (size_t)row * N + c0 + 16 * g);
 #pragma unroll
-    for (int i = 0; i < 16; i += 2) {
-      const float x0 = re[i] * scale, y0 = im[i] * scale, x1 = re[i + 1] * scale, y1 = im[i + 1] * scale;
-      d[i / 2] = make_float4(x0, y0, x1, y1);
-      if (ACC) {
-        const float a0 = fmaf(x0, x0, y0 * y0), a1 = fmaf(x1, x1, y1 * y1);
-        acc[16 * g + i] = first ? a0 : acc[16 * g + i] + a0;
-        acc[16 * g + i + 1] = first ? a1 : acc[16 * g + i + 1] + a1;
+    for (int h = 0; h < G; ++h) {
+      float4* d = (float4*)(dst + (size_t)row * N + c0 + 16 * (g + h));
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) {
+        const float x0 = re[h][i] * scale, y0 = im[h][i] * scale;
+        const float x1 = re[h][i + 1] * scale, y1 = im[h][i + 1] * scale;
+        d[i / 2] = make_float4(x0, y0, x1, y1);
+        if (ACC) {
+          const int c = 16 * (g + h) + i;
+          const float a0 = fmaf(x0, x0, y0 * y0), a1 = fmaf(x1, x1, y1 * y1);
+          acc[c] = first ? a0 : acc[c] + a0;
+          acc[c + 1] = first ? a1 : acc[c + 1] + a1;
+        }
       }
     }
   }
@@ -310,7 +333,13 @@ __global__ void __launch_bounds__(256, 1) k_far_tc(FarArgs a) {
   };
 
   const float invN = 1.0f / (float)N;
+  constexpr uint32_t IMG = (uint32_t)NN * sizeof(float2);
+  // L2 prefetch of an image this CTA reads next (thread 0)
+  auto prefetch = [&](const float2* p) {
+    if (tid == 0) tc::prefetch_l2(p, IMG);
+  };
   bool alive = true;
+  if (blockIdx.x < a.nb) prefetch(a.psi_s + (size_t)blockIdx.x * a.M * NN);
   for (int slot = blockIdx.x; slot < a.nb && alive; slot += gridDim.x) {
     const int e = a.b0 + slot;
     const int j = a.order ? a.order[e] : e;
@@ -319,12 +348,17 @@ __global__ void __launch_bounds__(256, 1) k_far_tc(FarArgs a) {
     if (!(j >= 0 && j < a.J) || !tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx))
       continue;   // flagged by the first part of the pass
     float2* psi = a.psi_s + (size_t)slot * a.M * NN;
+    if (tid == 0 && a.meas && a.mode != MODE_FWD) tc::prefetch_l2(a.meas + (size_t)j * NN, (uint32_t)NN * 4);
+    const bool more = slot + (int)gridDim.x < a.nb;
+    float2* next_slot = more ? a.psi_s + (size_t)(slot + gridDim.x) * a.M * NN : nullptr;
     float acc[HALF];
 #pragma unroll
     for (int i = 0; i < HALF; ++i) acc[i] = 0.f;
 
     // ---- forward: Psi_k = F psi_k F^T / N, I = sum_k |Psi_k|^2 ----------------------
     for (int k = 0; k < a.M && alive; ++k) {
+      if (k + 1 < a.M) prefetch(psi + (size_t)(k + 1) * NN);
+      else if (a.mode == MODE_FWD && next_slot) prefetch(next_slot);
       if (act) rows_to_planes<N, false>(planes, psi + (size_t)k * NN, row, c0, acc);
       if (!(alive = run_pass(false))) break;
       if (act) tmem_to_planes<N>(planes, trow, row, c0);
@@ -377,6 +411,8 @@ __global__ void __launch_bounds__(256, 1) k_far_tc(FarArgs a) {
 
     // ---- back-propagation: chi_k = conj(F) (fac Psi_k) conj(F)^T -------------------
     for (int k = a.M - 1; k >= 0 && alive; --k) {
+      if (k > 0) prefetch(psi + (size_t)(k - 1) * NN);
+      else if (next_slot) prefetch(next_slot);
       if (act) rows_to_planes<N, true>(planes, psi + (size_t)k * NN, row, c0, acc);
       if (!(alive = run_pass(true))) break;
       if (act) tmem_to_planes<N>(planes, trow, row, c0);

@@ -32,14 +32,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 // Waits for the phase with this parity to complete; gives up (false) after
-// about `limit` polls (each try_wait suspends for a bounded time, and the
-// loop sleeps between polls), so a wait that can never end returns.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint32_t limit = 1u << 20) {
-  for (uint32_t i = 0; i < limit; ++i) {
-    if (mbar_try_wait(b, parity)) return true;
-    if (i >= 32) __nanosleep(512);
-  }
-  return false;
+// about `max_cycles` SM clock cycles (2^31, about a second at 2 GHz), so a
+// wait that can never end returns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long max_cycles = 1ll << 31) {
+  if (mbar_try_wait(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(b, parity))
+    if (clock64() - t0 > max_cycles) return false;
+  return true;
 }
 
 // ---- bulk copy global -> shared (completes transaction bytes on an mbarrier) ------
@@ -49,6 +49,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                    smem_u32(dst)),
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
+}
+
+// Prefetch of `bytes` of global memory into L2 (16-byte aligned address, size a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
 }
 
 // Generic-proxy shared-memory writes become visible to the tensor core (async proxy).
