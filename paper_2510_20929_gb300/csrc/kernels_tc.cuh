@@ -16,13 +16,25 @@
 // products on separate re/im planes, the sign of the Fi terms chosen by the
 // instruction descriptor's negate-A bit.
 //
-// k_far_tc: per minibatch position (persistent CTAs, 8 warps): the exit waves
-// psi_jk (written by the first part of the per-position pass) are
-// transformed mode by mode; the far fields overwrite them in the scratch and
-// their intensities accumulate per thread; the data term (Eq. 1 amplitude
-// loss or the Poisson likelihood) gives the loss and the far-field factor;
-// every mode is then scaled and transformed back, and chi_jk = F^-1[(rho - 1)
-// Psi_jk] overwrites the scratch for the overlap-add part of the pass.
+// k_far_tc: per minibatch position (persistent CTAs): the exit waves psi_jk
+// (written by the first part of the per-position pass) are transformed mode
+// by mode; the far fields overwrite them in the scratch and their intensities
+// accumulate per thread; the data term (Eq. 1 amplitude loss or the Poisson
+// likelihood) gives the loss and the far-field factor; every mode is then
+// scaled and transformed back, and chi_jk = F^-1[(rho - 1) Psi_jk] overwrites
+// the scratch for the overlap-add part of the pass.
+//
+// Warp roles: eight producer warps write the B operand of every K step (a
+// 16-wide K slice of four BF16 planes) into a ring of shared-memory slots;
+// one MMA warp streams the DFT-matrix chunks and issues the MMAs as slices
+// land; one TMA warp stages the exit waves and the measured intensities from
+// global memory into a second ring with tiled tensor copies (128-byte
+// swizzle). Pass-1 slices come from the staged exit waves, from the last
+// forward far field still in TMEM (the first inverse transform) or from the
+// far fields in L2 (the other inverse transforms); pass-2 slices from the
+// pass-1 accumulator in TMEM. Pass 1 accumulates in TMEM buffer A, pass 2 in
+// buffer B, so an image's pass-2 result drains while the next image's pass 1
+// runs.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -34,24 +46,35 @@ namespace ptycho {
 template <int N>
 struct FarTc {
   static_assert(N == 32 || N == 64 || N == 128, "DFT-GEMM windows");
-  static constexpr int T = 256;                  // 8 warps: TMEM lane quarter w % 4, column half w / 4
-  static constexpr int HALF = N / 2;
-  static constexpr int NCH = N / 16;             // K-steps of one pass (= DFT chunks)
-  static constexpr int NS = 4;                   // ring slots of DFT chunks
-  static constexpr int MT = 128;                 // MMA tile rows (DFT rows beyond N are zero)
+  static constexpr int PW = 8;                    // producer warps: TMEM lane quarter w % 4, column set w / 4
+  static constexpr int T = 32 * (PW + 2);         // and the MMA warp (PW) and the TMA warp (PW + 1)
+  static constexpr int HALF = N / 2;              // columns per producer thread: 16 s + 8 (w / 4) + [0, 8)
+  static constexpr int NCH = N / 16;              // K steps of one pass (= DFT chunks)
+  static constexpr int NSF = 4;                   // ring slots of DFT chunks
+  static constexpr int NSB = 6;                   // ring slots of B slices
+  static constexpr int NSS = 4;                   // ring slots of staged tiles
+  static constexpr int MT = 128;                  // MMA tile rows (DFT rows beyond N are zero)
   static constexpr uint32_t APLANE = MT * 16 * 2;            // one 128 x 16 BF16 plane of a chunk
   static constexpr uint32_t CHUNK = 4 * APLANE;              // Fr_hi, Fr_lo, Fi_hi, Fi_lo
   static constexpr uint32_t ASBO = 256;                      // 8-row groups of a 16-wide K slice
-  static constexpr uint32_t BPLANE = (uint32_t)N * N * 2;    // one N x N BF16 operand plane
-  static constexpr uint32_t BSBO = (uint32_t)(N / 8) * 128;  // 8-row groups of a full-K plane
-  static constexpr size_t planes = 0;                        // Xr_hi, Xr_lo, Xi_hi, Xi_lo
-  static constexpr size_t ring = planes + 4 * (size_t)BPLANE;
-  static constexpr size_t bars = ring + (size_t)NS * CHUNK;  // full[NS], empty[NS], done
-  static constexpr size_t red = bars + 128;
-  static constexpr size_t misc = red + 32 * sizeof(double);
-  static constexpr size_t bytes = misc + 16;
-  static constexpr uint32_t COLS = 2 * N;                    // TMEM: D_re [0, N), D_im [N, 2N)
+  static constexpr uint32_t BPLANE = (uint32_t)N * 16 * 2;   // one N x 16 BF16 plane of a B slice
+  static constexpr uint32_t SLICE = 4 * BPLANE;              // Xr_hi, Xr_lo, Xi_hi, Xi_lo
+  static constexpr uint32_t BSBO = 256;
+  static constexpr uint32_t SSLOT = 128u * N;                // a staged tile: N rows x 32 floats
+  static constexpr size_t fring = 0;
+  static constexpr size_t sring = fring + (size_t)NSF * CHUNK;   // 1024-byte aligned (swizzled tiles)
+  static constexpr size_t bring = sring + (size_t)NSS * SSLOT;
+  static constexpr size_t bars = bring + (size_t)NSB * SLICE;
+  static constexpr int NBAR = 2 * NSF + 2 * NSB + 2 * NSS + 3;   // F, B and staging rings, p1, p2, drained
+  static constexpr size_t misc = bars + 8 * (size_t)NBAR;
+  static constexpr size_t bytes = misc + 16 + 1024;             // + alignment of the base to 1024 bytes
+  static constexpr uint32_t COLS = 4 * N;                    // buffer A [0, 2N), buffer B [2N, 4N)
   static constexpr size_t dft_bytes = (size_t)NCH * CHUNK;
+};
+
+// An encoded tensor map (CUtensorMap), passed by value as a kernel parameter.
+struct alignas(64) TmaDesc {
+  unsigned long long v[16];
 };
 
 struct FarArgs {
@@ -105,10 +128,10 @@ __global__ void k_dft_planes(uint16_t* out) {
   out[e + 3 * P] = bf16_bits((float)(im - (double)bf16_value(ih)));
 }
 
-// Eight consecutive K values (k0 % 8 == 0) of operand row `row` into the four
-// planes (hi/lo of the real and imaginary parts).
+// Eight consecutive K values (K offset 8 h of a 16-wide slice) of operand
+// row `row` into the four planes of a B slice (hi/lo of re and im).
 template <int N>
-__device__ __forceinline__ void put8(unsigned char* planes, int row, int k0, const float* re, const float* im) {
+__device__ __forceinline__ void put8(unsigned char* slice, int row, int h, const float* re, const float* im) {
   using C = FarTc<N>;
   uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
@@ -123,127 +146,77 @@ __device__ __forceinline__ void put8(unsigned char* planes, int row, int k0, con
     ih[q] = (uint32_t)a0 | ((uint32_t)a1 << 16);
     il[q] = (uint32_t)b0 | ((uint32_t)b1 << 16);
   }
-  unsigned char* p = planes + (size_t)(row / 8) * C::BSBO + (size_t)(k0 / 8) * 128 + (row % 8) * 16;
+  unsigned char* p = slice + (size_t)(row / 8) * C::BSBO + h * 128 + (row % 8) * 16;
   *(uint4*)p = make_uint4(rh[0], rh[1], rh[2], rh[3]);
   *(uint4*)(p + C::BPLANE) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
   *(uint4*)(p + 2 * C::BPLANE) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
   *(uint4*)(p + 3 * C::BPLANE) = make_uint4(il[0], il[1], il[2], il[3]);
 }
 
-// Row `row`, columns [c0, c0 + N/2) of an N x N complex image in global
-// memory (times the per-column factor f when SCALE) into the operand planes.
-template <int N, bool SCALE>
-__device__ __forceinline__ void rows_to_planes(unsigned char* planes, const float2* src, int row, int c0,
-                                               const float (&f)[N / 2]) {
-  // 16 columns (eight 16-byte loads) in flight per step
-#pragma unroll
-  for (int g = 0; g < N / 16; g += 2) {
-    const float4* s = (const float4*)(src + (size_t)row * N + c0 + 8 * g);
-    float4 v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = __ldcg(s + q);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      float re[8], im[8];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        re[2 * q] = v[4 * h + q].x; im[2 * q] = v[4 * h + q].y;
-        re[2 * q + 1] = v[4 * h + q].z; im[2 * q + 1] = v[4 * h + q].w;
+// Bounded wait that also gives up when another role has aborted; the
+// outcome is made uniform over the warp.
+__device__ __forceinline__ bool role_wait(uint64_t* b, uint32_t parity, volatile int* abort_s) {
+  bool ok = tc::mbar_try_wait(b, parity);
+  if (!ok) {
+    const long long t0 = clock64();
+    while (!(ok = tc::mbar_try_wait(b, parity))) {
+      if (*abort_s) break;
+      if (clock64() - t0 > (1ll << 31)) {
+        *abort_s = 1;
+        break;
       }
-      if (SCALE) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          re[i] *= f[8 * (g + h) + i];
-          im[i] *= f[8 * (g + h) + i];
-        }
-      }
-      put8<N>(planes, row, c0 + 8 * (g + h), re, im);
     }
   }
+  return !__any_sync(0xffffffffu, !ok);
 }
 
-// The pass result in TMEM (this thread's lane = operand row) into the planes
-// as the next pass's B operand.
-template <int N>
-__device__ __forceinline__ void tmem_to_planes(unsigned char* planes, uint32_t trow, int row, int c0) {
-  constexpr int G = N / 32 < 2 ? N / 32 : 2;   // 16-column groups per TMEM round trip
-#pragma unroll 1
-  for (int g = 0; g < N / 32; g += G) {
-    float re[G][16], im[G][16];
-#pragma unroll
-    for (int h = 0; h < G; ++h) {
-      tc::tmem_ld16(trow + c0 + 16 * (g + h), re[h]);
-      tc::tmem_ld16(trow + N + c0 + 16 * (g + h), im[h]);
-    }
-    tc::tmem_wait_ld();
-#pragma unroll
-    for (int h = 0; h < G; ++h) {
-      put8<N>(planes, row, c0 + 16 * (g + h), re[h], im[h]);
-      put8<N>(planes, row, c0 + 16 * (g + h) + 8, re[h] + 8, im[h] + 8);
-    }
-  }
-}
-
-// The pass result (row `row`, columns [c0, c0 + N/2)) times `scale` into
-// global memory; with ACC its squared modulus is added to (or, when `first`,
-// stored into) `acc`.
-template <int N, bool ACC>
-__device__ __forceinline__ void tmem_to_global(float2* dst, uint32_t trow, int row, int c0, float scale,
-                                               float (&acc)[N / 2], bool first) {
-  constexpr int G = N / 32 < 2 ? N / 32 : 2;   // 16-column groups per TMEM round trip
-#pragma unroll
-  for (int g = 0; g < N / 32; g += G) {
-    float re[G][16], im[G][16];
-#pragma unroll
-    for (int h = 0; h < G; ++h) {
-      tc::tmem_ld16(trow + c0 + 16 * (g + h), re[h]);
-      tc::tmem_ld16(trow + N + c0 + 16 * (g + h), im[h]);
-    }
-    tc::tmem_wait_ld();
-#pragma unroll
-    for (int h = 0; h < G; ++h) {
-      float4* d = (float4*)(dst + (size_t)row * N + c0 + 16 * (g + h));
-#pragma unroll
-      for (int i = 0; i < 16; i += 2) {
-        const float x0 = re[h][i] * scale, y0 = im[h][i] * scale;
-        const float x1 = re[h][i + 1] * scale, y1 = im[h][i + 1] * scale;
-        d[i / 2] = make_float4(x0, y0, x1, y1);
-        if (ACC) {
-          const int c = 16 * (g + h) + i;
-          const float a0 = fmaf(x0, x0, y0 * y0), a1 = fmaf(x1, x1, y1 * y1);
-          acc[c] = first ? a0 : acc[c] + a0;
-          acc[c + 1] = first ? a1 : acc[c + 1] + a1;
-        }
-      }
-    }
-  }
+// Staged-tile element of row `row`, 16-byte chunk `c` (of 8), in the
+// 128-byte swizzle the tensor copies write: chunk c of row r sits at c ^ (r % 8).
+__device__ __forceinline__ float4 staged_chunk(const unsigned char* tile, int row, int c) {
+  return *(const float4*)(tile + (size_t)row * 128 + ((c ^ (row & 7)) << 4));
 }
 
 template <int N>
-__global__ void __launch_bounds__(256, 1) k_far_tc(FarArgs a) {
+__global__ void __launch_bounds__(FarTc<N>::T, 1)
+    k_far_tc(FarArgs a, const __grid_constant__ TmaDesc tm_psi, const __grid_constant__ TmaDesc tm_meas) {
   using C = FarTc<N>;
-  constexpr int NN = N * N, HALF = C::HALF;
-  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NN = N * N, HALF = C::HALF, NCH = C::NCH, NSB = C::NSB, NSS = C::NSS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   wait_prior_grid();
-  unsigned char* planes = smem + C::planes;
-  unsigned char* ring = smem + C::ring;
-  uint64_t* full = (uint64_t*)(smem + C::bars);
-  uint64_t* empty = full + C::NS;
-  uint64_t* done = empty + C::NS;
-  double* red = (double*)(smem + C::red);
+  unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* fring = smem + C::fring;
+  unsigned char* sring = smem + C::sring;
+  unsigned char* bring = smem + C::bring;
+  uint64_t* fullF = (uint64_t*)(smem + C::bars);
+  uint64_t* emptyF = fullF + C::NSF;
+  uint64_t* fullB = emptyF + C::NSF;
+  uint64_t* emptyB = fullB + NSB;
+  uint64_t* fullS = emptyB + NSB;
+  uint64_t* emptyS = fullS + NSS;
+  uint64_t* p1done = emptyS + NSS;
+  uint64_t* p2done = p1done + 1;
+  uint64_t* drained = p2done + 1;
   uint32_t* holder = (uint32_t*)(smem + C::misc);
+  volatile int* abort_s = (volatile int*)(holder + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int row = 32 * (warp & 3) + lane;   // TMEM lane = operand row
-  const int c0 = (warp >> 2) * HALF;        // this thread's column half
-  const bool act = row < N;                 // warp-uniform (N is a multiple of 32)
-
   if (tid == 0) {
-    for (int s = 0; s < C::NS; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
+    for (int s = 0; s < C::NSF; ++s) {
+      tc::mbar_init(&fullF[s], 1);
+      tc::mbar_init(&emptyF[s], 1);
     }
-    tc::mbar_init(done, 1);
+    for (int s = 0; s < NSB; ++s) {
+      tc::mbar_init(&fullB[s], C::PW);
+      tc::mbar_init(&emptyB[s], 1);
+    }
+    for (int s = 0; s < NSS; ++s) {
+      tc::mbar_init(&fullS[s], 1);
+      tc::mbar_init(&emptyS[s], C::PW);
+    }
+    tc::mbar_init(p1done, 1);
+    tc::mbar_init(p2done, 1);
+    tc::mbar_init(drained, C::PW);
+    *abort_s = 0;
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -254,182 +227,444 @@ __global__ void __launch_bounds__(256, 1) k_far_tc(FarArgs a) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *holder;
-  const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-  const unsigned char* dft = (const unsigned char*)a.dft;
+  const uint32_t bufA = tmem, bufB = tmem + 2 * N;
 
-  // Ring of DFT chunks: chunk q of the (periodic) sequence 0..NCH-1, 0.. lives
-  // in slot q % NS; `full` completes when its bytes have landed, `empty` when
-  // the MMAs reading it have completed. Only thread 0 uses these counters.
-  long long qc = 0, issued = 0;
-  if (tid == 0) {
-    for (int s = 0; s < C::NS; ++s) {
-      tc::mbar_expect_tx(&full[s], C::CHUNK);
-      tc::bulk_g2s(ring + (size_t)s * C::CHUNK, dft + (size_t)(s % C::NCH) * C::CHUNK, C::CHUNK, &full[s]);
-    }
-    issued = C::NS;
-  }
-
-  constexpr uint32_t I_POS = tc::idesc_bf16(C::MT, N, false), I_NEG = tc::idesc_bf16(C::MT, N, true);
-  // One pass: NCH K-steps of 12 MMAs (3 split terms x 4 real products), then
-  // a commit to `done`. Thread 0 only; false if a wait gave up.
-  auto issue_pass = [&](bool inverse) -> bool {
-    const uint32_t pb = tc::smem_u32(planes);
-    const uint32_t i_re = inverse ? I_POS : I_NEG;   // Fi Xi into D_re: minus forward, plus inverse
-    const uint32_t i_im = inverse ? I_NEG : I_POS;   // Fi Xr into D_im: plus forward, minus inverse
-    const uint32_t dre = tmem, dim = tmem + N;
-    for (int s = 0; s < C::NCH; ++s, ++qc) {
-      const int sl = (int)(qc % C::NS);
-      if (!tc::mbar_wait(&full[sl], (uint32_t)((qc / C::NS) & 1))) return false;
-      const uint32_t sa = tc::smem_u32(ring + (size_t)sl * C::CHUNK);
-      const uint64_t aRh = tc::sdesc(sa, 128, C::ASBO), aRl = tc::sdesc(sa + C::APLANE, 128, C::ASBO);
-      const uint64_t aIh = tc::sdesc(sa + 2 * C::APLANE, 128, C::ASBO);
-      const uint64_t aIl = tc::sdesc(sa + 3 * C::APLANE, 128, C::ASBO);
-      const uint32_t bo = pb + 256u * (uint32_t)s;
-      const uint64_t bRh = tc::sdesc(bo, 128, C::BSBO), bRl = tc::sdesc(bo + C::BPLANE, 128, C::BSBO);
-      const uint64_t bIh = tc::sdesc(bo + 2 * C::BPLANE, 128, C::BSBO);
-      const uint64_t bIl = tc::sdesc(bo + 3 * C::BPLANE, 128, C::BSBO);
-      const uint32_t acc0 = s > 0 ? 1u : 0u;
-      tc::mma_bf16(dre, aRh, bRh, I_POS, acc0);
-      tc::mma_bf16(dre, aRl, bRh, I_POS, 1u);
-      tc::mma_bf16(dre, aRh, bRl, I_POS, 1u);
-      tc::mma_bf16(dre, aIh, bIh, i_re, 1u);
-      tc::mma_bf16(dre, aIl, bIh, i_re, 1u);
-      tc::mma_bf16(dre, aIh, bIl, i_re, 1u);
-      tc::mma_bf16(dim, aRh, bIh, I_POS, acc0);
-      tc::mma_bf16(dim, aRl, bIh, I_POS, 1u);
-      tc::mma_bf16(dim, aRh, bIl, I_POS, 1u);
-      tc::mma_bf16(dim, aIh, bRh, i_im, 1u);
-      tc::mma_bf16(dim, aIl, bRh, i_im, 1u);
-      tc::mma_bf16(dim, aIh, bRl, i_im, 1u);
-      tc::mma_commit(&empty[sl]);
-      if (qc >= 1) {   // refill the previous chunk's slot once its MMAs are done
-        const long long qp = qc - 1, qn = qp + C::NS;
-        const int sp = (int)(qp % C::NS);
-        if (!tc::mbar_wait(&empty[sp], (uint32_t)((qp / C::NS) & 1))) return false;
-        tc::mbar_expect_tx(&full[sp], C::CHUNK);
-        tc::bulk_g2s(ring + (size_t)sp * C::CHUNK, dft + (size_t)(qn % C::NCH) * C::CHUNK, C::CHUNK, &full[sp]);
-        ++issued;
-      }
-    }
-    tc::mma_commit(done);
-    return true;
-  };
-
-  uint32_t npass = 0;
-  // All threads: publish the planes, issue one pass, wait for it. False (on
-  // every thread) if any wait gave up.
-  auto run_pass = [&](bool inverse) -> bool {
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      if (!issue_pass(inverse)) atomicOr(a.status, FLAG_TIMEOUT);
-    }
-    const bool ok = tc::mbar_wait(done, npass & 1u);
-    ++npass;
-    tc::fence_after_sync();
-    return !__syncthreads_or(!ok);
-  };
-
-  const float invN = 1.0f / (float)N;
-  constexpr uint32_t IMG = (uint32_t)NN * sizeof(float2);
-  // L2 prefetch of an image this CTA reads next (thread 0)
-  auto prefetch = [&](const float2* p) {
-    if (tid == 0) tc::prefetch_l2(p, IMG);
-  };
-  bool alive = true;
-  if (blockIdx.x < a.nb) prefetch(a.psi_s + (size_t)blockIdx.x * a.M * NN);
-  for (int slot = blockIdx.x; slot < a.nb && alive; slot += gridDim.x) {
+  // The image sequence every role walks: per valid slot, M forward transforms,
+  // then (unless only intensities are wanted) M inverse ones.
+  auto slot_j = [&](int slot) -> int {
     const int e = a.b0 + slot;
     const int j = a.order ? a.order[e] : e;
     int ty, tx;
     float fy, fx;
-    if (!(j >= 0 && j < a.J) || !tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx))
-      continue;   // flagged by the first part of the pass
-    float2* psi = a.psi_s + (size_t)slot * a.M * NN;
-    if (tid == 0 && a.meas && a.mode != MODE_FWD) tc::prefetch_l2(a.meas + (size_t)j * NN, (uint32_t)NN * 4);
-    const bool more = slot + (int)gridDim.x < a.nb;
-    float2* next_slot = more ? a.psi_s + (size_t)(slot + gridDim.x) * a.M * NN : nullptr;
-    float acc[HALF];
-#pragma unroll
-    for (int i = 0; i < HALF; ++i) acc[i] = 0.f;
+    if (!(j >= 0 && j < a.J) || !tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx)) return -1;
+    return j;   // an invalid slot is flagged by the first part of the pass
+  };
+  const bool backward = a.mode != MODE_FWD;
 
-    // ---- forward: Psi_k = F psi_k F^T / N, I = sum_k |Psi_k|^2 ----------------------
-    for (int k = 0; k < a.M && alive; ++k) {
-      if (k + 1 < a.M) prefetch(psi + (size_t)(k + 1) * NN);
-      else if (a.mode == MODE_FWD && next_slot) prefetch(next_slot);
-      if (act) rows_to_planes<N, false>(planes, psi + (size_t)k * NN, row, c0, acc);
-      if (!(alive = run_pass(false))) break;
-      if (act) tmem_to_planes<N>(planes, trow, row, c0);
-      if (!(alive = run_pass(false))) break;
-      if (act) tmem_to_global<N, true>(psi + (size_t)k * NN, trow, row, c0, invN, acc, k == 0);
-    }
-    if (!alive) break;
-
-    // ---- data term: loss and the far-field factor (times 1/N for the inverse) --------
-    float lsum = 0.f;
-    bool bad = false;
-    if (act) {
-      const float* meas = a.meas ? a.meas + (size_t)j * NN + (size_t)row * N + c0 : nullptr;
-      float* ip = a.ipred ? a.ipred + (size_t)j * NN + (size_t)row * N + c0 : nullptr;
-#pragma unroll
-      for (int i = 0; i < HALF; ++i) {
-        const float I = acc[i];
-        if (ip) ip[i] = I;
-        if (a.mode == MODE_FWD) continue;
-        const float Im = __ldg(meas + i);
-        float fac;
-        if (a.mode == MODE_VJP) {
-          bad |= !isfinite(Im);
-          fac = 2.f * Im;
-        } else {
-          bad |= !(Im >= 0.f) || !isfinite(Im);
-          const float Ie = I + a.eps;
-          if (a.mode == MODE_LSQML_GAUSS || a.mode == MODE_GRAD_GAUSS) {
-            const float sIe = sqrtf(Ie), sIm = sqrtf(Im);
-            const float d = sIe - sIm;
-            lsum = fmaf(d, d, lsum);
-            const float rho = sIm / sIe;
-            fac = (a.mode == MODE_LSQML_GAUSS) ? rho - 1.f : 2.f * (1.f - rho);
-          } else {
-            lsum += I - Im * logf(Ie);
-            const float q = Im / Ie;
-            fac = (a.mode == MODE_LSQML_POISSON) ? 0.5f * (q - 1.f) : 2.f * (1.f - q);
+  if (warp == C::PW) {
+    // ================================ MMA warp ====================================
+    if (lane == 0) {
+      const unsigned char* dft = (const unsigned char*)a.dft;
+      uint32_t qc = 0, issued = 0, cb = 0;
+      for (int s = 0; s < C::NSF; ++s) {
+        tc::mbar_expect_tx(&fullF[s], C::CHUNK);
+        tc::bulk_g2s(fring + (size_t)s * C::CHUNK, dft + (size_t)(s % NCH) * C::CHUNK, C::CHUNK, &fullF[s]);
+      }
+      issued = C::NSF;
+      constexpr uint32_t I_POS = tc::idesc_bf16(C::MT, N, false), I_NEG = tc::idesc_bf16(C::MT, N, true);
+      bool ok = true;
+      // one pass into the accumulator at `d` (re at d, im at d + N)
+      auto pass = [&](uint32_t d, bool inverse, uint64_t* done) {
+        const uint32_t i_re = inverse ? I_POS : I_NEG;   // Fi Xi into D_re: minus forward, plus inverse
+        const uint32_t i_im = inverse ? I_NEG : I_POS;   // Fi Xr into D_im: plus forward, minus inverse
+        for (int s = 0; s < NCH && ok; ++s, ++qc, ++cb) {
+          const int sf = (int)(qc % C::NSF), sb = (int)(cb % NSB);
+          if (!tc::mbar_wait(&fullF[sf], (uint32_t)((qc / C::NSF) & 1)) ||
+              !tc::mbar_wait(&fullB[sb], (uint32_t)((cb / NSB) & 1))) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_u32(fring + (size_t)sf * C::CHUNK);
+          const uint64_t aRh = tc::sdesc(sa, 128, C::ASBO), aRl = tc::sdesc(sa + C::APLANE, 128, C::ASBO);
+          const uint64_t aIh = tc::sdesc(sa + 2 * C::APLANE, 128, C::ASBO);
+          const uint64_t aIl = tc::sdesc(sa + 3 * C::APLANE, 128, C::ASBO);
+          const uint32_t sbase = tc::smem_u32(bring + (size_t)sb * C::SLICE);
+          const uint64_t bRh = tc::sdesc(sbase, 128, C::BSBO), bRl = tc::sdesc(sbase + C::BPLANE, 128, C::BSBO);
+          const uint64_t bIh = tc::sdesc(sbase + 2 * C::BPLANE, 128, C::BSBO);
+          const uint64_t bIl = tc::sdesc(sbase + 3 * C::BPLANE, 128, C::BSBO);
+          const uint32_t acc0 = s > 0 ? 1u : 0u, dre = d, dim = d + N;
+          tc::mma_bf16(dre, aRh, bRh, I_POS, acc0);
+          tc::mma_bf16(dre, aRl, bRh, I_POS, 1u);
+          tc::mma_bf16(dre, aRh, bRl, I_POS, 1u);
+          tc::mma_bf16(dre, aIh, bIh, i_re, 1u);
+          tc::mma_bf16(dre, aIl, bIh, i_re, 1u);
+          tc::mma_bf16(dre, aIh, bIl, i_re, 1u);
+          tc::mma_bf16(dim, aRh, bIh, I_POS, acc0);
+          tc::mma_bf16(dim, aRl, bIh, I_POS, 1u);
+          tc::mma_bf16(dim, aRh, bIl, I_POS, 1u);
+          tc::mma_bf16(dim, aIh, bRh, i_im, 1u);
+          tc::mma_bf16(dim, aIl, bRh, i_im, 1u);
+          tc::mma_bf16(dim, aIh, bRl, i_im, 1u);
+          tc::mma_commit(&emptyF[sf]);
+          tc::mma_commit(&emptyB[sb]);
+          if (qc >= 1) {   // refill the previous chunk's slot once its MMAs are done
+            const uint32_t qp = qc - 1, qn = qp + C::NSF;
+            const int sp = (int)(qp % C::NSF);
+            if (!tc::mbar_wait(&emptyF[sp], (uint32_t)((qp / C::NSF) & 1))) {
+              ok = false;
+              break;
+            }
+            tc::mbar_expect_tx(&fullF[sp], C::CHUNK);
+            tc::bulk_g2s(fring + (size_t)sp * C::CHUNK, dft + (size_t)(qn % NCH) * C::CHUNK, C::CHUNK,
+                         &fullF[sp]);
+            ++issued;
           }
         }
-        acc[i] = fac * invN;
+        if (ok) tc::mma_commit(done);
+      };
+      uint32_t n = 0;
+      for (int slot = blockIdx.x; slot < a.nb && ok && !*abort_s; slot += gridDim.x) {
+        if (slot_j(slot) < 0) continue;
+        for (int t = 0; t < (backward ? 2 * a.M : a.M) && ok && !*abort_s; ++t, ++n) {
+          const bool inverse = t >= a.M;
+          pass(bufA, inverse, p1done);
+          if (ok && n >= 1 && !tc::mbar_wait(drained, (uint32_t)((n - 1) & 1))) ok = false;
+          if (ok) pass(bufB, inverse, p2done);
+        }
+      }
+      if (!ok) *abort_s = 1;
+      // copies still in flight land before the CTA exits
+      for (; qc < issued; ++qc)
+        if (!tc::mbar_wait(&fullF[(int)(qc % C::NSF)], (uint32_t)((qc / C::NSF) & 1))) {
+          *abort_s = 1;
+          break;
+        }
+    }
+  } else if (warp == C::PW + 1) {
+    // ================================ TMA warp ====================================
+    // Stages, in the order the producers consume them, the exit waves of the
+    // forward transforms (N x 32-float tiles, 16 complex columns each) and
+    // the measured intensities of the data term (N x 32-float tiles).
+    if (lane == 0) {
+      uint32_t ps = 0;
+      bool ok = true;
+      auto stage = [&](const TmaDesc* map, int x, int z) {
+        const int sl = (int)(ps % NSS);
+        if (ps >= NSS && !tc::mbar_wait(&emptyS[sl], (uint32_t)(((ps / NSS) - 1) & 1))) {
+          ok = false;
+          return;
+        }
+        tc::mbar_expect_tx(&fullS[sl], C::SSLOT);
+        tc::tma_load_3d(sring + (size_t)sl * C::SSLOT, map, x, 0, z, &fullS[sl]);
+        ++ps;
+      };
+      for (int slot = blockIdx.x; slot < a.nb && ok && !*abort_s; slot += gridDim.x) {
+        const int j = slot_j(slot);
+        if (j < 0) continue;
+        for (int k = 0; k < a.M && ok; ++k)
+          for (int s = 0; s < NCH && ok; ++s) stage(&tm_psi, 32 * s, slot * a.M + k);
+        if (backward)
+          for (int b = 0; b < (NCH + 1) / 2 && ok; ++b) stage(&tm_meas, 32 * b, j);
+      }
+      if (!ok) *abort_s = 1;
+      // tiles still in flight land before the CTA exits (the last fill of each slot)
+      for (uint32_t p = ps - (ps < (uint32_t)NSS ? ps : (uint32_t)NSS); p < ps; ++p)
+        if (!tc::mbar_wait(&fullS[(int)(p % NSS)], (uint32_t)((p / NSS) & 1))) {
+          *abort_s = 1;
+          break;
+        }
+    }
+  } else {
+    // ============================= producer warps =================================
+    const int q4 = warp & 3, h = warp >> 2;
+    const int row = 32 * q4 + lane;           // TMEM lane = operand row
+    const bool act = row < N;                  // warp-uniform
+    const uint32_t lrow = (uint32_t)(32 * q4) << 16;
+    const float invN = 1.0f / (float)N;
+    uint32_t pb = 0, ps = 0, n = 0, nd = 0;
+    float acc[HALF];                           // I, then the far-field factor, of columns 16 s + 8 h + [0, 8)
+#pragma unroll
+    for (int i = 0; i < HALF; ++i) acc[i] = 0.f;
+    bool alive = true;
+
+    // takes B slot pb (waiting for it to be free), fills it, publishes it
+    auto publish = [&](auto&& fill) {
+      const int sb = (int)(pb % NSB);
+      if (pb >= NSB && !role_wait(&emptyB[sb], (uint32_t)(((pb / NSB) - 1) & 1), abort_s)) {
+        alive = false;
+        return;
+      }
+      if (act) fill(bring + (size_t)sb * C::SLICE);
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&fullB[sb]);
+      ++pb;
+    };
+    // waits for staged tile ps; returns it (null if a wait gave up)
+    auto staged = [&]() -> const unsigned char* {
+      const int sl = (int)(ps % NSS);
+      if (!role_wait(&fullS[sl], (uint32_t)((ps / NSS) & 1), abort_s)) {
+        alive = false;
+        return nullptr;
+      }
+      return sring + (size_t)sl * C::SSLOT;
+    };
+    auto release_staged = [&]() {
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&emptyS[(int)(ps % NSS)]);
+      ++ps;
+    };
+    // pass-1 slices of a forward transform from the staged exit wave
+    auto produce_staged = [&]() {
+#pragma unroll 1
+      for (int s = 0; s < NCH; ++s) {
+        const unsigned char* tile = staged();
+        if (!alive) break;
+        float4 v[4];
+        if (act) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) v[i] = staged_chunk(tile, row, 4 * h + i);
+        }
+        publish([&](unsigned char* slice) {
+          float re[8], im[8];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            re[2 * i] = v[i].x; im[2 * i] = v[i].y; re[2 * i + 1] = v[i].z; im[2 * i + 1] = v[i].w;
+          }
+          put8<N>(slice, row, h, re, im);
+        });
+        if (!alive) break;
+        release_staged();
+      }
+    };
+    // pass-1 slices of an inverse transform from a far field in global memory
+    // (just written by this CTA, so in L2), times the factors
+    auto produce_global = [&](const float2* src) {
+      constexpr int G = 2;   // slices of loads in flight
+#pragma unroll
+      for (int s0 = 0; s0 < NCH; s0 += G) {
+        if (!alive) break;
+        float4 v[G][4];
+        if (act) {
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const float4* p4 = (const float4*)(src + (size_t)row * N + 16 * (s0 + g) + 8 * h);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[g][i] = __ldcg(p4 + i);
+          }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          if (!alive) break;
+          publish([&](unsigned char* slice) {
+            float re[8], im[8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              re[2 * i] = v[g][i].x; im[2 * i] = v[g][i].y; re[2 * i + 1] = v[g][i].z; im[2 * i + 1] = v[g][i].w;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              re[i] *= acc[8 * (s0 + g) + i];
+              im[i] *= acc[8 * (s0 + g) + i];
+            }
+            put8<N>(slice, row, h, re, im);
+          });
+        }
+      }
+    };
+    // slices from an accumulator in TMEM: pass-2 slices from buffer A, or
+    // (SCALE) the first inverse transform's pass-1 slices from the last forward
+    // far field in buffer B, times 1/N and the factors
+    auto produce_tmem = [&](uint32_t buf, bool scale) {
+      constexpr int G = NCH < 2 ? NCH : 2;   // slices per TMEM round trip
+      if (scale) {
+#pragma unroll
+        for (int s = 0; s < NCH; ++s) {
+          if (!alive) break;
+          float re[8], im[8];
+          if (act) {
+            tc::tmem_ld8(buf + lrow + 16 * s + 8 * h, re);
+            tc::tmem_ld8(buf + lrow + N + 16 * s + 8 * h, im);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const float f = acc[8 * s + i] * invN;
+              re[i] *= f;
+              im[i] *= f;
+            }
+          }
+          publish([&](unsigned char* slice) { put8<N>(slice, row, h, re, im); });
+        }
+        return;
+      }
+#pragma unroll 1
+      for (int s0 = 0; s0 < NCH; s0 += G) {
+        if (!alive) break;
+        float re[G][8], im[G][8];
+        if (act) {
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            tc::tmem_ld8(buf + lrow + 16 * (s0 + g) + 8 * h, re[g]);
+            tc::tmem_ld8(buf + lrow + N + 16 * (s0 + g) + 8 * h, im[g]);
+          }
+          tc::tmem_wait_ld();
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          if (!alive) break;
+          publish([&](unsigned char* slice) { put8<N>(slice, row, h, re[g], im[g]); });
+        }
+      }
+    };
+    // the pass-2 accumulator (buffer B) times `scale` to global memory (unless
+    // dst is null); with `accumulate` its squared modulus is stored into
+    // (first) or added to acc
+    auto drain = [&](float2* dst, bool accumulate, bool first, float scale) {
+      if (act) {
+#pragma unroll
+        for (int s = 0; s < NCH; ++s) {
+          float re[8], im[8];
+          tc::tmem_ld8(bufB + lrow + 16 * s + 8 * h, re);
+          tc::tmem_ld8(bufB + lrow + N + 16 * s + 8 * h, im);
+          tc::tmem_wait_ld();
+          float4* d4 = dst ? (float4*)(dst + (size_t)row * N + 16 * s + 8 * h) : nullptr;
+#pragma unroll
+          for (int i = 0; i < 8; i += 2) {
+            const float x0 = re[i] * scale, y0 = im[i] * scale, x1 = re[i + 1] * scale, y1 = im[i + 1] * scale;
+            if (d4) d4[i / 2] = make_float4(x0, y0, x1, y1);
+            if (accumulate) {
+              const float a0 = fmaf(x0, x0, y0 * y0), a1 = fmaf(x1, x1, y1 * y1);
+              acc[8 * s + i] = first ? a0 : acc[8 * s + i] + a0;
+              acc[8 * s + i + 1] = first ? a1 : acc[8 * s + i + 1] + a1;
+            }
+          }
+        }
+      }
+    };
+    auto arrive_drained = [&]() {
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(drained);
+    };
+    // the data term of position j from the intensities in acc: loss, ipred, and
+    // the far-field factor (times 1/N for the unnormalised inverse) into acc;
+    // the measured values come from the staged tiles (none in the forward mode)
+    auto data_term = [&](int j) {
+      float lsum = 0.f;
+      bool bad = false;
+      float* ip = (a.ipred && act) ? a.ipred + (size_t)j * NN + (size_t)row * N + 8 * h : nullptr;
+#pragma unroll
+      for (int b = 0; b < (NCH + 1) / 2; ++b) {
+        float mv[2][8];
+        if (backward) {
+          const unsigned char* tile = staged();
+          if (!alive) break;
+          if (act) {
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+              const float4 m0 = staged_chunk(tile, row, 4 * g + 2 * h), m1 = staged_chunk(tile, row, 4 * g + 2 * h + 1);
+              mv[g][0] = m0.x; mv[g][1] = m0.y; mv[g][2] = m0.z; mv[g][3] = m0.w;
+              mv[g][4] = m1.x; mv[g][5] = m1.y; mv[g][6] = m1.z; mv[g][7] = m1.w;
+            }
+          }
+          release_staged();
+        }
+        if (act) {
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+            const int s = 2 * b + g;
+            if (s >= NCH) break;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int c = 16 * s + i, ai = 8 * s + i;
+              const float I = acc[ai];
+              if (ip) ip[c] = I;
+              if (!backward) continue;
+              const float Im = mv[g][i];
+              float fac;
+              if (a.mode == MODE_VJP) {
+                bad |= !isfinite(Im);
+                fac = 2.f * Im;
+              } else {
+                bad |= !(Im >= 0.f) || !isfinite(Im);
+                const float Ie = I + a.eps;
+                if (a.mode == MODE_LSQML_GAUSS || a.mode == MODE_GRAD_GAUSS) {
+                  const float sIe = sqrtf(Ie), sIm = sqrtf(Im);
+                  const float dd = sIe - sIm;
+                  lsum = fmaf(dd, dd, lsum);
+                  const float rho = sIm / sIe;
+                  fac = (a.mode == MODE_LSQML_GAUSS) ? rho - 1.f : 2.f * (1.f - rho);
+                } else {
+                  lsum += I - Im * logf(Ie);
+                  const float qq = Im / Ie;
+                  fac = (a.mode == MODE_LSQML_POISSON) ? 0.5f * (qq - 1.f) : 2.f * (1.f - qq);
+                }
+              }
+              acc[ai] = fac * invN;
+            }
+          }
+        }
+      }
+      if (bad) atomicOr(a.status, FLAG_NONFINITE);
+      if (a.loss && backward && a.mode != MODE_VJP) {
+        double v = (double)lsum;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0 && v != 0.0) atomicAdd(a.loss, v);
+      }
+    };
+
+    // the previous image, drained once the next image's pass-1 slices are out
+    float2* prev_dst = nullptr;
+    bool have_prev = false, prev_fwd = false, prev_first = false, prev_last_fwd = false;
+    int prev_j = -1;
+    auto drain_prev = [&]() {
+      if (!role_wait(p2done, (uint32_t)(nd & 1), abort_s)) {
+        alive = false;
+        return;
+      }
+      tc::fence_after_sync();
+      // forward far fields are kept for the inverse transforms (not needed
+      // when only intensities are computed); inverse results are chi
+      drain(prev_fwd && !backward ? nullptr : prev_dst, prev_fwd, prev_first, prev_fwd ? invN : 1.f);
+      arrive_drained();
+      ++nd;
+      if (prev_fwd && prev_last_fwd && !backward) data_term(prev_j);
+      have_prev = false;
+    };
+
+    for (int slot = blockIdx.x; slot < a.nb && alive; slot += gridDim.x) {
+      const int j = slot_j(slot);
+      if (j < 0) continue;
+      float2* psi = a.psi_s + (size_t)slot * a.M * NN;
+      for (int t = 0; t < (backward ? 2 * a.M : a.M) && alive; ++t, ++n) {
+        const bool fwd = t < a.M;
+        const int k = fwd ? t : 2 * a.M - 1 - t;
+        float2* io = psi + (size_t)k * NN;
+        if (fwd) {
+          produce_staged();
+          if (have_prev && alive) drain_prev();
+        } else if (k == a.M - 1) {
+          // first inverse transform: the last forward far field is still in
+          // buffer B; its intensities complete I, then the data term gives the
+          // factor, then its pass-1 slices come straight from TMEM
+          if (!role_wait(p2done, (uint32_t)(nd & 1), abort_s)) {
+            alive = false;
+            break;
+          }
+          tc::fence_after_sync();
+          drain(nullptr, true, a.M == 1, invN);
+          ++nd;
+          data_term(j);
+          if (alive) produce_tmem(bufB, true);
+          arrive_drained();
+          have_prev = false;
+        } else {
+          produce_global(io);
+          if (have_prev && alive) drain_prev();
+        }
+        if (!alive) break;
+        if (!role_wait(p1done, (uint32_t)(n & 1), abort_s)) {
+          alive = false;
+          break;
+        }
+        tc::fence_after_sync();
+        produce_tmem(bufA, false);
+        prev_dst = io;
+        have_prev = true;
+        prev_fwd = fwd;
+        prev_first = fwd && k == 0;
+        prev_last_fwd = fwd && k == a.M - 1;
+        prev_j = j;
       }
     }
-    if (bad) atomicOr(a.status, FLAG_NONFINITE);
-    if (a.loss && a.mode != MODE_FWD && a.mode != MODE_VJP) {
-      double v[1] = {(double)lsum};
-      block_sum<1>(v, red);
-      if (tid == 0) atomicAdd(a.loss, v[0]);
-    }
-    if (a.mode == MODE_FWD) continue;
-
-    // ---- back-propagation: chi_k = conj(F) (fac Psi_k) conj(F)^T -------------------
-    for (int k = a.M - 1; k >= 0 && alive; --k) {
-      if (k > 0) prefetch(psi + (size_t)(k - 1) * NN);
-      else if (next_slot) prefetch(next_slot);
-      if (act) rows_to_planes<N, true>(planes, psi + (size_t)k * NN, row, c0, acc);
-      if (!(alive = run_pass(true))) break;
-      if (act) tmem_to_planes<N>(planes, trow, row, c0);
-      if (!(alive = run_pass(true))) break;
-      if (act) tmem_to_global<N, false>(psi + (size_t)k * NN, trow, row, c0, 1.f, acc, false);
-    }
+    if (alive && have_prev) drain_prev();
+    if (!alive) *abort_s = 1;
   }
-  if (!alive && tid == 0) atomicOr(a.status, FLAG_TIMEOUT);
 
-  // Copies still in flight land before the CTA exits; then TMEM is released.
-  if (tid == 0) {
-    for (; qc < issued; ++qc)
-      if (!tc::mbar_wait(&full[(int)(qc % C::NS)], (uint32_t)((qc / C::NS) & 1))) {
-        atomicOr(a.status, FLAG_TIMEOUT);
-        break;
-      }
-  }
+  if (tid == 0 && *abort_s) atomicOr(a.status, FLAG_TIMEOUT);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();

@@ -1,11 +1,53 @@
 // The split-BF16 DFT-GEMM form of the per-position pass (windows 32, 64 and
 // 128): the exit-wave part of k_pass1, the tensor-core far-field stage
 // k_far_tc, and the overlap-add part of k_pass1, plus the DFT-matrix fill.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <string.h>
+
+#include <mutex>
+
 #include "kernels.cuh"
 #include "kernels_tc.cuh"
 #include "launch.h"
 
 namespace ptycho {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// Tensor map of a float32 [d2][d1][d0] array, tiles of b1 rows x b0 floats
+// (b0 * 4 = 128 bytes) written to shared memory with the 128-byte swizzle.
+static bool encode_tiles(TmaDesc* out, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0,
+                         uint32_t b1) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tmap_encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {d0 * 4, d0 * d1 * 4};
+  const cuuint32_t box[3] = {b0, b1, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  CUtensorMap m;
+  static_assert(sizeof(CUtensorMap) == sizeof(TmaDesc), "tensor map size");
+  if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  memcpy(out, &m, sizeof(m));
+  return true;
+}
 
 template <int N>
 size_t dft_plane_bytes() {
@@ -45,7 +87,13 @@ cudaError_t launch_far_tc(const BatchArgs& b, const void* dft, cudaStream_t s) {
   a.pos = b.pos; a.order = b.order; a.b0 = b.b0; a.nb = b.nb; a.mode = b.mode; a.eps = b.eps;
   a.meas = b.meas; a.psi_s = b.psi_s; a.dft = (const uint16_t*)dft;
   a.ipred = b.ipred; a.loss = b.loss; a.status = b.status;
-  return launch_pdl(k_far_tc<N>, dim3(grid), dim3(C::T), C::bytes, s, a);
+  // exit-wave tiles: 16 complex columns x N rows of image slot * M + k;
+  // measured-intensity tiles: 32 columns x N rows of position j
+  TmaDesc tpsi, tmeas;
+  memset(&tmeas, 0, sizeof(tmeas));
+  if (!encode_tiles(&tpsi, b.psi_s, 2 * N, N, (uint64_t)b.nb * b.M, 32, N)) return cudaErrorInvalidValue;
+  if (b.mode != MODE_FWD && !encode_tiles(&tmeas, b.meas, N, N, (uint64_t)b.J, 32, N)) return cudaErrorInvalidValue;
+  return launch_pdl(k_far_tc<N>, dim3(grid), dim3(C::T), C::bytes, s, a, tpsi, tmeas);
 }
 
 #define PTYCHO_TC_INSTANCES(N)                                                     \
