@@ -1,4 +1,5 @@
-"""One small forward + gradient + LSQML epoch on cuda:0, checked against the FP64 oracle."""
+"""One small forward + gradient + LSQML epoch on cuda:0, checked against the FP64 oracle
+(the FP32 FFT path), and the forward model with the split-BF16 DFT-GEMM on the tensor cores."""
 import numpy as np
 
 
@@ -15,8 +16,10 @@ def run_smoke():
     dO, dP = to_dev(O, torch.complex64), to_dev(P, torch.complex64)
     dpos, dI = to_dev(pos, torch.float32), to_dev(I_m, torch.float32)
 
+    I_ref = orc.forward(O, P, pos)
     I = api.forward(dO, dP, dpos).cpu().numpy()
-    e_fwd = rel(I, orc.forward(O, P, pos))
+    e_fwd = rel(I, I_ref)
+    e_tc = rel(api.forward(dO, dP, dpos, precision="bf16x3", batch=8).cpu().numpy(), I_ref)
 
     loss, gO, gP, gr = api.adjoint(dO, dP, dpos, dI, "gaussian", eps=1e-6)
     L_ref, gO_ref, gP_ref, gr_ref = orc.loss_and_gradients(O, P, pos, I_m, orc.GAUSSIAN, 1e-6)
@@ -29,5 +32,6 @@ def run_smoke():
     l2, _ = api.lsqml_epoch(dO, dP, dpos, dI, to_dev(order, torch.int32), batch=6, delta_o=0.1,
                             delta_p=0.1, lam=1e-6, eps=1e-6)
     e_ep = max(rel(dO.cpu().numpy(), O_ref), rel(dP.cpu().numpy(), P_ref))
-    print(f"smoke: forward {e_fwd:.2e}  grad {e_grad:.2e}  loss {e_loss:.2e}  epoch {e_ep:.2e}")
-    assert e_fwd < 1e-5 and e_grad < 1e-4 and e_loss < 1e-5 and e_ep < 1e-4
+    print(f"smoke: forward {e_fwd:.2e}  grad {e_grad:.2e}  loss {e_loss:.2e}  epoch {e_ep:.2e}  "
+          f"forward split-BF16 {e_tc:.2e}")
+    assert e_fwd < 1e-5 and e_grad < 1e-4 and e_loss < 1e-5 and e_ep < 1e-4 and e_tc < 1e-3
