@@ -99,7 +99,8 @@ typedef struct {
  * FP32 accumulation in tensor memory) with every operand split into BF16
  * hi + lo parts and three products per real product (hi*hi + lo*hi + hi*lo);
  * windows N = 32, 64 and 128 (others: PTYCHO_ERR_UNSUPPORTED), the shared
- * probe only (the relaxed-probe and multislice entry points take FP32). Its
+ * probe only (the relaxed-probe and multislice entry points take FP32); the
+ * measured-intensity array must be 16-byte aligned (else PTYCHO_ERR_ARG). Its
  * per-element error against exact arithmetic is about 2^-17 of the operand
  * magnitudes, accumulated over N terms per pass. */
 #define PTYCHO_PRECISION_FP32 0

@@ -329,10 +329,12 @@ cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s, int variant) {
 }
 bool dft_gemm_supported(int N) { return N == 32 || N == 64 || N == 128; }
 
-ptycho_status check_precision(int N, int precision) {
+ptycho_status check_precision(int N, int precision, const void* meas) {
   if (precision == PTYCHO_PRECISION_FP32) return PTYCHO_OK;
   if (precision != PTYCHO_PRECISION_BF16X3) return PTYCHO_ERR_ARG;
-  return dft_gemm_supported(N) ? PTYCHO_OK : PTYCHO_ERR_UNSUPPORTED;
+  if (!dft_gemm_supported(N)) return PTYCHO_ERR_UNSUPPORTED;
+  // the measured intensities are read with tensor copies: 16-byte aligned
+  return ((uintptr_t)meas & 15) ? PTYCHO_ERR_ARG : PTYCHO_OK;
 }
 
 template <class Fn>
@@ -738,7 +740,7 @@ ptycho_status ptycho_forward_ex(const ptycho_dims* dims, int32_t precision, int3
                                 void* stream) {
   ptycho_status st = check_dims(dims);
   if (st != PTYCHO_OK) return st;
-  if ((st = check_precision(dims->N, precision)) != PTYCHO_OK) return st;
+  if ((st = check_precision(dims->N, precision, nullptr)) != PTYCHO_OK) return st;
   if (batch < 1) return PTYCHO_ERR_ARG;
   if (!object || !probe || (dims->J > 0 && (!pos || !I_pred))) return PTYCHO_ERR_ARG;
   const bool tc = precision == PTYCHO_PRECISION_BF16X3;
@@ -778,7 +780,7 @@ ptycho_status ptycho_adjoint_ex(const ptycho_dims* dims, int32_t precision, cons
                                 size_t ws_bytes, void* stream) {
   ptycho_status st = check_dims(dims);
   if (st != PTYCHO_OK) return st;
-  if ((st = check_precision(dims->N, precision)) != PTYCHO_OK) return st;
+  if ((st = check_precision(dims->N, precision, meas)) != PTYCHO_OK) return st;
   if (batch < 1 || !(eps >= 0.0)) return PTYCHO_ERR_ARG;
   if (noise != PTYCHO_NOISE_GAUSSIAN && noise != PTYCHO_NOISE_POISSON && noise != PTYCHO_NOISE_VJP)
     return PTYCHO_ERR_ARG;
@@ -825,7 +827,7 @@ ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* 
   ptycho_status st = check_dims(dims);
   if (st != PTYCHO_OK) return st;
   if ((st = check_opts(opts)) != PTYCHO_OK) return st;
-  if ((st = check_precision(dims->N, opts->precision)) != PTYCHO_OK) return st;
+  if ((st = check_precision(dims->N, opts->precision, meas)) != PTYCHO_OK) return st;
   if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
   const Layout L = layout_for(*dims, *opts);
   if ((st = check_ws(ws, ws_bytes, L.total)) != PTYCHO_OK) return st;
@@ -860,7 +862,8 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
   ptycho_status st = check_dims(dims);
   if (st != PTYCHO_OK) return st;
   if ((st = check_opts(opts)) != PTYCHO_OK) return st;
-  if ((st = check_precision(dims->N, opts->precision)) != PTYCHO_OK) return st;
+  // (the device copy of the host intensities sits at a 256-byte boundary)
+  if ((st = check_precision(dims->N, opts->precision, nullptr)) != PTYCHO_OK) return st;
   if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
   const Layout L = layout_for(*dims, *opts);
   if ((st = check_ws(ws, ws_bytes, L.total + host_extra(*dims))) != PTYCHO_OK) return st;

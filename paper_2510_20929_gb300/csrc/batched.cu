@@ -171,7 +171,7 @@ ptycho_status ptycho_lsqml_epoch_batched(int32_t n, const ptycho_dims* dims, flo
   for (int i = 0; i < n; ++i) {
     if ((st = check_dims(&dims[i])) != PTYCHO_OK) return st;
     if ((st = check_opts(&opts[i])) != PTYCHO_OK) return st;
-    if ((st = check_precision(dims[i].N, opts[i].precision)) != PTYCHO_OK) return st;
+    if ((st = check_precision(dims[i].N, opts[i].precision, meas[i])) != PTYCHO_OK) return st;
     if (!objects[i] || !probes[i] || (dims[i].J > 0 && (!pos[i] || !meas[i]))) return PTYCHO_ERR_ARG;
   }
   const size_t need = ptycho_workspace_bytes_batched(n, dims, opts);

@@ -55,8 +55,10 @@ cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s, int variant = 0);
 cudaError_t pass2(int N, const Pass2Args& a, cudaStream_t s, int variant = 0);
 // True when the split-BF16 DFT-GEMM form is built for window N.
 bool dft_gemm_supported(int N);
-// PTYCHO_OK, or the error for an unknown precision (ARG) or one not built for N (UNSUPPORTED).
-ptycho_status check_precision(int N, int precision);
+// PTYCHO_OK, or the error for an unknown precision or a measured-intensity
+// array that is not 16-byte aligned under BF16X3 (ARG), or a precision not
+// built for N (UNSUPPORTED).
+ptycho_status check_precision(int N, int precision, const void* meas);
 // Fills the DFT chunks of the workspace (once per call of an entry point).
 cudaError_t dft_planes(int N, void* dft, cudaStream_t s);
 // The per-position pass with the far field on the tensor cores: exit waves,

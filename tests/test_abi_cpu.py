@@ -124,6 +124,9 @@ def test_arguments_rejected_before_any_launch(L):
     assert L.ptycho_forward_ex(ctypes.byref(d), 1, 4, fake, fake, fake, fake, P(0x1000), 4096, None) == 7
     assert L.ptycho_adjoint_ex(ctypes.byref(d256), 1, fake, fake, fake, fake, 0, 0.0, 4, fake, fake, P(0), P(0),
                                fake, 1 << 30, None) == 6
+    # BF16X3 reads the measured intensities with tensor copies: 16-byte aligned
+    assert L.ptycho_adjoint_ex(ctypes.byref(d), 1, fake, fake, fake, P(0x100008), 0, 0.0, 4, fake, fake, P(0), P(0),
+                               fake, 1 << 30, None) == 1
     # the relaxed-probe epoch takes FP32 only
     opr = api.make_opr_opts(2)
     assert L.ptycho_lsqml_epoch_opr(ctypes.byref(d), ctypes.byref(opr), fake, fake, fake, fake, fake, fake,

@@ -158,3 +158,27 @@ def test_bf16x3_graph_replay_and_host_epoch_match_the_device_epoch():
         api.lsqml_epoch_host(hO_t, hP_t, torch.from_numpy(np.float32(pos)), torch.from_numpy(np.float32(I_m)),
                              torch.from_numpy(order), opts, device=dO.device)
     assert rel(hO_t.numpy(), res[0][0]) < 1e-5 and rel(hP_t.numpy(), res[0][1]) < 1e-5
+
+
+def test_bf16x3_batched_reconstructions_equal_their_single_epochs():
+    # two reconstructions of different window and mode count in one batched call
+    import torch
+    from paper_2510_20929_gb300 import api
+    recs = []
+    for (N, M, H, W, J, step) in ((64, 3, 150, 160, 20, 12.0), (128, 2, 300, 310, 12, 24.0)):
+        p = problem(N=N, M=M, H=H, W=W, J=J, step=step)
+        (_, _, _, _), (dO, dP, dpos, dI) = _dev(p)
+        recs.append((dO, dP, dpos, dI, to_dev(np.random.default_rng(N).permutation(J).astype(np.int32),
+                                                torch.int32)))
+    single = []
+    for dO, dP, dpos, dI, order in recs:
+        o, pr = dO.clone(), dP.clone()
+        L, _ = api.lsqml_epoch(o, pr, dpos, dI, order, batch=5, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6,
+                               precision="bf16x3")
+        single.append((o.cpu().numpy(), pr.cpu().numpy(), L.item()))
+    batch = [[dO.clone(), dP.clone(), dpos, dI, order] for dO, dP, dpos, dI, order in recs]
+    opts = [api.make_opts(batch=5, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6, precision="bf16x3")] * 2
+    losses = api.lsqml_epoch_batched(batch, opts).cpu().numpy()
+    for (o, pr, *_), (O1, P1, L1), L in zip(batch, single, losses):
+        assert rel(o.cpu().numpy(), O1) < 1e-5 and rel(pr.cpu().numpy(), P1) < 1e-5
+        assert abs(L - L1) <= 1e-5 * abs(L1)
