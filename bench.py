@@ -586,6 +586,8 @@ def run_ad256(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     w = synth.workload_spiral256()
+    if args.positions and args.positions < w["J"]:   # profiling runs: the first positions only
+        w["pos"], w["pos_init"], w["J"] = w["pos"][:args.positions], w["pos_init"][:args.positions], args.positions
     O_true = torch.tensor(w["object"], dtype=torch.complex64, device=dev)
     P = torch.tensor(w["probe"], dtype=torch.complex64, device=dev)
     pos_true = torch.tensor(w["pos"], dtype=torch.float32, device=dev)
@@ -646,6 +648,8 @@ def run_ms256(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     w = synth.workload_multislice256()
+    if args.positions and args.positions < w["J"]:   # profiling runs: the first positions only
+        w["pos"], w["J"] = w["pos"][:args.positions], args.positions
     ms = api.make_multislice(w["S"], w["dz"], w["wavelength"], w["pixel_size"])
     Os_true = torch.tensor(w["slices"], dtype=torch.complex64, device=dev)
     P = torch.tensor(w["probe"], dtype=torch.complex64, device=dev)

@@ -206,8 +206,10 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
   // ---- backward: each mode from the far field back through the slices ---------------
   float2* go_s = a.go_s + slotNN * S;
   float2* h_s = a.h_s + slotNN * M;
+  // modes last to first: the far field and incident waves written last are read
+  // first, while they are still in L2
 #pragma unroll 1
-  for (int k = 0; k < M; ++k) {
+  for (int k = M - 1; k >= 0; --k) {
     const float2* Pk = a.probe + (size_t)k * NN;
     __syncthreads();
     fft2_inverse<N, T>(
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
         const float2 a0 = cmulc(make_float2(i2.x, i2.y), g0), a1 = cmulc(make_float2(i2.z, i2.w), g1);
         float4* gp = (float4*)(go_s + (size_t)s * NN + p);
         gv = make_float4(a0.x, a0.y, a1.x, a1.y);
-        if (k > 0) {
+        if (k < M - 1) {
           const float4 prev = *gp;
           gv = make_float4(gv.x + prev.x, gv.y + prev.y, gv.z + prev.z, gv.w + prev.w);
         }
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
       const float2 a0 = cmulc(make_float2(P2.x, P2.y), g0), a1 = cmulc(make_float2(P2.z, P2.w), g1);
       float4 gv = make_float4(a0.x, a0.y, a1.x, a1.y);
       float4* gp = (float4*)(go_s + p);
-      if (k > 0) {
+      if (k < M - 1) {
         const float4 prev = *gp;
         gv = make_float4(gv.x + prev.x, gv.y + prev.y, gv.z + prev.z, gv.w + prev.w);
       }
