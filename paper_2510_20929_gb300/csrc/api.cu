@@ -884,10 +884,26 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
   cp(dobj, object, HW * 8, cudaMemcpyHostToDevice);
   cp(dprobe, probe, (size_t)d.M * NN * 8, cudaMemcpyHostToDevice);
   cp(dpos, pos, (size_t)d.J * 8, cudaMemcpyHostToDevice);
-  cp(dmeas, meas, (size_t)d.J * NN * 4, cudaMemcpyHostToDevice);
   if (order) cp(dorder, order, (size_t)d.J * 4, cudaMemcpyHostToDevice);
+  // The measured intensities, the bulk of the input: pinned host memory that is
+  // mapped into the device's address space is read in place by the per-position
+  // passes over the host link, so the transfer overlaps the epoch's compute;
+  // other host memory (and the tensor-copy form, which needs device memory) is
+  // staged first.
+  const float* mdev = nullptr;
+  if (opts->precision == PTYCHO_PRECISION_FP32 && d.J > 0) {
+    void* mapped = nullptr;
+    if (cudaHostGetDevicePointer(&mapped, (void*)meas, 0) == cudaSuccess)
+      mdev = (const float*)mapped;
+    else
+      (void)cudaGetLastError();   // not mapped pinned memory: clear the error and stage it
+  }
+  if (!mdev) {
+    cp(dmeas, meas, (size_t)d.J * NN * 4, cudaMemcpyHostToDevice);
+    mdev = dmeas;
+  }
   if (e != cudaSuccess) return PTYCHO_ERR_CUDA;
-  st = run_epoch(d, dobj, dprobe, dpos, dmeas, order ? dorder : nullptr, *opts, dloss, nullptr, ws, s);
+  st = run_epoch(d, dobj, dprobe, dpos, mdev, order ? dorder : nullptr, *opts, dloss, nullptr, ws, s);
   if (st != PTYCHO_OK) return st;
   cp(object, dobj, HW * 8, cudaMemcpyDeviceToHost);
   cp(probe, dprobe, (size_t)d.M * NN * 8, cudaMemcpyDeviceToHost);

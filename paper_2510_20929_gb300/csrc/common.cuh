@@ -183,6 +183,13 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
 }
 
+// Asynchronous prefetch of `bytes` (a multiple of 16) at a 16-byte aligned
+// global address into L2; no-op for a misaligned address.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  if (((uintptr_t)p & 15) == 0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Tile origin and fraction of a probe-centre position; false if the bilinear
 // (N+1)^2 tile is not inside the object or the value is not finite.
 __device__ __forceinline__ bool tile_of(float py, float px, int N, int H, int W, int& ty, int& tx,

@@ -170,6 +170,10 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
     return;
   }
   if (tid == 0 && a.valid) a.valid[slot] = 1;
+  // the measured intensities are first read by the data term, after the forward
+  // transforms: fetch them into L2 meanwhile (they may live in host memory)
+  if (PART == 0 && tid == 0 && a.meas && a.mode != MODE_FWD)
+    prefetch_l2_bulk(a.meas + (size_t)j * N * N, (uint32_t)(N * N * sizeof(float)));
   if (PART == 0) make_twiddles<N>(tw);
 
   const int M = a.M;
