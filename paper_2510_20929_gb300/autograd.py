@@ -31,25 +31,27 @@ from . import api
 
 class FarField(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, obj, probe, pos):
+    def forward(ctx, obj, probe, pos, precision="fp32"):
         obj, probe, pos = obj.contiguous(), probe.contiguous(), pos.contiguous()
         ctx.save_for_backward(obj, probe, pos)
-        return api.forward(obj, probe, pos)
+        ctx.precision = precision
+        return api.forward(obj, probe, pos, precision=precision)
 
     @staticmethod
     def backward(ctx, gI):
         obj, probe, pos = ctx.saved_tensors
         _, gO, gP, gr = api.adjoint(obj, probe, pos, gI.contiguous().to(torch.float32), "vjp",
-                                    batch=256, positions_grad=ctx.needs_input_grad[2])
+                                    batch=256, positions_grad=ctx.needs_input_grad[2], precision=ctx.precision)
         return (gO if ctx.needs_input_grad[0] else None, gP if ctx.needs_input_grad[1] else None,
-                gr if ctx.needs_input_grad[2] else None)
+                gr if ctx.needs_input_grad[2] else None, None)
 
 
 class DataTerm(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, obj, probe, pos, meas, noise="gaussian", eps=1e-9):
+    def forward(ctx, obj, probe, pos, meas, noise="gaussian", eps=1e-9, precision="fp32"):
         obj, probe, pos, meas = obj.contiguous(), probe.contiguous(), pos.contiguous(), meas.contiguous()
-        loss, gO, gP, gr = api.adjoint(obj, probe, pos, meas, noise, eps=eps, batch=256, positions_grad=True)
+        loss, gO, gP, gr = api.adjoint(obj, probe, pos, meas, noise, eps=eps, batch=256, positions_grad=True,
+                                       precision=precision)
         ctx.save_for_backward(gO, gP, gr)
         return loss
 
@@ -58,7 +60,7 @@ class DataTerm(torch.autograd.Function):
         gO, gP, gr = ctx.saved_tensors
         s = gL.to(torch.float32)
         return (gO * s if ctx.needs_input_grad[0] else None, gP * s if ctx.needs_input_grad[1] else None,
-                gr * s if ctx.needs_input_grad[2] else None, None, None, None)
+                gr * s if ctx.needs_input_grad[2] else None, None, None, None, None)
 
 
 class DataTermOPR(torch.autograd.Function):
@@ -130,18 +132,19 @@ def data_term_opr(obj, U, w, P_rest, pos, meas, noise="gaussian", eps=1e-9):
     return DataTermOPR.apply(obj, U, w, P_rest, pos, meas, noise, eps)
 
 
-def far_field(obj, probe, pos):
-    """Predicted intensities, differentiable in object, probe modes and positions."""
-    return FarField.apply(obj, probe, pos)
+def far_field(obj, probe, pos, precision="fp32"):
+    """Predicted intensities, differentiable in object, probe modes and positions
+    (``precision`` "bf16x3": the far field as split-BF16 DFT-GEMMs, windows 32-128)."""
+    return FarField.apply(obj, probe, pos, precision)
 
 
-def data_term(obj, probe, pos, meas, noise="gaussian", eps=1e-9):
+def data_term(obj, probe, pos, meas, noise="gaussian", eps=1e-9, precision="fp32"):
     """Scalar data term (Gaussian amplitude or Poisson), differentiable in object, probe, positions."""
-    return DataTerm.apply(obj, probe, pos, meas, noise, eps)
+    return DataTerm.apply(obj, probe, pos, meas, noise, eps, precision)
 
 
 def reconstruct_adam(obj, probe, pos, meas, epochs=10, lr_object=1e-2, lr_probe=1e-2, lr_pos=1e-1,
-                     noise="gaussian", eps=1e-9, update=("object", "probe", "positions")):
+                     noise="gaussian", eps=1e-9, update=("object", "probe", "positions"), precision="fp32"):
     """Adam on object, probe modes and positions (whole data set per step); returns the loss history.
 
     Learning rates are in the units of each variable (object and probe
@@ -161,7 +164,7 @@ def reconstruct_adam(obj, probe, pos, meas, epochs=10, lr_object=1e-2, lr_probe=
     hist = []
     for _ in range(epochs):
         opt.zero_grad(set_to_none=True)
-        loss = data_term(obj, probe, pos, meas, noise, eps)
+        loss = data_term(obj, probe, pos, meas, noise, eps, precision)
         loss.backward()
         opt.step()
         hist.append(loss.item())

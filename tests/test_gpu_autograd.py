@@ -51,6 +51,30 @@ def test_data_term_gradients_match_oracle():
     assert e[0] < 1e-5 and max(e[1:]) < 1e-4
 
 
+@pytest.mark.parametrize("which", ["far_field", "data_term"])
+def test_split_bf16_autograd_matches_oracle(which):
+    # the same Functions with the far field as split-BF16 DFT-GEMMs (tolerance 1e-3)
+    import torch
+    from paper_2510_20929_gb300.autograd import data_term, far_field
+    p = problem(N=64, M=2, H=150, W=160, J=20, step=12.0)
+    (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
+    for t in (dO, dP, dpos):
+        t.requires_grad_(True)
+    if which == "far_field":
+        wts = np.float32(np.random.default_rng(3).standard_normal((20, 64, 64))).astype(np.float64)
+        (far_field(dO, dP, dpos, precision="bf16x3") * to_dev(wts, torch.float32)).sum().backward()
+        gO, gP, gr = orc.vjp(O, P, pos, wts)
+        e = (0.0,)
+    else:
+        loss = data_term(dO, dP, dpos, dI, "gaussian", 1e-6, precision="bf16x3")
+        loss.backward()
+        L, gO, gP, gr = orc.loss_and_gradients(O, P, pos, I_m, orc.GAUSSIAN, 1e-6)
+        e = (abs(loss.item() - L) / L,)
+    e += (rel(dO.grad.cpu().numpy(), gO), rel(dP.grad.cpu().numpy(), gP), rel(dpos.grad.cpu().numpy(), gr))
+    print(f"{which} split BF16:", e)
+    assert max(e) < 1e-3
+
+
 def test_data_term_matches_finite_differences_on_gpu():
     import torch
     from paper_2510_20929_gb300.autograd import data_term
