@@ -91,6 +91,93 @@ struct FarArgs {
   int* status;
 };
 
+// Exit waves of the split-BF16 form: per position the object tile (rows
+// ty..ty+N, columns xs..xs+N+1 with xs = tx rounded down to an even column,
+// so that the copy starts on a 16-byte boundary) lands in shared memory with
+// one tiled tensor copy; the bilinear patch o_j = S_j(O) (Sec. 2.1, the same
+// weights and expression as the per-position pass) is interpolated from it,
+// and o_j and psi_jk = P_k o_j of every mode go to the scratch.
+template <int N>
+struct ExitTma {
+  static constexpr int T = 512;
+  static constexpr int TW = N + 2, TH = N + 1;   // staged tile: TH rows of TW complex values
+  static constexpr uint32_t TILE_BYTES = (uint32_t)TW * TH * 8;
+  static constexpr size_t tile = 0;
+  static constexpr size_t bar = ((size_t)TILE_BYTES + 127) / 128 * 128;
+  static constexpr size_t wsh = bar + 16;        // eigenmode weights of the position (OPR)
+  static constexpr size_t bytes = wsh + 4 * 8 + 128;   // + alignment of the base to 128 bytes
+};
+
+template <int N, bool OPR>
+__global__ void __launch_bounds__(512, 1) k_exit_tma(BatchArgs a, const __grid_constant__ TmaDesc tm_obj) {
+  using C = ExitTma<N>;
+  constexpr int NN = N * N, T = C::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  wait_prior_grid();
+  unsigned char* smem = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
+  const float2* tile = (const float2*)(smem + C::tile);
+  uint64_t* bar = (uint64_t*)(smem + C::bar);
+  float* wj = (float*)(smem + C::wsh);
+  const int slot = blockIdx.x, tid = threadIdx.x;
+  const int e = a.b0 + slot;
+  const int j = a.order ? a.order[e] : e;
+  int ty = 0, tx = 0;
+  float fy = 0.f, fx = 0.f;
+  bool ok = (j >= 0 && j < a.J);
+  if (ok) ok = tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
+  if (!ok) {
+    if (tid == 0) {
+      atomicOr(a.status, FLAG_BOUNDS);
+      if (a.valid) a.valid[slot] = 0;
+    }
+    return;
+  }
+  const int xs = tx & ~1, d = tx - xs;
+  if (tid == 0) {
+    if (a.valid) a.valid[slot] = 1;
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+    tc::mbar_expect_tx(bar, C::TILE_BYTES);
+    tc::tma_load_2d(smem + C::tile, &tm_obj, xs, ty, bar);
+  }
+  if (OPR && tid < a.K) wj[tid] = a.opr_w[(size_t)j * a.K + tid];
+  __syncthreads();
+  if (!__syncthreads_and(tc::mbar_wait(bar, 0))) {
+    if (tid == 0) atomicOr(a.status, FLAG_TIMEOUT);
+    return;
+  }
+  const int M = a.M;
+  const size_t slotNN = (size_t)slot * NN;
+  float2* o_s = a.o_s ? a.o_s + slotNN : nullptr;
+  float2* psi = a.psi_s + slotNN * M;
+  float2* p0 = (OPR && a.p0_s) ? a.p0_s + slotNN : nullptr;
+  const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
+#pragma unroll 2
+  for (int q = tid; q < NN / 2; q += T) {   // pixel pairs (r, c), (r, c + 1)
+    const int p = 2 * q, r = p / N, c = p % N;
+    const float2* t0 = tile + r * C::TW + c + d;
+    const float2* t1 = t0 + C::TW;
+    const float2 a0 = t0[0], a1 = t0[1], a2 = t0[2], b0 = t1[0], b1 = t1[1], b2 = t1[2];
+    const float2 o0 = make_float2(w00 * a0.x + w01 * a1.x + w10 * b0.x + w11 * b1.x,
+                                  w00 * a0.y + w01 * a1.y + w10 * b0.y + w11 * b1.y);
+    const float2 o1 = make_float2(w00 * a1.x + w01 * a2.x + w10 * b1.x + w11 * b2.x,
+                                  w00 * a1.y + w01 * a2.y + w10 * b1.y + w11 * b2.y);
+    if (o_s) *(float4*)(o_s + p) = make_float4(o0.x, o0.y, o1.x, o1.y);
+    for (int k = 0; k < M; ++k) {
+      const float2* Pk = shared_mode<OPR>(a, k, NN);
+      float4 P2;
+      if (!OPR || Pk) {
+        P2 = __ldg((const float4*)(Pk + p));
+      } else {   // relaxed primary mode of this position
+        P2 = opr_pair(a.opr_U, wj, a.K, NN, p);
+        if (p0) *(float4*)(p0 + p) = P2;
+      }
+      const float2 x0 = cmul(make_float2(P2.x, P2.y), o0), x1 = cmul(make_float2(P2.z, P2.w), o1);
+      *(float4*)(psi + (size_t)k * NN + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+    }
+  }
+}
+
 __device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ float bf16_value(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
 // x = hi + lo + O(2^-18 |x|)

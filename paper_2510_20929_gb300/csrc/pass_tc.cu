@@ -61,8 +61,42 @@ cudaError_t launch_dft_planes(void* dft, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Tensor map of the object as 8-byte elements [H][W], tiles of (N + 1) rows
+// x (N + 2) elements, no swizzle; needs W even and a 16-byte aligned base.
+static bool encode_object(TmaDesc* out, const void* base, int H, int W, int N) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tmap_encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[1] = {(cuuint64_t)W * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)(N + 2), (cuuint32_t)(N + 1)};
+  const cuuint32_t es[2] = {1, 1};
+  CUtensorMap m;
+  if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, const_cast<void*>(base), dims, strides, box, es,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  memcpy(out, &m, sizeof(m));
+  return true;
+}
+
+template <int N, bool OPR>
+static cudaError_t launch_exit_tma(const BatchArgs& a, const TmaDesc& t, cudaStream_t s) {
+  using C = ExitTma<N>;
+  static unsigned long long done = 0;
+  cudaError_t e = smem_optin(k_exit_tma<N, OPR>, C::bytes, &done);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_exit_tma<N, OPR>, dim3(a.nb), dim3(C::T), C::bytes, s, a, t);
+}
+
 template <int N>
 cudaError_t launch_pass1_part(const BatchArgs& a, cudaStream_t s, int part) {
+  if (part == 1 && a.nb > 0 && ((uintptr_t)a.obj & 15) == 0 && a.W % 2 == 0) {
+    // the exit waves from object tiles staged by tensor copies (rows of 8-byte
+    // elements need a 16-byte row pitch: even widths only)
+    TmaDesc t;
+    if (!encode_object(&t, a.obj, a.H, a.W, N)) return cudaErrorInvalidValue;
+    return a.opr_U ? launch_exit_tma<N, true>(a, t, s) : launch_exit_tma<N, false>(a, t, s);
+  }
   constexpr int T = Threads<N>::T;
   if (a.opr_U) return part == 1 ? launch_pass1_t<N, T, true, 1>(a, s) : launch_pass1_t<N, T, true, 2>(a, s);
   return part == 1 ? launch_pass1_t<N, T, false, 1>(a, s) : launch_pass1_t<N, T, false, 2>(a, s);

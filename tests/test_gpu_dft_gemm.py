@@ -50,6 +50,22 @@ def test_forward_bf16x3_matches_oracle(N, M, H, W, J, step):
         assert rel(I[j], ref[j]) < TOL_BF16
 
 
+@pytest.mark.parametrize("W", [151, 152])
+def test_bf16x3_exit_waves_on_odd_and_even_object_widths(W):
+    # even widths stage the object tile with one tensor copy; odd widths (a row
+    # pitch that is not a multiple of 16 bytes) take the per-pixel gather
+    from paper_2510_20929_gb300 import api
+    p = problem(N=64, M=2, H=160, W=W, J=20, step=12.0)
+    (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
+    e_fwd = rel(api.forward(dO, dP, dpos, precision="bf16x3", batch=7).cpu().numpy(), orc.forward(O, P, pos))
+    L, gO, gP, gr = orc.loss_and_gradients(O, P, pos, I_m, orc.GAUSSIAN, 1e-6)
+    loss, dgO, dgP, dgr = api.adjoint(dO, dP, dpos, dI, "gaussian", eps=1e-6, batch=7, precision="bf16x3")
+    e = (e_fwd, abs(loss.item() - L) / L, rel(dgO.cpu().numpy(), gO), rel(dgP.cpu().numpy(), gP),
+         rel(dgr.cpu().numpy(), gr))
+    print(f"bf16x3 W={W}:", " ".join(f"{x:.2e}" for x in e))
+    assert max(e) < TOL_BF16
+
+
 @pytest.mark.parametrize("noise", ["gaussian", "poisson"])
 @pytest.mark.parametrize("N,M,H,W,J,step", [CASES[0], CASES[2], CASES[4]])
 def test_gradients_bf16x3_match_oracle(noise, N, M, H, W, J, step):
