@@ -16,9 +16,12 @@
 // products on separate re/im planes, the sign of the Fi terms chosen by the
 // instruction descriptor's negate-A bit.
 //
+// k_exit_tma (below) writes the exit waves psi_jk of a minibatch to the
+// scratch from object tiles staged by tensor copies (objects of odd width go
+// through the first part of the per-position pass instead).
+//
 // k_far_tc: per minibatch position (persistent CTAs): the exit waves psi_jk
-// (written by the first part of the per-position pass) are transformed mode
-// by mode; the far fields overwrite them in the scratch and their intensities
+// are transformed mode by mode; the far fields overwrite them in the scratch and their intensities
 // accumulate per thread; the data term (Eq. 1 amplitude loss or the Poisson
 // likelihood) gives the loss and the far-field factor; every mode is then
 // scaled and transformed back, and chi_jk = F^-1[(rho - 1) Psi_jk] overwrites
