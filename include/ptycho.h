@@ -100,9 +100,10 @@ typedef struct {
  * hi + lo parts and three products per real product (hi*hi + lo*hi + hi*lo);
  * windows N = 32, 64 and 128 (others: PTYCHO_ERR_UNSUPPORTED), the shared
  * probe only (the relaxed-probe and multislice entry points take FP32); the
- * measured-intensity array must be 16-byte aligned (else PTYCHO_ERR_ARG). Its
- * per-element error against exact arithmetic is about 2^-17 of the operand
- * magnitudes, accumulated over N terms per pass. */
+ * measured-intensity array must be 16-byte aligned (else PTYCHO_ERR_ARG). Each
+ * operand is represented to within 2^-16 of its magnitude (about 2^-17
+ * typically), and the dropped lo*lo term is of the same order; the transform's
+ * norm-wise error is near 1e-5. */
 #define PTYCHO_PRECISION_FP32 0
 #define PTYCHO_PRECISION_BF16X3 1
 

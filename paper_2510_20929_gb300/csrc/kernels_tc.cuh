@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(512, 1) k_exit_tma(BatchArgs a, const __grid_c
 
 __device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ float bf16_value(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
-// x = hi + lo + O(2^-18 |x|)
+// x = hi + lo to within 2^-16 |x| (BF16 keeps 8 significant bits)
 __device__ __forceinline__ void split_bf16(float v, uint16_t& hi, uint16_t& lo) {
   hi = bf16_bits(v);
   lo = bf16_bits(v - bf16_value(hi));

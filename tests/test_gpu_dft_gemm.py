@@ -3,8 +3,8 @@ tcgen05 tensor cores) through the C ABI against the FP64 oracle, on the same
 seeded inputs as the FP32 parity tests.
 
 Tolerance: each operand is carried as hi + lo BF16 parts, so an element is
-represented to about 2^-17 of its magnitude and the dropped lo*lo product is
-of the same order; with FP32 accumulation over the N terms of each of the two
+represented to within 2^-16 of its magnitude (about 2^-17 typically) and the
+dropped lo*lo product is of the same order; with FP32 accumulation over the N terms of each of the two
 passes the transform's norm-wise error stays near 1e-5. TOL_BF16 = 1e-3 is
 the bound the path is specified to (split BF16 on exit waves and gradients);
 the measured errors are printed."""
