@@ -198,3 +198,47 @@ def test_bf16x3_batched_reconstructions_equal_their_single_epochs():
     for (o, pr, *_), (O1, P1, L1), L in zip(batch, single, losses):
         assert rel(o.cpu().numpy(), O1) < 1e-5 and rel(pr.cpu().numpy(), P1) < 1e-5
         assert abs(L - L1) <= 1e-5 * abs(L1)
+
+
+def test_bf16x3_empty_inputs_leave_everything_untouched():
+    import torch
+    from paper_2510_20929_gb300 import api
+    p = problem(N=32, M=2, H=72, W=76, J=4, step=6.0)
+    _, (dO, dP, dpos, dI) = _dev(p)
+    pos0 = dpos[:0].contiguous()
+    assert api.forward(dO, dP, pos0, precision="bf16x3").shape == (0, 32, 32)
+    loss, gO, gP, gr = api.adjoint(dO, dP, pos0, dI[:0].contiguous(), "gaussian", precision="bf16x3")
+    assert loss.item() == 0.0 and gO.abs().max().item() == 0.0 and gP.abs().max().item() == 0.0
+    O0, P0 = dO.clone(), dP.clone()
+    loss, _ = api.lsqml_epoch(dO, dP, pos0, dI[:0].contiguous(), None, batch=4, precision="bf16x3")
+    assert loss.item() == 0.0 and torch.equal(dO, O0) and torch.equal(dP, P0)
+
+
+@pytest.mark.parametrize("batch", [1, 100])
+def test_bf16x3_one_position_and_whole_set_minibatches(batch):
+    import torch
+    from paper_2510_20929_gb300 import api
+    p = problem(N=32, M=2, H=72, W=76, J=9, step=6.0)
+    (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
+    order = np.random.default_rng(5).permutation(9).astype(np.int32)
+    kw = dict(batch=batch, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6)
+    O1, P1, L1, a1 = orc.lsqml_epoch(O, P, pos, I_m, order, orc.LsqmlOptions(**kw))
+    loss, alpha = api.lsqml_epoch(dO, dP, dpos, dI, to_dev(order, torch.int32), want_alpha=True,
+                                  precision="bf16x3", **kw)
+    e = (rel(dO.cpu().numpy(), O1), rel(dP.cpu().numpy(), P1), rel(alpha.cpu().numpy(), a1))
+    print(f"bf16x3 batch {batch}:", e)
+    assert max(e) < TOL_BF16
+
+
+def test_bf16x3_sixteen_modes():
+    # the largest mode count: intensities summed over 16 modes, gradients of every mode
+    from paper_2510_20929_gb300 import api
+    p = problem(N=32, M=16, H=72, W=76, J=8, step=6.0)
+    (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
+    e_fwd = rel(api.forward(dO, dP, dpos, precision="bf16x3").cpu().numpy(), orc.forward(O, P, pos))
+    L, gO, gP, gr = orc.loss_and_gradients(O, P, pos, I_m, orc.POISSON, 1e-6)
+    loss, dgO, dgP, dgr = api.adjoint(dO, dP, dpos, dI, "poisson", eps=1e-6, batch=3, precision="bf16x3")
+    e = (e_fwd, abs(loss.item() - L) / abs(L), rel(dgO.cpu().numpy(), gO), rel(dgP.cpu().numpy(), gP),
+         rel(dgr.cpu().numpy(), gr))
+    print("bf16x3 16 modes:", " ".join(f"{x:.2e}" for x in e))
+    assert max(e) < TOL_BF16
