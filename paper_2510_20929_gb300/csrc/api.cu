@@ -327,6 +327,7 @@ cudaError_t pass1(int N, const BatchArgs& a, cudaStream_t s, int variant) {
     return dispatch_N(N, [&](auto c) { return launch_pass1<decltype(c)::value>(a, s, variant); });
   });
 }
+
 bool dft_gemm_supported(int N) { return N == 32 || N == 64 || N == 128; }
 
 ptycho_status check_precision(int N, int precision, const void* meas) {
