@@ -156,10 +156,17 @@ ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const
                              int32_t batch, float* g_object, float* g_probe, float* g_pos,
                              double* loss, void* ws, size_t ws_bytes, void* stream);
 
-/* ptycho_forward and ptycho_adjoint with the far-field precision chosen
- * (PTYCHO_PRECISION_*). The forward form processes positions in chunks of
- * `batch` and then needs ptycho_workspace_bytes(dims, batch) of workspace
- * (with FP32 the header suffices, as for ptycho_forward). */
+/* ptycho_forward (Sec. 2.1, Eq. 4) and ptycho_adjoint (Eq. 1-2) with the
+ * far-field precision chosen (PTYCHO_PRECISION_*); every other argument has
+ * the meaning, layout and ownership given above, and the same synchronous
+ * argument checks and device status apply. precision other than FP32 and
+ * BF16X3 is PTYCHO_ERR_ARG; BF16X3 on a window other than 32, 64 or 128 is
+ * PTYCHO_ERR_UNSUPPORTED, and with `meas` not 16-byte aligned PTYCHO_ERR_ARG.
+ * The forward form processes positions in chunks of `batch` (>= 1) and with
+ * BF16X3 needs ptycho_workspace_bytes(dims, batch) of workspace (with FP32
+ * the header suffices, as for ptycho_forward). A bounded wait of the
+ * tensor-core kernel that gives up is reported as PTYCHO_ERR_TIMEOUT by
+ * ptycho_status_read. */
 ptycho_status ptycho_forward_ex(const ptycho_dims* dims, int32_t precision, int32_t batch,
                                 const float* object, const float* probe, const float* pos,
                                 float* I_pred, void* ws, size_t ws_bytes, void* stream);
