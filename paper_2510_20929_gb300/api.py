@@ -274,7 +274,8 @@ def adjoint(obj, probe, pos, meas, noise="gaussian", eps: float = 0.0, batch: in
     """Loss and gradients (grad = 2 dL/dz*): returns (loss, g_object, g_probe, g_pos).
 
     ``noise`` is "gaussian", "poisson", or "vjp" (then ``meas`` holds dL/dI and
-    the returned loss is None).
+    the returned loss is None). ``precision`` "bf16x3" evaluates the far field as
+    split-BF16 DFT-GEMMs on the tensor cores (windows 32, 64, 128).
     """
     nz = _NOISE[noise] if isinstance(noise, str) else int(noise)
     _need(obj, "object", torch.complex64)
@@ -317,6 +318,9 @@ def make_opts(noise="gaussian", batch: int = 256, delta_o: float = 0.1, delta_p:
               update_probe: bool = True, graph: bool = False, autotune: bool = False,
               update_positions: bool = False, pos_step: float = 1.0, pos_max_shift: float = 1.0,
               object_per_epoch: bool = False, precision="fp32") -> LsqmlOpts:
+    """LSQML epoch options (the fields of ptycho_lsqml_opts). ``precision``:
+    "fp32" (shared-memory FFTs) or "bf16x3" (split-BF16 DFT-GEMMs on the tensor
+    cores, windows 32, 64, 128)."""
     o = LsqmlOpts()
     o.flags = (FLAG_GRAPH if graph else 0) | (FLAG_AUTOTUNE if autotune else 0)
     o.noise = _NOISE[noise] if isinstance(noise, str) else int(noise)
