@@ -396,6 +396,14 @@ ptycho_status ptycho_sampler_order(const float* pos, int32_t J, int32_t batch, i
  * PTYCHO_ERR_CUDA. */
 ptycho_status ptycho_status_read(void* ws, void* stream);
 
+/* Diagnostic of the bounded waits: launches on `stream` one kernel whose
+ * mbarrier wait cannot complete; the wait gives up after about 2^26 SM clock
+ * cycles (tens of milliseconds) and records the timeout in the workspace
+ * status, which the next ptycho_status_read() returns as PTYCHO_ERR_TIMEOUT.
+ * The GPU context stays usable. ws as for the other entry points (header
+ * size at least). */
+ptycho_status ptycho_selftest_wait_timeout(void* ws, size_t ws_bytes, void* stream);
+
 /* Static description of a status code. */
 const char* ptycho_status_string(ptycho_status status);
 

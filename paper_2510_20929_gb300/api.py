@@ -128,6 +128,7 @@ def lib() -> ctypes.CDLL:
             "ptycho_lsqml_epoch_batched": (ctypes.c_int, [ctypes.c_int32, dims_p, _P, _P, _P, _P, _P, opts_p, _P,
                                                           _P, ctypes.c_size_t, _P]),
             "ptycho_status_read": (ctypes.c_int, [_P, _P]),
+            "ptycho_selftest_wait_timeout": (ctypes.c_int, [_P, ctypes.c_size_t, _P]),
             "ptycho_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "ptycho_version": (ctypes.c_char_p, []),
             "ptycho_profile_enable": (ctypes.c_int, [ctypes.c_int32]),

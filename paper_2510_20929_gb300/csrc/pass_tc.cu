@@ -10,6 +10,7 @@
 #include "kernels.cuh"
 #include "kernels_tc.cuh"
 #include "launch.h"
+#include "ptycho.h"
 
 namespace ptycho {
 
@@ -130,6 +131,20 @@ cudaError_t launch_far_tc(const BatchArgs& b, const void* dft, cudaStream_t s) {
   return launch_pdl(k_far_tc<N>, dim3(grid), dim3(C::T), C::bytes, s, a, tpsi, tmeas);
 }
 
+// Diagnostic: one warp waits (bounded, about 2^26 SM cycles) on an mbarrier
+// that nothing arrives on, then records the timeout status as the tensor-core
+// kernels do when a wait gives up.
+__global__ void k_selftest_wait(int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  const bool done = tc::mbar_wait(&bar, 0, 1ll << 26);
+  if (threadIdx.x == 0 && !done) atomicOr(status, FLAG_TIMEOUT);
+}
+
 #define PTYCHO_TC_INSTANCES(N)                                                     \
   template size_t dft_plane_bytes<N>();                                           \
   template cudaError_t launch_dft_planes<N>(void*, cudaStream_t);                 \
@@ -140,3 +155,9 @@ PTYCHO_TC_INSTANCES(64)
 PTYCHO_TC_INSTANCES(128)
 
 }  // namespace ptycho
+
+extern "C" ptycho_status ptycho_selftest_wait_timeout(void* ws, size_t ws_bytes, void* stream) {
+  if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < sizeof(ptycho::WsHeader)) return PTYCHO_ERR_WORKSPACE;
+  ptycho::k_selftest_wait<<<1, 32, 0, (cudaStream_t)stream>>>(&((ptycho::WsHeader*)ws)->status);
+  return cudaGetLastError() == cudaSuccess ? PTYCHO_OK : PTYCHO_ERR_CUDA;
+}

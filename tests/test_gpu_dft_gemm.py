@@ -242,3 +242,18 @@ def test_bf16x3_sixteen_modes():
          rel(dgr.cpu().numpy(), gr))
     print("bf16x3 16 modes:", " ".join(f"{x:.2e}" for x in e))
     assert max(e) < TOL_BF16
+
+
+def test_bounded_wait_reports_timeout_and_the_context_stays_usable():
+    # a wait that can never complete gives up, the status reads TIMEOUT, and work runs on
+    from paper_2510_20929_gb300 import api
+    p = problem(N=32, M=2, H=72, W=76, J=6, step=6.0)
+    (O, P, pos, _), (dO, dP, dpos, _) = _dev(p)
+    d = api.dims_of(dO, dP, dpos)
+    ws = api.workspace(d, 4, dO.device)
+    ws.status()                                   # clear
+    assert api.lib().ptycho_selftest_wait_timeout(api._P(ws.ptr), ws.nbytes, api._stream()) == 0
+    assert ws.status() == 5                       # PTYCHO_ERR_TIMEOUT
+    assert ws.status() == 0                       # read clears it
+    I = api.forward(dO, dP, dpos, precision="bf16x3", batch=4).cpu().numpy()
+    assert rel(I, orc.forward(O, P, pos)) < TOL_BF16
