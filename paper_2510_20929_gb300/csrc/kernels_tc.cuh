@@ -73,6 +73,10 @@ struct FarTc {
   static constexpr size_t bytes = misc + 16 + 1024;             // + alignment of the base to 1024 bytes
   static constexpr uint32_t COLS = 4 * N;                    // buffer A [0, 2N), buffer B [2N, 4N)
   static constexpr size_t dft_bytes = (size_t)NCH * CHUNK;
+  static_assert(bytes <= 232448, "shared memory per CTA");
+  static_assert(COLS >= 32 && COLS <= 512 && (COLS & (COLS - 1)) == 0, "TMEM allocation: a power of two <= 512");
+  static_assert(sring % 1024 == 0 && SSLOT % 1024 == 0, "128-byte swizzled tiles need 1024-byte alignment");
+  static_assert(CHUNK % 16 == 0 && SLICE % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
 
 // An encoded tensor map (CUtensorMap), passed by value as a kernel parameter.
@@ -109,6 +113,9 @@ struct ExitTma {
   static constexpr size_t bar = ((size_t)TILE_BYTES + 127) / 128 * 128;
   static constexpr size_t wsh = bar + 16;        // eigenmode weights of the position (OPR)
   static constexpr size_t bytes = wsh + 4 * 8 + 128;   // + alignment of the base to 128 bytes
+  static_assert(TW <= 256 && TH <= 256, "tensor-copy box dimensions");
+  static_assert((TW * 8) % 16 == 0, "tensor-copy box rows are multiples of 16 bytes");
+  static_assert(bytes <= 232448, "shared memory per CTA");
 };
 
 template <int N, bool OPR>
