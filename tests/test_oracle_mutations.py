@@ -4,6 +4,9 @@ Every case monkeypatches one oracle function with a subtly wrong variant (a
 dropped normalisation, transposed fractions, a flipped sign, a missing
 conjugate) and re-runs a pin from test_oracle_pins; the pin must fail.
 """
+import inspect
+import textwrap
+
 import numpy as np
 import pytest
 
@@ -14,6 +17,16 @@ from tests import test_oracle_pins as pins
 def _fails(fn, *args):
     with pytest.raises(AssertionError):
         fn(*args)
+
+
+def _rewritten(fn, old, new):
+    """`fn` recompiled with the source fragment `old` replaced by `new` (exactly
+    one occurrence), resolving names in a copy of the oracle module's globals."""
+    src = textwrap.dedent(inspect.getsource(fn))
+    assert src.count(old) == 1, old
+    ns = dict(fn.__globals__)
+    exec(compile(src.replace(old, new), "<planted mistake>", "exec"), ns)
+    return ns[fn.__name__]
 
 
 def test_missing_fft_normalisation_is_caught(monkeypatch):
@@ -97,3 +110,36 @@ def test_propagator_of_the_wrong_handedness_is_caught(monkeypatch):
     real = orc.asm_propagator
     monkeypatch.setattr(orc, "asm_propagator", lambda *a: np.conj(real(*a)))
     _fails(pins.test_asm_propagator_properties)
+
+
+def test_poisson_full_likelihood_step_is_caught(monkeypatch):
+    real = orc.modulus_ratio
+
+    def full_step(I, Im, n, e):
+        if n == orc.POISSON:
+            return Im / (I + e)
+        return real(I, Im, n, e)
+
+    monkeypatch.setattr(orc, "modulus_ratio", full_step)
+    _fails(pins.test_lsqml_accumulators_are_fixed_multiples_of_the_finite_difference_gradients,
+           orc.POISSON, -0.25)
+
+
+def test_probe_direction_without_the_object_conjugate_is_caught(monkeypatch):
+    wrong = _rewritten(orc.lsqml_batch, "dP_acc += np.conj(o)[None] * chi", "dP_acc += o[None] * chi")
+    monkeypatch.setattr(orc, "lsqml_batch", wrong)
+    _fails(pins.test_lsqml_accumulators_are_fixed_multiples_of_the_finite_difference_gradients,
+           orc.GAUSSIAN, -0.5)
+    _fails(pins.test_probe_only_update_has_the_closed_form_of_a_known_object, 1)
+
+
+def test_probe_step_summed_instead_of_averaged_is_caught(monkeypatch):
+    wrong = _rewritten(orc.lsqml_batch, "float(np.mean(alpha[:, 1]))", "float(np.sum(alpha[:, 1]))")
+    monkeypatch.setattr(orc, "lsqml_batch", wrong)
+    _fails(pins.test_probe_only_update_has_the_closed_form_of_a_known_object, 2)
+
+
+def test_probe_damping_from_the_illumination_is_caught(monkeypatch):
+    wrong = _rewritten(orc.lsqml_batch, "opts.delta_p * float(np.max(Dp))", "opts.delta_p * float(np.max(illum))")
+    monkeypatch.setattr(orc, "lsqml_batch", wrong)
+    _fails(pins.test_probe_only_update_has_the_closed_form_of_a_known_object, 1)

@@ -583,3 +583,68 @@ def test_multislice_gradients_match_central_finite_differences():
     dr = g.standard_normal(pos.shape) * 0.1
     fd = (L_at(Os, P, pos + h * dr) - L_at(Os, P, pos - h * dr)) / (2 * h)
     assert abs(fd - np.sum(gr * dr)) < 1e-5 * abs(fd)
+
+
+# --------------------------------------------------------------------------- exit-wave step and probe direction
+@pytest.mark.parametrize("noise,factor", [(orc.GAUSSIAN, -0.5), (orc.POISSON, -0.25)])
+def test_lsqml_accumulators_are_fixed_multiples_of_the_finite_difference_gradients(noise, factor):
+    # The LSQML accumulators are the exit-wave changes back-projected onto the
+    # object (sum_k conj(P_k) chi_k) and onto the probe (conj(o) chi_k); their
+    # ratio to the loss gradient is fixed by the data term (Sec. 2.2):
+    #   Gaussian (Eq. 2): psi' - psi = F^-1[(rho - 1) Psi] with rho = sqrt(I_m)/sqrt(I + eps),
+    #     and 2 dL/dpsi* = F^-1[2 (1 - rho) Psi]: chi = -1/2 grad;
+    #   Poisson, half a likelihood step (rho - 1 = (I_m/(I + eps) - 1)/2) against
+    #     2 dL/dpsi* = F^-1[2 (1 - I_m/(I + eps)) Psi]: chi = -1/4 grad.
+    # The gradients are pinned by central finite differences, so a wrong step
+    # length or a missing conjugate in either accumulator fails here.
+    O, P, pos, I_m = _fd_problem(noise, seed=14)
+    opts = orc.LsqmlOptions(noise=noise, batch=4, eps=1e-3)
+    rec = {}
+    orc.lsqml_batch(O, P, pos, I_m, range(4), opts, rec)
+    _, gO, gP, _ = orc.loss_and_gradients(O, P, pos, I_m, noise, 1e-3)
+    assert np.max(np.abs(rec["dO_acc"] - factor * gO)) < 1e-10 * np.max(np.abs(gO))
+    assert np.max(np.abs(rec["dP_acc"] - factor * gP)) < 1e-10 * np.max(np.abs(gP))
+
+
+def _probe_step_problem(n_pos):
+    g = np.random.default_rng(15)
+    N, H, W = 16, 40, 40
+    P_true = synth.hg_probe(N, np.array([1.0, 0.5]), waist=N / 5.0, quad_phase=0.03) * 3.0
+    O = synth.make_object(H, W, 4, phase_sigma=1.0)
+    pos = np.array([[12.0, 13.0], [27.0, 26.0]])[:n_pos]     # integer, non-overlapping tiles
+    I_m = orc.forward(O, P_true, pos)
+    P = P_true * (1 + 0.2 * crandn(g, *P_true.shape))
+    return N, O, P, pos, I_m
+
+
+@pytest.mark.parametrize("n_pos", [1, 2])
+def test_probe_only_update_has_the_closed_form_of_a_known_object(n_pos):
+    # Object known and held (update_object False), lam = 0: the object step
+    # vanishes and each alpha_P,j is the 1x1 solve Re<v_j, chi_j> / ||v_j||^2
+    # with v_jk = o_j dP_k; the probe moves by mean_j(alpha_P,j) dP_k with
+    # dP_k = sum_j conj(o_j) chi_jk / (sum_j |o_j|^2 + delta_p max(...)).
+    # Written out on the crops with numpy's FFT, without S_j or the batch code.
+    N, O, P, pos, I_m = _probe_step_problem(n_pos)
+    dp = 5e-2
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=n_pos, delta_p=dp, lam=0.0, eps=0.0,
+                            update_object=False)
+    O_new, P_new, _, alpha = orc.lsqml_batch(O, P, pos, I_m, range(n_pos), opts)
+    crops, chis = [], []
+    for j in range(n_pos):
+        ty, tx = int(pos[j, 0]) - N // 2, int(pos[j, 1]) - N // 2
+        o = O[ty:ty + N, tx:tx + N]
+        Psi = np.fft.fft2(P * o[None]) / N
+        I = np.sum(np.abs(Psi) ** 2, axis=0)
+        chi = np.fft.ifft2(Psi * np.sqrt(I_m[j] / I)[None]) * N - P * o[None]
+        crops.append(o)
+        chis.append(chi)
+    Dp = sum(np.abs(o) ** 2 for o in crops)
+    d = sum(np.conj(o)[None] * c for o, c in zip(crops, chis)) / (Dp + dp * Dp.max())[None]
+    a = []
+    for o, c in zip(crops, chis):
+        v = o[None] * d
+        a.append(np.real(np.vdot(v, c)) / np.real(np.vdot(v, v)))
+    ref = P + np.mean(a) * d
+    assert np.allclose(alpha[:, 1], a, rtol=1e-10, atol=0) and np.all(alpha[:, 0] == 0.0)
+    assert np.max(np.abs(P_new - ref)) < 1e-12 * np.max(np.abs(P))
+    assert np.array_equal(O_new, O)
