@@ -34,7 +34,27 @@ METRIC = "patterns/s per LSQML epoch (fwd+adjoint) vs plain FP32 at matched erro
 UNIT = "patterns/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-SMS, FP32_LANES, MAX_SM_GHZ = 152, 128, 2.07   # FP32 ALU peak = SMs * lanes * 2 flop * clock
+FP32_LANES = 128   # FP32 lanes per SM; the ALU peak is SMs x lanes x 2 flop x the maximum SM clock
+
+
+def alu_peak(dev):
+    """Derived FP32 ALU peak (TFLOP/s) of `dev`: its SM count (queried) x 128
+    lanes x 2 flop x its maximum SM clock (nvidia-smi's clocks.max.sm, else the
+    measured maximum in MEASURED_PEAKS.json, else 2.07 GHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    ghz, src = None, None
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(dev.index or 0), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        ghz, src = float(out.stdout.strip().splitlines()[0]) / 1e3, "nvidia-smi clocks.max.sm"
+    except Exception:
+        try:
+            with open(PEAKS_FILE) as f:
+                ghz, src = float(json.load(f)["sm_max_mhz"]) / 1e3, "MEASURED_PEAKS sm_max_mhz"
+        except Exception:
+            ghz, src = 2.07, "nominal"
+    return sms * FP32_LANES * 2 * ghz * 1e-3, f"{sms} SM x {FP32_LANES} FP32 lanes x 2 flop x {ghz:.3f} GHz ({src}; derived)"
 
 
 def parse():
@@ -154,12 +174,13 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = None
 
     def start(self):
+        import tempfile
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix=f"ptycho_clocks_rank{self.index}_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
@@ -177,7 +198,13 @@ class Clocks:
         self.f.close()
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as f:
+            lines = f.readlines()
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -389,7 +416,7 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the dominant kernel (its launches timed live in the timed region)
     dom_n, dom_ms = live.get(dom_name, (0, 0.0))
     hbm, hbm_src = peaks()
-    alu_tflops = SMS * FP32_LANES * 2 * MAX_SM_GHZ * 1e-3
+    alu_tflops, alu_src = alu_peak(dev)
     if dom_name == "k_pass1":
         flops, nbytes = pass1_work(N, M, B)
         avg_s = dom_ms / dom_n * 1e-3
@@ -403,7 +430,7 @@ def run_ours(args, rank, world, local_rank):
         if alu_ach / alu_tflops >= hbm_ach / hbm:
             roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_tflops, "unit": "TFLOP/s",
                     "frac": alu_ach / alu_tflops, "traffic": None,
-                    "peak_source": "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)"}
+                    "peak_source": alu_src}
         else:
             roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm, "unit": "GB/s",
                     "frac": hbm_ach / hbm, "traffic": None, "peak_source": hbm_src}

@@ -150,7 +150,10 @@ ptycho_status ptycho_forward(const ptycho_dims* dims, const float* object, const
  * result; zero them first for a plain evaluation:
  *   g_object complex64 [H, W], g_probe complex64 [M, N, N],
  *   g_pos float32 [J, 2] (may be NULL), loss float64 scalar (may be NULL;
- *   untouched for VJP). Positions are processed in chunks of `batch`. */
+ *   untouched for VJP). Positions are processed in chunks of `batch`.
+ * With g_object, g_probe and g_pos all NULL (GAUSSIAN or POISSON, `loss`
+ * given) only the forward model and the data term run: the loss alone, at
+ * about half the cost (no back-propagation). */
 ptycho_status ptycho_adjoint(const ptycho_dims* dims, const float* object, const float* probe,
                              const float* pos, const float* meas, int32_t noise, double eps,
                              int32_t batch, float* g_object, float* g_probe, float* g_pos,
@@ -247,9 +250,14 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
  * no counterpart: this is an interface for embedding the library.
  * - Returns PTYCHO_ERR_TOO_LARGE, before touching the device, when
  *   ptycho_workspace_bytes_opts(dims, opts) exceeds PTYCHO_STATIC_WS_BYTES.
+ * - Argument errors return the statuses ptycho_lsqml_epoch returns for the
+ *   same arguments. PTYCHO_FLAG_GRAPH in opts->flags is ignored: the epoch
+ *   runs as eager launches (an executable graph would make the driver
+ *   allocate).
  * - The first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make it before any stream
- *   capture.
+ *   (cudaGetSymbolAddress) with that device current, and so does the first
+ *   call after that device's CUDA context was destroyed and created again;
+ *   make that call before any stream capture.
  * - All calls share the one array per device: calls whose work overlaps on the
  *   GPU (other streams, other host threads) race and must be serialised by
  *   the caller.

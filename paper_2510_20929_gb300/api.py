@@ -271,12 +271,14 @@ def forward(obj, probe, pos, *, precision="fp32", batch: int = 256, check: bool 
 
 
 def adjoint(obj, probe, pos, meas, noise="gaussian", eps: float = 0.0, batch: int = 256, *,
-            positions_grad: bool = True, precision="fp32", check: bool = True):
+            positions_grad: bool = True, precision="fp32", check: bool = True, gradients: bool = True):
     """Loss and gradients (grad = 2 dL/dz*): returns (loss, g_object, g_probe, g_pos).
 
     ``noise`` is "gaussian", "poisson", or "vjp" (then ``meas`` holds dL/dI and
     the returned loss is None). ``precision`` "bf16x3" evaluates the far field as
-    split-BF16 DFT-GEMMs on the tensor cores (windows 32, 64, 128).
+    split-BF16 DFT-GEMMs on the tensor cores (windows 32, 64, 128). With
+    ``gradients=False`` only the loss is evaluated (forward model and data
+    term, no back-propagation) and the three gradients are None.
     """
     nz = _NOISE[noise] if isinstance(noise, str) else int(noise)
     _need(obj, "object", torch.complex64)
@@ -284,10 +286,12 @@ def adjoint(obj, probe, pos, meas, noise="gaussian", eps: float = 0.0, batch: in
     _need(pos, "positions", torch.float32, device=obj.device)
     d = dims_of(obj, probe, pos)
     _need(meas, "meas", torch.float32, (d.J, d.N, d.N), device=obj.device)
+    if not gradients and nz == VJP:
+        raise ValueError("the vjp mode has no loss to evaluate without gradients")
     B = max(1, min(int(batch), max(d.J, 1)))
-    gO = torch.zeros_like(obj)
-    gP = torch.zeros_like(probe)
-    gr = torch.zeros((d.J, 2), dtype=torch.float32, device=obj.device) if positions_grad else None
+    gO = torch.zeros_like(obj) if gradients else None
+    gP = torch.zeros_like(probe) if gradients else None
+    gr = torch.zeros((d.J, 2), dtype=torch.float32, device=obj.device) if (positions_grad and gradients) else None
     loss = torch.zeros((), dtype=torch.float64, device=obj.device)
     ws = workspace(d, B, obj.device)
     _check(lib().ptycho_adjoint_ex(ctypes.byref(d), _precision(precision), _ptr(obj), _ptr(probe), _ptr(pos),

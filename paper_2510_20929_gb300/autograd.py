@@ -50,8 +50,13 @@ class DataTerm(torch.autograd.Function):
     @staticmethod
     def forward(ctx, obj, probe, pos, meas, noise="gaussian", eps=1e-9, precision="fp32"):
         obj, probe, pos, meas = obj.contiguous(), probe.contiguous(), pos.contiguous(), meas.contiguous()
-        loss, gO, gP, gr = api.adjoint(obj, probe, pos, meas, noise, eps=eps, batch=256, positions_grad=True,
-                                       precision=precision)
+        if not (torch.is_grad_enabled() and any(ctx.needs_input_grad[:3])):
+            # a loss evaluation only: forward model and data term, no back-propagation
+            loss, _, _, _ = api.adjoint(obj, probe, pos, meas, noise, eps=eps, batch=256, precision=precision,
+                                        gradients=False)
+            return loss
+        loss, gO, gP, gr = api.adjoint(obj, probe, pos, meas, noise, eps=eps, batch=256,
+                                       positions_grad=ctx.needs_input_grad[2], precision=precision)
         ctx.save_for_backward(gO, gP, gr)
         return loss
 

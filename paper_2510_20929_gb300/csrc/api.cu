@@ -362,7 +362,7 @@ cudaError_t pass1_dft(int N, const BatchArgs& a, const void* dft, cudaStream_t s
   e = timed(K_FAR_TC, s, [&] {
     return dispatch_tc(N, [&](auto c) { return launch_far_tc<decltype(c)::value>(a, dft, s); });
   });
-  if (e != cudaSuccess || a.mode == MODE_FWD) return e;
+  if (e != cudaSuccess || a.mode == MODE_FWD || a.loss_only) return e;
   return timed(K_PASS1_OVERLAP, s, [&] {
     return dispatch_tc(N, [&](auto c) { return launch_pass1_part<decltype(c)::value>(a, s, 2); });
   });
@@ -439,12 +439,24 @@ cudaError_t probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* h
   const int NP = NN / 2;
   const int threads = (dPacc ? Mc * NP : 0) + (Dp ? NP : 0);
   int bx = (threads + 255) / 256;
-  if (acc && bx < 2 * 152) bx = 2 * 152;
+  if (acc && bx < 2 * sm_count()) bx = 2 * sm_count();
   dim3 grid(bx > 0 ? bx : 1, acc ? 2 : 1);
   const cudaError_t e = launch_pdl(k_probe_reduce<16>, grid, dim3(256), 0, s, NN, k0, Mc, Ms, nb, h_s, o_s, valid,
                                    dPacc, accumulate, Dp, acc, HW, sc);
   profile_end(K_PROBE_REDUCE, e0, s);
   return e;
+}
+
+int sm_count() {
+  static int cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  int n = __atomic_load_n(&cached[dev], __ATOMIC_RELAXED);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 152;
+    __atomic_store_n(&cached[dev], n, __ATOMIC_RELAXED);
+  }
+  return n;
 }
 
 int grid_for(size_t n, int threads, int cap) {
@@ -457,7 +469,7 @@ cudaError_t norm_probe(int NN, int M, const float2* dPacc, const float* Dp, cons
                        int update_probe, const BatchScalars* sc, float2* dP, float2* Cp, float* Sdp,
                        cudaStream_t s) {
   return timed(K_NORM_PROBE, s, [&] {
-    return launch_pdl(k_norm_probe, dim3(grid_for(NN, 256, 152)), dim3(256), 0, s, NN, M, dPacc, Dp, probe, delta_p,
+    return launch_pdl(k_norm_probe, dim3(grid_for(NN, 256, sm_count())), dim3(256), 0, s, NN, M, dPacc, Dp, probe, delta_p,
                       update_probe, sc, dP, Cp, Sdp);
   });
 }
@@ -465,14 +477,14 @@ cudaError_t norm_probe(int NN, int M, const float2* dPacc, const float* Dp, cons
 cudaError_t probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
                          const BatchScalars* sc, BatchScalars* sc_next, cudaStream_t s) {
   return timed(K_UPDATE, s, [&] {
-    return launch_pdl(k_probe_update, dim3(grid_for(NN, 256, 152)), dim3(256), 0, s, NN, M, probe, dP, Sp,
+    return launch_pdl(k_probe_update, dim3(grid_for(NN, 256, sm_count())), dim3(256), 0, s, NN, M, probe, dP, Sp,
                       update_probe, sc, sc_next);
   });
 }
 
 cudaError_t init_epoch(int NN, int M, const float2* probe, float* Sp, WsHeader* hdr, cudaStream_t s) {
   return timed(K_INIT, s, [&] {
-    k_init_epoch<<<grid_for(NN, 256, 152), 256, 0, s>>>(NN, M, probe, Sp, hdr);
+    k_init_epoch<<<grid_for(NN, 256, sm_count()), 256, 0, s>>>(NN, M, probe, Sp, hdr);
     return cudaGetLastError();
   });
 }
@@ -500,7 +512,7 @@ cudaError_t clear_acc(bool tiles, const ptycho_dims& d, int nb, int b0, const fl
   if (!tiles) {
     const size_t n = (size_t)d.H * d.W;
     return timed(K_CLEAR_PLANE, s, [&] {
-      return launch_pdl(k_clear_plane, dim3(grid_for(n, 256, 8 * 152)), dim3(256), 0, s, n, acc);
+      return launch_pdl(k_clear_plane, dim3(grid_for(n, 256, 8 * sm_count())), dim3(256), 0, s, n, acc);
     });
   }
   return timed(K_TILE_CLEAR, s, [&] {
@@ -664,7 +676,7 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
     }
   }
   if (o.object_per_epoch) {
-    k_add_plane<<<grid_for((size_t)HW, 256, 4 * 152), 256, 0, s>>>((size_t)HW, obj, w.dOe);
+    k_add_plane<<<grid_for((size_t)HW, 256, 4 * sm_count()), 256, 0, s>>>((size_t)HW, obj, w.dOe);
     if ((e = cudaGetLastError()) != cudaSuccess) return PTYCHO_ERR_CUDA;
   }
   return PTYCHO_OK;
@@ -785,7 +797,10 @@ ptycho_status ptycho_adjoint_ex(const ptycho_dims* dims, int32_t precision, cons
   if (batch < 1 || !(eps >= 0.0)) return PTYCHO_ERR_ARG;
   if (noise != PTYCHO_NOISE_GAUSSIAN && noise != PTYCHO_NOISE_POISSON && noise != PTYCHO_NOISE_VJP)
     return PTYCHO_ERR_ARG;
-  if (!object || !probe || !g_object || !g_probe) return PTYCHO_ERR_ARG;
+  // no gradient buffer at all (and a loss): the forward model and data term only
+  const bool loss_only = !g_object && !g_probe && !g_pos;
+  if (!object || !probe) return PTYCHO_ERR_ARG;
+  if (loss_only ? (!loss || noise == PTYCHO_NOISE_VJP) : (!g_object || !g_probe)) return PTYCHO_ERR_ARG;
   if (dims->J > 0 && (!pos || !meas)) return PTYCHO_ERR_ARG;
   const Layout L = make_layout(*dims, batch);
   if ((st = check_ws(ws, ws_bytes, L.total)) != PTYCHO_OK) return st;
@@ -806,7 +821,9 @@ ptycho_status ptycho_adjoint_ex(const ptycho_dims* dims, int32_t precision, cons
     a.eps = (float)eps;
     a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
     a.gobj = (float2*)g_object; a.gpos = g_pos; a.loss = loss; a.status = &w.hdr->status;
+    a.loss_only = loss_only ? 1 : 0;
     if ((tc ? pass1_dft(dims->N, a, w.dft, s) : pass1(dims->N, a, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if (loss_only) continue;
     if (probe_reduce(NN, 0, dims->M, dims->M, nb, w.h, w.o, w.valid, (float2*)g_probe, 1, nullptr, nullptr, 0,
                      nullptr, s) != cudaSuccess)
       return PTYCHO_ERR_CUDA;

@@ -75,6 +75,9 @@ struct BatchArgs {
   // Position correction (LSQML): per slot the sums A11, A12, A22, b1, b2 of
   // the least-squares shift, FP64, accumulated with atomics (or null).
   double* possum;      // [B, 5]
+  // Gradient modes: evaluate the forward model and the data term (loss) only,
+  // without the back-propagation.
+  int loss_only;
 };
 
 struct Pass2Args {

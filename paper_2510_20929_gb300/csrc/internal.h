@@ -46,6 +46,8 @@ ptycho_status check_opts(const ptycho_lsqml_opts* o);
 ptycho_status check_ws(void* ws, size_t have, size_t need);
 ptycho_status cuda_status(cudaError_t e);
 int grid_for(size_t n, int threads, int cap);
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count();
 
 struct BatchArgs;
 struct Pass2Args;

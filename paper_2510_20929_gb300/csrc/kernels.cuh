@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
       block_sum<1>(v, red);
       if (tid == 0) atomicAdd(a.loss, v[0]);
     }
-    if (mode == MODE_FWD) return;
+    if (mode == MODE_FWD || a.loss_only) return;
   }
 
   // ---- back-propagation: chi_k = F^-1[fac Psi_k], g = sum_k conj(P_k) chi_k, h_k ----

@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
     block_sum<1>(v, red);
     if (tid == 0) atomicAdd(a.loss, v[0]);
   }
-  if (mode == MODE_FWD) {
+  if (mode == MODE_FWD || a.loss_only) {
     cluster.sync();   // no CTA leaves while another may still read its tile
     return;
   }

@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(FarTc<N>::T, 1)
     if (lane == 0) {
       const unsigned char* dft = (const unsigned char*)a.dft;
       uint32_t qc = 0, issued = 0, cb = 0;
+      int64_t last_mma = -1;   // the last chunk whose MMAs were issued (and committed)
       for (int s = 0; s < C::NSF; ++s) {
         tc::mbar_expect_tx(&fullF[s], C::CHUNK);
         tc::bulk_g2s(fring + (size_t)s * C::CHUNK, dft + (size_t)(s % NCH) * C::CHUNK, C::CHUNK, &fullF[s]);
@@ -385,6 +386,7 @@ __global__ void __launch_bounds__(FarTc<N>::T, 1)
           tc::mma_bf16(dim, aIh, bRl, i_im, 1u);
           tc::mma_commit(&emptyF[sf]);
           tc::mma_commit(&emptyB[sb]);
+          last_mma = qc;
           if (qc >= 1) {   // refill the previous chunk's slot once its MMAs are done
             const uint32_t qp = qc - 1, qn = qp + C::NSF;
             const int sp = (int)(qp % C::NSF);
@@ -417,6 +419,10 @@ __global__ void __launch_bounds__(FarTc<N>::T, 1)
           *abort_s = 1;
           break;
         }
+      // after an abort, the MMAs already issued finish (their last commit
+      // completes) before the tensor memory is released
+      if (*abort_s && last_mma >= 0)
+        tc::mbar_wait(&emptyF[(int)(last_mma % C::NSF)], (uint32_t)((last_mma / C::NSF) & 1));
     }
   } else if (warp == C::PW + 1) {
     // ================================ TMA warp ====================================

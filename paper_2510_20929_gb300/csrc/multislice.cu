@@ -104,7 +104,7 @@ MsLayout ms_setup(const ptycho_dims& d, const ptycho_multislice& ms, int batch, 
   a.h_s = (float2*)(b + L.h);
   a.valid = (int*)(b + L.valid);
   a.status = &((WsHeader*)ws)->status;
-  k_asm_propagator<<<grid_for((size_t)d.N * d.N, 256, 152), 256, 0, s>>>(d.N, ms.pixel_size, ms.wavelength, ms.dz,
+  k_asm_propagator<<<grid_for((size_t)d.N * d.N, 256, sm_count()), 256, 0, s>>>(d.N, ms.pixel_size, ms.wavelength, ms.dz,
                                                                           (float2*)(b + L.Hf));
   *err = cudaGetLastError();
   return L;

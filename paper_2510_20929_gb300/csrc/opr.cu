@@ -294,7 +294,7 @@ static cudaError_t opr_reduce(int NN, int M, int K, int nb, int b0, const int* o
   // pixel pairs across blockIdx.x, the batch split into enough chunks for two CTAs per SM
   const int NP = NN / 2;
   const int bx = (NP + 255) / 256;
-  int chunks = (2 * 152 + bx - 1) / bx;
+  int chunks = (2 * sm_count() + bx - 1) / bx;
   if (chunks > nb) chunks = nb;
   if (chunks < 1) chunks = 1;
   const int chunk = (nb + chunks - 1) / chunks;
@@ -316,7 +316,7 @@ static cudaError_t opr_weights(int N, int M, int K, int nb, int b0, const int* o
   if (e == cudaSuccess) {
     // pixel spans of whole chunks, enough CTAs for two per SM
     const int NN = N * N, groups = (nb + GRAM_SLOTS - 1) / GRAM_SLOTS;
-    int parts = (2 * 152 + groups - 1) / groups;
+    int parts = (2 * sm_count() + groups - 1) / groups;
     const int max_parts = (NN + GRAM_CHUNK - 1) / GRAM_CHUNK;
     if (parts > max_parts) parts = max_parts;
     const int span = ((NN + parts - 1) / parts + GRAM_CHUNK - 1) / GRAM_CHUNK * GRAM_CHUNK;
@@ -391,13 +391,13 @@ ptycho_status run_epoch_opr(const ptycho_dims& d, const ptycho_opr_opts& r, floa
         return PTYCHO_ERR_CUDA;
       if (opr_reduce(NN, M, K, nb, b0, order, wts, w.h, w.o, w.valid, w.dUacc, w.Du, s) != cudaSuccess)
         return PTYCHO_ERR_CUDA;
-      k_plane_max<<<grid_for(KNN, 256, 2 * 152), 256, 0, s>>>(w.Du, KNN, &sc->max_dp);
+      k_plane_max<<<grid_for(KNN, 256, 2 * sm_count()), 256, 0, s>>>(w.Du, KNN, &sc->max_dp);
       if (cudaGetLastError() != cudaSuccess) return PTYCHO_ERR_CUDA;
     }
     if (norm_probe(NN, M - 1, w.dPacc, w.Dp, P_rest, (float)o.delta_p, o.update_probe, sc, w.dP, w.Cp, w.Sdp,
                    s) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
-    k_norm_opr<<<grid_for(KNN, 256, 2 * 152), 256, 0, s>>>(KNN, w.dUacc, w.Du, o.update_probe, (float)o.delta_p,
+    k_norm_opr<<<grid_for(KNN, 256, 2 * sm_count()), 256, 0, s>>>(KNN, w.dUacc, w.Du, o.update_probe, (float)o.delta_p,
                                                              sc, w.dU);
     if (cudaGetLastError() != cudaSuccess) return PTYCHO_ERR_CUDA;
     Pass2Args q;

@@ -25,3 +25,12 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _parity_log(request):
+    """With PTYCHO_PARITY_LOG=<file>, every test appends the norm-wise and
+    element-wise errors its parity checks measured (one JSON object per line)."""
+    yield
+    from tests import parity_util
+    parity_util.write_log(os.environ.get("PTYCHO_PARITY_LOG"), request.node.nodeid)

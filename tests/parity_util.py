@@ -1,7 +1,9 @@
 """Helpers shared by the GPU parity tests and the smoke run: seeded problems
 (inputs from paper_2510_20929_gb300.synth, measured data from the FP64 oracle)
 and error metrics."""
+import json
 import math
+import os
 
 import numpy as np
 
@@ -15,6 +17,53 @@ def rel(a, b):
     b = np.asarray(b)
     nb = np.linalg.norm(b.ravel())
     return float(np.linalg.norm((a - b).ravel()) / (nb if nb > 0 else 1.0))
+
+
+def elem(a, b, axis=None):
+    """Element-wise relative error max|a - b| / max|b|.
+
+    With ``axis`` every slice along that axis is measured against its own
+    maximum and the worst slice is returned: axis 0 of a probe [M, N, N] gives
+    the worst mode, axis 1 of step sizes [J, 2] the worst of alpha_O and
+    alpha_P (each over all positions), so that one wrong mode plane or one
+    wrong position shows even when the norm of the whole array hides it.
+    """
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if axis is None:
+        mb = float(np.max(np.abs(b))) if b.size else 0.0
+        return float(np.max(np.abs(a - b)) / (mb if mb > 0 else 1.0)) if b.size else 0.0
+    return max((elem(np.take(a, i, axis=axis), np.take(b, i, axis=axis)) for i in range(b.shape[axis])),
+               default=0.0)
+
+
+# The largest element-wise error admitted per unit of norm-wise tolerance. For n
+# independent rounding errors of rms s the largest is near s sqrt(2 ln n)
+# (4.3 for n = 1e4, 5.3 for n = 1e6), and max|b| is at least the rms of b, so
+# an element-wise bar of 5x the norm-wise one passes rounding noise while a
+# localised mistake (one wrong column, mode plane or position) exceeds it.
+ELEM_FACTOR = 5.0
+
+_LOG = []
+
+
+def err(a, b, axis=None, label=None):
+    """max(norm-wise error, element-wise error / ELEM_FACTOR): below a tolerance
+    t means ||a - b|| < t ||b|| and max|a - b| < 5 t max|b| (per slice of
+    ``axis``). Both parts are recorded for the parity log."""
+    n, e = rel(a, b), elem(a, b, axis)
+    _LOG.append({"label": label, "norm": n, "elem": e})
+    return max(n, e / ELEM_FACTOR)
+
+
+def write_log(path, test_id):
+    """Appends the errors recorded since the last call, tagged with the test id."""
+    global _LOG
+    if path and _LOG:
+        with open(path, "a") as f:
+            for r in _LOG:
+                f.write(json.dumps({"test": test_id, **r}) + "\n")
+    _LOG = []
 
 
 def problem(N=16, M=2, H=40, W=44, J=12, seed=7, step=4.0, counts=2e4, perturb=0.15, noisy=True):

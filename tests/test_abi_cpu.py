@@ -141,3 +141,26 @@ def test_binding_refuses_cpu_tensors():
     pos = torch.zeros(3, 2)
     with pytest.raises(ValueError):
         api.forward(obj, probe, pos)
+
+
+def test_allocation_free_epoch_rejects_arguments_like_the_workspace_epoch(L):
+    # same statuses as ptycho_lsqml_epoch, all returned by host checks before the
+    # array's address is looked up (so no device is touched)
+    from paper_2510_20929_gb300 import api
+    P = ctypes.c_void_p
+    fake = P(0x1000)
+    opts = api.make_opts(batch=4)
+    for dims, want in ((_dims(N=48), 6), (_dims(M=17), 6), (_dims(H=32), 1)):
+        got_ws = L.ptycho_lsqml_epoch(ctypes.byref(dims), fake, fake, fake, fake, P(0), ctypes.byref(opts),
+                                      P(0), P(0), fake, 1 << 30, None)
+        got_static = L.ptycho_lsqml_epoch_static(ctypes.byref(dims), fake, fake, fake, fake, P(0),
+                                                 ctypes.byref(opts), P(0), P(0), None)
+        assert got_static == got_ws == want
+    bad = api.make_opts(batch=4, noise=7)
+    assert L.ptycho_lsqml_epoch_static(ctypes.byref(_dims()), fake, fake, fake, fake, P(0), ctypes.byref(bad),
+                                       P(0), P(0), None) == 1
+    assert L.ptycho_lsqml_epoch_static(None, fake, fake, fake, fake, P(0), ctypes.byref(opts), P(0), P(0),
+                                       None) == 1
+    big = _dims(H=8192, W=8192, N=128, M=5, J=100)
+    assert L.ptycho_lsqml_epoch_static(ctypes.byref(big), fake, fake, fake, fake, P(0), ctypes.byref(opts),
+                                       P(0), P(0), None) == 8

@@ -8,7 +8,7 @@ import pytest
 
 from oracle import ptycho_oracle as orc
 from paper_2510_20929_gb300 import synth
-from tests.parity_util import c64, f32pos, problem, rel, to_dev
+from tests.parity_util import c64, f32pos, problem, err, to_dev
 
 pytestmark = pytest.mark.gpu
 TOL_EPOCH = 1e-4
@@ -51,7 +51,7 @@ def test_batched_equals_standalone_and_oracle(graph):
         opts.append(api.make_opts(batch=it["np"][5], delta_o=0.1, delta_p=0.1, eps=1e-6, graph=graph))
     losses = api.lsqml_epoch_batched(recons, opts)
     for i, ((O, P, *_), (Or, Pr, Lr)) in enumerate(zip(recons, ref)):
-        e = (rel(O.cpu().numpy(), Or.cpu().numpy()), rel(P.cpu().numpy(), Pr.cpu().numpy()),
+        e = (err(O.cpu().numpy(), Or.cpu().numpy()), err(P.cpu().numpy(), Pr.cpu().numpy(), axis=0),
              abs(losses[i].item() - Lr) / abs(Lr))
         print(f"recon {i}: {e}")
         assert max(e) < TOL_EPOCH
@@ -59,7 +59,7 @@ def test_batched_equals_standalone_and_oracle(graph):
     O, P, pos, I_m, order, B = items[0]["np"]
     O_ref, P_ref, _, _ = orc.lsqml_epoch(O, P, pos, I_m, order,
                                          orc.LsqmlOptions(batch=B, delta_o=0.1, delta_p=0.1, eps=1e-6))
-    assert rel(recons[0][0].cpu().numpy(), O_ref) < TOL_EPOCH and rel(recons[0][1].cpu().numpy(), P_ref) < TOL_EPOCH
+    assert err(recons[0][0].cpu().numpy(), O_ref) < TOL_EPOCH and err(recons[0][1].cpu().numpy(), P_ref, axis=0) < TOL_EPOCH
 
 
 def test_graph_replay_equals_eager_over_consecutive_epochs():
@@ -73,7 +73,7 @@ def test_graph_replay_equals_eager_over_consecutive_epochs():
     for epoch in range(4):
         le, _ = api.lsqml_epoch(Oe, Pe, pos, meas, order, eager)
         lg, _ = api.lsqml_epoch(Og, Pg, pos, meas, order, graphed)
-        e = (rel(Og.cpu().numpy(), Oe.cpu().numpy()), rel(Pg.cpu().numpy(), Pe.cpu().numpy()),
+        e = (err(Og.cpu().numpy(), Oe.cpu().numpy()), err(Pg.cpu().numpy(), Pe.cpu().numpy(), axis=0),
              abs(lg.item() - le.item()) / abs(le.item()))
         print(f"epoch {epoch}: {e}")
         assert max(e) < TOL_EPOCH
@@ -94,7 +94,7 @@ def test_autotuned_epoch_matches_default_and_records_its_choice():
     ld, _ = api.lsqml_epoch(Od, Pd, pos, meas, order, api.make_opts(batch=8, delta_o=0.1, delta_p=0.1, eps=1e-6))
     lt, _ = api.lsqml_epoch(Ot, Pt, pos, meas, order,
                             api.make_opts(batch=8, delta_o=0.1, delta_p=0.1, eps=1e-6, autotune=True))
-    e = (rel(Ot.cpu().numpy(), Od.cpu().numpy()), rel(Pt.cpu().numpy(), Pd.cpu().numpy()),
+    e = (err(Ot.cpu().numpy(), Od.cpu().numpy()), err(Pt.cpu().numpy(), Pd.cpu().numpy(), axis=0),
          abs(lt.item() - ld.item()) / abs(ld.item()))
     t = api.tuning(api.dims_of(O0, P0, pos), 8)
     print("autotune:", e, t)

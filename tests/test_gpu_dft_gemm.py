@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import ptycho_oracle as orc
-from tests.parity_util import c64, f32pos, problem, rel, to_dev
+from tests.parity_util import c64, f32pos, problem, err, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +43,7 @@ def test_forward_bf16x3_matches_oracle(N, M, H, W, J, step):
     ref = orc.forward(O, P, pos)
     I = api.forward(dO, dP, dpos, precision="bf16x3", batch=5).cpu().numpy()   # ragged chunks of 5
     I32 = api.forward(dO, dP, dpos).cpu().numpy()
-    e, e32 = rel(I, ref), rel(I32, ref)
+    e, e32 = err(I, ref), err(I32, ref)
     print(f"forward bf16x3 N={N} M={M}: rel {e:.3e} (fp32 path {e32:.3e})")
     assert e < TOL_BF16
     for j in range(J):
@@ -57,11 +57,11 @@ def test_bf16x3_exit_waves_on_odd_and_even_object_widths(W):
     from paper_2510_20929_gb300 import api
     p = problem(N=64, M=2, H=160, W=W, J=20, step=12.0)
     (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
-    e_fwd = rel(api.forward(dO, dP, dpos, precision="bf16x3", batch=7).cpu().numpy(), orc.forward(O, P, pos))
+    e_fwd = err(api.forward(dO, dP, dpos, precision="bf16x3", batch=7).cpu().numpy(), orc.forward(O, P, pos))
     L, gO, gP, gr = orc.loss_and_gradients(O, P, pos, I_m, orc.GAUSSIAN, 1e-6)
     loss, dgO, dgP, dgr = api.adjoint(dO, dP, dpos, dI, "gaussian", eps=1e-6, batch=7, precision="bf16x3")
-    e = (e_fwd, abs(loss.item() - L) / L, rel(dgO.cpu().numpy(), gO), rel(dgP.cpu().numpy(), gP),
-         rel(dgr.cpu().numpy(), gr))
+    e = (e_fwd, abs(loss.item() - L) / L, err(dgO.cpu().numpy(), gO), err(dgP.cpu().numpy(), gP, axis=0),
+         err(dgr.cpu().numpy(), gr, axis=1))
     print(f"bf16x3 W={W}:", " ".join(f"{x:.2e}" for x in e))
     assert max(e) < TOL_BF16
 
@@ -76,8 +76,8 @@ def test_gradients_bf16x3_match_oracle(noise, N, M, H, W, J, step):
     nz = orc.GAUSSIAN if noise == "gaussian" else orc.POISSON
     L_ref, gO_ref, gP_ref, gr_ref = orc.loss_and_gradients(O, P, pos, I_m, nz, eps)
     loss, gO, gP, gr = api.adjoint(dO, dP, dpos, dI, noise, eps=eps, batch=4, precision="bf16x3")
-    e = (abs(loss.item() - L_ref) / abs(L_ref), rel(gO.cpu().numpy(), gO_ref),
-         rel(gP.cpu().numpy(), gP_ref), rel(gr.cpu().numpy(), gr_ref))
+    e = (abs(loss.item() - L_ref) / abs(L_ref), err(gO.cpu().numpy(), gO_ref),
+         err(gP.cpu().numpy(), gP_ref, axis=0), err(gr.cpu().numpy(), gr_ref, axis=1))
     print(f"grad bf16x3 {noise} N={N} M={M}: loss {e[0]:.2e} gO {e[1]:.2e} gP {e[2]:.2e} gr {e[3]:.2e}")
     assert max(e) < TOL_BF16
 
@@ -91,7 +91,7 @@ def test_vjp_bf16x3_matches_oracle():
     gO_ref, gP_ref, gr_ref = orc.vjp(O, P, pos, G)
     loss, gO, gP, gr = api.adjoint(dO, dP, dpos, to_dev(G, torch.float32), "vjp", batch=7, precision="bf16x3")
     assert loss is None
-    e = (rel(gO.cpu().numpy(), gO_ref), rel(gP.cpu().numpy(), gP_ref), rel(gr.cpu().numpy(), gr_ref))
+    e = (err(gO.cpu().numpy(), gO_ref), err(gP.cpu().numpy(), gP_ref, axis=0), err(gr.cpu().numpy(), gr_ref, axis=1))
     print(f"vjp bf16x3: {e}")
     assert max(e) < TOL_BF16
 
@@ -114,8 +114,8 @@ def test_lsqml_epoch_bf16x3_matches_oracle(N, M, H, W, J, step, batch, noise):
     loss, alpha = api.lsqml_epoch(dO, dP, dpos, dI, to_dev(order, torch.int32), noise=noise, batch=batch,
                                   delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6, want_alpha=True,
                                   precision="bf16x3")
-    e = dict(O=rel(dO.cpu().numpy(), O_ref), P=rel(dP.cpu().numpy(), P_ref),
-             alpha=rel(alpha.cpu().numpy(), a_ref), loss=abs(loss.item() - L_ref) / abs(L_ref))
+    e = dict(O=err(dO.cpu().numpy(), O_ref), P=err(dP.cpu().numpy(), P_ref, axis=0),
+             alpha=err(alpha.cpu().numpy(), a_ref, axis=1), loss=abs(loss.item() - L_ref) / abs(L_ref))
     print(f"epoch bf16x3 N={N} M={M} B={batch} {noise}: " + " ".join(f"{k} {v:.2e}" for k, v in e.items()))
     assert max(e.values()) < TOL_BF16
 
@@ -140,14 +140,14 @@ def test_bf16x3_skips_and_reports_out_of_bounds_positions():
     assert ws.status() == 2
     I = I.cpu().numpy()
     assert np.all(I[[3, 7]] == -7.0)
-    assert rel(I[keep], orc.forward(O, P, pos[keep])) < TOL_BF16
+    assert err(I[keep], orc.forward(O, P, pos[keep])) < TOL_BF16
     loss, gO, gP, gr = api.adjoint(dO, dP, dbad, dI, "gaussian", eps=1e-6, batch=4, precision="bf16x3",
                                    check=False)
     assert api.workspace(d, 4, dO.device).status() == 2
     L, gO_ref, gP_ref, gr_ref = orc.loss_and_gradients(O, P, pos[keep], I_m[keep], orc.GAUSSIAN, 1e-6)
     assert abs(loss.item() - L) / L < TOL_BF16
-    assert rel(gO.cpu().numpy(), gO_ref) < TOL_BF16 and rel(gP.cpu().numpy(), gP_ref) < TOL_BF16
-    assert rel(gr.cpu().numpy()[keep], gr_ref) < TOL_BF16 and np.all(gr.cpu().numpy()[[3, 7]] == 0)
+    assert err(gO.cpu().numpy(), gO_ref) < TOL_BF16 and err(gP.cpu().numpy(), gP_ref, axis=0) < TOL_BF16
+    assert err(gr.cpu().numpy()[keep], gr_ref, axis=1) < TOL_BF16 and np.all(gr.cpu().numpy()[[3, 7]] == 0)
 
 
 def test_bf16x3_graph_replay_and_host_epoch_match_the_device_epoch():
@@ -166,14 +166,14 @@ def test_bf16x3_graph_replay_and_host_epoch_match_the_device_epoch():
                             graph=graph, precision="bf16x3")
         res.append((o.cpu().numpy(), pr.cpu().numpy()))
     # (the overlap-add atomics may sum in another order: equal to rounding)
-    assert rel(res[1][0], res[0][0]) < 1e-5 and rel(res[1][1], res[0][1]) < 1e-5
+    assert err(res[1][0], res[0][0]) < 1e-5 and err(res[1][1], res[0][1], axis=0) < 1e-5
     hO, hP = O.astype(np.complex64), P.astype(np.complex64)
     opts = api.make_opts(batch=5, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6, precision="bf16x3")
     hO_t, hP_t = torch.from_numpy(hO.copy()), torch.from_numpy(hP.copy())
     for _ in range(2):
         api.lsqml_epoch_host(hO_t, hP_t, torch.from_numpy(np.float32(pos)), torch.from_numpy(np.float32(I_m)),
                              torch.from_numpy(order), opts, device=dO.device)
-    assert rel(hO_t.numpy(), res[0][0]) < 1e-5 and rel(hP_t.numpy(), res[0][1]) < 1e-5
+    assert err(hO_t.numpy(), res[0][0]) < 1e-5 and err(hP_t.numpy(), res[0][1], axis=0) < 1e-5
 
 
 def test_bf16x3_batched_reconstructions_equal_their_single_epochs():
@@ -196,7 +196,7 @@ def test_bf16x3_batched_reconstructions_equal_their_single_epochs():
     opts = [api.make_opts(batch=5, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6, precision="bf16x3")] * 2
     losses = api.lsqml_epoch_batched(batch, opts).cpu().numpy()
     for (o, pr, *_), (O1, P1, L1), L in zip(batch, single, losses):
-        assert rel(o.cpu().numpy(), O1) < 1e-5 and rel(pr.cpu().numpy(), P1) < 1e-5
+        assert err(o.cpu().numpy(), O1) < 1e-5 and err(pr.cpu().numpy(), P1, axis=0) < 1e-5
         assert abs(L - L1) <= 1e-5 * abs(L1)
 
 
@@ -225,7 +225,7 @@ def test_bf16x3_one_position_and_whole_set_minibatches(batch):
     O1, P1, L1, a1 = orc.lsqml_epoch(O, P, pos, I_m, order, orc.LsqmlOptions(**kw))
     loss, alpha = api.lsqml_epoch(dO, dP, dpos, dI, to_dev(order, torch.int32), want_alpha=True,
                                   precision="bf16x3", **kw)
-    e = (rel(dO.cpu().numpy(), O1), rel(dP.cpu().numpy(), P1), rel(alpha.cpu().numpy(), a1))
+    e = (err(dO.cpu().numpy(), O1), err(dP.cpu().numpy(), P1, axis=0), err(alpha.cpu().numpy(), a1, axis=1))
     print(f"bf16x3 batch {batch}:", e)
     assert max(e) < TOL_BF16
 
@@ -235,11 +235,11 @@ def test_bf16x3_sixteen_modes():
     from paper_2510_20929_gb300 import api
     p = problem(N=32, M=16, H=72, W=76, J=8, step=6.0)
     (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
-    e_fwd = rel(api.forward(dO, dP, dpos, precision="bf16x3").cpu().numpy(), orc.forward(O, P, pos))
+    e_fwd = err(api.forward(dO, dP, dpos, precision="bf16x3").cpu().numpy(), orc.forward(O, P, pos))
     L, gO, gP, gr = orc.loss_and_gradients(O, P, pos, I_m, orc.POISSON, 1e-6)
     loss, dgO, dgP, dgr = api.adjoint(dO, dP, dpos, dI, "poisson", eps=1e-6, batch=3, precision="bf16x3")
-    e = (e_fwd, abs(loss.item() - L) / abs(L), rel(dgO.cpu().numpy(), gO), rel(dgP.cpu().numpy(), gP),
-         rel(dgr.cpu().numpy(), gr))
+    e = (e_fwd, abs(loss.item() - L) / abs(L), err(dgO.cpu().numpy(), gO), err(dgP.cpu().numpy(), gP, axis=0),
+         err(dgr.cpu().numpy(), gr, axis=1))
     print("bf16x3 16 modes:", " ".join(f"{x:.2e}" for x in e))
     assert max(e) < TOL_BF16
 
@@ -256,4 +256,4 @@ def test_bounded_wait_reports_timeout_and_the_context_stays_usable():
     assert ws.status() == 5                       # PTYCHO_ERR_TIMEOUT
     assert ws.status() == 0                       # read clears it
     I = api.forward(dO, dP, dpos, precision="bf16x3", batch=4).cpu().numpy()
-    assert rel(I, orc.forward(O, P, pos)) < TOL_BF16
+    assert err(I, orc.forward(O, P, pos)) < TOL_BF16

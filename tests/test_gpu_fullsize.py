@@ -1,8 +1,8 @@
 """Parity at the paper-shaped workloads' full sizes, in the launch configuration
 bench.py times (minibatch, window, modes and object size), against the FP64
 oracle: the raster64 workload in full, and the spiral128 workload on one full
-minibatch of 256 positions plus sampled forward outputs and epoch-level
-properties over all 4096 positions."""
+minibatch of 256 positions, one whole epoch of all 4096 positions, sampled
+forward outputs and epoch-level properties."""
 import math
 
 import numpy as np
@@ -10,7 +10,7 @@ import pytest
 
 from oracle import ptycho_oracle as orc
 from paper_2510_20929_gb300 import synth
-from tests.parity_util import rel, to_dev
+from tests.parity_util import err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,7 @@ def test_raster64_full_workload(noise):
     dO, dP = to_dev(O0, torch.complex64), to_dev(P, torch.complex64)
     dpos, dI = to_dev(pos, torch.float32), to_dev(I_m, torch.float32)
     # forward
-    e = rel(api.forward(dO, dP, dpos).cpu().numpy(), orc.forward(O0, P, pos))
+    e = err(api.forward(dO, dP, dpos).cpu().numpy(), orc.forward(O0, P, pos))
     assert e < TOL_FWD, e
     # one epoch, one minibatch of all 100 positions (the workload's batch). From the flat
     # start many pixels are predicted near zero yet hold counts; the Poisson factor
@@ -54,7 +54,7 @@ def test_raster64_full_workload(noise):
     O_ref, P_ref, L_ref, a_ref = orc.lsqml_epoch(O0, P, pos, I_m, order, opts)
     loss, alpha = api.lsqml_epoch(dO, dP, dpos, dI, to_dev(order, torch.int32), noise=noise, batch=w["batch"],
                                   delta_o=0.1, delta_p=0.1, lam=1e-6, eps=eps, want_alpha=True)
-    e = (rel(dO.cpu().numpy(), O_ref), rel(dP.cpu().numpy(), P_ref), rel(alpha.cpu().numpy(), a_ref),
+    e = (err(dO.cpu().numpy(), O_ref), err(dP.cpu().numpy(), P_ref, axis=0), err(alpha.cpu().numpy(), a_ref, axis=1),
          abs(loss.item() - L_ref) / abs(L_ref))
     print(f"raster64 {noise}: O {e[0]:.2e} P {e[1]:.2e} alpha {e[2]:.2e} loss {e[3]:.2e}")
     assert max(e) < TOL_EPOCH
@@ -74,8 +74,8 @@ def test_raster64_full_workload_gradients():
     loss, gO, gP, gr = api.adjoint(to_dev(O, torch.complex64), to_dev(P, torch.complex64),
                                    to_dev(pos, torch.float32), to_dev(I_m, torch.float32), "gaussian", eps=1e-9,
                                    batch=100)
-    e = (abs(loss.item() - L_ref) / L_ref, rel(gO.cpu().numpy(), gO_ref), rel(gP.cpu().numpy(), gP_ref),
-         rel(gr.cpu().numpy(), gr_ref))
+    e = (abs(loss.item() - L_ref) / L_ref, err(gO.cpu().numpy(), gO_ref), err(gP.cpu().numpy(), gP_ref, axis=0),
+         err(gr.cpu().numpy(), gr_ref, axis=1))
     print("raster64 gradients:", e)
     assert e[0] < TOL_FWD and max(e[1:]) < TOL_EPOCH
 
@@ -102,7 +102,7 @@ def test_spiral128_first_minibatch(spiral):
     dO, dP = to_dev(O0, torch.complex64), to_dev(P, torch.complex64)
     loss, alpha = api.lsqml_epoch(dO, dP, to_dev(sub_pos, torch.float32), to_dev(I_sub, torch.float32),
                                   None, batch=256, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9, want_alpha=True)
-    e = (rel(dO.cpu().numpy(), O_ref), rel(dP.cpu().numpy(), P_ref), rel(alpha.cpu().numpy(), a_ref),
+    e = (err(dO.cpu().numpy(), O_ref), err(dP.cpu().numpy(), P_ref, axis=0), err(alpha.cpu().numpy(), a_ref, axis=1),
          abs(loss.item() - L_ref) / abs(L_ref))
     print(f"spiral128 first minibatch: O {e[0]:.2e} P {e[1]:.2e} alpha {e[2]:.2e} loss {e[3]:.2e}")
     assert max(e) < TOL_EPOCH
@@ -117,7 +117,7 @@ def test_spiral128_sampled_forward_and_epoch_properties(spiral):
     I = api.forward(dO_true, dP, dpos)
     sample = np.random.default_rng(9).choice(w["J"], 12, replace=False)
     ref = orc.forward(O_true, P, pos[sample])
-    e = rel(I[torch.as_tensor(sample, device=I.device)].cpu().numpy(), ref)
+    e = err(I[torch.as_tensor(sample, device=I.device)].cpu().numpy(), ref)
     assert e < TOL_FWD, e
     # epochs over all 4096 positions: finite, decreasing loss from a flat start (noiseless data)
     O = torch.ones_like(dO_true)
@@ -131,6 +131,33 @@ def test_spiral128_sampled_forward_and_epoch_properties(spiral):
         assert torch.isfinite(alpha).all()
     print("spiral128 losses:", losses)
     assert losses[2] < losses[1] < losses[0]
+
+
+def test_spiral128_full_epoch_matches_oracle():
+    # The epoch the bench times, in full: all 4096 positions in 16 minibatches of
+    # 256 in the bench's order, from the flat object and the true probe, on
+    # Poisson-sampled counts (1e6 per pattern) with the amplitude data term at
+    # eps = 1e-9; every minibatch updates the object and the probe, so the
+    # comparison covers the compounding of 16 updates.
+    import torch
+    from paper_2510_20929_gb300 import api
+    w = synth.workload_spiral128()
+    O_true = _f32(w["object"], True)
+    pos = _f32(w["pos"])
+    P, I_m = _measured(w, O_true, _f32(w["probe"], True), pos, 31)
+    P, I_m = _f32(P, True), _f32(I_m)
+    order = synth.random_order(w["J"], 5)
+    O0 = np.ones_like(O_true)
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=256, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9)
+    O_ref, P_ref, L_ref, a_ref = orc.lsqml_epoch(O0, P, pos, I_m, order, opts)
+    dO, dP = to_dev(O0, torch.complex64), to_dev(P, torch.complex64)
+    loss, alpha = api.lsqml_epoch(dO, dP, to_dev(pos, torch.float32), to_dev(I_m, torch.float32),
+                                  to_dev(order, torch.int32), batch=256, delta_o=0.1, delta_p=0.1, lam=1e-6,
+                                  eps=1e-9, want_alpha=True)
+    e = (err(dO.cpu().numpy(), O_ref), err(dP.cpu().numpy(), P_ref, axis=0), err(alpha.cpu().numpy(), a_ref, axis=1),
+         abs(loss.item() - L_ref) / abs(L_ref))
+    print(f"spiral128 full epoch: O {e[0]:.2e} P {e[1]:.2e} alpha {e[2]:.2e} loss {e[3]:.2e}")
+    assert max(e) < TOL_EPOCH
 
 
 @pytest.mark.parametrize("eps", [1.0, 1e-9])
@@ -153,8 +180,8 @@ def test_spiral128_first_minibatch_split_bf16(spiral, eps):
     loss, alpha = api.lsqml_epoch(dO, dP, to_dev(sub_pos, torch.float32), to_dev(I_sub, torch.float32),
                                   None, batch=256, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=eps, want_alpha=True,
                                   precision="bf16x3")
-    e = (rel(dO.cpu().numpy(), O_ref), rel(dP.cpu().numpy(), P_ref), abs(loss.item() - L_ref) / abs(L_ref),
-         rel(alpha.cpu().numpy(), a_ref))
+    e = (err(dO.cpu().numpy(), O_ref), err(dP.cpu().numpy(), P_ref, axis=0), abs(loss.item() - L_ref) / abs(L_ref),
+         err(alpha.cpu().numpy(), a_ref, axis=1))
     print(f"spiral128 first minibatch, split BF16, eps {eps:g}: O {e[0]:.2e} P {e[1]:.2e} loss {e[2]:.2e} "
           f"alpha {e[3]:.2e}")
     assert max(e[:3]) < 1e-3
@@ -184,8 +211,8 @@ def test_spiral256_sampled_gradients_match_oracle(spiral256):
         t.requires_grad_(True)
     loss = data_term(dO, dP, dpos, to_dev(I_m, torch.float32), "gaussian", 1e-6)
     loss.backward()
-    e = (abs(loss.item() - L) / L, rel(dO.grad.cpu().numpy(), gO), rel(dP.grad.cpu().numpy(), gP),
-         rel(dpos.grad.cpu().numpy(), gr))
+    e = (abs(loss.item() - L) / L, err(dO.grad.cpu().numpy(), gO), err(dP.grad.cpu().numpy(), gP, axis=0),
+         err(dpos.grad.cpu().numpy(), gr, axis=1))
     print("spiral256 sampled gradients:", e)
     assert e[0] < TOL_FWD and max(e[1:]) < TOL_EPOCH
 
@@ -232,13 +259,13 @@ def test_multislice256_sampled_forward_and_gradients_match_oracle(multislice256)
     dOs, dP, dpos = to_dev(Os, torch.complex64), to_dev(P, torch.complex64), to_dev(pos, torch.float32)
     I = api.forward_ms(dOs, dP, dpos, ms, batch=w["batch"]).cpu().numpy()
     ref = orc.forward_ms(Os, P, pos, Hf)
-    e_fwd = rel(I, ref)
+    e_fwd = err(I, ref)
     I_m = _f32(synth.poisson_counts(ref * 1.05, 9))
     L, gO, gP, gr = orc.loss_and_gradients_ms(Os, P, pos, Hf, I_m, orc.GAUSSIAN, 1e-6)
     loss, dgO, dgP, dgr = api.adjoint_ms(dOs, dP, dpos, to_dev(I_m, torch.float32), ms, "gaussian", eps=1e-6,
                                          batch=w["batch"])
-    e = (e_fwd, abs(loss.item() - L) / L, rel(dgO.cpu().numpy(), gO), rel(dgP.cpu().numpy(), gP),
-         rel(dgr.cpu().numpy(), gr))
+    e = (e_fwd, abs(loss.item() - L) / L, err(dgO.cpu().numpy(), gO), err(dgP.cpu().numpy(), gP, axis=0),
+         err(dgr.cpu().numpy(), gr, axis=1))
     print("multislice256 sampled:", e)
     assert e[0] < 10 * TOL_FWD and e[1] < TOL_FWD and max(e[2:]) < TOL_EPOCH
 
@@ -289,7 +316,7 @@ def test_uneven16_opr_batched_epoch_matches_oracle_on_sampled_minibatches():
         oprs.append(api.make_opr_opts(8))
     losses = api.lsqml_epoch_opr_batched(recons, opts, oprs).cpu().numpy()
     for (dO, dU, dw, _, _, _, _), (O1, U1, w1, _, L1, _), L in zip(recons, refs, losses):
-        e = (rel(dO.cpu().numpy(), O1), rel(dU.cpu().numpy(), U1), rel(dw.cpu().numpy(), w1), abs(L - L1) / L1)
+        e = (err(dO.cpu().numpy(), O1), err(dU.cpu().numpy(), U1, axis=0), err(dw.cpu().numpy(), w1, axis=1), abs(L - L1) / L1)
         print("uneven16opr first positions:", " ".join(f"{x:.2e}" for x in e))
         assert max(e) < TOL_EPOCH
 

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import ptycho_oracle as orc
-from tests.parity_util import c64, f32pos, opr_problem, rel, to_dev
+from tests.parity_util import c64, f32pos, opr_problem, err, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -51,7 +51,7 @@ def test_forward_opr_matches_oracle(N, K, M, H, W, J, step):
     d = _dev(h)
     I = api.forward_opr(*d[:5]).cpu().numpy()
     ref = orc.forward_opr(*h[:5])
-    e = rel(I, ref)
+    e = err(I, ref)
     print(f"forward_opr N={N} K={K} M={M}: rel {e:.3e}")
     assert e < TOL_FWD
     for j in range(J):
@@ -68,10 +68,10 @@ def test_adjoint_opr_matches_oracle(noise, N, K, M, H, W, J, step):
     nz = orc.GAUSSIAN if noise == "gaussian" else orc.POISSON
     L_ref, gO_ref, gU_ref, gw_ref, gP_ref, gr_ref = orc.loss_and_gradients_opr(O, U, w, Pr, pos, I_m, nz, eps)
     loss, gO, gU, gw, gP, gr = api.adjoint_opr(*_dev(h), noise, eps=eps, batch=4)   # ragged chunks
-    e = [abs(loss.item() - L_ref) / abs(L_ref), rel(gO.cpu().numpy(), gO_ref), rel(gU.cpu().numpy(), gU_ref),
-         rel(gw.cpu().numpy(), gw_ref), rel(gr.cpu().numpy(), gr_ref)]
+    e = [abs(loss.item() - L_ref) / abs(L_ref), err(gO.cpu().numpy(), gO_ref), err(gU.cpu().numpy(), gU_ref, axis=0),
+         err(gw.cpu().numpy(), gw_ref, axis=1), err(gr.cpu().numpy(), gr_ref, axis=1)]
     if Pr is not None:
-        e.append(rel(gP.cpu().numpy(), gP_ref))
+        e.append(err(gP.cpu().numpy(), gP_ref, axis=0))
     print(f"adjoint_opr {noise} N={N} K={K} M={M}:", " ".join(f"{x:.2e}" for x in e))
     assert max(e) < TOL_GRAD
 
@@ -87,8 +87,8 @@ def test_adjoint_opr_vjp_mode_is_the_chain_rule_of_the_forward():
     d = _dev(h)
     loss, gO, gU, gw, gP, gr = api.adjoint_opr(*d[:5], to_dev(G, torch.float32), "vjp", batch=3)
     assert loss is None
-    e = [rel(gO.cpu().numpy(), gO_ref), rel(gU.cpu().numpy(), gU_ref), rel(gw.cpu().numpy(), gw_ref),
-         rel(gP.cpu().numpy(), gP_ref), rel(gr.cpu().numpy(), gr_ref)]
+    e = [err(gO.cpu().numpy(), gO_ref), err(gU.cpu().numpy(), gU_ref, axis=0), err(gw.cpu().numpy(), gw_ref, axis=1),
+         err(gP.cpu().numpy(), gP_ref, axis=0), err(gr.cpu().numpy(), gr_ref, axis=1)]
     print("vjp_opr:", " ".join(f"{x:.2e}" for x in e))
     assert max(e) < TOL_GRAD
 
@@ -109,10 +109,10 @@ def _epoch_case(N, K, M, H, W, J, step, batch, update_weights, noise="gaussian",
     loss, alpha = api.lsqml_epoch_opr(dO, dU, dw, dPr, dpos, dI, to_dev(order, torch.int32), opts, opr,
                                       want_alpha=True)
     O1, U1, w1, Pr1, L1, a1 = ref
-    e = {"O": rel(dO.cpu().numpy(), O1), "U": rel(dU.cpu().numpy(), U1), "w": rel(dw.cpu().numpy(), w1),
-         "alpha": rel(alpha.cpu().numpy(), a1), "loss": abs(loss.item() - L1) / abs(L1)}
+    e = {"O": err(dO.cpu().numpy(), O1), "U": err(dU.cpu().numpy(), U1, axis=0), "w": err(dw.cpu().numpy(), w1, axis=1),
+         "alpha": err(alpha.cpu().numpy(), a1, axis=1), "loss": abs(loss.item() - L1) / abs(L1)}
     if Pr is not None:
-        e["P_rest"] = rel(dPr.cpu().numpy(), Pr1)
+        e["P_rest"] = err(dPr.cpu().numpy(), Pr1, axis=0)
     # the weights moved (when updated), so the comparison is not vacuous
     dw_ref = rel(w1, w)
     return e, dw_ref
@@ -156,7 +156,7 @@ def test_lsqml_epoch_opr_graph_replay_matches_direct():
             loss, _ = api.lsqml_epoch_opr(dO, dU, dw, dPr, dpos, dI, None, opts, opr)
         outs.append((dO.cpu().numpy(), dU.cpu().numpy(), dw.cpu().numpy(), loss.item()))
     (O0, U0, w0, L0), (O1, U1, w1, L1) = outs
-    assert rel(O1, O0) < 1e-5 and rel(U1, U0) < 1e-5 and rel(w1, w0) < 1e-5 and abs(L1 - L0) < 1e-5 * abs(L0)
+    assert err(O1, O0) < 1e-5 and err(U1, U0) < 1e-5 and err(w1, w0) < 1e-5 and abs(L1 - L0) < 1e-5 * abs(L0)
 
 
 def test_opr_rejects_bad_arguments():
@@ -196,8 +196,8 @@ def test_data_term_opr_autograd_and_adam():
     x = [t.clone().requires_grad_(True) for t in (dO, dU, dw)]
     loss = autograd.data_term_opr(x[0], x[1], x[2], dPr, dpos, dI, "gaussian", 1e-6)
     (2.0 * loss).backward()
-    e = [abs(loss.item() - L_ref) / L_ref, rel(x[0].grad.cpu().numpy(), 2 * gO_ref),
-         rel(x[1].grad.cpu().numpy(), 2 * gU_ref), rel(x[2].grad.cpu().numpy(), 2 * gw_ref)]
+    e = [abs(loss.item() - L_ref) / L_ref, err(x[0].grad.cpu().numpy(), 2 * gO_ref),
+         err(x[1].grad.cpu().numpy(), 2 * gU_ref, axis=0), err(x[2].grad.cpu().numpy(), 2 * gw_ref, axis=1)]
     print("autograd opr:", " ".join(f"{v:.2e}" for v in e))
     assert max(e) < TOL_GRAD
     hist = autograd.reconstruct_adam_opr(dO, dU, dw, dPr, dpos, dI, epochs=40, lr_object=2e-2, lr_probe=2e-2,
@@ -228,9 +228,9 @@ def test_opr_batched_matches_oracle_per_reconstruction(graph):
         oprs.append(api.make_opr_opts(K, weight_step=0.8))
     losses = api.lsqml_epoch_opr_batched(recons, opts, oprs).cpu().numpy()
     for i, ((dO, dU, dw, dPr, _, _, _), (O1, U1, w1, Pr1, L1, _)) in enumerate(zip(recons, refs)):
-        e = [rel(dO.cpu().numpy(), O1), rel(dU.cpu().numpy(), U1), rel(dw.cpu().numpy(), w1),
+        e = [err(dO.cpu().numpy(), O1), err(dU.cpu().numpy(), U1, axis=0), err(dw.cpu().numpy(), w1, axis=1),
              abs(losses[i] - L1) / abs(L1)]
         if Pr1 is not None:
-            e.append(rel(dPr.cpu().numpy(), Pr1))
+            e.append(err(dPr.cpu().numpy(), Pr1, axis=0))
         print(f"opr batched[{i}] N={OPR_SHAPES[i][0]}:", " ".join(f"{x:.2e}" for x in e))
         assert max(e) < TOL_EPOCH

@@ -13,7 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
-from tests.parity_util import c64, f32pos, problem, rel, to_dev
+from tests.parity_util import c64, f32pos, problem, err, to_dev
 
 TOL_EPOCH = 1e-4   # the tolerance of the epoch parity tests
 
@@ -63,8 +63,8 @@ def test_static_scratch_epoch_matches_workspace_epoch_on_consecutive_calls():
                                          ctypes.c_void_p(alpha.data_ptr()),
                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         assert st == 0, api.status_string(st)
-        e = (rel(O.cpu().numpy(), O_ref.cpu().numpy()), rel(P.cpu().numpy(), P_ref.cpu().numpy()),
-             rel(alpha.cpu().numpy(), alpha_ref.cpu().numpy()),
+        e = (err(O.cpu().numpy(), O_ref.cpu().numpy()), err(P.cpu().numpy(), P_ref.cpu().numpy(), axis=0),
+             err(alpha.cpu().numpy(), alpha_ref.cpu().numpy(), axis=1),
              abs(loss.item() - loss_ref.item()) / abs(loss_ref.item()))
         print("static vs workspace:", e)
         assert max(e) < TOL_EPOCH
