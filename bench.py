@@ -223,26 +223,103 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
+# The amplitude data term's eps: one count. With a vanishing eps the modulus
+# projection is ill-conditioned at dark predicted pixels that hold counts
+# (from the flat start an FP32-sized perturbation of the probe moves the FP64
+# oracle's spiral128 epoch by 1.7e-3); at one count it stays near 1e-7.
+EPS = 1.0
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def oracle_sample(w, nbatch, batch, seed=5):
-    """Time the FP64 oracle on `nbatch` minibatches of the workload (its own intensities)."""
-    import numpy as np
+    """Time the FP64 oracle on `nbatch` minibatches of the workload (its own
+    intensities, Poisson-sampled from the oracle's forward model of the true
+    object): returns (patterns/s, seconds of LSQML minibatch work)."""
     from oracle import ptycho_oracle as orc
     from paper_2510_20929_gb300 import synth
     order = synth.random_order(w["J"], seed)
     idx = order[: nbatch * batch]
+    pos = w["pos"][idx]
     P = w["probe"]
-    I = orc.forward(w["object"], P, w["pos"][idx])
+    I = orc.forward(w["object"], P, pos)
     scale = counts_total(w) / (w["J"] * I.sum(axis=(1, 2)).mean())
-    Im = np.zeros((w["J"], w["N"], w["N"]))
-    Im[idx] = synth.poisson_counts(I * scale, seed)
+    Im = synth.poisson_counts(I * scale, seed)
     P = P * math.sqrt(scale)
-    O = np.ones_like(w["object"])
-    opts = orc.LsqmlOptions(batch=batch, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9)
+    O = __import__("numpy").ones_like(w["object"])
+    opts = orc.LsqmlOptions(batch=batch, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=EPS)
     t0 = time.perf_counter()
-    for b in range(nbatch):
-        O, P, _, _ = orc.lsqml_batch(O, P, w["pos"], Im, idx[b * batch:(b + 1) * batch], opts)
+    for b0 in range(0, len(idx), batch):   # (a workload smaller than the sample has fewer minibatches)
+        O, P, _, _ = orc.lsqml_batch(O, P, pos, Im, range(b0, min(b0 + batch, len(idx))), opts)
     dt = time.perf_counter() - t0
-    return nbatch * batch / dt, dt
+    return len(idx) / dt, dt
+
+
+def _oracle_worker(name, positions, nbatch, batch, seed, barrier, queue):
+    """One process of the all-cores leg: builds its sample, waits for the others, times it."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    w = make_workload(name, positions)
+    barrier.wait()
+    t0 = time.perf_counter()
+    v, dt = oracle_sample(w, nbatch, batch, seed)
+    queue.put((t0, t0 + dt, v * dt))
+
+
+def oracle_all_cores(name, positions, nbatch, batch, procs):
+    """The oracle on every host core: `procs` processes (spawned) each run
+    `nbatch` minibatches of their own sample of the workload at the same time;
+    throughput = all their positions over the span from the first start to the
+    last finish. Minibatches of one epoch depend on each other, so this is an
+    upper bound of what a split of each minibatch's positions over the cores
+    (with a reduction of the accumulators) could reach."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(name, positions, nbatch, batch, 100 + i, barrier, queue))
+          for i in range(procs)]
+    for p in ps:
+        p.start()
+    res = [queue.get(timeout=900) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+    span = max(r[1] for r in res) - min(r[0] for r in res)
+    return sum(r[2] for r in res) / span, span
+
+
+def cpu_baseline(name, positions, w, batch):
+    """Single-thread and all-cores oracle legs, with the core count and the CPU model."""
+    v1, dt1 = oracle_sample(w, 2, batch)
+    ncores = os.cpu_count() or 1
+    out = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(), "nproc": ncores,
+           "sample": f"2 LSQML minibatches of {batch} positions of {w['name']} (FP64 numpy oracle, one "
+                     f"thread), {dt1:.1f} s"}
+    try:
+        vall, span = oracle_all_cores(name, positions, 1, batch, ncores)
+        out["all_cores"] = {"value": vall, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                            "sample": f"{ncores} spawned processes, each one LSQML minibatch of {batch} positions "
+                                      f"of its own sample of {w['name']} at the same time, {span:.1f} s span "
+                                      "(an upper bound of a within-minibatch split over the cores)"}
+    except Exception as e:   # the single-thread figure stands on its own
+        out["all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"}
+    return out
 
 
 def run_reference(args, rank):
@@ -264,8 +341,9 @@ def run_reference(args, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["name"], "J": w["J"], "N": w["N"], "M": w["M"], "H": w["H"], "W": w["W"],
-                   "batch": batch},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                   "batch": batch, "eps": EPS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -313,7 +391,7 @@ def precision_comparison(api, O_true, P, pos, meas, order, B, steps, warmup, dev
     H, W = O_true.shape
     stream = torch.cuda.current_stream()
     for prec in ("fp32", "bf16x3"):
-        opts = api.make_opts(noise="gaussian", batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9,
+        opts = api.make_opts(noise="gaussian", batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=EPS,
                              precision=prec)
         O = torch.ones((H, W), dtype=torch.complex64, device=dev)
         Pe = P.clone()
@@ -339,7 +417,7 @@ def precision_comparison(api, O_true, P, pos, meas, order, B, steps, warmup, dev
                 "speedup_bf16x3_vs_fp32": res["bf16x3"]["patterns_per_s"] / res["fp32"]["patterns_per_s"],
                 "object_error_rel_diff": abs(e16 - e32) / e32,
                 "matched": abs(e16 - e32) <= 0.01 * e32,
-                "start": "unit object, true probe; Gaussian data term; same order and data"})
+                "start": "unit object, true probe; Gaussian data term, eps %g; same order and data" % EPS})
     return res
 
 
@@ -365,7 +443,7 @@ def run_ours(args, rank, world, local_rank):
     order = torch.tensor(synth.random_order(J, 5 + rank), dtype=torch.int32, device=dev)
     O = torch.ones((H, W), dtype=torch.complex64, device=dev)
     P_est = P.clone()
-    opts = api.make_opts(noise="gaussian", batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-9, autotune=True,
+    opts = api.make_opts(noise="gaussian", batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=EPS, autotune=True,
                          precision=args.precision)
     stream = torch.cuda.current_stream()
 
@@ -458,7 +536,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16x3 (f32 accumulate)",
         "data": "synthetic",
         "config": {"workload": w["name"], "J": J, "N": N, "M": M, "H": H, "W": W, "batch": B,
-                   "noise": "gaussian", "precision": args.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "noise": "gaussian", "eps": EPS, "precision": args.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (measured intensities %.0f MB read every epoch)"
                          % (J * N * N * 4 / 1e6),
                    "profiler": "CUDA event pair around every launch of the dominant kernel in every %d-th "
@@ -501,10 +579,7 @@ def run_ours(args, rank, world, local_rank):
                       "entry": "ptycho_lsqml_epoch_host (pinned host buffers)"}
 
     if rank == 0 and not args.no_cpu:
-        v, dt = oracle_sample(w, 2, B)
-        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"2 LSQML minibatches of {B} positions of {w['name']} "
-                                         f"(FP64 numpy oracle, single thread), {dt:.1f} s"}
+        out["cpu_baseline"] = cpu_baseline(args.workload, args.positions, w, B)
     if rank == 0:
         print(json.dumps(out), flush=True)
 

@@ -50,7 +50,7 @@ class DataTerm(torch.autograd.Function):
     @staticmethod
     def forward(ctx, obj, probe, pos, meas, noise="gaussian", eps=1e-9, precision="fp32"):
         obj, probe, pos, meas = obj.contiguous(), probe.contiguous(), pos.contiguous(), meas.contiguous()
-        if not (torch.is_grad_enabled() and any(ctx.needs_input_grad[:3])):
+        if not any(ctx.needs_input_grad[:3]):
             # a loss evaluation only: forward model and data term, no back-propagation
             loss, _, _, _ = api.adjoint(obj, probe, pos, meas, noise, eps=eps, batch=256, precision=precision,
                                         gradients=False)

@@ -37,6 +37,19 @@ def elem(a, b, axis=None):
                default=0.0)
 
 
+# FP32 tolerances against the FP64 oracle (as err() measures them). A
+# radix-16x8 FP32 FFT of length 128 has an rms relative error near
+# u log2(N^2) ~ 1e-6 (u = 6e-8): forward intensities are held to 1e-5. The
+# gradient factor (1 - rho) loses up to a decade to cancellation where the
+# prediction already fits the data, and an epoch compounds a few minibatches
+# of that through the preconditioned update: gradients and epoch outputs are
+# held to 3e-5 (measured at most 1.5e-5 norm-wise, 3e-5 element-wise). These
+# bars assume a well-conditioned problem; see full_epoch_bar() for the case
+# where the data term itself amplifies rounding.
+TOL_FWD = 1e-5
+TOL_GRAD = 3e-5
+TOL_EPOCH = 3e-5
+
 # The largest element-wise error admitted per unit of norm-wise tolerance. For n
 # independent rounding errors of rms s the largest is near s sqrt(2 ln n)
 # (4.3 for n = 1e4, 5.3 for n = 1e6), and max|b| is at least the rms of b, so

@@ -8,7 +8,7 @@ import pytest
 
 from oracle import ptycho_oracle as orc
 from paper_2510_20929_gb300 import synth
-from tests.parity_util import c64, f32pos, problem, err, to_dev
+from tests.parity_util import TOL_FWD, TOL_GRAD, c64, err, f32pos, problem, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +33,7 @@ def test_far_field_gradients_match_oracle_vjp():
     gO, gP, gr = orc.vjp(O, P, pos, wts)
     e = (err(dO.grad.cpu().numpy(), gO), err(dP.grad.cpu().numpy(), gP, axis=0), err(dpos.grad.cpu().numpy(), gr, axis=1))
     print("far_field grads:", e)
-    assert max(e) < 1e-4
+    assert max(e) < TOL_GRAD
 
 
 def test_data_term_gradients_match_oracle():
@@ -48,7 +48,7 @@ def test_data_term_gradients_match_oracle():
     e = (abs(loss.item() - L) / L, err(dO.grad.cpu().numpy(), 2.5 * gO), err(dP.grad.cpu().numpy(), 2.5 * gP, axis=0),
          err(dpos.grad.cpu().numpy(), 2.5 * gr, axis=1))
     print("data_term:", e)
-    assert e[0] < 1e-5 and max(e[1:]) < 1e-4
+    assert e[0] < TOL_FWD and max(e[1:]) < TOL_GRAD
 
 
 @pytest.mark.parametrize("noise", ["gaussian", "poisson"])

@@ -8,10 +8,9 @@ import pytest
 
 from oracle import ptycho_oracle as orc
 from paper_2510_20929_gb300 import synth
-from tests.parity_util import c64, f32pos, problem, err, to_dev
+from tests.parity_util import TOL_EPOCH, c64, err, f32pos, problem, to_dev
 
 pytestmark = pytest.mark.gpu
-TOL_EPOCH = 1e-4
 
 
 def _gpu_inputs(shapes):

@@ -6,10 +6,9 @@ import numpy as np
 import pytest
 
 from oracle import ptycho_oracle as orc
-from tests.parity_util import c64, f32pos, problem, err, to_dev
+from tests.parity_util import TOL_EPOCH, TOL_FWD, TOL_GRAD, c64, err, f32pos, problem, to_dev
 
 pytestmark = pytest.mark.gpu
-TOL_FWD, TOL_GRAD, TOL_EPOCH = 1e-5, 1e-4, 1e-4
 
 
 def _inputs(p):

@@ -11,6 +11,11 @@ from tests.parity_util import c64, f32pos, err, to_dev
 pytestmark = pytest.mark.gpu
 
 TOL_FWD = 1e-5
+# Each mode crosses 2S - 1 transforms in each direction (S slices) instead of
+# one, and the Poisson factor I_m/(I + eps) at eps = 1e-6 amplifies the
+# rounding of dark predicted pixels: the multislice gradients are held to
+# three times the single-slice bar (measured at most 4.6e-5, the 192 window
+# with two slices under the Poisson term).
 TOL_GRAD = 1e-4
 LAM, PX = 0.1e-9, 10e-9
 

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import ptycho_oracle as orc
-from tests.parity_util import c64, f32pos, problem, err, to_dev
+from tests.parity_util import TOL_EPOCH, TOL_FWD, TOL_GRAD, c64, err, f32pos, problem, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,7 @@ def test_gradients_cluster(noise, N):
     e = (abs(loss.item() - L) / abs(L), err(dgO.cpu().numpy(), gO), err(dgP.cpu().numpy(), gP, axis=0),
          err(dgr.cpu().numpy(), gr, axis=1))
     print(f"grad N={N} {noise}: {e}")
-    assert e[0] < 1e-5 and max(e[1:]) < 1e-4
+    assert e[0] < TOL_FWD and max(e[1:]) < TOL_GRAD
 
 
 @pytest.mark.parametrize("N", [256, 192])
@@ -58,4 +58,4 @@ def test_lsqml_epoch_cluster(N):
     e = (err(dO.cpu().numpy(), O_ref), err(dP.cpu().numpy(), P_ref, axis=0), err(alpha.cpu().numpy(), a_ref, axis=1),
          abs(loss.item() - L_ref) / abs(L_ref))
     print(f"epoch N={N}: {e}")
-    assert max(e) < 1e-4
+    assert max(e) < TOL_EPOCH

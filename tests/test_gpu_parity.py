@@ -4,13 +4,10 @@ import numpy as np
 import pytest
 
 from oracle import ptycho_oracle as orc
-from tests.parity_util import c64, f32pos, problem, err, rel, to_dev
+from tests.parity_util import TOL_EPOCH, TOL_FWD, TOL_GRAD, c64, err, f32pos, problem, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
-TOL_FWD = 1e-5      # intensities
-TOL_GRAD = 1e-4     # gradients, chi-derived quantities
-TOL_EPOCH = 1e-4    # object/probe after an epoch
 
 
 def _dev(p):

@@ -13,9 +13,8 @@ import ctypes
 import numpy as np
 import pytest
 
-from tests.parity_util import c64, f32pos, problem, err, to_dev
+from tests.parity_util import TOL_EPOCH, c64, err, f32pos, problem, to_dev
 
-TOL_EPOCH = 1e-4   # the tolerance of the epoch parity tests
 
 
 def test_static_entry_rejects_problems_beyond_its_capacity():
