@@ -18,6 +18,7 @@
 //   FP64 2x2 solve, and the alpha-weighted object scatter.
 #pragma once
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace ptycho {
 
@@ -188,12 +189,87 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
   float2* psi_s = a.psi_s ? a.psi_s + slotNN * M : nullptr;
   float2* o_s = a.o_s ? a.o_s + slotNN : nullptr;
 
+  // Tensor memory as per-thread storage (the whole pass, window 128): the
+  // patch o_j and the running sum g_j of the thread's natural-layout pixel
+  // pairs stay on chip across the modes instead of making round trips through
+  // L2. Warp w reaches TMEM lanes 32 (w % 4) ..+31; the T/128 warps sharing a
+  // lane quarter split its 512 columns, CW each: o in the first 4 STEPS
+  // columns (pair q at 4q), g in the next 4 STEPS. The CTA holds all 512
+  // columns; no other TMEM-allocating CTA fits beside it on the SM (its
+  // shared memory alone exceeds half of the SM's), so the allocation never
+  // waits.
+  constexpr bool TM = (PART == 0 && N == 128);
+  constexpr int STEPS = NatPairs<N, T>::STEPS;
+  static_assert(!TM || (STEPS % 2 == 0 && 8 * STEPS == 65536 / T), "o and g fill each warp's TMEM columns");
+  // (the base address lives in shared memory, beyond the block reductions'
+  // 160 doubles; the thread's column base is recomputed where it is used, so
+  // that no register is held across the transforms)
+  uint32_t* tm_holder = (uint32_t*)(red + 250);
+  if constexpr (TM) {
+    if ((tid >> 5) == 0) {
+      tc::tmem_alloc(tm_holder, 512);
+      tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
+  auto tm_o = [&]() -> uint32_t {   // this thread's patch columns (g follows at + 4 STEPS)
+    const int w = (int)(threadIdx.x >> 5);
+    return *tm_holder + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)((w >> 2) * (65536 / T));
+  };
+  // releases the tensor memory once every thread's TMEM accesses have completed
+  auto tm_release = [&]() {
+    if constexpr (TM) {
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(*tm_holder, 512);
+    }
+  };
+
   // ---- forward model: I_j = sum_k |F(P_k o_j)|^2 -------------------------------
 #pragma unroll 1
   for (int k = 0; k < (PART == 2 ? 0 : M); ++k) {
     const float2* Pk = shared_mode<OPR>(a, k, NN);
     // psi_k = P_k o_j into the tile, two adjacent pixels per thread and iteration
     const NatPairs<N, T> np;
+    if constexpr (TM) {
+      // groups of two pairs; the patch from TMEM after the first mode
+      const uint32_t t_o = tm_o();
+#pragma unroll 1
+      for (int qg = 0; qg < STEPS / 2; ++qg) {
+        float ov[8];
+        if (k == 0) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int q = 2 * qg + u, p = np.pix(q);
+            float2 o0, o1;
+            bilinear2(a.obj, a.W, ty + np.row(q), tx + np.c, fy, fx, o0, o1);
+            if (o_s) *(float4*)(o_s + p) = make_float4(o0.x, o0.y, o1.x, o1.y);
+            ov[4 * u] = o0.x; ov[4 * u + 1] = o0.y; ov[4 * u + 2] = o1.x; ov[4 * u + 3] = o1.y;
+          }
+          tc::tmem_st8(t_o + 8 * qg, ov);
+        } else {
+          tc::tmem_ld8_wait(t_o + 8 * qg, ov);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int q = 2 * qg + u, p = np.pix(q);
+          float4 P2;
+          if (!OPR || Pk) {
+            P2 = __ldg((const float4*)(Pk + p));
+          } else {
+            P2 = opr_pair(a.opr_U, wj, a.K, NN, p);
+            if (p0) *(float4*)(p0 + p) = P2;
+          }
+          const float2 x0 = cmul(make_float2(P2.x, P2.y), make_float2(ov[4 * u], ov[4 * u + 1]));
+          const float2 x1 = cmul(make_float2(P2.z, P2.w), make_float2(ov[4 * u + 2], ov[4 * u + 3]));
+          store_pair(tile, np.phys(q), x0, x1);
+        }
+      }
+      if (k == 0) tc::tmem_wait_st();
+    } else
 #pragma unroll 4
     for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
       const int r = np.row(q), c = np.c, p = np.pix(q);
@@ -221,28 +297,40 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
     }
     if constexpr (PART == 1) continue;
     __syncthreads();
+    // the last mode's far field stays in the tile (each row in its own line's
+    // storage, free once the row transform is done): the first inverse
+    // transform reads it there instead of from the scratch
+    const bool keep = (PART == 0) && k == M - 1 && a.mode != MODE_FWD && !a.loss_only;
     fft2_forward<N, T>(tile, tw, [&](int row, float2 (&v)[R2]) {
+#pragma unroll
+      for (int m = 0; m < R2; ++m) v[m] = cscale(v[m], invN);
       if constexpr (F::S == 2) {
-        // registers (2q, 2q+1) hold two adjacent columns: 16-byte stores
+        // registers (2q, 2q+1) hold two adjacent columns: 8-byte intensity and
+        // 16-byte far-field accesses
 #pragma unroll
         for (int q = 0; q < R2 / 2; ++q) {
-          const int col = F::out_index(n, 2 * q);
-          const float2 X0 = cscale(v[2 * q], invN), X1 = cscale(v[2 * q + 1], invN);
-          float2* ri = (float2*)(rI + row * RP + col);
-          const float2 i2 = make_float2(cabs2(X0), cabs2(X1));
+          float2* ri = (float2*)(rI + row * RP + F::out_index(n, 2 * q));
+          const float2 i2 = make_float2(cabs2(v[2 * q]), cabs2(v[2 * q + 1]));
           *ri = (k == 0) ? i2 : make_float2(ri->x + i2.x, ri->y + i2.y);
-          if (psi_s)
-            *(float4*)(psi_s + (size_t)k * NN + row * N + col) = make_float4(X0.x, X0.y, X1.x, X1.y);
         }
       } else {
 #pragma unroll
         for (int m = 0; m < R2; ++m) {
-          const int col = F::out_index(n, m);
-          const float2 X = cscale(v[m], invN);
-          const float i2 = cabs2(X);
-          float* ri = rI + row * RP + col;
-          *ri = (k == 0) ? i2 : *ri + i2;
-          if (psi_s) psi_s[(size_t)k * NN + row * N + col] = X;
+          float* ri = rI + row * RP + F::out_index(n, m);
+          *ri = (k == 0) ? cabs2(v[m]) : *ri + cabs2(v[m]);
+        }
+      }
+      if (keep) {
+        F::template store_out<true>(v, tile, row, n);
+      } else if (psi_s) {
+        if constexpr (F::S == 2) {
+#pragma unroll
+          for (int q = 0; q < R2 / 2; ++q)
+            *(float4*)(psi_s + (size_t)k * NN + row * N + F::out_index(n, 2 * q)) =
+                make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
+        } else {
+#pragma unroll
+          for (int m = 0; m < R2; ++m) psi_s[(size_t)k * NN + row * N + F::out_index(n, m)] = v[m];
         }
       }
     });
@@ -300,7 +388,10 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
       block_sum<1>(v, red);
       if (tid == 0) atomicAdd(a.loss, v[0]);
     }
-    if (mode == MODE_FWD || a.loss_only) return;
+    if (mode == MODE_FWD || a.loss_only) {
+      tm_release();
+      return;
+    }
   }
 
   // ---- back-propagation: chi_k = F^-1[fac Psi_k], g = sum_k conj(P_k) chi_k, h_k ----
@@ -316,21 +407,30 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
       fft2_inverse<N, T>(
           tile, tw,
           [&](int row, float2 (&v)[R2]) {
-            if constexpr (F::S == 2) {
+            if (k == M - 1) {   // the last mode's far field was kept in the tile
+              F::template load_out<true>(v, tile, row, n);
+              __syncwarp();     // every lane of the line has read before the exchange writes
+            } else if constexpr (F::S == 2) {
 #pragma unroll
               for (int q = 0; q < R2 / 2; ++q) {
-                const int col = F::out_index(n, 2 * q);
-                const float4 X = *(const float4*)(psi_s + (size_t)k * NN + row * N + col);
-                const float2 f = *(const float2*)(rI + row * RP + col);
-                v[2 * q] = make_float2(X.x * f.x, X.y * f.x);
-                v[2 * q + 1] = make_float2(X.z * f.y, X.w * f.y);
+                const float4 X = *(const float4*)(psi_s + (size_t)k * NN + row * N + F::out_index(n, 2 * q));
+                v[2 * q] = make_float2(X.x, X.y);
+                v[2 * q + 1] = make_float2(X.z, X.w);
               }
             } else {
 #pragma unroll
-              for (int m = 0; m < R2; ++m) {
-                const int col = F::out_index(n, m);
-                v[m] = cscale(psi_s[(size_t)k * NN + row * N + col], rI[row * RP + col]);
+              for (int m = 0; m < R2; ++m) v[m] = psi_s[(size_t)k * NN + row * N + F::out_index(n, m)];
+            }
+            if constexpr (F::S == 2) {
+#pragma unroll
+              for (int q = 0; q < R2 / 2; ++q) {
+                const float2 f = *(const float2*)(rI + row * RP + F::out_index(n, 2 * q));
+                v[2 * q] = cscale(v[2 * q], f.x);
+                v[2 * q + 1] = cscale(v[2 * q + 1], f.y);
               }
+            } else {
+#pragma unroll
+              for (int m = 0; m < R2; ++m) v[m] = cscale(v[m], rI[row * RP + F::out_index(n, m)]);
             }
           },
           [&](int col, float2 (&v)[R2]) { F::template store_in<false>(v, tile, col, n); });
@@ -339,6 +439,41 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
     // chi_k (natural layout) is in the tile, or in PART 2 in the scratch:
     // g += conj(P_k) chi_k, h_k = conj(o) chi_k
     const NatPairs<N, T> np;
+    if constexpr (TM) {
+      // o and the running g from TMEM; the last mode's g goes to the scratch
+      // (for the step sizes) and over chi in the tile (for the scatter)
+      const uint32_t t_o = tm_o(), t_g = t_o + 4 * STEPS;
+#pragma unroll 1
+      for (int qg = 0; qg < STEPS / 2; ++qg) {
+        float ov[8], gv[8];
+        if (k < M - 1)
+          tc::tmem_ld8x2_wait(t_o + 8 * qg, ov, t_g + 8 * qg, gv);
+        else
+          tc::tmem_ld8_wait(t_o + 8 * qg, ov);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int q = 2 * qg + u, p = np.pix(q);
+          float2 x0, x1;
+          load_pair(tile, np.phys(q), x0, x1);
+          const float4 P2 = (!OPR || Pk) ? __ldg((const float4*)(Pk + p)) : *(const float4*)(p0 + p);
+          float2 g0 = cmulc(make_float2(P2.x, P2.y), x0), g1 = cmulc(make_float2(P2.z, P2.w), x1);
+          if (k < M - 1) {
+            g0.x += gv[4 * u]; g0.y += gv[4 * u + 1]; g1.x += gv[4 * u + 2]; g1.y += gv[4 * u + 3];
+          }
+          const float2 h0 = cmulc(make_float2(ov[4 * u], ov[4 * u + 1]), x0);
+          const float2 h1 = cmulc(make_float2(ov[4 * u + 2], ov[4 * u + 3]), x1);
+          __stcs((float4*)(h_s + (size_t)k * NN + p), make_float4(h0.x, h0.y, h1.x, h1.y));
+          if (k > 0) {
+            gv[4 * u] = g0.x; gv[4 * u + 1] = g0.y; gv[4 * u + 2] = g1.x; gv[4 * u + 3] = g1.y;
+          } else {
+            *(float4*)(g_s + p) = make_float4(g0.x, g0.y, g1.x, g1.y);
+            store_pair(tile, np.phys(q), g0, g1);
+          }
+        }
+        if (k > 0) tc::tmem_st8(t_g + 8 * qg, gv);
+      }
+      if (k > 0) tc::tmem_wait_st();
+    } else
 #pragma unroll 2
     for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
       const int p = np.pix(q);
@@ -366,7 +501,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
   __syncthreads();
 
   // ---- scatter S_j^T g (and the illumination) into the object frame ----------------
-  {
+  if (!TM) {   // (with TMEM the last mode wrote g into the tile already)
     const NatPairs<N, T> np;
 #pragma unroll 1
     for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
@@ -434,6 +569,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
       }
     }
   }
+  tm_release();
 }
 
 
