@@ -270,6 +270,7 @@ Layout make_layout(const ptycho_dims& d, int B, int K, bool epoch_object) {
     L.gram = take((size_t)B * (OPR_KMAX * (OPR_KMAX + 1) / 2 + OPR_KMAX) * sizeof(double));   // weight-step sums
   }
   L.possum = take((size_t)B * 5 * sizeof(double));
+  L.p2part = take((size_t)B * P2_CHUNKS * 5 * sizeof(double));
   L.dOe = epoch_object ? take(HW * sizeof(float2)) : 0;
   L.dft = 0;
   switch (d.N) {
@@ -543,6 +544,7 @@ Ptrs carve(void* ws, const Layout& L) {
   p.dU = L.dU ? (float2*)(b + L.dU) : nullptr;
   p.gram = L.gram ? (double*)(b + L.gram) : nullptr;
   p.possum = (double*)(b + L.possum);
+  p.p2part = (double*)(b + L.p2part);
   p.dOe = L.dOe ? (float2*)(b + L.dOe) : nullptr;
   p.dft = L.dft ? (void*)(b + L.dft) : nullptr;
   return p;
@@ -591,6 +593,7 @@ static ptycho_status autotune(const ptycho_dims& d, float2* obj, float2* probe, 
     q.o_s = w.o; q.g_s = w.g; q.h_s = w.h; q.valid = w.valid;
     q.acc = w.acc; q.Sp = w.Sp; q.Cp = w.Cp; q.Sdp = w.Sdp; q.dP = w.dP;
     q.obj = w.psi;  // stand-in object: the far-field scratch
+    q.part = w.p2part;
     q.sc = sc;
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
@@ -662,7 +665,7 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
     q.pos = pos; q.order = order; q.b0 = b0; q.nb = nb;
     q.o_s = w.o; q.g_s = w.g; q.h_s = w.h; q.valid = w.valid;
     q.acc = w.acc; q.Sp = w.Sp; q.Cp = w.Cp; q.Sdp = w.Sdp; q.dP = w.dP;
-    q.obj = o.object_per_epoch ? w.dOe : obj; q.alpha_out = alpha; q.sc = sc;
+    q.obj = o.object_per_epoch ? w.dOe : obj; q.alpha_out = alpha; q.sc = sc; q.part = w.p2part;
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
     if ((e = pass2(N, q, s, tune.v2)) != cudaSuccess) return PTYCHO_ERR_CUDA;

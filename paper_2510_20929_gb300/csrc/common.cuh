@@ -105,7 +105,13 @@ struct Pass2Args {
   const float* opr_w;   // [J, K]
   int K;
   const float2* p0_s;   // [B, N, N] primary mode of each slot
+  // Split form (k_pass2_sums + k_pass2_update): partial sums of the five
+  // step-size terms per slot and chunk, FP64 [B, P2_CHUNKS, 5]; null selects
+  // the single-kernel form.
+  double* part;
 };
+
+constexpr int P2_CHUNKS = 8;   // chunks of a position's pixels and h planes in the split step-size pass
 
 // Arguments of the multislice per-position pass (kernels_ms.cuh).
 struct MsArgs {

@@ -14,6 +14,7 @@ struct Layout {
   size_t hdr, acc, psi, o, g, h, dPacc, Dp, dP, Sp, Cp, Sdp, valid;
   size_t p0, dUacc, Du, dU, gram;   // orthogonal probe relaxation (K > 0) only
   size_t possum;                     // position-correction sums [B, 5] (FP64)
+  size_t p2part;                     // partial step-size sums [B, P2_CHUNKS, 5] (FP64)
   size_t dOe;                        // epoch object accumulator [H, W] (object_per_epoch) or 0
   size_t dft;                        // DFT-matrix chunks of the split-BF16 DFT-GEMM (N <= 128) or 0
   size_t total;
@@ -30,6 +31,7 @@ struct Ptrs {
   float* Du;
   double* gram;
   double* possum;
+  double* p2part;
   float2* dOe;
   void* dft;
 };

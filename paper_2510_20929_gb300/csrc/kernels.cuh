@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
 
 
 // CTA sizes of the step-size pass (default, alternative).
-constexpr int PASS2_T = 512, PASS2_ALT = 256;
+constexpr int PASS2_T = 512;
 
 // Bilinear sample of dO_hat = dO_acc / (illum + damp) at the patch pixel whose
 // four corners start at q (the quotient is taken per corner, then interpolated).
@@ -712,6 +712,166 @@ __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
   }
 }
 
+// Split form of the step-size pass. The five sums of a position are
+// independent over its pixels and its h planes, so k_pass2_sums spreads them
+// over P2_CHUNKS CTAs per position (every CTA a pure stream of 16-byte loads,
+// many CTAs per SM); each writes its FP64 partials without atomics, and
+// k_pass2_update adds a position's partials in chunk order (the result does
+// not depend on scheduling), solves the 2x2 system and scatters the object
+// update.
+constexpr int PASS2S_T = 256, PASS2U_T = 512;
+
+template <int N, bool OPR>
+__global__ void __launch_bounds__(PASS2S_T, 3) k_pass2_sums(Pass2Args a) {
+  constexpr int NN = N * N, T = PASS2S_T, C = P2_CHUNKS;
+  static_assert(NN % (2 * C) == 0, "chunks of pixel pairs");
+  wait_prior_grid();
+  __shared__ double red[32 * 5];
+  __shared__ float wsh[OPR_KMAX];
+  const int chunk = blockIdx.x, slot = blockIdx.y, tid = threadIdx.x;
+  double* out = a.part + ((size_t)slot * C + chunk) * 5;
+  if (!a.valid[slot]) {
+    if (tid < 5) out[tid] = 0.0;
+    return;
+  }
+  const int e = a.b0 + slot;
+  const int j = a.order ? a.order[e] : e;
+  int ty, tx;
+  float fy, fx;
+  tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
+  const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
+  const float damp = a.delta_o * __uint_as_float(a.sc->max_illum);
+  const size_t slotNN = (size_t)slot * NN;
+  const int M = a.M;
+  const float2* g_s = a.g_s + slotNN;
+  const float2* o_s = a.o_s + slotNN;
+  const float2* h_s = a.h_s + slotNN * M;
+  if (OPR) {
+    if (tid < a.K) wsh[tid] = a.opr_w[(size_t)j * a.K + tid];
+    __syncthreads();
+  }
+  const float2* p0 = OPR ? a.p0_s + slotNN : nullptr;
+
+  // pixels [p_lo, p_hi) of the patch
+  const int p_lo = chunk * (NN / C), p_hi = p_lo + NN / C;
+  float A11 = 0.f, A12 = 0.f, A22 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll 1
+  for (int p = p_lo + tid; p < p_hi; p += T) {
+    const int r = p / N, c = p % N;
+    const float2 g = __ldcs(g_s + p);
+    const float2 o = __ldcs(o_s + p);
+    float2 d = make_float2(0.f, 0.f);
+    if (a.update_object) d = dohat(a.acc + (size_t)(ty + r) * a.W + (tx + c), a.W, w00, w01, w10, w11, damp);
+    float sp = __ldg(a.Sp + p), sdp = __ldg(a.Sdp + p);
+    float2 cp = __ldg(a.Cp + p);
+    if (OPR) {
+      const float2 P0 = p0[p];
+      sp += cabs2(P0);
+      if (a.update_probe) {
+        const float2 d0 = opr_pixel(a.opr_dU, wsh, a.K, NN, p);
+        cp = cadd(cp, cmulc(P0, d0));
+        sdp += cabs2(d0);
+        const float2 h0 = __ldcs(h_s + p);
+        b2 += d0.x * h0.x + d0.y * h0.y;     // Re(conj(dP_j0) h_j0)
+      }
+    }
+    A11 += cabs2(d) * sp;
+    const float2 od = cmulc(d, o);           // conj(d) o
+    A12 += od.x * cp.x - od.y * cp.y;        // Re(conj(d) o Cp)
+    A22 += cabs2(o) * sdp;
+    b1 += d.x * g.x + d.y * g.y;             // Re(conj(d) g)
+  }
+  if (a.update_probe) {
+    // b2 over this chunk of the shared modes' h planes (contiguous pixel pairs)
+    const float4* h4 = (const float4*)(h_s + (OPR ? NN : 0));
+    const float4* d4 = (const float4*)a.dP;
+    const int Q = (OPR ? M - 1 : M) * NN / 2;
+    const int q_lo = (int)((long long)Q * chunk / C), q_hi = (int)((long long)Q * (chunk + 1) / C);
+    int q = q_lo + tid;
+    for (; q + 3 * T < q_hi; q += 4 * T) {      // four independent 16-byte streams per thread
+      float4 dp[4], h[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        dp[u] = __ldg(d4 + q + u * T);
+        h[u] = __ldcs(h4 + q + u * T);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) b2 += dp[u].x * h[u].x + dp[u].y * h[u].y + dp[u].z * h[u].z + dp[u].w * h[u].w;
+    }
+    for (; q < q_hi; q += T) {
+      const float4 dp = __ldg(d4 + q);
+      const float4 h = __ldcs(h4 + q);
+      b2 += dp.x * h.x + dp.y * h.y + dp.z * h.z + dp.w * h.w;   // Re(conj(dP_k) h_k)
+    }
+  }
+  double v[5] = {A11, A12, A22, b1, b2};
+  block_sum<5>(v, red);
+  if (tid == 0)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) out[i] = v[i];
+}
+
+template <int N>
+__global__ void __launch_bounds__(PASS2U_T, 2) k_pass2_update(Pass2Args a) {
+  constexpr int T = PASS2U_T, C = P2_CHUNKS;
+  wait_prior_grid();
+  __shared__ double alpha_sh;
+  const int slot = blockIdx.x, tid = threadIdx.x;
+  if (!a.valid[slot]) return;
+  const int e = a.b0 + slot;
+  const int j = a.order ? a.order[e] : e;
+  if (tid == 0) {
+    const double* pp = a.part + (size_t)slot * C * 5;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) v[i] += pp[c * 5 + i];
+    const double a11 = v[0], a12 = v[1], a22 = v[2], r1 = v[3], r2 = v[4];
+    const double tr = 0.5 * (a11 + a22);
+    const double d11 = a11 + a.lam * tr, d22 = a22 + a.lam * tr;
+    const double det = d11 * d22 - a12 * a12;
+    double aO, aP;
+    if (det > 0.0) {
+      aO = (d22 * r1 - a12 * r2) / det;
+      aP = (d11 * r2 - a12 * r1) / det;
+    } else {
+      aO = d11 > 0.0 ? r1 / d11 : 0.0;
+      aP = d22 > 0.0 ? r2 / d22 : 0.0;
+    }
+    alpha_sh = aO;
+    if (a.alpha_out) {
+      a.alpha_out[2 * j] = aO;
+      a.alpha_out[2 * j + 1] = aP;
+    }
+    atomicAdd(&a.sc->sum_alpha_p, aP);
+    atomicAdd(&a.sc->count, 1);
+  }
+  __syncthreads();
+  if (!a.update_object) return;
+  int ty, tx;
+  float fy, fx;
+  tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
+  const float damp = a.delta_o * __uint_as_float(a.sc->max_illum);
+  const float2* g_s = a.g_s + (size_t)slot * N * N;
+  const float aO = (float)alpha_sh;
+  const float c00 = aO * (1.f - fy) * (1.f - fx), c01 = aO * (1.f - fy) * fx;
+  const float c10 = aO * fy * (1.f - fx), c11 = aO * fy * fx;
+  constexpr int N1 = N + 1;
+  // O += alpha_O S_j^T g / (illum + delta_O): each object pixel of the (N+1)^2
+  // tile gathers its four patch neighbours, divided by its own preconditioner
+  for (int q = tid; q < N1 * N1; q += T) {
+    const int y = q / N1, x = q % N1;
+    float2 sacc = make_float2(0.f, 0.f);
+    if (y < N && x < N) { const float2 g = g_s[y * N + x]; sacc.x += c00 * g.x; sacc.y += c00 * g.y; }
+    if (y < N && x > 0) { const float2 g = g_s[y * N + x - 1]; sacc.x += c01 * g.x; sacc.y += c01 * g.y; }
+    if (y > 0 && x < N) { const float2 g = g_s[(y - 1) * N + x]; sacc.x += c10 * g.x; sacc.y += c10 * g.y; }
+    if (y > 0 && x > 0) { const float2 g = g_s[(y - 1) * N + x - 1]; sacc.x += c11 * g.x; sacc.y += c11 * g.y; }
+    const size_t oi = (size_t)(ty + y) * a.W + (tx + x);
+    const float inv = 1.f / (__ldg(&a.acc[oi].z) + damp);
+    atomicAdd(a.obj + oi, make_float2(sacc.x * inv, sacc.y * inv));
+  }
+}
+
 }  // namespace ptycho
 
 namespace ptycho {
@@ -749,11 +909,19 @@ cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s, int variant) {
                       : launch_pass1_t<N, Threads<N>::T, false>(a, s);
 }
 
+// variant 0: the split form (when the partials buffer is given), 1: the
+// single-kernel form of PASS2_T threads
 template <int N>
 cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s, int variant) {
   if (a.nb <= 0) return cudaSuccess;
+  if (a.part && variant == 0) {
+    cudaError_t e = a.opr_dU
+        ? launch_pdl(k_pass2_sums<N, true>, dim3(P2_CHUNKS, a.nb), dim3(PASS2S_T), 0, s, a)
+        : launch_pdl(k_pass2_sums<N, false>, dim3(P2_CHUNKS, a.nb), dim3(PASS2S_T), 0, s, a);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_pass2_update<N>, dim3(a.nb), dim3(PASS2U_T), 0, s, a);
+  }
   if (a.opr_dU) return launch_pdl(k_pass2<N, PASS2_T, true>, dim3(a.nb), dim3(PASS2_T), 0, s, a);
-  if (variant == 1) return launch_pdl(k_pass2<N, PASS2_ALT, false>, dim3(a.nb), dim3(PASS2_ALT), 0, s, a);
   return launch_pdl(k_pass2<N, PASS2_T, false>, dim3(a.nb), dim3(PASS2_T), 0, s, a);
 }
 

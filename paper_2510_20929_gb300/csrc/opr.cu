@@ -409,7 +409,7 @@ ptycho_status run_epoch_opr(const ptycho_dims& d, const ptycho_opr_opts& r, floa
     q.obj = obj; q.alpha_out = alpha; q.sc = sc;
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
-    q.opr_dU = w.dU; q.opr_w = wts; q.K = K; q.p0_s = w.p0;
+    q.opr_dU = w.dU; q.opr_w = wts; q.K = K; q.p0_s = w.p0; q.part = w.p2part;
     if (pass2(N, q, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if (r.update_weights && opr_weights(N, M, K, nb, b0, order, w.valid, U, w.h, w.o, wts, nullptr, w.gram,
                                         o.lambda_reg, (float)r.weight_step, s) != cudaSuccess)

@@ -143,3 +143,23 @@ def test_probe_damping_from_the_illumination_is_caught(monkeypatch):
     wrong = _rewritten(orc.lsqml_batch, "opts.delta_p * float(np.max(Dp))", "opts.delta_p * float(np.max(illum))")
     monkeypatch.setattr(orc, "lsqml_batch", wrong)
     _fails(pins.test_probe_only_update_has_the_closed_form_of_a_known_object, 1)
+
+
+def test_multislice_lsqml_backpropagation_with_the_forward_propagator_is_caught(monkeypatch):
+    wrong = _rewritten(orc.lsqml_batch_ms, "chi = propagate(chi, Hc)", "chi = propagate(chi, Hf)")
+    monkeypatch.setattr(orc, "lsqml_batch_ms", wrong)
+    _fails(pins.test_multislice_lsqml_accumulators_are_multiples_of_the_finite_difference_gradients,
+           orc.GAUSSIAN, -0.5)
+
+
+def test_multislice_lsqml_backpropagation_without_the_slice_conjugate_is_caught(monkeypatch):
+    wrong = _rewritten(orc.lsqml_batch_ms, "chi = np.conj(o[s])[None] * chi", "chi = o[s][None] * chi")
+    monkeypatch.setattr(orc, "lsqml_batch_ms", wrong)
+    _fails(pins.test_multislice_lsqml_accumulators_are_multiples_of_the_finite_difference_gradients,
+           orc.GAUSSIAN, -0.5)
+
+
+def test_multislice_lsqml_probe_damping_from_the_last_slice_is_caught(monkeypatch):
+    wrong = _rewritten(orc.lsqml_batch_ms, "Dp += np.abs(o[0]) ** 2", "Dp += np.abs(o[-1]) ** 2")
+    monkeypatch.setattr(orc, "lsqml_batch_ms", wrong)
+    _fails(pins.test_multislice_probe_only_update_has_the_closed_form_of_a_known_object)

@@ -648,3 +648,121 @@ def test_probe_only_update_has_the_closed_form_of_a_known_object(n_pos):
     assert np.allclose(alpha[:, 1], a, rtol=1e-10, atol=0) and np.all(alpha[:, 0] == 0.0)
     assert np.max(np.abs(P_new - ref)) < 1e-12 * np.max(np.abs(P))
     assert np.array_equal(O_new, O)
+
+
+# --------------------------------------------------------------------------- multislice LSQML
+def test_multislice_lsqml_with_one_slice_is_the_single_slice_minibatch():
+    Os, P, pos, Hf, I_m = _ms_problem(S=1)
+    g = np.random.default_rng(23)
+    Os = Os * (1 + 0.1 * crandn(g, *Os.shape))
+    for noise in (orc.GAUSSIAN, orc.POISSON):
+        opts = orc.LsqmlOptions(noise=noise, batch=4, eps=1e-3, delta_o=0.1, delta_p=0.1)
+        O1, P1, L1, a1 = orc.lsqml_batch_ms(Os, P, pos, I_m, range(4), Hf, opts)
+        O0, P0, L0, a0 = orc.lsqml_batch(Os[0], P, pos, I_m, range(4), opts)
+        assert np.max(np.abs(O1[0] - O0)) < 1e-13 and np.max(np.abs(P1 - P0)) < 1e-13
+        assert abs(L1 - L0) <= 1e-12 * abs(L0) and np.max(np.abs(a1 - a0)) <= 1e-12 * np.max(np.abs(a0))
+
+
+@pytest.mark.parametrize("noise,factor", [(orc.GAUSSIAN, -0.5), (orc.POISSON, -0.25)])
+def test_multislice_lsqml_accumulators_are_multiples_of_the_finite_difference_gradients(noise, factor):
+    # every slice's accumulator is its exit-plane change back-projected through
+    # the slices after it; against the finite-difference-pinned multislice
+    # gradients it is -1/2 (amplitude term) or -1/4 (Poisson half step) of the
+    # slice's gradient, and the probe accumulator likewise
+    Os, P, pos, Hf, I_m = _ms_problem(S=3)
+    opts = orc.LsqmlOptions(noise=noise, batch=4, eps=1e-3)
+    rec = {}
+    orc.lsqml_batch_ms(Os, P, pos, I_m, range(4), Hf, opts, rec)
+    _, gO, gP, _ = orc.loss_and_gradients_ms(Os, P, pos, Hf, I_m, noise, 1e-3)
+    for s in range(3):
+        assert np.max(np.abs(rec["dO_acc"][s] - factor * gO[s])) < 1e-10 * np.max(np.abs(gO[s]))
+    assert np.max(np.abs(rec["dP_acc"] - factor * gP)) < 1e-10 * np.max(np.abs(gP))
+
+
+def test_multislice_lsqml_step_sizes_solve_each_slices_least_squares_problem():
+    # slice 0 with the probe: numpy's least squares on the stacked real system of
+    # the slice-0 exit-plane change; slice s >= 1: the 1x1 fit of its own
+    # exit-plane change by dO_s(r_j) times its incident wave (lam = 0)
+    Os, P, pos, Hf, I_m = _ms_problem(S=3)
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=4, eps=1e-3, lam=0.0, delta_o=0.1, delta_p=0.1)
+    rec = {}
+    _, _, _, alpha = orc.lsqml_batch_ms(Os, P, pos, I_m, range(4), Hf, opts, rec)
+    for j in range(4):
+        _, inc, o = orc.exit_waves_ms(Os, P, pos[j], Hf)
+        chis = rec["chi"][j]
+        u = (orc.extract(rec["dO_hat"][0], pos[j], 8)[None] * P).ravel()
+        v = (o[0][None] * rec["dP"]).ravel()
+        A = np.concatenate([np.stack([u.real, v.real], 1), np.stack([u.imag, v.imag], 1)])
+        b = np.concatenate([chis[0].ravel().real, chis[0].ravel().imag])
+        ref = np.linalg.lstsq(A, b, rcond=None)[0]
+        assert np.max(np.abs(alpha[j, [0, 3]] - ref)) < 1e-8 * np.max(np.abs(ref))
+        for s in (1, 2):
+            us = (orc.extract(rec["dO_hat"][s], pos[j], 8)[None] * inc[s]).ravel()
+            A1 = np.concatenate([us.real, us.imag])[:, None]
+            b1 = np.concatenate([chis[s].ravel().real, chis[s].ravel().imag])
+            assert abs(alpha[j, s] - np.linalg.lstsq(A1, b1, rcond=None)[0][0]) < 1e-9 * abs(alpha[j, s])
+
+
+def test_multislice_lsqml_exit_plane_changes_are_the_propagated_differences():
+    # the last slice's change is psi' - psi of the exit wave; each earlier
+    # slice's is the adjoint propagation of conj(o_s) times the later one,
+    # written out with numpy's FFT
+    Os, P, pos, Hf, I_m = _ms_problem(S=2, M=1)
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=4, eps=1e-3)
+    rec = {}
+    orc.lsqml_batch_ms(Os, P, pos, I_m, range(4), Hf, opts, rec)
+    psi, inc, o = orc.exit_waves_ms(Os, P, pos[0], Hf)
+    Psi = np.fft.fft2(psi[0]) / 8
+    new = np.fft.ifft2(Psi * np.sqrt(I_m[0]) / np.sqrt(np.abs(Psi) ** 2 + 1e-3)) * 8
+    assert np.max(np.abs(rec["chi"][0][1][0] - (new - psi[0]))) < 1e-12
+    back = np.fft.ifft2(np.conj(Hf) * np.fft.fft2(np.conj(o[1]) * (new - psi[0])))
+    assert np.max(np.abs(rec["chi"][0][0][0] - back)) < 1e-12
+
+
+def test_multislice_lsqml_truth_is_fixed_and_noiseless_loss_falls():
+    Os, P, pos, Hf, _ = _ms_problem(S=2, seed=29)
+    I_t = orc.forward_ms(Os, P, pos, Hf)
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=2, eps=1e-12, delta_o=0.1, delta_p=0.1)
+    O1, P1, L1, _ = orc.lsqml_epoch_ms(Os, P, pos, I_t, np.arange(4), Hf, opts)
+    assert L1 < 1e-18 and np.max(np.abs(O1 - Os)) < 1e-9 and np.max(np.abs(P1 - P)) < 1e-9
+    g = np.random.default_rng(31)
+    O = Os * (1 + 0.05 * crandn(g, *Os.shape))
+    losses = []
+    for _ in range(8):
+        O, _, L, _ = orc.lsqml_epoch_ms(O, P, pos, I_t, np.arange(4), Hf,
+                                        orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=2, eps=1e-12, delta_o=0.1,
+                                                         update_probe=False))
+        losses.append(L)
+    assert losses[-1] < 0.1 * losses[0]
+
+
+def test_multislice_probe_only_update_has_the_closed_form_of_a_known_object():
+    # one position at an integer offset, two slices held fixed: the probe moves
+    # by alpha_P dP with dP = conj(o_0) chi_0 / (|o_0|^2 + delta_p max|o_0|^2),
+    # chi_0 the exit-plane change carried back through slice 1 and the
+    # propagator, alpha_P the 1x1 fit against chi_0; written out on the crops
+    g = np.random.default_rng(37)
+    N, H, W = 16, 30, 30
+    P_true = synth.hg_probe(N, np.array([1.0, 0.4]), waist=N / 5.0, quad_phase=0.03) * 3.0
+    Os = np.stack([synth.make_object(H, W, 5, phase_sigma=1.0), synth.make_object(H, W, 6, phase_sigma=1.0)])
+    Hf = orc.asm_propagator(N, 10e-9, 0.1e-9, 2e-6)
+    r = np.array([[15.0, 14.0]])
+    I_m = orc.forward_ms(Os, P_true, r, Hf)
+    P = P_true * (1 + 0.2 * crandn(g, *P_true.shape))
+    dp = 5e-2
+    opts = orc.LsqmlOptions(noise=orc.GAUSSIAN, batch=1, delta_p=dp, lam=0.0, eps=0.0, update_object=False)
+    O_new, P_new, _, alpha = orc.lsqml_batch_ms(Os, P, r, I_m, [0], Hf, opts)
+    o0, o1 = Os[0, 7:23, 6:22], Os[1, 7:23, 6:22]
+    inc1 = np.fft.ifft2(Hf * np.fft.fft2(P * o0[None]))
+    psi = inc1 * o1[None]
+    Psi = np.fft.fft2(psi) / N
+    I = np.sum(np.abs(Psi) ** 2, axis=0)
+    chi1 = np.fft.ifft2(Psi * np.sqrt(I_m[0] / I)[None]) * N - psi
+    chi0 = np.fft.ifft2(np.conj(Hf) * np.fft.fft2(np.conj(o1)[None] * chi1))
+    Dp = np.abs(o0) ** 2
+    d = np.conj(o0)[None] * chi0 / (Dp + dp * Dp.max())[None]
+    v = o0[None] * d
+    a = np.real(np.vdot(v, chi0)) / np.real(np.vdot(v, v))
+    assert abs(alpha[0, 2] - a) < 1e-10 * abs(a) and np.all(alpha[0, :2] == 0.0)
+    assert np.max(np.abs(P_new - (P + a * d))) < 1e-12 * np.max(np.abs(P))
+    assert np.array_equal(O_new, Os)
