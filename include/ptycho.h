@@ -377,6 +377,31 @@ ptycho_status ptycho_adjoint_ms(const ptycho_dims* dims, const ptycho_multislice
                                 double eps, int32_t batch, float* g_object, float* g_probe, float* g_pos,
                                 double* loss, void* ws, size_t ws_bytes, void* stream);
 
+/* One LSQML epoch with a multislice object (Sec. 1 and Sec. 2.1: multislice
+ * modelling as a forward-model option of every reconstructor; LSQML, Sec.
+ * 2.2), updating `object` ([S, H, W]) and `probe` in place. Per position the
+ * exit-plane change chi = F^-1[(rho - 1) Psi] of the last slice is carried
+ * back through the slices (adjoint propagation, times conj of each slice's
+ * patch); every slice s gets the direction numerator sum_k conj(inc_sk) chi_sk
+ * and the illumination sum_k |inc_sk|^2 of its incident waves, its own
+ * object-frame preconditioner (damping delta_o times its maximum) and its own
+ * least-squares step at its exit plane: slice 0 shares the 2x2 system of
+ * ptycho_lsqml_epoch with the probe (direction conj(o_0) chi_0 / (sum |o_0|^2
+ * + delta_p max)), slices 1..S-1 have 1x1 fits damped by (1 + lambda). With
+ * S = 1 this is ptycho_lsqml_epoch. alpha: float64 [J, S + 1] (the slices'
+ * alpha_O, then alpha_P) or NULL. opts as for ptycho_lsqml_epoch, except that
+ * precision BF16X3, update_positions and object_per_epoch return
+ * PTYCHO_ERR_UNSUPPORTED (PTYCHO_FLAG_AUTOTUNE has no variants to choose
+ * here). Workspace: ptycho_workspace_bytes_lsqml_ms(dims, ms, opts); the
+ * incident waves are kept there as for the adjoint, plus S accumulator
+ * planes [S, H, W] of 16 bytes and the slices' illumination per slot. */
+size_t ptycho_workspace_bytes_lsqml_ms(const ptycho_dims* dims, const ptycho_multislice* ms,
+                                        const ptycho_lsqml_opts* opts);
+ptycho_status ptycho_lsqml_epoch_ms(const ptycho_dims* dims, const ptycho_multislice* ms, float* object,
+                                    float* probe, const float* pos, const float* meas, const int32_t* order,
+                                    const ptycho_lsqml_opts* opts, double* loss, double* alpha, void* ws,
+                                    size_t ws_bytes, void* stream);
+
 /* Minibatch samplers (Sec. 2.1: random, uniform and compact batches).
  * Writes `order` (int32 [J], a permutation of 0..J-1) for the epoch entry
  * points, whose consecutive chunks of `batch` entries are the minibatches.

@@ -90,6 +90,9 @@ def lib() -> ctypes.CDLL:
                                                  _P]),
             "ptycho_adjoint_ms": (ctypes.c_int, [dims_p, ms_p, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double,
                                                  ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+            "ptycho_workspace_bytes_lsqml_ms": (ctypes.c_size_t, [dims_p, ms_p, opts_p]),
+            "ptycho_lsqml_epoch_ms": (ctypes.c_int, [dims_p, ms_p, _P, _P, _P, _P, _P, opts_p, _P, _P, _P,
+                                                     ctypes.c_size_t, _P]),
             "ptycho_workspace_bytes_opr": (ctypes.c_size_t, [dims_p, ctypes.c_int32, ctypes.c_int32]),
             "ptycho_forward_opr": (ctypes.c_int, [dims_p, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P,
                                                   ctypes.c_size_t, _P]),
@@ -657,3 +660,31 @@ def adjoint_ms(obj, probe, pos, meas, ms: Multislice, noise="gaussian", eps: flo
            "ptycho_adjoint_ms")
     _finish(ws, "ptycho_adjoint_ms", check)
     return (None if nz == VJP else loss), gO, gP, gr
+
+
+def lsqml_epoch_ms(obj, probe, pos, meas, order, ms: Multislice, opts: LsqmlOpts | None = None, *,
+                   want_alpha: bool = False, check: bool = True, **kw):
+    """One LSQML epoch with a multislice object (slices [S, H, W]), updating
+    ``obj`` and ``probe`` in place. Returns (loss, alpha): alpha is a float64
+    [J, S + 1] device tensor (each slice's alpha_O, then alpha_P) or None."""
+    if opts is None:
+        opts = make_opts(**kw)
+    d = _ms_dims(obj, probe, pos, ms)
+    _need(meas, "meas", torch.float32, (d.J, d.N, d.N), device=obj.device)
+    if order is not None:
+        _need(order, "order", torch.int32, (d.J,), device=obj.device)
+    need = lib().ptycho_workspace_bytes_lsqml_ms(ctypes.byref(d), ctypes.byref(ms), ctypes.byref(opts))
+    if need == 0:
+        raise PtychoError(6, "workspace_bytes_lsqml_ms")
+    key = (str(obj.device), "lsqml_ms")
+    ws = _ws_cache.get(key)
+    if ws is None or ws.nbytes < need:
+        ws = Workspace(need, obj.device)
+        _ws_cache[key] = ws
+    loss = torch.zeros((), dtype=torch.float64, device=obj.device)
+    alpha = torch.zeros((d.J, ms.S + 1), dtype=torch.float64, device=obj.device) if want_alpha else None
+    _check(lib().ptycho_lsqml_epoch_ms(ctypes.byref(d), ctypes.byref(ms), _ptr(obj), _ptr(probe), _ptr(pos),
+                                       _ptr(meas), _ptr(order), ctypes.byref(opts), _ptr(loss), _ptr(alpha),
+                                       _P(ws.ptr), ws.nbytes, _stream()), "ptycho_lsqml_epoch_ms")
+    _finish(ws, "ptycho_lsqml_epoch_ms", check)
+    return loss, alpha

@@ -46,7 +46,7 @@ template <int U>
 __global__ void k_probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* __restrict__ h_s,
                                const float2* __restrict__ o_s, const int* __restrict__ valid, float2* dPacc,
                                int accumulate, float* Dp, const float4* __restrict__ acc, int HW,
-                               BatchScalars* sc) {
+                               BatchScalars* sc, int o_stride) {
   __shared__ float red[32];
   wait_prior_grid();
   if (blockIdx.y == 1) {
@@ -84,12 +84,13 @@ __global__ void k_probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const flo
     *out = s;
   } else if (k == Mc && Dp) {
     const float4* o = (const float4*)o_s + q;
+    const size_t ostep = o_stride ? (size_t)o_stride / 2 : (size_t)NP;   // float4 per slot
     float2 d = make_float2(0.f, 0.f);
     for (int i = 0; i < nb; i += U) {
       float4 v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        v[u] = (i + u < nb && valid[i + u]) ? __ldg(o + (size_t)(i + u) * NP) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[u] = (i + u < nb && valid[i + u]) ? __ldg(o + (size_t)(i + u) * ostep) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         d.x += v[u].x * v[u].x + v[u].y * v[u].y;
@@ -435,7 +436,7 @@ static float time_launch(cudaStream_t s, int reps, F&& launch) {
 
 cudaError_t probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* h_s, const float2* o_s,
                          const int* valid, float2* dPacc, int accumulate, float* Dp, const float4* acc, int HW,
-                         BatchScalars* sc, cudaStream_t s) {
+                         BatchScalars* sc, cudaStream_t s, int o_stride) {
   cudaEvent_t e0 = profile_begin(K_PROBE_REDUCE, s);
   const int NP = NN / 2;
   const int threads = (dPacc ? Mc * NP : 0) + (Dp ? NP : 0);
@@ -443,7 +444,7 @@ cudaError_t probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* h
   if (acc && bx < 2 * sm_count()) bx = 2 * sm_count();
   dim3 grid(bx > 0 ? bx : 1, acc ? 2 : 1);
   const cudaError_t e = launch_pdl(k_probe_reduce<16>, grid, dim3(256), 0, s, NN, k0, Mc, Ms, nb, h_s, o_s, valid,
-                                   dPacc, accumulate, Dp, acc, HW, sc);
+                                   dPacc, accumulate, Dp, acc, HW, sc, o_stride);
   profile_end(K_PROBE_REDUCE, e0, s);
   return e;
 }

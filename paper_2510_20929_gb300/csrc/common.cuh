@@ -134,6 +134,13 @@ struct MsArgs {
   float* gpos;          // [J, 2] or null
   double* loss;
   int* status;
+  // LSQML (MODE_LSQML_*): minibatch order (null: identity), the per-slice
+  // object-frame accumulators, each slice's illumination sum_k |inc|^2 per
+  // slot (slices 1..S-1; slice 0 uses Sp = sum_k |P_k|^2)
+  const int* order;
+  float4* acc;          // [S, H, W] (dO_acc.re, dO_acc.im, illum, unused)
+  float* w_s;           // [B, S - 1, N, N]
+  const float* Sp;      // [N, N]
 };
 
 constexpr int OPR_KMAX = 8;   // eigenmodes of the relaxed primary probe mode

@@ -66,7 +66,10 @@ __device__ __forceinline__ void propagate_tile(float2* tile, const float2* tw, c
   __syncthreads();
 }
 
-template <int N, int T>
+// LS: the LSQML instantiation (exit-plane changes instead of gradients, the
+// slices' illumination, the per-slice accumulators); the gradient form has
+// none of it.
+template <int N, int T, bool LS>
 __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
   using F = Fft2<N>;
   using SM = Pass1Smem<N>;
@@ -79,7 +82,8 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
 
   const int slot = blockIdx.x;
   const int tid = threadIdx.x, n = F::line_lane();
-  const int j = a.b0 + slot;
+  const int e = a.b0 + slot;
+  const int j = a.order ? a.order[e] : e;
   int ty = 0, tx = 0;
   float fy = 0.f, fx = 0.f;
   bool ok = (j >= 0 && j < a.J);
@@ -100,6 +104,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
   const size_t slotNN = (size_t)slot * NN;
   const int mode = a.mode;
   const bool grad = mode != MODE_FWD;
+  constexpr bool lsqml = LS;
   float2* psi_s = grad ? a.psi_s + slotNN * M : nullptr;
   float2* o_s = a.o_s + slotNN * S;
   const NatPairs<N, T> np;
@@ -132,12 +137,23 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
     for (int s = 1; s < S; ++s) {
       propagate_tile<N, T, false>(tile, tw, a.Hf);
       float2* inc = grad ? a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN) : nullptr;
+      // LSQML: the slice's illumination sum_k |inc_k|^2
+      float2* wsl = lsqml ? (float2*)(a.w_s + (slotNN * (S - 1) + (size_t)(s - 1) * NN)) : nullptr;
 #pragma unroll 2
       for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
         const int p = np.pix(q);
         float2 x0, x1;
         load_pair(tile, np.phys(q), x0, x1);
         if (grad) *(float4*)(inc + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        if (lsqml) {
+          float2 w2 = make_float2(cabs2(x0), cabs2(x1));
+          if (k > 0) {
+            const float2 wp = wsl[p / 2];
+            w2.x += wp.x;
+            w2.y += wp.y;
+          }
+          wsl[p / 2] = w2;
+        }
         const float4 o2 = *(const float4*)(o_s + (size_t)s * NN + p);
         store_pair(tile, np.phys(q), cmul(x0, make_float2(o2.x, o2.y)), cmul(x1, make_float2(o2.z, o2.w)));
       }
@@ -182,13 +198,15 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
         } else {
           bad |= !(Im >= 0.f) || !isfinite(Im);
           const float Ie = I + eps;
-          if (mode == MODE_GRAD_GAUSS) {
+          if (mode == MODE_GRAD_GAUSS || mode == MODE_LSQML_GAUSS) {
             const float sIe = sqrtf(Ie), sIm = sqrtf(Im), d = sIe - sIm;
             lsum = fmaf(d, d, lsum);
-            fac = 2.f * (1.f - sIm / sIe);
+            const float rho = sIm / sIe;
+            fac = (mode == MODE_LSQML_GAUSS) ? rho - 1.f : 2.f * (1.f - rho);
           } else {
             lsum += I - Im * logf(Ie);
-            fac = 2.f * (1.f - Im / Ie);
+            const float qq = Im / Ie;
+            fac = (mode == MODE_LSQML_POISSON) ? 0.5f * (qq - 1.f) : 2.f * (1.f - qq);
           }
         }
         rI[row * RP + col] = fac * invN;
@@ -279,6 +297,19 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
       store_pair(tile, np.phys(q), make_float2(g2.x, g2.y), make_float2(g2.z, g2.w));
     }
     __syncthreads();
+    if (lsqml) {   // S_j^T of the slice's direction numerator and of its illumination
+      float4* acc = a.acc + s * HW;
+      const float* wsl = s > 0 ? a.w_s + (slotNN * (S - 1) + (size_t)(s - 1) * NN) : a.Sp;
+      bilinear_scatter<N, T>(
+          fy, fx,
+          [&](int y, int x) {
+            const float2 g = tile[tix<N>(y, x)];
+            return make_float4(g.x, g.y, wsl[y * N + x], 0.f);
+          },
+          [&](int y, int x, float4 v) {
+            atomicAdd(acc + (size_t)(ty + y) * a.W + (tx + x), make_float4(v.x, v.y, v.z, 0.f));
+          });
+    }
     if (a.gobj) {
       float2* gplane = a.gobj + s * HW;
       bilinear_scatter<N, T>(
@@ -322,11 +353,15 @@ template <int N>
 cudaError_t launch_pass1_ms(const MsArgs& a, cudaStream_t s) {
   constexpr int T = N == 128 ? 512 : Threads<N>::T;
   constexpr size_t sm = Pass1Smem<N>::bytes;
-  static unsigned long long done = 0;
-  cudaError_t e = smem_optin(k_pass1_ms<N, T>, sm, &done);
+  static unsigned long long done = 0, done_ls = 0;
+  const bool ls = a.mode == MODE_LSQML_GAUSS || a.mode == MODE_LSQML_POISSON;
+  cudaError_t e = ls ? smem_optin(k_pass1_ms<N, T, true>, sm, &done_ls) : smem_optin(k_pass1_ms<N, T, false>, sm, &done);
   if (e != cudaSuccess) return e;
   if (a.nb <= 0) return cudaSuccess;
-  k_pass1_ms<N, T><<<a.nb, T, sm, s>>>(a);
+  if (ls)
+    k_pass1_ms<N, T, true><<<a.nb, T, sm, s>>>(a);
+  else
+    k_pass1_ms<N, T, false><<<a.nb, T, sm, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -35,7 +35,8 @@ __device__ __forceinline__ void propagate_cluster(cg::cluster_group& cluster, fl
   inv2d<C>(cluster, tile, twr, twc, twn, twq, q);
 }
 
-template <class C>
+// LS: the LSQML instantiation (as in k_pass1_ms).
+template <class C, bool LS>
 __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
   constexpr int N = C::N, Q = C::Q, T = C::T, LR = C::LR, NN = C::NN, LNN = C::LNN;
   constexpr int NAT_STEPS = C::NAT_STEPS;
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
   const int q = (int)cluster.block_rank();
   const int slot = blockIdx.x / Q;
   const int tid = threadIdx.x;
-  const int j = a.b0 + slot;
+  const int j = a.order ? a.order[a.b0 + slot] : a.b0 + slot;
   int ty = 0, tx = 0;
   float fy = 0.f, fx = 0.f;
   bool ok = (j >= 0 && j < a.J);
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
 
   const int M = a.M, S = a.S, mode = a.mode;
   const bool grad = mode != MODE_FWD;
+  constexpr bool lsqml = LS;
   const size_t HW = (size_t)a.H * a.W;
   const float invN = 1.0f / (float)N;
   const size_t slotNN = (size_t)slot * NN;
@@ -119,6 +121,8 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
     for (int s = 1; s < S; ++s) {
       propagate_cluster<C, false>(cluster, tile, twr, twc, twn, twq, q, a.Hf);
       float2* inc = grad ? a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN) : nullptr;
+      // LSQML: the slice's illumination sum_k |inc_k|^2
+      float2* wsl = lsqml ? (float2*)(a.w_s + (slotNN * (S - 1) + (size_t)(s - 1) * NN)) : nullptr;
 #pragma unroll 2
       for (int st = 0; st < NAT_STEPS; ++st) {
         const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
@@ -126,6 +130,15 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
         float2 x0, x1;
         load_pair(tile, C::tix(r, c), x0, x1);
         if (grad) *(float4*)(inc + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        if (lsqml) {
+          float2 w2 = make_float2(cabs2(x0), cabs2(x1));
+          if (k > 0) {
+            const float2 wp = wsl[p / 2];
+            w2.x += wp.x;
+            w2.y += wp.y;
+          }
+          wsl[p / 2] = w2;
+        }
         const float4 o2 = *(const float4*)(o_s + (size_t)s * NN + p);
         store_pair(tile, C::tix(r, c), cmul(x0, make_float2(o2.x, o2.y)), cmul(x1, make_float2(o2.z, o2.w)));
       }
@@ -169,13 +182,15 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
       } else {
         bad |= !(Im >= 0.f) || !isfinite(Im);
         const float Ie = I + eps;
-        if (mode == MODE_GRAD_GAUSS) {
+        if (mode == MODE_GRAD_GAUSS || mode == MODE_LSQML_GAUSS) {
           const float sIe = sqrtf(Ie), sIm = sqrtf(Im), d = sIe - sIm;
           lsum = fmaf(d, d, lsum);
-          fac = 2.f * (1.f - sIm / sIe);
+          const float rho = sIm / sIe;
+          fac = (mode == MODE_LSQML_GAUSS) ? rho - 1.f : 2.f * (1.f - rho);
         } else {
           lsum += I - Im * logf(Ie);
-          fac = 2.f * (1.f - Im / Ie);
+          const float qq = Im / Ie;
+          fac = (mode == MODE_LSQML_POISSON) ? 0.5f * (qq - 1.f) : 2.f * (1.f - qq);
         }
       }
       ri[u] = fac * invN;
@@ -266,6 +281,43 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
 #pragma unroll 1
   for (int s = 0; s < S; ++s) {
     const float2* gsl = go_s + (size_t)s * NN;
+    if (lsqml) {   // S_j^T of the slice's direction numerator and of its illumination
+      float4* acc = a.acc + s * HW;
+      const float* wsl = s > 0 ? a.w_s + (slotNN * (S - 1) + (size_t)(s - 1) * NN) : a.Sp;
+      auto hrow4 = [&](int y, int x) {
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (y >= 0 && y < N) {
+          if (x < N) {
+            const float2 v = gsl[y * N + x];
+            const float w = wsl[y * N + x];
+            h = make_float4(gx * v.x, gx * v.y, gx * w, 0.f);
+          }
+          if (x > 0) {
+            const float2 v = gsl[y * N + x - 1];
+            const float w = wsl[y * N + x - 1];
+            h.x = fmaf(fx, v.x, h.x);
+            h.y = fmaf(fx, v.y, h.y);
+            h.z = fmaf(fx, w, h.z);
+          }
+        }
+        return h;
+      };
+      constexpr int SEG = T / N1 > 0 ? T / N1 : 1;
+      const int rows = y1 - y0, rs = (rows + SEG - 1) / SEG;
+      for (int item = tid; item < N1 * SEG; item += T) {
+        const int sg = item / N1, x = item % N1;
+        const int ya = y0 + sg * rs, yb = min(y1, ya + rs);
+        if (ya >= yb) continue;
+        float4 hp = hrow4(ya - 1, x);
+        for (int y = ya; y < yb; ++y) {
+          const float4 hc = hrow4(y, x);
+          atomicAdd(acc + (size_t)(ty + y) * a.W + (tx + x),
+                    make_float4(fmaf(gy, hc.x, fy * hp.x), fmaf(gy, hc.y, fy * hp.y), fmaf(gy, hc.z, fy * hp.z),
+                                0.f));
+          hp = hc;
+        }
+      }
+    }
     if (a.gobj) {
       float2* gplane = a.gobj + s * HW;
       auto hrow = [&](int y, int x) {
@@ -326,9 +378,9 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
 
 }  // namespace cl
 
-template <class C>
-cudaError_t launch_ms_cluster(const MsArgs& a, cudaStream_t s, unsigned long long* done) {
-  cudaError_t e = smem_optin(cl::k_pass1_ms_cluster<C>, C::Smem::bytes, done);
+template <class C, bool LS>
+cudaError_t launch_ms_cluster_t(const MsArgs& a, cudaStream_t s, unsigned long long* done) {
+  cudaError_t e = smem_optin(cl::k_pass1_ms_cluster<C, LS>, C::Smem::bytes, done);
   if (e != cudaSuccess) return e;
   if (a.nb <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
@@ -343,7 +395,14 @@ cudaError_t launch_ms_cluster(const MsArgs& a, cudaStream_t s, unsigned long lon
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, cl::k_pass1_ms_cluster<C>, a);
+  return cudaLaunchKernelEx(&cfg, cl::k_pass1_ms_cluster<C, LS>, a);
+}
+
+// done[0]: the gradient form's shared-memory opt-in, done[1]: the LSQML form's
+template <class C>
+cudaError_t launch_ms_cluster(const MsArgs& a, cudaStream_t s, unsigned long long* done) {
+  if (a.mode == MODE_LSQML_GAUSS || a.mode == MODE_LSQML_POISSON) return launch_ms_cluster_t<C, true>(a, s, done + 1);
+  return launch_ms_cluster_t<C, false>(a, s, done);
 }
 
 }  // namespace ptycho

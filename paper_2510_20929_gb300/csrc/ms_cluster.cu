@@ -7,14 +7,14 @@ namespace ptycho {
 
 template <>
 cudaError_t launch_pass1_ms<256>(const MsArgs& a, cudaStream_t s) {
-  static unsigned long long done = 0;
-  return launch_ms_cluster<cl::Cfg256>(a, s, &done);
+  static unsigned long long done[2] = {0, 0};
+  return launch_ms_cluster<cl::Cfg256>(a, s, done);
 }
 
 template <>
 cudaError_t launch_pass1_ms<192>(const MsArgs& a, cudaStream_t s) {
-  static unsigned long long done = 0;
-  return launch_ms_cluster<cl::Cfg192>(a, s, &done);
+  static unsigned long long done[2] = {0, 0};
+  return launch_ms_cluster<cl::Cfg192>(a, s, done);
 }
 
 }  // namespace ptycho

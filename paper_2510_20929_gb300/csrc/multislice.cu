@@ -12,6 +12,7 @@
 #include "internal.h"
 #include "launch.h"
 #include "profile.h"
+#include "kernels.cuh"
 
 namespace ptycho {
 
@@ -86,6 +87,187 @@ cudaError_t pass1_ms(int N, const MsArgs& a, cudaStream_t s) {
     case 256: e = launch_pass1_ms<256>(a, s); break;
   }
   profile_end(K_PASS1_MS, e0, s);
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// LSQML with a multislice object. Per slice s the exit-plane change carried
+// back through the slices gives the direction numerator g_js (go_s) and the
+// illumination sum_k |inc_jsk|^2 (w_s; slice 0: Sp); every slice has its own
+// object-frame accumulator and preconditioner damping; slice 0 shares the 2x2
+// step-size system with the probe, later slices have 1x1 fits.
+// ---------------------------------------------------------------------------
+struct MsLsqmlLayout {
+  MsLayout base;
+  size_t acc, w, dPacc, Dp, dP, Sp, Cp, Sdp, smax, total;
+};
+
+MsLsqmlLayout ms_lsqml_layout(const ptycho_dims& d, int S, int B) {
+  MsLsqmlLayout L;
+  L.base = ms_layout(d, S, B);
+  size_t off = L.base.total;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  const size_t NN = (size_t)d.N * d.N, M = d.M, HW = (size_t)d.H * d.W;
+  L.acc = take((size_t)S * HW * sizeof(float4));
+  L.w = take((size_t)B * (S > 1 ? S - 1 : 0) * NN * sizeof(float));
+  L.dPacc = take(M * NN * sizeof(float2));
+  L.Dp = take(NN * sizeof(float));
+  L.dP = take(M * NN * sizeof(float2));
+  L.Sp = take(NN * sizeof(float));
+  L.Cp = take(NN * sizeof(float2));
+  L.Sdp = take(NN * sizeof(float));
+  L.smax = take(16 * sizeof(unsigned int));
+  L.total = off;
+  return L;
+}
+
+struct MsPass2Args {
+  int H, W, M, J, S;
+  const float* pos;
+  const int* order;
+  int b0, nb;
+  const float2* o_s;          // [B, S, N, N]
+  const float2* go_s;         // [B, S, N, N] direction numerators
+  const float2* h_s;          // [B, M, N, N]
+  const float* w_s;           // [B, S - 1, N, N]
+  const int* valid;
+  const float4* acc;          // [S, H, W]
+  const unsigned int* smax;   // [S] float bits of each slice's maximum illumination
+  const float* Sp;
+  const float2* Cp;
+  const float* Sdp;
+  const float2* dP;
+  float2* obj;                // [S, H, W], updated in place
+  double* alpha_out;          // [J, S + 1] or null
+  BatchScalars* sc;
+  float delta_o;
+  double lam;
+  int update_object, update_probe;
+};
+
+// max over the illumination component of each slice's accumulator
+__global__ void k_ms_illum_max(size_t HW, const float4* __restrict__ acc, unsigned int* smax) {
+  __shared__ float red[32];
+  const float4* a = acc + (size_t)blockIdx.y * HW;
+  float m = 0.f;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < HW; p += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, __ldcs(&a[p].z));
+  m = block_max(m, red);
+  if (threadIdx.x == 0) atomicMax(smax + blockIdx.y, __float_as_uint(m));
+}
+
+// One CTA per (position, slice): the step-size sums of the slice (slice 0 with
+// the probe, as k_pass2), the FP64 solve and the slice's object update.
+template <int N>
+__global__ void __launch_bounds__(512, 1) k_pass2_ms(MsPass2Args a) {
+  constexpr int NN = N * N, T = 512;
+  __shared__ double red[32 * 5];
+  __shared__ double alpha_sh;
+  const int slot = blockIdx.x, s = blockIdx.y, tid = threadIdx.x, S = a.S;
+  if (!a.valid[slot]) return;
+  const int e = a.b0 + slot;
+  const int j = a.order ? a.order[e] : e;
+  int ty, tx;
+  float fy, fx;
+  tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
+  const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
+  const size_t HW = (size_t)a.H * a.W;
+  const float4* acc = a.acc + s * HW;
+  const float damp = a.delta_o * __uint_as_float(a.smax[s]);
+  const float2* g_s = a.go_s + ((size_t)slot * S + s) * NN;
+  const float2* o0 = a.o_s + (size_t)slot * S * NN;
+  const float* wsl = s > 0 ? a.w_s + ((size_t)slot * (S - 1) + (s - 1)) * NN : a.Sp;
+  float A11 = 0.f, A12 = 0.f, A22 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll 1
+  for (int p = tid; p < NN; p += T) {
+    const int r = p / N, c = p % N;
+    const float2 g = __ldcs(g_s + p);
+    float2 d = make_float2(0.f, 0.f);
+    if (a.update_object) d = dohat(acc + (size_t)(ty + r) * a.W + (tx + c), a.W, w00, w01, w10, w11, damp);
+    A11 += cabs2(d) * __ldg(wsl + p);
+    b1 += d.x * g.x + d.y * g.y;             // Re(conj(d) g)
+    if (s == 0) {
+      const float2 o = __ldg(o0 + p);
+      const float2 od = cmulc(d, o);
+      const float2 cp = __ldg(a.Cp + p);
+      A12 += od.x * cp.x - od.y * cp.y;      // Re(conj(d) o Cp)
+      A22 += cabs2(o) * __ldg(a.Sdp + p);
+    }
+  }
+  if (s == 0 && a.update_probe) {
+    const float4* h4 = (const float4*)(a.h_s + (size_t)slot * a.M * NN);
+    const float4* d4 = (const float4*)a.dP;
+    const int Q = a.M * NN / 2;
+    for (int q = tid; q < Q; q += T) {
+      const float4 dp = __ldg(d4 + q);
+      const float4 h = __ldcs(h4 + q);
+      b2 += dp.x * h.x + dp.y * h.y + dp.z * h.z + dp.w * h.w;   // Re(conj(dP_k) h_k)
+    }
+  }
+  double v[5] = {A11, A12, A22, b1, b2};
+  block_sum<5>(v, red);
+  if (tid == 0) {
+    double aO = 0.0, aP = 0.0;
+    const double a11 = v[0], a12 = v[1], a22 = v[2], r1 = v[3], r2 = v[4];
+    if (s == 0) {
+      const double tr = 0.5 * (a11 + a22);
+      const double d11 = a11 + a.lam * tr, d22 = a22 + a.lam * tr;
+      const double det = d11 * d22 - a12 * a12;
+      if (det > 0.0) {
+        aO = (d22 * r1 - a12 * r2) / det;
+        aP = (d11 * r2 - a12 * r1) / det;
+      } else {
+        aO = d11 > 0.0 ? r1 / d11 : 0.0;
+        aP = d22 > 0.0 ? r2 / d22 : 0.0;
+      }
+      atomicAdd(&a.sc->sum_alpha_p, aP);
+      atomicAdd(&a.sc->count, 1);
+      if (a.alpha_out) a.alpha_out[(size_t)j * (S + 1) + S] = aP;
+    } else {
+      const double d11 = a11 * (1.0 + a.lam);
+      aO = d11 > 0.0 ? r1 / d11 : 0.0;
+    }
+    if (a.alpha_out) a.alpha_out[(size_t)j * (S + 1) + s] = aO;
+    alpha_sh = aO;
+  }
+  __syncthreads();
+  if (!a.update_object) return;
+  const float aO = (float)alpha_sh;
+  const float c00 = aO * w00, c01 = aO * w01, c10 = aO * w10, c11 = aO * w11;
+  float2* obj = a.obj + s * HW;
+  constexpr int N1 = N + 1;
+  for (int q = tid; q < N1 * N1; q += T) {
+    const int y = q / N1, x = q % N1;
+    float2 sacc = make_float2(0.f, 0.f);
+    if (y < N && x < N) { const float2 g = g_s[y * N + x]; sacc.x += c00 * g.x; sacc.y += c00 * g.y; }
+    if (y < N && x > 0) { const float2 g = g_s[y * N + x - 1]; sacc.x += c01 * g.x; sacc.y += c01 * g.y; }
+    if (y > 0 && x < N) { const float2 g = g_s[(y - 1) * N + x]; sacc.x += c10 * g.x; sacc.y += c10 * g.y; }
+    if (y > 0 && x > 0) { const float2 g = g_s[(y - 1) * N + x - 1]; sacc.x += c11 * g.x; sacc.y += c11 * g.y; }
+    const size_t oi = (size_t)(ty + y) * a.W + (tx + x);
+    const float inv = 1.f / (__ldg(&acc[oi].z) + damp);
+    atomicAdd(obj + oi, make_float2(sacc.x * inv, sacc.y * inv));
+  }
+}
+
+cudaError_t pass2_ms(int N, const MsPass2Args& a, cudaStream_t s) {
+  if (a.nb <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)a.nb, (unsigned)a.S);
+  cudaEvent_t e0 = profile_begin(K_PASS2, s);
+  switch (N) {
+    case 16: k_pass2_ms<16><<<grid, 512, 0, s>>>(a); break;
+    case 32: k_pass2_ms<32><<<grid, 512, 0, s>>>(a); break;
+    case 64: k_pass2_ms<64><<<grid, 512, 0, s>>>(a); break;
+    case 128: k_pass2_ms<128><<<grid, 512, 0, s>>>(a); break;
+    case 192: k_pass2_ms<192><<<grid, 512, 0, s>>>(a); break;
+    case 256: k_pass2_ms<256><<<grid, 512, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  const cudaError_t e = cudaGetLastError();
+  profile_end(K_PASS2, e0, s);
   return e;
 }
 
@@ -177,6 +359,92 @@ ptycho_status ptycho_adjoint_ms(const ptycho_dims* dims, const ptycho_multislice
       return PTYCHO_ERR_CUDA;
   }
   return PTYCHO_OK;
+}
+
+size_t ptycho_workspace_bytes_lsqml_ms(const ptycho_dims* dims, const ptycho_multislice* ms,
+                                        const ptycho_lsqml_opts* opts) {
+  if (check_ms(dims, ms) != PTYCHO_OK || check_opts(opts) != PTYCHO_OK) return 0;
+  return ms_lsqml_layout(*dims, ms->S, opts->batch).total;
+}
+
+ptycho_status ptycho_lsqml_epoch_ms(const ptycho_dims* dims, const ptycho_multislice* ms, float* object, float* probe,
+                                    const float* pos, const float* meas, const int32_t* order,
+                                    const ptycho_lsqml_opts* opts, double* loss, double* alpha, void* ws,
+                                    size_t ws_bytes, void* stream) {
+  ptycho_status st = check_ms(dims, ms);
+  if (st != PTYCHO_OK) return st;
+  if ((st = check_opts(opts)) != PTYCHO_OK) return st;
+  if (opts->precision != PTYCHO_PRECISION_FP32 || opts->update_positions || opts->object_per_epoch)
+    return PTYCHO_ERR_UNSUPPORTED;
+  if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
+  const MsLsqmlLayout L = ms_lsqml_layout(*dims, ms->S, opts->batch);
+  if ((st = check_ws(ws, ws_bytes, L.total)) != PTYCHO_OK) return st;
+  auto body = [&](cudaStream_t s) -> ptycho_status {
+    const ptycho_dims& d = *dims;
+    const int S = ms->S, B = opts->batch, M = d.M, NN = d.N * d.N;
+    const size_t HW = (size_t)d.H * d.W;
+    char* b = (char*)ws;
+    WsHeader* hdr = (WsHeader*)ws;
+    float4* acc = (float4*)(b + L.acc);
+    float2* dPacc = (float2*)(b + L.dPacc);
+    float* Dp = (float*)(b + L.Dp);
+    float2* dP = (float2*)(b + L.dP);
+    float* Sp = (float*)(b + L.Sp);
+    float2* Cp = (float2*)(b + L.Cp);
+    float* Sdp = (float*)(b + L.Sdp);
+    unsigned int* smax = (unsigned int*)(b + L.smax);
+    MsArgs a;
+    cudaError_t e = cudaSuccess;
+    ms_setup(d, *ms, B, ws, a, s, &e);
+    if (e != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if (loss && cudaMemsetAsync(loss, 0, sizeof(double), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if (cudaMemsetAsync(acc, 0, (size_t)S * HW * sizeof(float4), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if (init_epoch(NN, M, (const float2*)probe, Sp, hdr, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    a.obj = (const float2*)object; a.probe = (const float2*)probe; a.pos = pos; a.meas = meas; a.order = order;
+    a.mode = opts->noise == PTYCHO_NOISE_POISSON ? MODE_LSQML_POISSON : MODE_LSQML_GAUSS;
+    a.eps = (float)opts->eps;
+    a.loss = loss;
+    a.acc = acc;
+    a.w_s = (float*)(b + L.w);
+    a.Sp = Sp;
+    const int nbatch = (d.J + B - 1) / B;
+    for (int bi = 0; bi < nbatch; ++bi) {
+      BatchScalars* sc = &hdr->sc[bi & 1];
+      BatchScalars* sc_next = &hdr->sc[(bi + 1) & 1];
+      a.b0 = bi * B;
+      a.nb = (d.J - a.b0 < B) ? d.J - a.b0 : B;
+      if (pass1_ms(d.N, a, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+      if (probe_reduce(NN, 0, M, M, a.nb, a.h_s, a.o_s, a.valid, opts->update_probe ? dPacc : nullptr, 0,
+                       opts->update_probe ? Dp : nullptr, nullptr, 0, sc, s, S * NN) != cudaSuccess)
+        return PTYCHO_ERR_CUDA;
+      if (cudaMemsetAsync(smax, 0, (size_t)S * sizeof(unsigned int), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+      k_ms_illum_max<<<dim3((unsigned)grid_for(HW, 256, 2 * sm_count()), (unsigned)S), 256, 0, s>>>(HW, acc, smax);
+      if (cudaGetLastError() != cudaSuccess) return PTYCHO_ERR_CUDA;
+      if (norm_probe(NN, M, dPacc, Dp, (const float2*)probe, (float)opts->delta_p, opts->update_probe, sc, dP, Cp,
+                     Sdp, s) != cudaSuccess)
+        return PTYCHO_ERR_CUDA;
+      MsPass2Args q;
+      memset(&q, 0, sizeof(q));
+      q.H = d.H; q.W = d.W; q.M = M; q.J = d.J; q.S = S;
+      q.pos = pos; q.order = order; q.b0 = a.b0; q.nb = a.nb;
+      q.o_s = a.o_s; q.go_s = a.go_s; q.h_s = a.h_s; q.w_s = a.w_s; q.valid = a.valid;
+      q.acc = acc; q.smax = smax; q.Sp = Sp; q.Cp = Cp; q.Sdp = Sdp; q.dP = dP;
+      q.obj = (float2*)object; q.alpha_out = alpha; q.sc = sc;
+      q.delta_o = (float)opts->delta_o; q.lam = opts->lambda_reg;
+      q.update_object = opts->update_object; q.update_probe = opts->update_probe;
+      if (pass2_ms(d.N, q, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+      if (clear_acc(false, ptycho_dims{(int32_t)(S * d.H), d.W, d.N, d.M, d.J}, a.nb, a.b0, pos, order, a.valid, acc,
+                    s) != cudaSuccess)
+        return PTYCHO_ERR_CUDA;
+      if (probe_update(NN, M, (float2*)probe, dP, Sp, opts->update_probe, sc, sc_next, s) != cudaSuccess)
+        return PTYCHO_ERR_CUDA;
+    }
+    return PTYCHO_OK;
+  };
+  if (!(opts->flags & PTYCHO_FLAG_GRAPH)) return body((cudaStream_t)stream);
+  GraphKey key;
+  key.add(*dims).add(*ms).add(object).add(probe).add(pos).add(meas).add(order).add(*opts).add(loss).add(alpha).add(ws);
+  return run_graphed(key, (cudaStream_t)stream, body);
 }
 
 }  // extern "C"

@@ -115,3 +115,74 @@ def test_multislice_autograd_and_adam():
     hist = autograd.reconstruct_adam_ms(dO, dP, dpos, dI, ms, epochs=40, lr_object=2e-2, update=("object",))
     print("adam ms:", hist[0], hist[-1])
     assert hist[-1] < 0.5 * hist[0]
+
+
+# ----------------------------------------------------------------------------- LSQML
+def _lsqml_ms_case(N, M, S, H, W, J, step, dz, batch, noise, update_probe=True, seed=7):
+    import torch
+    from paper_2510_20929_gb300 import api
+    Os, P, pos, Hf, I_m = ms_problem(N, M, S, H, W, J, step, dz, seed=seed)
+    dO, dP, dpos, dI = _dev(Os, P, pos, I_m)
+    order = np.random.default_rng(seed).permutation(J).astype(np.int32)
+    nz = orc.GAUSSIAN if noise == "gaussian" else orc.POISSON
+    kw = dict(batch=batch, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6, update_probe=update_probe)
+    O_ref, P_ref, L_ref, a_ref = orc.lsqml_epoch_ms(Os, P, pos, I_m, order, Hf, orc.LsqmlOptions(noise=nz, **kw))
+    loss, alpha = api.lsqml_epoch_ms(dO, dP, dpos, dI, to_dev(order, torch.int32), api.make_multislice(S, dz, LAM, PX),
+                                     noise=noise, want_alpha=True, **kw)
+    e = dict(O=err(dO.cpu().numpy(), O_ref, axis=0), P=err(dP.cpu().numpy(), P_ref, axis=0),
+             alpha=err(alpha.cpu().numpy(), a_ref, axis=1), loss=abs(loss.item() - L_ref) / abs(L_ref))
+    print(f"lsqml_ms N={N} M={M} S={S} B={batch} {noise}: " + " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    return e
+
+
+@pytest.mark.parametrize("noise", ["gaussian", "poisson"])
+@pytest.mark.parametrize("N,M,S,H,W,J,step,dz,batch", [
+    (16, 2, 3, 41, 37, 9, 3.0, 40e-6, 4),       # ragged minibatches (4, 4, 1)
+    (32, 1, 2, 72, 76, 12, 6.0, 10e-6, 12),
+    (64, 3, 2, 150, 160, 10, 12.0, 4e-6, 5),
+    (128, 2, 3, 290, 300, 6, 30.0, 2e-6, 4),
+    (192, 1, 2, 230, 236, 4, 12.0, 2e-6, 3),
+    (256, 2, 2, 290, 296, 3, 12.0, 2e-6, 2),
+])
+def test_lsqml_epoch_ms_matches_oracle(N, M, S, H, W, J, step, dz, batch, noise):
+    e = _lsqml_ms_case(N, M, S, H, W, J, step, dz, batch, noise)
+    assert e["loss"] < TOL_FWD
+    assert max(e["O"], e["P"], e["alpha"]) < TOL_GRAD
+
+
+def test_lsqml_epoch_ms_object_only_and_one_slice_equals_the_single_slice_epoch():
+    import torch
+    from paper_2510_20929_gb300 import api
+    e = _lsqml_ms_case(32, 2, 2, 72, 76, 12, 6.0, 10e-6, 5, "gaussian", update_probe=False)
+    assert max(e["O"], e["alpha"]) < TOL_GRAD and e["P"] == 0.0
+    # one slice: the multislice epoch computes what the single-slice epoch computes
+    Os, P, pos, Hf, I_m = ms_problem(32, 2, 1, 72, 76, 12, 6.0, 10e-6)
+    d1 = _dev(Os, P, pos, I_m)
+    d0 = _dev(Os, P, pos, I_m)
+    kw = dict(batch=5, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6)
+    l1, a1 = api.lsqml_epoch_ms(*d1, None, api.make_multislice(1, 10e-6, LAM, PX), want_alpha=True, **kw)
+    l0, a0 = api.lsqml_epoch(d0[0][0], d0[1], d0[2], d0[3], None, want_alpha=True, **kw)
+    assert err(d1[0][0].cpu().numpy(), d0[0][0].cpu().numpy()) < 1e-6
+    assert err(d1[1].cpu().numpy(), d0[1].cpu().numpy(), axis=0) < 1e-6
+    assert err(a1.cpu().numpy(), a0.cpu().numpy(), axis=1) < 1e-6
+    assert abs(l1.item() - l0.item()) < 1e-6 * abs(l0.item())
+
+
+def test_lsqml_epoch_ms_graph_replay_equals_eager_and_rejects_unsupported_options():
+    import torch
+    from paper_2510_20929_gb300 import api
+    Os, P, pos, Hf, I_m = ms_problem(64, 2, 3, 150, 160, 10, 12.0, 4e-6)
+    ms = api.make_multislice(3, 4e-6, LAM, PX)
+    outs = []
+    for graph in (False, True, True):
+        dO, dP, dpos, dI = _dev(Os, P, pos, I_m)
+        loss, _ = api.lsqml_epoch_ms(dO, dP, dpos, dI, None, ms, api.make_opts(batch=4, graph=graph))
+        outs.append((dO.cpu().numpy(), dP.cpu().numpy(), loss.item()))
+    for O1, P1, L1 in outs[1:]:
+        assert err(O1, outs[0][0], axis=0) < 1e-6 and err(P1, outs[0][1], axis=0) < 1e-6
+        assert abs(L1 - outs[0][2]) < 1e-6 * abs(outs[0][2])
+    dO, dP, dpos, dI = _dev(Os, P, pos, I_m)
+    for bad in (dict(precision="bf16x3"), dict(update_positions=True), dict(object_per_epoch=True)):
+        with pytest.raises(api.PtychoError) as ex:
+            api.lsqml_epoch_ms(dO, dP, dpos, dI, None, ms, api.make_opts(batch=4, **bad))
+        assert ex.value.status == 6
