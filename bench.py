@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["spiral128", "raster64", "uneven16", "uneven16opr", "spiral256", "multislice256"], default="spiral128")
+    ap.add_argument("--workload", choices=["spiral128", "raster64", "uneven16", "uneven16opr", "spiral256", "multislice256",
+                                           "multislice256-lsqml"], default="spiral128")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
@@ -663,6 +664,17 @@ def run_uneven(args, rank, world, local_rank, opr_K=0):
     ms_b = timed(lambda: batched(o_eager), args.steps)
     ms_g = timed(lambda: batched(o_graph), args.steps)
     checked()
+    # each reconstruction's epoch alone: its minibatches form a dependency chain
+    # (each reads the object and probe the previous one wrote), so the longest
+    # of these bounds any schedule that runs the reconstructions together
+    alone = []
+    for i, o in enumerate(o_eager):
+        if opr_K:
+            r = recons[i]
+            alone.append(timed(lambda: api.lsqml_epoch_opr(*r[:6], r[6], o, oprs, check=False), 1))
+        else:
+            O, P, pos, meas, order = recons[i]
+            alone.append(timed(lambda: api.lsqml_epoch(O, P, pos, meas, order, o, check=False), 1))
     ms_max = max_over_ranks(ms_g, world, dev)
     if rank == 0:
         print(json.dumps({
@@ -675,6 +687,8 @@ def run_uneven(args, rank, world, local_rank, opr_K=0):
                        "opr_eigenmodes": opr_K},
             "batched_graph_ms": ms_g, "batched_eager_ms": ms_b, "sequential_ms": ms_seq,
             "speedup_vs_sequential": ms_seq / ms_g,
+            "alone_ms": alone, "longest_chain_ms": max(alone),
+            "batched_over_longest_chain": ms_g / max(alone),
         }), flush=True)
 
 
@@ -803,6 +817,63 @@ def run_ms256(args, rank, world, local_rank):
         }), flush=True)
 
 
+def run_ms256_lsqml(args, rank, world, local_rank):
+    """Multislice LSQML: 4 slices of 2048^2, probe 256^2 with 4 modes, 8000
+    positions, minibatches of 512; a step is one LSQML epoch over all positions
+    (per-slice directions and step sizes), from flat slices and the true probe."""
+    import torch
+    from paper_2510_20929_gb300 import api, synth
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = synth.workload_multislice256()
+    if args.positions and args.positions < w["J"]:   # profiling runs: the first positions only
+        w["pos"], w["J"] = w["pos"][:args.positions], args.positions
+    ms = api.make_multislice(w["S"], w["dz"], w["wavelength"], w["pixel_size"])
+    Os_true = torch.tensor(w["slices"], dtype=torch.complex64, device=dev)
+    P = torch.tensor(w["probe"], dtype=torch.complex64, device=dev)
+    pos = torch.tensor(w["pos"], dtype=torch.float32, device=dev)
+    I0 = api.forward_ms(Os_true, P, pos, ms, batch=w["batch"])
+    scale = w["total_counts"] / I0.sum(dim=(1, 2)).mean().item()
+    P *= math.sqrt(scale)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(103 + rank)
+    meas = torch.poisson(I0 * scale, generator=gen)
+    del I0, Os_true
+    order = torch.tensor(synth.random_order(w["J"], 9 + rank), dtype=torch.int32, device=dev)
+    Os = torch.ones((w["S"],) + tuple(w["slices"].shape[1:]), dtype=torch.complex64, device=dev)
+    Pe = P.clone()
+    opts = api.make_opts(noise="gaussian", batch=w["batch"], delta_o=0.1, delta_p=0.1, lam=1e-6, eps=EPS)
+    for _ in range(args.warmup):
+        api.lsqml_epoch_ms(Os, Pe, pos, meas, order, ms, opts, check=False)
+    api.lsqml_epoch_ms(Os, Pe, pos, meas, order, ms, opts, check=True)
+    torch.cuda.synchronize()
+    api.profile_enable(True)
+    api.profile_read()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = []
+    for _ in range(args.steps):
+        loss, _ = api.lsqml_epoch_ms(Os, Pe, pos, meas, order, ms, opts, check=False)
+        losses.append(loss)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = api.profile_read()
+    api.profile_enable(False)
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": job_throughput(w["J"], world, ms_step * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "multislice256-lsqml", "J": w["J"], "N": 256, "M": 4, "S": w["S"], "H": 2048,
+                       "W": 2048, "dz_m": w["dz"], "wavelength_m": w["wavelength"], "pixel_m": w["pixel_size"],
+                       "batch": w["batch"], "eps": EPS,
+                       "step": "one LSQML epoch over all positions with per-slice directions and step sizes"},
+            "kernels": {k: {"launches": n, "ms_per_launch": t / max(n, 1)} for k, (n, t) in prof.items()},
+            "losses": [l.item() for l in losses[:3]],
+        }), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -824,6 +895,8 @@ def main():
             run_ad256(args, rank, world, local_rank)
         elif args.workload == "multislice256":
             run_ms256(args, rank, world, local_rank)
+        elif args.workload == "multislice256-lsqml":
+            run_ms256_lsqml(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

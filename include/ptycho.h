@@ -113,16 +113,36 @@ typedef struct {
  * first such call must not itself be inside a stream capture. */
 #define PTYCHO_FLAG_GRAPH 1
 /* opts->flags: on the first epoch for a given device and (N, M, H, W, batch),
- * time the CTA-size variants of the two per-position kernels on the first
+ * time the candidate variants of three kernels of the epoch on the first
  * minibatch (synchronising the stream; skipped while capturing) and use the
- * fastest from then on. Without it, or before tuning, the defaults are used. */
+ * fastest of each from then on. Without it, or before tuning, variant 0 of
+ * each is used. The candidates (the "variants" below):
+ *   [0] the per-position pass: windows <= 64: CTA sizes default / alternative;
+ *       window 128: 1024 threads (0), 512 threads (1), a pair of CTAs of 512
+ *       threads with 64 rows each exchanging the column transforms through
+ *       distributed shared memory, two pairs per SM (2); windows 192/256: one;
+ *   [1] the step-size pass: one kernel per position (0), or the partial sums
+ *       spread over 8 chunks of every position, then a
+ *       per-position solve and update (1);
+ *   [2] the probe reduction: 16 (0), 8 (1) or 32 (2) positions in flight per
+ *       thread. */
 #define PTYCHO_FLAG_AUTOTUNE 2
+#define PTYCHO_TUNE_KERNELS 3
+#define PTYCHO_TUNE_MAX 4
 
-/* Autotuner result for these dimensions and batch on the current device:
- * returns 1 and the chosen variants (0 = default CTA size, 1 = alternative)
- * and the measured milliseconds of both variants, or 0 if not tuned. */
-int32_t ptycho_tuning_read(const ptycho_dims* dims, int32_t batch, int32_t* variant_pass1,
-                           int32_t* variant_pass2, float* ms_pass1, float* ms_pass2);
+/* Autotuner choice for these dimensions and batch on the current device:
+ * returns 1 and fills variants[PTYCHO_TUNE_KERNELS] and the measured
+ * milliseconds ms[PTYCHO_TUNE_KERNELS * PTYCHO_TUNE_MAX] (row i: kernel i's
+ * candidates, 0 where not timed; either pointer may be NULL), or 0 if these
+ * dimensions were not tuned (or were pinned by ptycho_tuning_set, which
+ * records no times). */
+int32_t ptycho_tuning_read(const ptycho_dims* dims, int32_t batch, int32_t* variants, float* ms);
+
+/* Pins the variants used for these dimensions and batch on the current
+ * device (as if the autotuner had chosen them; a later PTYCHO_FLAG_AUTOTUNE
+ * call does not retune them). PTYCHO_ERR_ARG for a variant outside its
+ * kernel's candidates, PTYCHO_ERR_UNSUPPORTED for unsupported dimensions. */
+ptycho_status ptycho_tuning_set(const ptycho_dims* dims, int32_t batch, const int32_t* variants);
 
 /* Bytes of workspace needed by every entry point below for these dimensions
  * and minibatch size (ptycho_adjoint processes positions in chunks of

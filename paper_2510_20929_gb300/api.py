@@ -126,8 +126,8 @@ def lib() -> ctypes.CDLL:
             "ptycho_lsqml_epoch_static": (ctypes.c_int, [dims_p, _P, _P, _P, _P, _P, opts_p, _P, _P, _P]),
             "ptycho_workspace_bytes_batched": (ctypes.c_size_t, [ctypes.c_int32, dims_p, opts_p]),
             "ptycho_tuning_read": (ctypes.c_int32, [dims_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
-                                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
                                                     ctypes.POINTER(ctypes.c_float)]),
+            "ptycho_tuning_set": (ctypes.c_int, [dims_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
             "ptycho_lsqml_epoch_batched": (ctypes.c_int, [ctypes.c_int32, dims_p, _P, _P, _P, _P, _P, opts_p, _P,
                                                           _P, ctypes.c_size_t, _P]),
             "ptycho_status_read": (ctypes.c_int, [_P, _P]),
@@ -370,14 +370,27 @@ def lsqml_epoch(obj, probe, pos, meas, order=None, opts: LsqmlOpts | None = None
     return loss, alpha
 
 
+TUNED = ("pass1", "pass2", "probe_reduce")   # the kernels the autotuner chooses variants of
+TUNE_MAX = 4
+
+
 def tuning(dims: Dims, batch: int):
     """Autotuner choice for these dimensions on the current device, or None:
-    {"pass1": variant, "pass2": variant, "pass1_ms": [default, alt], "pass2_ms": [...]}."""
-    v1, v2 = ctypes.c_int32(0), ctypes.c_int32(0)
-    m1, m2 = (ctypes.c_float * 2)(), (ctypes.c_float * 2)()
-    if not lib().ptycho_tuning_read(ctypes.byref(dims), int(batch), ctypes.byref(v1), ctypes.byref(v2), m1, m2):
+    {"pass1": variant, "pass2": variant, "probe_reduce": variant,
+     "pass1_ms": [candidate ms...], "pass2_ms": [...], "probe_reduce_ms": [...]}."""
+    v = (ctypes.c_int32 * len(TUNED))()
+    m = (ctypes.c_float * (len(TUNED) * TUNE_MAX))()
+    if not lib().ptycho_tuning_read(ctypes.byref(dims), int(batch), v, m):
         return None
-    return {"pass1": v1.value, "pass2": v2.value, "pass1_ms": list(m1), "pass2_ms": list(m2)}
+    out = {k: v[i] for i, k in enumerate(TUNED)}
+    out.update({k + "_ms": list(m[i * TUNE_MAX:(i + 1) * TUNE_MAX]) for i, k in enumerate(TUNED)})
+    return out
+
+
+def set_tuning(dims: Dims, batch: int, pass1: int = 0, pass2: int = 0, probe_reduce: int = 0):
+    """Pins the kernel variants used for these dimensions and batch on the current device."""
+    v = (ctypes.c_int32 * len(TUNED))(int(pass1), int(pass2), int(probe_reduce))
+    _check(lib().ptycho_tuning_set(ctypes.byref(dims), int(batch), v), "ptycho_tuning_set")
 
 
 def lsqml_epoch_batched(recons, opts, *, check: bool = True):

@@ -386,11 +386,17 @@ struct TuneKey {
     return dev == o.dev && N == o.N && M == o.M && H == o.H && W == o.W && B == o.B;
   }
 };
+// v[0]: the per-position pass (candidates: pass1_variants(N)), v[1]: the
+// step-size pass (single kernel, split), v[2]: the probe reduction (positions
+// in flight per thread: 16, 8, 32); ms[i][c]: candidate c's mean time.
 struct TuneEntry {
   TuneKey key;
-  int v1, v2;
-  float ms1[2], ms2[2];
+  int v[PTYCHO_TUNE_KERNELS];
+  float ms[PTYCHO_TUNE_KERNELS][PTYCHO_TUNE_MAX];
 };
+
+static int pass1_variants(int N) { return N == 128 ? 3 : (N <= 128 ? 2 : 1); }
+static constexpr int kPass2Variants = 2, kReduceVariants = 3;
 static std::mutex g_tune_mu;
 static std::vector<TuneEntry> g_tune;
 
@@ -436,15 +442,16 @@ static float time_launch(cudaStream_t s, int reps, F&& launch) {
 
 cudaError_t probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* h_s, const float2* o_s,
                          const int* valid, float2* dPacc, int accumulate, float* Dp, const float4* acc, int HW,
-                         BatchScalars* sc, cudaStream_t s, int o_stride) {
+                         BatchScalars* sc, cudaStream_t s, int o_stride, int variant) {
   cudaEvent_t e0 = profile_begin(K_PROBE_REDUCE, s);
   const int NP = NN / 2;
   const int threads = (dPacc ? Mc * NP : 0) + (Dp ? NP : 0);
   int bx = (threads + 255) / 256;
   if (acc && bx < 2 * sm_count()) bx = 2 * sm_count();
   dim3 grid(bx > 0 ? bx : 1, acc ? 2 : 1);
-  const cudaError_t e = launch_pdl(k_probe_reduce<16>, grid, dim3(256), 0, s, NN, k0, Mc, Ms, nb, h_s, o_s, valid,
-                                   dPacc, accumulate, Dp, acc, HW, sc, o_stride);
+  auto kern = variant == 1 ? k_probe_reduce<8> : variant == 2 ? k_probe_reduce<32> : k_probe_reduce<16>;
+  const cudaError_t e = launch_pdl(kern, grid, dim3(256), 0, s, NN, k0, Mc, Ms, nb, h_s, o_s, valid, dPacc,
+                                   accumulate, Dp, acc, HW, sc, o_stride);
   profile_end(K_PROBE_REDUCE, e0, s);
   return e;
 }
@@ -573,19 +580,28 @@ static ptycho_status autotune(const ptycho_dims& d, float2* obj, float2* probe, 
   a.eps = (float)o.eps;
   a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
   a.Sp = w.Sp; a.acc = w.acc; a.loss = nullptr; a.status = &w.hdr->status;
-  for (int v = 0; v < 2; ++v) t->ms1[v] = time_launch(s, 3, [&] { return pass1(N, a, s, v); });
-  t->v1 = t->ms1[1] < t->ms1[0] ? 1 : 0;
-  // one clean pass 1 with the chosen variant feeds the pass-2 candidates
+  auto best = [](const float* ms, int n) {
+    int b = 0;
+    for (int c = 1; c < n; ++c)
+      if (ms[c] < ms[b]) b = c;
+    return b;
+  };
+  const int n1 = pass1_variants(N);
+  for (int v = 0; v < n1; ++v) t->ms[0][v] = time_launch(s, 3, [&] { return pass1(N, a, s, v); });
+  t->v[0] = best(t->ms[0], n1);
+  // one clean pass 1 with the chosen variant feeds the other candidates
   if (cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
-  if (pass1(N, a, s, t->v1) != cudaSuccess) return PTYCHO_ERR_CUDA;
-  if (probe_reduce(NN, 0, M, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
-                   o.update_probe ? w.Dp : nullptr, w.acc, HW, sc, s) != cudaSuccess)
-    return PTYCHO_ERR_CUDA;
+  if (pass1(N, a, s, t->v[0]) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  for (int v = 0; v < kReduceVariants; ++v)
+    t->ms[2][v] = time_launch(s, 3, [&] {
+      return probe_reduce(NN, 0, M, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
+                          o.update_probe ? w.Dp : nullptr, w.acc, HW, sc, s, 0, v);
+    });
+  t->v[2] = best(t->ms[2], kReduceVariants);
   if (norm_probe(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p, o.update_probe, sc, w.dP, w.Cp, w.Sdp, s) !=
       cudaSuccess)
     return PTYCHO_ERR_CUDA;
-  t->v2 = 0;
-  t->ms2[0] = t->ms2[1] = 0.f;
+  t->v[1] = 0;
   if (L.o - L.psi >= (size_t)HW * sizeof(float2) && o.update_object) {
     Pass2Args q;
     memset(&q, 0, sizeof(q));
@@ -598,8 +614,8 @@ static ptycho_status autotune(const ptycho_dims& d, float2* obj, float2* probe, 
     q.sc = sc;
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
-    for (int v = 0; v < 2; ++v) t->ms2[v] = time_launch(s, 3, [&] { return pass2(N, q, s, v); });
-    t->v2 = t->ms2[1] < t->ms2[0] ? 1 : 0;
+    for (int v = 0; v < kPass2Variants; ++v) t->ms[1][v] = time_launch(s, 3, [&] { return pass2(N, q, s, v); });
+    t->v[1] = best(t->ms[1], kPass2Variants);
   }
   // restore the epoch's starting state of the accumulators and scalars
   if (cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
@@ -622,7 +638,9 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
   if (tc && (e = dft_planes(N, w.dft, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
   int dev = 0;
   cudaGetDevice(&dev);
-  TuneEntry tune{{dev, N, M, d.H, d.W, B}, 0, 0, {0.f, 0.f}, {0.f, 0.f}};
+  TuneEntry tune;
+  memset(&tune, 0, sizeof(tune));
+  tune.key = {dev, N, M, d.H, d.W, B};
   if (!tc && !tune_lookup(tune.key, &tune) && (o.flags & PTYCHO_FLAG_AUTOTUNE) && d.J > 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
@@ -651,10 +669,11 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
       if ((e = cudaMemsetAsync(w.possum, 0, (size_t)nb * 5 * sizeof(double), s)) != cudaSuccess)
         return PTYCHO_ERR_CUDA;
     }
-    if ((e = tc ? pass1_dft(N, a, w.dft, s) : pass1(N, a, s, tune.v1)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if ((e = tc ? pass1_dft(N, a, w.dft, s) : pass1(N, a, s, tune.v[0])) != cudaSuccess) return PTYCHO_ERR_CUDA;
     const bool tiles = tiles_cheaper(nb, N, d.H, d.W);
     if ((e = probe_reduce(NN, 0, M, M, nb, w.h, w.o, w.valid, o.update_probe ? w.dPacc : nullptr, 0,
-                          o.update_probe ? w.Dp : nullptr, tiles ? nullptr : w.acc, HW, sc, s)) != cudaSuccess)
+                          o.update_probe ? w.Dp : nullptr, tiles ? nullptr : w.acc, HW, sc, s, 0, tune.v[2])) !=
+        cudaSuccess)
       return PTYCHO_ERR_CUDA;
     if (tiles && tile_illum_max(d, nb, b0, pos, order, w.valid, w.acc, sc, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if ((e = norm_probe(NN, M, w.dPacc, w.Dp, probe, (float)o.delta_p, o.update_probe, sc, w.dP, w.Cp, w.Sdp,
@@ -669,7 +688,7 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
     q.obj = o.object_per_epoch ? w.dOe : obj; q.alpha_out = alpha; q.sc = sc; q.part = w.p2part;
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
-    if ((e = pass2(N, q, s, tune.v2)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    if ((e = pass2(N, q, s, tune.v[1])) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if ((e = clear_acc(tiles, d, nb, b0, pos, order, w.valid, w.acc, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
     if ((e = probe_update(NN, M, probe, w.dP, w.Sp, o.update_probe, sc, sc_next, s)) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
@@ -723,18 +742,35 @@ const char* ptycho_status_string(ptycho_status s) {
   return "unknown status";
 }
 
-int32_t ptycho_tuning_read(const ptycho_dims* dims, int32_t batch, int32_t* variant_pass1, int32_t* variant_pass2,
-                           float* ms_pass1, float* ms_pass2) {
+int32_t ptycho_tuning_read(const ptycho_dims* dims, int32_t batch, int32_t* variants, float* ms) {
   if (!dims) return 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   TuneEntry t;
   if (!tune_lookup({dev, dims->N, dims->M, dims->H, dims->W, batch}, &t)) return 0;
-  if (variant_pass1) *variant_pass1 = t.v1;
-  if (variant_pass2) *variant_pass2 = t.v2;
-  if (ms_pass1) { ms_pass1[0] = t.ms1[0]; ms_pass1[1] = t.ms1[1]; }
-  if (ms_pass2) { ms_pass2[0] = t.ms2[0]; ms_pass2[1] = t.ms2[1]; }
+  for (int i = 0; i < PTYCHO_TUNE_KERNELS; ++i) {
+    if (variants) variants[i] = t.v[i];
+    if (ms)
+      for (int c = 0; c < PTYCHO_TUNE_MAX; ++c) ms[i * PTYCHO_TUNE_MAX + c] = t.ms[i][c];
+  }
   return 1;
+}
+
+ptycho_status ptycho_tuning_set(const ptycho_dims* dims, int32_t batch, const int32_t* variants) {
+  ptycho_status st = check_dims(dims);
+  if (st != PTYCHO_OK) return st;
+  if (batch < 1 || !variants) return PTYCHO_ERR_ARG;
+  const int n[PTYCHO_TUNE_KERNELS] = {pass1_variants(dims->N), kPass2Variants, kReduceVariants};
+  for (int i = 0; i < PTYCHO_TUNE_KERNELS; ++i)
+    if (variants[i] < 0 || variants[i] >= n[i]) return PTYCHO_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PTYCHO_ERR_CUDA;
+  TuneEntry t;
+  memset(&t, 0, sizeof(t));
+  t.key = {dev, dims->N, dims->M, dims->H, dims->W, batch};
+  for (int i = 0; i < PTYCHO_TUNE_KERNELS; ++i) t.v[i] = variants[i];
+  tune_store(t);
+  return PTYCHO_OK;
 }
 
 ptycho_status ptycho_workspace_init(void* ws, size_t ws_bytes, void* stream) {

@@ -244,7 +244,10 @@ __device__ __forceinline__ void bilinear2(const float2* __restrict__ O, int W, i
                    w00 * a1.y + w01 * a2.y + w10 * b1.y + w11 * b2.y);
 }
 
-// Block-wide sum of NV doubles; result valid in thread 0. `red` holds 32*NV doubles.
+// Block-wide sum of NV doubles; result valid in thread 0. `red` holds 32*NV
+// doubles. A shuffle tree within each warp, then warp 0 reduces the per-warp
+// partials with a second shuffle tree (five dependent FP64 additions instead
+// of a serial sum over the warps).
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -257,11 +260,12 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) red[warp * NV + q] = v[q];
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += red[w * NV + q];
+      double s = lane < nw ? red[lane * NV + q] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
       v[q] = s;
     }
   }

@@ -73,7 +73,7 @@ cudaError_t pass1_dft(int N, const BatchArgs& a, const void* dft, cudaStream_t s
 // slot i starts at o_s + i * o_stride (complex elements; 0: N * N).
 cudaError_t probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* h_s, const float2* o_s,
                          const int* valid, float2* dPacc, int accumulate, float* Dp, const float4* acc, int HW,
-                         BatchScalars* sc, cudaStream_t s, int o_stride = 0);
+                         BatchScalars* sc, cudaStream_t s, int o_stride = 0, int variant = 0);
 cudaError_t norm_probe(int NN, int M, const float2* dPacc, const float* Dp, const float2* probe, float delta_p,
                        int update_probe, const BatchScalars* sc, float2* dP, float2* Cp, float* Sdp,
                        cudaStream_t s);

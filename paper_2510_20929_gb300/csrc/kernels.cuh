@@ -351,6 +351,22 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
 #pragma unroll 1
       for (int it = 0; it < ITER; ++it) {
         const int row = gid + it * L;
+        // the row's measured intensities, all loads issued before any use
+        // (registers 2q, 2q+1 are adjacent columns when S = 2: 8-byte loads)
+        float Imv[R2];
+        if (mode != MODE_FWD) {
+          if constexpr (F::S == 2) {
+#pragma unroll
+            for (int q = 0; q < R2 / 2; ++q) {
+              const float2 t = __ldg((const float2*)(meas + row * N + F::out_index(n, 2 * q)));
+              Imv[2 * q] = t.x;
+              Imv[2 * q + 1] = t.y;
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < R2; ++m) Imv[m] = __ldg(meas + row * N + F::out_index(n, m));
+          }
+        }
 #pragma unroll
         for (int m = 0; m < R2; ++m) {
           const int col = F::out_index(n, m);
@@ -358,7 +374,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
           const float I = rI[row * RP + col];
           if (a.ipred) a.ipred[(size_t)j * NN + pix] = I;
           if (mode == MODE_FWD) continue;
-          const float Im = __ldg(meas + pix);
+          const float Im = Imv[m];
           float fac;
           if (mode == MODE_VJP) {
             bad |= !isfinite(Im);
@@ -909,12 +925,12 @@ cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s, int variant) {
                       : launch_pass1_t<N, Threads<N>::T, false>(a, s);
 }
 
-// variant 0: the split form (when the partials buffer is given), 1: the
-// single-kernel form of PASS2_T threads
+// variant 0: the single-kernel form of PASS2_T threads, 1: the split form
+// (when the partials buffer is given)
 template <int N>
 cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s, int variant) {
   if (a.nb <= 0) return cudaSuccess;
-  if (a.part && variant == 0) {
+  if (a.part && variant == 1) {
     cudaError_t e = a.opr_dU
         ? launch_pdl(k_pass2_sums<N, true>, dim3(P2_CHUNKS, a.nb), dim3(PASS2S_T), 0, s, a)
         : launch_pdl(k_pass2_sums<N, false>, dim3(P2_CHUNKS, a.nb), dim3(PASS2S_T), 0, s, a);

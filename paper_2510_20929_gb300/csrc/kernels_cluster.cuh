@@ -31,6 +31,10 @@ struct Swz256 {  // f = ((r << 2) ^ (r >> 1) ^ (c >> 4)) & 15
   __host__ __device__ static constexpr int fr(int r) { return ((r << 2) ^ (r >> 1)) & 15; }
   __host__ __device__ static constexpr int fcb(int c) { return (c >> 4) & 15; }
 };
+struct Swz128 {  // the single-CTA 128 window's swizzle: f = ((r << 3) ^ (r << 1) ^ (r >> 2) ^ (c >> 4)) & 15
+  __host__ __device__ static constexpr int fr(int r) { return ((r << 3) ^ (r << 1) ^ (r >> 2)) & 15; }
+  __host__ __device__ static constexpr int fcb(int c) { return (c >> 4) & 15; }
+};
 struct Swz192 {  // f = ((r << 3) ^ (r << 1) ^ (r >> 2) ^ (c >> 6)) & 15
   __host__ __device__ static constexpr int fr(int r) { return ((r << 3) ^ (r << 1) ^ (r >> 2)) & 15; }
   __host__ __device__ static constexpr int fcb(int c) { return (c >> 6) & 15; }
@@ -58,9 +62,10 @@ struct RectAddr {
   }
 };
 
-template <int N_, int Q_, int T_, int RR1_, int RR2_, bool RINTER_, bool CINTER_, class Z_>
+template <int N_, int Q_, int T_, int RR1_, int RR2_, bool RINTER_, bool CINTER_, class Z_, int MINB_ = 1>
 struct Cfg {
   static constexpr int N = N_, Q = Q_, T = T_, LR = 64, NN = N * N, LNN = LR * N;
+  static constexpr int MINB = MINB_;   // CTAs per SM the launch bounds ask for
   static constexpr int RR1 = RR1_, RR2 = RR2_;
   using Z = Z_;
   using RowF = LineFft<RR1, RR2, RINTER_, RectAddr<N, Z>>;   // N-point rows
@@ -84,6 +89,8 @@ struct Cfg {
 };
 
 using Cfg256 = Cfg<256, 4, 1024, 16, 16, false, true, Swz256>;
+// the 128 window on a pair of CTAs (64 rows each) that fit two to an SM
+using Cfg128 = Cfg<128, 2, 512, 8, 16, true, true, Swz128, 2>;
 using Cfg192 = Cfg<192, 3, 512, 8, 24, true, false, Swz192>;
 
 // a * W_Q^m (W_Q = e^{-2 pi i / Q}) from the table twq[m mod Q].
@@ -111,7 +118,7 @@ __device__ __forceinline__ float2 wqmul(float2 a, int m, const float2* twq) {
 template <class C, bool FWD>
 __device__ __forceinline__ void cross_exchange(cg::cluster_group& cluster, float2* tile, const float2* twn,
                                                const float2* twq, int q) {
-  constexpr int Q = C::Q, P = C::XPAIRS, XB = C::XB, GB = XB % 2 == 0 ? 2 : 1;
+  constexpr int Q = C::Q, P = C::XPAIRS, XB = C::XB, GB = (XB % 2 == 0 && C::MINB == 1) ? 2 : 1;
   float2* src[Q];
 #pragma unroll
   for (int qq = 0; qq < Q; ++qq) src[qq] = cluster.map_shared_rank(tile, qq);
@@ -221,7 +228,7 @@ __device__ __forceinline__ void inv2d(cg::cluster_group& cluster, float2* tile, 
 }
 
 template <class C, bool OPR>
-__global__ void __launch_bounds__(C::T, 1) k_pass1_cluster(BatchArgs a) {
+__global__ void __launch_bounds__(C::T, C::MINB) k_pass1_cluster(BatchArgs a) {
   constexpr int N = C::N, Q = C::Q, T = C::T, LR = C::LR, NN = C::NN, LNN = C::LNN;
   constexpr int NAT_STEPS = C::NAT_STEPS;
   using SM = typename C::Smem;

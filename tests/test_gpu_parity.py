@@ -234,3 +234,25 @@ def test_compact_sampler_with_per_epoch_object_update_matches_oracle():
          abs(loss.item() - L_ref) / L_ref)
     print("compact + per-epoch:", e)
     assert max(e) < TOL_EPOCH
+
+
+@pytest.mark.parametrize("pass1,pass2,reduce", [(0, 0, 0), (1, 1, 1), (2, 0, 2), (2, 1, 0)])
+def test_every_tuned_variant_matches_oracle(pass1, pass2, reduce):
+    # the autotuner's candidates pinned one combination at a time (window 128:
+    # 1024 threads, 512 threads, the pair of CTAs; single or split step-size
+    # pass; 16, 8 or 32 positions in flight in the probe reduction)
+    import torch
+    from paper_2510_20929_gb300 import api
+    N, M, H, W, J, step, batch = 128, 3, 300, 310, 10, 24.0, 4
+    p = problem(N=N, M=M, H=H, W=W, J=J, step=step, seed=19)
+    (O, P, pos, I_m), (dO, dP, dpos, dI) = _dev(p)
+    order = np.random.default_rng(19).permutation(J).astype(np.int32)
+    api.set_tuning(api.dims_of(dO, dP, dpos), batch, pass1, pass2, reduce)
+    kw = dict(batch=batch, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6)
+    O_ref, P_ref, L_ref, a_ref = orc.lsqml_epoch(O, P, pos, I_m, order, orc.LsqmlOptions(**kw))
+    loss, alpha = api.lsqml_epoch(dO, dP, dpos, dI, to_dev(order, torch.int32), want_alpha=True, autotune=True, **kw)
+    assert api.tuning(api.dims_of(dO, dP, dpos), batch)["pass1"] == pass1     # pinned, not retuned
+    e = (err(dO.cpu().numpy(), O_ref), err(dP.cpu().numpy(), P_ref, axis=0), err(alpha.cpu().numpy(), a_ref, axis=1),
+         abs(loss.item() - L_ref) / abs(L_ref))
+    print(f"variants {pass1}/{pass2}/{reduce}:", e)
+    assert max(e[:3]) < TOL_EPOCH and e[3] < TOL_FWD
