@@ -795,26 +795,26 @@ def loss_and_gradients_ms(Os, P, pos, Hf, I_m, noise=GAUSSIAN, eps=0.0):
 # a forward-model option of every reconstructor; LSQML, Sec. 2.2).
 # ---------------------------------------------------------------------------
 def lsqml_batch_ms(Os, P, pos, I_m, idx, Hf, opts: LsqmlOptions, record: dict | None = None):
-    """One LSQML minibatch with an object of S slices; returns (Os, P, loss, alpha [B, S + 1]).
+    """One LSQML minibatch with an object of S slices; returns (Os, P, loss, alpha [B, 2]).
 
     Per position j and mode k, the exit-plane change is that of the
-    single-slice method, chi_(S-1)k = F^-1[(rho_j - 1) Psi_jk], with Psi the far
+    single-slice method, chi_jk = F^-1[(rho_j - 1) Psi_jk], with Psi the far
     field of the last slice's exit wave. It is carried back through the slices
-    (s = S-1 .. 0) as each slice's exit-plane change: slice s, whose exit wave is
-    inc_jsk o_js, receives
+    (s = S-1 .. 0): slice s, whose exit wave is inc_jsk o_js, receives
         g_js = sum_k conj(inc_jsk) chi_jsk   (its direction numerator),
         w_js = sum_k |inc_jsk|^2             (its illumination),
-    and passes chi_j(s-1)k = H^H[conj(o_js) chi_jsk] to the slice before it; the
+    with chi_j(S-1)k = chi_jk and chi_j(s-1)k = H^H[conj(o_js) chi_jsk]; the
     probe (the wave entering slice 0) receives h_jk = conj(o_j0) chi_j0k.
     Directions: dO_s = sum_j S_j^T g_js / (illum_s + delta_o max illum_s) with
     illum_s = sum_j S_j^T w_js, one preconditioner per slice;
     dP_k = sum_j h_jk / (Dp + delta_p max Dp), Dp = sum_j |o_j0|^2.
-    Step sizes, per position, each the least-squares fit at a slice's exit
-    plane: slice 0 and the probe share the 2x2 system of :func:`lsqml_batch`
-    (u_k = dO_0(r_j) P_k, v_k = o_j0 dP_k against chi_j0k); slice s >= 1 has
-    the 1x1 fit alpha_s = Re<u_s, chi_js> / ((1 + lam) ||u_s||^2) with
-    u_sk = dO_s(r_j) inc_jsk (0 when ||u_s|| = 0).
-    Update: O_s += sum_j S_j^T(alpha_js g_js) / (illum_s + delta_O,s);
+    Step sizes, per position, the least-squares fit of the exit-plane change by
+    the first-order changes of the exit waves: u_jk when every slice moves
+    along its direction (the tangent of the forward model, carried through the
+    slices: u = dO_0 P at slice 0, then u <- H(u) o_s + inc_s dO_s(r_j)), v_jk
+    when the probe moves along dP (v = o_0 dP, then v <- H(v) o_s); the 2x2
+    system and its solve are those of :func:`lsqml_batch`.
+    Update: O_s += sum_j S_j^T(alpha_O,j g_js) / (illum_s + delta_O,s);
     P_k += mean_j(alpha_P,j) dP_k. With S = 1 this is :func:`lsqml_batch`.
     """
     S, H, W = Os.shape
@@ -860,46 +860,48 @@ def lsqml_batch_ms(Os, P, pos, I_m, idx, Hf, opts: LsqmlOptions, record: dict | 
         dO_hat = np.zeros_like(dO_hat)
     dP = dP_acc / (Dp + delta_P)[None] if opts.update_probe else np.zeros_like(dP_acc)
 
-    alpha = np.zeros((B, S + 1), np.float64)
+    alpha = np.zeros((B, 2), np.float64)
+    tangents = []
     for i, j in enumerate(idx):
         o, inc, g, w, chis = rec[i]
         u = extract(dO_hat[0], pos[j], N)[None] * P
         v = o[0][None] * dP
+        for s in range(1, S):
+            u = propagate(u, Hf) * o[s][None] + inc[s] * extract(dO_hat[s], pos[j], N)[None]
+            v = propagate(v, Hf) * o[s][None]
+        chi = chis[S - 1]
         A11 = float(np.sum(np.abs(u) ** 2))
         A12 = float(np.real(np.sum(np.conj(u) * v)))
         A22 = float(np.sum(np.abs(v) ** 2))
-        b1 = float(np.real(np.sum(np.conj(u) * chis[0])))
-        b2 = float(np.real(np.sum(np.conj(v) * chis[0])))
-        alpha[i, 0], alpha[i, S] = step_solve(A11, A12, A22, b1, b2, opts.lam)
-        for s in range(1, S):
-            us = extract(dO_hat[s], pos[j], N)[None] * inc[s]
-            a_s = float(np.sum(np.abs(us) ** 2)) * (1.0 + opts.lam)
-            b_s = float(np.real(np.sum(np.conj(us) * chis[s])))
-            alpha[i, s] = b_s / a_s if a_s > 0.0 else 0.0
+        b1 = float(np.real(np.sum(np.conj(u) * chi)))
+        b2 = float(np.real(np.sum(np.conj(v) * chi)))
+        alpha[i] = step_solve(A11, A12, A22, b1, b2, opts.lam)
+        tangents.append((u, v))
 
     Os_new = Os.copy()
     if opts.update_object:
         for s in range(S):
             upd = np.zeros((H, W), np.complex128)
             for i, j in enumerate(idx):
-                upd += scatter(alpha[i, s] * rec[i][2][s], pos[j], H, W)
+                upd += scatter(alpha[i, 0] * rec[i][2][s], pos[j], H, W)
             Os_new[s] = Os[s] + upd / (illum[s] + delta_O[s])
-    P_new = P + float(np.mean(alpha[:, S])) * dP if opts.update_probe else P.copy()
+    P_new = P + float(np.mean(alpha[:, 1])) * dP if opts.update_probe else P.copy()
     if record is not None:
         record.update(dict(dO_acc=dO_acc, illum=illum, dP_acc=dP_acc, Dp=Dp, delta_O=delta_O, delta_P=delta_P,
                            dO_hat=dO_hat, dP=dP, alpha=alpha, g=np.stack([r[2] for r in rec]),
-                           w=np.stack([r[3] for r in rec]), chi=np.stack([r[4] for r in rec])))
+                           w=np.stack([r[3] for r in rec]), chi=np.stack([r[4] for r in rec]),
+                           u=np.stack([t[0] for t in tangents]), v=np.stack([t[1] for t in tangents])))
     return Os_new, P_new, loss, alpha
 
 
 def lsqml_epoch_ms(Os, P, pos, I_m, order, Hf, opts: LsqmlOptions):
     """One epoch of multislice LSQML minibatches (``opts.batch`` positions of
-    ``order`` in turn); returns (Os, P, loss, alpha [J, S + 1])."""
+    ``order`` in turn); returns (Os, P, loss, alpha [J, 2])."""
     Os = np.asarray(Os, np.complex128).copy()
     P = np.asarray(P, np.complex128).copy()
     order = np.asarray(order)
     loss = 0.0
-    alpha = np.zeros((pos.shape[0], Os.shape[0] + 1), np.float64)
+    alpha = np.zeros((pos.shape[0], 2), np.float64)
     for b0 in range(0, order.shape[0], opts.batch):
         idx = order[b0:b0 + opts.batch]
         Os, P, l, a = lsqml_batch_ms(Os, P, pos, I_m, idx, Hf, opts)

@@ -163,3 +163,11 @@ def test_multislice_lsqml_probe_damping_from_the_last_slice_is_caught(monkeypatc
     wrong = _rewritten(orc.lsqml_batch_ms, "Dp += np.abs(o[0]) ** 2", "Dp += np.abs(o[-1]) ** 2")
     monkeypatch.setattr(orc, "lsqml_batch_ms", wrong)
     _fails(pins.test_multislice_probe_only_update_has_the_closed_form_of_a_known_object)
+
+
+def test_multislice_lsqml_tangent_without_the_slice_sources_is_caught(monkeypatch):
+    wrong = _rewritten(orc.lsqml_batch_ms,
+                       "u = propagate(u, Hf) * o[s][None] + inc[s] * extract(dO_hat[s], pos[j], N)[None]",
+                       "u = propagate(u, Hf) * o[s][None]")
+    monkeypatch.setattr(orc, "lsqml_batch_ms", wrong)
+    _fails(pins.test_multislice_lsqml_step_sizes_fit_the_exit_plane_change_by_finite_difference_tangents)
