@@ -403,18 +403,22 @@ ptycho_status ptycho_adjoint_ms(const ptycho_dims* dims, const ptycho_multislice
  * exit-plane change chi = F^-1[(rho - 1) Psi] of the last slice is carried
  * back through the slices (adjoint propagation, times conj of each slice's
  * patch); every slice s gets the direction numerator sum_k conj(inc_sk) chi_sk
- * and the illumination sum_k |inc_sk|^2 of its incident waves, its own
- * object-frame preconditioner (damping delta_o times its maximum) and its own
- * least-squares step at its exit plane: slice 0 shares the 2x2 system of
- * ptycho_lsqml_epoch with the probe (direction conj(o_0) chi_0 / (sum |o_0|^2
- * + delta_p max)), slices 1..S-1 have 1x1 fits damped by (1 + lambda). With
- * S = 1 this is ptycho_lsqml_epoch. alpha: float64 [J, S + 1] (the slices'
- * alpha_O, then alpha_P) or NULL. opts as for ptycho_lsqml_epoch, except that
- * precision BF16X3, update_positions and object_per_epoch return
- * PTYCHO_ERR_UNSUPPORTED (PTYCHO_FLAG_AUTOTUNE has no variants to choose
- * here). Workspace: ptycho_workspace_bytes_lsqml_ms(dims, ms, opts); the
- * incident waves are kept there as for the adjoint, plus S accumulator
- * planes [S, H, W] of 16 bytes and the slices' illumination per slot. */
+ * and the illumination sum_k |inc_sk|^2 of its incident waves and its own
+ * object-frame preconditioner (damping delta_o times its maximum); the probe
+ * direction is conj(o_0) chi_0 / (sum |o_0|^2 + delta_p max). The step sizes
+ * are the 2x2 least-squares fit of the exit-plane change by the tangents of
+ * the forward model (the first-order change of the exit waves when every
+ * slice moves along its direction, and when the probe moves along its own),
+ * solved like ptycho_lsqml_epoch's; every slice moves by the position's
+ * alpha_O, the probe by the mean alpha_P. With S = 1 this is
+ * ptycho_lsqml_epoch. alpha: float64 [J, 2] (alpha_O, alpha_P) or NULL.
+ * opts as for ptycho_lsqml_epoch, except that precision BF16X3,
+ * update_positions and object_per_epoch return PTYCHO_ERR_UNSUPPORTED
+ * (PTYCHO_FLAG_AUTOTUNE has no variants to choose here). Workspace:
+ * ptycho_workspace_bytes_lsqml_ms(dims, ms, opts); the incident waves are kept
+ * there as for the adjoint, plus S accumulator planes [S, H, W] of 16 bytes,
+ * the slices' illumination and directions per slot and one tangent plane per
+ * slot. */
 size_t ptycho_workspace_bytes_lsqml_ms(const ptycho_dims* dims, const ptycho_multislice* ms,
                                         const ptycho_lsqml_opts* opts);
 ptycho_status ptycho_lsqml_epoch_ms(const ptycho_dims* dims, const ptycho_multislice* ms, float* object,

@@ -679,7 +679,7 @@ def lsqml_epoch_ms(obj, probe, pos, meas, order, ms: Multislice, opts: LsqmlOpts
                    want_alpha: bool = False, check: bool = True, **kw):
     """One LSQML epoch with a multislice object (slices [S, H, W]), updating
     ``obj`` and ``probe`` in place. Returns (loss, alpha): alpha is a float64
-    [J, S + 1] device tensor (each slice's alpha_O, then alpha_P) or None."""
+    [J, 2] device tensor (alpha_O shared by the slices, alpha_P) or None."""
     if opts is None:
         opts = make_opts(**kw)
     d = _ms_dims(obj, probe, pos, ms)
@@ -695,7 +695,7 @@ def lsqml_epoch_ms(obj, probe, pos, meas, order, ms: Multislice, opts: LsqmlOpts
         ws = Workspace(need, obj.device)
         _ws_cache[key] = ws
     loss = torch.zeros((), dtype=torch.float64, device=obj.device)
-    alpha = torch.zeros((d.J, ms.S + 1), dtype=torch.float64, device=obj.device) if want_alpha else None
+    alpha = torch.zeros((d.J, 2), dtype=torch.float64, device=obj.device) if want_alpha else None
     _check(lib().ptycho_lsqml_epoch_ms(ctypes.byref(d), ctypes.byref(ms), _ptr(obj), _ptr(probe), _ptr(pos),
                                        _ptr(meas), _ptr(order), ctypes.byref(opts), _ptr(loss), _ptr(alpha),
                                        _P(ws.ptr), ws.nbytes, _stream()), "ptycho_lsqml_epoch_ms")

@@ -578,7 +578,7 @@ static ptycho_status autotune(const ptycho_dims& d, float2* obj, float2* probe, 
   a.b0 = 0; a.nb = nb;
   a.mode = (o.noise == PTYCHO_NOISE_POISSON) ? MODE_LSQML_POISSON : MODE_LSQML_GAUSS;
   a.eps = (float)o.eps;
-  a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
+  a.psi_s = w.h; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;   // (far fields under h: see run_epoch)
   a.Sp = w.Sp; a.acc = w.acc; a.loss = nullptr; a.status = &w.hdr->status;
   auto best = [](const float* ms, int n) {
     int b = 0;
@@ -661,7 +661,11 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
     a.b0 = b0; a.nb = nb;
     a.mode = (o.noise == PTYCHO_NOISE_POISSON) ? MODE_LSQML_POISSON : MODE_LSQML_GAUSS;
     a.eps = (float)o.eps;
-    a.psi_s = w.psi; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
+    // FP32: the far field of mode k shares its scratch with h_k, which the
+    // pass writes only after the inverse transform of mode k has consumed the
+    // far field (same slot, same mode, the same CTA): a far field still in L2
+    // is overwritten there instead of being written back to HBM
+    a.psi_s = tc ? w.psi : w.h; a.o_s = w.o; a.g_s = w.g; a.h_s = w.h; a.valid = w.valid;
     a.Sp = w.Sp; a.acc = w.acc;
     a.loss = loss; a.status = &w.hdr->status;
     if (o.update_positions) {

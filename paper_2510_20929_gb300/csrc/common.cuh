@@ -143,6 +143,25 @@ struct MsArgs {
   const float* Sp;      // [N, N]
 };
 
+// Arguments of the multislice LSQML tangent pass (k_step_ms): per slot the
+// first-order changes of the exit waves when every slice moves along its
+// direction (u) and when the probe moves along its direction (v), reduced to
+// the Gram entries |u|^2, Re<u, v>, |v|^2 of the step-size system.
+struct MsStepArgs {
+  int H, W, M, J, S;
+  const int* order;
+  int b0, nb;
+  const float2* probe;   // [M, N, N]
+  const float2* Hf;      // [N, N]
+  const float2* o_s;     // [B, S, N, N] slice patches
+  const float2* in_s;    // [B, M, S - 1, N, N] incident waves of slices 1..S-1
+  const float2* d_s;     // [B, S, N, N] each slice's direction at the slot's position
+  const float2* dP;      // [M, N, N] probe direction
+  float2* u_s;           // [B, N, N] the object tangent of one mode at the exit plane
+  const int* valid;
+  double* part;          // [B, Q, 3] Gram partials per CTA of a slot (Q CTAs per position)
+};
+
 constexpr int OPR_KMAX = 8;   // eigenmodes of the relaxed primary probe mode
 
 // Shared probe mode k, or null for the synthesised primary mode (OPR).

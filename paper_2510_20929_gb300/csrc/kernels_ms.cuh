@@ -347,6 +347,106 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
   }
 }
 
+// Tangents of the multislice forward model for the LSQML step sizes (one CTA
+// per position): per mode, u starts as P_k d_0 and is carried through the
+// slices as u <- H(u) o_s + inc_s d_s, v starts as dP_k o_0 and is carried as
+// v <- H(v) o_s; at the exit plane the CTA sums |u|^2, Re(conj(u) v), |v|^2
+// over the pixels and modes (u of the mode parked in scratch while v runs).
+template <int N, int T>
+__global__ void __launch_bounds__(T, 1) k_step_ms(MsStepArgs a) {
+  using SM = Pass1Smem<N>;
+  constexpr int NN = N * N;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* red = (double*)(smem + SM::red);
+  float2* tile = (float2*)(smem + SM::tile);
+  float2* tw = (float2*)(smem + SM::tw);
+  const int slot = blockIdx.x, tid = threadIdx.x;
+  double* out = a.part + (size_t)slot * 3;
+  if (!a.valid[slot]) {
+    if (tid < 3) out[tid] = 0.0;
+    return;
+  }
+  make_twiddles<N>(tw);
+  const int M = a.M, S = a.S;
+  const size_t slotNN = (size_t)slot * NN;
+  const float2* o_s = a.o_s + slotNN * S;
+  const float2* d_s = a.d_s + slotNN * S;
+  float2* u_s = a.u_s + slotNN;
+  const NatPairs<N, T> np;
+  float A11 = 0.f, A12 = 0.f, A22 = 0.f;
+  auto f2 = [](float4 v, int h) { return h ? make_float2(v.z, v.w) : make_float2(v.x, v.y); };
+#pragma unroll 1
+  for (int k = 0; k < M; ++k) {
+    const float2* Pk = a.probe + (size_t)k * NN;
+    const float2* dPk = a.dP + (size_t)k * NN;
+#pragma unroll 1
+    for (int t = 0; t < 2; ++t) {   // t = 0: the object tangent u, 1: the probe tangent v
+      __syncthreads();
+#pragma unroll 2
+      for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+        const int p = np.pix(q);
+        const float4 o2 = *(const float4*)(o_s + p);
+        const float4 x2 = t == 0 ? __ldg((const float4*)(Pk + p)) : __ldg((const float4*)(dPk + p));
+        const float4 y2 = t == 0 ? *(const float4*)(d_s + p) : o2;
+        store_pair(tile, np.phys(q), cmul(f2(x2, 0), f2(y2, 0)), cmul(f2(x2, 1), f2(y2, 1)));
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int s = 1; s < S; ++s) {
+        propagate_tile<N, T, false>(tile, tw, a.Hf);
+        const float2* inc = a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN);
+#pragma unroll 2
+        for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+          const int p = np.pix(q);
+          float2 x0, x1;
+          load_pair(tile, np.phys(q), x0, x1);
+          const float4 o2 = *(const float4*)(o_s + (size_t)s * NN + p);
+          x0 = cmul(x0, f2(o2, 0));
+          x1 = cmul(x1, f2(o2, 1));
+          if (t == 0) {   // the slice's own direction as a source
+            const float4 i2 = *(const float4*)(inc + p);
+            const float4 d2 = *(const float4*)(d_s + (size_t)s * NN + p);
+            x0 = cadd(x0, cmul(f2(i2, 0), f2(d2, 0)));
+            x1 = cadd(x1, cmul(f2(i2, 1), f2(d2, 1)));
+          }
+          store_pair(tile, np.phys(q), x0, x1);
+        }
+        __syncthreads();
+      }
+#pragma unroll 2
+      for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+        const int p = np.pix(q);
+        float2 x0, x1;
+        load_pair(tile, np.phys(q), x0, x1);
+        if (t == 0) {
+          A11 += cabs2(x0) + cabs2(x1);
+          *(float4*)(u_s + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        } else {
+          const float4 u2 = *(const float4*)(u_s + p);
+          A22 += cabs2(x0) + cabs2(x1);
+          A12 += u2.x * x0.x + u2.y * x0.y + u2.z * x1.x + u2.w * x1.y;   // Re(conj(u) v)
+        }
+      }
+    }
+  }
+  double v[3] = {(double)A11, (double)A12, (double)A22};
+  block_sum<3>(v, red);
+  if (tid == 0)
+    for (int i = 0; i < 3; ++i) out[i] = v[i];
+}
+
+template <int N>
+cudaError_t launch_step_ms(const MsStepArgs& a, cudaStream_t s) {
+  constexpr int T = N == 128 ? 512 : Threads<N>::T;
+  constexpr size_t sm = Pass1Smem<N>::bytes;
+  static unsigned long long done = 0;
+  cudaError_t e = smem_optin(k_step_ms<N, T>, sm, &done);
+  if (e != cudaSuccess) return e;
+  if (a.nb <= 0) return cudaSuccess;
+  k_step_ms<N, T><<<a.nb, T, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
 // CTA size of the multislice pass: the default of the single-slice pass, but
 // 512 threads at N = 128 (the slice loops need more than 64 registers).
 template <int N>

@@ -376,7 +376,134 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
   }
 }
 
+// The tangent pass of k_step_ms on the cluster windows: CTA q carries its 64
+// rows of u and v through the slices (propagate_cluster) and writes its
+// partial Gram entries; the step-size kernel adds the Q partials.
+template <class C>
+__global__ void __launch_bounds__(C::T, 1) k_step_ms_cluster(MsStepArgs a) {
+  constexpr int N = C::N, Q = C::Q, T = C::T, LR = C::LR, NN = C::NN;
+  constexpr int NAT_STEPS = C::NAT_STEPS;
+  using SM = typename C::Smem;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* red = (double*)(smem + SM::red);
+  float2* tile = (float2*)(smem + SM::tile);
+  float2* twr = (float2*)(smem + SM::twr);
+  float2* twc = (float2*)(smem + SM::twc);
+  float2* twn = (float2*)(smem + SM::twn);
+  float2* twq = (float2*)(smem + SM::twq);
+  const int q = (int)cluster.block_rank();
+  const int slot = blockIdx.x / Q;
+  const int tid = threadIdx.x;
+  double* out = a.part + ((size_t)slot * Q + q) * 3;
+  if (!a.valid[slot]) {   // the same decision in every CTA of the cluster
+    if (tid < 3) out[tid] = 0.0;
+    return;
+  }
+  make_line_twiddles<N, C::RR1, C::RR2>(twr);
+  make_line_twiddles<64, 8, 8>(twc);
+  for (int m = tid; m < N + Q; m += T) {
+    float sn, cs;
+    if (m < N) {
+      sincospif(2.0f * (float)m / (float)N, &sn, &cs);
+      twn[m] = make_float2(cs, -sn);
+    } else {
+      sincospif(2.0f * (float)(m - N) / (float)Q, &sn, &cs);
+      twq[m - N] = make_float2(cs, -sn);
+    }
+  }
+  const int M = a.M, S = a.S, rowbase = LR * q;
+  const size_t slotNN = (size_t)slot * NN;
+  const float2* o_s = a.o_s + slotNN * S;
+  const float2* d_s = a.d_s + slotNN * S;
+  float2* u_s = a.u_s + slotNN;
+  float A11 = 0.f, A12 = 0.f, A22 = 0.f;
+  auto f2 = [](float4 v, int h) { return h ? make_float2(v.z, v.w) : make_float2(v.x, v.y); };
+#pragma unroll 1
+  for (int k = 0; k < M; ++k) {
+    const float2* Pk = a.probe + (size_t)k * NN;
+    const float2* dPk = a.dP + (size_t)k * NN;
+#pragma unroll 1
+    for (int t = 0; t < 2; ++t) {   // t = 0: the object tangent u, 1: the probe tangent v
+      __syncthreads();
+#pragma unroll 2
+      for (int st = 0; st < NAT_STEPS; ++st) {
+        const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+        const int p = (rowbase + r) * N + c;
+        const float4 o2 = *(const float4*)(o_s + p);
+        const float4 x2 = t == 0 ? __ldg((const float4*)(Pk + p)) : __ldg((const float4*)(dPk + p));
+        const float4 y2 = t == 0 ? *(const float4*)(d_s + p) : o2;
+        store_pair(tile, C::tix(r, c), cmul(f2(x2, 0), f2(y2, 0)), cmul(f2(x2, 1), f2(y2, 1)));
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int s = 1; s < S; ++s) {
+        propagate_cluster<C, false>(cluster, tile, twr, twc, twn, twq, q, a.Hf);
+        const float2* inc = a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN);
+#pragma unroll 2
+        for (int st = 0; st < NAT_STEPS; ++st) {
+          const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+          const int p = (rowbase + r) * N + c;
+          float2 x0, x1;
+          load_pair(tile, C::tix(r, c), x0, x1);
+          const float4 o2 = *(const float4*)(o_s + (size_t)s * NN + p);
+          x0 = cmul(x0, f2(o2, 0));
+          x1 = cmul(x1, f2(o2, 1));
+          if (t == 0) {
+            const float4 i2 = *(const float4*)(inc + p);
+            const float4 d2 = *(const float4*)(d_s + (size_t)s * NN + p);
+            x0 = cadd(x0, cmul(f2(i2, 0), f2(d2, 0)));
+            x1 = cadd(x1, cmul(f2(i2, 1), f2(d2, 1)));
+          }
+          store_pair(tile, C::tix(r, c), x0, x1);
+        }
+        __syncthreads();
+      }
+#pragma unroll 2
+      for (int st = 0; st < NAT_STEPS; ++st) {
+        const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+        const int p = (rowbase + r) * N + c;
+        float2 x0, x1;
+        load_pair(tile, C::tix(r, c), x0, x1);
+        if (t == 0) {
+          A11 += cabs2(x0) + cabs2(x1);
+          *(float4*)(u_s + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        } else {
+          const float4 u2 = *(const float4*)(u_s + p);
+          A22 += cabs2(x0) + cabs2(x1);
+          A12 += u2.x * x0.x + u2.y * x0.y + u2.z * x1.x + u2.w * x1.y;   // Re(conj(u) v)
+        }
+      }
+    }
+  }
+  double v[3] = {(double)A11, (double)A12, (double)A22};
+  block_sum<3>(v, red);
+  if (tid == 0)
+    for (int i = 0; i < 3; ++i) out[i] = v[i];
+  cluster.sync();   // no CTA leaves while another may still read its tile
+}
+
 }  // namespace cl
+
+template <class C>
+cudaError_t launch_step_ms_cluster(const MsStepArgs& a, cudaStream_t s, unsigned long long* done) {
+  cudaError_t e = smem_optin(cl::k_step_ms_cluster<C>, C::Smem::bytes, done);
+  if (e != cudaSuccess) return e;
+  if (a.nb <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(C::Q * a.nb));
+  cfg.blockDim = dim3(C::T);
+  cfg.dynamicSmemBytes = C::Smem::bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C::Q;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, cl::k_step_ms_cluster<C>, a);
+}
 
 template <class C, bool LS>
 cudaError_t launch_ms_cluster_t(const MsArgs& a, cudaStream_t s, unsigned long long* done) {

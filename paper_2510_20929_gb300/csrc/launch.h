@@ -14,6 +14,11 @@ template <int N> cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s, in
 template <int N> cudaError_t launch_pass1_ms(const MsArgs& a, cudaStream_t s);
 template <> cudaError_t launch_pass1_ms<192>(const MsArgs& a, cudaStream_t s);
 template <> cudaError_t launch_pass1_ms<256>(const MsArgs& a, cudaStream_t s);
+// multislice LSQML tangent pass (step-size Gram entries); Q CTAs per position
+struct MsStepArgs;
+template <int N> cudaError_t launch_step_ms(const MsStepArgs& a, cudaStream_t s);
+template <> cudaError_t launch_step_ms<192>(const MsStepArgs& a, cudaStream_t s);
+template <> cudaError_t launch_step_ms<256>(const MsStepArgs& a, cudaStream_t s);
 // split-BF16 DFT-GEMM form (N = 32, 64, 128): bytes of the DFT chunks, their
 // fill, the two parts of the per-position pass (part 1: exit waves, part 2:
 // overlap-add) and the tensor-core far-field stage between them

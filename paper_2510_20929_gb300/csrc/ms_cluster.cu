@@ -17,4 +17,16 @@ cudaError_t launch_pass1_ms<192>(const MsArgs& a, cudaStream_t s) {
   return launch_ms_cluster<cl::Cfg192>(a, s, done);
 }
 
+template <>
+cudaError_t launch_step_ms<256>(const MsStepArgs& a, cudaStream_t s) {
+  static unsigned long long done = 0;
+  return launch_step_ms_cluster<cl::Cfg256>(a, s, &done);
+}
+
+template <>
+cudaError_t launch_step_ms<192>(const MsStepArgs& a, cudaStream_t s) {
+  static unsigned long long done = 0;
+  return launch_step_ms_cluster<cl::Cfg192>(a, s, &done);
+}
+
 }  // namespace ptycho

@@ -4,4 +4,5 @@
 
 namespace ptycho {
 template cudaError_t launch_pass1_ms<128>(const MsArgs&, cudaStream_t);
+template cudaError_t launch_step_ms<128>(const MsStepArgs&, cudaStream_t);
 }  // namespace ptycho

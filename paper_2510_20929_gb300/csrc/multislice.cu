@@ -7,6 +7,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "ptycho.h"
 #include "common.cuh"
 #include "internal.h"
@@ -99,7 +101,7 @@ cudaError_t pass1_ms(int N, const MsArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 struct MsLsqmlLayout {
   MsLayout base;
-  size_t acc, w, dPacc, Dp, dP, Sp, Cp, Sdp, smax, total;
+  size_t acc, w, dPacc, Dp, dP, Sp, Cp, Sdp, smax, d, u, part, dsum, total;
 };
 
 MsLsqmlLayout ms_lsqml_layout(const ptycho_dims& d, int S, int B) {
@@ -121,6 +123,10 @@ MsLsqmlLayout ms_lsqml_layout(const ptycho_dims& d, int S, int B) {
   L.Cp = take(NN * sizeof(float2));
   L.Sdp = take(NN * sizeof(float));
   L.smax = take(16 * sizeof(unsigned int));
+  L.d = take((size_t)B * S * NN * sizeof(float2));        // the slices' directions at each slot's position
+  L.u = take((size_t)B * NN * sizeof(float2));            // one mode's object tangent per slot
+  L.part = take((size_t)B * 4 * 3 * sizeof(double));      // Gram partials, up to 4 CTAs per position
+  L.dsum = take((size_t)B * S * 2 * sizeof(double));      // right-hand-side partials per slot and slice
   L.total = off;
   return L;
 }
@@ -142,11 +148,15 @@ struct MsPass2Args {
   const float* Sdp;
   const float2* dP;
   float2* obj;                // [S, H, W], updated in place
-  double* alpha_out;          // [J, S + 1] or null
+  double* alpha_out;          // [J, 2] or null
   BatchScalars* sc;
   float delta_o;
   double lam;
   int update_object, update_probe;
+  float2* d_s;                // [B, S, N, N] directions at the slots' positions (written by k_ms_dir)
+  double* dsum;               // [B, S, 2]: Re<d_s, g_s> per slice; slice 0 also Re sum_k <dP_k, h_k>
+  const double* part;         // [B, Q, 3] Gram partials of the tangents (k_step_ms)
+  int Q;                      // CTAs per position of the tangent pass
 };
 
 // max over the illumination component of each slice's accumulator
@@ -160,15 +170,21 @@ __global__ void k_ms_illum_max(size_t HW, const float4* __restrict__ acc, unsign
   if (threadIdx.x == 0) atomicMax(smax + blockIdx.y, __float_as_uint(m));
 }
 
-// One CTA per (position, slice): the step-size sums of the slice (slice 0 with
-// the probe, as k_pass2), the FP64 solve and the slice's object update.
+// One CTA per (position, slice): the slice's preconditioned direction at the
+// position, d_s = S_j(dO_acc_s / (illum_s + delta_O,s)) (bilinear, the
+// quotient taken per corner), into scratch for the tangent pass, and the
+// right-hand-side term Re<d_s, g_s>; the slice-0 CTA adds the probe's
+// Re sum_k <dP_k, h_k>.
 template <int N>
-__global__ void __launch_bounds__(512, 1) k_pass2_ms(MsPass2Args a) {
+__global__ void __launch_bounds__(512, 1) k_ms_dir(MsPass2Args a) {
   constexpr int NN = N * N, T = 512;
-  __shared__ double red[32 * 5];
-  __shared__ double alpha_sh;
+  __shared__ double red[32 * 2];
   const int slot = blockIdx.x, s = blockIdx.y, tid = threadIdx.x, S = a.S;
-  if (!a.valid[slot]) return;
+  double* out = a.dsum + ((size_t)slot * S + s) * 2;
+  if (!a.valid[slot]) {
+    if (tid < 2) out[tid] = 0.0;
+    return;
+  }
   const int e = a.b0 + slot;
   const int j = a.order ? a.order[e] : e;
   int ty, tx;
@@ -179,65 +195,92 @@ __global__ void __launch_bounds__(512, 1) k_pass2_ms(MsPass2Args a) {
   const float4* acc = a.acc + s * HW;
   const float damp = a.delta_o * __uint_as_float(a.smax[s]);
   const float2* g_s = a.go_s + ((size_t)slot * S + s) * NN;
-  const float2* o0 = a.o_s + (size_t)slot * S * NN;
-  const float* wsl = s > 0 ? a.w_s + ((size_t)slot * (S - 1) + (s - 1)) * NN : a.Sp;
-  float A11 = 0.f, A12 = 0.f, A22 = 0.f, b1 = 0.f, b2 = 0.f;
+  float2* d_s = a.d_s + ((size_t)slot * S + s) * NN;
+  float b1 = 0.f, b2 = 0.f;
 #pragma unroll 1
   for (int p = tid; p < NN; p += T) {
     const int r = p / N, c = p % N;
-    const float2 g = __ldcs(g_s + p);
     float2 d = make_float2(0.f, 0.f);
     if (a.update_object) d = dohat(acc + (size_t)(ty + r) * a.W + (tx + c), a.W, w00, w01, w10, w11, damp);
-    A11 += cabs2(d) * __ldg(wsl + p);
+    d_s[p] = d;
+    const float2 g = __ldcs(g_s + p);
     b1 += d.x * g.x + d.y * g.y;             // Re(conj(d) g)
-    if (s == 0) {
-      const float2 o = __ldg(o0 + p);
-      const float2 od = cmulc(d, o);
-      const float2 cp = __ldg(a.Cp + p);
-      A12 += od.x * cp.x - od.y * cp.y;      // Re(conj(d) o Cp)
-      A22 += cabs2(o) * __ldg(a.Sdp + p);
-    }
   }
   if (s == 0 && a.update_probe) {
     const float4* h4 = (const float4*)(a.h_s + (size_t)slot * a.M * NN);
     const float4* d4 = (const float4*)a.dP;
-    const int Q = a.M * NN / 2;
-    for (int q = tid; q < Q; q += T) {
+    const int Qp = a.M * NN / 2;
+    for (int q = tid; q < Qp; q += T) {
       const float4 dp = __ldg(d4 + q);
       const float4 h = __ldcs(h4 + q);
       b2 += dp.x * h.x + dp.y * h.y + dp.z * h.z + dp.w * h.w;   // Re(conj(dP_k) h_k)
     }
   }
-  double v[5] = {A11, A12, A22, b1, b2};
-  block_sum<5>(v, red);
+  double v[2] = {b1, b2};
+  block_sum<2>(v, red);
   if (tid == 0) {
-    double aO = 0.0, aP = 0.0;
-    const double a11 = v[0], a12 = v[1], a22 = v[2], r1 = v[3], r2 = v[4];
+    out[0] = v[0];
+    out[1] = v[1];
+  }
+}
+
+// One CTA per (position, slice): the 2x2 step-size system of the position
+// (Gram entries of the tangents, right-hand sides from the slices' and the
+// probe's numerators, summed in a fixed order), the FP64 solve (the same in
+// every slice's CTA), and the slice's update O_s += alpha_O S_j^T g_s /
+// (illum_s + delta_O,s); the slice-0 CTA records alpha and adds alpha_P to
+// the minibatch's mean.
+template <int N>
+__global__ void __launch_bounds__(512, 2) k_ms_update(MsPass2Args a) {
+  constexpr int NN = N * N, T = 512;
+  __shared__ double alpha_sh;
+  const int slot = blockIdx.x, s = blockIdx.y, tid = threadIdx.x, S = a.S;
+  if (!a.valid[slot]) return;
+  const int e = a.b0 + slot;
+  const int j = a.order ? a.order[e] : e;
+  if (tid == 0) {
+    double a11 = 0.0, a12 = 0.0, a22 = 0.0, r1 = 0.0;
+    for (int q = 0; q < a.Q; ++q) {
+      const double* pp = a.part + ((size_t)slot * a.Q + q) * 3;
+      a11 += pp[0];
+      a12 += pp[1];
+      a22 += pp[2];
+    }
+    for (int t = 0; t < S; ++t) r1 += a.dsum[((size_t)slot * S + t) * 2];
+    const double r2 = a.dsum[(size_t)slot * S * 2 + 1];
+    const double tr = 0.5 * (a11 + a22);
+    const double d11 = a11 + a.lam * tr, d22 = a22 + a.lam * tr;
+    const double det = d11 * d22 - a12 * a12;
+    double aO, aP;
+    if (det > 0.0) {
+      aO = (d22 * r1 - a12 * r2) / det;
+      aP = (d11 * r2 - a12 * r1) / det;
+    } else {
+      aO = d11 > 0.0 ? r1 / d11 : 0.0;
+      aP = d22 > 0.0 ? r2 / d22 : 0.0;
+    }
     if (s == 0) {
-      const double tr = 0.5 * (a11 + a22);
-      const double d11 = a11 + a.lam * tr, d22 = a22 + a.lam * tr;
-      const double det = d11 * d22 - a12 * a12;
-      if (det > 0.0) {
-        aO = (d22 * r1 - a12 * r2) / det;
-        aP = (d11 * r2 - a12 * r1) / det;
-      } else {
-        aO = d11 > 0.0 ? r1 / d11 : 0.0;
-        aP = d22 > 0.0 ? r2 / d22 : 0.0;
-      }
       atomicAdd(&a.sc->sum_alpha_p, aP);
       atomicAdd(&a.sc->count, 1);
-      if (a.alpha_out) a.alpha_out[(size_t)j * (S + 1) + S] = aP;
-    } else {
-      const double d11 = a11 * (1.0 + a.lam);
-      aO = d11 > 0.0 ? r1 / d11 : 0.0;
+      if (a.alpha_out) {
+        a.alpha_out[2 * j] = aO;
+        a.alpha_out[2 * j + 1] = aP;
+      }
     }
-    if (a.alpha_out) a.alpha_out[(size_t)j * (S + 1) + s] = aO;
     alpha_sh = aO;
   }
   __syncthreads();
   if (!a.update_object) return;
+  int ty, tx;
+  float fy, fx;
+  tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
+  const size_t HW = (size_t)a.H * a.W;
+  const float4* acc = a.acc + s * HW;
+  const float damp = a.delta_o * __uint_as_float(a.smax[s]);
+  const float2* g_s = a.go_s + ((size_t)slot * S + s) * NN;
   const float aO = (float)alpha_sh;
-  const float c00 = aO * w00, c01 = aO * w01, c10 = aO * w10, c11 = aO * w11;
+  const float c00 = aO * (1.f - fy) * (1.f - fx), c01 = aO * (1.f - fy) * fx;
+  const float c10 = aO * fy * (1.f - fx), c11 = aO * fy * fx;
   float2* obj = a.obj + s * HW;
   constexpr int N1 = N + 1;
   for (int q = tid; q < N1 * N1; q += T) {
@@ -253,20 +296,35 @@ __global__ void __launch_bounds__(512, 1) k_pass2_ms(MsPass2Args a) {
   }
 }
 
-cudaError_t pass2_ms(int N, const MsPass2Args& a, cudaStream_t s) {
+template <class Fn>
+cudaError_t dispatch_ms_N(int N, Fn&& fn) {
+  switch (N) {
+    case 16: return fn(std::integral_constant<int, 16>());
+    case 32: return fn(std::integral_constant<int, 32>());
+    case 64: return fn(std::integral_constant<int, 64>());
+    case 128: return fn(std::integral_constant<int, 128>());
+    case 192: return fn(std::integral_constant<int, 192>());
+    case 256: return fn(std::integral_constant<int, 256>());
+  }
+  return cudaErrorInvalidValue;
+}
+
+// The step-size pass of the multislice LSQML minibatch: directions at the
+// positions and the right-hand sides (k_ms_dir), the tangents' Gram entries
+// (k_step_ms), then the solve and the slices' updates (k_ms_update).
+cudaError_t pass2_ms(int N, const MsPass2Args& a, const MsStepArgs& t, cudaStream_t s) {
   if (a.nb <= 0) return cudaSuccess;
   const dim3 grid((unsigned)a.nb, (unsigned)a.S);
   cudaEvent_t e0 = profile_begin(K_PASS2, s);
-  switch (N) {
-    case 16: k_pass2_ms<16><<<grid, 512, 0, s>>>(a); break;
-    case 32: k_pass2_ms<32><<<grid, 512, 0, s>>>(a); break;
-    case 64: k_pass2_ms<64><<<grid, 512, 0, s>>>(a); break;
-    case 128: k_pass2_ms<128><<<grid, 512, 0, s>>>(a); break;
-    case 192: k_pass2_ms<192><<<grid, 512, 0, s>>>(a); break;
-    case 256: k_pass2_ms<256><<<grid, 512, 0, s>>>(a); break;
-    default: return cudaErrorInvalidValue;
-  }
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e = dispatch_ms_N(N, [&](auto c) {
+    constexpr int NC = decltype(c)::value;
+    k_ms_dir<NC><<<grid, 512, 0, s>>>(a);
+    cudaError_t r = cudaGetLastError();
+    if (r != cudaSuccess) return r;
+    if ((r = launch_step_ms<NC>(t, s)) != cudaSuccess) return r;
+    k_ms_update<NC><<<grid, 512, 0, s>>>(a);
+    return cudaGetLastError();
+  });
   profile_end(K_PASS2, e0, s);
   return e;
 }
@@ -432,7 +490,15 @@ ptycho_status ptycho_lsqml_epoch_ms(const ptycho_dims* dims, const ptycho_multis
       q.obj = (float2*)object; q.alpha_out = alpha; q.sc = sc;
       q.delta_o = (float)opts->delta_o; q.lam = opts->lambda_reg;
       q.update_object = opts->update_object; q.update_probe = opts->update_probe;
-      if (pass2_ms(d.N, q, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
+      q.d_s = (float2*)(b + L.d); q.dsum = (double*)(b + L.dsum); q.part = (double*)(b + L.part);
+      q.Q = d.N == 256 ? 4 : d.N == 192 ? 3 : 1;
+      MsStepArgs t;
+      memset(&t, 0, sizeof(t));
+      t.H = d.H; t.W = d.W; t.M = M; t.J = d.J; t.S = S;
+      t.order = order; t.b0 = a.b0; t.nb = a.nb;
+      t.probe = (const float2*)probe; t.Hf = a.Hf; t.o_s = a.o_s; t.in_s = a.in_s; t.d_s = q.d_s; t.dP = dP;
+      t.u_s = (float2*)(b + L.u); t.valid = a.valid; t.part = (double*)(b + L.part);
+      if (pass2_ms(d.N, q, t, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
       if (clear_acc(false, ptycho_dims{(int32_t)(S * d.H), d.W, d.N, d.M, d.J}, a.nb, a.b0, pos, order, a.valid, acc,
                     s) != cudaSuccess)
         return PTYCHO_ERR_CUDA;
