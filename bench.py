@@ -99,7 +99,7 @@ def bf16_peak():
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_pass1_traffic.txt")
 PROFILE_EVERY = 5   # timed epochs between two whose dominant-kernel launches carry CUDA events
-KERNEL_SOURCES = ["common.cuh", "fft.cuh", "kernels.cuh", "pass_n128.cu"]
+KERNEL_SOURCES = ["common.cuh", "fft.cuh", "kernels.cuh", "tc.cuh", "kernels_cluster.cuh", "pass_n128.cu", "api.cu"]
 
 
 def kernel_source_hash():
