@@ -71,6 +71,12 @@ def parse():
                     help="skip the FP32 vs split-BF16 comparison at matched reconstruction error")
     ap.add_argument("--precision", choices=["fp32", "bf16x3"], default="fp32",
                     help="far-field arithmetic of the timed epochs: FP32 FFTs or split-BF16 DFT-GEMMs")
+    ap.add_argument("--ms-backward", choices=["recompute", "keep"], default="recompute",
+                    help="multislice workloads: incident waves recomputed in the backward pass, or kept by the "
+                         "forward pass (the other design is timed beside it unless --no-compare)")
+    ap.add_argument("--variants", default="",
+                    help="pin the kernel variants (pass1,pass2,probe_reduce, e.g. 0,0,1) instead of autotuning them: "
+                         "profiling runs, where the autotuner's timings are distorted")
     ap.add_argument("--positions", type=int, default=0,
                     help="use only the first J positions of the workload (profiling runs)")
     return ap.parse_args()
@@ -446,6 +452,8 @@ def run_ours(args, rank, world, local_rank):
     P_est = P.clone()
     opts = api.make_opts(noise="gaussian", batch=B, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=EPS, autotune=True,
                          precision=args.precision)
+    if args.variants:   # pinned entries are not retuned
+        api.set_tuning(api.Dims(H, W, N, M, J), B, *[int(v) for v in args.variants.split(",")])
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -753,6 +761,31 @@ def run_ad256(args, rank, world, local_rank):
         }), flush=True)
 
 
+def ms_designs(args):
+    """Backward designs of a multislice run: the chosen one first, then the
+    other one unless --no-compare."""
+    other = "keep" if args.ms_backward == "recompute" else "recompute"
+    return [args.ms_backward] if args.no_compare else [args.ms_backward, other]
+
+
+def ms_design_report(api, w, mss, timed, opts):
+    """Per backward design: time per step, throughput, workspace bytes and
+    the per-position kernel's time per launch."""
+    import ctypes
+    d = api.Dims(w["slices"].shape[1], w["slices"].shape[2], 256, 4, w["J"])
+    out = {}
+    for name, (ms_step, prof, _) in timed.items():
+        m = mss[name]
+        if opts is None:
+            ws = api.lib().ptycho_workspace_bytes_ms(ctypes.byref(d), ctypes.byref(m), w["batch"])
+        else:
+            ws = api.lib().ptycho_workspace_bytes_lsqml_ms(ctypes.byref(d), ctypes.byref(m), ctypes.byref(opts))
+        p1 = prof.get("k_pass1_ms", (0, 0.0))
+        out[name] = {"ms_per_step": ms_step, "value": w["J"] / (ms_step * 1e-3), "workspace_bytes": int(ws),
+                     "k_pass1_ms_ms_per_launch": p1[1] / max(p1[0], 1)}
+    return out
+
+
 def run_ms256(args, rank, world, local_rank):
     """Multislice case: 4 slices of 2048^2, probe 256^2 with 4 modes, 8000
     positions; a step is one Adam step on the slices and the probe (fused
@@ -766,7 +799,10 @@ def run_ms256(args, rank, world, local_rank):
     w = synth.workload_multislice256()
     if args.positions and args.positions < w["J"]:   # profiling runs: the first positions only
         w["pos"], w["J"] = w["pos"][:args.positions], args.positions
-    ms = api.make_multislice(w["S"], w["dz"], w["wavelength"], w["pixel_size"])
+    designs = ms_designs(args)
+    mss = {d: api.make_multislice(w["S"], w["dz"], w["wavelength"], w["pixel_size"], recompute=d == "recompute")
+           for d in designs}
+    ms = mss[designs[0]]
     Os_true = torch.tensor(w["slices"], dtype=torch.complex64, device=dev)
     P = torch.tensor(w["probe"], dtype=torch.complex64, device=dev)
     pos = torch.tensor(w["pos"], dtype=torch.float32, device=dev)
@@ -781,27 +817,30 @@ def run_ms256(args, rank, world, local_rank):
     Pe = P.clone().requires_grad_(True)
     opt = torch.optim.Adam([{"params": [Os], "lr": 1e-2}, {"params": [Pe], "lr": 1e-3}])
 
-    def step():
+    def step(m):
         opt.zero_grad(set_to_none=True)
-        loss = data_term_ms(Os, Pe, pos, meas, ms, "gaussian", 1e-9, w["batch"])
+        loss = data_term_ms(Os, Pe, pos, meas, m, "gaussian", 1e-9, w["batch"])
         loss.backward()
         opt.step()
         return loss
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    api.profile_enable(True)
-    api.profile_read()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        loss = step()
-    e1.record()
-    torch.cuda.synchronize()
-    prof = api.profile_read()
-    api.profile_enable(False)
-    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    timed = {}
+    for d in designs:   # the headline design first, then the other one from where it left the parameters
+        for _ in range(args.warmup):
+            step(mss[d])
+        torch.cuda.synchronize()
+        api.profile_enable(True)
+        api.profile_read()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            loss = step(mss[d])
+        e1.record()
+        torch.cuda.synchronize()
+        prof_d = api.profile_read()
+        api.profile_enable(False)
+        timed[d] = (max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev), prof_d, loss)
+    ms_step, prof, loss = timed[designs[0]]
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": job_throughput(w["J"], world, ms_step * 1e-3), "unit": UNIT,
@@ -810,9 +849,11 @@ def run_ms256(args, rank, world, local_rank):
             "config": {"workload": "multislice256-adam", "J": w["J"], "N": 256, "M": 4, "S": w["S"], "H": 2048,
                        "W": 2048, "dz_m": w["dz"], "wavelength_m": w["wavelength"], "pixel_m": w["pixel_size"],
                        "batch": w["batch"],
+                       "backward": designs[0],
                        "step": "one Adam step on the object slices and the probe (fused multislice data term "
                                "and adjoint)"},
             "kernels": {k: {"launches": n, "ms_per_launch": t / max(n, 1)} for k, (n, t) in prof.items()},
+            "backward_designs": ms_design_report(api, w, mss, timed, None),
             "final_loss": loss.item(),
         }), flush=True)
 
@@ -828,7 +869,10 @@ def run_ms256_lsqml(args, rank, world, local_rank):
     w = synth.workload_multislice256()
     if args.positions and args.positions < w["J"]:   # profiling runs: the first positions only
         w["pos"], w["J"] = w["pos"][:args.positions], args.positions
-    ms = api.make_multislice(w["S"], w["dz"], w["wavelength"], w["pixel_size"])
+    designs = ms_designs(args)
+    mss = {d: api.make_multislice(w["S"], w["dz"], w["wavelength"], w["pixel_size"], recompute=d == "recompute")
+           for d in designs}
+    ms = mss[designs[0]]
     Os_true = torch.tensor(w["slices"], dtype=torch.complex64, device=dev)
     P = torch.tensor(w["probe"], dtype=torch.complex64, device=dev)
     pos = torch.tensor(w["pos"], dtype=torch.float32, device=dev)
@@ -840,26 +884,30 @@ def run_ms256_lsqml(args, rank, world, local_rank):
     meas = torch.poisson(I0 * scale, generator=gen)
     del I0, Os_true
     order = torch.tensor(synth.random_order(w["J"], 9 + rank), dtype=torch.int32, device=dev)
-    Os = torch.ones((w["S"],) + tuple(w["slices"].shape[1:]), dtype=torch.complex64, device=dev)
-    Pe = P.clone()
     opts = api.make_opts(noise="gaussian", batch=w["batch"], delta_o=0.1, delta_p=0.1, lam=1e-6, eps=EPS)
-    for _ in range(args.warmup):
-        api.lsqml_epoch_ms(Os, Pe, pos, meas, order, ms, opts, check=False)
-    api.lsqml_epoch_ms(Os, Pe, pos, meas, order, ms, opts, check=True)
-    torch.cuda.synchronize()
-    api.profile_enable(True)
-    api.profile_read()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    losses = []
-    for _ in range(args.steps):
-        loss, _ = api.lsqml_epoch_ms(Os, Pe, pos, meas, order, ms, opts, check=False)
-        losses.append(loss)
-    e1.record()
-    torch.cuda.synchronize()
-    prof = api.profile_read()
-    api.profile_enable(False)
-    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    timed = {}
+    for d in designs:   # each design from flat slices and the true probe
+        Os = torch.ones((w["S"],) + tuple(w["slices"].shape[1:]), dtype=torch.complex64, device=dev)
+        Pe = P.clone()
+        for _ in range(args.warmup):
+            api.lsqml_epoch_ms(Os, Pe, pos, meas, order, mss[d], opts, check=False)
+        api.lsqml_epoch_ms(Os, Pe, pos, meas, order, mss[d], opts, check=True)
+        torch.cuda.synchronize()
+        api.profile_enable(True)
+        api.profile_read()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        losses = []
+        for _ in range(args.steps):
+            loss, _ = api.lsqml_epoch_ms(Os, Pe, pos, meas, order, mss[d], opts, check=False)
+            losses.append(loss)
+        e1.record()
+        torch.cuda.synchronize()
+        prof_d = api.profile_read()
+        api.profile_enable(False)
+        timed[d] = (max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev), prof_d, losses)
+        del Os, Pe
+    ms_step, prof, losses = timed[designs[0]]
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": job_throughput(w["J"], world, ms_step * 1e-3), "unit": UNIT,
@@ -867,9 +915,10 @@ def run_ms256_lsqml(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "multislice256-lsqml", "J": w["J"], "N": 256, "M": 4, "S": w["S"], "H": 2048,
                        "W": 2048, "dz_m": w["dz"], "wavelength_m": w["wavelength"], "pixel_m": w["pixel_size"],
-                       "batch": w["batch"], "eps": EPS,
+                       "batch": w["batch"], "eps": EPS, "backward": designs[0],
                        "step": "one LSQML epoch over all positions with per-slice directions and step sizes"},
             "kernels": {k: {"launches": n, "ms_per_launch": t / max(n, 1)} for k, (n, t) in prof.items()},
+            "backward_designs": ms_design_report(api, w, mss, timed, opts),
             "losses": [l.item() for l in losses[:3]],
         }), flush=True)
 

@@ -368,12 +368,19 @@ ptycho_status ptycho_lsqml_epoch_opr_batched(int32_t n, const ptycho_dims* dims,
  * on the FFT grid f = k / (N pixel_size) (the constant phase 2 pi dz / lambda
  * dropped, evanescent frequencies zero; computed in FP64 on the device); the
  * far field of the last slice gives I_j = sum_k |F psi_jk|^2. Every window
- * size, 1 <= S <= 16. The incident waves of slices 1..S-1 are kept in the workspace
- * for the backward pass (B M (S-1) N^2 complex64).
+ * size, 1 <= S <= 16. The backward pass needs the incident waves of slices
+ * 1..S-1. With recompute = 0 the forward pass keeps every mode's in the
+ * workspace (B M (S-1) N^2 complex64). With recompute = 1 it keeps none: the
+ * backward pass runs each mode through the slices again just before carrying
+ * its exit-plane change back (2 (S-1) more 2-D transforms per mode; the LSQML
+ * tangent pass does the same), and the workspace holds one mode's waves per
+ * position (B (S-1) N^2 complex64), which stay mostly in L2 between their
+ * write and their read. Both give the same waves, bit for bit.
  * ------------------------------------------------------------------------- */
 typedef struct {
   int32_t S;          /* object slices */
-  int32_t reserved;   /* must be zero */
+  int32_t recompute;  /* 0: incident waves kept by the forward pass, 1: recomputed
+                         in the backward pass; any other value: PTYCHO_ERR_ARG */
   double dz;          /* slice spacing */
   double wavelength;  /* same unit as dz */
   double pixel_size;  /* object pixel, same unit */
@@ -416,7 +423,8 @@ ptycho_status ptycho_adjoint_ms(const ptycho_dims* dims, const ptycho_multislice
  * update_positions and object_per_epoch return PTYCHO_ERR_UNSUPPORTED
  * (PTYCHO_FLAG_AUTOTUNE has no variants to choose here). Workspace:
  * ptycho_workspace_bytes_lsqml_ms(dims, ms, opts); the incident waves are kept
- * there as for the adjoint, plus S accumulator planes [S, H, W] of 16 bytes,
+ * (or, with ms->recompute, one mode's parked) there as for the adjoint, plus S
+ * accumulator planes [S, H, W] of 16 bytes,
  * the slices' illumination and directions per slot and one tangent plane per
  * slot. */
 size_t ptycho_workspace_bytes_lsqml_ms(const ptycho_dims* dims, const ptycho_multislice* ms,

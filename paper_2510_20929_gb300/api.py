@@ -57,7 +57,7 @@ class LsqmlOpts(ctypes.Structure):
 
 
 class Multislice(ctypes.Structure):
-    _fields_ = [("S", ctypes.c_int32), ("reserved", ctypes.c_int32), ("dz", ctypes.c_double),
+    _fields_ = [("S", ctypes.c_int32), ("recompute", ctypes.c_int32), ("dz", ctypes.c_double),
                 ("wavelength", ctypes.c_double), ("pixel_size", ctypes.c_double)]
 
 
@@ -614,9 +614,14 @@ def lsqml_epoch_opr_batched(recons, opts, oprs, *, check: bool = True):
 # Multislice: object slices complex64 [S, H, W], angular-spectrum propagation
 # between slices (spacing dz, wavelength and pixel size in one unit).
 # ---------------------------------------------------------------------------
-def make_multislice(S: int, dz: float, wavelength: float, pixel_size: float) -> Multislice:
+def make_multislice(S: int, dz: float, wavelength: float, pixel_size: float, *,
+                    recompute: bool = False) -> Multislice:
+    """recompute: the backward passes recompute each mode's incident waves
+    instead of keeping every mode's from the forward pass (less workspace and
+    DRAM traffic, 2 (S-1) more 2-D transforms per mode)."""
     m = Multislice()
     m.S, m.dz, m.wavelength, m.pixel_size = int(S), float(dz), float(wavelength), float(pixel_size)
+    m.recompute = int(bool(recompute))
     return m
 
 

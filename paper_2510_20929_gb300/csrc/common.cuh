@@ -114,6 +114,12 @@ struct Pass2Args {
 constexpr int P2_CHUNKS = 8;   // chunks of a position's pixels and h planes in the split step-size pass
 
 // Arguments of the multislice per-position pass (kernels_ms.cuh).
+// Incident wave of slice s (1..S-1) of mode k in the slot's scratch: kept per
+// mode by the forward pass, or one mode's at a time when recomputed.
+__device__ __forceinline__ size_t ms_inc_offset(bool recompute, size_t slotNN, int M, int S, int k, int s, int NN) {
+  return (recompute ? slotNN * (S - 1) : (slotNN * M + (size_t)k * NN) * (S - 1)) + (size_t)(s - 1) * NN;
+}
+
 struct MsArgs {
   int H, W, M, J, S;
   const float2* obj;    // [S, H, W]
@@ -125,7 +131,9 @@ struct MsArgs {
   const float2* Hf;     // [N, N] propagator, FFT order
   float2* psi_s;        // [B, M, N, N] far fields (unitary scale)
   float2* o_s;          // [B, S, N, N] slice patches
-  float2* in_s;         // [B, M, S - 1, N, N] incident waves of slices 1..S-1
+  float2* in_s;         // [B, M, S - 1, N, N] incident waves of slices 1..S-1, or
+                        // [B, S - 1, N, N] of one mode when they are recomputed
+  int recompute;        // 1: the backward pass recomputes each mode's incident waves
   float2* go_s;         // [B, S, N, N] per-slice object gradients (patch frame)
   float2* h_s;          // [B, M, N, N] probe gradient of each position
   int* valid;           // [B]
@@ -154,7 +162,9 @@ struct MsStepArgs {
   const float2* probe;   // [M, N, N]
   const float2* Hf;      // [N, N]
   const float2* o_s;     // [B, S, N, N] slice patches
-  const float2* in_s;    // [B, M, S - 1, N, N] incident waves of slices 1..S-1
+  float2* in_s;          // [B, M, S - 1, N, N] incident waves of slices 1..S-1, or
+                         // [B, S - 1, N, N] scratch for one mode's (recompute)
+  int recompute;         // 1: each mode's incident waves are recomputed here first
   const float2* d_s;     // [B, S, N, N] each slice's direction at the slot's position
   const float2* dP;      // [M, N, N] probe direction
   float2* u_s;           // [B, N, N] the object tangent of one mode at the exit plane

@@ -12,7 +12,11 @@
 // column FFT pass, a fused row pass that transforms, multiplies by H / N^2 and
 // transforms back, and an inverse column pass), keeps the incident waves of
 // slices 1..S-1 in scratch for the backward pass, and forms the data term as
-// the single-slice kernel does. The backward pass runs each mode from the far
+// the single-slice kernel does. With a.recompute the forward pass keeps no
+// incident waves: the backward pass first runs the mode through the slices
+// again (2 (S-1) more 2-D transforms) and parks that mode's waves in the
+// slot's scratch, where they are read back soon after, mostly from L2. The
+// backward pass runs each mode from the far
 // field back through the slices (conj(H) propagation), accumulating the
 // per-slice object gradients conj(incident_s) g and the probe gradient
 // conj(o^(0)) g, then scatters every slice's gradient into its plane and
@@ -66,6 +70,45 @@ __device__ __forceinline__ void propagate_tile(float2* tile, const float2* tw, c
   __syncthreads();
 }
 
+// Runs probe mode Pk through the slices again and writes the incident waves of
+// slices 1..S-1 to inc (S-1 consecutive N x N planes): the same arithmetic as
+// the forward pass, so the waves are bitwise those it saw. Leaves the tile
+// holding the last incident wave; starts and ends synchronised.
+template <int N, int T>
+__device__ __forceinline__ void recompute_incident(float2* tile, const float2* tw, const float2* __restrict__ Hf,
+                                                   const float2* Pk, const float2* o_s, float2* inc, int S) {
+  constexpr int NN = N * N;
+  const NatPairs<N, T> np;
+  __syncthreads();
+#pragma unroll 2
+  for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+    const int p = np.pix(q);
+    const float4 o2 = *(const float4*)(o_s + p);
+    const float4 P2 = __ldg((const float4*)(Pk + p));
+    store_pair(tile, np.phys(q), cmul(make_float2(P2.x, P2.y), make_float2(o2.x, o2.y)),
+               cmul(make_float2(P2.z, P2.w), make_float2(o2.z, o2.w)));
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int s = 1; s < S; ++s) {
+    propagate_tile<N, T, false>(tile, tw, Hf);
+    float2* in = inc + (size_t)(s - 1) * NN;
+    const bool last = s == S - 1;
+#pragma unroll 2
+    for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
+      const int p = np.pix(q);
+      float2 x0, x1;
+      load_pair(tile, np.phys(q), x0, x1);
+      *(float4*)(in + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+      if (!last) {
+        const float4 o2 = *(const float4*)(o_s + (size_t)s * NN + p);
+        store_pair(tile, np.phys(q), cmul(x0, make_float2(o2.x, o2.y)), cmul(x1, make_float2(o2.z, o2.w)));
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // LS: the LSQML instantiation (exit-plane changes instead of gradients, the
 // slices' illumination, the per-slice accumulators); the gradient form has
 // none of it.
@@ -105,6 +148,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
   const int mode = a.mode;
   const bool grad = mode != MODE_FWD;
   constexpr bool lsqml = LS;
+  const bool rec = a.recompute != 0, keep = grad && !rec;
   float2* psi_s = grad ? a.psi_s + slotNN * M : nullptr;
   float2* o_s = a.o_s + slotNN * S;
   const NatPairs<N, T> np;
@@ -136,7 +180,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
 #pragma unroll 1
     for (int s = 1; s < S; ++s) {
       propagate_tile<N, T, false>(tile, tw, a.Hf);
-      float2* inc = grad ? a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN) : nullptr;
+      float2* inc = keep ? a.in_s + ms_inc_offset(false, slotNN, M, S, k, s, NN) : nullptr;
       // LSQML: the slice's illumination sum_k |inc_k|^2
       float2* wsl = lsqml ? (float2*)(a.w_s + (slotNN * (S - 1) + (size_t)(s - 1) * NN)) : nullptr;
 #pragma unroll 2
@@ -144,7 +188,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
         const int p = np.pix(q);
         float2 x0, x1;
         load_pair(tile, np.phys(q), x0, x1);
-        if (grad) *(float4*)(inc + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        if (keep) *(float4*)(inc + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
         if (lsqml) {
           float2 w2 = make_float2(cabs2(x0), cabs2(x1));
           if (k > 0) {
@@ -229,6 +273,8 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
 #pragma unroll 1
   for (int k = M - 1; k >= 0; --k) {
     const float2* Pk = a.probe + (size_t)k * NN;
+    if (rec && S > 1)
+      recompute_incident<N, T>(tile, tw, a.Hf, Pk, o_s, a.in_s + ms_inc_offset(true, slotNN, M, S, k, 1, NN), S);
     __syncthreads();
     fft2_inverse<N, T>(
         tile, tw,
@@ -243,7 +289,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1_ms(MsArgs a) {
     __syncthreads();
 #pragma unroll 1
     for (int s = S - 1; s >= 1; --s) {
-      const float2* inc = a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN);
+      const float2* inc = a.in_s + ms_inc_offset(rec, slotNN, M, S, k, s, NN);
 #pragma unroll 2
       for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
         const int p = np.pix(q);
@@ -372,6 +418,8 @@ __global__ void __launch_bounds__(T, 1) k_step_ms(MsStepArgs a) {
   const float2* o_s = a.o_s + slotNN * S;
   const float2* d_s = a.d_s + slotNN * S;
   float2* u_s = a.u_s + slotNN;
+  const bool rec = a.recompute != 0;
+  float2* in_w = rec ? a.in_s + ms_inc_offset(true, slotNN, M, S, 0, 1, NN) : nullptr;
   const NatPairs<N, T> np;
   float A11 = 0.f, A12 = 0.f, A22 = 0.f;
   auto f2 = [](float4 v, int h) { return h ? make_float2(v.z, v.w) : make_float2(v.x, v.y); };
@@ -379,6 +427,7 @@ __global__ void __launch_bounds__(T, 1) k_step_ms(MsStepArgs a) {
   for (int k = 0; k < M; ++k) {
     const float2* Pk = a.probe + (size_t)k * NN;
     const float2* dPk = a.dP + (size_t)k * NN;
+    if (rec && S > 1) recompute_incident<N, T>(tile, tw, a.Hf, Pk, o_s, in_w, S);
 #pragma unroll 1
     for (int t = 0; t < 2; ++t) {   // t = 0: the object tangent u, 1: the probe tangent v
       __syncthreads();
@@ -394,7 +443,7 @@ __global__ void __launch_bounds__(T, 1) k_step_ms(MsStepArgs a) {
 #pragma unroll 1
       for (int s = 1; s < S; ++s) {
         propagate_tile<N, T, false>(tile, tw, a.Hf);
-        const float2* inc = a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN);
+        const float2* inc = a.in_s + ms_inc_offset(rec, slotNN, M, S, k, s, NN);
 #pragma unroll 2
         for (int q = 0; q < NatPairs<N, T>::STEPS; ++q) {
           const int p = np.pix(q);

@@ -35,6 +35,48 @@ __device__ __forceinline__ void propagate_cluster(cg::cluster_group& cluster, fl
   inv2d<C>(cluster, tile, twr, twc, twn, twq, q);
 }
 
+// recompute_incident over the cluster: CTA q writes its own rows of the
+// incident waves of slices 1..S-1 of mode Pk to inc; starts and ends
+// synchronised.
+template <class C>
+__device__ __forceinline__ void recompute_incident_cluster(cg::cluster_group& cluster, float2* tile,
+                                                           const float2* twr, const float2* twc, const float2* twn,
+                                                           const float2* twq, int q, const float2* __restrict__ Hf,
+                                                           const float2* Pk, const float2* o_s, float2* inc, int S) {
+  constexpr int N = C::N, T = C::T, LR = C::LR, NN = C::NN, NAT_STEPS = C::NAT_STEPS;
+  const int tid = threadIdx.x, rowbase = LR * q;
+  __syncthreads();
+#pragma unroll 2
+  for (int st = 0; st < NAT_STEPS; ++st) {
+    const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+    const int p = (rowbase + r) * N + c;
+    const float4 o2 = *(const float4*)(o_s + p);
+    const float4 P2 = __ldg((const float4*)(Pk + p));
+    store_pair(tile, C::tix(r, c), cmul(make_float2(P2.x, P2.y), make_float2(o2.x, o2.y)),
+               cmul(make_float2(P2.z, P2.w), make_float2(o2.z, o2.w)));
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int s = 1; s < S; ++s) {
+    propagate_cluster<C, false>(cluster, tile, twr, twc, twn, twq, q, Hf);
+    float2* in = inc + (size_t)(s - 1) * NN;
+    const bool last = s == S - 1;
+#pragma unroll 2
+    for (int st = 0; st < NAT_STEPS; ++st) {
+      const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
+      const int p = (rowbase + r) * N + c;
+      float2 x0, x1;
+      load_pair(tile, C::tix(r, c), x0, x1);
+      *(float4*)(in + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+      if (!last) {
+        const float4 o2 = *(const float4*)(o_s + (size_t)s * NN + p);
+        store_pair(tile, C::tix(r, c), cmul(x0, make_float2(o2.x, o2.y)), cmul(x1, make_float2(o2.z, o2.w)));
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // LS: the LSQML instantiation (as in k_pass1_ms).
 template <class C, bool LS>
 __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
@@ -84,6 +126,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
   const int M = a.M, S = a.S, mode = a.mode;
   const bool grad = mode != MODE_FWD;
   constexpr bool lsqml = LS;
+  const bool rec = a.recompute != 0, keep = grad && !rec;
   const size_t HW = (size_t)a.H * a.W;
   const float invN = 1.0f / (float)N;
   const size_t slotNN = (size_t)slot * NN;
@@ -120,7 +163,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
 #pragma unroll 1
     for (int s = 1; s < S; ++s) {
       propagate_cluster<C, false>(cluster, tile, twr, twc, twn, twq, q, a.Hf);
-      float2* inc = grad ? a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN) : nullptr;
+      float2* inc = keep ? a.in_s + ms_inc_offset(false, slotNN, M, S, k, s, NN) : nullptr;
       // LSQML: the slice's illumination sum_k |inc_k|^2
       float2* wsl = lsqml ? (float2*)(a.w_s + (slotNN * (S - 1) + (size_t)(s - 1) * NN)) : nullptr;
 #pragma unroll 2
@@ -129,7 +172,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
         const int p = (rowbase + r) * N + c;
         float2 x0, x1;
         load_pair(tile, C::tix(r, c), x0, x1);
-        if (grad) *(float4*)(inc + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        if (keep) *(float4*)(inc + p) = make_float4(x0.x, x0.y, x1.x, x1.y);
         if (lsqml) {
           float2 w2 = make_float2(cabs2(x0), cabs2(x1));
           if (k > 0) {
@@ -215,6 +258,9 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
 #pragma unroll 1
   for (int k = M - 1; k >= 0; --k) {
     const float2* Pk = a.probe + (size_t)k * NN;
+    if (rec && S > 1)
+      recompute_incident_cluster<C>(cluster, tile, twr, twc, twn, twq, q, a.Hf, Pk, o_s,
+                                    a.in_s + ms_inc_offset(true, slotNN, M, S, k, 1, NN), S);
     __syncthreads();
 #pragma unroll 2
     for (int st = 0; st < NAT_STEPS; ++st) {
@@ -227,7 +273,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
     inv2d<C>(cluster, tile, twr, twc, twn, twq, q);
 #pragma unroll 1
     for (int s = S - 1; s >= 1; --s) {
-      const float2* inc = a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN);
+      const float2* inc = a.in_s + ms_inc_offset(rec, slotNN, M, S, k, s, NN);
 #pragma unroll 2
       for (int st = 0; st < NAT_STEPS; ++st) {
         const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
@@ -417,12 +463,15 @@ __global__ void __launch_bounds__(C::T, 1) k_step_ms_cluster(MsStepArgs a) {
   const float2* o_s = a.o_s + slotNN * S;
   const float2* d_s = a.d_s + slotNN * S;
   float2* u_s = a.u_s + slotNN;
+  const bool rec = a.recompute != 0;
+  float2* in_w = rec ? a.in_s + ms_inc_offset(true, slotNN, M, S, 0, 1, NN) : nullptr;
   float A11 = 0.f, A12 = 0.f, A22 = 0.f;
   auto f2 = [](float4 v, int h) { return h ? make_float2(v.z, v.w) : make_float2(v.x, v.y); };
 #pragma unroll 1
   for (int k = 0; k < M; ++k) {
     const float2* Pk = a.probe + (size_t)k * NN;
     const float2* dPk = a.dP + (size_t)k * NN;
+    if (rec && S > 1) recompute_incident_cluster<C>(cluster, tile, twr, twc, twn, twq, q, a.Hf, Pk, o_s, in_w, S);
 #pragma unroll 1
     for (int t = 0; t < 2; ++t) {   // t = 0: the object tangent u, 1: the probe tangent v
       __syncthreads();
@@ -439,7 +488,7 @@ __global__ void __launch_bounds__(C::T, 1) k_step_ms_cluster(MsStepArgs a) {
 #pragma unroll 1
       for (int s = 1; s < S; ++s) {
         propagate_cluster<C, false>(cluster, tile, twr, twc, twn, twq, q, a.Hf);
-        const float2* inc = a.in_s + ((slotNN * M + (size_t)k * NN) * (S - 1) + (size_t)(s - 1) * NN);
+        const float2* inc = a.in_s + ms_inc_offset(rec, slotNN, M, S, k, s, NN);
 #pragma unroll 2
         for (int st = 0; st < NAT_STEPS; ++st) {
           const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;

@@ -46,7 +46,7 @@ struct MsLayout {
   size_t hdr, Hf, psi, o, in, go, h, valid, total;
 };
 
-MsLayout ms_layout(const ptycho_dims& d, int S, int B) {
+MsLayout ms_layout(const ptycho_dims& d, int S, int B, bool recompute) {
   MsLayout L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -59,7 +59,8 @@ MsLayout ms_layout(const ptycho_dims& d, int S, int B) {
   L.Hf = take(NN * sizeof(float2));
   L.psi = take((size_t)B * M * NN * sizeof(float2));
   L.o = take((size_t)B * S * NN * sizeof(float2));
-  L.in = take((size_t)B * M * (S > 1 ? S - 1 : 0) * NN * sizeof(float2));
+  // incident waves: every mode's kept by the forward pass, or one mode's at a time
+  L.in = take((size_t)B * (recompute ? 1 : M) * (S > 1 ? S - 1 : 0) * NN * sizeof(float2));
   L.go = take((size_t)B * S * NN * sizeof(float2));
   L.h = take((size_t)B * M * NN * sizeof(float2));
   L.valid = take((size_t)B * sizeof(int));
@@ -70,7 +71,7 @@ MsLayout ms_layout(const ptycho_dims& d, int S, int B) {
 ptycho_status check_ms(const ptycho_dims* d, const ptycho_multislice* ms) {
   const ptycho_status st = check_dims(d);
   if (st != PTYCHO_OK) return st;
-  if (!ms || ms->reserved != 0) return PTYCHO_ERR_ARG;
+  if (!ms || (ms->recompute != 0 && ms->recompute != 1)) return PTYCHO_ERR_ARG;
   if (ms->S < 1 || ms->S > 16) return PTYCHO_ERR_UNSUPPORTED;
   if (!(ms->wavelength > 0.0) || !(ms->pixel_size > 0.0) || !(fabs(ms->dz) < 1e300)) return PTYCHO_ERR_ARG;
   if ((int64_t)ms->S * d->H * d->W > ((int64_t)1 << 31) - 1) return PTYCHO_ERR_ARG;
@@ -104,9 +105,9 @@ struct MsLsqmlLayout {
   size_t acc, w, dPacc, Dp, dP, Sp, Cp, Sdp, smax, d, u, part, dsum, total;
 };
 
-MsLsqmlLayout ms_lsqml_layout(const ptycho_dims& d, int S, int B) {
+MsLsqmlLayout ms_lsqml_layout(const ptycho_dims& d, int S, int B, bool recompute) {
   MsLsqmlLayout L;
-  L.base = ms_layout(d, S, B);
+  L.base = ms_layout(d, S, B, recompute);
   size_t off = L.base.total;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -332,7 +333,7 @@ cudaError_t pass2_ms(int N, const MsPass2Args& a, const MsStepArgs& t, cudaStrea
 // Fills the propagator and the common arguments; returns the layout.
 MsLayout ms_setup(const ptycho_dims& d, const ptycho_multislice& ms, int batch, void* ws, MsArgs& a, cudaStream_t s,
                   cudaError_t* err) {
-  const MsLayout L = ms_layout(d, ms.S, batch);
+  const MsLayout L = ms_layout(d, ms.S, batch, ms.recompute != 0);
   char* b = (char*)ws;
   memset(&a, 0, sizeof(a));
   a.H = d.H; a.W = d.W; a.M = d.M; a.J = d.J; a.S = ms.S;
@@ -340,6 +341,7 @@ MsLayout ms_setup(const ptycho_dims& d, const ptycho_multislice& ms, int batch, 
   a.psi_s = (float2*)(b + L.psi);
   a.o_s = (float2*)(b + L.o);
   a.in_s = ms.S > 1 ? (float2*)(b + L.in) : nullptr;
+  a.recompute = ms.recompute;
   a.go_s = (float2*)(b + L.go);
   a.h_s = (float2*)(b + L.h);
   a.valid = (int*)(b + L.valid);
@@ -359,7 +361,7 @@ extern "C" {
 
 size_t ptycho_workspace_bytes_ms(const ptycho_dims* dims, const ptycho_multislice* ms, int32_t batch) {
   if (check_ms(dims, ms) != PTYCHO_OK || batch < 1) return 0;
-  return ms_layout(*dims, ms->S, batch).total;
+  return ms_layout(*dims, ms->S, batch, ms->recompute != 0).total;
 }
 
 ptycho_status ptycho_forward_ms(const ptycho_dims* dims, const ptycho_multislice* ms, const float* object,
@@ -368,7 +370,8 @@ ptycho_status ptycho_forward_ms(const ptycho_dims* dims, const ptycho_multislice
   ptycho_status st = check_ms(dims, ms);
   if (st != PTYCHO_OK) return st;
   if (batch < 1 || !object || !probe || (dims->J > 0 && (!pos || !I_pred))) return PTYCHO_ERR_ARG;
-  if ((st = check_ws(ws, ws_bytes, ms_layout(*dims, ms->S, batch).total)) != PTYCHO_OK) return st;
+  if ((st = check_ws(ws, ws_bytes, ms_layout(*dims, ms->S, batch, ms->recompute != 0).total)) != PTYCHO_OK)
+    return st;
   if (dims->J == 0) return PTYCHO_OK;
   cudaStream_t s = (cudaStream_t)stream;
   MsArgs a;
@@ -395,7 +398,8 @@ ptycho_status ptycho_adjoint_ms(const ptycho_dims* dims, const ptycho_multislice
   if (noise != PTYCHO_NOISE_GAUSSIAN && noise != PTYCHO_NOISE_POISSON && noise != PTYCHO_NOISE_VJP)
     return PTYCHO_ERR_ARG;
   if (!object || !probe || !g_object || !g_probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
-  if ((st = check_ws(ws, ws_bytes, ms_layout(*dims, ms->S, batch).total)) != PTYCHO_OK) return st;
+  if ((st = check_ws(ws, ws_bytes, ms_layout(*dims, ms->S, batch, ms->recompute != 0).total)) != PTYCHO_OK)
+    return st;
   if (dims->J == 0) return PTYCHO_OK;
   cudaStream_t s = (cudaStream_t)stream;
   MsArgs a;
@@ -422,7 +426,7 @@ ptycho_status ptycho_adjoint_ms(const ptycho_dims* dims, const ptycho_multislice
 size_t ptycho_workspace_bytes_lsqml_ms(const ptycho_dims* dims, const ptycho_multislice* ms,
                                         const ptycho_lsqml_opts* opts) {
   if (check_ms(dims, ms) != PTYCHO_OK || check_opts(opts) != PTYCHO_OK) return 0;
-  return ms_lsqml_layout(*dims, ms->S, opts->batch).total;
+  return ms_lsqml_layout(*dims, ms->S, opts->batch, ms->recompute != 0).total;
 }
 
 ptycho_status ptycho_lsqml_epoch_ms(const ptycho_dims* dims, const ptycho_multislice* ms, float* object, float* probe,
@@ -435,7 +439,7 @@ ptycho_status ptycho_lsqml_epoch_ms(const ptycho_dims* dims, const ptycho_multis
   if (opts->precision != PTYCHO_PRECISION_FP32 || opts->update_positions || opts->object_per_epoch)
     return PTYCHO_ERR_UNSUPPORTED;
   if (!object || !probe || (dims->J > 0 && (!pos || !meas))) return PTYCHO_ERR_ARG;
-  const MsLsqmlLayout L = ms_lsqml_layout(*dims, ms->S, opts->batch);
+  const MsLsqmlLayout L = ms_lsqml_layout(*dims, ms->S, opts->batch, ms->recompute != 0);
   if ((st = check_ws(ws, ws_bytes, L.total)) != PTYCHO_OK) return st;
   auto body = [&](cudaStream_t s) -> ptycho_status {
     const ptycho_dims& d = *dims;
@@ -497,6 +501,7 @@ ptycho_status ptycho_lsqml_epoch_ms(const ptycho_dims* dims, const ptycho_multis
       t.H = d.H; t.W = d.W; t.M = M; t.J = d.J; t.S = S;
       t.order = order; t.b0 = a.b0; t.nb = a.nb;
       t.probe = (const float2*)probe; t.Hf = a.Hf; t.o_s = a.o_s; t.in_s = a.in_s; t.d_s = q.d_s; t.dP = dP;
+      t.recompute = a.recompute;
       t.u_s = (float2*)(b + L.u); t.valid = a.valid; t.part = (double*)(b + L.part);
       if (pass2_ms(d.N, q, t, s) != cudaSuccess) return PTYCHO_ERR_CUDA;
       if (clear_acc(false, ptycho_dims{(int32_t)(S * d.H), d.W, d.N, d.M, d.J}, a.nb, a.b0, pos, order, a.valid, acc,

@@ -66,6 +66,28 @@ def test_workspace_bytes_host_logic(L):
     assert L.ptycho_host_workspace_bytes(ctypes.byref(d), 4) > a
 
 
+def test_multislice_workspace_keeps_one_mode_of_incident_waves_when_recomputing(L):
+    from paper_2510_20929_gb300 import api
+    N, M, S, B = 32, 3, 4, 8
+    d = _dims(H=96, W=100, N=N, M=M, J=20)
+    keep = L.ptycho_workspace_bytes_ms(ctypes.byref(d), ctypes.byref(api.make_multislice(S, 2e-6, 1e-10, 1e-8)), B)
+    rec = L.ptycho_workspace_bytes_ms(ctypes.byref(d), ctypes.byref(api.make_multislice(S, 2e-6, 1e-10, 1e-8,
+                                                                                        recompute=True)), B)
+    # B (M - 1) (S - 1) N^2 complex64 fewer (up to the 256-byte alignment of the section)
+    assert abs((keep - rec) - B * (M - 1) * (S - 1) * N * N * 8) < 256
+    opts = api.make_opts(batch=B)
+    keep_l = L.ptycho_workspace_bytes_lsqml_ms(ctypes.byref(d), ctypes.byref(api.make_multislice(S, 2e-6, 1e-10, 1e-8)),
+                                               ctypes.byref(opts))
+    rec_l = L.ptycho_workspace_bytes_lsqml_ms(
+        ctypes.byref(d), ctypes.byref(api.make_multislice(S, 2e-6, 1e-10, 1e-8, recompute=True)), ctypes.byref(opts))
+    assert keep_l - rec_l == keep - rec
+    bad = api.make_multislice(S, 2e-6, 1e-10, 1e-8)
+    bad.recompute = 2
+    assert L.ptycho_workspace_bytes_ms(ctypes.byref(d), ctypes.byref(bad), B) == 0
+    ws = ctypes.create_string_buffer(16)
+    assert L.ptycho_forward_ms(ctypes.byref(d), ctypes.byref(bad), ws, ws, ws, ws, B, ws, 16, None) == 1   # ERR_ARG
+
+
 def test_arguments_rejected_before_any_launch(L):
     from paper_2510_20929_gb300 import api
     P = ctypes.c_void_p

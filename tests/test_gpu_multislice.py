@@ -186,3 +186,56 @@ def test_lsqml_epoch_ms_graph_replay_equals_eager_and_rejects_unsupported_option
         with pytest.raises(api.PtychoError) as ex:
             api.lsqml_epoch_ms(dO, dP, dpos, dI, None, ms, api.make_opts(batch=4, **bad))
         assert ex.value.status == 6
+
+
+# ----------------------------------------------------------------------------- recompute-in-backward
+@pytest.mark.parametrize("N,M,S,H,W,J,step,dz", CASES[1:])
+def test_adjoint_ms_recomputing_the_incident_waves_matches_oracle_and_the_kept_waves(N, M, S, H, W, J, step, dz):
+    from paper_2510_20929_gb300 import api
+    Os, P, pos, Hf, I_m = ms_problem(N, M, S, H, W, J, step, dz)
+    L_ref, gO_ref, gP_ref, gr_ref = orc.loss_and_gradients_ms(Os, P, pos, Hf, I_m, orc.POISSON, 1e-6)
+    out = {}
+    for rec in (False, True):
+        out[rec] = api.adjoint_ms(*_dev(Os, P, pos, I_m), api.make_multislice(S, dz, LAM, PX, recompute=rec),
+                                  "poisson", eps=1e-6, batch=4)
+    loss, gO, gP, gr = out[True]
+    e = [abs(loss.item() - L_ref) / abs(L_ref), err(gO.cpu().numpy(), gO_ref, axis=0),
+         err(gP.cpu().numpy(), gP_ref, axis=0), err(gr.cpu().numpy(), gr_ref, axis=1)]
+    print(f"adjoint_ms recompute N={N} M={M} S={S}:", " ".join(f"{x:.2e}" for x in e))
+    assert max(e) < TOL_GRAD
+    # the recomputed waves are the kept ones bit for bit; only the order of the
+    # scatter's atomic additions differs between the two runs
+    l0, g0, p0, r0 = out[False]
+    assert err(gO.cpu().numpy(), g0.cpu().numpy(), axis=0) < 1e-6
+    assert err(gP.cpu().numpy(), p0.cpu().numpy(), axis=0) < 1e-6
+    assert err(gr.cpu().numpy(), r0.cpu().numpy(), axis=1) < 1e-6
+    assert abs(loss.item() - l0.item()) <= 1e-9 * abs(l0.item())
+
+
+@pytest.mark.parametrize("N,M,S,H,W,J,step,dz,batch", [
+    (16, 2, 3, 41, 37, 9, 3.0, 40e-6, 4),
+    (128, 2, 3, 290, 300, 6, 30.0, 2e-6, 4),
+    (192, 1, 2, 230, 236, 4, 12.0, 2e-6, 3),
+    (256, 2, 3, 290, 296, 3, 12.0, 2e-6, 2),
+])
+def test_lsqml_epoch_ms_recomputing_the_incident_waves_matches_oracle(N, M, S, H, W, J, step, dz, batch):
+    import torch
+    from paper_2510_20929_gb300 import api
+    Os, P, pos, Hf, I_m = ms_problem(N, M, S, H, W, J, step, dz)
+    order = np.random.default_rng(7).permutation(J).astype(np.int32)
+    kw = dict(batch=batch, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6)
+    O_ref, P_ref, L_ref, a_ref = orc.lsqml_epoch_ms(Os, P, pos, I_m, order, Hf,
+                                                    orc.LsqmlOptions(noise=orc.GAUSSIAN, **kw))
+    res = {}
+    for rec in (False, True):
+        dO, dP, dpos, dI = _dev(Os, P, pos, I_m)
+        loss, alpha = api.lsqml_epoch_ms(dO, dP, dpos, dI, to_dev(order, torch.int32),
+                                         api.make_multislice(S, dz, LAM, PX, recompute=rec), want_alpha=True, **kw)
+        res[rec] = (dO.cpu().numpy(), dP.cpu().numpy(), alpha.cpu().numpy(), loss.item())
+    O1, P1, a1, l1 = res[True]
+    e = dict(O=err(O1, O_ref, axis=0), P=err(P1, P_ref, axis=0), alpha=err(a1, a_ref, axis=1),
+             loss=abs(l1 - L_ref) / abs(L_ref))
+    print(f"lsqml_ms recompute N={N} M={M} S={S}: " + " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    assert e["loss"] < TOL_FWD and max(e["O"], e["P"], e["alpha"]) < TOL_GRAD
+    O0, P0, a0, l0 = res[False]
+    assert err(O1, O0, axis=0) < 1e-6 and err(P1, P0, axis=0) < 1e-6 and err(a1, a0, axis=1) < 1e-6
