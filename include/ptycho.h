@@ -123,7 +123,9 @@ typedef struct {
  *       distributed shared memory, two pairs per SM (2); windows 192/256: one;
  *   [1] the step-size pass: one kernel per position (0), or the partial sums
  *       spread over 8 chunks of every position, then a
- *       per-position solve and update (1);
+ *       per-position solve and update (1), or (windows <= 128) a cluster of 4
+ *       CTAs per position adding their partial sums over distributed shared
+ *       memory, at 4 (2) or 3 (3) CTAs per SM;
  *   [2] the probe reduction: 16 (0), 8 (1) or 32 (2) positions in flight per
  *       thread. */
 #define PTYCHO_FLAG_AUTOTUNE 2

@@ -387,7 +387,8 @@ struct TuneKey {
   }
 };
 // v[0]: the per-position pass (candidates: pass1_variants(N)), v[1]: the
-// step-size pass (single kernel, split), v[2]: the probe reduction (positions
+// step-size pass (candidates: pass2_variants(N): single kernel, split, cluster
+// at 4 or 3 CTAs per SM), v[2]: the probe reduction (positions
 // in flight per thread: 16, 8, 32); ms[i][c]: candidate c's mean time.
 struct TuneEntry {
   TuneKey key;
@@ -396,7 +397,8 @@ struct TuneEntry {
 };
 
 static int pass1_variants(int N) { return N == 128 ? 3 : (N <= 128 ? 2 : 1); }
-static constexpr int kPass2Variants = 2, kReduceVariants = 3;
+static int pass2_variants(int N) { return N <= 128 ? 4 : 2; }
+static constexpr int kReduceVariants = 3;
 static std::mutex g_tune_mu;
 static std::vector<TuneEntry> g_tune;
 
@@ -614,8 +616,9 @@ static ptycho_status autotune(const ptycho_dims& d, float2* obj, float2* probe, 
     q.sc = sc;
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
-    for (int v = 0; v < kPass2Variants; ++v) t->ms[1][v] = time_launch(s, 3, [&] { return pass2(N, q, s, v); });
-    t->v[1] = best(t->ms[1], kPass2Variants);
+    const int n2 = pass2_variants(N);
+    for (int v = 0; v < n2; ++v) t->ms[1][v] = time_launch(s, 3, [&] { return pass2(N, q, s, v); });
+    t->v[1] = best(t->ms[1], n2);
   }
   // restore the epoch's starting state of the accumulators and scalars
   if (cudaMemsetAsync(w.acc, 0, (size_t)HW * sizeof(float4), s) != cudaSuccess) return PTYCHO_ERR_CUDA;
@@ -764,7 +767,7 @@ ptycho_status ptycho_tuning_set(const ptycho_dims* dims, int32_t batch, const in
   ptycho_status st = check_dims(dims);
   if (st != PTYCHO_OK) return st;
   if (batch < 1 || !variants) return PTYCHO_ERR_ARG;
-  const int n[PTYCHO_TUNE_KERNELS] = {pass1_variants(dims->N), kPass2Variants, kReduceVariants};
+  const int n[PTYCHO_TUNE_KERNELS] = {pass1_variants(dims->N), pass2_variants(dims->N), kReduceVariants};
   for (int i = 0; i < PTYCHO_TUNE_KERNELS; ++i)
     if (variants[i] < 0 || variants[i] >= n[i]) return PTYCHO_ERR_ARG;
   int dev = 0;

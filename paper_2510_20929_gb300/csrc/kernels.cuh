@@ -17,10 +17,12 @@
 //   least-squares step (LSQML's self-adaptive step sizes, Sec. 2.2), the
 //   FP64 2x2 solve, and the alpha-weighted object scatter.
 #pragma once
+#include <cooperative_groups.h>
 #include "common.cuh"
 #include "tc.cuh"
 
 namespace ptycho {
+namespace cg = cooperative_groups;
 
 // CTA sizes of the per-position pass: the default and the alternative the
 // autotuner may pick (the full count of line slots N*R1, or half of it with
@@ -888,6 +890,142 @@ __global__ void __launch_bounds__(PASS2U_T, 2) k_pass2_update(Pass2Args a) {
   }
 }
 
+// Cluster form of the step-size pass (N <= 128): the PASS2C_C CTAs of a
+// cluster share one position. CTA q reduces rows [q N/C, (q+1) N/C) of the
+// patch and chunk q of the h planes and keeps its rows of g in shared memory;
+// the C partial sums meet over distributed shared memory and are added in
+// rank order, so every CTA holds the same FP64 totals and solves the 2x2
+// system itself; then CTA q scatters the object update of its band of the
+// (N+1)^2 tile (rows q N/C .. (q+1) N/C - 1, the last band also row N) from
+// its own rows of g and, for its first row, the row above from L2. Against
+// one CTA per position: four times the CTAs (the minibatch no longer leaves
+// some SMs with one position and others with two), the serial solve of one
+// cluster overlaps the streams of the others, and g is read once.
+constexpr int PASS2C_T = 256, PASS2C_C = 4;
+
+template <int N, int MINB>
+__global__ void __cluster_dims__(PASS2C_C, 1, 1) __launch_bounds__(PASS2C_T, MINB) k_pass2_cluster(Pass2Args a) {
+  constexpr int NN = N * N, T = PASS2C_T, C = PASS2C_C, RB = N / C, N1 = N + 1;
+  static_assert(N % C == 0 && N <= 128, "bands of whole rows, g band in static shared memory");
+  wait_prior_grid();
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ double red[32 * 5];
+  __shared__ double part[5];
+  __shared__ double alpha_sh;
+  __shared__ __align__(16) float2 gsh[RB * N];
+  const int q = (int)cluster.block_rank();
+  const int slot = blockIdx.x / C, tid = threadIdx.x;
+  if (!a.valid[slot]) return;   // the same decision in every CTA of the cluster
+  const int e = a.b0 + slot;
+  const int j = a.order ? a.order[e] : e;
+  int ty, tx;
+  float fy, fx;
+  tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
+  const float w00 = (1.f - fy) * (1.f - fx), w01 = (1.f - fy) * fx, w10 = fy * (1.f - fx), w11 = fy * fx;
+  const float damp = a.delta_o * __uint_as_float(a.sc->max_illum);
+  const size_t slotNN = (size_t)slot * NN;
+  const int M = a.M;
+  const float2* g_s = a.g_s + slotNN;
+  const float2* o_s = a.o_s + slotNN;
+  const float2* h_s = a.h_s + slotNN * M;
+
+  const int p_lo = q * RB * N;
+  float A11 = 0.f, A12 = 0.f, A22 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll 1
+  for (int i = tid; i < RB * N; i += T) {
+    const int p = p_lo + i, r = p / N, c = p % N;
+    const float2 g = __ldcs(g_s + p);
+    const float2 o = __ldcs(o_s + p);
+    gsh[i] = g;
+    float2 d = make_float2(0.f, 0.f);
+    if (a.update_object) d = dohat(a.acc + (size_t)(ty + r) * a.W + (tx + c), a.W, w00, w01, w10, w11, damp);
+    const float sp = __ldg(a.Sp + p), sdp = __ldg(a.Sdp + p);
+    const float2 cp = __ldg(a.Cp + p);
+    A11 += cabs2(d) * sp;
+    const float2 od = cmulc(d, o);           // conj(d) o
+    A12 += od.x * cp.x - od.y * cp.y;        // Re(conj(d) o Cp)
+    A22 += cabs2(o) * sdp;
+    b1 += d.x * g.x + d.y * g.y;             // Re(conj(d) g)
+  }
+  if (a.update_probe) {
+    // b2 over chunk q of the h planes (contiguous pixel pairs)
+    const float4* h4 = (const float4*)h_s;
+    const float4* d4 = (const float4*)a.dP;
+    const int Q = M * NN / 2;
+    const int q_lo = (int)((long long)Q * q / C), q_hi = (int)((long long)Q * (q + 1) / C);
+    int k = q_lo + tid;
+    for (; k + 3 * T < q_hi; k += 4 * T) {   // four independent 16-byte streams per thread
+      float4 dp[4], h[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        dp[u] = __ldg(d4 + k + u * T);
+        h[u] = __ldcs(h4 + k + u * T);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) b2 += dp[u].x * h[u].x + dp[u].y * h[u].y + dp[u].z * h[u].z + dp[u].w * h[u].w;
+    }
+    for (; k < q_hi; k += T) {
+      const float4 dp = __ldg(d4 + k);
+      const float4 h = __ldcs(h4 + k);
+      b2 += dp.x * h.x + dp.y * h.y + dp.z * h.z + dp.w * h.w;   // Re(conj(dP_k) h_k)
+    }
+  }
+  double v[5] = {A11, A12, A22, b1, b2};
+  block_sum<5>(v, red);
+  if (tid == 0)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) part[i] = v[i];
+  cluster.sync();   // every CTA's partials (and its g band) are written
+  if (tid == 0) {
+    double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      const double* pr = cluster.map_shared_rank(part, r);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) t[i] += pr[i];
+    }
+    const double a11 = t[0], a12 = t[1], a22 = t[2], r1 = t[3], r2 = t[4];
+    const double tr = 0.5 * (a11 + a22);
+    const double d11 = a11 + a.lam * tr, d22 = a22 + a.lam * tr;
+    const double det = d11 * d22 - a12 * a12;
+    double aO, aP;
+    if (det > 0.0) {
+      aO = (d22 * r1 - a12 * r2) / det;
+      aP = (d11 * r2 - a12 * r1) / det;
+    } else {
+      aO = d11 > 0.0 ? r1 / d11 : 0.0;
+      aP = d22 > 0.0 ? r2 / d22 : 0.0;
+    }
+    alpha_sh = aO;
+    if (q == 0) {
+      if (a.alpha_out) {
+        a.alpha_out[2 * j] = aO;
+        a.alpha_out[2 * j + 1] = aP;
+      }
+      atomicAdd(&a.sc->sum_alpha_p, aP);
+      atomicAdd(&a.sc->count, 1);
+    }
+  }
+  cluster.sync();   // no CTA leaves while another reads its partials; alpha_sh is visible
+  if (!a.update_object) return;
+  const float aO = (float)alpha_sh;
+  const float c00 = aO * w00, c01 = aO * w01, c10 = aO * w10, c11 = aO * w11;
+  const int y0 = q * RB, y1 = y0 + RB + (q == C - 1 ? 1 : 0);
+  // g at patch row yy (y0 - 1 <= yy < y0 + RB): the band from shared memory, the row above from L2
+  auto gat = [&](int yy, int xx) { return yy >= y0 ? gsh[(yy - y0) * N + xx] : __ldg(g_s + yy * N + xx); };
+  for (int i = tid; i < (y1 - y0) * N1; i += T) {
+    const int y = y0 + i / N1, x = i % N1;
+    float2 sacc = make_float2(0.f, 0.f);
+    if (y < N && x < N) { const float2 g = gat(y, x); sacc.x += c00 * g.x; sacc.y += c00 * g.y; }
+    if (y < N && x > 0) { const float2 g = gat(y, x - 1); sacc.x += c01 * g.x; sacc.y += c01 * g.y; }
+    if (y > 0 && x < N) { const float2 g = gat(y - 1, x); sacc.x += c10 * g.x; sacc.y += c10 * g.y; }
+    if (y > 0 && x > 0) { const float2 g = gat(y - 1, x - 1); sacc.x += c11 * g.x; sacc.y += c11 * g.y; }
+    const size_t oi = (size_t)(ty + y) * a.W + (tx + x);
+    const float inv = 1.f / (__ldg(&a.acc[oi].z) + damp);
+    atomicAdd(a.obj + oi, make_float2(sacc.x * inv, sacc.y * inv));
+  }
+}
+
 }  // namespace ptycho
 
 namespace ptycho {
@@ -926,10 +1064,17 @@ cudaError_t launch_pass1(const BatchArgs& a, cudaStream_t s, int variant) {
 }
 
 // variant 0: the single-kernel form of PASS2_T threads, 1: the split form
-// (when the partials buffer is given)
+// (when the partials buffer is given), 2 and 3: the cluster form at four and
+// three CTAs per SM (64 and 80 registers; N <= 128, not OPR)
 template <int N>
 cudaError_t launch_pass2(const Pass2Args& a, cudaStream_t s, int variant) {
   if (a.nb <= 0) return cudaSuccess;
+  if constexpr (N <= 128) {
+    if (variant == 2 && !a.opr_dU)
+      return launch_pdl(k_pass2_cluster<N, 4>, dim3(PASS2C_C * a.nb), dim3(PASS2C_T), 0, s, a);
+    if (variant == 3 && !a.opr_dU)
+      return launch_pdl(k_pass2_cluster<N, 3>, dim3(PASS2C_C * a.nb), dim3(PASS2C_T), 0, s, a);
+  }
   if (a.part && variant == 1) {
     cudaError_t e = a.opr_dU
         ? launch_pdl(k_pass2_sums<N, true>, dim3(P2_CHUNKS, a.nb), dim3(PASS2S_T), 0, s, a)
