@@ -697,6 +697,11 @@ def run_uneven(args, rank, world, local_rank, opr_K=0):
             "speedup_vs_sequential": ms_seq / ms_g,
             "alone_ms": alone, "longest_chain_ms": max(alone),
             "batched_over_longest_chain": ms_g / max(alone),
+            # the batched epoch against the reconstructions' epochs timed one by one,
+            # and where those epochs spend their time, per window size
+            "sum_alone_ms": sum(alone), "batched_over_sum_alone": ms_g / sum(alone),
+            "alone_ms_per_window": {str(n): sum(a for a, w in zip(alone, ws) if w["N"] == n)
+                                    for n in sorted({w["N"] for w in ws})},
         }), flush=True)
 
 

@@ -1,20 +1,27 @@
 // Per-position pass for windows larger than one CTA's shared memory, on a
-// cluster of Q CTAs (N = 256: Q = 4; N = 192: Q = 3).
+// cluster of Q CTAs (N = 256: Q = 4; N = 192: Q = 3; and a pair of CTAs for
+// the 128 window).
 //
-// The N x N complex tile is shared by the cluster: CTA q holds the 64 rows
-// 64q .. 64q+63 (N = 64 Q). The 2-D DFT runs as
+// The N x N complex tile is shared by the cluster: in the spatial domain CTA q
+// holds the 64 rows 64q .. 64q+63 (N = 64 Q). The 2-D DFT runs as
 //   * N-point transforms of the CTA's own rows (shared memory, as in the
 //     single-CTA kernel);
-//   * the column transform split as N = Q x 64 (decimation in time over the
-//     row index R = 64q + r): a Q-point DFT across the cluster for every
-//     (r, c), reading the other CTAs' tiles through distributed shared memory,
-//     times the twiddle W_N^(r k1), after which CTA k1 holds the inputs of
-//     the outputs k = k1 + Q k2; then 64-point transforms of its local columns;
-//   * the inverse mirrors it: local 64-point column inverses, the conjugate
-//     twiddle and Q-point inverse DFT across the cluster, local row inverses.
-// Everything else (patch gather, data term, back-propagation, scatter, the
-// position gradient) follows the single-CTA k_pass1 on the CTA's own rows;
-// the far fields of CTA q are the frequency rows q + Q k2.
+//   * a transpose across the cluster: CTA q gathers, from every CTA s, the
+//     64 x 64 block of s's rows at columns 64q .. 64q+63 (distributed shared
+//     memory), and stores it transposed, so that its local row x now holds
+//     column 64q + x of the whole tile (all N rows);
+//   * N-point transforms of those local rows, which are the columns.
+// CTA q then holds the far-field columns 64q .. 64q+63 (local row x = column
+// 64q + x, local column = frequency row). The inverse mirrors it (row
+// inverses, the same transpose back, row inverses). Each CTA reads 3/4 of its
+// 128 KB from the other CTAs once per transform (a Q-point DFT across the
+// cluster would read every element from every CTA: four times that).
+// Everything else (patch gather, back-propagation, scatter, the position
+// gradient) follows the single-CTA k_pass1 on the CTA's own spatial rows; the
+// far-field loops (intensity, data term, the inverse's input) walk the CTA's
+// columns with consecutive threads on consecutive columns (freq_index), so
+// that the measured intensities and the predicted ones are read and written
+// coalesced in their natural [k_y][k_x] order.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -62,168 +69,123 @@ struct RectAddr {
   }
 };
 
-template <int N_, int Q_, int T_, int RR1_, int RR2_, bool RINTER_, bool CINTER_, class Z_, int MINB_ = 1>
+template <int N_, int Q_, int T_, int RR1_, int RR2_, bool RINTER_, class Z_, int MINB_ = 1>
 struct Cfg {
   static constexpr int N = N_, Q = Q_, T = T_, LR = 64, NN = N * N, LNN = LR * N;
   static constexpr int MINB = MINB_;   // CTAs per SM the launch bounds ask for
   static constexpr int RR1 = RR1_, RR2 = RR2_;
   using Z = Z_;
   using RowF = LineFft<RR1, RR2, RINTER_, RectAddr<N, Z>>;   // N-point rows
-  using ColF = LineFft<8, 8, CINTER_, RectAddr<N, Z>>;       // 64-point local columns
-  static constexpr int ROW_ITER = LR * RR1 / T, COL_ITER = N * 8 / T;
+  static constexpr int ROW_ITER = LR * RR1 / T;
   static constexpr int NAT_STEPS = LNN / (2 * T);              // natural pixel pairs per thread
-  static constexpr int XB = N / 64, XPAIRS = 2048 / T;        // exchange column blocks, pairs per thread
-  static_assert(ROW_ITER >= 1 && COL_ITER >= 1 && XPAIRS >= 1, "CTA size");
+  static constexpr int XG = (T >= 1024 && Q % 2 == 0) ? 2 : 1;   // transpose rounds per cluster barrier
+  static_assert(ROW_ITER >= 1 && 2048 % T == 0 && LNN % T == 0, "CTA size");
   __device__ __forceinline__ static int tix(int r, int c) { return r * N + (c ^ Z::fr(r) ^ Z::fcb(c)); }
+  // far-field element e (0 .. LNN-1) of CTA q: local row x = e % 64 (column
+  // 64q + x of the far field), local column ky = e / 64 (its row)
+  __device__ __forceinline__ static void freq_index(int e, int& x, int& ky) {
+    x = e & 63;
+    ky = e >> 6;
+  }
   struct Smem {
-    static constexpr int RP = N + 16;
+    static constexpr int RP = N + 1;   // intensity plane [64][RP]: the column walk is conflict-free
     static constexpr size_t red = 0;
     static constexpr size_t tile = red + 256 * sizeof(double);
     static constexpr size_t twr = tile + (size_t)LNN * sizeof(float2);
-    static constexpr size_t twc = twr + RR1 * (RR2 + 1) * sizeof(float2);
-    static constexpr size_t twn = twc + 8 * 9 * sizeof(float2);
-    static constexpr size_t twq = twn + N * sizeof(float2);
-    static constexpr size_t rI = twq + 8 * sizeof(float2);
+    static constexpr size_t rI = twr + RR1 * (RR2 + 1) * sizeof(float2);
     static constexpr size_t bytes = rI + (size_t)LR * RP * sizeof(float);
   };
 };
 
-using Cfg256 = Cfg<256, 4, 1024, 16, 16, false, true, Swz256>;
+using Cfg256 = Cfg<256, 4, 1024, 16, 16, false, Swz256>;
 // the 128 window on a pair of CTAs (64 rows each) that fit two to an SM
-using Cfg128 = Cfg<128, 2, 512, 8, 16, true, true, Swz128, 2>;
-using Cfg192 = Cfg<192, 3, 512, 8, 24, true, false, Swz192>;
+using Cfg128 = Cfg<128, 2, 512, 8, 16, true, Swz128, 2>;
+using Cfg192 = Cfg<192, 3, 512, 8, 24, true, Swz192>;
 
-// a * W_Q^m (W_Q = e^{-2 pi i / Q}) from the table twq[m mod Q].
-template <int Q>
-__device__ __forceinline__ float2 wqmul(float2 a, int m, const float2* twq) {
-  if constexpr (Q == 4) {
-    switch (m & 3) {
-      case 0: return a;
-      case 1: return make_float2(a.y, -a.x);
-      case 2: return make_float2(-a.x, -a.y);
-      default: return make_float2(-a.y, a.x);
+// The transpose across the cluster: tile[x][64 s + r] <- tile_s[r][64 q + x]
+// for every CTA s of the cluster and r, x in 0..63. It runs in Q rounds; in
+// round t CTA q trades blocks with CTA s = (t - q) mod Q (a symmetric pairing:
+// the two read each other's block and then overwrite the block the other
+// has read; s = q transposes its own diagonal block). Block s of CTA q's tile
+// is read only by CTA s and overwritten only in the round that pairs the two,
+// after the barrier, so G rounds can share one cluster barrier: their reads
+// go to registers first (G x 4096 / T pixels per thread), then the barrier,
+// then the transposed stores. Ends synchronised.
+template <class C>
+__device__ __forceinline__ void transpose_exchange(cg::cluster_group& cluster, float2* tile, int q) {
+  constexpr int Q = C::Q, T = C::T, G = C::XG, P = 2048 / T;   // rounds per barrier, pairs per round
+  static_assert(Q % G == 0 && 2048 % T == 0, "rounds and pairs per thread");
+#pragma unroll 1
+  for (int t0 = 0; t0 < Q; t0 += G) {
+    float2 v[G][P][2];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int s = (t0 + g - q + Q) % Q;
+      const float2* src = cluster.map_shared_rank(tile, s);
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        const int p = (int)threadIdx.x + T * i;   // (r, pair of x): 64 x 32 pairs
+        const int r = p >> 5, x = 2 * (p & 31);
+        load_pair(src, C::tix(r, 64 * q + x), v[g][i][0], v[g][i][1]);
+      }
     }
-  } else {
-    const int mm = ((m % Q) + Q) % Q;
-    return mm == 0 ? a : cmul(a, twq[mm]);
+    cluster.sync();   // the blocks of these rounds are read in every CTA
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int s = (t0 + g - q + Q) % Q;
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        const int p = (int)threadIdx.x + T * i;
+        const int r = p >> 5, x = 2 * (p & 31);
+        tile[C::tix(x, 64 * s + r)] = v[g][i][0];
+        tile[C::tix(x + 1, 64 * s + r)] = v[g][i][1];
+      }
+    }
   }
+  __syncthreads();
 }
 
-// Cross-cluster Q-point DFT of the tiles, in blocks of 64 columns, two blocks
-// per cluster barrier when the block count is even (the barrier orders every
-// CTA's reads of a block before its owner overwrites it; fewer, larger steps
-// halve the barrier latency).
-// Forward: tile_q <- W_N^(r q) sum_q' W_Q^(q' q) tile_q'.
-// Inverse: tile_q <- sum_k1 W_Q^(-q k1) conj(W_N^(r k1)) tile_k1.
+// N-point transforms (forward: natural in, natural out) of the CTA's 64 local
+// rows, in place.
 template <class C, bool FWD>
-__device__ __forceinline__ void cross_exchange(cg::cluster_group& cluster, float2* tile, const float2* twn,
-                                               const float2* twq, int q) {
-  constexpr int Q = C::Q, P = C::XPAIRS, XB = C::XB, GB = (XB % 2 == 0 && C::MINB == 1) ? 2 : 1;
-  float2* src[Q];
-#pragma unroll
-  for (int qq = 0; qq < Q; ++qq) src[qq] = cluster.map_shared_rank(tile, qq);
-#pragma unroll 1
-  for (int h0 = 0; h0 < XB; h0 += GB) {
-    float2 acc[GB][P][2];
-#pragma unroll
-    for (int hh = 0; hh < GB; ++hh) {
-      const int h = h0 + hh;
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        const int p = 2 * (int)threadIdx.x + 2 * C::T * j;   // within a 64 x 64 block: 4096 pixels
-        const int rr = p / 64, cc = 64 * h + p % 64;
-        acc[hh][j][0] = acc[hh][j][1] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int qq = 0; qq < Q; ++qq) {
-          float2 x0, x1;
-          load_pair(src[qq], C::tix(rr, cc), x0, x1);
-          if constexpr (FWD) {
-            const int m = qq * q;
-            acc[hh][j][0] = cadd(acc[hh][j][0], wqmul<Q>(x0, m, twq));
-            acc[hh][j][1] = cadd(acc[hh][j][1], wqmul<Q>(x1, m, twq));
-          } else {
-            const float2 t = twn[rr * qq];     // W_N^(r k1), conjugated below
-            const int m = -(q * qq);
-            acc[hh][j][0] = cadd(acc[hh][j][0], wqmul<Q>(cmulc(t, x0), m, twq));
-            acc[hh][j][1] = cadd(acc[hh][j][1], wqmul<Q>(cmulc(t, x1), m, twq));
-          }
-        }
-      }
-    }
-    cluster.sync();   // every CTA has read these blocks of every tile
-#pragma unroll
-    for (int hh = 0; hh < GB; ++hh) {
-      const int h = h0 + hh;
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        const int p = 2 * (int)threadIdx.x + 2 * C::T * j;
-        const int rr = p / 64, cc = 64 * h + p % 64;
-        if constexpr (FWD) {
-          const float2 t = twn[rr * q];
-          store_pair(tile, C::tix(rr, cc), cmul(acc[hh][j][0], t), cmul(acc[hh][j][1], t));
-        } else {
-          store_pair(tile, C::tix(rr, cc), acc[hh][j][0], acc[hh][j][1]);
-        }
-      }
-    }
-  }
-  __syncthreads();
-}
-
-// 2-D forward DFT (unnormalised) of the cluster's tile; on return CTA q's tile
-// holds the frequency rows q + Q k2 (local row k2), natural layout.
-template <class C>
-__device__ __forceinline__ void fwd2d(cg::cluster_group& cluster, float2* tile, const float2* twr,
-                                      const float2* twc, const float2* twn, const float2* twq, int q) {
+__device__ __forceinline__ void row_pass(float2* tile, const float2* twr) {
   using RowF = typename C::RowF;
-  using ColF = typename C::ColF;
 #pragma unroll 1
   for (int it = 0; it < C::ROW_ITER; ++it) {
     const int n = RowF::line_lane(), row = RowF::line_slot() + (C::T / C::RR1) * it;
     float2 v[C::RR2];
-    RowF::template load_in<true>(v, tile, row, n);
-    RowF::template line_fwd<true>(v, tile, row, n, twr);
-    RowF::template store_out<true>(v, tile, row, n);
+    if constexpr (FWD) {
+      RowF::template load_in<true>(v, tile, row, n);
+      RowF::template line_fwd<true>(v, tile, row, n, twr);
+      RowF::template store_out<true>(v, tile, row, n);
+    } else {
+      RowF::template load_out<true>(v, tile, row, n);
+      RowF::template line_inv<true>(v, tile, row, n, twr);
+      RowF::template store_in<true>(v, tile, row, n);
+    }
   }
-  cluster.sync();
-  cross_exchange<C, true>(cluster, tile, twn, twq, q);
-#pragma unroll 1
-  for (int it = 0; it < C::COL_ITER; ++it) {
-    const int n = ColF::line_lane(), col = ColF::line_slot() + (C::T / 8) * it;
-    float2 v[8];
-    ColF::template load_in<false>(v, tile, col, n);
-    ColF::template line_fwd<false>(v, tile, col, n, twc);
-    ColF::template store_out<false>(v, tile, col, n);
-  }
+}
+
+// 2-D forward DFT (unnormalised) of the cluster's tile: CTA q holds the
+// spatial rows 64q .. on entry and the far-field columns 64q .. on return
+// (local row x = column 64q + x, natural order along it). Ends synchronised.
+template <class C>
+__device__ __forceinline__ void fwd2d(cg::cluster_group& cluster, float2* tile, const float2* twr, int q) {
+  row_pass<C, true>(tile, twr);
+  cluster.sync();   // every CTA's rows are transformed before any CTA reads them
+  transpose_exchange<C>(cluster, tile, q);
+  row_pass<C, true>(tile, twr);
   __syncthreads();
 }
 
-// 2-D inverse DFT (unnormalised): tile_q holds frequency rows q + Q k2 on entry
-// and the spatial rows 64q + r on return, natural layout.
+// 2-D inverse DFT (unnormalised): the far-field columns 64q .. on entry, the
+// spatial rows 64q .. on return. Ends synchronised.
 template <class C>
-__device__ __forceinline__ void inv2d(cg::cluster_group& cluster, float2* tile, const float2* twr,
-                                      const float2* twc, const float2* twn, const float2* twq, int q) {
-  using RowF = typename C::RowF;
-  using ColF = typename C::ColF;
-#pragma unroll 1
-  for (int it = 0; it < C::COL_ITER; ++it) {
-    const int n = ColF::line_lane(), col = ColF::line_slot() + (C::T / 8) * it;
-    float2 v[8];
-    ColF::template load_out<false>(v, tile, col, n);
-    ColF::template line_inv<false>(v, tile, col, n, twc);
-    ColF::template store_in<false>(v, tile, col, n);
-  }
-  __syncthreads();
+__device__ __forceinline__ void inv2d(cg::cluster_group& cluster, float2* tile, const float2* twr, int q) {
+  row_pass<C, false>(tile, twr);
   cluster.sync();
-  cross_exchange<C, false>(cluster, tile, twn, twq, q);
-#pragma unroll 1
-  for (int it = 0; it < C::ROW_ITER; ++it) {
-    const int n = RowF::line_lane(), row = RowF::line_slot() + (C::T / C::RR1) * it;
-    float2 v[C::RR2];
-    RowF::template load_out<true>(v, tile, row, n);
-    RowF::template line_inv<true>(v, tile, row, n, twr);
-    RowF::template store_in<true>(v, tile, row, n);
-  }
+  transpose_exchange<C>(cluster, tile, q);
+  row_pass<C, false>(tile, twr);
   __syncthreads();
 }
 
@@ -231,15 +193,13 @@ template <class C, bool OPR>
 __global__ void __launch_bounds__(C::T, C::MINB) k_pass1_cluster(BatchArgs a) {
   constexpr int N = C::N, Q = C::Q, T = C::T, LR = C::LR, NN = C::NN, LNN = C::LNN;
   constexpr int NAT_STEPS = C::NAT_STEPS;
+  static_assert(LNN % (2 * T) == 0, "data-term loop takes two elements per step");
   using SM = typename C::Smem;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem[];
   double* red = (double*)(smem + SM::red);
   float2* tile = (float2*)(smem + SM::tile);
   float2* twr = (float2*)(smem + SM::twr);
-  float2* twc = (float2*)(smem + SM::twc);
-  float2* twn = (float2*)(smem + SM::twn);
-  float2* twq = (float2*)(smem + SM::twq);
   float* rI = (float*)(smem + SM::rI);
   constexpr int RP = SM::RP;
 
@@ -261,17 +221,6 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_pass1_cluster(BatchArgs a) {
   }
   if (tid == 0 && q == 0 && a.valid) a.valid[slot] = 1;
   make_line_twiddles<N, C::RR1, C::RR2>(twr);
-  make_line_twiddles<64, 8, 8>(twc);
-  for (int m = tid; m < N + Q; m += T) {
-    float s, c;
-    if (m < N) {
-      sincospif(2.0f * (float)m / (float)N, &s, &c);
-      twn[m] = make_float2(c, -s);
-    } else {
-      sincospif(2.0f * (float)(m - N) / (float)Q, &s, &c);
-      twq[m - N] = make_float2(c, -s);
-    }
-  }
 
   const int M = a.M;
   const float invN = 1.0f / (float)N;
@@ -314,39 +263,39 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_pass1_cluster(BatchArgs a) {
       store_pair(tile, C::tix(r, c), cmul(make_float2(P2.x, P2.y), o0), cmul(make_float2(P2.z, P2.w), o1));
     }
     __syncthreads();
-    fwd2d<C>(cluster, tile, twr, twc, twn, twq, q);
-#pragma unroll 2
-    for (int s = 0; s < NAT_STEPS; ++s) {
-      const int pl = 2 * tid + 2 * T * s, r = pl / N, c = pl % N;   // r = local frequency row k2
-      float2 X0, X1;
-      load_pair(tile, C::tix(r, c), X0, X1);
-      X0 = cscale(X0, invN);
-      X1 = cscale(X1, invN);
-      float2* ri = (float2*)(rI + r * RP + c);
-      const float2 i2 = make_float2(cabs2(X0), cabs2(X1));
-      *ri = (k == 0) ? i2 : make_float2(ri->x + i2.x, ri->y + i2.y);
-      if (psi_s)
-        *(float4*)(psi_s + (size_t)k * NN + (q + Q * r) * N + c) = make_float4(X0.x, X0.y, X1.x, X1.y);
+    fwd2d<C>(cluster, tile, twr, q);
+    // far field of this CTA's columns: the intensity sum and (gradient and
+    // LSQML modes) the far field itself, in a CTA-private scratch order
+#pragma unroll 4
+    for (int e = tid; e < LNN; e += T) {
+      int x, ky;
+      C::freq_index(e, x, ky);
+      const float2 X = cscale(tile[C::tix(x, ky)], invN);
+      float* ri = rI + x * RP + ky;
+      *ri = (k == 0) ? cabs2(X) : *ri + cabs2(X);
+      if (psi_s) psi_s[(size_t)k * NN + (size_t)q * LNN + e] = X;
     }
   }
 
-  // ---- data term (frequency rows q + Q k2) ----------------------------------------
+  // ---- data term (far-field columns 64q .. 64q+63) -------------------------------
   const int mode = a.mode;
   const float eps = a.eps;
   const float* meas = a.meas + (size_t)j * NN;
   float lsum = 0.f;
   bool bad = false;
 #pragma unroll 1
-  for (int s = 0; s < NAT_STEPS; ++s) {
-    const int pl = 2 * tid + 2 * T * s, r = pl / N, c = pl % N;
-    const int pix = (q + Q * r) * N + c;
-    float* ri = rI + r * RP + c;
+  for (int e0 = tid; e0 < LNN; e0 += 2 * T) {
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const float I = ri[u];
-      if (a.ipred) a.ipred[(size_t)j * NN + pix + u] = I;
+      const int e = e0 + u * T;
+      int x, ky;
+      C::freq_index(e, x, ky);
+      const int pix = ky * N + 64 * q + x;
+      float* ri = rI + x * RP + ky;
+      const float I = *ri;
+      if (a.ipred) a.ipred[(size_t)j * NN + pix] = I;
       if (mode == MODE_FWD) continue;
-      const float Im = __ldg(meas + pix + u);
+      const float Im = __ldg(meas + pix);
       float fac;
       if (mode == MODE_VJP) {
         bad |= !isfinite(Im);
@@ -366,7 +315,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_pass1_cluster(BatchArgs a) {
           fac = (mode == MODE_LSQML_POISSON) ? 0.5f * (qq - 1.f) : 2.f * (1.f - qq);
         }
       }
-      ri[u] = fac * invN;
+      *ri = fac * invN;
     }
   }
   if (bad) atomicOr(a.status, FLAG_NONFINITE);
@@ -388,15 +337,14 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_pass1_cluster(BatchArgs a) {
   for (int k = M - 1; k >= 0; --k) {
     const float2* Pk = shared_mode<OPR>(a, k, NN);
     __syncthreads();
-#pragma unroll 2
-    for (int s = 0; s < NAT_STEPS; ++s) {
-      const int pl = 2 * tid + 2 * T * s, r = pl / N, c = pl % N;
-      const float4 X = *(const float4*)(psi_s + (size_t)k * NN + (q + Q * r) * N + c);
-      const float2 f = *(const float2*)(rI + r * RP + c);
-      store_pair(tile, C::tix(r, c), make_float2(X.x * f.x, X.y * f.x), make_float2(X.z * f.y, X.w * f.y));
+#pragma unroll 4
+    for (int e = tid; e < LNN; e += T) {
+      int x, ky;
+      C::freq_index(e, x, ky);
+      tile[C::tix(x, ky)] = cscale(psi_s[(size_t)k * NN + (size_t)q * LNN + e], rI[x * RP + ky]);
     }
     __syncthreads();
-    inv2d<C>(cluster, tile, twr, twc, twn, twq, q);
+    inv2d<C>(cluster, tile, twr, q);
 #pragma unroll 2
     for (int s = 0; s < NAT_STEPS; ++s) {
       const int pl = 2 * tid + 2 * T * s, r = pl / N, c = pl % N;

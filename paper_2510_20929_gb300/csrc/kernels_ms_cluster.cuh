@@ -1,8 +1,8 @@
 // Multislice per-position pass for the cluster windows (N = 192, 256): the
 // model and the phases of k_pass1_ms, with the N x N tile shared by a cluster
 // of Q CTAs as in k_pass1_cluster. CTA q holds the spatial rows 64q..64q+63;
-// a 2-D transform (cl::fwd2d) leaves it the frequency rows q + Q k2, so a
-// propagation is fwd2d, a multiplication of those rows by H / N^2, and
+// a 2-D transform (cl::fwd2d) leaves it the frequency columns 64q..64q+63, so
+// a propagation is fwd2d, a multiplication of those columns by H / N^2, and
 // cl::inv2d back to the CTA's spatial rows.
 #pragma once
 #include "kernels_cluster.cuh"
@@ -12,27 +12,22 @@ namespace cl {
 
 // tile <- F^-1[H F tile] over the cluster (CONJ: conj(H)); ends synchronised.
 template <class C, bool CONJ>
-__device__ __forceinline__ void propagate_cluster(cg::cluster_group& cluster, float2* tile, const float2* twr,
-                                                  const float2* twc, const float2* twn, const float2* twq, int q,
+__device__ __forceinline__ void propagate_cluster(cg::cluster_group& cluster, float2* tile, const float2* twr, int q,
                                                   const float2* __restrict__ Hf) {
-  constexpr int N = C::N, Q = C::Q, T = C::T;
+  constexpr int N = C::N, T = C::T, LNN = C::LNN;
   const float sc = 1.0f / (float)(N * N);
-  fwd2d<C>(cluster, tile, twr, twc, twn, twq, q);
-#pragma unroll 2
-  for (int s = 0; s < C::NAT_STEPS; ++s) {
-    const int pl = 2 * (int)threadIdx.x + 2 * T * s, r = pl / N, c = pl % N;   // local frequency row r
-    float2 x0, x1;
-    load_pair(tile, C::tix(r, c), x0, x1);
-    const float4 h2 = __ldg((const float4*)(Hf + (size_t)(q + Q * r) * N + c));
-    float2 h0 = make_float2(h2.x, h2.y), h1 = make_float2(h2.z, h2.w);
-    if (CONJ) {
-      h0.y = -h0.y;
-      h1.y = -h1.y;
-    }
-    store_pair(tile, C::tix(r, c), cscale(cmul(x0, h0), sc), cscale(cmul(x1, h1), sc));
+  fwd2d<C>(cluster, tile, twr, q);
+#pragma unroll 4
+  for (int e = (int)threadIdx.x; e < LNN; e += T) {   // this CTA's frequency columns
+    int x, ky;
+    C::freq_index(e, x, ky);
+    float2 h = __ldg(Hf + (size_t)ky * N + 64 * q + x);
+    if (CONJ) h.y = -h.y;
+    const int t = C::tix(x, ky);
+    tile[t] = cscale(cmul(tile[t], h), sc);
   }
   __syncthreads();
-  inv2d<C>(cluster, tile, twr, twc, twn, twq, q);
+  inv2d<C>(cluster, tile, twr, q);
 }
 
 // recompute_incident over the cluster: CTA q writes its own rows of the
@@ -40,8 +35,7 @@ __device__ __forceinline__ void propagate_cluster(cg::cluster_group& cluster, fl
 // synchronised.
 template <class C>
 __device__ __forceinline__ void recompute_incident_cluster(cg::cluster_group& cluster, float2* tile,
-                                                           const float2* twr, const float2* twc, const float2* twn,
-                                                           const float2* twq, int q, const float2* __restrict__ Hf,
+                                                           const float2* twr, int q, const float2* __restrict__ Hf,
                                                            const float2* Pk, const float2* o_s, float2* inc, int S) {
   constexpr int N = C::N, T = C::T, LR = C::LR, NN = C::NN, NAT_STEPS = C::NAT_STEPS;
   const int tid = threadIdx.x, rowbase = LR * q;
@@ -58,7 +52,7 @@ __device__ __forceinline__ void recompute_incident_cluster(cg::cluster_group& cl
   __syncthreads();
 #pragma unroll 1
   for (int s = 1; s < S; ++s) {
-    propagate_cluster<C, false>(cluster, tile, twr, twc, twn, twq, q, Hf);
+    propagate_cluster<C, false>(cluster, tile, twr, q, Hf);
     float2* in = inc + (size_t)(s - 1) * NN;
     const bool last = s == S - 1;
 #pragma unroll 2
@@ -89,9 +83,6 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
   double* red = (double*)(smem + SM::red);
   float2* tile = (float2*)(smem + SM::tile);
   float2* twr = (float2*)(smem + SM::twr);
-  float2* twc = (float2*)(smem + SM::twc);
-  float2* twn = (float2*)(smem + SM::twn);
-  float2* twq = (float2*)(smem + SM::twq);
   float* rI = (float*)(smem + SM::rI);
 
   const int q = (int)cluster.block_rank();
@@ -111,17 +102,6 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
   }
   if (tid == 0 && q == 0 && a.valid) a.valid[slot] = 1;
   make_line_twiddles<N, C::RR1, C::RR2>(twr);
-  make_line_twiddles<64, 8, 8>(twc);
-  for (int m = tid; m < N + Q; m += T) {
-    float s, c;
-    if (m < N) {
-      sincospif(2.0f * (float)m / (float)N, &s, &c);
-      twn[m] = make_float2(c, -s);
-    } else {
-      sincospif(2.0f * (float)(m - N) / (float)Q, &s, &c);
-      twq[m - N] = make_float2(c, -s);
-    }
-  }
 
   const int M = a.M, S = a.S, mode = a.mode;
   const bool grad = mode != MODE_FWD;
@@ -162,7 +142,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
     __syncthreads();
 #pragma unroll 1
     for (int s = 1; s < S; ++s) {
-      propagate_cluster<C, false>(cluster, tile, twr, twc, twn, twq, q, a.Hf);
+      propagate_cluster<C, false>(cluster, tile, twr, q, a.Hf);
       float2* inc = keep ? a.in_s + ms_inc_offset(false, slotNN, M, S, k, s, NN) : nullptr;
       // LSQML: the slice's illumination sum_k |inc_k|^2
       float2* wsl = lsqml ? (float2*)(a.w_s + (slotNN * (S - 1) + (size_t)(s - 1) * NN)) : nullptr;
@@ -187,37 +167,37 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
       }
       __syncthreads();
     }
-    fwd2d<C>(cluster, tile, twr, twc, twn, twq, q);
-#pragma unroll 2
-    for (int st = 0; st < NAT_STEPS; ++st) {
-      const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;   // local frequency row r
-      float2 X0, X1;
-      load_pair(tile, C::tix(r, c), X0, X1);
-      X0 = cscale(X0, invN);
-      X1 = cscale(X1, invN);
-      float2* ri = (float2*)(rI + r * RP + c);
-      const float2 i2 = make_float2(cabs2(X0), cabs2(X1));
-      *ri = (k == 0) ? i2 : make_float2(ri->x + i2.x, ri->y + i2.y);
-      if (grad) *(float4*)(psi_s + (size_t)k * NN + (q + Q * r) * N + c) = make_float4(X0.x, X0.y, X1.x, X1.y);
+    fwd2d<C>(cluster, tile, twr, q);
+#pragma unroll 4
+    for (int e = tid; e < LNN; e += T) {   // this CTA's far-field columns
+      int x, ky;
+      C::freq_index(e, x, ky);
+      const float2 X = cscale(tile[C::tix(x, ky)], invN);
+      float* ri = rI + x * RP + ky;
+      *ri = (k == 0) ? cabs2(X) : *ri + cabs2(X);
+      if (grad) psi_s[(size_t)k * NN + (size_t)q * LNN + e] = X;
     }
   }
 
-  // ---- data term (frequency rows q + Q k2) ------------------------------------------
+  // ---- data term (far-field columns 64q .. 64q+63) -----------------------------------
   const float eps = a.eps;
   const float* meas = a.meas ? a.meas + (size_t)j * NN : nullptr;
   float lsum = 0.f;
   bool bad = false;
+  static_assert(LNN % (2 * T) == 0, "data-term loop takes two elements per step");
 #pragma unroll 1
-  for (int st = 0; st < NAT_STEPS; ++st) {
-    const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
-    const int pix = (q + Q * r) * N + c;
-    float* ri = rI + r * RP + c;
+  for (int e0 = tid; e0 < LNN; e0 += 2 * T) {
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      const float I = ri[u];
-      if (a.ipred) a.ipred[(size_t)j * NN + pix + u] = I;
+      const int e = e0 + u * T;
+      int x, ky;
+      C::freq_index(e, x, ky);
+      const int pix = ky * N + 64 * q + x;
+      float* ri = rI + x * RP + ky;
+      const float I = *ri;
+      if (a.ipred) a.ipred[(size_t)j * NN + pix] = I;
       if (!grad) continue;
-      const float Im = __ldg(meas + pix + u);
+      const float Im = __ldg(meas + pix);
       float fac;
       if (mode == MODE_VJP) {
         bad |= !isfinite(Im);
@@ -236,7 +216,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
           fac = (mode == MODE_LSQML_POISSON) ? 0.5f * (qq - 1.f) : 2.f * (1.f - qq);
         }
       }
-      ri[u] = fac * invN;
+      *ri = fac * invN;
     }
   }
   if (bad) atomicOr(a.status, FLAG_NONFINITE);
@@ -259,18 +239,17 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
   for (int k = M - 1; k >= 0; --k) {
     const float2* Pk = a.probe + (size_t)k * NN;
     if (rec && S > 1)
-      recompute_incident_cluster<C>(cluster, tile, twr, twc, twn, twq, q, a.Hf, Pk, o_s,
+      recompute_incident_cluster<C>(cluster, tile, twr, q, a.Hf, Pk, o_s,
                                     a.in_s + ms_inc_offset(true, slotNN, M, S, k, 1, NN), S);
     __syncthreads();
-#pragma unroll 2
-    for (int st = 0; st < NAT_STEPS; ++st) {
-      const int pl = 2 * tid + 2 * T * st, r = pl / N, c = pl % N;
-      const float4 X = *(const float4*)(psi_s + (size_t)k * NN + (q + Q * r) * N + c);
-      const float2 f = *(const float2*)(rI + r * RP + c);
-      store_pair(tile, C::tix(r, c), make_float2(X.x * f.x, X.y * f.x), make_float2(X.z * f.y, X.w * f.y));
+#pragma unroll 4
+    for (int e = tid; e < LNN; e += T) {
+      int x, ky;
+      C::freq_index(e, x, ky);
+      tile[C::tix(x, ky)] = cscale(psi_s[(size_t)k * NN + (size_t)q * LNN + e], rI[x * RP + ky]);
     }
     __syncthreads();
-    inv2d<C>(cluster, tile, twr, twc, twn, twq, q);
+    inv2d<C>(cluster, tile, twr, q);
 #pragma unroll 1
     for (int s = S - 1; s >= 1; --s) {
       const float2* inc = a.in_s + ms_inc_offset(rec, slotNN, M, S, k, s, NN);
@@ -293,7 +272,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
         store_pair(tile, C::tix(r, c), cmulc(make_float2(o2.x, o2.y), g0), cmulc(make_float2(o2.z, o2.w), g1));
       }
       __syncthreads();
-      propagate_cluster<C, true>(cluster, tile, twr, twc, twn, twq, q, a.Hf);
+      propagate_cluster<C, true>(cluster, tile, twr, q, a.Hf);
     }
 #pragma unroll 2
     for (int st = 0; st < NAT_STEPS; ++st) {
@@ -435,9 +414,6 @@ __global__ void __launch_bounds__(C::T, 1) k_step_ms_cluster(MsStepArgs a) {
   double* red = (double*)(smem + SM::red);
   float2* tile = (float2*)(smem + SM::tile);
   float2* twr = (float2*)(smem + SM::twr);
-  float2* twc = (float2*)(smem + SM::twc);
-  float2* twn = (float2*)(smem + SM::twn);
-  float2* twq = (float2*)(smem + SM::twq);
   const int q = (int)cluster.block_rank();
   const int slot = blockIdx.x / Q;
   const int tid = threadIdx.x;
@@ -447,17 +423,6 @@ __global__ void __launch_bounds__(C::T, 1) k_step_ms_cluster(MsStepArgs a) {
     return;
   }
   make_line_twiddles<N, C::RR1, C::RR2>(twr);
-  make_line_twiddles<64, 8, 8>(twc);
-  for (int m = tid; m < N + Q; m += T) {
-    float sn, cs;
-    if (m < N) {
-      sincospif(2.0f * (float)m / (float)N, &sn, &cs);
-      twn[m] = make_float2(cs, -sn);
-    } else {
-      sincospif(2.0f * (float)(m - N) / (float)Q, &sn, &cs);
-      twq[m - N] = make_float2(cs, -sn);
-    }
-  }
   const int M = a.M, S = a.S, rowbase = LR * q;
   const size_t slotNN = (size_t)slot * NN;
   const float2* o_s = a.o_s + slotNN * S;
@@ -471,7 +436,7 @@ __global__ void __launch_bounds__(C::T, 1) k_step_ms_cluster(MsStepArgs a) {
   for (int k = 0; k < M; ++k) {
     const float2* Pk = a.probe + (size_t)k * NN;
     const float2* dPk = a.dP + (size_t)k * NN;
-    if (rec && S > 1) recompute_incident_cluster<C>(cluster, tile, twr, twc, twn, twq, q, a.Hf, Pk, o_s, in_w, S);
+    if (rec && S > 1) recompute_incident_cluster<C>(cluster, tile, twr, q, a.Hf, Pk, o_s, in_w, S);
 #pragma unroll 1
     for (int t = 0; t < 2; ++t) {   // t = 0: the object tangent u, 1: the probe tangent v
       __syncthreads();
@@ -487,7 +452,7 @@ __global__ void __launch_bounds__(C::T, 1) k_step_ms_cluster(MsStepArgs a) {
       __syncthreads();
 #pragma unroll 1
       for (int s = 1; s < S; ++s) {
-        propagate_cluster<C, false>(cluster, tile, twr, twc, twn, twq, q, a.Hf);
+        propagate_cluster<C, false>(cluster, tile, twr, q, a.Hf);
         const float2* inc = a.in_s + ms_inc_offset(rec, slotNN, M, S, k, s, NN);
 #pragma unroll 2
         for (int st = 0; st < NAT_STEPS; ++st) {
