@@ -25,8 +25,8 @@
  * - Gradients follow the complex convention grad = 2 dL/dz* (PyTorch's), so
  *   dL = Re<grad, dz> for a perturbation dz.
  * - Supported window sizes N: 16, 32, 64, 128, 192, 256 (192 and 256 run on
- *   clusters of three and four CTAs sharing the tile through distributed
- *   shared memory).
+ *   clusters of six and eight CTAs, 32 rows each, sharing the tile through
+ *   distributed shared memory).
  *   Modes: 1 <= M <= 16.
  * - The library never allocates device memory. Scratch lives in a caller
  *   workspace of ptycho_workspace_bytes() bytes (256-byte aligned).

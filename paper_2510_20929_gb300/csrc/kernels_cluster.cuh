@@ -1,21 +1,21 @@
 // Per-position pass for windows larger than one CTA's shared memory, on a
-// cluster of Q CTAs (N = 256: Q = 4; N = 192: Q = 3; and a pair of CTAs for
+// cluster of Q CTAs (N = 256: Q = 8; N = 192: Q = 6; and a pair of CTAs for
 // the 128 window).
 //
 // The N x N complex tile is shared by the cluster: in the spatial domain CTA q
-// holds the 64 rows 64q .. 64q+63 (N = 64 Q). The 2-D DFT runs as
+// holds the LR = N / Q rows LR q .. LR q + LR - 1. The 2-D DFT runs as
 //   * N-point transforms of the CTA's own rows (shared memory, as in the
 //     single-CTA kernel);
 //   * a transpose across the cluster: CTA q gathers, from every CTA s, the
-//     64 x 64 block of s's rows at columns 64q .. 64q+63 (distributed shared
-//     memory), and stores it transposed, so that its local row x now holds
-//     column 64q + x of the whole tile (all N rows);
+//     LR x LR block of s's rows at columns LR q .. LR q + LR - 1 (distributed
+//     shared memory), and stores it transposed, so that its local row x now
+//     holds column LR q + x of the whole tile (all N rows);
 //   * N-point transforms of those local rows, which are the columns.
-// CTA q then holds the far-field columns 64q .. 64q+63 (local row x = column
-// 64q + x, local column = frequency row). The inverse mirrors it (row
-// inverses, the same transpose back, row inverses). Each CTA reads 3/4 of its
-// 128 KB from the other CTAs once per transform (a Q-point DFT across the
-// cluster would read every element from every CTA: four times that).
+// CTA q then holds the far-field columns LR q .. (local row x = column LR q +
+// x, local column = frequency row). The inverse mirrors it (row inverses, the
+// same transpose back, row inverses). Each CTA reads (Q-1)/Q of its tile from
+// the other CTAs once per transform (a Q-point DFT across the cluster would
+// read every element from every CTA: Q times that).
 // Everything else (patch gather, back-propagation, scatter, the position
 // gradient) follows the single-CTA k_pass1 on the CTA's own spatial rows; the
 // far-field loops (intensity, data term, the inverse's input) walk the CTA's
@@ -32,7 +32,7 @@ namespace cl {
 
 namespace cg = cooperative_groups;
 
-// Swizzles of the local 64 x N tile (column bits XOR f(r, c), linear over
+// Swizzles of the local LR x N tile (column bits XOR f(r, c), linear over
 // GF(2)), chosen with the half-warp bank model for the row and column lines.
 struct Swz256 {  // f = ((r << 2) ^ (r >> 1) ^ (c >> 4)) & 15
   __host__ __device__ static constexpr int fr(int r) { return ((r << 2) ^ (r >> 1)) & 15; }
@@ -47,7 +47,7 @@ struct Swz192 {  // f = ((r << 3) ^ (r << 1) ^ (r >> 2) ^ (c >> 6)) & 15
   __host__ __device__ static constexpr int fcb(int c) { return (c >> 6) & 15; }
 };
 
-// Element i = i_rt + i_ct of a row or column line of the local 64 x N tile.
+// Element i = i_rt + i_ct of a row or column line of the local LR x N tile.
 // For power-of-two N with disjoint bits in i_rt and i_ct the linear swizzle
 // splits into a hoisted per-line part XOR a compile-time part; otherwise (N =
 // 192, or the S = 3 exchange offsets) the column is formed first.
@@ -69,26 +69,33 @@ struct RectAddr {
   }
 };
 
+// Q CTAs of T threads per position, LR = N / Q rows (and, after a forward
+// transform, LR far-field columns) each; MINB CTAs per SM for the launch bounds.
 template <int N_, int Q_, int T_, int RR1_, int RR2_, bool RINTER_, class Z_, int MINB_ = 1>
 struct Cfg {
-  static constexpr int N = N_, Q = Q_, T = T_, LR = 64, NN = N * N, LNN = LR * N;
+  static constexpr int N = N_, Q = Q_, T = T_, LR = N_ / Q_, NN = N * N, LNN = LR * N;
+  static_assert(LR * Q == N && (LR == 32 || LR == 64), "rows per CTA");
   static constexpr int MINB = MINB_;   // CTAs per SM the launch bounds ask for
   static constexpr int RR1 = RR1_, RR2 = RR2_;
   using Z = Z_;
   using RowF = LineFft<RR1, RR2, RINTER_, RectAddr<N, Z>>;   // N-point rows
   static constexpr int ROW_ITER = LR * RR1 / T;
   static constexpr int NAT_STEPS = LNN / (2 * T);              // natural pixel pairs per thread
-  static constexpr int XG = (T >= 1024 && Q % 2 == 0) ? 2 : 1;   // transpose rounds per cluster barrier
-  static_assert(ROW_ITER >= 1 && 2048 % T == 0 && LNN % T == 0, "CTA size");
+  static_assert(ROW_ITER >= 1 && (LR * LR / 2) % T == 0 && LNN % T == 0, "CTA size");
   __device__ __forceinline__ static int tix(int r, int c) { return r * N + (c ^ Z::fr(r) ^ Z::fcb(c)); }
-  // far-field element e (0 .. LNN-1) of CTA q: local row x = e % 64 (column
-  // 64q + x of the far field), local column ky = e / 64 (its row)
+  // far-field element e (0 .. LNN-1) of CTA q: local row x = e % LR (column
+  // LR q + x of the far field), local column ky = e / LR (its row)
   __device__ __forceinline__ static void freq_index(int e, int& x, int& ky) {
-    x = e & 63;
-    ky = e >> 6;
+    x = e & (LR - 1);
+    ky = e / LR;
   }
+  // transpose: pixel pairs of one LR x LR block per thread, rounds per cluster
+  // barrier (at most 16 values held per thread, a divisor of Q)
+  static constexpr int XP = LR * LR / 2 / T;
+  static constexpr int XG = (4 / (XP > 0 ? XP : 1) >= 4 && Q % 4 == 0) ? 4
+                          : (4 / (XP > 0 ? XP : 1) >= 2 && Q % 2 == 0) ? 2 : 1;
   struct Smem {
-    static constexpr int RP = N + 1;   // intensity plane [64][RP]: the column walk is conflict-free
+    static constexpr int RP = N + 1;   // intensity plane [LR][RP]: the column walk is conflict-free
     static constexpr size_t red = 0;
     static constexpr size_t tile = red + 256 * sizeof(double);
     static constexpr size_t twr = tile + (size_t)LNN * sizeof(float2);
@@ -97,24 +104,28 @@ struct Cfg {
   };
 };
 
-using Cfg256 = Cfg<256, 4, 1024, 16, 16, false, Swz256>;
+// 32 rows per CTA, two CTAs per SM (103 KB and 78 KB of shared memory): one
+// cluster's CTA computes while another's waits on the exchange (against 64
+// rows and one CTA per SM: the spiral256 pass 2.99 -> 2.48 ms per 256
+// positions, multislice256 29.5K -> 32.6K patterns/s)
+using Cfg256 = Cfg<256, 8, 512, 16, 16, false, Swz256, 2>;
 // the 128 window on a pair of CTAs (64 rows each) that fit two to an SM
 using Cfg128 = Cfg<128, 2, 512, 8, 16, true, Swz128, 2>;
-using Cfg192 = Cfg<192, 3, 512, 8, 24, true, Swz192>;
+using Cfg192 = Cfg<192, 6, 256, 8, 24, true, Swz192, 2>;
 
-// The transpose across the cluster: tile[x][64 s + r] <- tile_s[r][64 q + x]
-// for every CTA s of the cluster and r, x in 0..63. It runs in Q rounds; in
+// The transpose across the cluster: tile[x][LR s + r] <- tile_s[r][LR q + x]
+// for every CTA s of the cluster and r, x in 0..LR-1. It runs in Q rounds; in
 // round t CTA q trades blocks with CTA s = (t - q) mod Q (a symmetric pairing:
 // the two read each other's block and then overwrite the block the other
 // has read; s = q transposes its own diagonal block). Block s of CTA q's tile
 // is read only by CTA s and overwritten only in the round that pairs the two,
-// after the barrier, so G rounds can share one cluster barrier: their reads
-// go to registers first (G x 4096 / T pixels per thread), then the barrier,
+// after the barrier, so XG rounds can share one cluster barrier: their reads
+// go to registers first (XG x LR^2 / T pixels per thread), then the barrier,
 // then the transposed stores. Ends synchronised.
 template <class C>
 __device__ __forceinline__ void transpose_exchange(cg::cluster_group& cluster, float2* tile, int q) {
-  constexpr int Q = C::Q, T = C::T, G = C::XG, P = 2048 / T;   // rounds per barrier, pairs per round
-  static_assert(Q % G == 0 && 2048 % T == 0, "rounds and pairs per thread");
+  constexpr int Q = C::Q, T = C::T, G = C::XG, P = C::XP, LR = C::LR, HP = LR / 2;
+  static_assert(Q % G == 0 && P >= 1, "rounds and pairs per thread");
 #pragma unroll 1
   for (int t0 = 0; t0 < Q; t0 += G) {
     float2 v[G][P][2];
@@ -124,9 +135,9 @@ __device__ __forceinline__ void transpose_exchange(cg::cluster_group& cluster, f
       const float2* src = cluster.map_shared_rank(tile, s);
 #pragma unroll
       for (int i = 0; i < P; ++i) {
-        const int p = (int)threadIdx.x + T * i;   // (r, pair of x): 64 x 32 pairs
-        const int r = p >> 5, x = 2 * (p & 31);
-        load_pair(src, C::tix(r, 64 * q + x), v[g][i][0], v[g][i][1]);
+        const int p = (int)threadIdx.x + T * i;   // (r, pair of x): LR x LR/2 pairs
+        const int r = p / HP, x = 2 * (p % HP);
+        load_pair(src, C::tix(r, LR * q + x), v[g][i][0], v[g][i][1]);
       }
     }
     cluster.sync();   // the blocks of these rounds are read in every CTA
@@ -136,16 +147,16 @@ __device__ __forceinline__ void transpose_exchange(cg::cluster_group& cluster, f
 #pragma unroll
       for (int i = 0; i < P; ++i) {
         const int p = (int)threadIdx.x + T * i;
-        const int r = p >> 5, x = 2 * (p & 31);
-        tile[C::tix(x, 64 * s + r)] = v[g][i][0];
-        tile[C::tix(x + 1, 64 * s + r)] = v[g][i][1];
+        const int r = p / HP, x = 2 * (p % HP);
+        tile[C::tix(x, LR * s + r)] = v[g][i][0];
+        tile[C::tix(x + 1, LR * s + r)] = v[g][i][1];
       }
     }
   }
   __syncthreads();
 }
 
-// N-point transforms (forward: natural in, natural out) of the CTA's 64 local
+// N-point transforms (forward: natural in, natural out) of the CTA's LR local
 // rows, in place.
 template <class C, bool FWD>
 __device__ __forceinline__ void row_pass(float2* tile, const float2* twr) {
@@ -167,8 +178,8 @@ __device__ __forceinline__ void row_pass(float2* tile, const float2* twr) {
 }
 
 // 2-D forward DFT (unnormalised) of the cluster's tile: CTA q holds the
-// spatial rows 64q .. on entry and the far-field columns 64q .. on return
-// (local row x = column 64q + x, natural order along it). Ends synchronised.
+// spatial rows LR q .. on entry and the far-field columns LR q .. on return
+// (local row x = column LR q + x, natural order along it). Ends synchronised.
 template <class C>
 __device__ __forceinline__ void fwd2d(cg::cluster_group& cluster, float2* tile, const float2* twr, int q) {
   row_pass<C, true>(tile, twr);
@@ -178,8 +189,8 @@ __device__ __forceinline__ void fwd2d(cg::cluster_group& cluster, float2* tile, 
   __syncthreads();
 }
 
-// 2-D inverse DFT (unnormalised): the far-field columns 64q .. on entry, the
-// spatial rows 64q .. on return. Ends synchronised.
+// 2-D inverse DFT (unnormalised): the far-field columns LR q .. on entry, the
+// spatial rows LR q .. on return. Ends synchronised.
 template <class C>
 __device__ __forceinline__ void inv2d(cg::cluster_group& cluster, float2* tile, const float2* twr, int q) {
   row_pass<C, false>(tile, twr);
@@ -212,7 +223,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_pass1_cluster(BatchArgs a) {
   float fy = 0.f, fx = 0.f;
   bool ok = (j >= 0 && j < a.J);
   if (ok) ok = tile_of(a.pos[2 * j], a.pos[2 * j + 1], N, a.H, a.W, ty, tx, fy, fx);
-  if (!ok) {   // the same decision in all four CTAs of the cluster
+  if (!ok) {   // the same decision in every CTA of the cluster
     if (tid == 0 && q == 0) {
       atomicOr(a.status, FLAG_BOUNDS);
       if (a.valid) a.valid[slot] = 0;
@@ -277,7 +288,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_pass1_cluster(BatchArgs a) {
     }
   }
 
-  // ---- data term (far-field columns 64q .. 64q+63) -------------------------------
+  // ---- data term (this CTA's far-field columns) ------------------------------------
   const int mode = a.mode;
   const float eps = a.eps;
   const float* meas = a.meas + (size_t)j * NN;
@@ -290,7 +301,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_pass1_cluster(BatchArgs a) {
       const int e = e0 + u * T;
       int x, ky;
       C::freq_index(e, x, ky);
-      const int pix = ky * N + 64 * q + x;
+      const int pix = ky * N + LR * q + x;
       float* ri = rI + x * RP + ky;
       const float I = *ri;
       if (a.ipred) a.ipred[(size_t)j * NN + pix] = I;
@@ -367,7 +378,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_pass1_cluster(BatchArgs a) {
   // every CTA's rows of g are written (the scatter reads one row of the neighbour)
   cluster.sync();
 
-  // ---- scatter S_j^T g (and the illumination), rows 64q .. 64q+63 (+ row 256) ------
+  // ---- scatter S_j^T g (and the illumination), this CTA's rows (+ row N) ----------
   const bool lsqml = (mode == MODE_LSQML_GAUSS || mode == MODE_LSQML_POISSON);
   {
     const int y0 = rowbase, y1 = rowbase + LR + (q == Q - 1 ? 1 : 0);

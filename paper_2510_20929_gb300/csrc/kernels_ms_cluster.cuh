@@ -1,7 +1,7 @@
 // Multislice per-position pass for the cluster windows (N = 192, 256): the
 // model and the phases of k_pass1_ms, with the N x N tile shared by a cluster
-// of Q CTAs as in k_pass1_cluster. CTA q holds the spatial rows 64q..64q+63;
-// a 2-D transform (cl::fwd2d) leaves it the frequency columns 64q..64q+63, so
+// of Q CTAs as in k_pass1_cluster. CTA q holds the spatial rows LR q ..;
+// a 2-D transform (cl::fwd2d) leaves it the frequency columns LR q .., so
 // a propagation is fwd2d, a multiplication of those columns by H / N^2, and
 // cl::inv2d back to the CTA's spatial rows.
 #pragma once
@@ -21,7 +21,7 @@ __device__ __forceinline__ void propagate_cluster(cg::cluster_group& cluster, fl
   for (int e = (int)threadIdx.x; e < LNN; e += T) {   // this CTA's frequency columns
     int x, ky;
     C::freq_index(e, x, ky);
-    float2 h = __ldg(Hf + (size_t)ky * N + 64 * q + x);
+    float2 h = __ldg(Hf + (size_t)ky * N + C::LR * q + x);
     if (CONJ) h.y = -h.y;
     const int t = C::tix(x, ky);
     tile[t] = cscale(cmul(tile[t], h), sc);
@@ -73,7 +73,7 @@ __device__ __forceinline__ void recompute_incident_cluster(cg::cluster_group& cl
 
 // LS: the LSQML instantiation (as in k_pass1_ms).
 template <class C, bool LS>
-__global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
+__global__ void __launch_bounds__(C::T, C::MINB) k_pass1_ms_cluster(MsArgs a) {
   constexpr int N = C::N, Q = C::Q, T = C::T, LR = C::LR, NN = C::NN, LNN = C::LNN;
   constexpr int NAT_STEPS = C::NAT_STEPS;
   using SM = typename C::Smem;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
     }
   }
 
-  // ---- data term (far-field columns 64q .. 64q+63) -----------------------------------
+  // ---- data term (this CTA's far-field columns) ---------------------------------------
   const float eps = a.eps;
   const float* meas = a.meas ? a.meas + (size_t)j * NN : nullptr;
   float lsum = 0.f;
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
       const int e = e0 + u * T;
       int x, ky;
       C::freq_index(e, x, ky);
-      const int pix = ky * N + 64 * q + x;
+      const int pix = ky * N + LR * q + x;
       float* ri = rI + x * RP + ky;
       const float I = *ri;
       if (a.ipred) a.ipred[(size_t)j * NN + pix] = I;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
   // row of the neighbour); also no CTA leaves while another reads its tile
   cluster.sync();
 
-  // ---- per slice: scatter rows 64q .. 64q+63 (+ row N); position gradient -----------
+  // ---- per slice: scatter this CTA's rows (+ row N); position gradient --------------
   float gyv = 0.f, gxv = 0.f;
   const int y0 = rowbase, y1 = rowbase + LR + (q == Q - 1 ? 1 : 0);
   constexpr int N1 = N + 1;
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(C::T, 1) k_pass1_ms_cluster(MsArgs a) {
 // rows of u and v through the slices (propagate_cluster) and writes its
 // partial Gram entries; the step-size kernel adds the Q partials.
 template <class C>
-__global__ void __launch_bounds__(C::T, 1) k_step_ms_cluster(MsStepArgs a) {
+__global__ void __launch_bounds__(C::T, C::MINB) k_step_ms_cluster(MsStepArgs a) {
   constexpr int N = C::N, Q = C::Q, T = C::T, LR = C::LR, NN = C::NN;
   constexpr int NAT_STEPS = C::NAT_STEPS;
   using SM = typename C::Smem;

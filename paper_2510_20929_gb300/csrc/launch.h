@@ -15,7 +15,9 @@ template <int N> cudaError_t launch_pass1_ms(const MsArgs& a, cudaStream_t s);
 template <> cudaError_t launch_pass1_ms<192>(const MsArgs& a, cudaStream_t s);
 template <> cudaError_t launch_pass1_ms<256>(const MsArgs& a, cudaStream_t s);
 // multislice LSQML tangent pass (step-size Gram entries); Q CTAs per position
+// (ms_cluster_ctas(N), at most 8)
 struct MsStepArgs;
+int ms_cluster_ctas(int N);
 template <int N> cudaError_t launch_step_ms(const MsStepArgs& a, cudaStream_t s);
 template <> cudaError_t launch_step_ms<192>(const MsStepArgs& a, cudaStream_t s);
 template <> cudaError_t launch_step_ms<256>(const MsStepArgs& a, cudaStream_t s);

@@ -1,9 +1,11 @@
-// Multislice per-position pass for the cluster windows: 256 x 256 (four CTAs)
-// and 192 x 192 (three CTAs).
+// Multislice per-position pass for the cluster windows: 256 x 256 (eight CTAs)
+// and 192 x 192 (six CTAs).
 #include "kernels_ms_cluster.cuh"
 #include "launch.h"
 
 namespace ptycho {
+
+int ms_cluster_ctas(int N) { return N == 256 ? cl::Cfg256::Q : N == 192 ? cl::Cfg192::Q : 1; }
 
 template <>
 cudaError_t launch_pass1_ms<256>(const MsArgs& a, cudaStream_t s) {

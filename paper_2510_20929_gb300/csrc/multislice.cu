@@ -126,7 +126,7 @@ MsLsqmlLayout ms_lsqml_layout(const ptycho_dims& d, int S, int B, bool recompute
   L.smax = take(16 * sizeof(unsigned int));
   L.d = take((size_t)B * S * NN * sizeof(float2));        // the slices' directions at each slot's position
   L.u = take((size_t)B * NN * sizeof(float2));            // one mode's object tangent per slot
-  L.part = take((size_t)B * 4 * 3 * sizeof(double));      // Gram partials, up to 4 CTAs per position
+  L.part = take((size_t)B * 8 * 3 * sizeof(double));      // Gram partials, up to 8 CTAs per position
   L.dsum = take((size_t)B * S * 2 * sizeof(double));      // right-hand-side partials per slot and slice
   L.total = off;
   return L;
@@ -495,7 +495,7 @@ ptycho_status ptycho_lsqml_epoch_ms(const ptycho_dims* dims, const ptycho_multis
       q.delta_o = (float)opts->delta_o; q.lam = opts->lambda_reg;
       q.update_object = opts->update_object; q.update_probe = opts->update_probe;
       q.d_s = (float2*)(b + L.d); q.dsum = (double*)(b + L.dsum); q.part = (double*)(b + L.part);
-      q.Q = d.N == 256 ? 4 : d.N == 192 ? 3 : 1;
+      q.Q = ms_cluster_ctas(d.N);
       MsStepArgs t;
       memset(&t, 0, sizeof(t));
       t.H = d.H; t.W = d.W; t.M = M; t.J = d.J; t.S = S;

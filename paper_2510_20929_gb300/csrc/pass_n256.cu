@@ -1,4 +1,4 @@
-// Per-position kernels for the 256 x 256 window: the four-CTA cluster pass 1
+// Per-position kernels for the 256 x 256 window: the eight-CTA cluster pass 1
 // and the step-size pass 2.
 #include "kernels_cluster.cuh"
 #include "launch.h"
