@@ -715,6 +715,40 @@ __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
   const float aO = (float)alpha_sh;
   const float c00 = aO * w00, c01 = aO * w01, c10 = aO * w10, c11 = aO * w11;
   constexpr int N1 = N + 1;
+  if (((uintptr_t)a.obj & 15) == 0 && (a.W & 1) == 0) {
+    // pairs of object pixels at even object columns, one 16-byte vector atomic
+    // each (half the atomic operations); per tile row N/2 pairs and one single
+    // pixel (the first when tx is odd, else the last)
+    constexpr int PR = N / 2 + 1;
+    const int odd = tx & 1;
+    auto gat = [&](int y, int x) {
+      return (y >= 0 && y < N && x >= 0 && x < N) ? g_s[y * N + x] : make_float2(0.f, 0.f);
+    };
+    for (int i = tid; i < N1 * PR; i += T) {
+      const int y = i / PR, k = i % PR;
+      const size_t row = (size_t)(ty + y) * a.W + tx;
+      if (k < N / 2) {
+        const int x = 2 * k + odd;   // pixels x, x + 1 of the tile row
+        const float2 gA = gat(y, x - 1), gB = gat(y, x), gC = gat(y, x + 1);
+        const float2 hA = gat(y - 1, x - 1), hB = gat(y - 1, x), hC = gat(y - 1, x + 1);
+        const float2 s0 = make_float2(c00 * gB.x + c01 * gA.x + c10 * hB.x + c11 * hA.x,
+                                      c00 * gB.y + c01 * gA.y + c10 * hB.y + c11 * hA.y);
+        const float2 s1 = make_float2(c00 * gC.x + c01 * gB.x + c10 * hC.x + c11 * hB.x,
+                                      c00 * gC.y + c01 * gB.y + c10 * hC.y + c11 * hB.y);
+        const float i0 = 1.f / (__ldg(&a.acc[row + x].z) + damp);
+        const float i1 = 1.f / (__ldg(&a.acc[row + x + 1].z) + damp);
+        atomicAdd((float4*)(a.obj + row + x), make_float4(s0.x * i0, s0.y * i0, s1.x * i1, s1.y * i1));
+      } else {
+        const int x = odd ? 0 : N;
+        const float2 gA = gat(y, x - 1), gB = gat(y, x), hA = gat(y - 1, x - 1), hB = gat(y - 1, x);
+        const float2 s0 = make_float2(c00 * gB.x + c01 * gA.x + c10 * hB.x + c11 * hA.x,
+                                      c00 * gB.y + c01 * gA.y + c10 * hB.y + c11 * hA.y);
+        const float i0 = 1.f / (__ldg(&a.acc[row + x].z) + damp);
+        atomicAdd(a.obj + row + x, make_float2(s0.x * i0, s0.y * i0));
+      }
+    }
+    return;
+  }
   // each object pixel of the (N+1)^2 tile gathers its four patch neighbours
   // (independent outputs keep many global loads in flight)
   for (int q = tid; q < N1 * N1; q += T) {
