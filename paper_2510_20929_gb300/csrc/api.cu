@@ -627,7 +627,7 @@ static ptycho_status autotune(const ptycho_dims& d, float2* obj, float2* probe, 
 
 ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float* pos,
                                const float* meas, const int32_t* order, const ptycho_lsqml_opts& o,
-                               double* loss, double* alpha, void* ws, cudaStream_t s) {
+                               double* loss, double* alpha, void* ws, cudaStream_t s, const MeasSwitch* later) {
   const int B = o.batch, N = d.N, M = d.M, NN = N * N, HW = d.H * d.W;
   const Layout L = layout_for(d, o);
   Ptrs w = carve(ws, L);
@@ -657,10 +657,13 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
     const int b0 = b * B, nb = (d.J - b0 < B) ? d.J - b0 : B;
     BatchScalars* sc = &w.hdr->sc[b & 1];
     BatchScalars* sc_next = &w.hdr->sc[(b + 1) & 1];
+    if (later && later->meas && b == later->from_batch && (e = cudaStreamWaitEvent(s, later->ready, 0)) != cudaSuccess)
+      return PTYCHO_ERR_CUDA;
     BatchArgs a;
     memset(&a, 0, sizeof(a));
     a.H = d.H; a.W = d.W; a.M = M; a.J = d.J;
-    a.obj = obj; a.probe = probe; a.pos = pos; a.meas = meas; a.order = order;
+    a.obj = obj; a.probe = probe; a.pos = pos; a.order = order;
+    a.meas = (later && later->meas && b >= later->from_batch) ? later->meas : meas;
     a.b0 = b0; a.nb = nb;
     a.mode = (o.noise == PTYCHO_NOISE_POISSON) ? MODE_LSQML_POISSON : MODE_LSQML_GAUSS;
     a.eps = (float)o.eps;
@@ -963,12 +966,47 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
     else
       (void)cudaGetLastError();   // not mapped pinned memory: clear the error and stage it
   }
+  // Mapped intensities: the first quarter of the minibatches read them in place
+  // while a copy engine brings the whole array into the workspace on a worker
+  // stream; the later minibatches wait for that copy and read device memory
+  // (reads over the host link slow the per-position pass down).
+  MeasSwitch later;
+  cudaEvent_t fork = nullptr, ready = nullptr;
+  cudaStream_t cs = nullptr;
+  const int nbatch = (d.J + opts->batch - 1) / opts->batch;
+  if (mdev && nbatch >= 4) {
+    cudaStream_t* workers = nullptr;
+    int nw = 0;
+    if ((st = worker_streams(&workers, &nw)) != PTYCHO_OK) return st;
+    cs = workers[0];
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) {
+      if (fork) cudaEventDestroy(fork);
+      return PTYCHO_ERR_CUDA;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, fork, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dmeas, meas, (size_t)d.J * NN * 4, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ready, cs);
+    later.meas = dmeas;
+    later.from_batch = nbatch / 4;
+    later.ready = ready;
+  }
   if (!mdev) {
     cp(dmeas, meas, (size_t)d.J * NN * 4, cudaMemcpyHostToDevice);
     mdev = dmeas;
   }
-  if (e != cudaSuccess) return PTYCHO_ERR_CUDA;
-  st = run_epoch(d, dobj, dprobe, dpos, mdev, order ? dorder : nullptr, *opts, dloss, nullptr, ws, s);
+  if (e == cudaSuccess)
+    st = run_epoch(d, dobj, dprobe, dpos, mdev, order ? dorder : nullptr, *opts, dloss, nullptr, ws, s, &later);
+  else
+    st = PTYCHO_ERR_CUDA;
+  if (fork) {
+    // on success the epoch waited for the worker copy (from_batch < nbatch);
+    // on an error it may still be running into the workspace: let it finish
+    if (st != PTYCHO_OK) cudaStreamSynchronize(cs);
+    cudaEventDestroy(fork);
+    cudaEventDestroy(ready);
+  }
   if (st != PTYCHO_OK) return st;
   cp(object, dobj, HW * 8, cudaMemcpyDeviceToHost);
   cp(probe, dprobe, (size_t)d.M * NN * 8, cudaMemcpyDeviceToHost);

@@ -191,14 +191,17 @@ def test_lsqml_epoch_with_both_modes_on_host_buffers_matches_oracle():
     assert max(e[:3]) < TOL_EPOCH and e[3] < 1e-3
 
 
-def test_host_epoch_with_pinned_and_with_pageable_intensities_match_oracle():
-    # pinned (mapped) intensities are read in place by the passes, pageable ones staged first
+@pytest.mark.parametrize("batch", [8, 3])
+def test_host_epoch_with_pinned_and_with_pageable_intensities_match_oracle(batch):
+    # pinned (mapped) intensities are read in place by the passes, pageable ones
+    # staged first; with four minibatches or more (batch 3: seven) the later
+    # ones read the copy a worker stream makes during the first ones
     import torch
     from paper_2510_20929_gb300 import api
     p = problem(N=64, M=2, H=150, W=160, J=20, step=12.0, seed=17)
     O, P, pos, I_m = c64(p["O"]), c64(p["P"]), f32pos(p["pos"]), np.float32(p["I_m"]).astype(np.float64)
     order = np.random.default_rng(6).permutation(20).astype(np.int32)
-    kw = dict(batch=8, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6)
+    kw = dict(batch=batch, delta_o=0.1, delta_p=0.1, lam=1e-6, eps=1e-6)
     O_ref, P_ref, L_ref, _ = orc.lsqml_epoch(O, P, pos, I_m, order, orc.LsqmlOptions(**kw))
     out = []
     for pinned in (True, False):
