@@ -273,21 +273,27 @@ __device__ __forceinline__ void bilinear2(const float2* __restrict__ O, int W, i
                    w00 * a1.y + w01 * a2.y + w10 * b1.y + w11 * b2.y);
 }
 
-// Block-wide sum of NV doubles; result valid in thread 0. `red` holds 32*NV
-// doubles. A shuffle tree within each warp, then warp 0 reduces the per-warp
-// partials with a second shuffle tree (five dependent FP64 additions instead
-// of a serial sum over the warps).
+// Block-wide sum of NV per-thread FP32 partials (passed as doubles, which
+// hold them exactly); result valid in thread 0. `red` holds 32*NV doubles. A
+// shuffle tree in FP32 within each warp, then warp 0 adds the warps' sums with
+// a second shuffle tree in FP64. FP64 runs at about 1/64 of the FP32 rate on
+// this part, so an FP64 tree over every thread of a 1024-thread CTA cost
+// microseconds; the FP32 warp tree adds five roundings to each thread's own
+// partial sum.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  float f[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q)
+  for (int q = 0; q < NV; ++q) {
+    f[q] = (float)v[q];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    for (int o = 16; o > 0; o >>= 1) f[q] += __shfl_down_sync(0xffffffffu, f[q], o);
+  }
   __syncthreads();
   if (lane == 0)
 #pragma unroll
-    for (int q = 0; q < NV; ++q) red[warp * NV + q] = v[q];
+    for (int q = 0; q < NV; ++q) red[warp * NV + q] = (double)f[q];
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
