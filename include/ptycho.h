@@ -127,7 +127,8 @@ typedef struct {
  *       CTAs per position adding their partial sums over distributed shared
  *       memory, at 4 (2) or 3 (3) CTAs per SM;
  *   [2] the probe reduction: 16 (0), 8 (1) or 32 (2) positions in flight per
- *       thread. */
+ *       thread, or the minibatch split into 4 ranges summed by 4 threads of
+ *       a block with 8 positions in flight each (3). */
 #define PTYCHO_FLAG_AUTOTUNE 2
 #define PTYCHO_TUNE_KERNELS 3
 #define PTYCHO_TUNE_MAX 4

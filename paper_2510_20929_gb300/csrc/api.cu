@@ -36,18 +36,22 @@ __global__ void k_init_epoch(int NN, int M, const float2* probe, float* Sp, WsHe
   if (blockIdx.x == 0 && threadIdx.x == 0) memset(hdr->sc, 0, sizeof(hdr->sc));
 }
 
-// Batch sums per probe pixel, without atomics: for blockIdx.y == 0 the thread
-// (k, q) with k < Mc sums conj(o_j) chi_j,k0+k over the batch (pixel pair q,
+// Batch sums of the probe-direction numerator and of the patch intensity:
+// item (k, q) with k < Mc sums conj(o_j) chi_j,k0+k over the batch (pixel pair q,
 // into dPacc_k, added to its previous value when `accumulate`; each slot holds
 // Ms planes), and k == Mc sums |o_j|^2 into Dp and reports max(Dp). Blocks
 // with blockIdx.y == 1 scan the illumination plane for its maximum. U
-// positions are loaded per iteration.
-template <int U>
+// positions are loaded per iteration; with PG > 1 the batch is split into PG
+// consecutive ranges, each summed by its own thread of the block (PG times the
+// loads in flight), and the block adds the PG partial sums in range order.
+template <int U, int PG>
 __global__ void k_probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* __restrict__ h_s,
                                const float2* __restrict__ o_s, const int* __restrict__ valid, float2* dPacc,
                                int accumulate, float* Dp, const float4* __restrict__ acc, int HW,
                                BatchScalars* sc, int o_stride) {
+  constexpr int IPB = 256 / PG;   // items per block (blockDim.x == 256)
   __shared__ float red[32];
+  __shared__ float4 part[PG][IPB];
   wait_prior_grid();
   if (blockIdx.y == 1) {
     if (!acc) return;
@@ -59,46 +63,61 @@ __global__ void k_probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const flo
     return;
   }
   const int NP = NN / 2;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = (int)threadIdx.x / IPB, li = (int)threadIdx.x % IPB;
+  const int t = blockIdx.x * IPB + li;
   const int k = t / NP, q = t % NP;
-  float dmax = 0.f;
-  if (k < Mc && dPacc) {
+  const int i_lo = (int)((long long)nb * g / PG), i_hi = (int)((long long)nb * (g + 1) / PG);
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);   // dPacc: the pixel pair; Dp: (d.x, d.y, -, -)
+  const bool num = k < Mc && dPacc, den = k == Mc && Dp;
+  if (num) {
     const float4* h = (const float4*)h_s + (size_t)(k0 + k) * NP + q;
     const size_t stride = (size_t)Ms * NP;
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = 0; i < nb; i += U) {
+    for (int i = i_lo; i < i_hi; i += U) {
       float4 v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        v[u] = (i + u < nb && valid[i + u]) ? __ldcs(h + (size_t)(i + u) * stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[u] = (i + u < i_hi && valid[i + u]) ? __ldcs(h + (size_t)(i + u) * stride) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         s.x += v[u].x; s.y += v[u].y; s.z += v[u].z; s.w += v[u].w;
       }
     }
+  } else if (den) {
+    const float4* o = (const float4*)o_s + q;
+    const size_t ostep = o_stride ? (size_t)o_stride / 2 : (size_t)NP;   // float4 per slot
+    for (int i = i_lo; i < i_hi; i += U) {
+      float4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        v[u] = (i + u < i_hi && valid[i + u]) ? __ldg(o + (size_t)(i + u) * ostep) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        s.x += v[u].x * v[u].x + v[u].y * v[u].y;
+        s.y += v[u].z * v[u].z + v[u].w * v[u].w;
+      }
+    }
+  }
+  if constexpr (PG > 1) {
+    part[g][li] = s;
+    __syncthreads();
+    if (g == 0)
+#pragma unroll
+      for (int r = 1; r < PG; ++r) {
+        const float4 v = part[r][li];
+        s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+      }
+  }
+  float dmax = 0.f;
+  if (g == 0 && num) {
     float4* out = (float4*)dPacc + (size_t)k * NP + q;
     if (accumulate) {
       const float4 o = *out;
       s.x += o.x; s.y += o.y; s.z += o.z; s.w += o.w;
     }
     *out = s;
-  } else if (k == Mc && Dp) {
-    const float4* o = (const float4*)o_s + q;
-    const size_t ostep = o_stride ? (size_t)o_stride / 2 : (size_t)NP;   // float4 per slot
-    float2 d = make_float2(0.f, 0.f);
-    for (int i = 0; i < nb; i += U) {
-      float4 v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        v[u] = (i + u < nb && valid[i + u]) ? __ldg(o + (size_t)(i + u) * ostep) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        d.x += v[u].x * v[u].x + v[u].y * v[u].y;
-        d.y += v[u].z * v[u].z + v[u].w * v[u].w;
-      }
-    }
-    ((float2*)Dp)[q] = d;
-    dmax = fmaxf(d.x, d.y);
+  } else if (g == 0 && den) {
+    ((float2*)Dp)[q] = make_float2(s.x, s.y);
+    dmax = fmaxf(s.x, s.y);
   }
   if (Dp) {
     dmax = block_max(dmax, red);
@@ -389,7 +408,8 @@ struct TuneKey {
 // v[0]: the per-position pass (candidates: pass1_variants(N)), v[1]: the
 // step-size pass (candidates: pass2_variants(N): single kernel, split, cluster
 // at 4 or 3 CTAs per SM), v[2]: the probe reduction (positions
-// in flight per thread: 16, 8, 32); ms[i][c]: candidate c's mean time.
+// in flight per thread: 16, 8, 32, or 8 in each of 4 threads splitting the
+// batch); ms[i][c]: candidate c's mean time.
 struct TuneEntry {
   TuneKey key;
   int v[PTYCHO_TUNE_KERNELS];
@@ -398,7 +418,7 @@ struct TuneEntry {
 
 static int pass1_variants(int N) { return N == 128 ? 3 : (N <= 128 ? 2 : 1); }
 static int pass2_variants(int N) { return N <= 128 ? 4 : 2; }
-static constexpr int kReduceVariants = 3;
+static constexpr int kReduceVariants = 4;
 static std::mutex g_tune_mu;
 static std::vector<TuneEntry> g_tune;
 
@@ -447,11 +467,14 @@ cudaError_t probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const float2* h
                          BatchScalars* sc, cudaStream_t s, int o_stride, int variant) {
   cudaEvent_t e0 = profile_begin(K_PROBE_REDUCE, s);
   const int NP = NN / 2;
-  const int threads = (dPacc ? Mc * NP : 0) + (Dp ? NP : 0);
-  int bx = (threads + 255) / 256;
+  const int items = (dPacc ? Mc * NP : 0) + (Dp ? NP : 0);
+  const int ipb = variant == 3 ? 256 / 4 : 256;   // items per block
+  int bx = (items + ipb - 1) / ipb;
   if (acc && bx < 2 * sm_count()) bx = 2 * sm_count();
   dim3 grid(bx > 0 ? bx : 1, acc ? 2 : 1);
-  auto kern = variant == 1 ? k_probe_reduce<8> : variant == 2 ? k_probe_reduce<32> : k_probe_reduce<16>;
+  auto kern = variant == 1 ? k_probe_reduce<8, 1>
+            : variant == 2 ? k_probe_reduce<32, 1>
+            : variant == 3 ? k_probe_reduce<8, 4> : k_probe_reduce<16, 1>;
   const cudaError_t e = launch_pdl(kern, grid, dim3(256), 0, s, NN, k0, Mc, Ms, nb, h_s, o_s, valid, dPacc,
                                    accumulate, Dp, acc, HW, sc, o_stride);
   profile_end(K_PROBE_REDUCE, e0, s);

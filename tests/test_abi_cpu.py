@@ -191,7 +191,7 @@ def test_allocation_free_epoch_rejects_arguments_like_the_workspace_epoch(L):
 def test_tuning_set_rejects_unknown_variants(L):
     from paper_2510_20929_gb300 import api
     for dims, v in ((_dims(N=128, H=300, W=300), (3, 0, 0)), (_dims(N=64, H=100, W=100), (2, 0, 0)),
-                    (_dims(), (0, 4, 0)), (_dims(N=256, H=300, W=300), (0, 2, 0)), (_dims(), (0, 0, 3)),
+                    (_dims(), (0, 4, 0)), (_dims(N=256, H=300, W=300), (0, 2, 0)), (_dims(), (0, 0, 4)),
                     (_dims(), (-1, 0, 0))):
         arr = (ctypes.c_int32 * 3)(*v)
         assert L.ptycho_tuning_set(ctypes.byref(dims), 4, arr) == 1

@@ -98,5 +98,5 @@ def test_autotuned_epoch_matches_default_and_records_its_choice():
     t = api.tuning(api.dims_of(O0, P0, pos), 8)
     print("autotune:", e, t)
     assert max(e) < TOL_EPOCH
-    assert t is not None and t["pass1"] in (0, 1) and t["pass2"] in (0, 1, 2, 3) and t["probe_reduce"] in (0, 1, 2)
-    assert min(t["pass1_ms"][:2]) > 0 and min(t["pass2_ms"][:4]) > 0 and min(t["probe_reduce_ms"][:3]) > 0
+    assert t is not None and t["pass1"] in (0, 1) and t["pass2"] in (0, 1, 2, 3) and t["probe_reduce"] in (0, 1, 2, 3)
+    assert min(t["pass1_ms"][:2]) > 0 and min(t["pass2_ms"][:4]) > 0 and min(t["probe_reduce_ms"][:4]) > 0

@@ -239,12 +239,12 @@ def test_compact_sampler_with_per_epoch_object_update_matches_oracle():
     assert max(e) < TOL_EPOCH
 
 
-@pytest.mark.parametrize("pass1,pass2,reduce", [(0, 0, 0), (1, 1, 1), (2, 0, 2), (2, 1, 0), (0, 2, 1), (1, 3, 2)])
+@pytest.mark.parametrize("pass1,pass2,reduce", [(0, 0, 0), (1, 1, 1), (2, 0, 2), (2, 1, 0), (0, 2, 1), (1, 3, 3)])
 def test_every_tuned_variant_matches_oracle(pass1, pass2, reduce):
     # the autotuner's candidates pinned one combination at a time (window 128:
     # 1024 threads, 512 threads, the pair of CTAs; single, split or cluster
     # step-size pass at 4 or 3 CTAs per SM; 16, 8 or 32 positions in flight
-    # in the probe reduction)
+    # in the probe reduction, or the batch split over 4 threads)
     import torch
     from paper_2510_20929_gb300 import api
     N, M, H, W, J, step, batch = 128, 3, 300, 310, 10, 24.0, 4
