@@ -150,8 +150,12 @@ __global__ void k_norm_probe(int NN, int M, const float2* dPacc, const float* Dp
 // P_k += mean_j(alpha_P) dP_k; refresh Sp = sum_k |P_k|^2 (when Sp is set); clear the next
 // batch's scalars.
 __global__ void k_probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
-                               const BatchScalars* sc, BatchScalars* sc_next) {
+                               const BatchScalars* sc, BatchScalars* sc_next, float4* clear, size_t nclear) {
   wait_prior_grid();
+  // (when given) the minibatch's object-frame accumulator plane is zeroed in
+  // the same launch: both only have to follow the step-size pass
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < nclear; p += (size_t)gridDim.x * blockDim.x)
+    clear[p] = make_float4(0.f, 0.f, 0.f, 0.f);
   const float mean_ap = sc->count > 0 ? (float)(sc->sum_alpha_p / (double)sc->count) : 0.f;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += gridDim.x * blockDim.x) {
     float s = 0.f;
@@ -509,10 +513,11 @@ cudaError_t norm_probe(int NN, int M, const float2* dPacc, const float* Dp, cons
 }
 
 cudaError_t probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
-                         const BatchScalars* sc, BatchScalars* sc_next, cudaStream_t s) {
+                         const BatchScalars* sc, BatchScalars* sc_next, cudaStream_t s, float4* clear, size_t nclear) {
   return timed(K_UPDATE, s, [&] {
-    return launch_pdl(k_probe_update, dim3(grid_for(NN, 256, sm_count())), dim3(256), 0, s, NN, M, probe, dP, Sp,
-                      update_probe, sc, sc_next);
+    const int g = clear ? grid_for(nclear, 256, 8 * sm_count()) : grid_for(NN, 256, sm_count());
+    return launch_pdl(k_probe_update, dim3(g), dim3(256), 0, s, NN, M, probe, dP, Sp, update_probe, sc, sc_next,
+                      clear, clear ? nclear : (size_t)0);
   });
 }
 
@@ -722,8 +727,11 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
     q.delta_o = (float)o.delta_o; q.lam = o.lambda_reg;
     q.update_object = o.update_object; q.update_probe = o.update_probe;
     if ((e = pass2(N, q, s, tune.v[1])) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    if ((e = clear_acc(tiles, d, nb, b0, pos, order, w.valid, w.acc, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
-    if ((e = probe_update(NN, M, probe, w.dP, w.Sp, o.update_probe, sc, sc_next, s)) != cudaSuccess)
+    // the whole plane is zeroed by the probe update's launch; tiles by their own kernel
+    if (tiles && (e = clear_acc(tiles, d, nb, b0, pos, order, w.valid, w.acc, s)) != cudaSuccess)
+      return PTYCHO_ERR_CUDA;
+    if ((e = probe_update(NN, M, probe, w.dP, w.Sp, o.update_probe, sc, sc_next, s, tiles ? nullptr : w.acc,
+                          (size_t)HW)) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
     if (o.update_positions) {   // last: pass 2 and the tile clear read this batch's positions
       k_pos_apply<<<(nb + 127) / 128, 128, 0, s>>>(nb, b0, order, w.valid, w.possum, pos, N, d.H, d.W,

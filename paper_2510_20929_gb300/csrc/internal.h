@@ -78,7 +78,8 @@ cudaError_t norm_probe(int NN, int M, const float2* dPacc, const float* Dp, cons
                        int update_probe, const BatchScalars* sc, float2* dP, float2* Cp, float* Sdp,
                        cudaStream_t s);
 cudaError_t probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
-                         const BatchScalars* sc, BatchScalars* sc_next, cudaStream_t s);
+                         const BatchScalars* sc, BatchScalars* sc_next, cudaStream_t s, float4* clear = nullptr,
+                         size_t nclear = 0);
 cudaError_t init_epoch(int NN, int M, const float2* probe, float* Sp, struct WsHeader* hdr, cudaStream_t s);
 // True when a minibatch's object tiles are cheaper to visit than the whole
 // object plane: the illumination maximum then scans only those tiles
