@@ -636,6 +636,39 @@ __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
   const float2* p0 = opr ? a.p0_s + slotNN : nullptr;
 
   float A11 = 0.f, A12 = 0.f, A22 = 0.f, b1 = 0.f, b2 = 0.f;
+  if constexpr (!OPR) {
+    // two adjacent pixels per iteration: 16-byte loads of g, o and Cp, and the
+    // six accumulator corners the pair shares (half the trips of this
+    // latency-bound loop)
+#pragma unroll 1
+    for (int p = 2 * tid; p < NN; p += 2 * T) {
+      const int r = p / N, c = p % N;
+      const float4 g2 = __ldcs((const float4*)(g_s + p));
+      const float4 o2 = __ldcs((const float4*)(o_s + p));
+      float2 d0 = make_float2(0.f, 0.f), d1 = d0;
+      if (a.update_object) {
+        const float4* q = a.acc + (size_t)(ty + r) * a.W + (tx + c);
+        const float4 qa = __ldg(q), qb = __ldg(q + 1), qc = __ldg(q + 2);
+        const float4 qd = __ldg(q + a.W), qe = __ldg(q + a.W + 1), qf = __ldg(q + a.W + 2);
+        const float ia = 1.f / (qa.z + damp), ib = 1.f / (qb.z + damp), ic = 1.f / (qc.z + damp);
+        const float id = 1.f / (qd.z + damp), ie = 1.f / (qe.z + damp), iF = 1.f / (qf.z + damp);
+        // dO_hat at the pixel: each corner's quotient, then the bilinear weights
+        d0 = make_float2(w00 * ia * qa.x + w01 * ib * qb.x + w10 * id * qd.x + w11 * ie * qe.x,
+                         w00 * ia * qa.y + w01 * ib * qb.y + w10 * id * qd.y + w11 * ie * qe.y);
+        d1 = make_float2(w00 * ib * qb.x + w01 * ic * qc.x + w10 * ie * qe.x + w11 * iF * qf.x,
+                         w00 * ib * qb.y + w01 * ic * qc.y + w10 * ie * qe.y + w11 * iF * qf.y);
+      }
+      const float2 sp = __ldg((const float2*)(a.Sp + p)), sdp = __ldg((const float2*)(a.Sdp + p));
+      const float4 cp = __ldg((const float4*)(a.Cp + p));
+      const float2 g0 = make_float2(g2.x, g2.y), g1 = make_float2(g2.z, g2.w);
+      const float2 o0 = make_float2(o2.x, o2.y), o1 = make_float2(o2.z, o2.w);
+      A11 += cabs2(d0) * sp.x + cabs2(d1) * sp.y;
+      const float2 od0 = cmulc(d0, o0), od1 = cmulc(d1, o1);   // conj(d) o
+      A12 += od0.x * cp.x - od0.y * cp.y + od1.x * cp.z - od1.y * cp.w;   // Re(conj(d) o Cp)
+      A22 += cabs2(o0) * sdp.x + cabs2(o1) * sdp.y;
+      b1 += d0.x * g0.x + d0.y * g0.y + d1.x * g1.x + d1.y * g1.y;       // Re(conj(d) g)
+    }
+  } else
 #pragma unroll 1
   for (int p = tid; p < NN; p += T) {
     const int r = p / N, c = p % N;
