@@ -237,10 +237,20 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
     // psi_k = P_k o_j into the tile, two adjacent pixels per thread and iteration
     const NatPairs<N, T> np;
     if constexpr (TM) {
-      // groups of two pairs; the patch from TMEM after the first mode
+      // groups of two pairs; the patch from TMEM after the first mode; the
+      // probe pairs of the next group are loaded (L2) before this group's work
       const uint32_t t_o = tm_o();
+      const bool pre = !OPR || Pk;
+      float4 Pn[2];
+      if (pre)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) Pn[u] = __ldg((const float4*)(Pk + np.pix(u)));
 #pragma unroll 1
       for (int qg = 0; qg < STEPS / 2; ++qg) {
+        const float4 Pc[2] = {Pn[0], Pn[1]};
+        if (pre && qg + 1 < STEPS / 2)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) Pn[u] = __ldg((const float4*)(Pk + np.pix(2 * qg + 2 + u)));
         float ov[8];
         if (k == 0) {
 #pragma unroll
@@ -259,8 +269,8 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
         for (int u = 0; u < 2; ++u) {
           const int q = 2 * qg + u, p = np.pix(q);
           float4 P2;
-          if (!OPR || Pk) {
-            P2 = __ldg((const float4*)(Pk + p));
+          if (pre) {
+            P2 = Pc[u];
           } else {
             P2 = opr_pair(a.opr_U, wj, a.K, NN, p);
             if (p0) *(float4*)(p0 + p) = P2;
@@ -461,8 +471,21 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
       // o and the running g from TMEM; the last mode's g goes to the scratch
       // (for the step sizes) and over chi in the tile (for the scatter)
       const uint32_t t_o = tm_o(), t_g = t_o + 4 * STEPS;
+      // the probe (or primary-mode) pairs of the next group are loaded before
+      // this group's work
+      // (the primary modes of OPR were written by this kernel: plain loads)
+      auto ldP = [&](int p) {
+        return (!OPR || Pk) ? __ldg((const float4*)(Pk + p)) : *(const float4*)(p0 + p);
+      };
+      float4 Pn[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) Pn[u] = ldP(np.pix(u));
 #pragma unroll 1
       for (int qg = 0; qg < STEPS / 2; ++qg) {
+        const float4 Pc[2] = {Pn[0], Pn[1]};
+        if (qg + 1 < STEPS / 2)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) Pn[u] = ldP(np.pix(2 * qg + 2 + u));
         float ov[8], gv[8];
         if (k < M - 1)
           tc::tmem_ld8x2_wait(t_o + 8 * qg, ov, t_g + 8 * qg, gv);
@@ -473,7 +496,7 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
           const int q = 2 * qg + u, p = np.pix(q);
           float2 x0, x1;
           load_pair(tile, np.phys(q), x0, x1);
-          const float4 P2 = (!OPR || Pk) ? __ldg((const float4*)(Pk + p)) : *(const float4*)(p0 + p);
+          const float4 P2 = Pc[u];
           float2 g0 = cmulc(make_float2(P2.x, P2.y), x0), g1 = cmulc(make_float2(P2.z, P2.w), x1);
           if (k < M - 1) {
             g0.x += gv[4 * u]; g0.y += gv[4 * u + 1]; g1.x += gv[4 * u + 2]; g1.y += gv[4 * u + 3];
