@@ -550,15 +550,31 @@ __global__ void __launch_bounds__(T, 1) k_pass1(BatchArgs a) {
       store_pair(tile, np.phys(q), make_float2(g2.x, g2.y), make_float2(g2.z, g2.w));
     }
   }
-  __syncthreads();
   const bool lsqml = (mode == MODE_LSQML_GAUSS || mode == MODE_LSQML_POISSON);
+  // LSQML: the probe intensity sum_k |P_k|^2 of every pixel into shared memory
+  // (the intensity/factor plane is free by now), so that the scatter's row walk
+  // waits on shared memory rather than on L2
+  float* spS = rI;
+  if (PART != 1 && lsqml) {
+    static_assert((size_t)N * RP >= (size_t)NN, "room for the probe intensity");
+#pragma unroll 2
+    for (int p = 4 * tid; p < NN; p += 4 * T) {
+      float4 v = __ldg((const float4*)(a.Sp + p));
+      if (OPR && p0) {
+        const float4 q0 = *(const float4*)(p0 + p), q1 = *(const float4*)(p0 + p + 2);
+        v.x += q0.x * q0.x + q0.y * q0.y; v.y += q0.z * q0.z + q0.w * q0.w;
+        v.z += q1.x * q1.x + q1.y * q1.y; v.w += q1.z * q1.z + q1.w * q1.w;
+      }
+      *(float4*)(spS + p) = v;
+    }
+  }
+  __syncthreads();
   if (lsqml) {
     bilinear_scatter<N, T>(
         fy, fx,
         [&](int y, int x) {
           const float2 g = tile[tix<N>(y, x)];
-          const float sp = __ldg(a.Sp + y * N + x) + ((OPR && p0) ? cabs2(p0[y * N + x]) : 0.f);
-          return make_float4(g.x, g.y, sp, 0.f);
+          return make_float4(g.x, g.y, spS[y * N + x], 0.f);
         },
         [&](int y, int x, float4 v) {
           atomicAdd(a.acc + (size_t)(ty + y) * a.W + (tx + x), make_float4(v.x, v.y, v.z, 0.f));
