@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
 #pragma unroll 1
     for (int p = 2 * tid; p < NN; p += 2 * T) {
       const int r = p / N, c = p % N;
-      const float4 g2 = __ldcs((const float4*)(g_s + p));
+      const float4 g2 = __ldg((const float4*)(g_s + p));   // kept in L2: the update reads g again
       const float4 o2 = __ldcs((const float4*)(o_s + p));
       float2 d0 = make_float2(0.f, 0.f), d1 = d0;
       if (a.update_object) {
@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
 #pragma unroll 1
   for (int p = tid; p < NN; p += T) {
     const int r = p / N, c = p % N;
-    const float2 g = __ldcs(g_s + p);
+    const float2 g = __ldg(g_s + p);   // kept in L2: the update reads g again
     const float2 o = __ldcs(o_s + p);
     float2 d = make_float2(0.f, 0.f);
     if (a.update_object) d = dohat(a.acc + (size_t)(ty + r) * a.W + (tx + c), a.W, w00, w01, w10, w11, damp);
