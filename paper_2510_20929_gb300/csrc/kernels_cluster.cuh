@@ -371,21 +371,43 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_pass1_cluster(BatchArgs a) {
         gv = make_float4(gv.x + gp.x, gv.y + gp.y, gv.z + gp.z, gv.w + gp.w);
       }
       *(float4*)(g_s + p) = gv;
+      if (k == 0)   // the finished g of this CTA's rows also into its (now free) tile
+        store_pair(tile, C::tix(r, c), make_float2(gv.x, gv.y), make_float2(gv.z, gv.w));
       const float2 h0 = cmulc(make_float2(o2.x, o2.y), x0), h1 = cmulc(make_float2(o2.z, o2.w), x1);
       __stcs((float4*)(h_s + (size_t)k * NN + p), make_float4(h0.x, h0.y, h1.x, h1.y));
+    }
+  }
+  const bool lsqml = (mode == MODE_LSQML_GAUSS || mode == MODE_LSQML_POISSON);
+  // LSQML: the probe intensity of this CTA's rows into the free intensity/factor
+  // plane, so that the scatter reads its own rows from shared memory
+  float* spS = rI;
+  if (lsqml) {
+    static_assert(LR * RP >= LNN, "room for the probe intensity");
+    for (int e = 4 * tid; e < LNN; e += 4 * T) {
+      const int p = rowbase * N + e;
+      float4 v = __ldg((const float4*)(a.Sp + p));
+      if (OPR && p0) {
+        const float4 q0 = *(const float4*)(p0 + p), q1 = *(const float4*)(p0 + p + 2);
+        v.x += q0.x * q0.x + q0.y * q0.y; v.y += q0.z * q0.z + q0.w * q0.w;
+        v.z += q1.x * q1.x + q1.y * q1.y; v.w += q1.z * q1.z + q1.w * q1.w;
+      }
+      *(float4*)(spS + e) = v;
     }
   }
   // every CTA's rows of g are written (the scatter reads one row of the neighbour)
   cluster.sync();
 
   // ---- scatter S_j^T g (and the illumination), this CTA's rows (+ row N) ----------
-  const bool lsqml = (mode == MODE_LSQML_GAUSS || mode == MODE_LSQML_POISSON);
   {
     const int y0 = rowbase, y1 = rowbase + LR + (q == Q - 1 ? 1 : 0);
     constexpr int N1 = N + 1;
     const float gx = 1.f - fx, gy = 1.f - fy;
     auto loadg = [&](int y, int x) {
-      const float2 g = g_s[y * N + x];
+      if (y >= y0 && y < y0 + LR) {   // this CTA's rows: shared memory
+        const float2 g = tile[C::tix(y - y0, x)];
+        return make_float4(g.x, g.y, lsqml ? spS[(y - y0) * N + x] : 0.f, 0.f);
+      }
+      const float2 g = g_s[y * N + x];   // the row above, from the neighbour's rows in L2
       const float sp = lsqml ? __ldg(a.Sp + y * N + x) + ((OPR && p0) ? cabs2(p0[y * N + x]) : 0.f) : 0.f;
       return make_float4(g.x, g.y, sp, 0.f);
     };
