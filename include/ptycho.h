@@ -253,12 +253,11 @@ ptycho_status ptycho_lsqml_epoch_batched(int32_t n, const ptycho_dims* dims, flo
  * before returning. Host buffers should be pinned for full copy bandwidth.
  * With PTYCHO_PRECISION_FP32, a `meas` array in pinned host memory that is
  * mapped into the device address space (cudaHostAlloc, or page-locked tensors
- * on a unified-addressing system) is not staged before the epoch: the first
- * quarter of the minibatches read it in place over the host link while a copy
- * engine brings the whole array into `ws` on one of the library's worker
- * streams (the one ptycho_lsqml_epoch_batched also uses), and the later
- * minibatches wait for that copy and read device memory, so the transfer
- * overlaps the compute. */
+ * on a unified-addressing system) is not staged before the epoch: a gather
+ * kernel on one of the library's worker streams (the one
+ * ptycho_lsqml_epoch_batched also uses) reads it over the host link into `ws`
+ * minibatch by minibatch, in the epoch's order, and each minibatch waits only
+ * for its own positions, so the transfer overlaps the compute. */
 size_t ptycho_host_workspace_bytes(const ptycho_dims* dims, int32_t batch);
 size_t ptycho_host_workspace_bytes_opts(const ptycho_dims* dims, const ptycho_lsqml_opts* opts);
 ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, float* probe,

@@ -669,6 +669,10 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
   if (tc && (e = dft_planes(N, w.dft, s)) != cudaSuccess) return PTYCHO_ERR_CUDA;
   int dev = 0;
   cudaGetDevice(&dev);
+  if (later && later->meas && d.J > 0) {   // the first minibatch (and the autotuner) read the arriving copy
+    if ((e = cudaStreamWaitEvent(s, later->ready[0], 0)) != cudaSuccess) return PTYCHO_ERR_CUDA;
+    meas = later->meas;
+  }
   TuneEntry tune;
   memset(&tune, 0, sizeof(tune));
   tune.key = {dev, N, M, d.H, d.W, B};
@@ -685,13 +689,13 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
     const int b0 = b * B, nb = (d.J - b0 < B) ? d.J - b0 : B;
     BatchScalars* sc = &w.hdr->sc[b & 1];
     BatchScalars* sc_next = &w.hdr->sc[(b + 1) & 1];
-    if (later && later->meas && b == later->from_batch && (e = cudaStreamWaitEvent(s, later->ready, 0)) != cudaSuccess)
+    if (later && later->meas && b > 0 && (e = cudaStreamWaitEvent(s, later->ready[b], 0)) != cudaSuccess)
       return PTYCHO_ERR_CUDA;
     BatchArgs a;
     memset(&a, 0, sizeof(a));
     a.H = d.H; a.W = d.W; a.M = M; a.J = d.J;
     a.obj = obj; a.probe = probe; a.pos = pos; a.order = order;
-    a.meas = (later && later->meas && b >= later->from_batch) ? later->meas : meas;
+    a.meas = (later && later->meas) ? later->meas : meas;
     a.b0 = b0; a.nb = nb;
     a.mode = (o.noise == PTYCHO_NOISE_POISSON) ? MODE_LSQML_POISSON : MODE_LSQML_GAUSS;
     a.eps = (float)o.eps;
@@ -939,6 +943,31 @@ ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* 
   return run_graphed(key, (cudaStream_t)stream, body);
 }
 
+// Copies the measured intensities of the minibatch positions order[b0 ..
+// b0 + nb) from mapped host memory (read over the host link) to their own
+// rows of the device copy; entries outside 0..J-1 are left to the epoch's
+// checks. One CTA per position at a time, 16-byte loads, four in flight per
+// thread.
+__global__ void k_gather_meas(const float4* __restrict__ src, float4* dst, const int* __restrict__ order, int b0,
+                              int nb, int J, int NN4) {
+  for (int i = blockIdx.x; i < nb; i += gridDim.x) {
+    const int e = b0 + i;
+    const int j = order ? order[e] : e;
+    if (j < 0 || j >= J) continue;
+    const float4* sp = src + (size_t)j * NN4;
+    float4* dp = dst + (size_t)j * NN4;
+    int q = threadIdx.x;
+    for (; q + 3 * (int)blockDim.x < NN4; q += 4 * blockDim.x) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = sp[q + u * blockDim.x];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) dp[q + u * blockDim.x] = v[u];
+    }
+    for (; q < NN4; q += blockDim.x) dp[q] = sp[q];
+  }
+}
+
 static size_t host_extra(const ptycho_dims& d) {  // device staging of the host buffers
   const size_t HW = (size_t)d.H * d.W, NN = (size_t)d.N * d.N;
   return align256(HW * 8) + align256((size_t)d.M * NN * 8) + align256((size_t)d.J * 8) +
@@ -985,10 +1014,9 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
   cp(dpos, pos, (size_t)d.J * 8, cudaMemcpyHostToDevice);
   if (order) cp(dorder, order, (size_t)d.J * 4, cudaMemcpyHostToDevice);
   // The measured intensities, the bulk of the input: pinned host memory that is
-  // mapped into the device's address space is read in place by the per-position
-  // passes over the host link, so the transfer overlaps the epoch's compute;
-  // other host memory (and the tensor-copy form, which needs device memory) is
-  // staged first.
+  // mapped into the device's address space is gathered into the workspace
+  // during the epoch (below), so the transfer overlaps the compute; other host
+  // memory (and the tensor-copy form) is staged first.
   const float* mdev = nullptr;
   if (opts->precision == PTYCHO_PRECISION_FP32 && d.J > 0) {
     void* mapped = nullptr;
@@ -997,46 +1025,49 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
     else
       (void)cudaGetLastError();   // not mapped pinned memory: clear the error and stage it
   }
-  // Mapped intensities: the first quarter of the minibatches read them in place
-  // while a copy engine brings the whole array into the workspace on a worker
-  // stream; the later minibatches wait for that copy and read device memory
-  // (reads over the host link slow the per-position pass down).
+  // Mapped intensities: a gather kernel on a worker stream copies them into the
+  // workspace copy minibatch by minibatch, in the epoch's order, reading them
+  // over the host link; minibatch b waits only for its own positions, so
+  // after the first minibatch's copy the transfer runs under the compute.
   MeasSwitch later;
-  cudaEvent_t fork = nullptr, ready = nullptr;
+  std::vector<cudaEvent_t> ready;
   cudaStream_t cs = nullptr;
-  const int nbatch = (d.J + opts->batch - 1) / opts->batch;
-  if (mdev && nbatch >= 4) {
+  const int B = opts->batch, nbatch = (d.J + B - 1) / B;
+  if (mdev) {
     cudaStream_t* workers = nullptr;
     int nw = 0;
     if ((st = worker_streams(&workers, &nw)) != PTYCHO_OK) return st;
     cs = workers[0];
-    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) {
-      if (fork) cudaEventDestroy(fork);
-      return PTYCHO_ERR_CUDA;
+    ready.assign((size_t)nbatch + 1, nullptr);   // [nbatch]: the fork from the caller's stream
+    for (auto& ev : ready)
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ready[nbatch], s);   // the order is on the device
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready[nbatch], 0);
+    const int gx = sm_count() / 8 > 0 ? sm_count() / 8 : 1;
+    for (int b = 0; b < nbatch && e == cudaSuccess; ++b) {
+      const int b0 = b * B, nb = (d.J - b0 < B) ? d.J - b0 : B;
+      k_gather_meas<<<gx, 256, 0, cs>>>((const float4*)mdev, (float4*)dmeas, order ? dorder : nullptr, b0, nb, d.J,
+                                        (int)(NN / 4));
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaEventRecord(ready[b], cs);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, fork, 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dmeas, meas, (size_t)d.J * NN * 4, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess) e = cudaEventRecord(ready, cs);
     later.meas = dmeas;
-    later.from_batch = nbatch / 4;
-    later.ready = ready;
-  }
-  if (!mdev) {
+    later.ready = ready.data();
+  } else {
     cp(dmeas, meas, (size_t)d.J * NN * 4, cudaMemcpyHostToDevice);
     mdev = dmeas;
   }
   if (e == cudaSuccess)
-    st = run_epoch(d, dobj, dprobe, dpos, mdev, order ? dorder : nullptr, *opts, dloss, nullptr, ws, s, &later);
+    st = run_epoch(d, dobj, dprobe, dpos, mdev, order ? dorder : nullptr, *opts, dloss, nullptr, ws, s,
+                   later.meas ? &later : nullptr);
   else
     st = PTYCHO_ERR_CUDA;
-  if (fork) {
-    // on success the epoch waited for the worker copy (from_batch < nbatch);
-    // on an error it may still be running into the workspace: let it finish
+  if (!ready.empty()) {
+    // on success the epoch waited for every gather; on an error they may
+    // still be running into the workspace: let them finish
     if (st != PTYCHO_OK) cudaStreamSynchronize(cs);
-    cudaEventDestroy(fork);
-    cudaEventDestroy(ready);
+    for (auto ev : ready)
+      if (ev) cudaEventDestroy(ev);
   }
   if (st != PTYCHO_OK) return st;
   cp(object, dobj, HW * 8, cudaMemcpyDeviceToHost);

@@ -90,12 +90,12 @@ cudaError_t tile_illum_max(const ptycho_dims& d, int nb, int b0, const float* po
 cudaError_t clear_acc(bool tiles, const ptycho_dims& d, int nb, int b0, const float* pos, const int32_t* order,
                       const int* valid, float4* acc, cudaStream_t s);
 // One LSQML epoch on stream s with workspace ws (arguments already validated).
-// Measured intensities that arrive during the epoch: minibatches from
-// `from_batch` on wait for `ready` and read `meas` here instead.
+// Measured intensities that arrive during the epoch: minibatch b waits for
+// ready[b] (its positions' intensities are in `meas` from then on) and reads
+// `meas` instead of the epoch's own pointer.
 struct MeasSwitch {
   const float* meas = nullptr;
-  int from_batch = 0;
-  cudaEvent_t ready = nullptr;
+  const cudaEvent_t* ready = nullptr;   // one per minibatch
 };
 ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float* pos, const float* meas,
                         const int32_t* order, const ptycho_lsqml_opts& o, double* loss, double* alpha, void* ws,
