@@ -1009,9 +1009,8 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
   auto cp = [&](void* dst, const void* src, size_t n, cudaMemcpyKind k) {
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, k, s);
   };
-  cp(dobj, object, HW * 8, cudaMemcpyHostToDevice);
-  cp(dprobe, probe, (size_t)d.M * NN * 8, cudaMemcpyHostToDevice);
-  cp(dpos, pos, (size_t)d.J * 8, cudaMemcpyHostToDevice);
+  // the order first: the intensity gather below needs it, and it runs while
+  // the object, probe and positions are copied
   if (order) cp(dorder, order, (size_t)d.J * 4, cudaMemcpyHostToDevice);
   // The measured intensities, the bulk of the input: pinned host memory that is
   // mapped into the device's address space is gathered into the workspace
@@ -1057,6 +1056,9 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
     cp(dmeas, meas, (size_t)d.J * NN * 4, cudaMemcpyHostToDevice);
     mdev = dmeas;
   }
+  cp(dobj, object, HW * 8, cudaMemcpyHostToDevice);
+  cp(dprobe, probe, (size_t)d.M * NN * 8, cudaMemcpyHostToDevice);
+  cp(dpos, pos, (size_t)d.J * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     st = run_epoch(d, dobj, dprobe, dpos, mdev, order ? dorder : nullptr, *opts, dloss, nullptr, ws, s,
                    later.meas ? &later : nullptr);
