@@ -125,22 +125,37 @@ __global__ void k_probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const flo
   }
 }
 
-// dP_k = dPacc_k / (Dp + delta_p max(Dp)); Cp = sum_k conj(P_k) dP_k; Sdp = sum_k |dP_k|^2
-__global__ void k_norm_probe(int NN, int M, const float2* dPacc, const float* Dp, const float2* probe,
-                             float delta_p, int update_probe, const BatchScalars* sc, float2* dP, float2* Cp,
-                             float* Sdp) {
+// dP_k = dPacc_k / (Dp + delta_p max(Dp)); Cp = sum_k conj(P_k) dP_k; Sdp = sum_k |dP_k|^2.
+// The loads of up to KB modes are issued together (one L2 round trip per KB
+// modes instead of one per mode); the sums run over k in order.
+constexpr int kModeChunk = 8;
+__global__ void k_norm_probe(int NN, int M, const float2* __restrict__ dPacc, const float* __restrict__ Dp,
+                             const float2* __restrict__ probe, float delta_p, int update_probe,
+                             const BatchScalars* sc, float2* __restrict__ dP, float2* __restrict__ Cp,
+                             float* __restrict__ Sdp) {
+  constexpr int KB = kModeChunk;
   wait_prior_grid();
   const float damp = delta_p * __uint_as_float(sc->max_dp);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += gridDim.x * blockDim.x) {
     float2 c = make_float2(0.f, 0.f);
     float sd = 0.f;
     const float inv = update_probe ? 1.f / (Dp[p] + damp) : 0.f;
-    for (int k = 0; k < M; ++k) {
-      const size_t q = (size_t)k * NN + p;
-      const float2 v = update_probe ? cscale(dPacc[q], inv) : make_float2(0.f, 0.f);
-      dP[q] = v;
-      c = cadd(c, cmulc(probe[q], v));
-      sd += cabs2(v);
+    for (int k0 = 0; k0 < M; k0 += KB) {
+      float2 a[KB], P[KB];
+#pragma unroll
+      for (int u = 0; u < KB; ++u) {
+        const size_t q = (size_t)(k0 + u) * NN + p;
+        a[u] = (k0 + u < M && update_probe) ? dPacc[q] : make_float2(0.f, 0.f);
+        P[u] = (k0 + u < M) ? probe[q] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < KB; ++u)
+        if (k0 + u < M) {
+          const float2 v = cscale(a[u], inv);
+          dP[(size_t)(k0 + u) * NN + p] = v;
+          c = cadd(c, cmulc(P[u], v));
+          sd += cabs2(v);
+        }
     }
     Cp[p] = c;
     Sdp[p] = sd;
@@ -148,30 +163,40 @@ __global__ void k_norm_probe(int NN, int M, const float2* dPacc, const float* Dp
 }
 
 // P_k += mean_j(alpha_P) dP_k; refresh Sp = sum_k |P_k|^2 (when Sp is set); clear the next
-// batch's scalars.
-__global__ void k_probe_update(int NN, int M, float2* probe, const float2* dP, float* Sp, int update_probe,
-                               const BatchScalars* sc, BatchScalars* sc_next, float4* clear, size_t nclear) {
+// batch's scalars. Loads of up to KB modes at a time, as in k_norm_probe.
+__global__ void k_probe_update(int NN, int M, float2* __restrict__ probe, const float2* __restrict__ dP,
+                               float* __restrict__ Sp, int update_probe, const BatchScalars* sc,
+                               BatchScalars* sc_next, float4* __restrict__ clear, size_t nclear) {
+  constexpr int KB = kModeChunk;
   wait_prior_grid();
+  const float mean_ap = sc->count > 0 ? (float)(sc->sum_alpha_p / (double)sc->count) : 0.f;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k0 = 0; k0 < M; k0 += KB) {
+      float2 v[KB], d[KB];
+#pragma unroll
+      for (int u = 0; u < KB; ++u) {
+        const size_t q = (size_t)(k0 + u) * NN + p;
+        v[u] = (k0 + u < M) ? probe[q] : make_float2(0.f, 0.f);
+        d[u] = (k0 + u < M && update_probe) ? dP[q] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < KB; ++u)
+        if (k0 + u < M) {
+          if (update_probe) {
+            v[u].x = fmaf(mean_ap, d[u].x, v[u].x);
+            v[u].y = fmaf(mean_ap, d[u].y, v[u].y);
+            probe[(size_t)(k0 + u) * NN + p] = v[u];
+          }
+          s += cabs2(v[u]);
+        }
+    }
+    if (Sp) Sp[p] = s;
+  }
   // (when given) the minibatch's object-frame accumulator plane is zeroed in
   // the same launch: both only have to follow the step-size pass
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < nclear; p += (size_t)gridDim.x * blockDim.x)
     clear[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-  const float mean_ap = sc->count > 0 ? (float)(sc->sum_alpha_p / (double)sc->count) : 0.f;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NN; p += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < M; ++k) {
-      const size_t q = (size_t)k * NN + p;
-      float2 v = probe[q];
-      if (update_probe) {
-        const float2 d = dP[q];
-        v.x = fmaf(mean_ap, d.x, v.x);
-        v.y = fmaf(mean_ap, d.y, v.y);
-        probe[q] = v;
-      }
-      s += cabs2(v);
-    }
-    if (Sp) Sp[p] = s;
-  }
   if (blockIdx.x == 0 && threadIdx.x == 0) memset(sc_next, 0, sizeof(BatchScalars));
 }
 
@@ -507,7 +532,7 @@ cudaError_t norm_probe(int NN, int M, const float2* dPacc, const float* Dp, cons
                        int update_probe, const BatchScalars* sc, float2* dP, float2* Cp, float* Sdp,
                        cudaStream_t s) {
   return timed(K_NORM_PROBE, s, [&] {
-    return launch_pdl(k_norm_probe, dim3(grid_for(NN, 256, sm_count())), dim3(256), 0, s, NN, M, dPacc, Dp, probe, delta_p,
+    return launch_pdl(k_norm_probe, dim3(grid_for(NN, 128, 2 * sm_count())), dim3(128), 0, s, NN, M, dPacc, Dp, probe, delta_p,
                       update_probe, sc, dP, Cp, Sdp);
   });
 }
