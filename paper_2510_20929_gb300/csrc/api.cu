@@ -789,6 +789,39 @@ ptycho_status check_opts(const ptycho_lsqml_opts* o) {
   return PTYCHO_OK;
 }
 
+// Copies the measured intensities of the minibatch positions order[b0 ..
+// b0 + nb) from mapped host memory (read over the host link) to their own
+// rows of the device copy; entries outside 0..J-1 are left to the epoch's
+// checks. The minibatch's nb * NN4 16-byte elements are walked flat, U loads
+// in flight per thread: few CTAs can keep the host link busy, and each CTA
+// keeps an SM from the per-position pass only for as long as it copies.
+template <int U>
+__global__ void k_gather_meas(const float4* __restrict__ src, float4* dst, const int* __restrict__ order, int b0,
+                              int nb, int J, int NN4) {
+  const size_t total = (size_t)nb * NN4, stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < total; base += U * stride) {
+    float4 v[U];
+    size_t at[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const size_t idx = base + u * stride;
+      at[u] = ~(size_t)0;
+      if (idx < total) {
+        const int i = (int)(idx / NN4), off = (int)(idx % NN4);
+        const int e = b0 + i;
+        const int j = order ? order[e] : e;
+        if (j >= 0 && j < J) {
+          at[u] = (size_t)j * NN4 + off;
+          v[u] = src[at[u]];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (at[u] != ~(size_t)0) dst[at[u]] = v[u];
+  }
+}
+
 }  // namespace ptycho
 
 using namespace ptycho;
@@ -968,31 +1001,6 @@ ptycho_status ptycho_lsqml_epoch(const ptycho_dims* dims, float* object, float* 
   return run_graphed(key, (cudaStream_t)stream, body);
 }
 
-// Copies the measured intensities of the minibatch positions order[b0 ..
-// b0 + nb) from mapped host memory (read over the host link) to their own
-// rows of the device copy; entries outside 0..J-1 are left to the epoch's
-// checks. One CTA per position at a time, 16-byte loads, four in flight per
-// thread.
-__global__ void k_gather_meas(const float4* __restrict__ src, float4* dst, const int* __restrict__ order, int b0,
-                              int nb, int J, int NN4) {
-  for (int i = blockIdx.x; i < nb; i += gridDim.x) {
-    const int e = b0 + i;
-    const int j = order ? order[e] : e;
-    if (j < 0 || j >= J) continue;
-    const float4* sp = src + (size_t)j * NN4;
-    float4* dp = dst + (size_t)j * NN4;
-    int q = threadIdx.x;
-    for (; q + 3 * (int)blockDim.x < NN4; q += 4 * blockDim.x) {
-      float4 v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = sp[q + u * blockDim.x];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) dp[q + u * blockDim.x] = v[u];
-    }
-    for (; q < NN4; q += blockDim.x) dp[q] = sp[q];
-  }
-}
-
 static size_t host_extra(const ptycho_dims& d) {  // device staging of the host buffers
   const size_t HW = (size_t)d.H * d.W, NN = (size_t)d.N * d.N;
   return align256(HW * 8) + align256((size_t)d.M * NN * 8) + align256((size_t)d.J * 8) +
@@ -1067,11 +1075,16 @@ ptycho_status ptycho_lsqml_epoch_host(const ptycho_dims* dims, float* object, fl
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(ready[nbatch], s);   // the order is on the device
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready[nbatch], 0);
-    const int gx = sm_count() / 8 > 0 ? sm_count() / 8 : 1;
     for (int b = 0; b < nbatch && e == cudaSuccess; ++b) {
       const int b0 = b * B, nb = (d.J - b0 < B) ? d.J - b0 : B;
-      k_gather_meas<<<gx, 256, 0, cs>>>((const float4*)mdev, (float4*)dmeas, order ? dorder : nullptr, b0, nb, d.J,
-                                        (int)(NN / 4));
+      // the first minibatch precedes all compute: a wide grid; the later ones
+      // run under it on two CTAs
+      if (b == 0)
+        k_gather_meas<4><<<2 * sm_count(), 256, 0, cs>>>((const float4*)mdev, (float4*)dmeas,
+                                                         order ? dorder : nullptr, b0, nb, d.J, (int)(NN / 4));
+      else
+        k_gather_meas<8><<<2, 1024, 0, cs>>>((const float4*)mdev, (float4*)dmeas, order ? dorder : nullptr, b0, nb,
+                                             d.J, (int)(NN / 4));
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaEventRecord(ready[b], cs);
     }
