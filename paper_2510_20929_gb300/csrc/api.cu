@@ -55,9 +55,8 @@ __global__ void k_probe_reduce(int NN, int k0, int Mc, int Ms, int nb, const flo
   wait_prior_grid();
   if (blockIdx.y == 1) {
     if (!acc) return;
-    float m = 0.f;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x)
-      m = fmaxf(m, __ldcs(&acc[p].z));
+    float m = illum_max_share<8>(acc, (size_t)HW, (size_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                 (size_t)gridDim.x * blockDim.x);
     m = block_max(m, red);
     if (threadIdx.x == 0) atomicMax(&sc->max_illum, __float_as_uint(m));
     return;
@@ -219,10 +218,22 @@ __global__ void k_tile_illum_max(int N, int H, int W, int J, const float* pos, c
   __shared__ float red[32];
   int ty, tx;
   if (!slot_tile(N, H, W, J, pos, order, b0, valid, ty, tx)) return;
-  const int N1 = N + 1;
+  // (the launch gives each thread about four elements of the tile: all four
+  // loads are issued before the first use)
+  constexpr int U = 4;
+  const int N1 = N + 1, n = N1 * N1, nt = gridDim.x * blockDim.x;
   float m = 0.f;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N1 * N1; i += gridDim.x * blockDim.x)
-    m = fmaxf(m, __ldcs(&acc[(size_t)(ty + i / N1) * W + tx + i % N1].z));
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i < n; i += U * nt) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = i + u * nt;
+      v[u] = k < n ? __ldcs(&acc[(size_t)(ty + k / N1) * W + tx + k % N1].z) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) m = fmaxf(m, v[u]);
+  }
   m = block_max(m, red);
   if (threadIdx.x == 0) atomicMax(&sc->max_illum, __float_as_uint(m));
 }
@@ -554,8 +565,10 @@ cudaError_t init_epoch(int NN, int M, const float2* probe, float* Sp, WsHeader* 
 }
 
 bool tiles_cheaper(int nb, int N, int H, int W) {
-  // tile rows are short, strided runs: count them twice against the plane
-  return 2 * (size_t)nb * (N + 1) * (N + 1) < (size_t)H * W;
+  // a tile row is a run of 16 (N + 1) bytes, which the scan and the clear
+  // stream at about the plane's bandwidth (measured on the 192 and 256
+  // windows), so the tiles win as soon as they hold fewer elements
+  return (size_t)nb * (N + 1) * (N + 1) < (size_t)H * W;
 }
 
 static dim3 tile_grid(int nb, int N) {

@@ -235,6 +235,24 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// max(0, illumination) over the elements t, t + nt, t + 2 nt, ... < n of an
+// accumulator plane (component .z), U loads in flight per thread (a plane
+// scan that waits on one load at a time runs at a fraction of HBM speed).
+template <int U>
+__device__ __forceinline__ float illum_max_share(const float4* __restrict__ p, size_t n, size_t t, size_t nt) {
+  float m = 0.f;
+  size_t i = t;
+  for (; i + (U - 1) * nt < n; i += U * nt) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = __ldcs(&p[i + u * nt].z);
+#pragma unroll
+    for (int u = 0; u < U; ++u) m = fmaxf(m, v[u]);
+  }
+  for (; i < n; i += nt) m = fmaxf(m, __ldcs(&p[i].z));
+  return m;
+}
+
 // Tile origin and fraction of a probe-centre position; false if the bilinear
 // (N+1)^2 tile is not inside the object or the value is not finite.
 __device__ __forceinline__ bool tile_of(float py, float px, int N, int H, int W, int& ty, int& tx,

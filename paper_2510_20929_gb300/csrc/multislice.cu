@@ -164,9 +164,7 @@ struct MsPass2Args {
 __global__ void k_ms_illum_max(size_t HW, const float4* __restrict__ acc, unsigned int* smax) {
   __shared__ float red[32];
   const float4* a = acc + (size_t)blockIdx.y * HW;
-  float m = 0.f;
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < HW; p += (size_t)gridDim.x * blockDim.x)
-    m = fmaxf(m, __ldcs(&a[p].z));
+  float m = illum_max_share<8>(a, HW, blockIdx.x * (size_t)blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
   m = block_max(m, red);
   if (threadIdx.x == 0) atomicMax(smax + blockIdx.y, __float_as_uint(m));
 }
