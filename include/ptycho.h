@@ -115,8 +115,10 @@ typedef struct {
 /* opts->flags: on the first epoch for a given device and (N, M, H, W, batch),
  * time the candidate variants of three kernels of the epoch on the first
  * minibatch (synchronising the stream; skipped while capturing) and use the
- * fastest of each from then on. Without it, or before tuning, variant 0 of
- * each is used. The candidates (the "variants" below):
+ * fastest of each from then on. Without it, or before tuning, the
+ * per-position and step-size passes use variant 0 and the probe reduction
+ * variant 3 (the fastest candidate on every workload measured). The
+ * candidates (the "variants" below):
  *   [0] the per-position pass: windows <= 64: CTA sizes default / alternative;
  *       window 128: 1024 threads (0), 512 threads (1), a pair of CTAs of 512
  *       threads with 64 rows each exchanging the column transforms through

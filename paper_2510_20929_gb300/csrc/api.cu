@@ -713,6 +713,7 @@ ptycho_status run_epoch(const ptycho_dims& d, float2* obj, float2* probe, float*
   }
   TuneEntry tune;
   memset(&tune, 0, sizeof(tune));
+  tune.v[2] = kReduceDefault;   // (until tuned or pinned)
   tune.key = {dev, N, M, d.H, d.W, B};
   if (!tc && !tune_lookup(tune.key, &tune) && (o.flags & PTYCHO_FLAG_AUTOTUNE) && d.J > 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
