@@ -675,10 +675,11 @@ __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
   const float2* p0 = opr ? a.p0_s + slotNN : nullptr;
 
   float A11 = 0.f, A12 = 0.f, A22 = 0.f, b1 = 0.f, b2 = 0.f;
-  if constexpr (!OPR) {
+  {
     // two adjacent pixels per iteration: 16-byte loads of g, o and Cp, and the
     // six accumulator corners the pair shares (half the trips of this
-    // latency-bound loop)
+    // latency-bound loop); with OPR also the pair's primary mode, its
+    // direction sum_m w_jm dU_m (K 16-byte loads) and h_j0
 #pragma unroll 1
     for (int p = 2 * tid; p < NN; p += 2 * T) {
       const int r = p / N, c = p % N;
@@ -697,8 +698,24 @@ __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
         d1 = make_float2(w00 * ib * qb.x + w01 * ic * qc.x + w10 * ie * qe.x + w11 * iF * qf.x,
                          w00 * ib * qb.y + w01 * ic * qc.y + w10 * ie * qe.y + w11 * iF * qf.y);
       }
-      const float2 sp = __ldg((const float2*)(a.Sp + p)), sdp = __ldg((const float2*)(a.Sdp + p));
-      const float4 cp = __ldg((const float4*)(a.Cp + p));
+      float2 sp = __ldg((const float2*)(a.Sp + p)), sdp = __ldg((const float2*)(a.Sdp + p));
+      float4 cp = __ldg((const float4*)(a.Cp + p));
+      if constexpr (OPR) {
+        const float4 P2 = *(const float4*)(p0 + p);
+        const float2 Pa = make_float2(P2.x, P2.y), Pb = make_float2(P2.z, P2.w);
+        sp.x += cabs2(Pa);
+        sp.y += cabs2(Pb);
+        if (a.update_probe) {
+          const float4 D2 = opr_pair(a.opr_dU, wsh, a.K, NN, p);
+          const float2 ea = make_float2(D2.x, D2.y), eb = make_float2(D2.z, D2.w);
+          const float2 ca = cmulc(Pa, ea), cb = cmulc(Pb, eb);
+          cp = make_float4(cp.x + ca.x, cp.y + ca.y, cp.z + cb.x, cp.w + cb.y);
+          sdp.x += cabs2(ea);
+          sdp.y += cabs2(eb);
+          const float4 h2 = __ldcs((const float4*)(h_s + p));
+          b2 += ea.x * h2.x + ea.y * h2.y + eb.x * h2.z + eb.y * h2.w;   // Re(conj(dP_j0) h_j0)
+        }
+      }
       const float2 g0 = make_float2(g2.x, g2.y), g1 = make_float2(g2.z, g2.w);
       const float2 o0 = make_float2(o2.x, o2.y), o1 = make_float2(o2.z, o2.w);
       A11 += cabs2(d0) * sp.x + cabs2(d1) * sp.y;
@@ -707,32 +724,6 @@ __global__ void __launch_bounds__(T, 1024 / T) k_pass2(Pass2Args a) {
       A22 += cabs2(o0) * sdp.x + cabs2(o1) * sdp.y;
       b1 += d0.x * g0.x + d0.y * g0.y + d1.x * g1.x + d1.y * g1.y;       // Re(conj(d) g)
     }
-  } else
-#pragma unroll 1
-  for (int p = tid; p < NN; p += T) {
-    const int r = p / N, c = p % N;
-    const float2 g = __ldg(g_s + p);   // kept in L2: the update reads g again
-    const float2 o = __ldcs(o_s + p);
-    float2 d = make_float2(0.f, 0.f);
-    if (a.update_object) d = dohat(a.acc + (size_t)(ty + r) * a.W + (tx + c), a.W, w00, w01, w10, w11, damp);
-    float sp = __ldg(a.Sp + p), sdp = __ldg(a.Sdp + p);
-    float2 cp = __ldg(a.Cp + p);
-    if (opr) {
-      const float2 P0 = p0[p];
-      sp += cabs2(P0);
-      if (a.update_probe) {
-        const float2 d0 = opr_pixel(a.opr_dU, wsh, a.K, NN, p);
-        cp = cadd(cp, cmulc(P0, d0));
-        sdp += cabs2(d0);
-        const float2 h0 = __ldcs(h_s + p);
-        b2 += d0.x * h0.x + d0.y * h0.y;     // Re(conj(dP_j0) h_j0)
-      }
-    }
-    A11 += cabs2(d) * sp;
-    const float2 od = cmulc(d, o);           // conj(d) o
-    A12 += od.x * cp.x - od.y * cp.y;        // Re(conj(d) o Cp)
-    A22 += cabs2(o) * sdp;
-    b1 += d.x * g.x + d.y * g.y;             // Re(conj(d) g)
   }
   if (a.update_probe) {
     // b2 = Re sum_k <dP_k, h_k> over the shared modes: their planes are
