@@ -27,15 +27,19 @@ namespace ptycho {
 // Batch sums of the relaxed primary mode per probe pixel pair q. Block row
 // blockIdx.y takes slots [chunk * y, chunk * (y + 1)) of the batch and adds,
 // with vector atomics, dUacc_m += sum_j w_jm h_j0 and (when D is set)
-// D_m += sum_j w_jm^2 |o_j|^2.
+// D_m += sum_j w_jm^2 |o_j|^2. The slots' validity and weights are staged in
+// shared memory, RS slots at a time, so that the loop over the slots waits
+// only on the h and o loads, two slots' loads in flight (added in slot order).
 template <int KM>
 __global__ void __launch_bounds__(256) k_opr_reduce(int NN, int M, int K, int nb, int chunk, int b0,
                                                     const int* __restrict__ order, const float* __restrict__ w,
                                                     const float2* __restrict__ h_s, const float2* __restrict__ o_s,
                                                     const int* __restrict__ valid, float2* dUacc, float* D) {
+  constexpr int RS = 64;
+  __shared__ int ok_s[RS];
+  __shared__ float w_s[RS][KM];
   const int NP = NN / 2;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= NP) return;
   const int i0 = blockIdx.y * chunk, i1 = min(nb, i0 + chunk);
   float4 s[KM];
   float2 d[KM];
@@ -44,27 +48,53 @@ __global__ void __launch_bounds__(256) k_opr_reduce(int NN, int M, int K, int nb
     s[m] = make_float4(0.f, 0.f, 0.f, 0.f);
     d[m] = make_float2(0.f, 0.f);
   }
-  for (int i = i0; i < i1; ++i) {
-    if (!valid[i]) continue;
-    const int e = b0 + i;
-    const int j = order ? order[e] : e;
-    const float4 h = __ldg((const float4*)(h_s + (size_t)i * M * NN) + q);
-    float oa0 = 0.f, oa1 = 0.f;
-    if (D) {
-      const float4 o = __ldg((const float4*)(o_s + (size_t)i * NN) + q);
-      oa0 = o.x * o.x + o.y * o.y;
-      oa1 = o.z * o.z + o.w * o.w;
-    }
+  auto add = [&](int r, const float4& h, const float4& o) {
+    const float oa0 = o.x * o.x + o.y * o.y, oa1 = o.z * o.z + o.w * o.w;
 #pragma unroll
     for (int m = 0; m < KM; ++m) {
       if (m < K) {
-        const float wm = __ldg(w + (size_t)j * K + m), w2 = wm * wm;
+        const float wm = w_s[r][m], w2 = wm * wm;
         s[m].x = fmaf(wm, h.x, s[m].x); s[m].y = fmaf(wm, h.y, s[m].y);
         s[m].z = fmaf(wm, h.z, s[m].z); s[m].w = fmaf(wm, h.w, s[m].w);
         d[m].x = fmaf(w2, oa0, d[m].x); d[m].y = fmaf(w2, oa1, d[m].y);
       }
     }
+  };
+  for (int t0 = i0; t0 < i1; t0 += RS) {
+    const int n = min(RS, i1 - t0);
+    __syncthreads();   // the previous round's staging is consumed
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const int i = t0 + r;
+      const int ok = valid[i];   // (an invalid slot's position index may be out of range)
+      ok_s[r] = ok;
+      if (ok) {
+        const int e = b0 + i;
+        const int j = order ? order[e] : e;
+        for (int m = 0; m < K; ++m) w_s[r][m] = __ldg(w + (size_t)j * K + m);
+      }
+    }
+    __syncthreads();
+    if (q < NP) {
+      int r = 0;
+      for (; r + 1 < n; r += 2) {
+        const bool v0 = ok_s[r] != 0, v1 = ok_s[r + 1] != 0;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        const size_t i = (size_t)(t0 + r);
+        const float4 h0 = v0 ? __ldg((const float4*)(h_s + i * M * NN) + q) : z;
+        const float4 h1 = v1 ? __ldg((const float4*)(h_s + (i + 1) * M * NN) + q) : z;
+        const float4 o0 = (v0 && D) ? __ldg((const float4*)(o_s + i * NN) + q) : z;
+        const float4 o1 = (v1 && D) ? __ldg((const float4*)(o_s + (i + 1) * NN) + q) : z;
+        if (v0) add(r, h0, o0);
+        if (v1) add(r + 1, h1, o1);
+      }
+      if (r < n && ok_s[r]) {
+        const size_t i = (size_t)(t0 + r);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        add(r, __ldg((const float4*)(h_s + i * M * NN) + q), D ? __ldg((const float4*)(o_s + i * NN) + q) : z);
+      }
+    }
   }
+  if (q >= NP) return;
 #pragma unroll
   for (int m = 0; m < KM; ++m) {
     if (m < K) {
